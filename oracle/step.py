@@ -1,0 +1,449 @@
+"""One time step of the axion Monte-Carlo operators on one cell, plain FP64.
+
+Test infrastructure only (imported by tests/, smoke() and bench.py's CPU
+baseline). Nothing here is blocked, fused or reordered: each operator is
+applied to the cell's particle lists in the order the step defines.
+
+Operators and the passages they follow:
+* absorb_cell  - Primakoff a->gamma (Sec. II.F.1, last paragraph) and the
+  detailed-balance absorption of the thermal-bath channels (Sec. II.I,
+  Eq. gamma_abs, P_abs = 1 - exp(-Gamma_abs dt)).
+* emit_cell    - Primakoff gamma->a on photons (Sec. II.F, Eqs. prim_rate,
+  prim_prob, lambda_P, weight depletion) and Compton-like / bremsstrahlung
+  emission on electrons (Sec. II.D.1 Eq. lambda_macro, II.D.2 Eqs. lambda_eff,
+  wa_rescaled, II.G, II.H).
+* feedback_cell - cell moments, affine remap and temperature relaxation
+  (Sec. II.J, Eqs. cell_moments to b_def, Te_est, Te_relax).
+* init_cell    - the synthetic initial plasma (NR Maxwellian electrons, Planck
+  photons at T_e, optional MB-equilibrium axions).
+
+Readings of the paper that both implementations share (the paper is silent on
+each): step order absorb -> emit -> feedback; Philox4x32-10 counters
+(step, cell, particle, stream<<24 | sub); decisions use one 32-bit word per
+particle, word (i & 3) of block (i >> 2); event j of particle i uses block
+(step, cell, i, stream<<24 | j) with words (cos theta, phi, energy); new axions
+are appended after the survivors, photon products first (photon order), then
+electron products (electron order, Compton events before bremsstrahlung
+events); removed particles leave holes that are filled by the survivors found
+beyond the new count, in ascending order ("tail fill"); weights are binary32
+quantities and depletion is evaluated in binary32 because it decides whether
+the parent survives.
+"""
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+from scipy import special
+
+from . import constants as K
+from . import spectra
+from .philox import philox4x32_10, uniform23, split_seed
+from .plasma import Params, CellState, primakoff_F, absorption_rate, cell_state
+from .poisson import cap_lambda, poisson_count
+
+CH_PRIMAKOFF = 1
+CH_COMPTON = 2
+CH_BREMS = 4
+
+STREAM_PRIM_FWD = 0
+STREAM_COMPTON = 1
+STREAM_BREMS = 2
+STREAM_PRIM_INV = 3
+STREAM_ABSORB = 4
+STREAM_EV_COMPTON = 5
+STREAM_EV_BREMS = 6
+STREAM_INIT_E = 8
+STREAM_INIT_G = 9
+STREAM_INIT_A = 10
+INIT_STEP = 0xFFFFFFFF
+
+F32 = np.float32
+
+
+@dataclass
+class Species:
+    """One species' particles in a cell, in slot order; p in m_e c, positions in cell units."""
+    w: np.ndarray
+    px: np.ndarray
+    py: np.ndarray
+    pz: np.ndarray
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+
+    @staticmethod
+    def empty():
+        e = np.zeros(0)
+        return Species(e.copy(), e.copy(), e.copy(), e.copy(), e.copy(), e.copy(), e.copy())
+
+    def __len__(self):
+        return len(self.w)
+
+    def fields(self):
+        return [self.w, self.px, self.py, self.pz, self.x, self.y, self.z]
+
+    def take(self, idx):
+        return Species(*[f[idx] for f in self.fields()])
+
+    def concat(self, other):
+        return Species(*[np.concatenate([a, b]) for a, b in zip(self.fields(), other.fields())])
+
+    def copy(self):
+        return Species(*[f.copy() for f in self.fields()])
+
+    def pmag(self):
+        return np.sqrt(self.px ** 2 + self.py ** 2 + self.pz ** 2)
+
+
+@dataclass
+class StepTally:
+    """Per-cell bookkeeping of one step (energies in keV, momenta in m_e c)."""
+    dE: float = 0.0
+    dP: np.ndarray = field(default_factory=lambda: np.zeros(3))
+    events: dict = field(default_factory=lambda: {"prim": 0, "compton": 0, "brems": 0, "prim_inv": 0})
+    absorbed: dict = field(default_factory=lambda: {"compton": 0, "brems": 0})
+    cap_hits: int = 0
+    clamp_hits: int = 0
+    n_g0: int = 0
+    new_axion_channel: np.ndarray = field(default_factory=lambda: np.zeros(0, dtype=np.int64))
+    new_axion_E: np.ndarray = field(default_factory=lambda: np.zeros(0))
+
+
+def _key(p: Params):
+    return split_seed(p.seed)
+
+
+def decision_uniforms(p: Params, step, cell, stream, n):
+    """u_i for particles i < n: word (i & 3) of block (step, cell, i >> 2, stream << 24)."""
+    if n == 0:
+        return np.zeros(0)
+    nq = (n + 3) // 4
+    ctr = np.zeros((nq, 4), dtype=np.uint32)
+    ctr[:, 0] = np.uint32(step & 0xFFFFFFFF)
+    ctr[:, 1] = np.uint32(cell)
+    ctr[:, 2] = np.arange(nq, dtype=np.uint32)
+    ctr[:, 3] = np.uint32(stream << 24)
+    return uniform23(philox4x32_10(ctr, _key(p)).reshape(-1)[:n])
+
+
+def event_uniforms(p: Params, step, cell, stream, idx, sub):
+    """Four uniforms of block (step, cell, idx, stream << 24 | sub), shape (m, 4)."""
+    idx = np.asarray(idx, dtype=np.int64)
+    m = len(idx)
+    ctr = np.zeros((m, 4), dtype=np.uint32)
+    ctr[:, 0] = np.uint32(step & 0xFFFFFFFF)
+    ctr[:, 1] = np.uint32(cell)
+    ctr[:, 2] = idx.astype(np.uint32)
+    ctr[:, 3] = (np.uint32(stream << 24) | np.asarray(sub, dtype=np.uint32))
+    return uniform23(philox4x32_10(ctr, _key(p)))
+
+
+def isotropic(u_cos, u_phi):
+    """Unit vectors with cos(theta) = 2u - 1 and phi = 2 pi u."""
+    ct = 2.0 * u_cos - 1.0
+    st = np.sqrt(np.maximum(0.0, 1.0 - ct * ct))
+    ph = 2.0 * math.pi * u_phi
+    return st * np.cos(ph), st * np.sin(ph), ct
+
+
+def tail_fill(keep):
+    """New slot -> old index after removing ~keep: holes below the survivor
+    count take, in ascending order, the survivors found at or beyond it."""
+    keep = np.asarray(keep, dtype=bool)
+    ns = int(keep.sum())
+    idx = np.arange(len(keep))
+    order = np.arange(ns)
+    holes = idx[:ns][~keep[:ns]]
+    movers = idx[ns:][keep[ns:]]
+    order[holes] = movers
+    return order
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float64).astype(F32)
+
+
+def deplete(w_parent, K, w_prod):
+    """Weight depletion of a parent by K products of weight w_prod (Sec. II.F.1).
+
+    If K w_prod exceeds the parent weight the products share the parent weight
+    equally (reading: number is conserved exactly). Evaluated in binary32.
+    Returns (product weight, remaining parent weight, clamped flag)."""
+    w32 = f32(w_parent)
+    wp32 = f32(w_prod)
+    k32 = np.asarray(K).astype(F32)
+    conv = (k32 * wp32).astype(F32)
+    over = (np.asarray(K) > 0) & (conv > w32)
+    safe_k = np.where(np.asarray(K) > 0, k32, F32(1.0))
+    wprod = np.where(over, (w32 / safe_k).astype(F32), wp32)
+    wrem = np.where(over, F32(0.0), (w32 - conv).astype(F32))
+    return wprod.astype(np.float64), wrem.astype(np.float64), over
+
+
+def primakoff_prob(cs: CellState, p: Params, omega_keV, mult=1.0):
+    """P = 1 - exp(-m Gamma(omega) dt) (Eqs. prim_rate, prim_prob)."""
+    s = 4.0 * np.asarray(omega_keV) ** 2 / cs.kappa_keV ** 2
+    return -np.expm1(-mult * cs.Gamma0_P * primakoff_F(s) * p.dt_phys_s)
+
+
+def _repeat_products(parent: Species, K, wprod, pos_from: Species = None):
+    """Products in parent order, K[i] copies of parent i with weight wprod[i]."""
+    idx = np.repeat(np.arange(len(K)), K)
+    src = parent if pos_from is None else pos_from
+    return Species(np.asarray(wprod)[idx], parent.px[idx], parent.py[idx], parent.pz[idx],
+                   src.x[idx], src.y[idx], src.z[idx])
+
+
+def absorb_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally):
+    """Inverse operators on the axions present at the start of the step."""
+    a = parts["a"]
+    tally.n_g0 = len(parts["g"])
+    n = len(a)
+    if n == 0:
+        return
+    omega = a.pmag() * K.ME_C2_KEV
+    w = a.w.copy()
+    if mask & CH_PRIMAKOFF:
+        P = primakoff_prob(cs, p, omega, p.prim_inverse_mult)
+        lam = w * P / F32(p.w_gref).astype(np.float64)
+        lam_eff, fac, capped = cap_lambda(lam, p.lambda_cap)
+        u = decision_uniforms(p, step, cell, STREAM_PRIM_INV, n)
+        Kc = poisson_count(u, lam_eff)
+        wprod, w, over = deplete(w, Kc, F32(p.w_gref).astype(np.float64) * fac)
+        tally.events["prim_inv"] += int(Kc.sum())
+        tally.cap_hits += int(capped.sum())
+        tally.clamp_hits += int(over.sum())
+        if Kc.sum() > 0:
+            parts["g"] = parts["g"].concat(_repeat_products(a, Kc, wprod))
+    keep = w > 0
+    want_c = bool(mask & CH_COMPTON)
+    want_b = bool(mask & CH_BREMS)
+    if want_c or want_b:
+        E = omega
+        tau_c = absorption_rate(cs, "compton", E, p) * p.dt_phys_s if want_c else np.zeros(n)
+        tau_b = absorption_rate(cs, "brems", E, p) * p.dt_phys_s if want_b else np.zeros(n)
+        tau = tau_c + tau_b
+        if p.absorb_mode == 0:
+            P_abs = -np.expm1(-tau)
+            u = decision_uniforms(p, step, cell, STREAM_ABSORB, n)
+            absorbed = keep & (f32(u) < f32(P_abs))
+            tally.dE += float(np.sum(w[absorbed] * omega[absorbed]))
+            tally.dP += np.array([np.sum(w[absorbed] * a.px[absorbed]),
+                                  np.sum(w[absorbed] * a.py[absorbed]),
+                                  np.sum(w[absorbed] * a.pz[absorbed])])
+            frac_c = f32(np.where(tau > 0, tau_c / np.where(tau > 0, tau, 1.0), 0.0))
+            safeP = np.where(P_abs > 0, P_abs, 1.0)
+            is_c = (f32(u) / f32(safeP)).astype(F32) < frac_c
+            tally.absorbed["compton"] += int(np.sum(absorbed & is_c))
+            tally.absorbed["brems"] += int(np.sum(absorbed & ~is_c))
+            keep = keep & ~absorbed
+        else:
+            w_new = (f32(w) * f32(np.exp(-tau))).astype(np.float64)
+            lost = w - w_new
+            tally.dE += float(np.sum(lost * omega))
+            tally.dP += np.array([np.sum(lost * a.px), np.sum(lost * a.py), np.sum(lost * a.pz)])
+            w = w_new
+            keep = keep & (w > 0)
+    a2 = a.copy()
+    a2.w = w
+    parts["a"] = a2.take(tail_fill(keep))
+
+
+def emit_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, n_g0=None):
+    """Forward operators: Primakoff on photons present at step start, then
+    thermal-bath emission on electrons; products are appended to the axions."""
+    if n_g0 is None:
+        n_g0 = len(parts["g"])
+    g = parts["g"]
+    w_a = F32(p.w_a).astype(np.float64)
+    new_blocks = []
+    chan_blocks = []
+    energy_blocks = []
+    if (mask & CH_PRIMAKOFF) and n_g0 > 0:
+        g0 = g.take(np.arange(n_g0))
+        omega = g0.pmag() * K.ME_C2_KEV
+        P = primakoff_prob(cs, p, omega)
+        lam = g0.w * P / w_a
+        lam_eff, fac, capped = cap_lambda(lam, p.lambda_cap)
+        u = decision_uniforms(p, step, cell, STREAM_PRIM_FWD, n_g0)
+        Kc = poisson_count(u, lam_eff)
+        wprod, wrem, over = deplete(g0.w, Kc, w_a * fac)
+        tally.events["prim"] += int(Kc.sum())
+        tally.cap_hits += int(capped.sum())
+        tally.clamp_hits += int(over.sum())
+        prods = _repeat_products(g0, Kc, wprod)
+        new_blocks.append(prods)
+        chan_blocks.append(np.full(len(prods), CH_PRIMAKOFF))
+        energy_blocks.append(np.repeat(omega, Kc))
+        g = g.copy()
+        g.w[:n_g0] = wrem
+    parts["g"] = g.take(tail_fill(g.w > 0))
+    e = parts["e"]
+    ne = len(e)
+    if (mask & (CH_COMPTON | CH_BREMS)) and ne > 0:
+        per_channel = []
+        for ch, rate, dstream, estream, icdf in (
+                (CH_COMPTON, cs.Gamma_C, STREAM_COMPTON, STREAM_EV_COMPTON, spectra.compton_icdf),
+                (CH_BREMS, cs.Gamma_B, STREAM_BREMS, STREAM_EV_BREMS,
+                 lambda uu: spectra.brems_icdf(p.brems_gamma_shape, uu))):
+            if not (mask & ch):
+                per_channel.append(None)
+                continue
+            lam = e.w * rate * p.dt_phys_s / w_a
+            lam_eff, fac, capped = cap_lambda(lam, p.lambda_cap)
+            u = decision_uniforms(p, step, cell, dstream, ne)
+            Kc = poisson_count(u, lam_eff)
+            tally.cap_hits += int(capped.sum())
+            parent = np.repeat(np.arange(ne), Kc)
+            sub = np.concatenate([np.arange(k) for k in Kc]) if Kc.sum() > 0 else np.zeros(0, dtype=np.int64)
+            uu = event_uniforms(p, step, cell, estream, parent, sub)
+            xE = icdf(uu[:, 2]) if len(parent) else np.zeros(0)
+            E = xE * cs.T_keV
+            dx, dy, dz = isotropic(uu[:, 0], uu[:, 1]) if len(parent) else (np.zeros(0),) * 3
+            pm = E / K.ME_C2_KEV
+            wv = f32(w_a * fac[parent]).astype(np.float64)
+            prods = Species(wv, pm * dx, pm * dy, pm * dz, e.x[parent], e.y[parent], e.z[parent])
+            tally.dE -= float(np.sum(wv * E))
+            tally.dP -= np.array([np.sum(wv * prods.px), np.sum(wv * prods.py), np.sum(wv * prods.pz)])
+            name = "compton" if ch == CH_COMPTON else "brems"
+            tally.events[name] += int(Kc.sum())
+            per_channel.append((parent, prods, E, ch))
+        # electron order, Compton events of an electron before its bremsstrahlung events
+        pieces = [pc for pc in per_channel if pc is not None]
+        if pieces:
+            parent_all = np.concatenate([pc[0] for pc in pieces])
+            chan_rank = np.concatenate([np.full(len(pc[0]), r) for r, pc in enumerate(pieces)])
+            order = np.lexsort((chan_rank, parent_all))   # stable: event order kept within a channel
+            prods_all = pieces[0][1]
+            for pc in pieces[1:]:
+                prods_all = prods_all.concat(pc[1])
+            E_all = np.concatenate([pc[2] for pc in pieces])
+            ch_all = np.concatenate([np.full(len(pc[0]), pc[3]) for pc in pieces])
+            new_blocks.append(prods_all.take(order))
+            chan_blocks.append(ch_all[order])
+            energy_blocks.append(E_all[order])
+    if new_blocks:
+        new = new_blocks[0]
+        for b in new_blocks[1:]:
+            new = new.concat(b)
+        parts["a"] = parts["a"].concat(new)
+        tally.new_axion_channel = np.concatenate(chan_blocks)
+        tally.new_axion_E = np.concatenate(energy_blocks)
+
+
+@dataclass
+class FeedbackResult:
+    T_new: float
+    res_E: float
+    res_P: np.ndarray
+    S: float
+    b: np.ndarray
+    var: float
+    var_new: float
+    applied_E: float
+    applied_P: np.ndarray
+    W: float
+
+
+def feedback_cell(cs: CellState, parts, p: Params, tally: StepTally, res_E=0.0, res_P=None):
+    """Affine remap of the electron momenta (Sec. II.J.1) and temperature
+    relaxation (Sec. II.J.2). Energies in keV; mu = 1 (electrons)."""
+    if res_P is None:
+        res_P = np.zeros(3)
+    dE_req = tally.dE + res_E
+    dP_req = tally.dP + res_P
+    e = parts["e"]
+    T = cs.T_keV
+    if len(e) == 0 or np.sum(e.w) <= 0:
+        return FeedbackResult(T, dE_req, dP_req.copy(), 1.0, np.zeros(3), 0.0, 0.0, 0.0, np.zeros(3), 0.0)
+    pv = np.stack([e.px, e.py, e.pz], axis=1)
+    W = float(np.sum(e.w))                                   # Eq. cell_moments
+    Pm = np.sum(e.w[:, None] * pv, axis=0)
+    U2 = float(np.sum(e.w * np.sum(pv * pv, axis=1)))
+    mu = 1.0
+    dE = dE_req / K.ME_C2_KEV                                # m_e c^2 units
+    delta = dP_req / W                                       # Eq. delta_def
+    dE_bulk = (2.0 * np.dot(delta, Pm) + W * np.dot(delta, delta)) / (2.0 * mu)   # Eq. dE_bulk
+    dE_th = dE - dE_bulk                                     # Eq. dE_th
+    var = U2 - np.dot(Pm, Pm) / W                            # Eq. var_unnormalized
+    if var > 0:
+        var_new = max(0.0, var + 2.0 * mu * dE_th)           # Eq. var_new
+        S = math.sqrt(var_new / var)                         # Eq. s_def
+    else:
+        var_new = var
+        S = 1.0
+    b = (1.0 - S) * Pm / W + delta                           # Eq. b_def
+    pnew = S * pv + b                                        # Eq. affine_map
+    d = pnew - pv
+    applied_E = float(np.sum(e.w * np.sum(d * (2.0 * pv + d), axis=1)) / 2.0) * K.ME_C2_KEV
+    applied_P = np.sum(e.w[:, None] * d, axis=0)
+    e2 = e.copy()
+    e2.px, e2.py, e2.pz = pnew[:, 0].copy(), pnew[:, 1].copy(), pnew[:, 2].copy()
+    parts["e"] = e2
+    T_new = T
+    if p.T_mode == 2:
+        T_est = K.ME_C2_KEV / 3.0 * var_new / W              # Eq. Te_est
+        T_new = (1.0 - p.relax_r) * T + p.relax_r * T_est    # Eq. Te_relax
+        T_new = min(max(T_new, p.T_floor_keV), p.T_ceil_keV)
+    return FeedbackResult(T_new, dE_req - applied_E, dP_req - applied_P, S, b, var, var_new,
+                          applied_E, applied_P, W)
+
+
+@dataclass
+class CellInput:
+    T_keV: float
+    n_ion: np.ndarray
+    Z: np.ndarray
+    A: np.ndarray
+
+
+def step_cell(ci: CellInput, parts, p: Params, step, cell, mask, res_E=0.0, res_P=None, feedback=True):
+    """absorb -> emit -> feedback for one cell; returns (tally, feedback result)."""
+    cs = cell_state(ci.T_keV, ci.n_ion, ci.Z, ci.A, p)
+    tally = StepTally()
+    absorb_cell(cs, parts, p, step, cell, mask, tally)
+    emit_cell(cs, parts, p, step, cell, mask, tally, n_g0=tally.n_g0)
+    fb = None
+    if feedback:
+        fb = feedback_cell(cs, parts, p, tally, res_E, res_P)
+    return tally, fb
+
+
+def photon_number_density(T_keV):
+    """Planck photon density 2 zeta(3) T^3 / (pi^2 (hbar c)^3) [cm^-3]."""
+    return 2.0 * special.zeta(3.0) * T_keV ** 3 / (math.pi ** 2 * K.HBARC_KEV_CM ** 3)
+
+
+def init_cell(p: Params, cell, T_keV, n_e, volume_cm3, n_el, n_ph, n_ax):
+    """Synthetic initial state of one cell: n_el NR-Maxwellian electrons of
+    weight n_e V/n_el, n_ph Planck photons of weight n_gamma V/n_ph, and n_ax
+    MB-equilibrium axions of weight w_a; positions uniform in the cell."""
+    out = {}
+    key_streams = (("e", STREAM_INIT_E, n_el), ("g", STREAM_INIT_G, n_ph), ("a", STREAM_INIT_A, n_ax))
+    for name, stream, n in key_streams:
+        if n == 0:
+            out[name] = Species.empty()
+            continue
+        idx = np.arange(n)
+        b0 = event_uniforms(p, INIT_STEP, cell, stream, idx, np.zeros(n, dtype=np.int64))
+        b1 = event_uniforms(p, INIT_STEP, cell, stream, idx, np.ones(n, dtype=np.int64))
+        if name == "e":
+            sigma = math.sqrt(T_keV / K.ME_C2_KEV)
+            r1 = np.sqrt(-2.0 * np.log(b0[:, 0]))
+            r2 = np.sqrt(-2.0 * np.log(b0[:, 2]))
+            px = sigma * r1 * np.cos(2.0 * math.pi * b0[:, 1])
+            py = sigma * r1 * np.sin(2.0 * math.pi * b0[:, 1])
+            pz = sigma * r2 * np.cos(2.0 * math.pi * b0[:, 3])
+            w = np.full(n, f32(n_e * volume_cm3 / n_el).astype(np.float64))
+        else:
+            if name == "g":
+                xE = spectra.planck_icdf(b0[:, 0])
+                w = np.full(n, f32(photon_number_density(T_keV) * volume_cm3 / n_ph).astype(np.float64))
+            else:
+                xE = spectra.mb_axion_icdf(b0[:, 0])
+                w = np.full(n, F32(p.w_a).astype(np.float64))
+            pm = xE * T_keV / K.ME_C2_KEV
+            dx, dy, dz = isotropic(b0[:, 1], b0[:, 2])
+            px, py, pz = pm * dx, pm * dy, pm * dz
+        out[name] = Species(w, px, py, pz, b1[:, 0].copy(), b1[:, 1].copy(), b1[:, 2].copy())
+    return out
