@@ -1,0 +1,373 @@
+"""Throughput of the axion Monte-Carlo step on GB300.
+
+One "step" is one fused pass of the whole hot path (absorb -> emit ->
+feedback -> temperature update) over every cell of the workload. The default
+workload is the 2-D 256x256 all-channel relaxation: T_e = 3 keV, 90 % H +
+10 % He by number at n_e = 6e25 cm^-3, 512 Maxwellian electrons and 256
+Planck photons per cell, axion-free start, forward and inverse operators of
+all three channels, binary32 rates with FP64 exchange buffers and temperature.
+
+Metric: particle-steps/s = sum over timed steps of the particles (electrons +
+photons + axions) present at the start of the step / device time. Under
+torchrun every rank runs its own full-size shard (weak scaling, no data-path
+collective) and rank 0 reports the aggregate.
+
+--impl reference times the oracle (plain FP64 CPU) on bounded samples of the
+same workload on the host cores.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s, 3-channel emit+absorb; surrogate vs table at ≤1e-3 rate err"
+UNIT = "particle-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2604_24627_gb300 import workloads
+    w = workloads.config2()
+    wg = workloads.photon_weight(3.0, w.volume_cm3, w.n_ph)
+    w.params["w_a"] = float(np.float32(wg * w.w_a_over_w_gamma))
+    w.params["seed"] = 0
+    w.params["tally_enable"] = 0
+    return w
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(tot, ncells_steps, T_mode):
+    """Minimum DRAM bytes of the fused step (read once, write what changes):
+    electrons: w (4 B) each, plus p read and written (24 B) in remapped cells;
+    photons and axions present at the start: w, p (16 B) each;
+    each product: 28 B written + 12 B of parent position read;
+    per cell: rate record (64 B), three counts (12 B read + 12 B written),
+    and in evolved-T mode T (8 B read + 8 B written) and the record's
+    temperature half (32 B written)."""
+    products = tot["events_p"] + tot["events_c"] + tot["events_b"] + tot["events_pinv"]
+    b = 4.0 * tot["part_e"] + 16.0 * (tot["part_g"] + tot["part_a"]) + 24.0 * tot["remap_e"]
+    b += 40.0 * products
+    b += ncells_steps * (64.0 + 24.0 + (48.0 if T_mode == 2 else 0.0))
+    return b
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.5)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append((time.time(), parts))
+
+    def mark(self, which):
+        if which == "start":
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        inside = [p for t, p in self.samples if self.t0 is not None and self.t0 - 0.06 <= t <= self.t1 + 0.06]
+        use = inside if inside else [p for _, p in self.samples]
+        sm = [float(p[1]) for p in use if p[1].replace(".", "").isdigit()]
+        smax = [float(p[2]) for p in use if p[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for p in use:
+            for name, v in zip(names, p[5:9]):
+                if v.strip().lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(use), "samples_in_window": len(inside)}
+
+
+def oracle_state(w, ncells_sample):
+    """Initial state of the first cells of the workload from the oracle's own
+    sampler (same Philox streams as the library's sampler)."""
+    from oracle import step as ostep
+    from oracle.plasma import Params
+    prm = Params(**{k: v for k, v in w.params.items() if k in Params.__dataclass_fields__})
+    return [ostep.init_cell(prm, c, float(w.T_keV[c]), float(np.sum(w.Z * w.n_ion[c])), w.volume_cm3,
+                            w.n_el, w.n_ph, w.n_ax) for c in range(ncells_sample)]
+
+
+def cpu_baseline(w, seconds, state_cells, step0=7):
+    """Time the oracle, as it stands, on a bounded sample of the workload: the
+    given cells (all of their particles) are stepped once each, cycling with
+    new step indices, until `seconds` of CPU time have passed. Returns
+    particle-steps/s, cell-steps, particle-steps and seconds."""
+    from oracle import step as ostep
+    from oracle.plasma import Params
+    prm = Params(**{k: v for k, v in w.params.items() if k in Params.__dataclass_fields__})
+    done = 0
+    cell_steps = 0
+    t_work = 0.0
+    k = 0
+    while t_work < seconds:
+        c = k % len(state_cells)
+        parts = {s: v.copy() for s, v in state_cells[c].items()}
+        n = sum(len(v) for v in parts.values())
+        ci = ostep.CellInput(float(w.T_keV[c]), w.n_ion[c], w.Z, w.A)
+        t0 = time.perf_counter()
+        ostep.step_cell(ci, parts, prm, step0 + k // len(state_cells), c, w.mask)
+        t_work += time.perf_counter() - t0
+        done += n
+        cell_steps += 1
+        k += 1
+    return done / t_work, cell_steps, done, t_work
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step = one oracle step over a
+    bounded sample of cells of the same workload (FP64, host cores)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload()
+    state = oracle_state(w, 16)
+    # each step is a bounded sample: the whole run stays near two minutes
+    per_step = min(0.5, 120.0 / max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        cpu_baseline(w, 0.2, state)
+    vals = []
+    total_p = 0
+    total_t = 0.0
+    cells_total = 0
+    for _ in range(args.steps):
+        v, cells, parts, t = cpu_baseline(w, per_step, state)
+        total_p += parts
+        total_t += t
+        cells_total += cells
+        vals.append(v)
+    value = total_p / total_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (uniform thermal plasma, seeded)",
+            "config": {"workload": w.name, "cells": w.ncells, "electrons_per_cell": w.n_el,
+                       "photons_per_cell": w.n_ph, "parallelism": "oracle on host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d cell-steps of the workload (%d particle-steps) over %d steps"
+                                       % (cells_total, total_p, args.steps)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2604_24627_gb300 import AxionPlasma, _lib
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload()
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        pl = AxionPlasma(w.ncells, w.T_keV, w.n_ion, w.Z, w.A, w.volume_cm3, w.caps, w.params, device=dev,
+                         cell_index_base=rank * w.ncells, stream=stream)
+        pl.sample(w.n_el, w.n_ph, w.n_ax)
+    torch.cuda.synchronize(dev)
+
+    for s in range(args.warmup):
+        pl.step(s, w.mask)
+    pl.tally()  # clears counters: the timed region starts from zero
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.mark("start")
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[2 * k].record(stream)
+        pl.step(args.warmup + k, w.mask)
+        ev[2 * k + 1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks.mark("end")
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    launch_ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)]
+    H, tot = pl.tally()
+    particles = tot["part_e"] + tot["part_g"] + tot["part_a"]
+    cell_steps = tot["cell_steps"]
+    alg = algorithmic_bytes(tot, cell_steps, w.params.get("T_mode", 0))
+    if world > 1:
+        t = torch.tensor([elapsed_ms, particles], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        elapsed_ms, particles = float(mx[0]), float(t[1])
+
+    # end to end through the public API with host buffers: every step copies
+    # the whole plasma state host -> device, runs the step, copies it back
+    e2e = None
+    if args.e2e_steps > 0:
+        tensors = []
+        for slab in pl.slabs.values():
+            tensors += list(slab.data.values()) + [slab.count]
+        tensors += [pl.T]
+        host = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in tensors]
+        for h, t in zip(host, tensors):
+            h.copy_(t)
+        nbytes = sum(t.numel() * t.element_size() for t in tensors)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        pl.tally()
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for k in range(args.e2e_steps):
+                for h, t in zip(host, tensors):
+                    t.copy_(h, non_blocking=True)
+                pl.step(args.warmup + args.steps + k, w.mask)
+                for h, t in zip(host, tensors):
+                    h.copy_(t, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        _, tot_e = pl.tally()
+        p_e = tot_e["part_e"] + tot_e["part_g"] + tot_e["part_a"]
+        e_ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([e_ms, p_e], dtype=torch.float64, device=dev)
+            mx = t.clone()
+            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            e_ms, p_e = float(mx[0]), float(t[1])
+        e2e = {"value": p_e / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
+
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        avg_launch_s = statistics.mean(launch_ms) * 1e-3
+        bytes_per_launch = alg / args.steps
+        achieved = bytes_per_launch / avg_launch_s / 1e9
+        traffic = None
+        prof = os.path.join(ROOT, "profiles", "step_kernel_c2_traffic.json")
+        if os.path.exists(prof):
+            try:
+                with open(prof) as f:
+                    pj = json.load(f)
+                if pj.get("kernel_hash") == kernel_hash():
+                    traffic = pj.get("dram_bytes_per_launch")
+            except Exception:
+                traffic = None
+        value = particles / (elapsed_ms * 1e-3)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (uniform thermal plasma, seeded Philox sampler)",
+                "config": {"workload": w.name, "cells": w.ncells, "electrons_per_cell": w.n_el,
+                           "photons_per_cell": w.n_ph, "axions_at_start": w.n_ax, "channels": "all, fwd+inv",
+                           "T_mode": "evolved", "l2": "inputs larger than L2 (%.2f GB touched per step)"
+                           % (bytes_per_launch / 1e9),
+                           "parallelism": "cells sharded per GPU" if world > 1 else "single GPU"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                             "kernel": "axpic::step_kernel<7>",
+                             "algorithmic_bytes_per_launch": bytes_per_launch},
+                "gpu_launches": args.steps, "clocks": clk,
+                "counts": {"particle_steps": particles, "events_primakoff": tot["events_p"],
+                           "events_compton": tot["events_c"], "events_brems": tot["events_b"],
+                           "events_inverse": tot["events_pinv"], "remapped_cells": tot["remaps"]}}
+        if e2e:
+            line["e2e"] = e2e
+        if world == 1 and not args.no_cpu_baseline:
+            cells = [pl.cell(c) for c in range(64)]
+            from oracle import step as ostep
+            state = [{k: ostep.Species(*[np.asarray(d[k][f]) for f in ("w", "px", "py", "pz", "x", "y", "z")])
+                      for k in "ega"} for d in cells]
+            v, ncell, npart, t = cpu_baseline(w, args.cpu_seconds, state_cells=state)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "%d cells of the workload stepped once (%d particle-steps, %.1f s)"
+                                              % (ncell, npart, t)}
+        print(json.dumps(line))
+    pl.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("step.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2604_24627_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,256 @@
+/*
+ * axpic.h - C ABI of the GB300 (sm_103a) axion Monte-Carlo operators for
+ * particle-in-cell plasmas.
+ *
+ * The library implements, per cell and per macroparticle, the three axion
+ * channels of the paper "An axion framework for Particle-in-Cell codes with
+ * Monte-Carlo sampling": screened Primakoff conversion (Sec. II.F), Compton-like
+ * photoproduction (Sec. II.G) and electron-ion / electron-electron
+ * bremsstrahlung (Sec. II.H), their detailed-balance inverse operators
+ * (Sec. II.I), Poisson macro-event sampling with cap-and-rescale variance
+ * control (Sec. II.D), and the conservative cell-local energy/momentum
+ * feedback with temperature evolution (Sec. II.J).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Units: energies in keV, momenta in m_e c, times in seconds, densities in
+ *   cm^-3, volumes in cm^3, couplings g_agg in GeV^-1 and g_ae dimensionless.
+ * - Particles live in cell-sorted slabs. Species s of cell c occupies slots
+ *   [c*capacity, c*capacity + count[c]) of each of its seven binary32 arrays
+ *   (w, px, py, pz, x, y, z); positions are fractions of the cell in [0, 1).
+ *   capacity must be a multiple of 4 and every array 16-byte aligned.
+ * - Pointers marked "device" are CUDA device pointers owned by the caller; the
+ *   library never frees them. Pointers marked "host" are read or written
+ *   synchronously before the call returns. The library owns only its scratch
+ *   (cell records, feedback buffers, counters, tallies) and its sampling
+ *   tables, allocated by axpic_init_plasma and released by axpic_destroy.
+ * - Step calls (axpic_absorb, axpic_emit, axpic_feedback, axpic_step,
+ *   axpic_update_cells, axpic_sample_plasma) only enqueue kernels on the
+ *   context's stream: they neither allocate nor synchronise, so a sequence of
+ *   them can be captured in a CUDA graph. Arguments are validated on the host
+ *   first; an invalid call returns AXPIC_E_INVALID and launches nothing.
+ * - Errors found on the device (slab capacity exceeded, non-finite values)
+ *   are latched in a device flag and reported by the next synchronising call
+ *   (axpic_sync, axpic_tally_spectrum, axpic_destroy).
+ * - Random numbers: one Philox4x32-10 stream keyed by the 64-bit seed, with
+ *   counter (step, global cell index, particle, stream << 24 | sub), so a
+ *   result does not depend on launch shape or on how cells are sharded.
+ */
+#ifndef AXPIC_H
+#define AXPIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct axpic_ctx axpic_ctx; /* opaque; owned by the library */
+
+typedef enum {
+  AXPIC_OK = 0,
+  AXPIC_E_INVALID = 1,  /* bad argument; nothing was launched */
+  AXPIC_E_CAPACITY = 2, /* a slab overflowed; the excess products were dropped */
+  AXPIC_E_CUDA = 3,     /* a CUDA runtime call failed */
+  AXPIC_E_TIMEOUT = 4,  /* a bounded device wait gave up */
+  AXPIC_E_NUMERIC = 5   /* a non-finite value was produced */
+} axpic_status;
+
+/* Channel mask bits. */
+enum {
+  AXPIC_CH_PRIMAKOFF = 1, /* gamma + Z <-> a + Z (Sec. II.F) */
+  AXPIC_CH_COMPTON = 2,   /* gamma + e -> a + e in a blackbody bath (Sec. II.G) */
+  AXPIC_CH_BREMS = 4,     /* e + Z -> e + Z + a and e + e -> e + e + a (Sec. II.H) */
+  AXPIC_CH_ALL = 7
+};
+
+/* One particle species in cell-sorted SoA slabs (Sec. II.D.1: weighted
+ * macroparticles; Sec. II.B: p in m_e c). All pointers are device pointers of
+ * ncells*capacity binary32 values (count: ncells int32). */
+typedef struct {
+  float *w, *px, *py, *pz, *x, *y, *z;
+  int32_t *count;
+  int32_t capacity;
+} axpic_species;
+
+/* The plasma (Sec. II.E, Eqs. rho_def, qn_def). */
+typedef struct {
+  int32_t ncells;          /* cells owned by this context */
+  int32_t nspecies;        /* ion species, 1..8 */
+  int64_t cell_index_base; /* global index of cell 0 (keys the RNG; sharding) */
+  double *T_keV;           /* device [ncells] electron temperature, read/write */
+  const double *n_ion;     /* device [ncells*nspecies] ion densities, cm^-3 */
+  const double *Z;         /* host [nspecies] charge states */
+  const double *A;         /* host [nspecies] mass numbers */
+  double cell_volume_cm3;  /* volume represented by one cell */
+  axpic_species electrons, photons, axions;
+} axpic_plasma_desc;
+
+/* Operator options. Defaults (axpic_default_params) are the readings listed
+ * beside each field. */
+typedef struct {
+  double g_agg_GeV_inv;     /* axion-photon coupling, GeV^-1 (Eq. prim_xs) */
+  double g_ae;              /* axion-electron coupling (Eqs. epsC, eps_eZ) */
+  double dt_phys_s;         /* physical step, s (Eq. dt_phys) */
+  double w_a;               /* axion macroparticle weight (Eq. lambda_macro) */
+  double w_gamma_ref;       /* weight of photons made by a->gamma; <= 0: w_a */
+  double lambda_cap;        /* Poisson-mean cap (Eq. lambda_eff); <= 0: off.
+                               A ceiling of 64 always applies. */
+  int32_t kappa_mode;       /* 0 Debye (Eq. kappa_debye), 1 fixed kappa */
+  double kappa_fixed_keV;   /* used when kappa_mode == 1 */
+  int32_t prim_targets;     /* 0: sum_i Z_i^2 n_i over ions (Sec. II.F);
+                               1: all charges, n_eff */
+  double prim_inverse_mult; /* a->gamma rate = mult * gamma->a rate (1) */
+  int32_t eq_stats;         /* absorption target: 0 Maxwell-Boltzmann,
+                               1 Bose-Einstein (Sec. II.I) */
+  int32_t brems_ee;         /* 1: add e-e bremsstrahlung (Eq. eps_ee) */
+  int32_t absorb_mode;      /* 0 Bernoulli deletion, 1 weight reduction
+                               (Sec. II.I, P_abs) */
+  double brems_gamma_shape; /* Gamma(a) energy sampler shape (1.70) */
+  double relax_r;           /* temperature relaxation r (Eq. Te_relax) */
+  double T_floor_keV;       /* temperature clamp */
+  double T_ceil_keV;
+  int32_t T_mode;           /* 0 fixed, 1 prescribed field, 2 evolved (Sec. II.E) */
+  uint64_t seed;            /* Philox key */
+  int32_t tally_nbins;      /* emitted-spectrum histogram bins (160) */
+  double tally_Emax_keV;    /* histogram range [0, Emax) (80 keV) */
+  int32_t tally_enable;     /* 1: step calls accumulate the emitted spectrum */
+  int32_t diag_enable;      /* 1: feedback writes per-cell diagnostics */
+  int32_t threads_per_block;/* launch shape of the step kernel; 0: default */
+  int32_t reserved[7];
+} axpic_params;
+
+/* Number of doubles written by axpic_tally_spectrum into totals_out. */
+#define AXPIC_TOTALS_LEN 32
+/* Layout of totals_out. */
+enum {
+  AXPIC_T_NEMIT_P = 0, AXPIC_T_NEMIT_C, AXPIC_T_NEMIT_B, /* sum w' of emitted axions */
+  AXPIC_T_UEMIT_P, AXPIC_T_UEMIT_C, AXPIC_T_UEMIT_B,     /* sum w'E, keV */
+  AXPIC_T_EVENTS_P, AXPIC_T_EVENTS_C, AXPIC_T_EVENTS_B,  /* macro-events */
+  AXPIC_T_EVENTS_PINV,                                   /* a->gamma events */
+  AXPIC_T_ABSORBED_C, AXPIC_T_ABSORBED_B,                /* Bernoulli absorptions */
+  AXPIC_T_CAP_HITS, AXPIC_T_CLAMP_HITS, AXPIC_T_DROPPED,
+  AXPIC_T_N_AXIONS, AXPIC_T_U_AXIONS,                    /* alive: sum w, sum wE (keV) */
+  AXPIC_T_MACRO_AXIONS, AXPIC_T_MACRO_PHOTONS,
+  AXPIC_T_RESIDUAL_E,                                    /* sum of carried energy, keV */
+  AXPIC_T_N_PHOTONS, AXPIC_T_U_PHOTONS,
+  AXPIC_T_U_ELECTRONS,                                   /* NR kinetic, keV */
+  AXPIC_T_REMAPS,                                        /* cell remaps applied */
+  AXPIC_T_PART_E, AXPIC_T_PART_G, AXPIC_T_PART_A,        /* sum over step calls of the
+                                                            particles present at the start */
+  AXPIC_T_REMAP_E,                                       /* electrons in remapped cells */
+  AXPIC_T_CALLS                                          /* cell-steps processed */
+};
+
+/* Per-cell FP64 quantities returned by axpic_get_cell_info (Sec. II.E-II.H). */
+#define AXPIC_CELL_INFO_LEN 16
+enum {
+  AXPIC_CI_RHO = 0, AXPIC_CI_XH, AXPIC_CI_NE, AXPIC_CI_NEFF, AXPIC_CI_SZ,
+  AXPIC_CI_KAPPA, AXPIC_CI_QC, AXPIC_CI_QB, AXPIC_CI_GAMMA_C, AXPIC_CI_GAMMA_B,
+  AXPIC_CI_GAMMA0_P, AXPIC_CI_ETA, AXPIC_CI_T
+};
+
+/* Per-cell FP64 feedback diagnostics of the last feedback (Sec. II.J). */
+#define AXPIC_CELL_DIAG_LEN 16
+enum {
+  AXPIC_CD_DE = 0, AXPIC_CD_DPX, AXPIC_CD_DPY, AXPIC_CD_DPZ, /* this step's exchange */
+  AXPIC_CD_S_MINUS_1, AXPIC_CD_BX, AXPIC_CD_BY, AXPIC_CD_BZ,
+  AXPIC_CD_VAR, AXPIC_CD_VAR_NEW, AXPIC_CD_W,
+  AXPIC_CD_APPLIED_E, AXPIC_CD_RES_E, AXPIC_CD_RES_PX, AXPIC_CD_RES_PY, AXPIC_CD_RES_PZ
+};
+
+/* Fill *p with the default options. Never fails for a non-NULL p. */
+void axpic_default_params(axpic_params *p);
+
+/* Create a context for one plasma (Sec. II.E): validate the description,
+ * allocate the library's scratch, build the energy-sampling tables
+ * (Sec. II.G, II.H) and compute every cell's rate record (Sec. II.E-II.I).
+ * The particle slabs are used as they are (see axpic_sample_plasma).
+ * stream: a cudaStream_t (NULL: the legacy default stream) on which every
+ * later call of this context is enqueued. The only call that allocates,
+ * besides axpic_destroy which frees. Returns AXPIC_E_INVALID for a NULL or
+ * inconsistent description, AXPIC_E_CUDA if an allocation fails. */
+axpic_status axpic_init_plasma(axpic_ctx **out, const axpic_plasma_desc *desc,
+                               const axpic_params *params, void *stream);
+
+/* Fill the slabs with the synthetic initial plasma: per cell n_el
+ * non-relativistic Maxwellian electrons of weight n_e V/n_el, n_ph Planck
+ * photons at T_e of weight n_gamma V/n_ph (Sec. II.G, blackbody bath) and
+ * n_ax Maxwell-Boltzmann-equilibrium axions of weight w_a, with isotropic
+ * directions and uniform positions; counts are set. AXPIC_E_INVALID if a
+ * count exceeds its capacity. */
+axpic_status axpic_sample_plasma(axpic_ctx *ctx, int32_t n_el, int32_t n_ph, int32_t n_ax);
+
+/* Recompute every cell's rate record after the caller changed T_keV or
+ * n_ion (temperature mode "prescribed field", Sec. II.E). */
+axpic_status axpic_update_cells(axpic_ctx *ctx);
+
+/* Inverse operators on the axions present when the call starts (Sec. II.F.1
+ * last paragraph; Sec. II.I): Primakoff a->gamma conversion with weight
+ * depletion (photon products appended) and detailed-balance absorption of the
+ * thermal-bath channels, P_abs = 1 - exp(-Gamma_abs dt). Absorbed energy and
+ * momentum go to the cell exchange buffer (Sec. II.J). */
+axpic_status axpic_absorb(axpic_ctx *ctx, int64_t step, int32_t channel_mask);
+
+/* Forward operators (Sec. II.D, II.F-II.H): Primakoff gamma->a on the
+ * photons present before this step's axpic_absorb, Compton-like and
+ * bremsstrahlung emission on electrons, with Poisson macro-events, capping
+ * and inverse-CDF energy sampling; new axions are appended (stream
+ * compaction) and the emitted energy and momentum go to the exchange buffer. */
+axpic_status axpic_emit(axpic_ctx *ctx, int64_t step, int32_t channel_mask);
+
+/* Conservative feedback (Sec. II.J, Eqs. cell_moments to b_def): affine
+ * remap of the electron momenta with the cell's exchange buffer plus the
+ * energy carried from earlier steps, then the temperature update
+ * (Eqs. Te_est, Te_relax) in temperature mode "evolved". Clears the buffer. */
+axpic_status axpic_feedback(axpic_ctx *ctx, int64_t step);
+
+/* One fused step, absorb -> emit -> feedback, in a single pass over each
+ * cell's particles; identical results to the three calls above. */
+axpic_status axpic_step(axpic_ctx *ctx, int64_t step, int32_t channel_mask);
+
+/* Emitted-spectrum tally (App. B): H_out (host, 3*nbins doubles, channel-
+ * major: Primakoff, Compton-like, bremsstrahlung) receives
+ * H_k = sum w'E (keV) of the axions emitted since the previous call, and
+ * totals_out (host, AXPIC_TOTALS_LEN doubles, may be NULL) the counters
+ * listed above; both accumulators are then cleared. nbins must equal the
+ * context's tally_nbins. Synchronises the stream and reports latched errors. */
+axpic_status axpic_tally_spectrum(axpic_ctx *ctx, int32_t nbins, double *H_out,
+                                  double *totals_out);
+
+/* Deterministic rates for one cell, for checking (Eqs. prim_prob,
+ * gamma_abs): for each of n energies E_keV[i] (device) writes four binary32
+ * values to out[4*i..4*i+3] (device): P_{gamma->a}, P_{a->gamma},
+ * Gamma_abs,C dt and Gamma_abs,B dt. Enqueued on the stream. */
+axpic_status axpic_eval_rates(axpic_ctx *ctx, int32_t cell, const float *E_keV, int32_t n,
+                              float *out);
+
+/* Copy AXPIC_CELL_INFO_LEN doubles per cell for cells [first, first+count)
+ * into host_out. Synchronises the stream. */
+axpic_status axpic_get_cell_info(axpic_ctx *ctx, int32_t first, int32_t count, double *host_out);
+
+/* Copy AXPIC_CELL_DIAG_LEN doubles per cell of the last feedback (written
+ * only with diag_enable) into host_out. Synchronises the stream. */
+axpic_status axpic_get_cell_diag(axpic_ctx *ctx, int32_t first, int32_t count, double *host_out);
+
+/* Copy the carried (not yet applied) energy and momentum per cell, 4 doubles
+ * per cell (keV, m_e c), into host_out. Synchronises the stream. */
+axpic_status axpic_get_residuals(axpic_ctx *ctx, int32_t first, int32_t count, double *host_out);
+
+/* Wait for the stream and return the first latched device error, if any. */
+axpic_status axpic_sync(axpic_ctx *ctx);
+
+/* Wait for the stream, free the library's scratch and the context. */
+axpic_status axpic_destroy(axpic_ctx *ctx);
+
+/* Message of the last error on this context (never NULL; static for NULL ctx). */
+const char *axpic_last_error(const axpic_ctx *ctx);
+
+/* Library version string. */
+const char *axpic_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AXPIC_H */

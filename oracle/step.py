@@ -100,6 +100,8 @@ class StepTally:
     """Per-cell bookkeeping of one step (energies in keV, momenta in m_e c)."""
     dE: float = 0.0
     dP: np.ndarray = field(default_factory=lambda: np.zeros(3))
+    gross_E: float = 0.0          # sum of |contributions| to dE (for error bounds)
+    gross_P: float = 0.0          # sum of |contributions| to dP
     events: dict = field(default_factory=lambda: {"prim": 0, "compton": 0, "brems": 0, "prim_inv": 0})
     absorbed: dict = field(default_factory=lambda: {"compton": 0, "brems": 0})
     cap_hits: int = 0
@@ -228,6 +230,8 @@ def absorb_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTa
             u = decision_uniforms(p, step, cell, STREAM_ABSORB, n)
             absorbed = keep & (f32(u) < f32(P_abs))
             tally.dE += float(np.sum(w[absorbed] * omega[absorbed]))
+            tally.gross_E += float(np.sum(w[absorbed] * omega[absorbed]))
+            tally.gross_P += float(np.sum(w[absorbed] * a.pmag()[absorbed]))
             tally.dP += np.array([np.sum(w[absorbed] * a.px[absorbed]),
                                   np.sum(w[absorbed] * a.py[absorbed]),
                                   np.sum(w[absorbed] * a.pz[absorbed])])
@@ -241,6 +245,8 @@ def absorb_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTa
             w_new = (f32(w) * f32(np.exp(-tau))).astype(np.float64)
             lost = w - w_new
             tally.dE += float(np.sum(lost * omega))
+            tally.gross_E += float(np.sum(np.abs(lost) * omega))
+            tally.gross_P += float(np.sum(np.abs(lost) * a.pmag()))
             tally.dP += np.array([np.sum(lost * a.px), np.sum(lost * a.py), np.sum(lost * a.pz)])
             w = w_new
             keep = keep & (w > 0)
@@ -304,6 +310,8 @@ def emit_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTall
             wv = f32(w_a * fac[parent]).astype(np.float64)
             prods = Species(wv, pm * dx, pm * dy, pm * dz, e.x[parent], e.y[parent], e.z[parent])
             tally.dE -= float(np.sum(wv * E))
+            tally.gross_E += float(np.sum(wv * E))
+            tally.gross_P += float(np.sum(wv * pm))
             tally.dP -= np.array([np.sum(wv * prods.px), np.sum(wv * prods.py), np.sum(wv * prods.pz)])
             name = "compton" if ch == CH_COMPTON else "brems"
             tally.events[name] += int(Kc.sum())

@@ -1,0 +1,185 @@
+"""ctypes binding of libaxpic's C ABI (include/axpic.h).
+
+Argument marshalling only: every entry point forwards to the CUDA library with
+the same name. The library must have been built (``build.py``); importing this
+module on a machine where it is missing raises instead of falling back to
+anything else.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaxpic.so")
+
+AXPIC_OK, AXPIC_E_INVALID, AXPIC_E_CAPACITY, AXPIC_E_CUDA, AXPIC_E_TIMEOUT, AXPIC_E_NUMERIC = range(6)
+STATUS_NAMES = {0: "AXPIC_OK", 1: "AXPIC_E_INVALID", 2: "AXPIC_E_CAPACITY", 3: "AXPIC_E_CUDA",
+                4: "AXPIC_E_TIMEOUT", 5: "AXPIC_E_NUMERIC"}
+CH_PRIMAKOFF, CH_COMPTON, CH_BREMS, CH_ALL = 1, 2, 4, 7
+
+TOTALS_LEN = 32
+TOTALS_NAMES = ["nemit_p", "nemit_c", "nemit_b", "uemit_p", "uemit_c", "uemit_b", "events_p", "events_c",
+                "events_b", "events_pinv", "absorbed_c", "absorbed_b", "cap_hits", "clamp_hits", "dropped",
+                "n_axions", "u_axions", "macro_axions", "macro_photons", "residual_e", "n_photons", "u_photons",
+                "u_electrons", "remaps", "part_e", "part_g", "part_a", "remap_e", "cell_steps"]
+CELL_INFO_LEN = 16
+CELL_INFO_NAMES = ["rho", "X_H", "n_e", "n_eff", "S_Z", "kappa", "Q_C", "Q_B", "Gamma_C", "Gamma_B",
+                   "Gamma0_P", "eta", "T"]
+CELL_DIAG_LEN = 16
+CELL_DIAG_NAMES = ["dE", "dPx", "dPy", "dPz", "S_minus_1", "bx", "by", "bz", "var", "var_new", "W",
+                   "applied_E", "res_E", "res_Px", "res_Py", "res_Pz"]
+
+
+class Species(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_void_p), ("px", ctypes.c_void_p), ("py", ctypes.c_void_p),
+                ("pz", ctypes.c_void_p), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("z", ctypes.c_void_p), ("count", ctypes.c_void_p), ("capacity", ctypes.c_int32)]
+
+
+class PlasmaDesc(ctypes.Structure):
+    _fields_ = [("ncells", ctypes.c_int32), ("nspecies", ctypes.c_int32), ("cell_index_base", ctypes.c_int64),
+                ("T_keV", ctypes.c_void_p), ("n_ion", ctypes.c_void_p), ("Z", ctypes.POINTER(ctypes.c_double)),
+                ("A", ctypes.POINTER(ctypes.c_double)), ("cell_volume_cm3", ctypes.c_double),
+                ("electrons", Species), ("photons", Species), ("axions", Species)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("g_agg_GeV_inv", ctypes.c_double), ("g_ae", ctypes.c_double), ("dt_phys_s", ctypes.c_double),
+                ("w_a", ctypes.c_double), ("w_gamma_ref", ctypes.c_double), ("lambda_cap", ctypes.c_double),
+                ("kappa_mode", ctypes.c_int32), ("kappa_fixed_keV", ctypes.c_double),
+                ("prim_targets", ctypes.c_int32), ("prim_inverse_mult", ctypes.c_double),
+                ("eq_stats", ctypes.c_int32), ("brems_ee", ctypes.c_int32), ("absorb_mode", ctypes.c_int32),
+                ("brems_gamma_shape", ctypes.c_double), ("relax_r", ctypes.c_double),
+                ("T_floor_keV", ctypes.c_double), ("T_ceil_keV", ctypes.c_double), ("T_mode", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("tally_nbins", ctypes.c_int32), ("tally_Emax_keV", ctypes.c_double),
+                ("tally_enable", ctypes.c_int32), ("diag_enable", ctypes.c_int32),
+                ("threads_per_block", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class AxpicError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+EXPORTS = {
+    "axpic_default_params": (None, [ctypes.POINTER(Params)]),
+    "axpic_init_plasma": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(PlasmaDesc),
+                                         ctypes.POINTER(Params), ctypes.c_void_p]),
+    "axpic_sample_plasma": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "axpic_update_cells": (ctypes.c_int, [ctypes.c_void_p]),
+    "axpic_absorb": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]),
+    "axpic_emit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]),
+    "axpic_feedback": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "axpic_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]),
+    "axpic_tally_spectrum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double)]),
+    "axpic_eval_rates": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                        ctypes.c_void_p]),
+    "axpic_get_cell_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "axpic_get_cell_diag": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "axpic_get_residuals": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "axpic_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "axpic_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "axpic_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "axpic_version": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """Load libaxpic.so (once). Raises if the CUDA library has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libaxpic.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def _check(ctx, status):
+    if status != AXPIC_OK:
+        msg = lib().axpic_last_error(ctx)
+        raise AxpicError(status, msg.decode() if msg else "")
+
+
+def default_params():
+    p = Params()
+    lib().axpic_default_params(ctypes.byref(p))
+    return p
+
+
+def axpic_init_plasma(desc, params, stream=0):
+    ctx = ctypes.c_void_p()
+    st = lib().axpic_init_plasma(ctypes.byref(ctx), ctypes.byref(desc), ctypes.byref(params),
+                                 ctypes.c_void_p(stream))
+    if st != AXPIC_OK:
+        raise AxpicError(st, "axpic_init_plasma failed (see stderr)")
+    return ctx
+
+
+def axpic_sample_plasma(ctx, n_el, n_ph, n_ax):
+    _check(ctx, lib().axpic_sample_plasma(ctx, n_el, n_ph, n_ax))
+
+
+def axpic_update_cells(ctx):
+    _check(ctx, lib().axpic_update_cells(ctx))
+
+
+def axpic_absorb(ctx, step, mask):
+    _check(ctx, lib().axpic_absorb(ctx, step, mask))
+
+
+def axpic_emit(ctx, step, mask):
+    _check(ctx, lib().axpic_emit(ctx, step, mask))
+
+
+def axpic_feedback(ctx, step):
+    _check(ctx, lib().axpic_feedback(ctx, step))
+
+
+def axpic_step(ctx, step, mask):
+    _check(ctx, lib().axpic_step(ctx, step, mask))
+
+
+def axpic_tally_spectrum(ctx, nbins, H_out, totals_out):
+    """H_out and totals_out: ctypes double arrays (or None)."""
+    _check(ctx, lib().axpic_tally_spectrum(ctx, nbins, H_out, totals_out))
+
+
+def axpic_eval_rates(ctx, cell, E_ptr, n, out_ptr):
+    _check(ctx, lib().axpic_eval_rates(ctx, cell, ctypes.c_void_p(E_ptr), n, ctypes.c_void_p(out_ptr)))
+
+
+def axpic_get_cell_info(ctx, first, count, out):
+    _check(ctx, lib().axpic_get_cell_info(ctx, first, count, out))
+
+
+def axpic_get_cell_diag(ctx, first, count, out):
+    _check(ctx, lib().axpic_get_cell_diag(ctx, first, count, out))
+
+
+def axpic_get_residuals(ctx, first, count, out):
+    _check(ctx, lib().axpic_get_residuals(ctx, first, count, out))
+
+
+def axpic_sync(ctx):
+    _check(ctx, lib().axpic_sync(ctx))
+
+
+def axpic_destroy(ctx):
+    st = lib().axpic_destroy(ctx)
+    if st != AXPIC_OK:
+        raise AxpicError(st, "axpic_destroy reported a latched error")
+
+
+def axpic_version():
+    return lib().axpic_version().decode()

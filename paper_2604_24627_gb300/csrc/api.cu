@@ -1,0 +1,511 @@
+// C ABI of libaxpic (declared in include/axpic.h): context life cycle,
+// argument validation, constant folding and kernel launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "misc.h"
+#include "step.h"
+
+using namespace axpic;
+
+namespace {
+
+// CODATA 2018 constants (binary64), folded into the binary32 record.
+constexpr double kHbarcKeVcm = 1.973269804e-8;
+constexpr double kHbarcGeVcm = 1.973269804e-14;
+constexpr double kAlpha = 1.0 / 137.035999084;
+constexpr double kMu = 1.66053906660e-24;
+constexpr double kC = 2.99792458e10;
+constexpr double kKb = 8.617333262e-8;
+constexpr double kKeVerg = 1.602176634e-9;
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kDefaultWarps = 4;
+constexpr int kInfoChunk = 4096;
+
+}  // namespace
+
+struct axpic_ctx {
+  axpic_plasma_desc desc;
+  axpic_params prm;
+  std::vector<double> Z, A;
+  cudaStream_t stream = nullptr;
+  float* rec = nullptr;
+  float* mom = nullptr;
+  double* xbuf = nullptr;
+  double* res = nullptr;
+  double* diag = nullptr;
+  int32_t* photon_start = nullptr;
+  float* tables = nullptr;
+  double* tally = nullptr;
+  unsigned long long* counters = nullptr;
+  int* err = nullptr;
+  double* scratch = nullptr;  // totals (8) + counters (kNumCounters) + info chunk
+  CellConst cc;
+  int warps = kDefaultWarps;
+  int grid = 0;
+  int64_t last_absorb_step = -1;
+  std::string last_error;
+};
+
+static const char* kNoCtxMsg = "no context";
+
+static axpic_status fail(axpic_ctx* c, axpic_status s, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return s;
+}
+
+static axpic_status cuda_fail(axpic_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, AXPIC_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+static SpeciesPtrs to_ptrs(const axpic_species& s) {
+  SpeciesPtrs p;
+  p.w = s.w;
+  p.px = s.px;
+  p.py = s.py;
+  p.pz = s.pz;
+  p.x = s.x;
+  p.y = s.y;
+  p.z = s.z;
+  p.count = s.count;
+  p.cap = s.capacity;
+  return p;
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static std::string check_species(const axpic_species& s, const char* name) {
+  if (s.capacity < 0 || (s.capacity & 3)) return std::string(name) + ": capacity must be a non-negative multiple of 4";
+  if (s.capacity > 65532) return std::string(name) + ": capacity above 65532";
+  if (!s.count) return std::string(name) + ": count is NULL";
+  if (s.capacity == 0) return "";
+  const float* f[7] = {s.w, s.px, s.py, s.pz, s.x, s.y, s.z};
+  for (auto p : f) {
+    if (!p) return std::string(name) + ": a particle array is NULL";
+    if (!aligned16(p)) return std::string(name) + ": particle arrays must be 16-byte aligned";
+  }
+  return "";
+}
+
+static double w_gref(const axpic_params& p) { return p.w_gamma_ref > 0 ? p.w_gamma_ref : p.w_a; }
+
+static void fold_constants(axpic_ctx* ctx) {
+  const axpic_params& p = ctx->prm;
+  CellConst& cc = ctx->cc;
+  std::memset(&cc, 0, sizeof(cc));
+  cc.nspecies = ctx->desc.nspecies;
+  for (int s = 0; s < cc.nspecies; ++s) {
+    cc.Z[s] = (float)ctx->Z[s];
+    cc.A[s] = (float)ctx->A[s];
+    cc.is_h[s] = ctx->Z[s] == 1.0;
+  }
+  cc.kappa_mode = p.kappa_mode;
+  cc.kappa_fixed = (float)p.kappa_fixed_keV;
+  cc.prim_targets = p.prim_targets;
+  cc.prim_mult = (float)p.prim_inverse_mult;
+  cc.brems_ee = p.brems_ee;
+  const double z5 = zeta(5.0), z6 = zeta(6.0);
+  const double mean_xc = 5.0 * z6 / z5;
+  const double a = p.brems_gamma_shape;
+  const double wa32 = (double)(float)p.w_a;
+  const double hc3 = kHbarcKeVcm * kHbarcKeVcm * kHbarcKeVcm;
+  const double gcm = p.g_agg_GeV_inv * kHbarcGeVcm;
+  cc.k_kappa2 = (float)(4.0 * kPi * kAlpha * hc3 * 1e24);
+  cc.k_rho = (float)(kMu * 1e24);
+  cc.k_T7 = (float)(1.0 / (kKb * 1e7));
+  cc.afac = (float)(p.g_ae * p.g_ae / (4.0 * kPi * 1.60e-23));
+  cc.k_AP = (float)(kAlpha * gcm * gcm / 8.0 * kC * 1e24 * p.dt_phys_s);
+  cc.k_CC = (float)(p.dt_phys_s / (wa32 * mean_xc * kKeVerg * 1e24));
+  cc.k_CB = (float)(p.dt_phys_s / (wa32 * a * kKeVerg * 1e24));
+  cc.k_BC = (float)(2.0 * kPi * kPi * hc3 * p.dt_phys_s / (24.0 * z5 * mean_xc * kKeVerg));
+  cc.k_BB = (float)(2.0 * kPi * kPi * hc3 * p.dt_phys_s / (std::tgamma(a) * a * kKeVerg));
+}
+
+static StepArgs make_args(axpic_ctx* ctx, int64_t step, int mask) {
+  const axpic_params& p = ctx->prm;
+  StepArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.e = to_ptrs(ctx->desc.electrons);
+  A.g = to_ptrs(ctx->desc.photons);
+  A.a = to_ptrs(ctx->desc.axions);
+  A.ncells = ctx->desc.ncells;
+  A.cell_base = (uint32_t)ctx->desc.cell_index_base;
+  A.step = (uint32_t)(step & 0xFFFFFFFF);
+  A.key0 = (uint32_t)(p.seed & 0xFFFFFFFFu);
+  A.key1 = (uint32_t)(p.seed >> 32);
+  A.mask = mask;
+  A.w_a = (float)p.w_a;
+  A.w_gref = (float)w_gref(p);
+  A.inv_w_a = 1.0f / A.w_a;
+  A.inv_w_gref = 1.0f / A.w_gref;
+  A.lam_cap = p.lambda_cap > 0 ? (float)std::fmin(p.lambda_cap, (double)kLambdaHardCap) : kLambdaHardCap;
+  A.brems_am3 = (float)(p.brems_gamma_shape - 3.0);
+  A.eq_stats = p.eq_stats;
+  A.absorb_mode = p.absorb_mode;
+  A.T_mode = p.T_mode;
+  A.tally_enable = p.tally_enable;
+  A.diag_enable = p.diag_enable;
+  A.relax_r = (float)p.relax_r;
+  A.T_floor = p.T_floor_keV;
+  A.T_ceil = p.T_ceil_keV;
+  A.rec = ctx->rec;
+  A.mom = ctx->mom;
+  A.T = ctx->desc.T_keV;
+  A.n_ion = ctx->desc.n_ion;
+  A.xbuf = ctx->xbuf;
+  A.res = ctx->res;
+  A.diag = ctx->diag;
+  A.photon_start = ctx->photon_start;
+  A.tables = ctx->tables;
+  A.tally = ctx->tally;
+  A.nbins = p.tally_nbins;
+  A.inv_dE_bin = (float)(p.tally_nbins / p.tally_Emax_keV);
+  A.counters = ctx->counters;
+  A.err = ctx->err;
+  A.cc = ctx->cc;
+  return A;
+}
+
+static void free_ctx(axpic_ctx* ctx) {
+  void* bufs[] = {ctx->rec,    ctx->mom,    ctx->xbuf,     ctx->res, ctx->diag, ctx->photon_start,
+                  ctx->tables, ctx->tally, ctx->counters, ctx->err, ctx->scratch};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete ctx;
+}
+
+extern "C" {
+
+void axpic_default_params(axpic_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->g_agg_GeV_inv = 1e-10;
+  p->g_ae = 1e-13;
+  p->dt_phys_s = 1.0;
+  p->w_a = 1.0;
+  p->w_gamma_ref = 0.0;
+  p->lambda_cap = 0.0;
+  p->kappa_mode = 0;
+  p->prim_targets = 0;
+  p->prim_inverse_mult = 1.0;
+  p->eq_stats = 0;
+  p->brems_ee = 1;
+  p->absorb_mode = 0;
+  p->brems_gamma_shape = 1.70;
+  p->relax_r = 0.1;
+  p->T_floor_keV = 0.0;
+  p->T_ceil_keV = 1e30;
+  p->T_mode = 0;
+  p->seed = 0;
+  p->tally_nbins = 160;
+  p->tally_Emax_keV = 80.0;
+  p->tally_enable = 1;
+  p->diag_enable = 0;
+  p->threads_per_block = 0;
+}
+
+axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, const axpic_params* params,
+                               void* stream) {
+  if (!out || !desc || !params) return AXPIC_E_INVALID;
+  *out = nullptr;
+  const axpic_plasma_desc& d = *desc;
+  const axpic_params& p = *params;
+  auto* ctx = new axpic_ctx();
+  ctx->desc = d;
+  ctx->prm = p;
+  ctx->stream = (cudaStream_t)stream;
+  auto bad = [&](const std::string& m) {
+    fprintf(stderr, "axpic_init_plasma: %s\n", m.c_str());
+    delete ctx;
+    return AXPIC_E_INVALID;
+  };
+  if (d.ncells < 0) return bad("ncells < 0");
+  if (d.nspecies < 1 || d.nspecies > kMaxSpecies) return bad("nspecies must be in 1..8");
+  if (d.cell_index_base < 0 || d.cell_index_base + d.ncells > (int64_t)0xFFFFFFFF)
+    return bad("global cell indices must fit in 32 bits");
+  if (d.ncells > 0 && (!d.T_keV || !d.n_ion)) return bad("T_keV or n_ion is NULL");
+  if (!d.Z || !d.A) return bad("Z or A is NULL");
+  if (!(d.cell_volume_cm3 > 0)) return bad("cell_volume_cm3 must be > 0");
+  for (auto sp : {std::make_pair(&d.electrons, "electrons"), std::make_pair(&d.photons, "photons"),
+                  std::make_pair(&d.axions, "axions")}) {
+    const std::string m = check_species(*sp.first, sp.second);
+    if (!m.empty()) return bad(m);
+  }
+  if (!(p.dt_phys_s > 0) || !(p.w_a > 0)) return bad("dt_phys_s and w_a must be > 0");
+  if (!((float)p.w_a > 0) || !std::isfinite((float)p.w_a)) return bad("w_a must be representable in binary32");
+  if (!(p.relax_r >= 0 && p.relax_r <= 1)) return bad("relax_r must be in [0, 1]");
+  if (!(p.brems_gamma_shape > 0)) return bad("brems_gamma_shape must be > 0");
+  if (p.kappa_mode != 0 && p.kappa_mode != 1) return bad("kappa_mode must be 0 or 1");
+  if (p.kappa_mode == 1 && !(p.kappa_fixed_keV > 0)) return bad("kappa_fixed_keV must be > 0");
+  if (p.eq_stats != 0 && p.eq_stats != 1) return bad("eq_stats must be 0 or 1");
+  if (p.absorb_mode != 0 && p.absorb_mode != 1) return bad("absorb_mode must be 0 or 1");
+  if (p.T_mode < 0 || p.T_mode > 2) return bad("T_mode must be 0, 1 or 2");
+  if (!(p.T_floor_keV <= p.T_ceil_keV)) return bad("T_floor_keV > T_ceil_keV");
+  if (p.tally_nbins < 1 || !(p.tally_Emax_keV > 0)) return bad("tally_nbins >= 1 and tally_Emax_keV > 0");
+  if (!(p.prim_inverse_mult >= 0)) return bad("prim_inverse_mult must be >= 0");
+  for (int s = 0; s < d.nspecies; ++s) {
+    if (!(d.Z[s] > 0) || !(d.A[s] > 0)) return bad("Z and A must be > 0");
+    ctx->Z.push_back(d.Z[s]);
+    ctx->A.push_back(d.A[s]);
+  }
+  const size_t per_warp = step_smem_per_warp(d.axions.capacity, d.photons.capacity, d.electrons.capacity);
+  int warps = p.threads_per_block > 0 ? p.threads_per_block / 32 : kDefaultWarps;
+  if (warps < 1 || warps > 8 || (p.threads_per_block > 0 && p.threads_per_block % 32))
+    return bad("threads_per_block must be 32..256, a multiple of 32");
+  const size_t smem_limit = 227 * 1024 - 128;
+  while (warps > 1 && per_warp * warps > smem_limit) --warps;
+  if (per_warp > smem_limit) return bad("slab capacities too large for shared-memory scratch");
+  ctx->warps = warps;
+  ctx->grid = (d.ncells + warps - 1) / warps;
+  fold_constants(ctx);
+
+  const int n = d.ncells;
+  cudaError_t e;
+#define ALLOC(ptr, bytes)                                                 \
+  if ((e = cudaMalloc((void**)&ptr, (bytes) > 0 ? (bytes) : 16)) != cudaSuccess) { \
+    ctx->last_error = cudaGetErrorString(e);                              \
+    free_ctx(ctx);                                                        \
+    return AXPIC_E_CUDA;                                                  \
+  }
+  ALLOC(ctx->rec, sizeof(float) * kRecLen * (size_t)n);
+  ALLOC(ctx->mom, sizeof(float) * kMomLen * (size_t)n);
+  ALLOC(ctx->xbuf, sizeof(double) * 4 * (size_t)n);
+  ALLOC(ctx->res, sizeof(double) * 4 * (size_t)n);
+  ALLOC(ctx->diag, sizeof(double) * AXPIC_CELL_DIAG_LEN * (size_t)n);
+  ALLOC(ctx->photon_start, sizeof(int32_t) * (size_t)n);
+  ALLOC(ctx->tables, sizeof(float) * kNumTables * kTableN);
+  ALLOC(ctx->tally, sizeof(double) * (3 * (size_t)p.tally_nbins + 6));
+  ALLOC(ctx->counters, sizeof(unsigned long long) * kNumCounters * (size_t)ctx->grid);
+  ALLOC(ctx->err, sizeof(int));
+  ALLOC(ctx->scratch, sizeof(double) * (8 + kNumCounters + (size_t)kInfoChunk * AXPIC_CELL_INFO_LEN));
+#undef ALLOC
+  std::vector<float> tab((size_t)kNumTables * kTableN);
+  build_tables(p.brems_gamma_shape, tab.data());
+  cudaStream_t st = ctx->stream;
+  if ((e = cudaMemcpyAsync(ctx->tables, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemsetAsync(ctx->xbuf, 0, sizeof(double) * 4 * (size_t)n, st)) ||
+      (e = cudaMemsetAsync(ctx->res, 0, sizeof(double) * 4 * (size_t)n, st)) ||
+      (e = cudaMemsetAsync(ctx->diag, 0, sizeof(double) * AXPIC_CELL_DIAG_LEN * (size_t)n, st)) ||
+      (e = cudaMemsetAsync(ctx->photon_start, 0, sizeof(int32_t) * (size_t)n, st)) ||
+      (e = cudaMemsetAsync(ctx->tally, 0, sizeof(double) * (3 * (size_t)p.tally_nbins + 6), st)) ||
+      (e = cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * kNumCounters * (size_t)ctx->grid, st)) ||
+      (e = cudaMemsetAsync(ctx->err, 0, sizeof(int), st)) ||
+      (e = set_step_smem_limits(per_warp * warps)) ||
+      (e = launch_records(n, d.nspecies, ctx->cc, d.T_keV, d.n_ion, ctx->rec, ctx->err, st)) ||
+      (e = launch_moments(n, to_ptrs(d.electrons), ctx->mom, st)) || (e = cudaStreamSynchronize(st))) {
+    ctx->last_error = cudaGetErrorString(e);
+    fprintf(stderr, "axpic_init_plasma: %s\n", ctx->last_error.c_str());
+    free_ctx(ctx);
+    return AXPIC_E_CUDA;
+  }
+  *out = ctx;
+  return AXPIC_OK;
+}
+
+axpic_status axpic_sample_plasma(axpic_ctx* ctx, int32_t n_el, int32_t n_ph, int32_t n_ax) {
+  if (!ctx) return AXPIC_E_INVALID;
+  const axpic_plasma_desc& d = ctx->desc;
+  if (n_el < 0 || n_ph < 0 || n_ax < 0 || n_el > d.electrons.capacity || n_ph > d.photons.capacity ||
+      n_ax > d.axions.capacity)
+    return fail(ctx, AXPIC_E_INVALID, "axpic_sample_plasma: count outside [0, capacity]");
+  SampleArgs S;
+  std::memset(&S, 0, sizeof(S));
+  S.e = to_ptrs(d.electrons);
+  S.g = to_ptrs(d.photons);
+  S.a = to_ptrs(d.axions);
+  S.ncells = d.ncells;
+  S.n_el = n_el;
+  S.n_ph = n_ph;
+  S.n_ax = n_ax;
+  S.cell_base = (uint32_t)d.cell_index_base;
+  S.key0 = (uint32_t)(ctx->prm.seed & 0xFFFFFFFFu);
+  S.key1 = (uint32_t)(ctx->prm.seed >> 32);
+  S.k_we = n_el > 0 ? (float)(d.cell_volume_cm3 * 1e24 / n_el) : 0.f;
+  const double hc3 = kHbarcKeVcm * kHbarcKeVcm * kHbarcKeVcm;
+  S.k_wg = n_ph > 0 ? (float)(2.0 * zeta(3.0) / (kPi * kPi * hc3) * d.cell_volume_cm3 / n_ph) : 0.f;
+  S.w_a = (float)ctx->prm.w_a;
+  S.rec = ctx->rec;
+  S.tables = ctx->tables;
+  CK(launch_sample(S, ctx->stream), "sample");
+  CK(launch_moments(d.ncells, to_ptrs(d.electrons), ctx->mom, ctx->stream), "moments");
+  return AXPIC_OK;
+}
+
+axpic_status axpic_update_cells(axpic_ctx* ctx) {
+  if (!ctx) return AXPIC_E_INVALID;
+  const axpic_plasma_desc& d = ctx->desc;
+  CK(launch_records(d.ncells, d.nspecies, ctx->cc, d.T_keV, d.n_ion, ctx->rec, ctx->err, ctx->stream), "records");
+  CK(launch_moments(d.ncells, to_ptrs(d.electrons), ctx->mom, ctx->stream), "moments");
+  return AXPIC_OK;
+}
+
+static axpic_status run_phases(axpic_ctx* ctx, int phases, int64_t step, int32_t mask, const char* name) {
+  if (!ctx) return AXPIC_E_INVALID;
+  if (step < 0 || step >= (int64_t)0xFFFFFFFF) return fail(ctx, AXPIC_E_INVALID, std::string(name) + ": step out of range");
+  if (mask & ~AXPIC_CH_ALL) return fail(ctx, AXPIC_E_INVALID, std::string(name) + ": unknown channel bits");
+  StepArgs A = make_args(ctx, step, mask);
+  if (phases == PH_EMIT) A.use_snapshot = ctx->last_absorb_step == step;
+  CK(launch_step(phases, A, ctx->warps, ctx->stream), name);
+  if (phases == PH_ABSORB) ctx->last_absorb_step = step;
+  return AXPIC_OK;
+}
+
+axpic_status axpic_absorb(axpic_ctx* ctx, int64_t step, int32_t channel_mask) {
+  return run_phases(ctx, PH_ABSORB, step, channel_mask, "axpic_absorb");
+}
+
+axpic_status axpic_emit(axpic_ctx* ctx, int64_t step, int32_t channel_mask) {
+  return run_phases(ctx, PH_EMIT, step, channel_mask, "axpic_emit");
+}
+
+axpic_status axpic_feedback(axpic_ctx* ctx, int64_t step) {
+  return run_phases(ctx, PH_FEEDBACK, step, 0, "axpic_feedback");
+}
+
+axpic_status axpic_step(axpic_ctx* ctx, int64_t step, int32_t channel_mask) {
+  return run_phases(ctx, PH_ALL, step, channel_mask, "axpic_step");
+}
+
+static axpic_status read_err(axpic_ctx* ctx) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "read error flag");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  if (h & ERR_CAPACITY) return fail(ctx, AXPIC_E_CAPACITY, "a slab capacity was exceeded; products were dropped");
+  if (h & ERR_NUMERIC) return fail(ctx, AXPIC_E_NUMERIC, "a non-finite or non-positive temperature was found");
+  return AXPIC_OK;
+}
+
+axpic_status axpic_tally_spectrum(axpic_ctx* ctx, int32_t nbins, double* H_out, double* totals_out) {
+  if (!ctx) return AXPIC_E_INVALID;
+  if (nbins != ctx->prm.tally_nbins) return fail(ctx, AXPIC_E_INVALID, "axpic_tally_spectrum: nbins mismatch");
+  const axpic_plasma_desc& d = ctx->desc;
+  cudaStream_t st = ctx->stream;
+  const size_t hn = 3 * (size_t)nbins + 6;
+  std::vector<double> h(hn), tot(8 + kNumCounters);
+  CK(cudaMemsetAsync(ctx->scratch, 0, sizeof(double) * (8 + kNumCounters), st), "memset");
+  CK(launch_totals(d.ncells, to_ptrs(d.electrons), to_ptrs(d.photons), to_ptrs(d.axions), ctx->res, ctx->counters,
+                   ctx->grid, ctx->scratch, ctx->scratch + 8, st),
+     "totals");
+  CK(cudaMemcpyAsync(h.data(), ctx->tally, hn * sizeof(double), cudaMemcpyDeviceToHost, st), "copy tally");
+  CK(cudaMemcpyAsync(tot.data(), ctx->scratch, tot.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
+     "copy totals");
+  CK(cudaMemsetAsync(ctx->tally, 0, hn * sizeof(double), st), "reset tally");
+  CK(cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * kNumCounters * (size_t)ctx->grid, st),
+     "reset counters");
+  CK(cudaStreamSynchronize(st), "synchronize");
+  if (H_out) std::memcpy(H_out, h.data(), 3 * (size_t)nbins * sizeof(double));
+  if (totals_out) {
+    double* T = totals_out;
+    std::memset(T, 0, sizeof(double) * AXPIC_TOTALS_LEN);
+    const double* em = h.data() + 3 * (size_t)nbins;
+    for (int c = 0; c < 3; ++c) {
+      T[AXPIC_T_NEMIT_P + c] = em[c];
+      T[AXPIC_T_UEMIT_P + c] = em[3 + c];
+    }
+    const double* cn = tot.data() + 8;
+    T[AXPIC_T_EVENTS_P] = cn[C_EV_P];
+    T[AXPIC_T_EVENTS_C] = cn[C_EV_C];
+    T[AXPIC_T_EVENTS_B] = cn[C_EV_B];
+    T[AXPIC_T_EVENTS_PINV] = cn[C_EV_PINV];
+    T[AXPIC_T_ABSORBED_C] = cn[C_ABS_C];
+    T[AXPIC_T_ABSORBED_B] = cn[C_ABS_B];
+    T[AXPIC_T_CAP_HITS] = cn[C_CAP];
+    T[AXPIC_T_CLAMP_HITS] = cn[C_CLAMP];
+    T[AXPIC_T_DROPPED] = cn[C_DROP];
+    T[AXPIC_T_N_AXIONS] = tot[0];
+    T[AXPIC_T_U_AXIONS] = tot[1] * kMeC2;
+    T[AXPIC_T_N_PHOTONS] = tot[2];
+    T[AXPIC_T_U_PHOTONS] = tot[3] * kMeC2;
+    T[AXPIC_T_U_ELECTRONS] = tot[4] * kMeC2;
+    T[AXPIC_T_MACRO_AXIONS] = tot[5];
+    T[AXPIC_T_MACRO_PHOTONS] = tot[6];
+    T[AXPIC_T_RESIDUAL_E] = tot[7];
+    T[AXPIC_T_REMAPS] = cn[C_REMAP];
+    T[AXPIC_T_PART_E] = cn[C_NE];
+    T[AXPIC_T_PART_G] = cn[C_NG];
+    T[AXPIC_T_PART_A] = cn[C_NA];
+    T[AXPIC_T_REMAP_E] = cn[C_REMAP_E];
+    T[AXPIC_T_CALLS] = cn[C_CELLS];
+  }
+  return read_err(ctx);
+}
+
+axpic_status axpic_eval_rates(axpic_ctx* ctx, int32_t cell, const float* E_keV, int32_t n, float* out) {
+  if (!ctx) return AXPIC_E_INVALID;
+  if (cell < 0 || cell >= ctx->desc.ncells || n < 0 || (n > 0 && (!E_keV || !out)))
+    return fail(ctx, AXPIC_E_INVALID, "axpic_eval_rates: bad cell, count or pointer");
+  CK(launch_rates(ctx->rec, cell, E_keV, n, ctx->prm.eq_stats, (float)(ctx->prm.brems_gamma_shape - 3.0), out,
+                  ctx->stream),
+     "rates");
+  return AXPIC_OK;
+}
+
+axpic_status axpic_get_cell_info(axpic_ctx* ctx, int32_t first, int32_t count, double* host_out) {
+  if (!ctx) return AXPIC_E_INVALID;
+  if (first < 0 || count < 0 || first + count > ctx->desc.ncells || (count > 0 && !host_out))
+    return fail(ctx, AXPIC_E_INVALID, "axpic_get_cell_info: range outside the cells");
+  double* dev = ctx->scratch + 8 + kNumCounters;
+  const double k_gamma = (double)(float)ctx->prm.w_a / ctx->prm.dt_phys_s;
+  for (int c0 = 0; c0 < count; c0 += kInfoChunk) {
+    const int m = std::min(kInfoChunk, count - c0);
+    CK(launch_info(first + c0, m, ctx->cc, k_gamma, ctx->rec, dev, ctx->stream), "info");
+    CK(cudaMemcpyAsync(host_out + (size_t)c0 * AXPIC_CELL_INFO_LEN, dev, sizeof(double) * m * AXPIC_CELL_INFO_LEN,
+                       cudaMemcpyDeviceToHost, ctx->stream),
+       "copy info");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    for (int i = 0; i < m; ++i)
+      host_out[(size_t)(c0 + i) * AXPIC_CELL_INFO_LEN + AXPIC_CI_GAMMA0_P] /= ctx->prm.dt_phys_s;
+  }
+  return AXPIC_OK;
+}
+
+axpic_status axpic_get_cell_diag(axpic_ctx* ctx, int32_t first, int32_t count, double* host_out) {
+  if (!ctx) return AXPIC_E_INVALID;
+  if (first < 0 || count < 0 || first + count > ctx->desc.ncells || (count > 0 && !host_out))
+    return fail(ctx, AXPIC_E_INVALID, "axpic_get_cell_diag: range outside the cells");
+  CK(cudaMemcpyAsync(host_out, ctx->diag + (size_t)first * AXPIC_CELL_DIAG_LEN,
+                     sizeof(double) * AXPIC_CELL_DIAG_LEN * (size_t)count, cudaMemcpyDeviceToHost, ctx->stream),
+     "copy diag");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  return AXPIC_OK;
+}
+
+axpic_status axpic_get_residuals(axpic_ctx* ctx, int32_t first, int32_t count, double* host_out) {
+  if (!ctx) return AXPIC_E_INVALID;
+  if (first < 0 || count < 0 || first + count > ctx->desc.ncells || (count > 0 && !host_out))
+    return fail(ctx, AXPIC_E_INVALID, "axpic_get_residuals: range outside the cells");
+  CK(cudaMemcpyAsync(host_out, ctx->res + (size_t)first * 4, sizeof(double) * 4 * (size_t)count,
+                     cudaMemcpyDeviceToHost, ctx->stream),
+     "copy residuals");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  return AXPIC_OK;
+}
+
+axpic_status axpic_sync(axpic_ctx* ctx) {
+  if (!ctx) return AXPIC_E_INVALID;
+  return read_err(ctx);
+}
+
+axpic_status axpic_destroy(axpic_ctx* ctx) {
+  if (!ctx) return AXPIC_E_INVALID;
+  axpic_status s = read_err(ctx);
+  free_ctx(ctx);
+  return s;
+}
+
+const char* axpic_last_error(const axpic_ctx* ctx) { return ctx ? ctx->last_error.c_str() : kNoCtxMsg; }
+
+const char* axpic_version(void) { return "axpic 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

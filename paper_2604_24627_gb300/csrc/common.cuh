@@ -1,0 +1,319 @@
+// Internal definitions shared by the CUDA translation units of libaxpic.
+//
+// Device helpers: Philox4x32-10, uniforms, the screened Primakoff factor
+// F(s), Poisson inversion, inverse-CDF table lookup, isotropic directions and
+// the per-cell rate record. Everything per particle is binary32; the record
+// is computed in binary32 from constants folded in binary64 on the host, so
+// that no per-particle or common-path per-cell work touches the FP64 pipe
+// (about 1/60 of the FP32 rate on GB300).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/axpic.h"
+#include "tables.h"
+
+namespace axpic {
+
+// ---------------------------------------------------------------- constants
+constexpr double kMeC2 = 510.99895000;     // keV
+constexpr float kMeC2f = 510.99895000f;
+constexpr float kInvMeC2f = (float)(1.0 / 510.99895000);
+constexpr int kMaxSpecies = 8;
+constexpr int kPoissonKmax = 255;
+constexpr float kLambdaHardCap = 64.0f;
+
+// Philox streams (counter word 3 = stream << 24 | sub).
+enum : uint32_t {
+  S_PRIM_FWD = 0, S_COMPTON = 1, S_BREMS = 2, S_PRIM_INV = 3, S_ABSORB = 4,
+  S_EV_COMPTON = 5, S_EV_BREMS = 6, S_INIT_E = 8, S_INIT_G = 9, S_INIT_A = 10
+};
+constexpr uint32_t kInitStep = 0xFFFFFFFFu;
+
+// Inverse-CDF tables: ln x tabulated on a uniform grid of y = logit(u)
+// (layout and construction in tables.h / tables.cpp).
+
+// Per-cell binary32 rate record (16 floats = 64 B). The composition part
+// depends only on the ion densities; the temperature part is recomputed
+// whenever T_e changes.
+constexpr int kRecLen = 16;
+enum {
+  R_T = 0,     // T_e, keV
+  R_INVT,      // 1/T_e
+  R_FOURK2,    // 4/kappa^2 (s = omega^2 * R_FOURK2)
+  R_CC,        // Gamma_C dt / w_a (lambda_C = w_e * R_CC)
+  R_CB,        // Gamma_B dt / w_a
+  R_BC,        // Compton absorption prefactor (tau_C = R_BC x^2 [/(1-e^-x)])
+  R_BB,        // bremsstrahlung absorption prefactor (tau_B = R_BB x^(a-3) [(1-e^-x)])
+  R_AP,        // Gamma_0 dt of gamma->a (Gamma dt = R_AP * F(s))   [composition]
+  R_APINV,     // m * R_AP (a->gamma)                              [composition]
+  R_NE,        // n_e / 1e24 cm^-3                                  [composition]
+  R_NEFF,      // n_eff / 1e24 cm^-3                                [composition]
+  R_RHO,       // rho, g cm^-3                                      [composition]
+  R_XH,        // hydrogen mass fraction                            [composition]
+  R_SZ         // Primakoff target sum / 1e24 cm^-3                 [composition]
+};
+
+// Cached electron moments per cell (binary32): W, Px, Py, Pz, U2, var.
+constexpr int kMomLen = 8;
+enum { M_W = 0, M_PX, M_PY, M_PZ, M_U2, M_VAR };
+
+// Per-CTA counters (u64), reduced by axpic_tally_spectrum.
+enum {
+  C_EV_P = 0, C_EV_C, C_EV_B, C_EV_PINV, C_ABS_C, C_ABS_B, C_CAP, C_CLAMP, C_DROP, C_REMAP,
+  C_NE, C_NG, C_NA, C_REMAP_E, C_CELLS,
+  kNumCounters
+};
+
+// Device error flag bits.
+enum { ERR_CAPACITY = 1, ERR_NUMERIC = 2 };
+
+// Constants folded on the host (binary64) for the binary32 record.
+struct CellConst {
+  int nspecies;
+  float Z[kMaxSpecies];
+  float A[kMaxSpecies];
+  int is_h[kMaxSpecies];
+  int kappa_mode;
+  float kappa_fixed;
+  int prim_targets;
+  float prim_mult;
+  int brems_ee;
+  float k_kappa2;   // 4 pi alpha (hbar c)^3 * 1e24  [keV^3 per (1e24 cm^-3)]
+  float k_rho;      // m_u * 1e24  [g per (1e24 cm^-3)]
+  float k_T7;       // 1 / (k_B 1e7 K)  [1/keV]
+  float afac;       // g_ae^2 / (4 pi 1.6e-23)
+  float k_AP;       // alpha (g hbar c)^2 c / 8 * 1e24 * dt
+  float k_CC;       // dt / (w_a <x>_C keV_erg 1e24)
+  float k_CB;       // dt / (w_a a keV_erg 1e24)
+  float k_BC;       // 2 pi^2 (hbar c)^3 dt / (Gamma(5) zeta(5) <x>_C keV_erg)
+  float k_BB;       // 2 pi^2 (hbar c)^3 dt / (Gamma(a) a keV_erg)
+};
+
+struct SpeciesPtrs {
+  float *w, *px, *py, *pz, *x, *y, *z;
+  int32_t *count;
+  int32_t cap;
+};
+
+// ---------------------------------------------------------------- Philox
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// ((word >> 9) + 0.5) * 2^-23: exact in binary32, in (0, 1).
+__device__ __forceinline__ float u23(uint32_t w) {
+  return ((float)(w >> 9) + 0.5f) * 1.1920928955078125e-07f;
+}
+
+__device__ __forceinline__ uint32_t word(const uint4& b, int j) {
+  return j == 0 ? b.x : (j == 1 ? b.y : (j == 2 ? b.z : b.w));
+}
+
+// ---------------------------------------------------------------- physics
+// F(s) = (1 + 1/s) ln(1 + s) - 1; below s = 0.25 its power series
+// sum_{n>=1} (-1)^(n+1) s^n / (n (n+1)) (12 terms) avoids the cancellation.
+__device__ __forceinline__ float prim_F(float s) {
+  if (s < 0.25f) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int n = 12; n >= 1; --n) {
+      const float c = ((n & 1) ? 1.0f : -1.0f) / (float)(n * (n + 1));
+      acc = fmaf(acc, s, c);
+    }
+    return acc * s;
+  }
+  return (1.0f + 1.0f / s) * log1pf(s) - 1.0f;
+}
+
+// K = min{k : u <= F_k}, p_k = p_{k-1} * (lambda / k), F_k = F_{k-1} + p_k,
+// binary32 with no contraction, bounded by 255 iterations.
+__device__ __forceinline__ int poisson_inv(float u, float lam) {
+  float p = expf(-lam);
+  float F = p;
+  int k = 0;
+  while (u > F && k < kPoissonKmax) {
+    ++k;
+    p = __fmul_rn(p, __fdiv_rn(lam, (float)k));
+    F = __fadd_rn(F, p);
+    if (p == 0.0f) break;
+  }
+  return k;
+}
+
+// Cap-and-rescale (Eqs. lambda_eff, wa_rescaled): returns lambda_eff and sets
+// *fac = lambda_macro / lambda_eff (1 exactly when no cap applies).
+__device__ __forceinline__ float cap_lambda(float lam, float cap, float* fac, bool* capped) {
+  if (lam > cap) {
+    *fac = lam / cap;
+    *capped = true;
+    return cap;
+  }
+  *fac = 1.0f;
+  *capped = false;
+  return lam;
+}
+
+// Weight depletion in binary32: returns the product weight and sets *wrem.
+__device__ __forceinline__ float deplete(float w, int K, float wprod, float* wrem, bool* over) {
+  const float conv = __fmul_rn((float)K, wprod);
+  *over = (K > 0) && (conv > w);
+  if (*over) {
+    *wrem = 0.0f;
+    return __fdiv_rn(w, (float)K);
+  }
+  *wrem = __fsub_rn(w, conv);
+  return wprod;
+}
+
+// x = exp(g(logit u)), g linearly interpolated on kTableN nodes.
+__device__ __forceinline__ float icdf_lookup(const float* __restrict__ tab, float u) {
+  const float y = logf(u) - logf(1.0f - u);
+  const float inv_h = (float)(kTableN - 1) / (kTableY1 - kTableY0);
+  float t = (y - kTableY0) * inv_h;
+  t = fminf(fmaxf(t, 0.0f), (float)(kTableN - 1) - 1e-3f);
+  const int i = (int)t;
+  const float f = t - (float)i;
+  const float g0 = __ldg(tab + i);
+  const float g1 = __ldg(tab + i + 1);
+  return expf(fmaf(f, g1 - g0, g0));
+}
+
+// Isotropic unit vector: cos(theta) = 2u0 - 1, phi = 2 pi u1.
+__device__ __forceinline__ float3 iso_dir(float u0, float u1) {
+  const float ct = fmaf(2.0f, u0, -1.0f);
+  const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+  float sp, cp;
+  sincospif(2.0f * u1, &sp, &cp);
+  return make_float3(st * cp, st * sp, ct);
+}
+
+// Composition part of the record from the ion densities (Eqs. rho_def,
+// qn_def, kappa_debye's n_eff, prim_rate's sum Z^2 n).
+__device__ __forceinline__ void compute_composition(const CellConst& cc,
+                                                    const double* __restrict__ n_ion, float* rec) {
+  float rho_u = 0.f, ne = 0.f, zsq = 0.f, mh = 0.f;
+  for (int s = 0; s < cc.nspecies; ++s) {
+    const float n = (float)(n_ion[s] * 1e-24);
+    rho_u += n * cc.A[s];
+    ne += n * cc.Z[s];
+    zsq += n * cc.Z[s] * cc.Z[s];
+    if (cc.is_h[s]) mh += n * cc.A[s];
+  }
+  const float neff = ne + zsq;
+  rec[R_NE] = ne;
+  rec[R_NEFF] = neff;
+  rec[R_RHO] = rho_u * cc.k_rho;
+  rec[R_XH] = rho_u > 0.f ? mh / rho_u : 0.f;
+  rec[R_SZ] = cc.prim_targets == 0 ? zsq : neff;
+  rec[R_AP] = cc.k_AP * rec[R_SZ];
+  rec[R_APINV] = cc.prim_mult * rec[R_AP];
+}
+
+struct CellExtras {
+  float kappa, QC, QB, eta;
+};
+
+// Temperature part of the record (Eqs. kappa_debye, epsC, QC, GammaC,
+// eps_eZ, eps_ee, gamma_abs), binary32 from the composition slots.
+__device__ __forceinline__ CellExtras compute_temperature(const CellConst& cc, float T, float* rec) {
+  const float invT = 1.0f / T;
+  const float ne = rec[R_NE];
+  const float rho = rec[R_RHO];
+  const float XH = rec[R_XH];
+  float kappa2;
+  if (cc.kappa_mode == 0) kappa2 = cc.k_kappa2 * rec[R_NEFF] * invT;
+  else kappa2 = cc.kappa_fixed * cc.kappa_fixed;
+  const float T7 = T * cc.k_T7;
+  const float rho2 = rho * 0.01f;
+  const float T7sq = T7 * T7;
+  const float eta = (3.0f + XH) * rho2 / T7sq;
+  const float onepx = 1.0f + XH;
+  const float eps_C = 2.67e-2f * onepx * (T7sq * T7sq * T7sq) * cc.afac;
+  const float t25 = T7sq * sqrtf(T7);
+  const float eps_eZ = 0.150f * t25 * rho2 * onepx * cc.afac * fmaxf(0.f, 1.0f - 6.98e-2f * eta);
+  float eps_ee = 0.f;
+  if (cc.brems_ee)
+    eps_ee = 0.150f * t25 * rho2 * onepx * (onepx * 0.35355339059327373f) * cc.afac *
+             fmaxf(0.f, 1.0f - 0.140f * eta);
+  const float QC = rho * eps_C;
+  const float QB = rho * (eps_eZ + eps_ee);
+  rec[R_T] = T;
+  rec[R_INVT] = invT;
+  rec[R_FOURK2] = 4.0f / kappa2;
+  rec[R_CC] = ne > 0.f ? QC * cc.k_CC / (ne * T) : 0.f;
+  rec[R_CB] = ne > 0.f ? QB * cc.k_CB / (ne * T) : 0.f;
+  const float invT2 = invT * invT;
+  rec[R_BC] = QC * cc.k_BC * (invT2 * invT2);
+  rec[R_BB] = QB * cc.k_BB * (invT2 * invT2);
+  CellExtras ex;
+  ex.kappa = sqrtf(kappa2);
+  ex.QC = QC;
+  ex.QB = QB;
+  ex.eta = eta;
+  return ex;
+}
+
+// Primakoff conversion probability over one step (Eqs. prim_xs to
+// prim_prob): P = 1 - exp(-A F(4 omega^2 / kappa^2)), A = R_AP or R_APINV.
+__device__ __forceinline__ float prim_prob(const float* rec, float omega, float A) {
+  const float s = omega * omega * rec[R_FOURK2];
+  return -expm1f(-A * prim_F(s));
+}
+
+// Detailed-balance absorption optical depths over one step (Eq. gamma_abs):
+// Compton-like tau_C = R_BC x^2 e^x/(e^x-1) (MB) or R_BC x^2 (BE);
+// bremsstrahlung tau_B = R_BB x^(a-3) (MB) or R_BB x^(a-3) (1-e^-x) (BE).
+__device__ __forceinline__ float tau_compton(const float* rec, float x, int eq_stats) {
+  const float base = rec[R_BC] * x * x;
+  return eq_stats ? base : base / (-expm1f(-x));
+}
+
+__device__ __forceinline__ float tau_brems(const float* rec, float x, float am3, int eq_stats) {
+  const float base = rec[R_BB] * powf(x, am3);
+  return eq_stats ? base * (-expm1f(-x)) : base;
+}
+
+// Kernel parameters shared by the step kernels (passed by value).
+struct StepArgs {
+  SpeciesPtrs e, g, a;
+  int ncells;
+  uint32_t cell_base;     // global index of cell 0 (low 32 bits)
+  uint32_t step;
+  uint32_t key0, key1;
+  int mask;
+  float w_a, w_gref, inv_w_a, inv_w_gref;
+  float lam_cap;          // effective cap, <= 64
+  float brems_am3;        // a - 3
+  int eq_stats, absorb_mode, T_mode, tally_enable, diag_enable, use_snapshot;
+  float relax_r;
+  double T_floor, T_ceil;
+  float* rec;             // [ncells * kRecLen]
+  float* mom;             // [ncells * kMomLen]
+  double* T;              // [ncells]
+  const double* n_ion;    // [ncells * nspecies]
+  double* xbuf;           // [ncells * 4] exchange buffer (separate calls)
+  double* res;            // [ncells * 4] carried energy / momentum
+  double* diag;           // [ncells * AXPIC_CELL_DIAG_LEN]
+  int32_t* photon_start;  // [ncells] photon count before absorb
+  const float* tables;    // [kNumTables * kTableN]
+  double* tally;          // [3 * nbins + 6]
+  int nbins;
+  float inv_dE_bin;
+  unsigned long long* counters;  // [gridDim * kNumCounters]
+  int* err;
+  CellConst cc;
+};
+
+}  // namespace axpic

@@ -1,0 +1,13 @@
+// Launch interface of the step kernels (internal to libaxpic).
+#pragma once
+#include "common.cuh"
+
+namespace axpic {
+
+enum { PH_ABSORB = 1, PH_EMIT = 2, PH_FEEDBACK = 4, PH_ALL = 7 };
+
+size_t step_smem_per_warp(int acap, int gcap, int ecap);
+cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t st);
+cudaError_t set_step_smem_limits(size_t bytes);
+
+}  // namespace axpic
