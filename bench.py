@@ -43,12 +43,13 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nx", type=int, default=256, help="cells per side (256: the full workload)")
     return ap.parse_args()
 
 
-def workload():
+def workload(nx=256):
     from paper_2604_24627_gb300 import workloads
-    w = workloads.config2()
+    w = workloads.config2(nx, nx)
     wg = workloads.photon_weight(3.0, w.volume_cm3, w.n_ph)
     w.params["w_a"] = float(np.float32(wg * w.w_a_over_w_gamma))
     w.params["seed"] = 0
@@ -228,7 +229,7 @@ def main():
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = workload()
+    w = workload(args.nx)
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         pl = AxionPlasma(w.ncells, w.T_keV, w.n_ion, w.Z, w.A, w.volume_cm3, w.caps, w.params, device=dev,

@@ -23,8 +23,9 @@ each): step order absorb -> emit -> feedback; Philox4x32-10 counters
 particle, word (i & 3) of block (i >> 2); event j of particle i uses block
 (step, cell, i, stream<<24 | j) with words (cos theta, phi, energy); new axions
 are appended after the survivors, photon products first (photon order), then
-electron products (electron order, Compton events before bremsstrahlung
-events); removed particles leave holes that are filled by the survivors found
+electron products (electron order, then event order; an electron's two
+thermal-bath channels are drawn as one superposed Poisson process and each
+event is attributed to a channel by a further uniform); removed particles leave holes that are filled by the survivors found
 beyond the new count, in ascending order ("tail fill"); weights are binary32
 quantities and depletion is evaluated in binary32 because it decides whether
 the parent survives.
@@ -46,12 +47,10 @@ CH_COMPTON = 2
 CH_BREMS = 4
 
 STREAM_PRIM_FWD = 0
-STREAM_COMPTON = 1
-STREAM_BREMS = 2
+STREAM_EMIT_E = 1      # thermal-bath emission decision of an electron (both channels)
 STREAM_PRIM_INV = 3
 STREAM_ABSORB = 4
-STREAM_EV_COMPTON = 5
-STREAM_EV_BREMS = 6
+STREAM_EV_E = 5        # thermal-bath emission event (direction, energy, channel)
 STREAM_INIT_E = 8
 STREAM_INIT_G = 9
 STREAM_INIT_A = 10
@@ -287,49 +286,46 @@ def emit_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTall
     e = parts["e"]
     ne = len(e)
     if (mask & (CH_COMPTON | CH_BREMS)) and ne > 0:
-        per_channel = []
-        for ch, rate, dstream, estream, icdf in (
-                (CH_COMPTON, cs.Gamma_C, STREAM_COMPTON, STREAM_EV_COMPTON, spectra.compton_icdf),
-                (CH_BREMS, cs.Gamma_B, STREAM_BREMS, STREAM_EV_BREMS,
-                 lambda uu: spectra.brems_icdf(p.brems_gamma_shape, uu))):
-            if not (mask & ch):
-                per_channel.append(None)
-                continue
-            lam = e.w * rate * p.dt_phys_s / w_a
-            lam_eff, fac, capped = cap_lambda(lam, p.lambda_cap)
-            u = decision_uniforms(p, step, cell, dstream, ne)
-            Kc = poisson_count(u, lam_eff)
-            tally.cap_hits += int(capped.sum())
+        # The Compton-like and bremsstrahlung operators of one electron are
+        # independent Poisson processes (Sec. II.D.1, per channel, each with
+        # its own cap, Eqs. lambda_eff and wa_rescaled). They are sampled as
+        # their superposition: K ~ Poisson(lambda_C,eff + lambda_B,eff), and
+        # event j goes to channel C when u < lambda_C,eff / (sum) (word 3 of
+        # the event's block), which has the same law as two separate draws.
+        zero = np.zeros(ne)
+        lam_c = e.w * cs.Gamma_C * p.dt_phys_s / w_a if mask & CH_COMPTON else zero
+        lam_b = e.w * cs.Gamma_B * p.dt_phys_s / w_a if mask & CH_BREMS else zero
+        le_c, fac_c, cap_c = cap_lambda(lam_c, p.lambda_cap)
+        le_b, fac_b, cap_b = cap_lambda(lam_b, p.lambda_cap)
+        tally.cap_hits += int(cap_c.sum()) + int(cap_b.sum())
+        # the sum and the channel split are decided in binary32 like the kernel
+        lc32, lb32 = f32(le_c), f32(le_b)
+        lsum32 = (lc32 + lb32).astype(F32)
+        frac_c = np.where(lsum32 > 0, (lc32 / np.where(lsum32 > 0, lsum32, F32(1))).astype(F32), F32(0))
+        u = decision_uniforms(p, step, cell, STREAM_EMIT_E, ne)
+        Kc = poisson_count(u, lsum32.astype(np.float64))
+        if Kc.sum() > 0:
             parent = np.repeat(np.arange(ne), Kc)
-            sub = np.concatenate([np.arange(k) for k in Kc]) if Kc.sum() > 0 else np.zeros(0, dtype=np.int64)
-            uu = event_uniforms(p, step, cell, estream, parent, sub)
-            xE = icdf(uu[:, 2]) if len(parent) else np.zeros(0)
+            sub = np.concatenate([np.arange(k) for k in Kc])
+            uu = event_uniforms(p, step, cell, STREAM_EV_E, parent, sub)
+            is_c = f32(uu[:, 3]) < frac_c[parent]
+            xE = np.where(is_c, spectra.compton_icdf(uu[:, 2]),
+                          spectra.brems_icdf(p.brems_gamma_shape, uu[:, 2]))
             E = xE * cs.T_keV
-            dx, dy, dz = isotropic(uu[:, 0], uu[:, 1]) if len(parent) else (np.zeros(0),) * 3
+            dx, dy, dz = isotropic(uu[:, 0], uu[:, 1])
             pm = E / K.ME_C2_KEV
-            wv = f32(w_a * fac[parent]).astype(np.float64)
+            fac = np.where(is_c, fac_c[parent], fac_b[parent])
+            wv = f32(w_a * fac).astype(np.float64)
             prods = Species(wv, pm * dx, pm * dy, pm * dz, e.x[parent], e.y[parent], e.z[parent])
             tally.dE -= float(np.sum(wv * E))
             tally.gross_E += float(np.sum(wv * E))
             tally.gross_P += float(np.sum(wv * pm))
             tally.dP -= np.array([np.sum(wv * prods.px), np.sum(wv * prods.py), np.sum(wv * prods.pz)])
-            name = "compton" if ch == CH_COMPTON else "brems"
-            tally.events[name] += int(Kc.sum())
-            per_channel.append((parent, prods, E, ch))
-        # electron order, Compton events of an electron before its bremsstrahlung events
-        pieces = [pc for pc in per_channel if pc is not None]
-        if pieces:
-            parent_all = np.concatenate([pc[0] for pc in pieces])
-            chan_rank = np.concatenate([np.full(len(pc[0]), r) for r, pc in enumerate(pieces)])
-            order = np.lexsort((chan_rank, parent_all))   # stable: event order kept within a channel
-            prods_all = pieces[0][1]
-            for pc in pieces[1:]:
-                prods_all = prods_all.concat(pc[1])
-            E_all = np.concatenate([pc[2] for pc in pieces])
-            ch_all = np.concatenate([np.full(len(pc[0]), pc[3]) for pc in pieces])
-            new_blocks.append(prods_all.take(order))
-            chan_blocks.append(ch_all[order])
-            energy_blocks.append(E_all[order])
+            tally.events["compton"] += int(is_c.sum())
+            tally.events["brems"] += int((~is_c).sum())
+            new_blocks.append(prods)
+            chan_blocks.append(np.where(is_c, CH_COMPTON, CH_BREMS))
+            energy_blocks.append(E)
     if new_blocks:
         new = new_blocks[0]
         for b in new_blocks[1:]:

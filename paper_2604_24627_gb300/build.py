@@ -24,28 +24,32 @@ def nvcc():
     raise RuntimeError("nvcc not found")
 
 
-def _compile(src):
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-    cmd = [nvcc()] + ARCH + FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+def _compile(src, defines=(), tag=""):
+    obj = os.path.join(BUILD, tag + os.path.basename(src) + ".o")
+    cmd = [nvcc()] + ARCH + FLAGS + ["-D" + d for d in defines] + ["-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
     return obj
 
 
-def build(verbose=False):
+def build(verbose=False, defines=(), out=None):
+    """Compile and link; `defines` (NAME=VALUE strings) and `out` select a
+    variant build (launch-shape tuning), the default is the package library."""
     os.makedirs(BUILD, exist_ok=True)
+    tag = "_".join(d.replace("=", "") for d in defines) + "_" if defines else ""
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(_compile, SOURCES))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, defines, tag), SOURCES))
+    lib = out or LIB
+    tmp = lib + ".tmp"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
-        print("built", LIB)
-    return LIB
+        print("built", lib)
+    return lib
 
 
 if __name__ == "__main__":

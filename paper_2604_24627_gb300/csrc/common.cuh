@@ -26,8 +26,12 @@ constexpr float kLambdaHardCap = 64.0f;
 
 // Philox streams (counter word 3 = stream << 24 | sub).
 enum : uint32_t {
-  S_PRIM_FWD = 0, S_COMPTON = 1, S_BREMS = 2, S_PRIM_INV = 3, S_ABSORB = 4,
-  S_EV_COMPTON = 5, S_EV_BREMS = 6, S_INIT_E = 8, S_INIT_G = 9, S_INIT_A = 10
+  S_PRIM_FWD = 0,  // gamma->a decision of a photon
+  S_EMIT_E = 1,    // thermal-bath emission decision of an electron (both channels)
+  S_PRIM_INV = 3,  // a->gamma decision of an axion
+  S_ABSORB = 4,    // absorption decision of an axion
+  S_EV_E = 5,      // thermal-bath event: cos theta, phi, energy, channel
+  S_INIT_E = 8, S_INIT_G = 9, S_INIT_A = 10
 };
 constexpr uint32_t kInitStep = 0xFFFFFFFFu;
 
@@ -55,9 +59,11 @@ enum {
   R_SZ         // Primakoff target sum / 1e24 cm^-3                 [composition]
 };
 
-// Cached electron moments per cell (binary32): W, Px, Py, Pz, U2, var.
+// Cached electron moments per cell (binary32): W, Px, Py, Pz, U2, var, and
+// the common electron weight when every electron of the cell has the same
+// weight (0 otherwise). Electrons change only through the remap.
 constexpr int kMomLen = 8;
-enum { M_W = 0, M_PX, M_PY, M_PZ, M_U2, M_VAR };
+enum { M_W = 0, M_PX, M_PY, M_PZ, M_U2, M_VAR, M_WU };
 
 // Per-CTA counters (u64), reduced by axpic_tally_spectrum.
 enum {
@@ -281,7 +287,7 @@ __device__ __forceinline__ float tau_compton(const float* rec, float x, int eq_s
 }
 
 __device__ __forceinline__ float tau_brems(const float* rec, float x, float am3, int eq_stats) {
-  const float base = rec[R_BB] * powf(x, am3);
+  const float base = rec[R_BB] * exp2f(am3 * log2f(x));
   return eq_stats ? base * (-expm1f(-x)) : base;
 }
 

@@ -77,8 +77,11 @@ __global__ void moments_kernel(int ncells, SpeciesPtrs e, float* mom) {
   const int n = min(max(e.count[c], 0), e.cap);
   const long b = (long)c * e.cap;
   float W = 0.f, Px = 0.f, Py = 0.f, Pz = 0.f, U2 = 0.f;
+  float wmin = 3.0e38f, wmax = -3.0e38f;
   for (int i = lane; i < n; i += 32) {
     const float w = e.w[b + i], px = e.px[b + i], py = e.py[b + i], pz = e.pz[b + i];
+    wmin = fminf(wmin, w);
+    wmax = fmaxf(wmax, w);
     W += w;
     Px += w * px;
     Py += w * py;
@@ -91,6 +94,8 @@ __global__ void moments_kernel(int ncells, SpeciesPtrs e, float* mom) {
     Py += __shfl_xor_sync(kFullMask, Py, o);
     Pz += __shfl_xor_sync(kFullMask, Pz, o);
     U2 += __shfl_xor_sync(kFullMask, U2, o);
+    wmin = fminf(wmin, __shfl_xor_sync(kFullMask, wmin, o));
+    wmax = fmaxf(wmax, __shfl_xor_sync(kFullMask, wmax, o));
   }
   if (lane == 0) {
     float* m = mom + (size_t)c * kMomLen;
@@ -100,7 +105,7 @@ __global__ void moments_kernel(int ncells, SpeciesPtrs e, float* mom) {
     m[M_PZ] = Pz;
     m[M_U2] = U2;
     m[M_VAR] = W > 0.f ? fmaxf(0.f, U2 - (Px * Px + Py * Py + Pz * Pz) / W) : 0.f;
-    m[6] = 0.f;
+    m[M_WU] = (n > 0 && wmin == wmax && wmin > 0.f) ? wmin : 0.f;
     m[7] = 0.f;
   }
 }

@@ -34,7 +34,7 @@ def base_params(**kw):
     return prm
 
 
-def make(ncells, T, prm, caps=(64, 128, 128), n_e=6e25, counts=(61, 37, 13), cell_index_base=0):
+def make(ncells, T, prm, caps=(64, 192, 512), n_e=6e25, counts=(61, 37, 13), cell_index_base=0):
     pl = AxionPlasma(ncells, T, mix_density(n_e, ncells), MIX_Z, MIX_A, 1e-12, caps, prm,
                      cell_index_base=cell_index_base)
     pl.sample(*counts)

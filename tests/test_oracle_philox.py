@@ -57,8 +57,8 @@ def test_uniformity_chi_square():
 
 def test_decision_word_layout():
     p = Params(seed=0x0000000500000003)
-    u = ostep.decision_uniforms(p, 9, 17, ostep.STREAM_COMPTON, 10)
+    u = ostep.decision_uniforms(p, 9, 17, ostep.STREAM_EMIT_E, 10)
     for i in range(10):
-        blk = philox4x32_10(np.array([9, 17, i >> 2, ostep.STREAM_COMPTON << 24], dtype=np.uint32),
+        blk = philox4x32_10(np.array([9, 17, i >> 2, ostep.STREAM_EMIT_E << 24], dtype=np.uint32),
                             (3, 5))
         assert u[i] == uniform23(blk[i & 3])

@@ -316,3 +316,35 @@ def test_primakoff_pair_steady_state():
         if m == 1.0:
             plateau = np.mean(qg / (qg + qa))
             assert abs(plateau - 0.5) < 1e-12
+
+
+def test_superposed_channels_keep_each_channel_power():
+    """Compton-like and bremsstrahlung drawn as one Poisson process per
+    electron: each channel's emitted power still equals its own Q V dt, and
+    the event split follows lambda_C : lambda_B (superposition of Poisson
+    processes, Sec. II.D.1 per channel)."""
+    T, V = 3.0, 1e-12
+    ci = S.CellInput(T, *_hyd())
+    p = Params(g_ae=1e-13, dt_phys_s=1e12, seed=12)
+    cs = cell_state(T, *_hyd(), p)
+    e = _electrons(256, T)
+    e.w[:] = 6e25 * V / 256
+    p.w_a = (cs.Q_C + cs.Q_B) * V * p.dt_phys_s / (80 * 4.0 * T * K.KEV_ERG)
+    steps = 60
+    UC = UB = 0.0
+    NC = NB = 0
+    for st in range(steps):
+        pr = {"e": e.copy(), "g": S.Species.empty(), "a": S.Species.empty()}
+        t = S.StepTally()
+        S.emit_cell(cs, pr, p, st, 0, S.CH_COMPTON | S.CH_BREMS, t)
+        a = pr["a"]
+        isC = t.new_axion_channel == S.CH_COMPTON
+        UC += np.sum(a.w[isC] * t.new_axion_E[isC])
+        UB += np.sum(a.w[~isC] * t.new_axion_E[~isC])
+        NC += t.events["compton"]
+        NB += t.events["brems"]
+    QV = V * p.dt_phys_s * steps / K.KEV_ERG
+    assert abs(UC / (cs.Q_C * QV) - 1) < 0.06
+    assert abs(UB / (cs.Q_B * QV) - 1) < 0.12
+    lam_ratio = (cs.Gamma_C / cs.Gamma_B)
+    assert abs((NC / NB) / lam_ratio - 1) < 0.2
