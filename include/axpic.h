@@ -116,7 +116,8 @@ typedef struct {
   double tally_Emax_keV;    /* histogram range [0, Emax) (80 keV) */
   int32_t tally_enable;     /* 1: step calls accumulate the emitted spectrum */
   int32_t diag_enable;      /* 1: feedback writes per-cell diagnostics */
-  int32_t threads_per_block;/* launch shape of the step kernel; 0: default */
+  int32_t threads_per_block;/* threads per CTA of the step kernel (32..128, one warp
+                               per cell); 0: default 128 */
   int32_t reserved[7];
 } axpic_params;
 
@@ -205,8 +206,8 @@ axpic_status axpic_emit(axpic_ctx *ctx, int64_t step, int32_t channel_mask);
  * (Eqs. Te_est, Te_relax) in temperature mode "evolved". Clears the buffer. */
 axpic_status axpic_feedback(axpic_ctx *ctx, int64_t step);
 
-/* One fused step, absorb -> emit -> feedback, in a single pass over each
- * cell's particles; identical results to the three calls above. */
+/* One step, absorb -> emit -> feedback: the three calls above enqueued
+ * together (identical results). */
 axpic_status axpic_step(axpic_ctx *ctx, int64_t step, int32_t channel_mask);
 
 /* Emitted-spectrum tally (App. B): H_out (host, 3*nbins doubles, channel-

@@ -106,9 +106,9 @@ static void fold_constants(axpic_ctx* ctx) {
   std::memset(&cc, 0, sizeof(cc));
   cc.nspecies = ctx->desc.nspecies;
   for (int s = 0; s < cc.nspecies; ++s) {
-    cc.Z[s] = (float)ctx->Z[s];
-    cc.A[s] = (float)ctx->A[s];
-    cc.is_h[s] = ctx->Z[s] == 1.0;
+    cc.Z[s] = (float)ctx->desc.Z[s];
+    cc.A[s] = (float)ctx->desc.A[s];
+    cc.is_h[s] = ctx->desc.Z[s] == 1.0;
   }
   cc.kappa_mode = p.kappa_mode;
   cc.kappa_fixed = (float)p.kappa_fixed_keV;
@@ -159,6 +159,9 @@ static StepArgs make_args(axpic_ctx* ctx, int64_t step, int mask) {
   A.relax_r = (float)p.relax_r;
   A.T_floor = p.T_floor_keV;
   A.T_ceil = p.T_ceil_keV;
+  // widened so that the binary32 test never misses a clamp the FP64 one needs
+  A.T_floor_f = (float)p.T_floor_keV * (1.0f + 1e-6f) + 1e-30f;
+  A.T_ceil_f = p.T_ceil_keV > 3e38 ? 3e38f : (float)p.T_ceil_keV * (1.0f - 1e-6f);
   A.rec = ctx->rec;
   A.mom = ctx->mom;
   A.T = ctx->desc.T_keV;
@@ -261,8 +264,8 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
   }
   const size_t per_warp = step_smem_per_warp(d.axions.capacity, d.photons.capacity, d.electrons.capacity);
   int warps = p.threads_per_block > 0 ? p.threads_per_block / 32 : kDefaultWarps;
-  if (warps < 1 || warps > 8 || (p.threads_per_block > 0 && p.threads_per_block % 32))
-    return bad("threads_per_block must be 32..256, a multiple of 32");
+  if (warps < 1 || warps > 4 || (p.threads_per_block > 0 && p.threads_per_block % 32))
+    return bad("threads_per_block must be 32..128, a multiple of 32");
   const size_t smem_limit = 227 * 1024 - 128;
   while (warps > 1 && per_warp * warps > smem_limit) --warps;
   if (per_warp > smem_limit) return bad("slab capacities too large for shared-memory scratch");
@@ -503,6 +506,7 @@ axpic_status axpic_destroy(axpic_ctx* ctx) {
   free_ctx(ctx);
   return s;
 }
+
 
 const char* axpic_last_error(const axpic_ctx* ctx) { return ctx ? ctx->last_error.c_str() : kNoCtxMsg; }
 

@@ -305,6 +305,7 @@ struct StepArgs {
   int eq_stats, absorb_mode, T_mode, tally_enable, diag_enable, use_snapshot;
   float relax_r;
   double T_floor, T_ceil;
+  float T_floor_f, T_ceil_f;  // binary32 copies for the common-path test
   float* rec;             // [ncells * kRecLen]
   float* mom;             // [ncells * kMomLen]
   double* T;              // [ncells]

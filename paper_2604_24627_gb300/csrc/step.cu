@@ -388,7 +388,7 @@ __device__ __noinline__ int feedback_cell(const StepArgs& A, int cell, long ebas
   float* mom = A.mom + (size_t)cell * kMomLen;
   const float W = mom[M_W], Px = mom[M_PX], Py = mom[M_PY], Pz = mom[M_PZ], U2 = mom[M_U2], var = mom[M_VAR];
   float var_new = var;
-  double s1d = 0.0, bx = 0.0, by = 0.0, bz = 0.0, applied_E = 0.0, vnd = var;
+  double s1d = 0.0, bx = 0.0, by = 0.0, bz = 0.0, applied_E = 0.0, vnd = 0.0;
   double nrE = 0.0, nrPx = 0.0, nrPy = 0.0, nrPz = 0.0;
   if (has_x || has_res) {
     const double qE = dE + rE, qPx = dPx + rPx, qPy = dPy + rPy, qPz = dPz + rPz;
@@ -408,6 +408,7 @@ __device__ __noinline__ int feedback_cell(const StepArgs& A, int cell, long ebas
       const double dx = qPx / Wd, dy = qPy / Wd, dz = qPz / Wd;
       const double dEb = (2.0 * (dx * Px + dy * Py + dz * Pz) + Wd * (dx * dx + dy * dy + dz * dz)) * 0.5;
       const double dEth = qE / kMeC2 - dEb;
+      vnd = var;
       if (var > 0.f) {
         vnd = fmax(0.0, (double)var + 2.0 * dEth);
         const double S = sqrt(vnd / (double)var);
@@ -451,7 +452,7 @@ __device__ __noinline__ int feedback_cell(const StepArgs& A, int cell, long ebas
     dg[AXPIC_CD_BY] = by;
     dg[AXPIC_CD_BZ] = bz;
     dg[AXPIC_CD_VAR] = var;
-    dg[AXPIC_CD_VAR_NEW] = vnd;
+    dg[AXPIC_CD_VAR_NEW] = remapped ? vnd : (double)var;
     dg[AXPIC_CD_W] = W;
     dg[AXPIC_CD_APPLIED_E] = applied_E;
     dg[AXPIC_CD_RES_E] = nrE;
@@ -461,10 +462,14 @@ __device__ __noinline__ int feedback_cell(const StepArgs& A, int cell, long ebas
   }
   // temperature (Eqs. Te_est, Te_relax), then the record's temperature half
   if (A.T_mode == 2 && W > 0.f) {
+    // T stays FP64; the relaxation step is formed in binary32 and added once
     const double T = A.T[cell];
+    const float Tf = (float)T;
     const float Test = (kMeC2f / 3.0f) * var_new / W;
-    double Tn = T + (double)(A.relax_r * (Test - (float)T));
-    Tn = fmin(fmax(Tn, A.T_floor), A.T_ceil);
+    const float dT = A.relax_r * (Test - Tf);
+    double Tn = T + (double)dT;
+    const float Tnf = Tf + dT;
+    if (Tnf <= A.T_floor_f || Tnf >= A.T_ceil_f) Tn = fmin(fmax(Tn, A.T_floor), A.T_ceil);
     float rec[kRecLen];
     const float4* ri = reinterpret_cast<const float4*>(A.rec + (size_t)cell * kRecLen);
 #pragma unroll
@@ -519,7 +524,9 @@ __device__ __forceinline__ void process_cell(const StepArgs& A, int cell, WarpSc
   Lane64 x64;
   double xa[4] = {0.0, 0.0, 0.0, 0.0};  // reduced absorb exchange (same order as separate calls)
   bool xa_any = false;
-  if (lane == 0 && (PH & (PH_ABSORB | PH_EMIT))) {
+  // particles present at the start of the step: counted by the absorb phase,
+  // or by the emit phase when no absorb ran this step
+  if (lane == 0 && ((PH & PH_ABSORB) || ((PH & PH_EMIT) && !A.use_snapshot))) {
     cnt.add(C_NE, ne);
     cnt.add(C_NG, ng_start);
     cnt.add(C_NA, na);
@@ -604,7 +611,7 @@ __device__ __forceinline__ void process_cell(const StepArgs& A, int cell, WarpSc
           const long src = abase + slot;
           const float w = A.a.w[src], px = A.a.px[src], py = A.a.py[src], pz = A.a.pz[src];
           const float xx = A.a.x[src], yy = A.a.y[src], zz = A.a.z[src];
-          const AxionDecision d = axion_decide(rec, A, mask, w, px, py, pz, word(rP, slot & 3), word(rA, slot & 3));
+          const AxionDecision d = axion_decide_slow(A, cell, mask, w, px, py, pz, word(rP, slot & 3), word(rA, slot & 3));
           for (int k = 0; k < K; ++k, ++off) {
             const int dst = ng + off;
             if (dst < A.g.cap) write_particle(A.g, gbase + dst, d.wprod, px, py, pz, xx, yy, zz);
@@ -761,7 +768,7 @@ __device__ __forceinline__ void process_cell(const StepArgs& A, int cell, WarpSc
           const long src = gbase + slot;
           const float w = A.g.w[src], px = A.g.px[src], py = A.g.py[src], pz = A.g.pz[src];
           const float xx = A.g.x[src], yy = A.g.y[src], zz = A.g.z[src];
-          const PhotonDecision d = photon_decide(rec, A, w, px, py, pz, word(r, slot & 3));
+          const PhotonDecision d = photon_decide_slow(A, cell, w, px, py, pz, word(r, slot & 3));
           for (int k = 0; k < K; ++k, ++off) {
             const int dst = abase_new + off;
             if (dst < A.a.cap) {
@@ -907,22 +914,27 @@ __device__ __forceinline__ void process_cell(const StepArgs& A, int cell, WarpSc
 template <int PH>
 __global__ void __launch_bounds__(128, AXPIC_STEP_MIN_CTAS) step_kernel(StepArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned long long cta_cnt[kNumCounters];
+  // per-warp counters: each warp flushes its own, so no warp waits for the
+  // slowest cell of its CTA
+  __shared__ unsigned long long warp_cnt[4][kNumCounters];
   const int wid = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int cell = blockIdx.x * nw + wid;
-  if (threadIdx.x < kNumCounters) cta_cnt[threadIdx.x] = 0ull;
-  __syncthreads();
-  const Cnt cnt{cta_cnt};
+  if (lane < kNumCounters) warp_cnt[wid][lane] = 0ull;
+  __syncwarp();
+  const Cnt cnt{warp_cnt[wid]};
   if (cell < A.ncells) {
     const size_t bytes = warp_scratch_bytes(A.a.cap, A.g.cap, A.e.cap);
     WarpScratch S = carve(smem + wid * bytes, A.a.cap, A.g.cap, A.e.cap);
     process_cell<PH>(A, cell, S, cnt);
   }
-  __syncthreads();
-  if (threadIdx.x < kNumCounters && cta_cnt[threadIdx.x])
-    A.counters[(size_t)blockIdx.x * kNumCounters + threadIdx.x] += cta_cnt[threadIdx.x];
-  if (threadIdx.x == 0 && cta_cnt[C_DROP]) atomicOr(A.err, ERR_CAPACITY);
+  __syncwarp();
+  if (lane < kNumCounters) {
+    const unsigned long long v = warp_cnt[wid][lane];
+    if (v) atomicAdd(A.counters + (size_t)blockIdx.x * kNumCounters + lane, v);
+    if (lane == C_DROP && v) atomicOr(A.err, ERR_CAPACITY);
+  }
 }
 
 size_t step_smem_per_warp(int acap, int gcap, int ecap) { return warp_scratch_bytes(acap, gcap, ecap); }
@@ -941,7 +953,17 @@ cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t s
     case PH_ABSORB: return launch<PH_ABSORB>(A, warps, st);
     case PH_EMIT: return launch<PH_EMIT>(A, warps, st);
     case PH_FEEDBACK: return launch<PH_FEEDBACK>(A, warps, st);
-    case PH_ALL: return launch<PH_ALL>(A, warps, st);
+    case PH_ALL: {
+      // one step as three kernels: each phase's code and registers stay small
+      // (a single fused kernel measured twice as slow); the exchange passes
+      // through the per-cell FP64 buffer in the same summation order
+      cudaError_t e = launch<PH_ABSORB>(A, warps, st);
+      if (e) return e;
+      StepArgs B = A;
+      B.use_snapshot = 1;
+      if ((e = launch<PH_EMIT>(B, warps, st))) return e;
+      return launch<PH_FEEDBACK>(A, warps, st);
+    }
     default: return cudaErrorInvalidValue;
   }
 }
@@ -950,8 +972,7 @@ cudaError_t set_step_smem_limits(size_t bytes) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(step_kernel<PH_ABSORB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes))) return e;
   if ((e = cudaFuncSetAttribute(step_kernel<PH_EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes))) return e;
-  if ((e = cudaFuncSetAttribute(step_kernel<PH_FEEDBACK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes))) return e;
-  return cudaFuncSetAttribute(step_kernel<PH_ALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaFuncSetAttribute(step_kernel<PH_FEEDBACK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 }  // namespace axpic
