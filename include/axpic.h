@@ -238,6 +238,36 @@ axpic_status axpic_get_cell_diag(axpic_ctx *ctx, int32_t first, int32_t count, d
  * per cell (keV, m_e c), into host_out. Synchronises the stream. */
 axpic_status axpic_get_residuals(axpic_ctx *ctx, int32_t first, int32_t count, double *host_out);
 
+/* One fused step (the same kernels as axpic_step) for callers that cannot
+ * allocate device memory: a host code whose memory manager owns the whole GPU
+ * heap, or a real-time loop where a cudaMalloc could stall or fail. It needs
+ * no context and calls no cudaMalloc, cudaFree or other allocating routine.
+ * The paper has no counterpart: this is an interface convenience.
+ *
+ * Its scratch (rate records, electron moments, sampling tables, counters,
+ * exchange buffer, photon counts, error flag; about 2.8 MB) is a file-scope
+ * device array of the library, held
+ * by every GPU that loads the library until the process exits; it limits a
+ * call to 16384 cells (more returns AXPIC_E_INVALID without launching).
+ * The first call on a device looks up the array's device address with that
+ * device current and uploads the sampling tables; make that first call
+ * before any stream capture. Later calls reupload the tables only when
+ * brems_gamma_shape changes.
+ *
+ * desc, params: as for axpic_init_plasma (read during the call).
+ * carry: device [ncells*4] FP64, owned by the caller, read and written: the
+ *   energy (keV) and momentum (m_e c) not yet applied by the remap, which
+ *   axpic_step keeps inside its context; zero it before the first step.
+ * Rates are recomputed from T_keV and n_ion, and electron moments from the
+ * electrons, on every call; no tally or per-cell diagnostics are produced.
+ * Every call shares the one scratch array (it keeps the last call's
+ * contents; what must start at zero is cleared by each call), so calls that
+ * overlap on the GPU, on different streams or threads, race. Synchronises
+ * the stream and returns AXPIC_E_CAPACITY or AXPIC_E_NUMERIC found on the
+ * device. */
+axpic_status axpic_step_noalloc(const axpic_plasma_desc *desc, const axpic_params *params, int64_t step,
+                                int32_t channel_mask, double *carry, void *stream);
+
 /* Wait for the stream and return the first latched device error, if any. */
 axpic_status axpic_sync(axpic_ctx *ctx);
 

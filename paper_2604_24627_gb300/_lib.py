@@ -83,6 +83,8 @@ EXPORTS = {
                                            ctypes.POINTER(ctypes.c_double)]),
     "axpic_get_residuals": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_double)]),
+    "axpic_step_noalloc": (ctypes.c_int, [ctypes.POINTER(PlasmaDesc), ctypes.POINTER(Params), ctypes.c_int64,
+                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "axpic_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "axpic_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "axpic_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -169,6 +171,15 @@ def axpic_get_cell_diag(ctx, first, count, out):
 
 def axpic_get_residuals(ctx, first, count, out):
     _check(ctx, lib().axpic_get_residuals(ctx, first, count, out))
+
+
+def axpic_step_noalloc(desc, params, step, mask, carry_ptr, stream=0):
+    """One fused step without a context or any allocation (carry: device
+    pointer to ncells*4 doubles, caller-owned)."""
+    st = lib().axpic_step_noalloc(ctypes.byref(desc), ctypes.byref(params), step, mask,
+                                  ctypes.c_void_p(carry_ptr), ctypes.c_void_p(stream))
+    if st != AXPIC_OK:
+        raise AxpicError(st, "axpic_step_noalloc failed (see stderr)")
 
 
 def axpic_sync(ctx):

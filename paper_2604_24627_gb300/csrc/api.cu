@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -507,6 +508,118 @@ axpic_status axpic_destroy(axpic_ctx* ctx) {
   return s;
 }
 
+
+// ---------------------------------------------------------------- no-alloc step
+// Scratch of axpic_step_noalloc: a file-scope device array, so the call
+// allocates nothing. Every GPU that loads the library holds it until exit.
+// Layout: rate records, electron moments, sampling tables, per-CTA counters,
+// error flag.
+namespace {
+constexpr int kNoAllocMaxCells = 16384;
+constexpr int kNoAllocWarps = 4;
+constexpr int kNoAllocMaxGrid = kNoAllocMaxCells / kNoAllocWarps;
+constexpr size_t kNaRec = 0;
+constexpr size_t kNaMom = kNaRec + sizeof(float) * kRecLen * kNoAllocMaxCells;
+constexpr size_t kNaTables = kNaMom + sizeof(float) * kMomLen * kNoAllocMaxCells;
+constexpr size_t kNaCounters = kNaTables + sizeof(float) * kNumTables * kTableN;
+constexpr size_t kNaErr = kNaCounters + sizeof(unsigned long long) * kNumCounters * kNoAllocMaxGrid;
+constexpr size_t kNaXbuf = kNaErr + 256;
+constexpr size_t kNaStart = kNaXbuf + sizeof(double) * 4 * kNoAllocMaxCells;
+constexpr size_t kNaUnused = kNaStart + sizeof(int32_t) * kNoAllocMaxCells;  // diagnostic/tally slots never touched
+constexpr size_t kNoAllocBytes = kNaUnused + 256;
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_na_mu;
+unsigned char* g_na_base[kNoAllocMaxDevices] = {};
+double g_na_brems[kNoAllocMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+axpic_status axpic_step_noalloc(const axpic_plasma_desc* desc, const axpic_params* params, int64_t step,
+                                int32_t channel_mask, double* carry, void* stream) {
+  if (!desc || !params || !carry) return AXPIC_E_INVALID;
+  const axpic_plasma_desc& d = *desc;
+  const axpic_params& p = *params;
+  auto bad = [](const char* m) {
+    fprintf(stderr, "axpic_step_noalloc: %s\n", m);
+    return AXPIC_E_INVALID;
+  };
+  if (d.ncells < 0 || d.ncells > kNoAllocMaxCells) return bad("ncells outside [0, 16384], the scratch maximum");
+  if (d.nspecies < 1 || d.nspecies > kMaxSpecies || !d.Z || !d.A) return bad("bad ion species");
+  if (d.ncells > 0 && (!d.T_keV || !d.n_ion)) return bad("T_keV or n_ion is NULL");
+  if (d.cell_index_base < 0 || d.cell_index_base + d.ncells > (int64_t)0xFFFFFFFF) return bad("cell indices");
+  for (auto sp : {&d.electrons, &d.photons, &d.axions})
+    if (!check_species(*sp, "species").empty()) return bad("bad species slab");
+  if (!(p.dt_phys_s > 0) || !(p.w_a > 0) || !(p.brems_gamma_shape > 0)) return bad("bad params");
+  if (p.T_mode < 0 || p.T_mode > 2 || p.eq_stats < 0 || p.eq_stats > 1 || p.absorb_mode < 0 || p.absorb_mode > 1)
+    return bad("bad params");
+  if (step < 0 || step >= (int64_t)0xFFFFFFFF || (channel_mask & ~AXPIC_CH_ALL)) return bad("bad step or mask");
+  const size_t per_warp = step_smem_per_warp(d.axions.capacity, d.photons.capacity, d.electrons.capacity);
+  if (per_warp * kNoAllocWarps > 227 * 1024 - 128) return bad("slab capacities too large");
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return AXPIC_E_CUDA;
+  unsigned char* base = nullptr;
+  {
+    // set-up, once per device and with that device current: the device
+    // address of the scratch array (its name is only a host stand-in here)
+    // and the sampling tables for the requested bremsstrahlung shape
+    std::lock_guard<std::mutex> lock(g_na_mu);
+    if (!g_na_base[dev]) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return AXPIC_E_CUDA;
+      g_na_base[dev] = static_cast<unsigned char*>(ptr);
+      g_na_brems[dev] = -1.0;
+    }
+    base = g_na_base[dev];
+    if (g_na_brems[dev] != p.brems_gamma_shape) {
+      static float tab[kNumTables * kTableN];
+      build_tables(p.brems_gamma_shape, tab);
+      if (cudaMemcpyAsync(base + kNaTables, tab, sizeof(tab), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return AXPIC_E_CUDA;
+      g_na_brems[dev] = p.brems_gamma_shape;
+    }
+  }
+  // a context on the stack that points into the scratch (no member allocates)
+  axpic_ctx c;
+  c.desc = d;
+  c.prm = p;
+  c.prm.diag_enable = 0;
+  c.prm.tally_enable = 0;
+  c.stream = st;
+  c.rec = reinterpret_cast<float*>(base + kNaRec);
+  c.mom = reinterpret_cast<float*>(base + kNaMom);
+  c.tables = reinterpret_cast<float*>(base + kNaTables);
+  c.counters = reinterpret_cast<unsigned long long*>(base + kNaCounters);
+  c.err = reinterpret_cast<int*>(base + kNaErr);
+  c.xbuf = reinterpret_cast<double*>(base + kNaXbuf);
+  c.photon_start = reinterpret_cast<int32_t*>(base + kNaStart);
+  c.diag = reinterpret_cast<double*>(base + kNaUnused);
+  c.tally = reinterpret_cast<double*>(base + kNaUnused);
+  c.res = carry;
+  c.warps = kNoAllocWarps;
+  c.grid = (d.ncells + kNoAllocWarps - 1) / kNoAllocWarps;
+  fold_constants(&c);
+  const StepArgs A = make_args(&c, step, channel_mask);
+  int h_err = 0;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(c.err, 0, sizeof(int), st)) ||
+      (e = cudaMemsetAsync(c.counters, 0, sizeof(unsigned long long) * kNumCounters * (size_t)c.grid, st)) ||
+      (e = cudaMemsetAsync(c.xbuf, 0, sizeof(double) * 4 * (size_t)d.ncells, st)) ||
+      (e = set_step_smem_limits(per_warp * kNoAllocWarps)) ||
+      (e = launch_records(d.ncells, d.nspecies, c.cc, d.T_keV, d.n_ion, c.rec, c.err, st)) ||
+      (e = launch_moments(d.ncells, to_ptrs(d.electrons), c.mom, st)) ||
+      (e = launch_step(PH_ALL, A, kNoAllocWarps, st)) ||
+      (e = cudaMemcpyAsync(&h_err, c.err, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+      (e = cudaStreamSynchronize(st))) {
+    fprintf(stderr, "axpic_step_noalloc: %s\n", cudaGetErrorString(e));
+    return AXPIC_E_CUDA;
+  }
+  if (h_err & ERR_CAPACITY) return AXPIC_E_CAPACITY;
+  if (h_err & ERR_NUMERIC) return AXPIC_E_NUMERIC;
+  return AXPIC_OK;
+}
 
 const char* axpic_last_error(const axpic_ctx* ctx) { return ctx ? ctx->last_error.c_str() : kNoCtxMsg; }
 
