@@ -238,17 +238,18 @@ axpic_status axpic_get_cell_diag(axpic_ctx *ctx, int32_t first, int32_t count, d
  * per cell (keV, m_e c), into host_out. Synchronises the stream. */
 axpic_status axpic_get_residuals(axpic_ctx *ctx, int32_t first, int32_t count, double *host_out);
 
-/* One fused step (the same kernels as axpic_step) for callers that cannot
+/* One step (the same kernels as axpic_step) for callers that cannot
  * allocate device memory: a host code whose memory manager owns the whole GPU
  * heap, or a real-time loop where a cudaMalloc could stall or fail. It needs
  * no context and calls no cudaMalloc, cudaFree or other allocating routine.
  * The paper has no counterpart: this is an interface convenience.
  *
  * Its scratch (rate records, electron moments, sampling tables, counters,
- * exchange buffer, photon counts, error flag; about 2.8 MB) is a file-scope
- * device array of the library, held
- * by every GPU that loads the library until the process exits; it limits a
- * call to 16384 cells (more returns AXPIC_E_INVALID without launching).
+ * exchange buffer, photon counts, decision bit masks, error flag; about
+ * 6.9 MB) is a file-scope device array of the library, held by every GPU that
+ * loads the library until the process exits. It limits a call to 16384 cells
+ * and to ncells * (sum of the three capacities) / 8 <= 4 MiB of bit masks;
+ * larger requests return AXPIC_E_INVALID without launching.
  * The first call on a device looks up the array's device address with that
  * device current and uploads the sampling tables; make that first call
  * before any stream capture. Later calls reupload the tables only when

@@ -46,6 +46,7 @@ struct axpic_ctx {
   unsigned long long* counters = nullptr;
   int* err = nullptr;
   double* scratch = nullptr;  // totals (8) + counters (kNumCounters) + info chunk
+  uint32_t* bits = nullptr;   // decision bit masks: axions, photons, electrons
   CellConst cc;
   int warps = kDefaultWarps;
   int grid = 0;
@@ -177,13 +178,19 @@ static StepArgs make_args(axpic_ctx* ctx, int64_t step, int mask) {
   A.inv_dE_bin = (float)(p.tally_nbins / p.tally_Emax_keV);
   A.counters = ctx->counters;
   A.err = ctx->err;
+  A.Wa = (ctx->desc.axions.capacity + 31) / 32;
+  A.Wg = (ctx->desc.photons.capacity + 31) / 32;
+  A.We = (ctx->desc.electrons.capacity + 31) / 32;
+  A.bitsA = ctx->bits;
+  A.bitsG = ctx->bits + (size_t)A.Wa * ctx->desc.ncells;
+  A.bitsE = A.bitsG + (size_t)A.Wg * ctx->desc.ncells;
   A.cc = ctx->cc;
   return A;
 }
 
 static void free_ctx(axpic_ctx* ctx) {
-  void* bufs[] = {ctx->rec,    ctx->mom,    ctx->xbuf,     ctx->res, ctx->diag, ctx->photon_start,
-                  ctx->tables, ctx->tally, ctx->counters, ctx->err, ctx->scratch};
+  void* bufs[] = {ctx->rec,    ctx->mom,   ctx->xbuf,     ctx->res, ctx->diag,    ctx->photon_start,
+                  ctx->tables, ctx->tally, ctx->counters, ctx->err, ctx->scratch, ctx->bits};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete ctx;
@@ -293,6 +300,9 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
   ALLOC(ctx->counters, sizeof(unsigned long long) * kNumCounters * (size_t)ctx->grid);
   ALLOC(ctx->err, sizeof(int));
   ALLOC(ctx->scratch, sizeof(double) * (8 + kNumCounters + (size_t)kInfoChunk * AXPIC_CELL_INFO_LEN));
+  const size_t bit_words = (size_t)n * ((d.axions.capacity + 31) / 32 + (d.photons.capacity + 31) / 32 +
+                                        (d.electrons.capacity + 31) / 32);
+  ALLOC(ctx->bits, sizeof(uint32_t) * bit_words);
 #undef ALLOC
   std::vector<float> tab((size_t)kNumTables * kTableN);
   build_tables(p.brems_gamma_shape, tab.data());
@@ -305,6 +315,7 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
       (e = cudaMemsetAsync(ctx->tally, 0, sizeof(double) * (3 * (size_t)p.tally_nbins + 6), st)) ||
       (e = cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * kNumCounters * (size_t)ctx->grid, st)) ||
       (e = cudaMemsetAsync(ctx->err, 0, sizeof(int), st)) ||
+      (e = cudaMemsetAsync(ctx->bits, 0, sizeof(uint32_t) * (bit_words > 0 ? bit_words : 1), st)) ||
       (e = set_step_smem_limits(per_warp * warps)) ||
       (e = launch_records(n, d.nspecies, ctx->cc, d.T_keV, d.n_ion, ctx->rec, ctx->err, st)) ||
       (e = launch_moments(n, to_ptrs(d.electrons), ctx->mom, st)) || (e = cudaStreamSynchronize(st))) {
@@ -525,7 +536,9 @@ constexpr size_t kNaCounters = kNaTables + sizeof(float) * kNumTables * kTableN;
 constexpr size_t kNaErr = kNaCounters + sizeof(unsigned long long) * kNumCounters * kNoAllocMaxGrid;
 constexpr size_t kNaXbuf = kNaErr + 256;
 constexpr size_t kNaStart = kNaXbuf + sizeof(double) * 4 * kNoAllocMaxCells;
-constexpr size_t kNaUnused = kNaStart + sizeof(int32_t) * kNoAllocMaxCells;  // diagnostic/tally slots never touched
+constexpr size_t kNaBitsBytes = 4u << 20;  // decision bit masks: cells * (acap + gcap + ecap) / 8 bytes
+constexpr size_t kNaBits = kNaStart + sizeof(int32_t) * kNoAllocMaxCells;
+constexpr size_t kNaUnused = kNaBits + kNaBitsBytes;  // diagnostic/tally slots never touched
 constexpr size_t kNoAllocBytes = kNaUnused + 256;
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_na_mu;
@@ -556,6 +569,10 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc* desc, const axpic_param
   if (step < 0 || step >= (int64_t)0xFFFFFFFF || (channel_mask & ~AXPIC_CH_ALL)) return bad("bad step or mask");
   const size_t per_warp = step_smem_per_warp(d.axions.capacity, d.photons.capacity, d.electrons.capacity);
   if (per_warp * kNoAllocWarps > 227 * 1024 - 128) return bad("slab capacities too large");
+  const size_t bit_bytes = sizeof(uint32_t) * (size_t)d.ncells *
+                           ((d.axions.capacity + 31) / 32 + (d.photons.capacity + 31) / 32 +
+                            (d.electrons.capacity + 31) / 32);
+  if (bit_bytes > kNaBitsBytes) return bad("ncells * (capacities) / 8 above the 4 MiB mask scratch");
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return AXPIC_E_CUDA;
@@ -597,6 +614,7 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc* desc, const axpic_param
   c.photon_start = reinterpret_cast<int32_t*>(base + kNaStart);
   c.diag = reinterpret_cast<double*>(base + kNaUnused);
   c.tally = reinterpret_cast<double*>(base + kNaUnused);
+  c.bits = reinterpret_cast<uint32_t*>(base + kNaBits);
   c.res = carry;
   c.warps = kNoAllocWarps;
   c.grid = (d.ncells + kNoAllocWarps - 1) / kNoAllocWarps;
@@ -607,6 +625,7 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc* desc, const axpic_param
   if ((e = cudaMemsetAsync(c.err, 0, sizeof(int), st)) ||
       (e = cudaMemsetAsync(c.counters, 0, sizeof(unsigned long long) * kNumCounters * (size_t)c.grid, st)) ||
       (e = cudaMemsetAsync(c.xbuf, 0, sizeof(double) * 4 * (size_t)d.ncells, st)) ||
+      (e = cudaMemsetAsync(c.bits, 0, bit_bytes > 0 ? bit_bytes : 4, st)) ||
       (e = set_step_smem_limits(per_warp * kNoAllocWarps)) ||
       (e = launch_records(d.ncells, d.nspecies, c.cc, d.T_keV, d.n_ion, c.rec, c.err, st)) ||
       (e = launch_moments(d.ncells, to_ptrs(d.electrons), c.mom, st)) ||

@@ -319,6 +319,8 @@ struct StepArgs {
   int nbins;
   float inv_dE_bin;
   unsigned long long* counters;  // [gridDim * kNumCounters]
+  uint32_t *bitsA, *bitsG, *bitsE;  // per-cell "needs a full decision" bit masks
+  int Wa, Wg, We;                   // words per cell of each mask
   int* err;
   CellConst cc;
 };
