@@ -67,19 +67,30 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def algorithmic_bytes(tot, ncells_steps, T_mode):
-    """Minimum DRAM bytes of the fused step (read once, write what changes):
-    electrons: w (4 B) each, plus p read and written (24 B) in remapped cells;
-    photons and axions present at the start: w, p (16 B) each;
-    each product: 28 B written + 12 B of parent position read;
-    per cell: rate record (64 B), three counts (12 B read + 12 B written),
-    and in evolved-T mode T (8 B read + 8 B written) and the record's
-    temperature half (32 B written)."""
+def kernel_bytes(tot, T_mode):
+    """Algorithmic DRAM bytes of each kernel of the step, summed over the timed
+    steps (the minimum each kernel has to move):
+      axion decisions: w, p of every axion present (16 B) + count and three
+        record words per cell (16 B);
+      emit decisions: w, p of every photon present (16 B), w of electrons in
+        cells without a common weight (4 B; 0 here) + counts, snapshot, record
+        words and common weight per cell (32 B);
+      events: the decision masks (1 bit per particle), counts, snapshot and
+        flags per cell (40 B), each product written (28 B) with its parent's
+        w, p and position read (28 B), each removed slot refilled (56 B);
+      feedback: exchange, carried exchange, moments, count and T per cell
+        (104 B), plus 80 B of record traffic in evolved-T mode, plus 28 B per
+        electron of remapped cells (w, p read, p written)."""
+    cells = tot["cell_steps"]
     products = tot["events_p"] + tot["events_c"] + tot["events_b"] + tot["events_pinv"]
-    b = 4.0 * tot["part_e"] + 16.0 * (tot["part_g"] + tot["part_a"]) + 24.0 * tot["remap_e"]
-    b += 40.0 * products
-    b += ncells_steps * (64.0 + 24.0 + (48.0 if T_mode == 2 else 0.0))
-    return b
+    removed = tot["events_p"] + tot["absorbed_c"] + tot["absorbed_b"] + tot["events_pinv"]
+    parts = tot["part_e"] + tot["part_g"] + tot["part_a"]
+    return {
+        "axion_decide_kernel": 16.0 * tot["part_a"] + 16.0 * cells,
+        "emit_decide_kernel": 16.0 * tot["part_g"] + 32.0 * cells,
+        "event_kernel": parts / 8.0 + 40.0 * cells + 56.0 * products + 56.0 * removed,
+        "feedback_kernel": (104.0 + (80.0 if T_mode == 2 else 0.0)) * cells + 28.0 * tot["remap_e"],
+    }
 
 
 class ClockSampler:
@@ -240,6 +251,7 @@ def main():
     for s in range(args.warmup):
         pl.step(s, w.mask)
     pl.tally()  # clears counters: the timed region starts from zero
+    pl.profile_begin(args.steps)  # events around each kernel of the timed steps
     clocks = ClockSampler(local)
     clocks.start()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
@@ -262,10 +274,10 @@ def main():
     clk = clocks.stop()
     elapsed_ms = t_start.elapsed_time(t_end)
     launch_ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)]
+    kms, nprof = pl.profile_end()
     H, tot = pl.tally()
     particles = tot["part_e"] + tot["part_g"] + tot["part_a"]
-    cell_steps = tot["cell_steps"]
-    alg = algorithmic_bytes(tot, cell_steps, w.params.get("T_mode", 0))
+    kbytes = kernel_bytes(tot, w.params.get("T_mode", 0))
     if world > 1:
         t = torch.tensor([elapsed_ms, particles], dtype=torch.float64, device=dev)
         mx = t.clone()
@@ -313,17 +325,22 @@ def main():
 
     if rank == 0:
         peak, peak_kind = measured_peaks()
-        avg_launch_s = statistics.mean(launch_ms) * 1e-3
-        bytes_per_launch = alg / args.steps
+        # the dominant kernel of the step: largest summed device time
+        dom = max(kms, key=kms.get)
+        per_kernel = {k: {"ms_per_launch": kms[k] / max(nprof, 1),
+                          "GBps": kbytes[k] / (kms[k] * 1e-3) / 1e9 if kms[k] > 0 else None,
+                          "share": kms[k] / sum(kms.values())} for k in kms}
+        avg_launch_s = kms[dom] * 1e-3 / max(nprof, 1)
+        bytes_per_launch = kbytes[dom] / max(nprof, 1)
         achieved = bytes_per_launch / avg_launch_s / 1e9
         traffic = None
-        prof = os.path.join(ROOT, "profiles", "step_kernel_c2_traffic.json")
+        prof = os.path.join(ROOT, "profiles", "step_kernels_c2_traffic.json")
         if os.path.exists(prof):
             try:
                 with open(prof) as f:
                     pj = json.load(f)
                 if pj.get("kernel_hash") == kernel_hash():
-                    traffic = pj.get("dram_bytes_per_launch")
+                    traffic = pj.get("dram_bytes_per_launch", {}).get(dom)
             except Exception:
                 traffic = None
         value = particles / (elapsed_ms * 1e-3)
@@ -334,13 +351,13 @@ def main():
                 "config": {"workload": w.name, "cells": w.ncells, "electrons_per_cell": w.n_el,
                            "photons_per_cell": w.n_ph, "axions_at_start": w.n_ax, "channels": "all, fwd+inv",
                            "T_mode": "evolved", "l2": "inputs larger than L2 (%.2f GB touched per step)"
-                           % (bytes_per_launch / 1e9),
+                           % (sum(kbytes.values()) / args.steps / 1e9),
                            "parallelism": "cells sharded per GPU" if world > 1 else "single GPU"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                             "kernel": "axpic::step_kernel<7>",
-                             "algorithmic_bytes_per_launch": bytes_per_launch},
-                "gpu_launches": args.steps, "clocks": clk,
+                             "kernel": "axpic::" + dom, "algorithmic_bytes_per_launch": bytes_per_launch,
+                             "kernels": per_kernel},
+                "gpu_launches": 4 * args.steps, "clocks": clk,
                 "counts": {"particle_steps": particles, "events_primakoff": tot["events_p"],
                            "events_compton": tot["events_c"], "events_brems": tot["events_b"],
                            "events_inverse": tot["events_pinv"], "remapped_cells": tot["remaps"]}}
@@ -364,7 +381,7 @@ def main():
 def kernel_hash():
     import hashlib
     h = hashlib.sha256()
-    for name in ("step.cu", "common.cuh"):
+    for name in ("step.cu", "common.cuh", "tables.h"):
         with open(os.path.join(ROOT, "paper_2604_24627_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -245,11 +245,13 @@ axpic_status axpic_get_residuals(axpic_ctx *ctx, int32_t first, int32_t count, d
  * The paper has no counterpart: this is an interface convenience.
  *
  * Its scratch (rate records, electron moments, sampling tables, counters,
- * exchange buffer, photon counts, decision bit masks, error flag; about
- * 6.9 MB) is a file-scope device array of the library, held by every GPU that
- * loads the library until the process exits. It limits a call to 16384 cells
- * and to ncells * (sum of the three capacities) / 8 <= 4 MiB of bit masks;
- * larger requests return AXPIC_E_INVALID without launching.
+ * exchange buffer, photon counts, decision bit masks and records, error
+ * flag; about 23 MB) is a file-scope device array of the library, held by
+ * every GPU that loads the library until the process exits. It limits a call
+ * to 16384 cells, to ncells * (sum of the three capacities) / 8 <= 4 MiB of
+ * bit masks and to ncells * (16 (axion + photon capacity) + 4 electron
+ * capacity) <= 16 MiB of decision records (about 1300 cells with capacities
+ * 512/384/384); larger requests return AXPIC_E_INVALID without launching.
  * The first call on a device looks up the array's device address with that
  * device current and uploads the sampling tables; make that first call
  * before any stream capture. Later calls reupload the tables only when
@@ -268,6 +270,17 @@ axpic_status axpic_get_residuals(axpic_ctx *ctx, int32_t first, int32_t count, d
  * device. */
 axpic_status axpic_step_noalloc(const axpic_plasma_desc *desc, const axpic_params *params, int64_t step,
                                 int32_t channel_mask, double *carry, void *stream);
+
+/* Measurement of the step's kernels. axpic_profile_begin (synchronises)
+ * prepares CUDA events for the next max_steps calls of axpic_step, which then
+ * record an event on the context's stream before and after each of their
+ * four kernels (recording adds no kernel work). axpic_profile_end
+ * (synchronises) writes to ms_out (host, 4 doubles) the summed device time of
+ * each kernel over the recorded steps, in the order axion decisions, emit
+ * decisions, events, feedback, sets *steps_out (may be NULL) to the number of
+ * steps recorded, and releases the events. Not part of the paper's method. */
+axpic_status axpic_profile_begin(axpic_ctx *ctx, int32_t max_steps);
+axpic_status axpic_profile_end(axpic_ctx *ctx, double *ms_out, int32_t *steps_out);
 
 /* Wait for the stream and return the first latched device error, if any. */
 axpic_status axpic_sync(axpic_ctx *ctx);

@@ -85,6 +85,9 @@ EXPORTS = {
                                            ctypes.POINTER(ctypes.c_double)]),
     "axpic_step_noalloc": (ctypes.c_int, [ctypes.POINTER(PlasmaDesc), ctypes.POINTER(Params), ctypes.c_int64,
                                           ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "axpic_profile_begin": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "axpic_profile_end": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int32)]),
     "axpic_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "axpic_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "axpic_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -180,6 +183,21 @@ def axpic_step_noalloc(desc, params, step, mask, carry_ptr, stream=0):
                                   ctypes.c_void_p(carry_ptr), ctypes.c_void_p(stream))
     if st != AXPIC_OK:
         raise AxpicError(st, "axpic_step_noalloc failed (see stderr)")
+
+
+STEP_KERNELS = ("axion_decide_kernel", "emit_decide_kernel", "event_kernel", "feedback_kernel")
+
+
+def axpic_profile_begin(ctx, max_steps):
+    _check(ctx, lib().axpic_profile_begin(ctx, max_steps))
+
+
+def axpic_profile_end(ctx):
+    """(dict kernel -> summed ms, number of steps recorded)."""
+    ms = (ctypes.c_double * 4)()
+    n = ctypes.c_int32()
+    _check(ctx, lib().axpic_profile_end(ctx, ms, ctypes.byref(n)))
+    return dict(zip(STEP_KERNELS, list(ms))), n.value
 
 
 def axpic_sync(ctx):

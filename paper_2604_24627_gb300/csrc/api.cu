@@ -47,11 +47,16 @@ struct axpic_ctx {
   int* err = nullptr;
   double* scratch = nullptr;  // totals (8) + counters (kNumCounters) + info chunk
   uint32_t* bits = nullptr;   // decision bit masks: axions, photons, electrons
+  uint4* recA = nullptr;      // full decisions of flagged axion / photon slots
+  uint4* recG = nullptr;
+  uint32_t* recE = nullptr;   // event counts of flagged electrons
   CellConst cc;
   int warps = kDefaultWarps;
   int grid = 0;
   int64_t last_absorb_step = -1;
   std::string last_error;
+  std::vector<cudaEvent_t> prof_events;  // 5 per recorded step, created by axpic_profile_begin
+  int prof_max = 0, prof_used = 0;
 };
 
 static const char* kNoCtxMsg = "no context";
@@ -184,13 +189,25 @@ static StepArgs make_args(axpic_ctx* ctx, int64_t step, int mask) {
   A.bitsA = ctx->bits;
   A.bitsG = ctx->bits + (size_t)A.Wa * ctx->desc.ncells;
   A.bitsE = A.bitsG + (size_t)A.Wg * ctx->desc.ncells;
+  A.recA = ctx->recA;
+  A.recG = ctx->recG;
+  A.recE = ctx->recE;
+  A.dec_cells = AXPIC_DEC_CELLS;
   A.cc = ctx->cc;
   return A;
 }
 
+static void free_events(axpic_ctx* ctx) {
+  for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
+  ctx->prof_events.clear();
+  ctx->prof_max = ctx->prof_used = 0;
+}
+
 static void free_ctx(axpic_ctx* ctx) {
+  free_events(ctx);
   void* bufs[] = {ctx->rec,    ctx->mom,   ctx->xbuf,     ctx->res, ctx->diag,    ctx->photon_start,
-                  ctx->tables, ctx->tally, ctx->counters, ctx->err, ctx->scratch, ctx->bits};
+                  ctx->tables, ctx->tally, ctx->counters, ctx->err, ctx->scratch, ctx->bits,
+                  ctx->recA,   ctx->recG,  ctx->recE};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete ctx;
@@ -303,6 +320,9 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
   const size_t bit_words = (size_t)n * ((d.axions.capacity + 31) / 32 + (d.photons.capacity + 31) / 32 +
                                         (d.electrons.capacity + 31) / 32);
   ALLOC(ctx->bits, sizeof(uint32_t) * bit_words);
+  ALLOC(ctx->recA, sizeof(uint4) * (size_t)n * d.axions.capacity);
+  ALLOC(ctx->recG, sizeof(uint4) * (size_t)n * d.photons.capacity);
+  ALLOC(ctx->recE, sizeof(uint32_t) * (size_t)n * d.electrons.capacity);
 #undef ALLOC
   std::vector<float> tab((size_t)kNumTables * kTableN);
   build_tables(p.brems_gamma_shape, tab.data());
@@ -371,7 +391,9 @@ static axpic_status run_phases(axpic_ctx* ctx, int phases, int64_t step, int32_t
   if (mask & ~AXPIC_CH_ALL) return fail(ctx, AXPIC_E_INVALID, std::string(name) + ": unknown channel bits");
   StepArgs A = make_args(ctx, step, mask);
   if (phases == PH_EMIT) A.use_snapshot = ctx->last_absorb_step == step;
-  CK(launch_step(phases, A, ctx->warps, ctx->stream), name);
+  cudaEvent_t* ev = nullptr;
+  if (phases == PH_ALL && ctx->prof_used < ctx->prof_max) ev = ctx->prof_events.data() + 5 * (ctx->prof_used++);
+  CK(launch_step(phases, A, ctx->warps, ctx->stream, ev), name);
   if (phases == PH_ABSORB) ctx->last_absorb_step = step;
   return AXPIC_OK;
 }
@@ -507,6 +529,32 @@ axpic_status axpic_get_residuals(axpic_ctx* ctx, int32_t first, int32_t count, d
   return AXPIC_OK;
 }
 
+axpic_status axpic_profile_begin(axpic_ctx* ctx, int32_t max_steps) {
+  if (!ctx || max_steps < 0 || max_steps > (1 << 20)) return AXPIC_E_INVALID;
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  free_events(ctx);
+  ctx->prof_events.resize(5 * (size_t)max_steps);
+  for (auto& e : ctx->prof_events) CK(cudaEventCreate(&e), "event create");
+  ctx->prof_max = max_steps;
+  return AXPIC_OK;
+}
+
+axpic_status axpic_profile_end(axpic_ctx* ctx, double* ms_out, int32_t* steps_out) {
+  if (!ctx || !ms_out) return AXPIC_E_INVALID;
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  for (int k = 0; k < kStepKernels; ++k) ms_out[k] = 0.0;
+  for (int s = 0; s < ctx->prof_used; ++s) {
+    for (int k = 0; k < kStepKernels; ++k) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ctx->prof_events[5 * s + k], ctx->prof_events[5 * s + k + 1]), "elapsed");
+      ms_out[k] += ms;
+    }
+  }
+  if (steps_out) *steps_out = ctx->prof_used;
+  free_events(ctx);
+  return AXPIC_OK;
+}
+
 axpic_status axpic_sync(axpic_ctx* ctx) {
   if (!ctx) return AXPIC_E_INVALID;
   return read_err(ctx);
@@ -538,7 +586,9 @@ constexpr size_t kNaXbuf = kNaErr + 256;
 constexpr size_t kNaStart = kNaXbuf + sizeof(double) * 4 * kNoAllocMaxCells;
 constexpr size_t kNaBitsBytes = 4u << 20;  // decision bit masks: cells * (acap + gcap + ecap) / 8 bytes
 constexpr size_t kNaBits = kNaStart + sizeof(int32_t) * kNoAllocMaxCells;
-constexpr size_t kNaUnused = kNaBits + kNaBitsBytes;  // diagnostic/tally slots never touched
+constexpr size_t kNaRecBytes = 16u << 20;  // decision records: cells * (16 (acap + gcap) + 4 ecap) bytes
+constexpr size_t kNaRecs = kNaBits + kNaBitsBytes;
+constexpr size_t kNaUnused = kNaRecs + kNaRecBytes;  // diagnostic/tally slots never touched
 constexpr size_t kNoAllocBytes = kNaUnused + 256;
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_na_mu;
@@ -573,6 +623,9 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc* desc, const axpic_param
                            ((d.axions.capacity + 31) / 32 + (d.photons.capacity + 31) / 32 +
                             (d.electrons.capacity + 31) / 32);
   if (bit_bytes > kNaBitsBytes) return bad("ncells * (capacities) / 8 above the 4 MiB mask scratch");
+  const size_t rec_bytes = (size_t)d.ncells * (16 * ((size_t)d.axions.capacity + d.photons.capacity) +
+                                               4 * (size_t)d.electrons.capacity);
+  if (rec_bytes > kNaRecBytes) return bad("ncells * (16 (acap + gcap) + 4 ecap) above the 16 MiB record scratch");
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return AXPIC_E_CUDA;
@@ -615,6 +668,9 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc* desc, const axpic_param
   c.diag = reinterpret_cast<double*>(base + kNaUnused);
   c.tally = reinterpret_cast<double*>(base + kNaUnused);
   c.bits = reinterpret_cast<uint32_t*>(base + kNaBits);
+  c.recA = reinterpret_cast<uint4*>(base + kNaRecs);
+  c.recG = c.recA + (size_t)d.ncells * d.axions.capacity;
+  c.recE = reinterpret_cast<uint32_t*>(c.recG + (size_t)d.ncells * d.photons.capacity);
   c.res = carry;
   c.warps = kNoAllocWarps;
   c.grid = (d.ncells + kNoAllocWarps - 1) / kNoAllocWarps;

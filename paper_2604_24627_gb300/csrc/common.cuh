@@ -63,6 +63,13 @@ enum {
 // the common electron weight when every electron of the cell has the same
 // weight (0 otherwise). Electrons change only through the remap.
 constexpr int kMomLen = 8;
+
+// Cells per decision CTA: at most kDecMaxCells; the default is a compile-time
+// choice that launch-shape sweeps override.
+constexpr int kDecMaxCells = 16;
+#ifndef AXPIC_DEC_CELLS
+#define AXPIC_DEC_CELLS 8
+#endif
 enum { M_W = 0, M_PX, M_PY, M_PZ, M_U2, M_VAR, M_WU };
 
 // Per-CTA counters (u64), reduced by axpic_tally_spectrum.
@@ -321,7 +328,10 @@ struct StepArgs {
   unsigned long long* counters;  // [gridDim * kNumCounters]
   uint32_t *bitsA, *bitsG, *bitsE;  // per-cell "needs a full decision" bit masks
   int Wa, Wg, We;                   // words per cell of each mask
+  uint4 *recA, *recG;               // full decisions of flagged slots (slot-indexed)
+  uint32_t* recE;
   int* err;
+  int dec_cells;  // cells per decision CTA, 1..kDecMaxCells
   CellConst cc;
 };
 

@@ -312,6 +312,16 @@ __device__ __noinline__ RemapOut remap_electrons(const StepArgs& A, long ebase, 
 
 __device__ __forceinline__ bool nz64(double v) { return (__double_as_longlong(v) << 1) != 0; }
 
+// ---------------------------------------------------------------- decision records
+// A flagged slot's full decision, written by the decision kernels and read by
+// the event kernel (slot-indexed arrays, touched only for flagged slots):
+// x = K | flags << 8, y = product weight, z = new weight (axions) or the
+// remaining weight (photons).
+enum : uint32_t {
+  DF_KEEP = 1u << 8, DF_ABSORBED = 1u << 9, DF_ABS_C = 1u << 10, DF_CAPPED = 1u << 11, DF_OVER = 1u << 12,
+  DF_CAPPED_B = 1u << 13
+};
+
 // ---------------------------------------------------------------- decision kernels
 // Bit masks: word (cell * W + s / 32), bit s % 32 flags slot s. Words are
 // set by atomicOr (rare) and cleared by the event kernel after reading.
@@ -320,117 +330,294 @@ __device__ __forceinline__ void flag_quad(uint32_t* bits, int W, int cell, int q
   if (nib) atomicOr(bits + (size_t)cell * W + ((4 * q) >> 5), nib << ((4 * q) & 31));
 }
 
+// Decision CTAs take A.dec_cells consecutive cells and give their quads to
+// threads in one flat range (thread per quad, cell-major), so uneven counts
+// still fill the warps. Slots that the guards cannot clear go to a CTA-wide
+// list in shared memory, and their full decisions are taken with the
+// list spread over all threads: the out-of-line chain then runs with full
+// warps instead of a few lanes of every warp. List order does not matter:
+// records are indexed by slot.
+constexpr int kDecThreads = 256;
+static_assert(AXPIC_DEC_CELLS >= 1 && AXPIC_DEC_CELLS <= kDecMaxCells, "cells per decision CTA");
+constexpr int kDecListCap = 5 * kDecThreads;  // one pass of flags (4 per thread) + a partial batch
+
+struct DecideSmem {
+  int qoff[kDecMaxCells + 1];  // prefix of the cells' quad counts
+  int n[kDecMaxCells];         // slots to decide per cell
+  float c0[kDecMaxCells], c1[kDecMaxCells], c2[kDecMaxCells], c3[kDecMaxCells], c4[kDecMaxCells];  // per cell
+  int count;
+  uint32_t item[kDecListCap];  // (cell in CTA << 16) | slot
+  uint2 u[kDecListCap];        // the slot's decision words
+};
+
+// Quad counts of this CTA's cells, from the per-cell slot counts n (set by
+// lanes < ncell of warp 0 before the call).
+__device__ __forceinline__ void dec_prefix(DecideSmem& S, int ncell, int n) {
+  if (threadIdx.x < 32) {
+    const int nq = threadIdx.x < ncell ? (n + 3) >> 2 : 0;
+    int tot;
+    const int off = warp_excl_scan(nq, &tot);
+    if (threadIdx.x < ncell) {
+      S.qoff[threadIdx.x] = off;
+      S.n[threadIdx.x] = n;
+    }
+    if (threadIdx.x == 0) {
+      S.qoff[ncell] = tot;
+      S.count = 0;
+    }
+  }
+  __syncthreads();
+}
+
+// Cell in CTA of flat quad g (g < qoff[ncell]).
+__device__ __forceinline__ int dec_cell_of(const DecideSmem& S, int ncell, int g) {
+  int lc = 0;
+  while (lc + 1 < ncell && S.qoff[lc + 1] <= g) ++lc;
+  return lc;
+}
+
+// Appends the flagged slots of this thread's quad (bits of nib; words w0/w1
+// rotate with the slot) to the CTA list with one shared atomic per warp.
+__device__ __forceinline__ void dec_append(DecideSmem& S, int lc, int slot0, uint32_t nib, uint4 w0, uint4 w1) {
+  const int cnt = __popc(nib);
+  int tot;
+  const int off = warp_excl_scan(cnt, &tot);
+  int base = 0;
+  if (lane_id() == 0 && tot) base = atomicAdd(&S.count, tot);
+  base = __shfl_sync(kFull, base, 0) + off;
+#pragma unroll
+  for (int j = 0; j < 4; ++j, rot(w0), rot(w1)) {
+    if ((nib >> j) & 1u) {
+      S.item[base] = ((uint32_t)lc << 16) | (uint32_t)(slot0 + j);
+      S.u[base] = make_uint2(w0.x, w1.x);
+      ++base;
+    }
+  }
+}
+
+// Runs f(item, words) for every listed slot: full batches of kDecThreads
+// after each pass over the quads (drain == true), the rest at the end.
+template <class F>
+__device__ __forceinline__ void dec_drain(DecideSmem& S, bool final_pass, F f) {
+  __syncthreads();
+  int cnt = S.count;
+  if (final_pass) {
+    if ((int)threadIdx.x < cnt) f(S.item[threadIdx.x], S.u[threadIdx.x]);
+    return;
+  }
+  while (cnt >= kDecThreads) {
+    cnt -= kDecThreads;
+    f(S.item[cnt + threadIdx.x], S.u[cnt + threadIdx.x]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) S.count = cnt;
+  __syncthreads();
+}
+
 // Axions present at the start of the step: a->gamma and absorption.
-__global__ void __launch_bounds__(256) axion_decide_kernel(StepArgs A) {
-  const int Q = A.a.cap >> 2;
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int cell = (int)(t / Q);
-  const int q = (int)(t - (long)cell * Q);
-  if (cell >= A.ncells) return;
-  const int n = min(max(A.a.count[cell], 0), A.a.cap);
-  if (4 * q >= n) return;
-  const int nj = min(4, n - 4 * q);
+__global__ void __launch_bounds__(kDecThreads) axion_decide_kernel(StepArgs A) {
+  __shared__ DecideSmem S;
+  const int cfirst = blockIdx.x * A.dec_cells;
+  const int ncell = min(A.dec_cells, A.ncells - cfirst);
   const int mask = A.mask;
   const bool prim = mask & AXPIC_CH_PRIMAKOFF;
   const bool bath = mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS);
-  uint32_t nib;
-  if (A.absorb_mode == 1 && bath) {
-    nib = (1u << nj) - 1u;  // weight reduction changes every axion
-  } else {
-    const float* rec = A.rec + (size_t)cell * kRecLen;
-    const float c_s = kMeC2f * kMeC2f * __ldg(rec + R_FOURK2);
-    const float apinv = __ldg(rec + R_APINV);
-    const float invT = __ldg(rec + R_INVT);
-    const uint32_t gcell = A.cell_base + (uint32_t)cell;
-    const long b = (long)cell * A.a.cap + 4 * q;
-    float4 w4 = ld4(A.a.w + b), x4 = ld4(A.a.px + b), y4 = ld4(A.a.py + b), z4 = ld4(A.a.pz + b);
-    uint4 rP = make_uint4(0, 0, 0, 0), rA = make_uint4(0, 0, 0, 0);
-    if (prim) rP = philox4x32_10(make_uint4(A.step, gcell, (uint32_t)q, S_PRIM_INV << 24), A.key0, A.key1);
-    if (bath) rA = philox4x32_10(make_uint4(A.step, gcell, (uint32_t)q, S_ABSORB << 24), A.key0, A.key1);
-    nib = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j, rot(w4), rot(x4), rot(y4), rot(z4), rot(rP), rot(rA)) {
-      if (j >= nj) break;
-      const float p2 = x4.x * x4.x + y4.x * y4.x + z4.x * z4.x;
-      bool fast = true;
-      if (prim) fast = no_conversion(w4.x, p2, c_s, apinv, A.inv_w_gref, u23(rP.x), A.lam_cap);
-      if (fast && bath) fast = no_absorption(rec, A, mask, sqrtf(p2) * kMeC2f * invT, u23(rA.x));
-      if (!fast) nib |= 1u << j;
-    }
+  const bool all = A.absorb_mode == 1 && bath;  // weight reduction changes every axion
+  if (threadIdx.x < ncell) {
+    const int c = cfirst + threadIdx.x;
+    const float* rec = A.rec + (size_t)c * kRecLen;
+    S.c0[threadIdx.x] = kMeC2f * kMeC2f * __ldg(rec + R_FOURK2);
+    S.c1[threadIdx.x] = __ldg(rec + R_APINV);
+    S.c2[threadIdx.x] = __ldg(rec + R_INVT);
   }
-  flag_quad(A.bitsA, A.Wa, cell, q, nib);
+  dec_prefix(S, ncell, threadIdx.x < ncell ? min(max(A.a.count[cfirst + threadIdx.x], 0), A.a.cap) : 0);
+  const int nq = S.qoff[ncell];
+  auto full = [&](uint32_t it, uint2 uu) {
+    const int cell = cfirst + (int)(it >> 16);
+    const long idx = (long)cell * A.a.cap + (it & 0xFFFFu);
+    const AxionDecision d =
+        axion_decide_slow(A, cell, mask, A.a.w[idx], A.a.px[idx], A.a.py[idx], A.a.pz[idx], uu.x, uu.y);
+    uint32_t f = (uint32_t)d.K;
+    if (d.keep) f |= DF_KEEP;
+    if (d.absorbed) f |= DF_ABSORBED;
+    if (d.abs_c) f |= DF_ABS_C;
+    if (d.capped) f |= DF_CAPPED;
+    if (d.over) f |= DF_OVER;
+    A.recA[idx] = make_uint4(f, __float_as_uint(d.wprod), __float_as_uint(d.wnew), 0u);
+  };
+  for (int g0 = 0; g0 < nq; g0 += kDecThreads) {
+    const int g = g0 + threadIdx.x;
+    uint32_t nib = 0;
+    int lc = 0, q = 0;
+    uint4 rP = make_uint4(0, 0, 0, 0), rA = make_uint4(0, 0, 0, 0);
+    if (g < nq) {
+      lc = dec_cell_of(S, ncell, g);
+      q = g - S.qoff[lc];
+      const int cell = cfirst + lc;
+      const int nj = min(4, S.n[lc] - 4 * q);
+      const float* rec = A.rec + (size_t)cell * kRecLen;
+      const float c_s = S.c0[lc], apinv = S.c1[lc], invT = S.c2[lc];
+      const uint32_t gcell = A.cell_base + (uint32_t)cell;
+      const long b = (long)cell * A.a.cap + 4 * q;
+      float4 w4 = ld4(A.a.w + b), x4 = ld4(A.a.px + b), y4 = ld4(A.a.py + b), z4 = ld4(A.a.pz + b);
+      if (prim) rP = philox4x32_10(make_uint4(A.step, gcell, (uint32_t)q, S_PRIM_INV << 24), A.key0, A.key1);
+      if (bath) rA = philox4x32_10(make_uint4(A.step, gcell, (uint32_t)q, S_ABSORB << 24), A.key0, A.key1);
+      uint4 tP = rP, tA = rA;
+#pragma unroll
+      for (int j = 0; j < 4; ++j, rot(w4), rot(x4), rot(y4), rot(z4), rot(tP), rot(tA)) {
+        if (j >= nj) break;
+        const float p2 = x4.x * x4.x + y4.x * y4.x + z4.x * z4.x;
+        bool fast = !all;
+        if (fast && prim) fast = no_conversion(w4.x, p2, c_s, apinv, A.inv_w_gref, u23(tP.x), A.lam_cap);
+        if (fast && bath) fast = no_absorption(rec, A, mask, sqrtf(p2) * kMeC2f * invT, u23(tA.x));
+        if (!fast) nib |= 1u << j;
+      }
+      flag_quad(A.bitsA, A.Wa, cell, q, nib);
+    }
+    dec_append(S, lc, 4 * q, nib, rP, rA);
+    dec_drain(S, false, full);
+  }
+  dec_drain(S, true, full);
 }
 
-// Photons present at the start of the step (gamma->a) and electrons
-// (thermal-bath emission): photon quads first, then electron quads.
-__global__ void __launch_bounds__(256) emit_decide_kernel(StepArgs A) {
-  const int Qg = A.g.cap >> 2, Qe = A.e.cap >> 2;
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long ng_quads = (long)A.ncells * Qg;
-  const int mask = A.mask;
-  if (t < ng_quads) {
-    if (!(mask & AXPIC_CH_PRIMAKOFF)) return;
-    const int cell = (int)(t / Qg);
-    const int q = (int)(t - (long)cell * Qg);
-    const int cnt = min(max(A.g.count[cell], 0), A.g.cap);
-    const int n = A.use_snapshot ? min(A.photon_start[cell], cnt) : cnt;
-    if (4 * q >= n) return;
-    const int nj = min(4, n - 4 * q);
-    const float* rec = A.rec + (size_t)cell * kRecLen;
-    const float c_s = kMeC2f * kMeC2f * __ldg(rec + R_FOURK2);
-    const float ap = __ldg(rec + R_AP);
-    const long b = (long)cell * A.g.cap + 4 * q;
-    float4 w4 = ld4(A.g.w + b), x4 = ld4(A.g.px + b), y4 = ld4(A.g.py + b), z4 = ld4(A.g.pz + b);
-    uint4 r = philox4x32_10(make_uint4(A.step, A.cell_base + (uint32_t)cell, (uint32_t)q, S_PRIM_FWD << 24), A.key0,
-                            A.key1);
+// Photons present at the start of the step (gamma->a): y == 0 of the grid.
+__device__ __forceinline__ void photon_decide_cta(const StepArgs& A, DecideSmem& S, int cfirst, int ncell) {
+  if (threadIdx.x < ncell) {
+    const int c = cfirst + threadIdx.x;
+    const float* rec = A.rec + (size_t)c * kRecLen;
+    S.c0[threadIdx.x] = kMeC2f * kMeC2f * __ldg(rec + R_FOURK2);
+    S.c1[threadIdx.x] = __ldg(rec + R_AP);
+  }
+  int n = 0;
+  if (threadIdx.x < ncell) {
+    const int c = cfirst + threadIdx.x;
+    const int cnt = min(max(A.g.count[c], 0), A.g.cap);
+    n = A.use_snapshot ? min(A.photon_start[c], cnt) : cnt;
+  }
+  dec_prefix(S, ncell, n);
+  const int nq = S.qoff[ncell];
+  auto full = [&](uint32_t it, uint2 uu) {
+    const int cell = cfirst + (int)(it >> 16);
+    const long idx = (long)cell * A.g.cap + (it & 0xFFFFu);
+    const PhotonDecision d = photon_decide_slow(A, cell, A.g.w[idx], A.g.px[idx], A.g.py[idx], A.g.pz[idx], uu.x);
+    uint32_t f = (uint32_t)d.K;
+    if (d.wrem > 0.f) f |= DF_KEEP;
+    if (d.capped) f |= DF_CAPPED;
+    if (d.over) f |= DF_OVER;
+    A.recG[idx] = make_uint4(f, __float_as_uint(d.wprod), __float_as_uint(d.wrem), 0u);
+  };
+  for (int g0 = 0; g0 < nq; g0 += kDecThreads) {
+    const int g = g0 + threadIdx.x;
     uint32_t nib = 0;
+    int lc = 0, q = 0;
+    uint4 r = make_uint4(0, 0, 0, 0);
+    if (g < nq) {
+      lc = dec_cell_of(S, ncell, g);
+      q = g - S.qoff[lc];
+      const int cell = cfirst + lc;
+      const int nj = min(4, S.n[lc] - 4 * q);
+      const float c_s = S.c0[lc], ap = S.c1[lc];
+      const long b = (long)cell * A.g.cap + 4 * q;
+      float4 w4 = ld4(A.g.w + b), x4 = ld4(A.g.px + b), y4 = ld4(A.g.py + b), z4 = ld4(A.g.pz + b);
+      r = philox4x32_10(make_uint4(A.step, A.cell_base + (uint32_t)cell, (uint32_t)q, S_PRIM_FWD << 24), A.key0,
+                        A.key1);
+      uint4 t = r;
 #pragma unroll
-    for (int j = 0; j < 4; ++j, rot(w4), rot(x4), rot(y4), rot(z4), rot(r)) {
-      if (j >= nj) break;
-      const float p2 = x4.x * x4.x + y4.x * y4.x + z4.x * z4.x;
-      if (!no_conversion(w4.x, p2, c_s, ap, A.inv_w_a, u23(r.x), A.lam_cap)) nib |= 1u << j;
+      for (int j = 0; j < 4; ++j, rot(w4), rot(x4), rot(y4), rot(z4), rot(t)) {
+        if (j >= nj) break;
+        const float p2 = x4.x * x4.x + y4.x * y4.x + z4.x * z4.x;
+        if (!no_conversion(w4.x, p2, c_s, ap, A.inv_w_a, u23(t.x), A.lam_cap)) nib |= 1u << j;
+      }
+      flag_quad(A.bitsG, A.Wg, cell, q, nib);
     }
-    flag_quad(A.bitsG, A.Wg, cell, q, nib);
-    return;
+    dec_append(S, lc, 4 * q, nib, r, r);
+    dec_drain(S, false, full);
   }
-  const long te = t - ng_quads;
-  const int cell = (int)(te / Qe);
-  const int q = (int)(te - (long)cell * Qe);
-  if (cell >= A.ncells) return;
+  dec_drain(S, true, full);
+}
+
+// Electrons (thermal-bath emission): y == 1 of the grid. Their full
+// decision is a short Poisson inversion, taken in place.
+__device__ __forceinline__ void electron_decide_cta(const StepArgs& A, DecideSmem& S, int cfirst, int ncell) {
+  const int mask = A.mask;
   const bool eC = mask & AXPIC_CH_COMPTON, eB = mask & AXPIC_CH_BREMS;
-  if (!(eC || eB)) return;
-  const int n = min(max(A.e.count[cell], 0), A.e.cap);
-  if (4 * q >= n) return;
-  const int nj = min(4, n - 4 * q);
-  const float* rec = A.rec + (size_t)cell * kRecLen;
-  const float rcc = __ldg(rec + R_CC), rcb = __ldg(rec + R_CB);
-  uint4 r = philox4x32_10(make_uint4(A.step, A.cell_base + (uint32_t)cell, (uint32_t)q, S_EMIT_E << 24), A.key0,
-                          A.key1);
-  const float wu = __ldg(A.mom + (size_t)cell * kMomLen + M_WU);
-  uint32_t nib = 0;
-  if (wu > 0.f) {
-    // common weight: K > 0 exactly when u > exp(-lambda), lambda shared
-    float fac;
-    bool cc = false, cb = false;
-    const float lc = eC ? cap_lambda(wu * rcc, A.lam_cap, &fac, &cc) : 0.f;
-    const float lb = eB ? cap_lambda(wu * rcb, A.lam_cap, &fac, &cb) : 0.f;
-    const float F0 = expf(-(lc + lb));
-#pragma unroll
-    for (int j = 0; j < 4; ++j, rot(r)) {
-      if (j >= nj) break;
-      if (u23(r.x) > F0) nib |= 1u << j;
+  if (threadIdx.x < ncell) {
+    const int c = cfirst + threadIdx.x;
+    const float* rec = A.rec + (size_t)c * kRecLen;
+    const float rcc = __ldg(rec + R_CC), rcb = __ldg(rec + R_CB);
+    const float wu = __ldg(A.mom + (size_t)c * kMomLen + M_WU);
+    S.c0[threadIdx.x] = rcc;
+    S.c1[threadIdx.x] = rcb;
+    S.c2[threadIdx.x] = wu;
+    float lsum = 0.f, F0 = 0.f;
+    if (wu > 0.f) {
+      // common weight: K > 0 exactly when u > exp(-lambda), lambda shared
+      float fac;
+      bool cc = false, cb = false;
+      const float lc = eC ? cap_lambda(wu * rcc, A.lam_cap, &fac, &cc) : 0.f;
+      const float lb = eB ? cap_lambda(wu * rcb, A.lam_cap, &fac, &cb) : 0.f;
+      lsum = lc + lb;
+      F0 = expf(-lsum);
     }
-  } else {
-    float4 w4 = ld4(A.e.w + (long)cell * A.e.cap + 4 * q);
-    const float rsum = ((eC ? rcc : 0.f) + (eB ? rcb : 0.f)) * 1.0001f;
-#pragma unroll
-    for (int j = 0; j < 4; ++j, rot(w4), rot(r)) {
-      if (j >= nj) break;
-      const float lb = w4.x * rsum;
-      if (!(lb < A.lam_cap && u23(r.x) <= 1.0f - lb - 1e-6f)) nib |= 1u << j;
-    }
+    S.c3[threadIdx.x] = F0;
+    S.c4[threadIdx.x] = lsum;
   }
-  flag_quad(A.bitsE, A.We, cell, q, nib);
+  dec_prefix(S, ncell, threadIdx.x < ncell ? min(max(A.e.count[cfirst + threadIdx.x], 0), A.e.cap) : 0);
+  const int nq = S.qoff[ncell];
+  for (int g = threadIdx.x; g < nq; g += kDecThreads) {
+    const int lc = dec_cell_of(S, ncell, g);
+    const int q = g - S.qoff[lc];
+    const int cell = cfirst + lc;
+    const int nj = min(4, S.n[lc] - 4 * q);
+    uint4 r = philox4x32_10(make_uint4(A.step, A.cell_base + (uint32_t)cell, (uint32_t)q, S_EMIT_E << 24), A.key0,
+                            A.key1);
+    const long b = (long)cell * A.e.cap + 4 * q;
+    uint32_t nib = 0;
+    if (S.c2[lc] > 0.f) {
+      const float F0 = S.c3[lc], lsum = S.c4[lc];
+#pragma unroll
+      for (int j = 0; j < 4; ++j, rot(r)) {
+        if (j >= nj) break;
+        const float u = u23(r.x);
+        if (u > F0) {
+          A.recE[b + j] = (uint32_t)poisson_inv(u, lsum);
+          nib |= 1u << j;
+        }
+      }
+    } else {
+      const float rcc = S.c0[lc], rcb = S.c1[lc];
+      float4 w4 = ld4(A.e.w + b);
+      const float rsum = ((eC ? rcc : 0.f) + (eB ? rcb : 0.f)) * 1.0001f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j, rot(w4), rot(r)) {
+        if (j >= nj) break;
+        const float lbnd = w4.x * rsum;
+        if (!(lbnd < A.lam_cap && u23(r.x) <= 1.0f - lbnd - 1e-6f)) {
+          float fac;
+          bool cc = false, cb = false;
+          const float lc2 = eC ? cap_lambda(w4.x * rcc, A.lam_cap, &fac, &cc) : 0.f;
+          const float lb2 = eB ? cap_lambda(w4.x * rcb, A.lam_cap, &fac, &cb) : 0.f;
+          uint32_t f = (uint32_t)poisson_inv(u23(r.x), lc2 + lb2);
+          if (cc) f |= DF_CAPPED;
+          if (cb) f |= DF_CAPPED_B;
+          A.recE[b + j] = f;
+          nib |= 1u << j;
+        }
+      }
+    }
+    flag_quad(A.bitsE, A.We, cell, q, nib);
+  }
+}
+
+__global__ void __launch_bounds__(kDecThreads) emit_decide_kernel(StepArgs A) {
+  __shared__ DecideSmem S;
+  const int cfirst = blockIdx.x * A.dec_cells;
+  const int ncell = min(A.dec_cells, A.ncells - cfirst);
+  if (blockIdx.y == 0) {
+    if (A.mask & AXPIC_CH_PRIMAKOFF) photon_decide_cta(A, S, cfirst, ncell);
+  } else if (A.mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS)) {
+    electron_decide_cta(A, S, cfirst, ncell);
+  }
 }
 
 // ---------------------------------------------------------------- event kernel
@@ -463,26 +650,32 @@ __device__ inline EvScratch ev_carve(unsigned char* base, int acap, int gcap, in
   return s;
 }
 
-// Reads the cell's bit-mask words covering [0, n), clears them, and writes
-// the flagged slots in ascending order to `list`. Returns their number.
-__device__ __forceinline__ int gather_flags(uint32_t* bits, int W, int cell, int n, uint16_t* list) {
+// Turns one bit-mask word per lane (words [w0, w0 + 32) of a row covering
+// [0, n)) into the ascending list of flagged slots; returns the new length.
+__device__ __forceinline__ int list_flags(uint32_t v, int wi, int nw, int n, uint16_t* list, int total) {
+  if (wi == nw - 1 && (n & 31)) v &= (1u << (n & 31)) - 1u;  // bits beyond n never count
+  int tot;
+  int at = total + warp_excl_scan(__popc(v), &tot);
+  while (v) {
+    const int bpos = __ffs(v) - 1;
+    v &= v - 1u;
+    list[at++] = (uint16_t)(32 * wi + bpos);
+  }
+  return total + tot;
+}
+
+// Reads and clears the cell's bit-mask words covering [0, n) and writes the
+// flagged slots in ascending order to `list`. Returns their number.
+__device__ __noinline__ int gather_flags(uint32_t* bits, int W, int cell, int n, uint16_t* list) {
   const int lane = lane_id();
   const int nw = (n + 31) >> 5;
   uint32_t* row = bits + (size_t)cell * W;
   int total = 0;
   for (int w0 = 0; w0 < nw; w0 += 32) {
     const int wi = w0 + lane;
-    uint32_t v = wi < nw ? row[wi] : 0u;
+    const uint32_t v = wi < nw ? row[wi] : 0u;
     if (v) row[wi] = 0u;
-    if (wi == nw - 1 && (n & 31)) v &= (1u << (n & 31)) - 1u;  // bits beyond n never count
-    int tot;
-    int at = total + warp_excl_scan(__popc(v), &tot);
-    while (v) {
-      const int bpos = __ffs(v) - 1;
-      v &= v - 1u;
-      list[at++] = (uint16_t)(32 * wi + bpos);
-    }
-    total += tot;
+    total = list_flags(v, wi, nw, n, list, total);
   }
   return total;
 }
@@ -516,11 +709,16 @@ __device__ __forceinline__ void event_cell(const StepArgs& A, int cell, EvScratc
   const int mask = A.mask;
   const int ne = min(max(A.e.count[cell], 0), A.e.cap);
   const int ng_start = min(max(A.g.count[cell], 0), A.g.cap);
+  const int na_start = min(max(A.a.count[cell], 0), A.a.cap);
   int ng = ng_start;
-  int na = min(max(A.a.count[cell], 0), A.a.cap);
+  int na = na_start;
   const long abase = (long)cell * A.a.cap;
   const long gbase = (long)cell * A.g.cap;
   const long ebase = (long)cell * A.e.cap;
+  const bool prim = mask & AXPIC_CH_PRIMAKOFF;
+  const bool bath = mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS);
+  const bool eC = mask & AXPIC_CH_COMPTON, eB = mask & AXPIC_CH_BREMS;
+  const int ng0 = (PH & PH_ABSORB) ? ng_start : (A.use_snapshot ? min(A.photon_start[cell], ng) : ng);
   // particles present at the start of the step: counted by the absorb phase,
   // or by the emit phase when no absorb ran this step
   if (lane == 0 && ((PH & PH_ABSORB) || ((PH & PH_EMIT) && !A.use_snapshot))) {
@@ -529,6 +727,32 @@ __device__ __forceinline__ void event_cell(const StepArgs& A, int cell, EvScratc
     cnt.add(C_NA, na);
     cnt.add(C_CELLS, 1);
   }
+  // all decision masks of this call are read (and cleared) up front
+  int nflA = 0, nflG = 0, nflE = 0;
+  {
+    const int nwA = (PH & PH_ABSORB) ? (na_start + 31) >> 5 : 0;
+    const int nwG = ((PH & PH_EMIT) && prim) ? (ng0 + 31) >> 5 : 0;
+    const int nwE = ((PH & PH_EMIT) && (eC || eB)) ? (ne + 31) >> 5 : 0;
+    if (nwA <= 32 && nwG <= 32 && nwE <= 32) {
+      uint32_t* rA = A.bitsA + (size_t)cell * A.Wa;
+      uint32_t* rG = A.bitsG + (size_t)cell * A.Wg;
+      uint32_t* rE = A.bitsE + (size_t)cell * A.We;
+      const uint32_t vA = lane < nwA ? rA[lane] : 0u;
+      const uint32_t vG = lane < nwG ? rG[lane] : 0u;
+      const uint32_t vE = lane < nwE ? rE[lane] : 0u;
+      if (vA) rA[lane] = 0u;
+      if (vG) rG[lane] = 0u;
+      if (vE) rE[lane] = 0u;
+      if (__any_sync(kFull, vA != 0)) nflA = list_flags(vA, lane, nwA, na_start, S.flA, 0);
+      if (__any_sync(kFull, vG != 0)) nflG = list_flags(vG, lane, nwG, ng0, S.flG, 0);
+      if (__any_sync(kFull, vE != 0)) nflE = list_flags(vE, lane, nwE, ne, S.flE, 0);
+    } else {
+      if (nwA) nflA = gather_flags(A.bitsA, A.Wa, cell, na_start, S.flA);
+      if (nwG) nflG = gather_flags(A.bitsG, A.Wg, cell, ng0, S.flG);
+      if (nwE) nflE = gather_flags(A.bitsE, A.We, cell, ne, S.flE);
+    }
+    __syncwarp();
+  }
   Lane64 x64;
   double xa[4] = {0.0, 0.0, 0.0, 0.0};
   bool xa_any = false;
@@ -536,63 +760,53 @@ __device__ __forceinline__ void event_cell(const StepArgs& A, int cell, EvScratc
   // ------------------------------------------------------------ absorb
   if (PH & PH_ABSORB) {
     if (lane == 0) A.photon_start[cell] = ng;
-    const int na0 = na;
-    const int nfl = gather_flags(A.bitsA, A.Wa, cell, na0, S.flA);
-    if (nfl > 0) {
-      const bool prim = mask & AXPIC_CH_PRIMAKOFF;
-      const bool bath = mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS);
-      for (int i = lane; i < (na0 + 31) / 32; i += 32) S.rbA[i] = 0u;
+    if (nflA > 0) {
+      for (int i = lane; i < (na_start + 31) / 32; i += 32) S.rbA[i] = 0u;
       __syncwarp();
       int run = 0, nrm = 0, NPg = 0;
-      for (int i0 = 0; i0 < nfl; i0 += 32) {
+      for (int i0 = 0; i0 < nflA; i0 += 32) {
         const int i = i0 + lane;
-        int K = 0;
+        int K = 0, slot = 0;
         bool removed = false;
-        AxionDecision d;
-        d.K = 0;
-        d.keep = true;
-        int slot = 0;
-        float px = 0.f, py = 0.f, pz = 0.f, xx = 0.f, yy = 0.f, zz = 0.f;
-        if (i < nfl) {
+        float wprod = 0.f, px = 0.f, py = 0.f, pz = 0.f, xx = 0.f, yy = 0.f, zz = 0.f;
+        if (i < nflA) {
           slot = S.flA[i];
-          const uint32_t q = slot >> 2;
-          uint4 rP = make_uint4(0, 0, 0, 0), rA = make_uint4(0, 0, 0, 0);
-          if (prim) rP = philox4x32_10(make_uint4(A.step, gcell, q, S_PRIM_INV << 24), A.key0, A.key1);
-          if (bath) rA = philox4x32_10(make_uint4(A.step, gcell, q, S_ABSORB << 24), A.key0, A.key1);
           const long src = abase + slot;
+          const uint4 r = A.recA[src];
           const float w = A.a.w[src];
           px = A.a.px[src];
           py = A.a.py[src];
           pz = A.a.pz[src];
-          d = axion_decide_slow(A, cell, mask, w, px, py, pz, word(rP, slot & 3), word(rA, slot & 3));
-          cnt.add(C_CAP, d.capped);
-          cnt.add(C_CLAMP, d.over);
-          cnt.add(C_EV_PINV, d.K);
-          if (d.absorbed) {
-            x64.add((double)d.wnew, d.om, px, py, pz);
-            if (d.abs_c) cnt.add(C_ABS_C, 1);
-            else cnt.add(C_ABS_B, 1);
+          K = r.x & 0xFF;
+          wprod = __uint_as_float(r.y);
+          const float wnew = __uint_as_float(r.z);
+          const float om = sqrtf(px * px + py * py + pz * pz) * kMeC2f;
+          cnt.add(C_CAP, (r.x & DF_CAPPED) ? 1u : 0u);
+          cnt.add(C_CLAMP, (r.x & DF_OVER) ? 1u : 0u);
+          cnt.add(C_EV_PINV, (unsigned)K);
+          if (r.x & DF_ABSORBED) {
+            x64.add((double)wnew, om, px, py, pz);
+            cnt.add((r.x & DF_ABS_C) ? C_ABS_C : C_ABS_B, 1);
           } else if (A.absorb_mode == 1 && bath) {
             // weight reduction: the lost weight's energy goes to the plasma
             float wrem = w;
-            if (d.K > 0) wrem = d.over ? 0.f : __fsub_rn(w, __fmul_rn((float)d.K, d.wprod));
-            x64.add((double)wrem - (double)d.wnew, d.om, px, py, pz);
+            if (K > 0) wrem = (r.x & DF_OVER) ? 0.f : __fsub_rn(w, __fmul_rn((float)K, wprod));
+            x64.add((double)wrem - (double)wnew, om, px, py, pz);
           }
-          K = d.K;
-          removed = !d.keep;
+          removed = !(r.x & DF_KEEP);
           if (K) {
             xx = A.a.x[src];
             yy = A.a.y[src];
             zz = A.a.z[src];
           }
-          if (d.keep && d.wnew != w) A.a.w[src] = d.wnew;
+          if (!removed && wnew != w) A.a.w[src] = wnew;
         }
         // photon products of a->gamma after the photons present
         int tot;
         int off = run + warp_excl_scan(K, &tot);
         for (int k = 0; k < K; ++k, ++off) {
           const int dst = ng + off;
-          if (dst < A.g.cap) write_particle(A.g, gbase + dst, d.wprod, px, py, pz, xx, yy, zz);
+          if (dst < A.g.cap) write_particle(A.g, gbase + dst, wprod, px, py, pz, xx, yy, zz);
           else cnt.add(C_DROP, 1);
         }
         run += tot;
@@ -607,9 +821,9 @@ __device__ __forceinline__ void event_cell(const StepArgs& A, int cell, EvScratc
       NPg = warp_sum_i(NPg);
       ng = min(ng + NPg, A.g.cap);
       __syncwarp();
-      if (nrm > 0) compact_removed(A.a, abase, S.rmA, nrm, S.rbA, na0);
+      if (nrm > 0) compact_removed(A.a, abase, S.rmA, nrm, S.rbA, na_start);
       __syncwarp();
-      na = na0 - nrm;
+      na = na_start - nrm;
     }
     if (__any_sync(kFull, x64.any)) {
       xa[0] = warp_sum_d(x64.dE);
@@ -623,75 +837,65 @@ __device__ __forceinline__ void event_cell(const StepArgs& A, int cell, EvScratc
 
   // ------------------------------------------------------------ emit
   if (PH & PH_EMIT) {
-    const int ng0 = (PH & PH_ABSORB) ? ng_start : (A.use_snapshot ? min(A.photon_start[cell], ng) : ng);
     const int ng_tot = ng;
-    const bool prim = mask & AXPIC_CH_PRIMAKOFF;
     const int abase_new = na;
     int NPa = 0, nrm = 0;
-    // (c) photon decisions for the flagged photons; axion products after the
-    // surviving axions
-    if (prim) {
-      const int nfl = gather_flags(A.bitsG, A.Wg, cell, ng0, S.flG);
-      if (nfl > 0) {
-        for (int i = lane; i < (ng_tot + 31) / 32; i += 32) S.rbG[i] = 0u;
-        __syncwarp();
-        int run = 0;
-        for (int i0 = 0; i0 < nfl; i0 += 32) {
-          const int i = i0 + lane;
-          int K = 0;
-          bool removed = false;
-          int slot = 0;
-          PhotonDecision d;
-          d.K = 0;
-          float px = 0.f, py = 0.f, pz = 0.f, xx = 0.f, yy = 0.f, zz = 0.f;
-          if (i < nfl) {
-            slot = S.flG[i];
-            const uint4 r =
-                philox4x32_10(make_uint4(A.step, gcell, (uint32_t)(slot >> 2), S_PRIM_FWD << 24), A.key0, A.key1);
-            const long src = gbase + slot;
-            const float w = A.g.w[src];
+    // (c) flagged photons; axion products after the surviving axions
+    if (nflG > 0) {
+      for (int i = lane; i < (ng_tot + 31) / 32; i += 32) S.rbG[i] = 0u;
+      __syncwarp();
+      int run = 0;
+      for (int i0 = 0; i0 < nflG; i0 += 32) {
+        const int i = i0 + lane;
+        int K = 0, slot = 0;
+        bool removed = false;
+        float wprod = 0.f, om = 0.f, px = 0.f, py = 0.f, pz = 0.f, xx = 0.f, yy = 0.f, zz = 0.f;
+        if (i < nflG) {
+          slot = S.flG[i];
+          const long src = gbase + slot;
+          const uint4 r = A.recG[src];
+          K = r.x & 0xFF;
+          wprod = __uint_as_float(r.y);
+          const float wrem = __uint_as_float(r.z);
+          cnt.add(C_CAP, (r.x & DF_CAPPED) ? 1u : 0u);
+          cnt.add(C_CLAMP, (r.x & DF_OVER) ? 1u : 0u);
+          cnt.add(C_EV_P, (unsigned)K);
+          removed = !(r.x & DF_KEEP);
+          if (K) {
             px = A.g.px[src];
             py = A.g.py[src];
             pz = A.g.pz[src];
-            d = photon_decide_slow(A, cell, w, px, py, pz, word(r, slot & 3));
-            cnt.add(C_CAP, d.capped);
-            cnt.add(C_CLAMP, d.over);
-            cnt.add(C_EV_P, d.K);
-            K = d.K;
-            removed = !(d.wrem > 0.f);
-            if (K) {
-              xx = A.g.x[src];
-              yy = A.g.y[src];
-              zz = A.g.z[src];
-              if (!removed) A.g.w[src] = d.wrem;
-            }
+            xx = A.g.x[src];
+            yy = A.g.y[src];
+            zz = A.g.z[src];
+            om = sqrtf(px * px + py * py + pz * pz) * kMeC2f;
+            if (!removed) A.g.w[src] = wrem;
           }
-          int tot;
-          int off = run + warp_excl_scan(K, &tot);
-          for (int k = 0; k < K; ++k, ++off) {
-            const int dst = abase_new + off;
-            if (dst < A.a.cap) {
-              write_particle(A.a, abase + dst, d.wprod, px, py, pz, xx, yy, zz);
-              if (A.tally_enable) tally_add(A, 0, d.wprod, d.om);
-            } else {
-              cnt.add(C_DROP, 1);
-            }
-          }
-          run += tot;
-          NPa += K;
-          const unsigned m = __ballot_sync(kFull, removed);
-          if (removed) {
-            S.rmG[nrm + __popc(m & lt)] = (uint16_t)slot;
-            atomicOr(&S.rbG[slot >> 5], 1u << (slot & 31));
-          }
-          nrm += __popc(m);
         }
-        NPa = warp_sum_i(NPa);
+        int tot;
+        int off = run + warp_excl_scan(K, &tot);
+        for (int k = 0; k < K; ++k, ++off) {
+          const int dst = abase_new + off;
+          if (dst < A.a.cap) {
+            write_particle(A.a, abase + dst, wprod, px, py, pz, xx, yy, zz);
+            if (A.tally_enable) tally_add(A, 0, wprod, om);
+          } else {
+            cnt.add(C_DROP, 1);
+          }
+        }
+        run += tot;
+        NPa += K;
+        const unsigned m = __ballot_sync(kFull, removed);
+        if (removed) {
+          S.rmG[nrm + __popc(m & lt)] = (uint16_t)slot;
+          atomicOr(&S.rbG[slot >> 5], 1u << (slot & 31));
+        }
+        nrm += __popc(m);
       }
+      NPa = warp_sum_i(NPa);
     }
     // (d) electron events, in electron then event order; event k of
     // electron i: cos theta, phi, energy and channel from one Philox block
-    const bool eC = mask & AXPIC_CH_COMPTON, eB = mask & AXPIC_CH_BREMS;
     int NE = 0;
     if (eC || eB) {
       const float* rec = A.rec + (size_t)cell * kRecLen;
@@ -703,31 +907,29 @@ __device__ __forceinline__ void event_cell(const StepArgs& A, int cell, EvScratc
         if (eB) cap_lambda(wu * rec[R_CB], A.lam_cap, &fac, &cb);
         cnt.add(C_CAP, (unsigned)ne * ((unsigned)cc + (unsigned)cb));
       }
-      const int nfl = gather_flags(A.bitsE, A.We, cell, ne, S.flE);
-      if (nfl > 0) {
+      if (nflE > 0) {
         const float* tabC = A.tables + TAB_COMPTON * kTableN;
         const float* tabB = A.tables + TAB_BREMS * kTableN;
         int run = 0;
-        for (int i0 = 0; i0 < nfl; i0 += 32) {
+        for (int i0 = 0; i0 < nflE; i0 += 32) {
           const int i = i0 + lane;
           int K = 0, slot = 0;
-          float w = 0.f, lc = 0.f, lb = 0.f, facC = 1.f, facB = 1.f;
-          bool cc = false, cb = false;
-          if (i < nfl) {
+          if (i < nflE) {
             slot = S.flE[i];
-            const uint4 r =
-                philox4x32_10(make_uint4(A.step, gcell, (uint32_t)(slot >> 2), S_EMIT_E << 24), A.key0, A.key1);
-            w = wu > 0.f ? wu : A.e.w[ebase + slot];
-            lc = eC ? cap_lambda(w * rec[R_CC], A.lam_cap, &facC, &cc) : 0.f;
-            lb = eB ? cap_lambda(w * rec[R_CB], A.lam_cap, &facB, &cb) : 0.f;
-            if (wu <= 0.f) cnt.add(C_CAP, (unsigned)cc + (unsigned)cb);
-            K = poisson_inv(u23(word(r, slot & 3)), lc + lb);
+            const uint32_t f = A.recE[ebase + slot];
+            K = f & 0xFF;
+            if (wu <= 0.f) cnt.add(C_CAP, ((f & DF_CAPPED) ? 1u : 0u) + ((f & DF_CAPPED_B) ? 1u : 0u));
           }
           int tot;
           int off = run + warp_excl_scan(K, &tot);
           if (K) {
             const long src = ebase + slot;
+            const float w = wu > 0.f ? wu : A.e.w[src];
             const float xx = A.e.x[src], yy = A.e.y[src], zz = A.e.z[src];
+            float facC = 1.f, facB = 1.f;
+            bool cc = false, cb = false;
+            const float lc = eC ? cap_lambda(w * rec[R_CC], A.lam_cap, &facC, &cc) : 0.f;
+            const float lb = eB ? cap_lambda(w * rec[R_CB], A.lam_cap, &facB, &cb) : 0.f;
             const float fracC = lc / (lc + lb);
             const float wvC = cc ? A.w_a * facC : A.w_a;
             const float wvB = cb ? A.w_a * facB : A.w_a;
@@ -748,8 +950,7 @@ __device__ __forceinline__ void event_cell(const StepArgs& A, int cell, EvScratc
                 cnt.add(C_DROP, 1);
               }
               x64.add(-(double)wv, E, px, py, pz);
-              if (isC) cnt.add(C_EV_C, 1);
-              else cnt.add(C_EV_B, 1);
+              cnt.add(isC ? C_EV_C : C_EV_B, 1);
             }
           }
           run += tot;
@@ -989,17 +1190,17 @@ static cudaError_t launch_events(const StepArgs& A, int warps, cudaStream_t st) 
   return cudaGetLastError();
 }
 
+static int dec_blocks(const StepArgs& A) { return (A.ncells + A.dec_cells - 1) / A.dec_cells; }
+
 static cudaError_t launch_axion_decide(const StepArgs& A, cudaStream_t st) {
-  const long threads = (long)A.ncells * (A.a.cap >> 2);
-  if (threads == 0) return cudaSuccess;
-  axion_decide_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A);
+  if (A.a.cap == 0 || A.ncells == 0) return cudaSuccess;
+  axion_decide_kernel<<<dec_blocks(A), kDecThreads, 0, st>>>(A);
   return cudaGetLastError();
 }
 
 static cudaError_t launch_emit_decide(const StepArgs& A, cudaStream_t st) {
-  const long threads = (long)A.ncells * ((A.g.cap >> 2) + (A.e.cap >> 2));
-  if (threads == 0) return cudaSuccess;
-  emit_decide_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A);
+  if ((A.g.cap == 0 && A.e.cap == 0) || A.ncells == 0) return cudaSuccess;
+  emit_decide_kernel<<<dim3(dec_blocks(A), 2), kDecThreads, 0, st>>>(A);
   return cudaGetLastError();
 }
 
@@ -1008,9 +1209,11 @@ static cudaError_t launch_feedback(const StepArgs& A, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t st) {
+cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t st, cudaEvent_t* ev) {
   if (A.ncells == 0) return cudaSuccess;
   cudaError_t e;
+  // optional measurement: events between the kernels of a full step
+  auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], st) : cudaSuccess; };
   switch (phases) {
     case PH_ABSORB:
       if ((e = launch_axion_decide(A, st))) return e;
@@ -1024,10 +1227,11 @@ cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t s
       // the photon decisions of the emit phase read the photons present at
       // the start of the step, before the absorb phase appends a->gamma
       // products, so both decision kernels run first
-      if ((e = launch_axion_decide(A, st))) return e;
-      if ((e = launch_emit_decide(A, st))) return e;
-      if ((e = launch_events<PH_ABSORB | PH_EMIT>(A, warps, st))) return e;
-      return launch_feedback(A, st);
+      if ((e = mark(0)) || (e = launch_axion_decide(A, st)) || (e = mark(1))) return e;
+      if ((e = launch_emit_decide(A, st)) || (e = mark(2))) return e;
+      if ((e = launch_events<PH_ABSORB | PH_EMIT>(A, warps, st)) || (e = mark(3))) return e;
+      if ((e = launch_feedback(A, st)) || (e = mark(4))) return e;
+      return cudaSuccess;
     }
     default:
       return cudaErrorInvalidValue;

@@ -7,7 +7,9 @@ namespace axpic {
 enum { PH_ABSORB = 1, PH_EMIT = 2, PH_FEEDBACK = 4, PH_ALL = 7 };
 
 size_t step_smem_per_warp(int acap, int gcap, int ecap);
-cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t st);
+// ev: NULL, or 5 events recorded around the kernels of a PH_ALL step.
+cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t st, cudaEvent_t* ev = nullptr);
+constexpr int kStepKernels = 4;
 cudaError_t set_step_smem_limits(size_t bytes);
 
 }  // namespace axpic

@@ -143,6 +143,12 @@ class AxionPlasma:
         _lib.axpic_get_residuals(self.ctx, first, count, buf)
         return np.array(buf)[:4 * count].reshape(count, 4)
 
+    def profile_begin(self, max_steps):
+        _lib.axpic_profile_begin(self.ctx, max_steps)
+
+    def profile_end(self):
+        return _lib.axpic_profile_end(self.ctx)
+
     def sync(self):
         _lib.axpic_sync(self.ctx)
 
