@@ -69,12 +69,16 @@ def measured_peaks():
 
 def kernel_bytes(tot, T_mode):
     """Algorithmic DRAM bytes of each kernel of the step, summed over the timed
-    steps (the minimum each kernel has to move):
-      axion decisions: w, p of every axion present (16 B) + count and three
-        record words per cell (16 B);
-      emit decisions: w, p of every photon present (16 B), w of electrons in
-        cells without a common weight (4 B; 0 here) + counts, snapshot, record
-        words and common weight per cell (32 B);
+    steps.
+
+    "step": the minimum of a fused cell-local pass with feedback every step,
+    28 B per electron (w, p read, p written), 16 B per photon and 16 B per
+    axion (w, p read); the step's roofline is taken against it.
+
+    Each kernel is charged the minimum it moves:
+      decisions: w, p of every axion and photon present (16 B), w of
+        electrons in cells without a common weight (4 B; 0 here) + counts,
+        snapshot, record words and common weight per cell (48 B);
       events: the decision masks (1 bit per particle), counts, snapshot and
         flags per cell (40 B), each product written (28 B) with its parent's
         w, p and position read (28 B), each removed slot refilled (56 B);
@@ -86,8 +90,8 @@ def kernel_bytes(tot, T_mode):
     removed = tot["events_p"] + tot["absorbed_c"] + tot["absorbed_b"] + tot["events_pinv"]
     parts = tot["part_e"] + tot["part_g"] + tot["part_a"]
     return {
-        "axion_decide_kernel": 16.0 * tot["part_a"] + 16.0 * cells,
-        "emit_decide_kernel": 16.0 * tot["part_g"] + 32.0 * cells,
+        "step": 28.0 * tot["part_e"] + 16.0 * tot["part_g"] + 16.0 * tot["part_a"],
+        "decide_kernel": 16.0 * tot["part_a"] + 16.0 * tot["part_g"] + 48.0 * cells,
         "event_kernel": parts / 8.0 + 40.0 * cells + 56.0 * products + 56.0 * removed,
         "feedback_kernel": (104.0 + (80.0 if T_mode == 2 else 0.0)) * cells + 28.0 * tot["remap_e"],
     }
@@ -344,6 +348,10 @@ def main():
             except Exception:
                 traffic = None
         value = particles / (elapsed_ms * 1e-3)
+        # the whole step against the fused-pass minimum (28 B per electron,
+        # 16 B per photon and axion), over the summed device time of its kernels
+        step_s = sum(kms.values()) * 1e-3
+        step_gbs = kbytes["step"] / step_s / 1e9 if step_s > 0 else None
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -357,7 +365,11 @@ def main():
                              "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                              "kernel": "axpic::" + dom, "algorithmic_bytes_per_launch": bytes_per_launch,
                              "kernels": per_kernel},
-                "gpu_launches": 4 * args.steps, "clocks": clk,
+                "roofline_step": {"bound": "hbm", "basis": "28 B per electron, 16 B per photon and axion",
+                                  "achieved": step_gbs, "peak": peak, "unit": "GB/s",
+                                  "frac": step_gbs / peak if step_gbs else None,
+                                  "bytes_per_step": kbytes["step"] / max(nprof, 1)},
+                "gpu_launches": len(kms) * args.steps, "clocks": clk,
                 "counts": {"particle_steps": particles, "events_primakoff": tot["events_p"],
                            "events_compton": tot["events_c"], "events_brems": tot["events_b"],
                            "events_inverse": tot["events_pinv"], "remapped_cells": tot["remaps"]}}

@@ -273,14 +273,21 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc *desc, const axpic_param
 
 /* Measurement of the step's kernels. axpic_profile_begin (synchronises)
  * prepares CUDA events for the next max_steps calls of axpic_step, which then
- * record an event on the context's stream before and after each of their
- * four kernels (recording adds no kernel work). axpic_profile_end
- * (synchronises) writes to ms_out (host, 4 doubles) the summed device time of
- * each kernel over the recorded steps, in the order axion decisions, emit
- * decisions, events, feedback, sets *steps_out (may be NULL) to the number of
- * steps recorded, and releases the events. Not part of the paper's method. */
+ * record an event on the context's stream before and after each kernel they
+ * launch (recording adds no kernel work). axpic_profile_end (synchronises)
+ * writes to ms_out (host, AXPIC_PROFILE_SLOTS doubles) the summed device time
+ * of each kernel over the recorded steps, in the order that
+ * axpic_step_kernel_names gives (unused slots are 0), sets *steps_out (may be
+ * NULL) to the number of steps recorded, and releases the events. Not part of
+ * the paper's method. */
+#define AXPIC_PROFILE_SLOTS 4
 axpic_status axpic_profile_begin(axpic_ctx *ctx, int32_t max_steps);
 axpic_status axpic_profile_end(axpic_ctx *ctx, double *ms_out, int32_t *steps_out);
+
+/* Comma-separated names of the kernels that one axpic_step launches, in
+ * launch order (decisions, events, feedback). The string is static; "" for a
+ * NULL context. */
+const char *axpic_step_kernel_names(const axpic_ctx *ctx);
 
 /* Wait for the stream and return the first latched device error, if any. */
 axpic_status axpic_sync(axpic_ctx *ctx);

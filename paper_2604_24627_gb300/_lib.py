@@ -88,6 +88,7 @@ EXPORTS = {
     "axpic_profile_begin": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "axpic_profile_end": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int32)]),
+    "axpic_step_kernel_names": (ctypes.c_char_p, [ctypes.c_void_p]),
     "axpic_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "axpic_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "axpic_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -185,7 +186,12 @@ def axpic_step_noalloc(desc, params, step, mask, carry_ptr, stream=0):
         raise AxpicError(st, "axpic_step_noalloc failed (see stderr)")
 
 
-STEP_KERNELS = ("axion_decide_kernel", "emit_decide_kernel", "event_kernel", "feedback_kernel")
+PROFILE_SLOTS = 4
+
+
+def axpic_step_kernel_names(ctx):
+    """Names of the kernels one axpic_step launches, in order."""
+    return tuple(n for n in lib().axpic_step_kernel_names(ctx).decode().split(",") if n)
 
 
 def axpic_profile_begin(ctx, max_steps):
@@ -194,10 +200,10 @@ def axpic_profile_begin(ctx, max_steps):
 
 def axpic_profile_end(ctx):
     """(dict kernel -> summed ms, number of steps recorded)."""
-    ms = (ctypes.c_double * 4)()
+    ms = (ctypes.c_double * PROFILE_SLOTS)()
     n = ctypes.c_int32()
     _check(ctx, lib().axpic_profile_end(ctx, ms, ctypes.byref(n)))
-    return dict(zip(STEP_KERNELS, list(ms))), n.value
+    return dict(zip(axpic_step_kernel_names(ctx), list(ms))), n.value
 
 
 def axpic_sync(ctx):

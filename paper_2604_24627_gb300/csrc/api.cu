@@ -52,7 +52,8 @@ struct axpic_ctx {
   uint32_t* recE = nullptr;   // event counts of flagged electrons
   CellConst cc;
   int warps = kDefaultWarps;
-  int grid = 0;
+  int grid = 0;      // event-kernel CTAs, also the rows of per-CTA counters
+  int dec_grid = 1;  // CTAs of the persistent decision kernel
   int64_t last_absorb_step = -1;
   std::string last_error;
   std::vector<cudaEvent_t> prof_events;  // 5 per recorded step, created by axpic_profile_begin
@@ -139,6 +140,7 @@ static void fold_constants(axpic_ctx* ctx) {
   cc.k_BB = (float)(2.0 * kPi * kPi * hc3 * p.dt_phys_s / (std::tgamma(a) * a * kKeVerg));
 }
 
+
 static StepArgs make_args(axpic_ctx* ctx, int64_t step, int mask) {
   const axpic_params& p = ctx->prm;
   StepArgs A;
@@ -151,6 +153,10 @@ static StepArgs make_args(axpic_ctx* ctx, int64_t step, int mask) {
   A.step = (uint32_t)(step & 0xFFFFFFFF);
   A.key0 = (uint32_t)(p.seed & 0xFFFFFFFFu);
   A.key1 = (uint32_t)(p.seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    A.rk.k0[r] = A.key0 + (uint32_t)r * 0x9E3779B9u;
+    A.rk.k1[r] = A.key1 + (uint32_t)r * 0xBB67AE85u;
+  }
   A.mask = mask;
   A.w_a = (float)p.w_a;
   A.w_gref = (float)w_gref(p);
@@ -192,7 +198,7 @@ static StepArgs make_args(axpic_ctx* ctx, int64_t step, int mask) {
   A.recA = ctx->recA;
   A.recG = ctx->recG;
   A.recE = ctx->recE;
-  A.dec_cells = AXPIC_DEC_CELLS;
+  A.dec_grid = ctx->dec_grid;
   A.cc = ctx->cc;
   return A;
 }
@@ -336,7 +342,7 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
       (e = cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * kNumCounters * (size_t)ctx->grid, st)) ||
       (e = cudaMemsetAsync(ctx->err, 0, sizeof(int), st)) ||
       (e = cudaMemsetAsync(ctx->bits, 0, sizeof(uint32_t) * (bit_words > 0 ? bit_words : 1), st)) ||
-      (e = set_step_smem_limits(per_warp * warps)) ||
+      (e = set_step_smem_limits(per_warp * warps)) || (e = decide_resident_ctas(&ctx->dec_grid)) ||
       (e = launch_records(n, d.nspecies, ctx->cc, d.T_keV, d.n_ion, ctx->rec, ctx->err, st)) ||
       (e = launch_moments(n, to_ptrs(d.electrons), ctx->mom, st)) || (e = cudaStreamSynchronize(st))) {
     ctx->last_error = cudaGetErrorString(e);
@@ -392,7 +398,8 @@ static axpic_status run_phases(axpic_ctx* ctx, int phases, int64_t step, int32_t
   StepArgs A = make_args(ctx, step, mask);
   if (phases == PH_EMIT) A.use_snapshot = ctx->last_absorb_step == step;
   cudaEvent_t* ev = nullptr;
-  if (phases == PH_ALL && ctx->prof_used < ctx->prof_max) ev = ctx->prof_events.data() + 5 * (ctx->prof_used++);
+  if (phases == PH_ALL && ctx->prof_used < ctx->prof_max)
+    ev = ctx->prof_events.data() + (kStepKernels + 1) * (ctx->prof_used++);
   CK(launch_step(phases, A, ctx->warps, ctx->stream, ev), name);
   if (phases == PH_ABSORB) ctx->last_absorb_step = step;
   return AXPIC_OK;
@@ -533,7 +540,7 @@ axpic_status axpic_profile_begin(axpic_ctx* ctx, int32_t max_steps) {
   if (!ctx || max_steps < 0 || max_steps > (1 << 20)) return AXPIC_E_INVALID;
   CK(cudaStreamSynchronize(ctx->stream), "synchronize");
   free_events(ctx);
-  ctx->prof_events.resize(5 * (size_t)max_steps);
+  ctx->prof_events.resize((kStepKernels + 1) * (size_t)max_steps);
   for (auto& e : ctx->prof_events) CK(cudaEventCreate(&e), "event create");
   ctx->prof_max = max_steps;
   return AXPIC_OK;
@@ -542,17 +549,22 @@ axpic_status axpic_profile_begin(axpic_ctx* ctx, int32_t max_steps) {
 axpic_status axpic_profile_end(axpic_ctx* ctx, double* ms_out, int32_t* steps_out) {
   if (!ctx || !ms_out) return AXPIC_E_INVALID;
   CK(cudaStreamSynchronize(ctx->stream), "synchronize");
-  for (int k = 0; k < kStepKernels; ++k) ms_out[k] = 0.0;
+  for (int k = 0; k < AXPIC_PROFILE_SLOTS; ++k) ms_out[k] = 0.0;
   for (int s = 0; s < ctx->prof_used; ++s) {
+    const cudaEvent_t* ev = ctx->prof_events.data() + (kStepKernels + 1) * s;
     for (int k = 0; k < kStepKernels; ++k) {
       float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, ctx->prof_events[5 * s + k], ctx->prof_events[5 * s + k + 1]), "elapsed");
+      CK(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]), "elapsed");
       ms_out[k] += ms;
     }
   }
   if (steps_out) *steps_out = ctx->prof_used;
   free_events(ctx);
   return AXPIC_OK;
+}
+
+const char* axpic_step_kernel_names(const axpic_ctx* ctx) {
+  return ctx ? step_kernel_names() : "";
 }
 
 axpic_status axpic_sync(axpic_ctx* ctx) {
@@ -682,7 +694,7 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc* desc, const axpic_param
       (e = cudaMemsetAsync(c.counters, 0, sizeof(unsigned long long) * kNumCounters * (size_t)c.grid, st)) ||
       (e = cudaMemsetAsync(c.xbuf, 0, sizeof(double) * 4 * (size_t)d.ncells, st)) ||
       (e = cudaMemsetAsync(c.bits, 0, bit_bytes > 0 ? bit_bytes : 4, st)) ||
-      (e = set_step_smem_limits(per_warp * kNoAllocWarps)) ||
+      (e = set_step_smem_limits(per_warp * kNoAllocWarps)) || (e = decide_resident_ctas(&c.dec_grid)) ||
       (e = launch_records(d.ncells, d.nspecies, c.cc, d.T_keV, d.n_ion, c.rec, c.err, st)) ||
       (e = launch_moments(d.ncells, to_ptrs(d.electrons), c.mom, st)) ||
       (e = launch_step(PH_ALL, A, kNoAllocWarps, st)) ||

@@ -64,11 +64,10 @@ enum {
 // weight (0 otherwise). Electrons change only through the remap.
 constexpr int kMomLen = 8;
 
-// Cells per decision CTA: at most kDecMaxCells; the default is a compile-time
-// choice that launch-shape sweeps override.
-constexpr int kDecMaxCells = 16;
-#ifndef AXPIC_DEC_CELLS
-#define AXPIC_DEC_CELLS 8
+// Cells per chunk of a decision warp; the default is a compile-time choice
+// that launch-shape sweeps override.
+#ifndef AXPIC_DEC_CHUNK
+#define AXPIC_DEC_CHUNK 4
 #endif
 enum { M_W = 0, M_PX, M_PY, M_PZ, M_U2, M_VAR, M_WU };
 
@@ -125,9 +124,28 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
-// ((word >> 9) + 0.5) * 2^-23: exact in binary32, in (0, 1).
+// ((word >> 9) + 0.5) * 2^-23: exact in binary32, in (0, 1). Formed from the
+// bits: 1 + m 2^-23 (exponent 0, mantissa m = word >> 9) minus (1 - 2^-24)
+// is exact by Sterbenz's lemma, with no integer-to-float conversion.
 __device__ __forceinline__ float u23(uint32_t w) {
-  return ((float)(w >> 9) + 0.5f) * 1.1920928955078125e-07f;
+  return __fsub_rn(__uint_as_float((w >> 9) | 0x3F800000u), __uint_as_float(0x3F7FFFFFu));
+}
+
+// Round keys of Philox4x32-10 for one key (k + r W mod 2^32, r = 0..9),
+// formed on the host so that the rounds take them as constant operands.
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& K) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ K.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ K.k1[r],
+                   (uint32_t)p0);
+  }
+  return c;
 }
 
 __device__ __forceinline__ uint32_t word(const uint4& b, int j) {
@@ -305,6 +323,7 @@ struct StepArgs {
   uint32_t cell_base;     // global index of cell 0 (low 32 bits)
   uint32_t step;
   uint32_t key0, key1;
+  PhiloxKeys rk;  // round keys of (key0, key1)
   int mask;
   float w_a, w_gref, inv_w_a, inv_w_gref;
   float lam_cap;          // effective cap, <= 64
@@ -331,7 +350,7 @@ struct StepArgs {
   uint4 *recA, *recG;               // full decisions of flagged slots (slot-indexed)
   uint32_t* recE;
   int* err;
-  int dec_cells;  // cells per decision CTA, 1..kDecMaxCells
+  int dec_grid;   // CTAs of the persistent decision kernel
   CellConst cc;
 };
 

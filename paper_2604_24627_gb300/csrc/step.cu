@@ -64,10 +64,6 @@ __device__ __forceinline__ float f4(const float4& v, int j) {
 
 __device__ __forceinline__ bool bit(const uint32_t* b, int i) { return (b[i >> 5] >> (i & 31)) & 1u; }
 
-// Quads are consumed element by element from .x and then rotated, so that a
-// runtime slot index never forces them into local memory.
-__device__ __forceinline__ void rot(float4& v) { v = make_float4(v.y, v.z, v.w, v.x); }
-__device__ __forceinline__ void rot(uint4& v) { v = make_uint4(v.y, v.z, v.w, v.x); }
 
 // Lane-local FP64 exchange (Delta E keV, Delta P m_e c) and a flag that avoids
 // FP64 zero tests on the common path.
@@ -234,10 +230,10 @@ __device__ __forceinline__ bool no_conversion(float w, float p2, float c_s, floa
 
 // Absorption: P_abs <= tau; x/(1-e^-x) <= 1 + x bounds the Compton-like
 // factor, (1 - e^-x) <= 1 the Bose-Einstein one.
-__device__ __forceinline__ bool no_absorption(const float* rec, const StepArgs& A, int mask, float x, float u) {
+__device__ __forceinline__ bool no_absorption(float r_bc, float r_bb, const StepArgs& A, int mask, float x, float u) {
   float tb = 0.f;
-  if (mask & AXPIC_CH_COMPTON) tb += rec[R_BC] * x * (1.0f + x);
-  if (mask & AXPIC_CH_BREMS) tb += rec[R_BB] * __expf(A.brems_am3 * __logf(x));
+  if (mask & AXPIC_CH_COMPTON) tb += r_bc * x * (1.0f + x);
+  if (mask & AXPIC_CH_BREMS) tb += r_bb * __expf(A.brems_am3 * __logf(x));
   return u >= tb * 1.001f + 1e-6f;
 }
 
@@ -330,274 +326,169 @@ __device__ __forceinline__ void flag_quad(uint32_t* bits, int W, int cell, int q
   if (nib) atomicOr(bits + (size_t)cell * W + ((4 * q) >> 5), nib << ((4 * q) & 31));
 }
 
-// Decision CTAs take A.dec_cells consecutive cells and give their quads to
-// threads in one flat range (thread per quad, cell-major), so uneven counts
-// still fill the warps. Slots that the guards cannot clear go to a CTA-wide
-// list in shared memory, and their full decisions are taken with the
-// list spread over all threads: the out-of-line chain then runs with full
-// warps instead of a few lanes of every warp. List order does not matter:
-// records are indexed by slot.
+// A persistent grid of warps. Warp i owns the chunks i, i + nwarps, ... of
+// kChunk consecutive cells and, per chunk and species, gives the chunk's quads
+// to its lanes as one flat range (lane per quad, cell-major), so uneven counts
+// still fill the lanes. Slots that the guards cannot clear go to the warp's
+// own list in shared memory, which carries over from chunk to chunk and is
+// decided 32 at a time: the out-of-line chain runs with full lanes and no CTA
+// barrier is needed. List order does not matter: records are indexed by slot.
 constexpr int kDecThreads = 256;
-static_assert(AXPIC_DEC_CELLS >= 1 && AXPIC_DEC_CELLS <= kDecMaxCells, "cells per decision CTA");
-constexpr int kDecListCap = 5 * kDecThreads;  // one pass of flags (4 per thread) + a partial batch
+constexpr int kDecWarps = kDecThreads / 32;
+constexpr int kChunk = AXPIC_DEC_CHUNK;
+static_assert(kChunk >= 1 && kChunk <= 32, "cells per decision chunk");
+constexpr int kListCap = 32 + 4 * 32;  // < 32 pending + one pass of flags
 
-struct DecideSmem {
-  int qoff[kDecMaxCells + 1];  // prefix of the cells' quad counts
-  int n[kDecMaxCells];         // slots to decide per cell
-  float c0[kDecMaxCells], c1[kDecMaxCells], c2[kDecMaxCells], c3[kDecMaxCells], c4[kDecMaxCells];  // per cell
-  int count;
-  uint32_t item[kDecListCap];  // (cell in CTA << 16) | slot
-  uint2 u[kDecListCap];        // the slot's decision words
+// Per-warp lists: {cell, slot, decision word(s)}.
+struct DecLists {
+  uint4 a[kDecWarps][kListCap];
+  uint4 g[kDecWarps][kListCap];
 };
 
-// Quad counts of this CTA's cells, from the per-cell slot counts n (set by
-// lanes < ncell of warp 0 before the call).
-__device__ __forceinline__ void dec_prefix(DecideSmem& S, int ncell, int n) {
-  if (threadIdx.x < 32) {
-    const int nq = threadIdx.x < ncell ? (n + 3) >> 2 : 0;
-    int tot;
-    const int off = warp_excl_scan(nq, &tot);
-    if (threadIdx.x < ncell) {
-      S.qoff[threadIdx.x] = off;
-      S.n[threadIdx.x] = n;
-    }
-    if (threadIdx.x == 0) {
-      S.qoff[ncell] = tot;
-      S.count = 0;
-    }
-  }
-  __syncthreads();
+// Flat quad range of a chunk: lanes < nc hold their cell's slot count n; on
+// return every lane holds its cell's first quad (qoff), the starts of cells
+// 1..kChunk-1 (qo, cells beyond nc start at the total) and the total.
+struct QuadRange {
+  int qoff, total;
+  int qo[kChunk];
+};
+
+__device__ __forceinline__ QuadRange quad_range(int n, int lane, int nc) {
+  QuadRange R;
+  const int nq = lane < nc ? (n + 3) >> 2 : 0;
+  R.qoff = warp_excl_scan(nq, &R.total);
+#pragma unroll
+  for (int c = 0; c < kChunk; ++c) R.qo[c] = __shfl_sync(kFull, R.qoff, c);
+#pragma unroll
+  for (int c = 0; c < kChunk; ++c)
+    if (c >= nc) R.qo[c] = R.total;
+  return R;
 }
 
-// Cell in CTA of flat quad g (g < qoff[ncell]).
-__device__ __forceinline__ int dec_cell_of(const DecideSmem& S, int ncell, int g) {
+// Cell (in the chunk) of flat quad g.
+__device__ __forceinline__ int quad_cell(const QuadRange& R, int g) {
   int lc = 0;
-  while (lc + 1 < ncell && S.qoff[lc + 1] <= g) ++lc;
+#pragma unroll
+  for (int c = 1; c < kChunk; ++c) lc += g >= R.qo[c] ? 1 : 0;
   return lc;
 }
 
-// Appends the flagged slots of this thread's quad (bits of nib; words w0/w1
-// rotate with the slot) to the CTA list with one shared atomic per warp.
-__device__ __forceinline__ void dec_append(DecideSmem& S, int lc, int slot0, uint32_t nib, uint4 w0, uint4 w1) {
-  const int cnt = __popc(nib);
+// Appends this lane's flagged slots (bits of nib; words w0/w1 rotate with the
+// slot) to a warp list of current length pend; returns the new length.
+__device__ __forceinline__ int list_append(uint4* L, int pend, int cell, int slot0, uint32_t nib, uint4 w0, uint4 w1) {
   int tot;
-  const int off = warp_excl_scan(cnt, &tot);
-  int base = 0;
-  if (lane_id() == 0 && tot) base = atomicAdd(&S.count, tot);
-  base = __shfl_sync(kFull, base, 0) + off;
+  int o = pend + warp_excl_scan(__popc(nib), &tot);
 #pragma unroll
-  for (int j = 0; j < 4; ++j, rot(w0), rot(w1)) {
-    if ((nib >> j) & 1u) {
-      S.item[base] = ((uint32_t)lc << 16) | (uint32_t)(slot0 + j);
-      S.u[base] = make_uint2(w0.x, w1.x);
-      ++base;
-    }
-  }
+  for (int j = 0; j < 4; ++j)
+    if ((nib >> j) & 1u) L[o++] = make_uint4((uint32_t)cell, (uint32_t)(slot0 + j), word(w0, j), word(w1, j));
+  __syncwarp();
+  return pend + tot;
 }
 
-// Runs f(item, words) for every listed slot: full batches of kDecThreads
-// after each pass over the quads (drain == true), the rest at the end.
-template <class F>
-__device__ __forceinline__ void dec_drain(DecideSmem& S, bool final_pass, F f) {
-  __syncthreads();
-  int cnt = S.count;
-  if (final_pass) {
-    if ((int)threadIdx.x < cnt) f(S.item[threadIdx.x], S.u[threadIdx.x]);
-    return;
-  }
-  while (cnt >= kDecThreads) {
-    cnt -= kDecThreads;
-    f(S.item[cnt + threadIdx.x], S.u[cnt + threadIdx.x]);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) S.count = cnt;
-  __syncthreads();
+__device__ __forceinline__ void axion_full(const StepArgs& A, uint4 it) {
+  const int cell = (int)it.x;
+  const long idx = (long)cell * A.a.cap + it.y;
+  const AxionDecision d =
+      axion_decide_slow(A, cell, A.mask, A.a.w[idx], A.a.px[idx], A.a.py[idx], A.a.pz[idx], it.z, it.w);
+  uint32_t f = (uint32_t)d.K;
+  if (d.keep) f |= DF_KEEP;
+  if (d.absorbed) f |= DF_ABSORBED;
+  if (d.abs_c) f |= DF_ABS_C;
+  if (d.capped) f |= DF_CAPPED;
+  if (d.over) f |= DF_OVER;
+  A.recA[idx] = make_uint4(f, __float_as_uint(d.wprod), __float_as_uint(d.wnew), 0u);
 }
 
-// Axions present at the start of the step: a->gamma and absorption.
-__global__ void __launch_bounds__(kDecThreads) axion_decide_kernel(StepArgs A) {
-  __shared__ DecideSmem S;
-  const int cfirst = blockIdx.x * A.dec_cells;
-  const int ncell = min(A.dec_cells, A.ncells - cfirst);
-  const int mask = A.mask;
-  const bool prim = mask & AXPIC_CH_PRIMAKOFF;
-  const bool bath = mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS);
-  const bool all = A.absorb_mode == 1 && bath;  // weight reduction changes every axion
-  if (threadIdx.x < ncell) {
-    const int c = cfirst + threadIdx.x;
-    const float* rec = A.rec + (size_t)c * kRecLen;
-    S.c0[threadIdx.x] = kMeC2f * kMeC2f * __ldg(rec + R_FOURK2);
-    S.c1[threadIdx.x] = __ldg(rec + R_APINV);
-    S.c2[threadIdx.x] = __ldg(rec + R_INVT);
-  }
-  dec_prefix(S, ncell, threadIdx.x < ncell ? min(max(A.a.count[cfirst + threadIdx.x], 0), A.a.cap) : 0);
-  const int nq = S.qoff[ncell];
-  auto full = [&](uint32_t it, uint2 uu) {
-    const int cell = cfirst + (int)(it >> 16);
-    const long idx = (long)cell * A.a.cap + (it & 0xFFFFu);
-    const AxionDecision d =
-        axion_decide_slow(A, cell, mask, A.a.w[idx], A.a.px[idx], A.a.py[idx], A.a.pz[idx], uu.x, uu.y);
-    uint32_t f = (uint32_t)d.K;
-    if (d.keep) f |= DF_KEEP;
-    if (d.absorbed) f |= DF_ABSORBED;
-    if (d.abs_c) f |= DF_ABS_C;
-    if (d.capped) f |= DF_CAPPED;
-    if (d.over) f |= DF_OVER;
-    A.recA[idx] = make_uint4(f, __float_as_uint(d.wprod), __float_as_uint(d.wnew), 0u);
-  };
-  for (int g0 = 0; g0 < nq; g0 += kDecThreads) {
-    const int g = g0 + threadIdx.x;
-    uint32_t nib = 0;
-    int lc = 0, q = 0;
-    uint4 rP = make_uint4(0, 0, 0, 0), rA = make_uint4(0, 0, 0, 0);
-    if (g < nq) {
-      lc = dec_cell_of(S, ncell, g);
-      q = g - S.qoff[lc];
-      const int cell = cfirst + lc;
-      const int nj = min(4, S.n[lc] - 4 * q);
-      const float* rec = A.rec + (size_t)cell * kRecLen;
-      const float c_s = S.c0[lc], apinv = S.c1[lc], invT = S.c2[lc];
-      const uint32_t gcell = A.cell_base + (uint32_t)cell;
-      const long b = (long)cell * A.a.cap + 4 * q;
-      float4 w4 = ld4(A.a.w + b), x4 = ld4(A.a.px + b), y4 = ld4(A.a.py + b), z4 = ld4(A.a.pz + b);
-      if (prim) rP = philox4x32_10(make_uint4(A.step, gcell, (uint32_t)q, S_PRIM_INV << 24), A.key0, A.key1);
-      if (bath) rA = philox4x32_10(make_uint4(A.step, gcell, (uint32_t)q, S_ABSORB << 24), A.key0, A.key1);
-      uint4 tP = rP, tA = rA;
-#pragma unroll
-      for (int j = 0; j < 4; ++j, rot(w4), rot(x4), rot(y4), rot(z4), rot(tP), rot(tA)) {
-        if (j >= nj) break;
-        const float p2 = x4.x * x4.x + y4.x * y4.x + z4.x * z4.x;
-        bool fast = !all;
-        if (fast && prim) fast = no_conversion(w4.x, p2, c_s, apinv, A.inv_w_gref, u23(tP.x), A.lam_cap);
-        if (fast && bath) fast = no_absorption(rec, A, mask, sqrtf(p2) * kMeC2f * invT, u23(tA.x));
-        if (!fast) nib |= 1u << j;
-      }
-      flag_quad(A.bitsA, A.Wa, cell, q, nib);
-    }
-    dec_append(S, lc, 4 * q, nib, rP, rA);
-    dec_drain(S, false, full);
-  }
-  dec_drain(S, true, full);
+__device__ __forceinline__ void photon_full(const StepArgs& A, uint4 it) {
+  const int cell = (int)it.x;
+  const long idx = (long)cell * A.g.cap + it.y;
+  const PhotonDecision d = photon_decide_slow(A, cell, A.g.w[idx], A.g.px[idx], A.g.py[idx], A.g.pz[idx], it.z);
+  uint32_t f = (uint32_t)d.K;
+  if (d.wrem > 0.f) f |= DF_KEEP;
+  if (d.capped) f |= DF_CAPPED;
+  if (d.over) f |= DF_OVER;
+  A.recG[idx] = make_uint4(f, __float_as_uint(d.wprod), __float_as_uint(d.wrem), 0u);
 }
 
-// Photons present at the start of the step (gamma->a): y == 0 of the grid.
-__device__ __forceinline__ void photon_decide_cta(const StepArgs& A, DecideSmem& S, int cfirst, int ncell) {
-  if (threadIdx.x < ncell) {
-    const int c = cfirst + threadIdx.x;
-    const float* rec = A.rec + (size_t)c * kRecLen;
-    S.c0[threadIdx.x] = kMeC2f * kMeC2f * __ldg(rec + R_FOURK2);
-    S.c1[threadIdx.x] = __ldg(rec + R_AP);
+// Decides full batches of 32 from the top of a list; returns what is left.
+template <bool AX>
+__device__ __forceinline__ int list_drain(const StepArgs& A, const uint4* L, int pend, int lane) {
+  while (pend >= 32) {
+    pend -= 32;
+    const uint4 it = L[pend + lane];
+    if (AX) axion_full(A, it);
+    else photon_full(A, it);
   }
-  int n = 0;
-  if (threadIdx.x < ncell) {
-    const int c = cfirst + threadIdx.x;
-    const int cnt = min(max(A.g.count[c], 0), A.g.cap);
-    n = A.use_snapshot ? min(A.photon_start[c], cnt) : cnt;
-  }
-  dec_prefix(S, ncell, n);
-  const int nq = S.qoff[ncell];
-  auto full = [&](uint32_t it, uint2 uu) {
-    const int cell = cfirst + (int)(it >> 16);
-    const long idx = (long)cell * A.g.cap + (it & 0xFFFFu);
-    const PhotonDecision d = photon_decide_slow(A, cell, A.g.w[idx], A.g.px[idx], A.g.py[idx], A.g.pz[idx], uu.x);
-    uint32_t f = (uint32_t)d.K;
-    if (d.wrem > 0.f) f |= DF_KEEP;
-    if (d.capped) f |= DF_CAPPED;
-    if (d.over) f |= DF_OVER;
-    A.recG[idx] = make_uint4(f, __float_as_uint(d.wprod), __float_as_uint(d.wrem), 0u);
-  };
-  for (int g0 = 0; g0 < nq; g0 += kDecThreads) {
-    const int g = g0 + threadIdx.x;
-    uint32_t nib = 0;
-    int lc = 0, q = 0;
-    uint4 r = make_uint4(0, 0, 0, 0);
-    if (g < nq) {
-      lc = dec_cell_of(S, ncell, g);
-      q = g - S.qoff[lc];
-      const int cell = cfirst + lc;
-      const int nj = min(4, S.n[lc] - 4 * q);
-      const float c_s = S.c0[lc], ap = S.c1[lc];
-      const long b = (long)cell * A.g.cap + 4 * q;
-      float4 w4 = ld4(A.g.w + b), x4 = ld4(A.g.px + b), y4 = ld4(A.g.py + b), z4 = ld4(A.g.pz + b);
-      r = philox4x32_10(make_uint4(A.step, A.cell_base + (uint32_t)cell, (uint32_t)q, S_PRIM_FWD << 24), A.key0,
-                        A.key1);
-      uint4 t = r;
-#pragma unroll
-      for (int j = 0; j < 4; ++j, rot(w4), rot(x4), rot(y4), rot(z4), rot(t)) {
-        if (j >= nj) break;
-        const float p2 = x4.x * x4.x + y4.x * y4.x + z4.x * z4.x;
-        if (!no_conversion(w4.x, p2, c_s, ap, A.inv_w_a, u23(t.x), A.lam_cap)) nib |= 1u << j;
-      }
-      flag_quad(A.bitsG, A.Wg, cell, q, nib);
-    }
-    dec_append(S, lc, 4 * q, nib, r, r);
-    dec_drain(S, false, full);
-  }
-  dec_drain(S, true, full);
+  __syncwarp();
+  return pend;
 }
 
-// Electrons (thermal-bath emission): y == 1 of the grid. Their full
-// decision is a short Poisson inversion, taken in place.
-__device__ __forceinline__ void electron_decide_cta(const StepArgs& A, DecideSmem& S, int cfirst, int ncell) {
+// Electrons of a chunk (thermal-bath emission). With a common weight the
+// decision is u > exp(-lambda) with lambda shared by the cell; the full
+// decision of a flagged electron is a short Poisson inversion, taken here.
+__device__ __forceinline__ void electron_chunk(const StepArgs& A, int c0, int nc, int lane) {
   const int mask = A.mask;
   const bool eC = mask & AXPIC_CH_COMPTON, eB = mask & AXPIC_CH_BREMS;
-  if (threadIdx.x < ncell) {
-    const int c = cfirst + threadIdx.x;
+  int n = 0, thr = 0;
+  float wu = 0.f, lsum = 0.f, rcc = 0.f, rcb = 0.f;
+  if (lane < nc) {
+    const int c = c0 + lane;
     const float* rec = A.rec + (size_t)c * kRecLen;
-    const float rcc = __ldg(rec + R_CC), rcb = __ldg(rec + R_CB);
-    const float wu = __ldg(A.mom + (size_t)c * kMomLen + M_WU);
-    S.c0[threadIdx.x] = rcc;
-    S.c1[threadIdx.x] = rcb;
-    S.c2[threadIdx.x] = wu;
-    float lsum = 0.f, F0 = 0.f;
+    n = min(max(A.e.count[c], 0), A.e.cap);
+    rcc = __ldg(rec + R_CC);
+    rcb = __ldg(rec + R_CB);
+    wu = __ldg(A.mom + (size_t)c * kMomLen + M_WU);
     if (wu > 0.f) {
-      // common weight: K > 0 exactly when u > exp(-lambda), lambda shared
       float fac;
       bool cc = false, cb = false;
       const float lc = eC ? cap_lambda(wu * rcc, A.lam_cap, &fac, &cc) : 0.f;
       const float lb = eB ? cap_lambda(wu * rcb, A.lam_cap, &fac, &cb) : 0.f;
       lsum = lc + lb;
-      F0 = expf(-lsum);
+      // u23(w) > F0 exactly when (w >> 9) > floor(F0 2^23 - 1/2): the
+      // scaling and the subtraction are exact in binary32
+      thr = (int)floorf(__fsub_rn(__fmul_rn(expf(-lsum), 8388608.0f), 0.5f));
     }
-    S.c3[threadIdx.x] = F0;
-    S.c4[threadIdx.x] = lsum;
   }
-  dec_prefix(S, ncell, threadIdx.x < ncell ? min(max(A.e.count[cfirst + threadIdx.x], 0), A.e.cap) : 0);
-  const int nq = S.qoff[ncell];
-  for (int g = threadIdx.x; g < nq; g += kDecThreads) {
-    const int lc = dec_cell_of(S, ncell, g);
-    const int q = g - S.qoff[lc];
-    const int cell = cfirst + lc;
-    const int nj = min(4, S.n[lc] - 4 * q);
-    uint4 r = philox4x32_10(make_uint4(A.step, A.cell_base + (uint32_t)cell, (uint32_t)q, S_EMIT_E << 24), A.key0,
-                            A.key1);
+  const QuadRange R = quad_range(n, lane, nc);
+  for (int g0 = 0; g0 < R.total; g0 += 32) {
+    const int g = g0 + lane;
+    const int lc = quad_cell(R, g);
+    const int qb = __shfl_sync(kFull, R.qoff, lc);
+    const int nn = __shfl_sync(kFull, n, lc);
+    const float cwu = __shfl_sync(kFull, wu, lc);
+    const int cthr = __shfl_sync(kFull, thr, lc);
+    const float cls = __shfl_sync(kFull, lsum, lc);
+    const float ccc = __shfl_sync(kFull, rcc, lc);
+    const float ccb = __shfl_sync(kFull, rcb, lc);
+    if (g >= R.total) continue;
+    const int cell = c0 + lc;
+    const int q = g - qb;
+    const int nj = min(4, nn - 4 * q);
+    const uint4 r = philox4x32_10(make_uint4(A.step, A.cell_base + (uint32_t)cell, (uint32_t)q, S_EMIT_E << 24), A.rk);
     const long b = (long)cell * A.e.cap + 4 * q;
     uint32_t nib = 0;
-    if (S.c2[lc] > 0.f) {
-      const float F0 = S.c3[lc], lsum = S.c4[lc];
+    if (cwu > 0.f) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j, rot(r)) {
-        if (j >= nj) break;
-        const float u = u23(r.x);
-        if (u > F0) {
-          A.recE[b + j] = (uint32_t)poisson_inv(u, lsum);
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t wj = word(r, j);
+        if (j < nj && (int)(wj >> 9) > cthr) {
+          A.recE[b + j] = (uint32_t)poisson_inv(u23(wj), cls);
           nib |= 1u << j;
         }
       }
     } else {
-      const float rcc = S.c0[lc], rcb = S.c1[lc];
-      float4 w4 = ld4(A.e.w + b);
-      const float rsum = ((eC ? rcc : 0.f) + (eB ? rcb : 0.f)) * 1.0001f;
+      const float4 w4 = ld4(A.e.w + b);
+      const float rsum = ((eC ? ccc : 0.f) + (eB ? ccb : 0.f)) * 1.0001f;
 #pragma unroll
-      for (int j = 0; j < 4; ++j, rot(w4), rot(r)) {
-        if (j >= nj) break;
-        const float lbnd = w4.x * rsum;
-        if (!(lbnd < A.lam_cap && u23(r.x) <= 1.0f - lbnd - 1e-6f)) {
+      for (int j = 0; j < 4; ++j) {
+        const float wj = f4(w4, j);
+        const float lbnd = wj * rsum;
+        if (j < nj && !(lbnd < A.lam_cap && u23(word(r, j)) <= 1.0f - lbnd - 1e-6f)) {
           float fac;
           bool cc = false, cb = false;
-          const float lc2 = eC ? cap_lambda(w4.x * rcc, A.lam_cap, &fac, &cc) : 0.f;
-          const float lb2 = eB ? cap_lambda(w4.x * rcb, A.lam_cap, &fac, &cb) : 0.f;
-          uint32_t f = (uint32_t)poisson_inv(u23(r.x), lc2 + lb2);
+          const float l1 = eC ? cap_lambda(wj * ccc, A.lam_cap, &fac, &cc) : 0.f;
+          const float l2 = eB ? cap_lambda(wj * ccb, A.lam_cap, &fac, &cb) : 0.f;
+          uint32_t f = (uint32_t)poisson_inv(u23(word(r, j)), l1 + l2);
           if (cc) f |= DF_CAPPED;
           if (cb) f |= DF_CAPPED_B;
           A.recE[b + j] = f;
@@ -609,31 +500,164 @@ __device__ __forceinline__ void electron_decide_cta(const StepArgs& A, DecideSme
   }
 }
 
-__global__ void __launch_bounds__(kDecThreads) emit_decide_kernel(StepArgs A) {
-  __shared__ DecideSmem S;
-  const int cfirst = blockIdx.x * A.dec_cells;
-  const int ncell = min(A.dec_cells, A.ncells - cfirst);
-  if (blockIdx.y == 0) {
-    if (A.mask & AXPIC_CH_PRIMAKOFF) photon_decide_cta(A, S, cfirst, ncell);
-  } else if (A.mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS)) {
-    electron_decide_cta(A, S, cfirst, ncell);
+// Photons of a chunk present at the start of the step (gamma->a).
+__device__ __forceinline__ int photon_chunk(const StepArgs& A, int c0, int nc, int lane, uint4* L, int pend) {
+  int n = 0;
+  float c_s = 0.f, ap = 0.f;
+  if (lane < nc) {
+    const int c = c0 + lane;
+    const float* rec = A.rec + (size_t)c * kRecLen;
+    const int cnt = min(max(A.g.count[c], 0), A.g.cap);
+    n = A.use_snapshot ? min(A.photon_start[c], cnt) : cnt;
+    c_s = kMeC2f * kMeC2f * __ldg(rec + R_FOURK2);
+    ap = __ldg(rec + R_AP);
   }
+  const QuadRange R = quad_range(n, lane, nc);
+  for (int g0 = 0; g0 < R.total; g0 += 32) {
+    const int g = g0 + lane;
+    const int lc = quad_cell(R, g);
+    const int qb = __shfl_sync(kFull, R.qoff, lc);
+    const int nn = __shfl_sync(kFull, n, lc);
+    const float cs = __shfl_sync(kFull, c_s, lc);
+    const float ca = __shfl_sync(kFull, ap, lc);
+    const int cell = c0 + lc;
+    const int q = g - qb;
+    uint32_t nib = 0;
+    uint4 r = make_uint4(0, 0, 0, 0);
+    if (g < R.total) {
+      const int nj = min(4, nn - 4 * q);
+      const long b = (long)cell * A.g.cap + 4 * q;
+      const float4 w4 = ld4(A.g.w + b), x4 = ld4(A.g.px + b), y4 = ld4(A.g.py + b), z4 = ld4(A.g.pz + b);
+      r = philox4x32_10(make_uint4(A.step, A.cell_base + (uint32_t)cell, (uint32_t)q, S_PRIM_FWD << 24), A.rk);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float px = f4(x4, j), py = f4(y4, j), pz = f4(z4, j);
+        const float p2 = px * px + py * py + pz * pz;
+        if (j < nj && !no_conversion(f4(w4, j), p2, cs, ca, A.inv_w_a, u23(word(r, j)), A.lam_cap)) nib |= 1u << j;
+      }
+      flag_quad(A.bitsG, A.Wg, cell, q, nib);
+    }
+    pend = list_append(L, pend, cell, 4 * q, nib, r, r);
+    pend = list_drain<false>(A, L, pend, lane);
+  }
+  return pend;
+}
+
+// Axions of a chunk present at the start of the step: a->gamma and absorption.
+__device__ __forceinline__ int axion_chunk(const StepArgs& A, int c0, int nc, int lane, uint4* L, int pend) {
+  const int mask = A.mask;
+  const bool prim = mask & AXPIC_CH_PRIMAKOFF;
+  const bool bath = mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS);
+  const bool all = A.absorb_mode == 1 && bath;  // weight reduction changes every axion
+  int n = 0;
+  float c_s = 0.f, apinv = 0.f, invT = 0.f, r_bc = 0.f, r_bb = 0.f;
+  if (lane < nc) {
+    const int c = c0 + lane;
+    const float* rec = A.rec + (size_t)c * kRecLen;
+    n = min(max(A.a.count[c], 0), A.a.cap);
+    c_s = kMeC2f * kMeC2f * __ldg(rec + R_FOURK2);
+    apinv = __ldg(rec + R_APINV);
+    invT = __ldg(rec + R_INVT);
+    r_bc = __ldg(rec + R_BC);
+    r_bb = __ldg(rec + R_BB);
+  }
+  const QuadRange R = quad_range(n, lane, nc);
+  for (int g0 = 0; g0 < R.total; g0 += 32) {
+    const int g = g0 + lane;
+    const int lc = quad_cell(R, g);
+    const int qb = __shfl_sync(kFull, R.qoff, lc);
+    const int nn = __shfl_sync(kFull, n, lc);
+    const float cs = __shfl_sync(kFull, c_s, lc);
+    const float cap_inv = __shfl_sync(kFull, apinv, lc);
+    const float cinvT = __shfl_sync(kFull, invT, lc);
+    const float cbc = __shfl_sync(kFull, r_bc, lc);
+    const float cbb = __shfl_sync(kFull, r_bb, lc);
+    const int cell = c0 + lc;
+    const int q = g - qb;
+    uint32_t nib = 0;
+    uint4 rP = make_uint4(0, 0, 0, 0), rA = make_uint4(0, 0, 0, 0);
+    if (g < R.total) {
+      const int nj = min(4, nn - 4 * q);
+      const uint32_t gcell = A.cell_base + (uint32_t)cell;
+      const long b = (long)cell * A.a.cap + 4 * q;
+      const float4 w4 = ld4(A.a.w + b), x4 = ld4(A.a.px + b), y4 = ld4(A.a.py + b), z4 = ld4(A.a.pz + b);
+      if (prim) rP = philox4x32_10(make_uint4(A.step, gcell, (uint32_t)q, S_PRIM_INV << 24), A.rk);
+      if (bath) rA = philox4x32_10(make_uint4(A.step, gcell, (uint32_t)q, S_ABSORB << 24), A.rk);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float px = f4(x4, j), py = f4(y4, j), pz = f4(z4, j);
+        const float p2 = px * px + py * py + pz * pz;
+        bool fast = !all;
+        if (fast && prim) fast = no_conversion(f4(w4, j), p2, cs, cap_inv, A.inv_w_gref, u23(word(rP, j)), A.lam_cap);
+        if (fast && bath) fast = no_absorption(cbc, cbb, A, mask, sqrtf(p2) * kMeC2f * cinvT, u23(word(rA, j)));
+        if (j < nj && !fast) nib |= 1u << j;
+      }
+      flag_quad(A.bitsA, A.Wa, cell, q, nib);
+    }
+    pend = list_append(L, pend, cell, 4 * q, nib, rP, rA);
+    pend = list_drain<true>(A, L, pend, lane);
+  }
+  return pend;
+}
+
+// All decisions of a call in one launch. The photon decisions read the
+// photons present at the start of the step: the absorb phase appends a->gamma
+// products only in the event kernel.
+enum : int { DK_ELECTRON = 1, DK_PHOTON = 2, DK_AXION = 4 };
+
+#ifndef AXPIC_DEC_MIN_CTAS
+#define AXPIC_DEC_MIN_CTAS 4
+#endif
+
+__global__ void __launch_bounds__(kDecThreads, AXPIC_DEC_MIN_CTAS) decide_kernel(StepArgs A, int kinds) {
+  __shared__ DecLists L;
+  const int lane = lane_id(), wid = threadIdx.x >> 5;
+  const int nwarps = gridDim.x * kDecWarps;
+  const int nchunks = (A.ncells + kChunk - 1) / kChunk;
+  int pa = 0, pg = 0;
+  for (int ch = blockIdx.x * kDecWarps + wid; ch < nchunks; ch += nwarps) {
+    const int c0 = ch * kChunk;
+    const int nc = min(kChunk, A.ncells - c0);
+    if (kinds & DK_ELECTRON) electron_chunk(A, c0, nc, lane);
+    if (kinds & DK_PHOTON) pg = photon_chunk(A, c0, nc, lane, L.g[wid], pg);
+    if (kinds & DK_AXION) pa = axion_chunk(A, c0, nc, lane, L.a[wid], pa);
+  }
+  if (lane < pg) photon_full(A, L.g[wid][lane]);
+  if (lane < pa) axion_full(A, L.a[wid][lane]);
 }
 
 // ---------------------------------------------------------------- event kernel
 // Per-warp shared scratch: ascending lists of flagged slots and of removed
 // slots (u16), and removed-slot bit masks.
+// Flagged items staged in shared memory by asynchronous copies (no register
+// holds a load in flight): the first 32 flagged axions and photons of a cell,
+// and the first 32 tail positions of each species' tail fill.
+struct Fields7 {
+  float w[32], px[32], py[32], pz[32], x[32], y[32], z[32];
+};
+struct EvStage {
+  uint4 ar[32];
+  Fields7 a;  // flagged axions; then the axion tail-fill movers
+  uint4 gr[32];
+  Fields7 g;   // flagged photons (w unused)
+  Fields7 mg;  // photon tail-fill movers
+};
+
+// Per-warp scratch: flagged-slot lists (the removed lists reuse them: a
+// chunk's entries are read before removed entries at or below their index
+// are written), removed-slot bits and the stage.
 struct EvScratch {
   uint16_t *flA, *flG, *flE, *rmA, *rmG;
   uint32_t *rbA, *rbG;
+  EvStage* st;
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
 __host__ __device__ inline size_t ev_scratch_bytes(int acap, int gcap, int ecap) {
-  size_t b = 2 * (2 * (size_t)acap + 2 * (size_t)gcap + (size_t)ecap);
-  b = align16(b) + 4 * (size_t)((acap + 31) / 32 + (gcap + 31) / 32);
-  return align16(b);
+  size_t b = align16(2 * ((size_t)acap + (size_t)gcap + (size_t)ecap));
+  b = align16(b + 4 * (size_t)((acap + 31) / 32 + (gcap + 31) / 32));
+  return b + sizeof(EvStage);
 }
 
 __device__ inline EvScratch ev_carve(unsigned char* base, int acap, int gcap, int ecap) {
@@ -642,12 +666,27 @@ __device__ inline EvScratch ev_carve(unsigned char* base, int acap, int gcap, in
   s.flA = h; h += acap;
   s.flG = h; h += gcap;
   s.flE = h; h += ecap;
-  s.rmA = h; h += acap;
-  s.rmG = h; h += gcap;
-  uint32_t* u = reinterpret_cast<uint32_t*>(align16(reinterpret_cast<size_t>(h)));
+  s.rmA = s.flA;
+  s.rmG = s.flG;
+  uint32_t* u = reinterpret_cast<uint32_t*>(base + align16(2 * ((size_t)acap + gcap + ecap)));
   s.rbA = u; u += (acap + 31) / 32;
   s.rbG = u;
+  s.st = reinterpret_cast<EvStage*>(base + align16(align16(2 * ((size_t)acap + gcap + ecap)) +
+                                                   4 * (size_t)((acap + 31) / 32 + (gcap + 31) / 32)));
   return s;
+}
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+// Waits for this thread's copies; the warp then synchronises to see all.
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 // Turns one bit-mask word per lane (words [w0, w0 + 32) of a row covering
@@ -681,14 +720,44 @@ __device__ __noinline__ int gather_flags(uint32_t* bits, int W, int cell, int n,
 }
 
 // Tail fill with the ascending removed list: holes are the removed slots
-// below n_surv, movers the kept slots at or beyond it, matched in order.
-__device__ __noinline__ void compact_removed(const SpeciesPtrs& s, long base, const uint16_t* rm, int nrm,
-                                             const uint32_t* rb, int n) {
+// below n_surv, movers the kept slots at or beyond it, matched in order. The
+// movers of the first 32 positions of the tail [n_surv, n) are staged by
+// mover_stage (so that their copies are in flight with other work) and
+// written by mover_commit; compact_rest moves the positions from n_surv + 32
+// on.
+// Stages the movers of the first 32 tail positions; *dst is the slot this
+// lane's mover fills (or -1). Returns the number of movers staged.
+__device__ __forceinline__ int mover_stage(const SpeciesPtrs& s, long base, const uint16_t* rm, const uint32_t* rb,
+                                           int n_surv, int n, Fields7& F, int* dst) {
+  const int lane = lane_id();
+  const int i = n_surv + lane;
+  const bool mv = i < n && !bit(rb, i);
+  const unsigned msk = __ballot_sync(kFull, mv);
+  *dst = -1;
+  if (mv) {
+    const long src = base + i;
+    *dst = rm[__popc(msk & ((1u << lane) - 1u))];
+    cp_async4(&F.w[lane], s.w + src);
+    cp_async4(&F.px[lane], s.px + src);
+    cp_async4(&F.py[lane], s.py + src);
+    cp_async4(&F.pz[lane], s.pz + src);
+    cp_async4(&F.x[lane], s.x + src);
+    cp_async4(&F.y[lane], s.y + src);
+    cp_async4(&F.z[lane], s.z + src);
+  }
+  return __popc(msk);
+}
+
+__device__ __forceinline__ void mover_commit(const SpeciesPtrs& s, long base, const Fields7& F, int dst) {
+  const int lane = lane_id();
+  if (dst >= 0) write_particle(s, base + dst, F.w[lane], F.px[lane], F.py[lane], F.pz[lane], F.x[lane], F.y[lane], F.z[lane]);
+}
+
+__device__ __noinline__ void compact_rest(const SpeciesPtrs& s, long base, const uint16_t* rm, int run,
+                                          const uint32_t* rb, int n_surv, int n) {
   const int lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
-  const int n_surv = n - nrm;
-  int run = 0;
-  for (int b0 = n_surv; b0 < n; b0 += 32) {
+  for (int b0 = n_surv + 32; b0 < n; b0 += 32) {
     const int i = b0 + lane;
     const bool mv = i < n && !bit(rb, i);
     const unsigned m = __ballot_sync(kFull, mv);
@@ -701,130 +770,273 @@ __device__ __noinline__ void compact_removed(const SpeciesPtrs& s, long base, co
   }
 }
 
+// A flagged slot with its decision record and the fields its outcome may
+// need, loaded in one round trip.
+struct AxItem {
+  uint4 r;
+  float w, px, py, pz, x, y, z;
+  int slot;
+};
+struct PhItem {
+  uint4 r;
+  float px, py, pz, x, y, z;
+  int slot;
+};
+struct ElItem {
+  uint32_t f;
+  float w, x, y, z;
+  int slot;
+};
+
+__device__ __forceinline__ AxItem ax_load(const StepArgs& A, long base, const uint16_t* fl, int i, int n) {
+  AxItem t;
+  t.slot = -1;
+  t.r = make_uint4(0, 0, 0, 0);
+  t.w = t.px = t.py = t.pz = t.x = t.y = t.z = 0.f;
+  if (i < n) {
+    t.slot = fl[i];
+    const long src = base + t.slot;
+    t.r = A.recA[src];
+    t.w = A.a.w[src];
+    t.px = A.a.px[src];
+    t.py = A.a.py[src];
+    t.pz = A.a.pz[src];
+    t.x = A.a.x[src];
+    t.y = A.a.y[src];
+    t.z = A.a.z[src];
+  }
+  return t;
+}
+
+__device__ __forceinline__ PhItem ph_load(const StepArgs& A, long base, const uint16_t* fl, int i, int n) {
+  PhItem t;
+  t.slot = -1;
+  t.r = make_uint4(0, 0, 0, 0);
+  t.px = t.py = t.pz = t.x = t.y = t.z = 0.f;
+  if (i < n) {
+    t.slot = fl[i];
+    const long src = base + t.slot;
+    t.r = A.recG[src];
+    t.px = A.g.px[src];
+    t.py = A.g.py[src];
+    t.pz = A.g.pz[src];
+    t.x = A.g.x[src];
+    t.y = A.g.y[src];
+    t.z = A.g.z[src];
+  }
+  return t;
+}
+
+__device__ __forceinline__ AxItem ax_staged(const EvStage& T, const uint16_t* fl, int lane, int n) {
+  AxItem t;
+  t.slot = -1;
+  t.r = make_uint4(0, 0, 0, 0);
+  t.w = t.px = t.py = t.pz = t.x = t.y = t.z = 0.f;
+  if (lane < n) {
+    t.slot = fl[lane];
+    t.r = T.ar[lane];
+    t.w = T.a.w[lane];
+    t.px = T.a.px[lane];
+    t.py = T.a.py[lane];
+    t.pz = T.a.pz[lane];
+    t.x = T.a.x[lane];
+    t.y = T.a.y[lane];
+    t.z = T.a.z[lane];
+  }
+  return t;
+}
+
+__device__ __forceinline__ PhItem ph_staged(const EvStage& T, const uint16_t* fl, int lane, int n) {
+  PhItem t;
+  t.slot = -1;
+  t.r = make_uint4(0, 0, 0, 0);
+  t.px = t.py = t.pz = t.x = t.y = t.z = 0.f;
+  if (lane < n) {
+    t.slot = fl[lane];
+    t.r = T.gr[lane];
+    t.px = T.g.px[lane];
+    t.py = T.g.py[lane];
+    t.pz = T.g.pz[lane];
+    t.x = T.g.x[lane];
+    t.y = T.g.y[lane];
+    t.z = T.g.z[lane];
+  }
+  return t;
+}
+
+__device__ __forceinline__ ElItem el_load(const StepArgs& A, long base, const uint16_t* fl, int i, int n, float wu) {
+  ElItem t;
+  t.slot = -1;
+  t.f = 0u;
+  t.w = wu;
+  t.x = t.y = t.z = 0.f;
+  if (i < n) {
+    t.slot = fl[i];
+    const long src = base + t.slot;
+    t.f = A.recE[src];
+    t.x = A.e.x[src];
+    t.y = A.e.y[src];
+    t.z = A.e.z[src];
+    if (wu <= 0.f) t.w = A.e.w[src];
+  }
+  return t;
+}
+
+// One cell's events, by one warp. Round trips: (1) counts, decision masks,
+// per-cell constants and the exchange buffer; (2) the records and fields of
+// the flagged slots of every species; (3) the tail-fill movers of both
+// species; then the stores. Output order is the method's: photon products of
+// a->gamma after the photons present, axion products of gamma->a after the
+// surviving axions, then the thermal-bath products in electron then event
+// order; removed slots are refilled from the tail.
 template <int PH>
 __device__ __forceinline__ void event_cell(const StepArgs& A, int cell, EvScratch& S, const Cnt& cnt) {
   const int lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t gcell = A.cell_base + (uint32_t)cell;
   const int mask = A.mask;
-  const int ne = min(max(A.e.count[cell], 0), A.e.cap);
-  const int ng_start = min(max(A.g.count[cell], 0), A.g.cap);
-  const int na_start = min(max(A.a.count[cell], 0), A.a.cap);
-  int ng = ng_start;
-  int na = na_start;
-  const long abase = (long)cell * A.a.cap;
-  const long gbase = (long)cell * A.g.cap;
-  const long ebase = (long)cell * A.e.cap;
   const bool prim = mask & AXPIC_CH_PRIMAKOFF;
   const bool bath = mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS);
   const bool eC = mask & AXPIC_CH_COMPTON, eB = mask & AXPIC_CH_BREMS;
-  const int ng0 = (PH & PH_ABSORB) ? ng_start : (A.use_snapshot ? min(A.photon_start[cell], ng) : ng);
+  const bool emitG = (PH & PH_EMIT) && prim;
+  const bool emitE = (PH & PH_EMIT) && (eC || eB);
+  const long abase = (long)cell * A.a.cap;
+  const long gbase = (long)cell * A.g.cap;
+  const long ebase = (long)cell * A.e.cap;
+
+  // ------------------------------------------------------------ round trip 1
+  const int ne = min(max(A.e.count[cell], 0), A.e.cap);
+  const int ng_start = min(max(A.g.count[cell], 0), A.g.cap);
+  const int na_start = min(max(A.a.count[cell], 0), A.a.cap);
+  const int pstart = (!(PH & PH_ABSORB) && A.use_snapshot) ? A.photon_start[cell] : 0;
+  float wu = 0.f, r_cc = 0.f, r_cb = 0.f, r_T = 0.f;
+  if (emitE) {
+    const float* rec = A.rec + (size_t)cell * kRecLen;
+    wu = A.mom[(size_t)cell * kMomLen + M_WU];
+    r_cc = rec[R_CC];
+    r_cb = rec[R_CB];
+    r_T = rec[R_T];
+  }
+  // lanes 0..3 hold one component each of the cell's exchange buffer
+  double* xb = A.xbuf + (size_t)cell * 4;
+  const double xb_old = lane < 4 ? xb[lane] : 0.0;
+  int nflA = 0, nflG = 0, nflE = 0;
+  const int ng0 = (PH & PH_ABSORB) ? ng_start : (A.use_snapshot ? min(pstart, ng_start) : ng_start);
+  {
+    // whole mask rows are loaded without waiting for the counts: bits beyond
+    // a count are never set
+    if (A.Wa <= 32 && A.Wg <= 32 && A.We <= 32) {
+      uint32_t* rA = A.bitsA + (size_t)cell * A.Wa;
+      uint32_t* rG = A.bitsG + (size_t)cell * A.Wg;
+      uint32_t* rE = A.bitsE + (size_t)cell * A.We;
+      const uint32_t vA = (PH & PH_ABSORB) && lane < A.Wa ? rA[lane] : 0u;
+      const uint32_t vG = emitG && lane < A.Wg ? rG[lane] : 0u;
+      const uint32_t vE = emitE && lane < A.We ? rE[lane] : 0u;
+      if (vA) rA[lane] = 0u;
+      if (vG) rG[lane] = 0u;
+      if (vE) rE[lane] = 0u;
+      if (__any_sync(kFull, vA != 0)) nflA = list_flags(vA, lane, (na_start + 31) >> 5, na_start, S.flA, 0);
+      if (__any_sync(kFull, vG != 0)) nflG = list_flags(vG, lane, (ng0 + 31) >> 5, ng0, S.flG, 0);
+      if (__any_sync(kFull, vE != 0)) nflE = list_flags(vE, lane, (ne + 31) >> 5, ne, S.flE, 0);
+    } else {
+      if (PH & PH_ABSORB) nflA = gather_flags(A.bitsA, A.Wa, cell, na_start, S.flA);
+      if (emitG) nflG = gather_flags(A.bitsG, A.Wg, cell, ng0, S.flG);
+      if (emitE) nflE = gather_flags(A.bitsE, A.We, cell, ne, S.flE);
+    }
+    __syncwarp();
+  }
   // particles present at the start of the step: counted by the absorb phase,
   // or by the emit phase when no absorb ran this step
   if (lane == 0 && ((PH & PH_ABSORB) || ((PH & PH_EMIT) && !A.use_snapshot))) {
     cnt.add(C_NE, ne);
     cnt.add(C_NG, ng_start);
-    cnt.add(C_NA, na);
+    cnt.add(C_NA, na_start);
     cnt.add(C_CELLS, 1);
   }
-  // all decision masks of this call are read (and cleared) up front
-  int nflA = 0, nflG = 0, nflE = 0;
-  {
-    const int nwA = (PH & PH_ABSORB) ? (na_start + 31) >> 5 : 0;
-    const int nwG = ((PH & PH_EMIT) && prim) ? (ng0 + 31) >> 5 : 0;
-    const int nwE = ((PH & PH_EMIT) && (eC || eB)) ? (ne + 31) >> 5 : 0;
-    if (nwA <= 32 && nwG <= 32 && nwE <= 32) {
-      uint32_t* rA = A.bitsA + (size_t)cell * A.Wa;
-      uint32_t* rG = A.bitsG + (size_t)cell * A.Wg;
-      uint32_t* rE = A.bitsE + (size_t)cell * A.We;
-      const uint32_t vA = lane < nwA ? rA[lane] : 0u;
-      const uint32_t vG = lane < nwG ? rG[lane] : 0u;
-      const uint32_t vE = lane < nwE ? rE[lane] : 0u;
-      if (vA) rA[lane] = 0u;
-      if (vG) rG[lane] = 0u;
-      if (vE) rE[lane] = 0u;
-      if (__any_sync(kFull, vA != 0)) nflA = list_flags(vA, lane, nwA, na_start, S.flA, 0);
-      if (__any_sync(kFull, vG != 0)) nflG = list_flags(vG, lane, nwG, ng0, S.flG, 0);
-      if (__any_sync(kFull, vE != 0)) nflE = list_flags(vE, lane, nwE, ne, S.flE, 0);
-    } else {
-      if (nwA) nflA = gather_flags(A.bitsA, A.Wa, cell, na_start, S.flA);
-      if (nwG) nflG = gather_flags(A.bitsG, A.Wg, cell, ng0, S.flG);
-      if (nwE) nflE = gather_flags(A.bitsE, A.We, cell, ne, S.flE);
-    }
-    __syncwarp();
+  if ((PH & PH_ABSORB) && lane == 0) A.photon_start[cell] = ng_start;
+
+  // ------------------------------------------------------------ round trip 2
+  // records and fields of the first 32 flagged axions and photons, staged by
+  // asynchronous copies
+  EvStage& T = *S.st;
+  if ((PH & PH_ABSORB) && lane < nflA) {
+    const long src = abase + S.flA[lane];
+    cp_async16(&T.ar[lane], A.recA + src);
+    cp_async4(&T.a.w[lane], A.a.w + src);
+    cp_async4(&T.a.px[lane], A.a.px + src);
+    cp_async4(&T.a.py[lane], A.a.py + src);
+    cp_async4(&T.a.pz[lane], A.a.pz + src);
+    cp_async4(&T.a.x[lane], A.a.x + src);
+    cp_async4(&T.a.y[lane], A.a.y + src);
+    cp_async4(&T.a.z[lane], A.a.z + src);
   }
+  if (emitG && lane < nflG) {
+    const long src = gbase + S.flG[lane];
+    cp_async16(&T.gr[lane], A.recG + src);
+    cp_async4(&T.g.px[lane], A.g.px + src);
+    cp_async4(&T.g.py[lane], A.g.py + src);
+    cp_async4(&T.g.pz[lane], A.g.pz + src);
+    cp_async4(&T.g.x[lane], A.g.x + src);
+    cp_async4(&T.g.y[lane], A.g.y + src);
+    cp_async4(&T.g.z[lane], A.g.z + src);
+  }
+  cp_async_wait_all();
+  __syncwarp();
+
   Lane64 x64;
   double xa[4] = {0.0, 0.0, 0.0, 0.0};
   bool xa_any = false;
+  int ng = ng_start, na = na_start, nrmA = 0;
 
   // ------------------------------------------------------------ absorb
-  if (PH & PH_ABSORB) {
-    if (lane == 0) A.photon_start[cell] = ng;
-    if (nflA > 0) {
-      for (int i = lane; i < (na_start + 31) / 32; i += 32) S.rbA[i] = 0u;
-      __syncwarp();
-      int run = 0, nrm = 0, NPg = 0;
-      for (int i0 = 0; i0 < nflA; i0 += 32) {
-        const int i = i0 + lane;
-        int K = 0, slot = 0;
-        bool removed = false;
-        float wprod = 0.f, px = 0.f, py = 0.f, pz = 0.f, xx = 0.f, yy = 0.f, zz = 0.f;
-        if (i < nflA) {
-          slot = S.flA[i];
-          const long src = abase + slot;
-          const uint4 r = A.recA[src];
-          const float w = A.a.w[src];
-          px = A.a.px[src];
-          py = A.a.py[src];
-          pz = A.a.pz[src];
-          K = r.x & 0xFF;
-          wprod = __uint_as_float(r.y);
-          const float wnew = __uint_as_float(r.z);
-          const float om = sqrtf(px * px + py * py + pz * pz) * kMeC2f;
-          cnt.add(C_CAP, (r.x & DF_CAPPED) ? 1u : 0u);
-          cnt.add(C_CLAMP, (r.x & DF_OVER) ? 1u : 0u);
-          cnt.add(C_EV_PINV, (unsigned)K);
-          if (r.x & DF_ABSORBED) {
-            x64.add((double)wnew, om, px, py, pz);
-            cnt.add((r.x & DF_ABS_C) ? C_ABS_C : C_ABS_B, 1);
-          } else if (A.absorb_mode == 1 && bath) {
-            // weight reduction: the lost weight's energy goes to the plasma
-            float wrem = w;
-            if (K > 0) wrem = (r.x & DF_OVER) ? 0.f : __fsub_rn(w, __fmul_rn((float)K, wprod));
-            x64.add((double)wrem - (double)wnew, om, px, py, pz);
-          }
-          removed = !(r.x & DF_KEEP);
-          if (K) {
-            xx = A.a.x[src];
-            yy = A.a.y[src];
-            zz = A.a.z[src];
-          }
-          if (!removed && wnew != w) A.a.w[src] = wnew;
+  if ((PH & PH_ABSORB) && nflA > 0) {
+    for (int i = lane; i < (na_start + 31) / 32; i += 32) S.rbA[i] = 0u;
+    __syncwarp();
+    int run = 0, NPg = 0;
+    for (int i0 = 0; i0 < nflA; i0 += 32) {
+      const AxItem t = i0 == 0 ? ax_staged(T, S.flA, lane, nflA) : ax_load(A, abase, S.flA, i0 + lane, nflA);
+      int K = 0;
+      bool removed = false;
+      float wprod = 0.f;
+      if (t.slot >= 0) {
+        K = t.r.x & 0xFF;
+        wprod = __uint_as_float(t.r.y);
+        const float wnew = __uint_as_float(t.r.z);
+        const float om = sqrtf(t.px * t.px + t.py * t.py + t.pz * t.pz) * kMeC2f;
+        cnt.add(C_CAP, (t.r.x & DF_CAPPED) ? 1u : 0u);
+        cnt.add(C_CLAMP, (t.r.x & DF_OVER) ? 1u : 0u);
+        cnt.add(C_EV_PINV, (unsigned)K);
+        if (t.r.x & DF_ABSORBED) {
+          x64.add((double)wnew, om, t.px, t.py, t.pz);
+          cnt.add((t.r.x & DF_ABS_C) ? C_ABS_C : C_ABS_B, 1);
+        } else if (A.absorb_mode == 1 && bath) {
+          // weight reduction: the lost weight's energy goes to the plasma
+          float wrem = t.w;
+          if (K > 0) wrem = (t.r.x & DF_OVER) ? 0.f : __fsub_rn(t.w, __fmul_rn((float)K, wprod));
+          x64.add((double)wrem - (double)wnew, om, t.px, t.py, t.pz);
         }
-        // photon products of a->gamma after the photons present
-        int tot;
-        int off = run + warp_excl_scan(K, &tot);
-        for (int k = 0; k < K; ++k, ++off) {
-          const int dst = ng + off;
-          if (dst < A.g.cap) write_particle(A.g, gbase + dst, wprod, px, py, pz, xx, yy, zz);
-          else cnt.add(C_DROP, 1);
-        }
-        run += tot;
-        NPg += K;
-        const unsigned m = __ballot_sync(kFull, removed);
-        if (removed) {
-          S.rmA[nrm + __popc(m & lt)] = (uint16_t)slot;
-          atomicOr(&S.rbA[slot >> 5], 1u << (slot & 31));
-        }
-        nrm += __popc(m);
+        removed = !(t.r.x & DF_KEEP);
+        if (!removed && wnew != t.w) A.a.w[abase + t.slot] = wnew;
       }
-      NPg = warp_sum_i(NPg);
-      ng = min(ng + NPg, A.g.cap);
-      __syncwarp();
-      if (nrm > 0) compact_removed(A.a, abase, S.rmA, nrm, S.rbA, na_start);
-      __syncwarp();
-      na = na_start - nrm;
+      // photon products of a->gamma after the photons present
+      int tot;
+      int off = run + warp_excl_scan(K, &tot);
+      for (int k = 0; k < K; ++k, ++off) {
+        const int dst = ng + off;
+        if (dst < A.g.cap) write_particle(A.g, gbase + dst, wprod, t.px, t.py, t.pz, t.x, t.y, t.z);
+        else cnt.add(C_DROP, 1);
+      }
+      run += tot;
+      NPg += K;
+      const unsigned m = __ballot_sync(kFull, removed);
+      if (removed) {
+        S.rmA[nrmA + __popc(m & lt)] = (uint16_t)t.slot;
+        atomicOr(&S.rbA[t.slot >> 5], 1u << (t.slot & 31));
+      }
+      nrmA += __popc(m);
     }
+    NPg = warp_sum_i(NPg);
+    ng = min(ng + NPg, A.g.cap);
     if (__any_sync(kFull, x64.any)) {
       xa[0] = warp_sum_d(x64.dE);
       xa[1] = warp_sum_d(x64.dPx);
@@ -833,78 +1045,134 @@ __device__ __forceinline__ void event_cell(const StepArgs& A, int cell, EvScratc
       xa_any = true;
     }
     x64 = Lane64();
+    na = na_start - nrmA;
   }
 
-  // ------------------------------------------------------------ emit
-  if (PH & PH_EMIT) {
-    const int ng_tot = ng;
-    const int abase_new = na;
-    int NPa = 0, nrm = 0;
-    // (c) flagged photons; axion products after the surviving axions
-    if (nflG > 0) {
-      for (int i = lane; i < (ng_tot + 31) / 32; i += 32) S.rbG[i] = 0u;
-      __syncwarp();
-      int run = 0;
-      for (int i0 = 0; i0 < nflG; i0 += 32) {
-        const int i = i0 + lane;
-        int K = 0, slot = 0;
-        bool removed = false;
-        float wprod = 0.f, om = 0.f, px = 0.f, py = 0.f, pz = 0.f, xx = 0.f, yy = 0.f, zz = 0.f;
-        if (i < nflG) {
-          slot = S.flG[i];
-          const long src = gbase + slot;
-          const uint4 r = A.recG[src];
-          K = r.x & 0xFF;
-          wprod = __uint_as_float(r.y);
-          const float wrem = __uint_as_float(r.z);
-          cnt.add(C_CAP, (r.x & DF_CAPPED) ? 1u : 0u);
-          cnt.add(C_CLAMP, (r.x & DF_OVER) ? 1u : 0u);
-          cnt.add(C_EV_P, (unsigned)K);
-          removed = !(r.x & DF_KEEP);
-          if (K) {
-            px = A.g.px[src];
-            py = A.g.py[src];
-            pz = A.g.pz[src];
-            xx = A.g.x[src];
-            yy = A.g.y[src];
-            zz = A.g.z[src];
-            om = sqrtf(px * px + py * py + pz * pz) * kMeC2f;
-            if (!removed) A.g.w[src] = wrem;
-          }
-        }
-        int tot;
-        int off = run + warp_excl_scan(K, &tot);
-        for (int k = 0; k < K; ++k, ++off) {
-          const int dst = abase_new + off;
-          if (dst < A.a.cap) {
-            write_particle(A.a, abase + dst, wprod, px, py, pz, xx, yy, zz);
-            if (A.tally_enable) tally_add(A, 0, wprod, om);
-          } else {
-            cnt.add(C_DROP, 1);
-          }
-        }
-        run += tot;
-        NPa += K;
-        const unsigned m = __ballot_sync(kFull, removed);
-        if (removed) {
-          S.rmG[nrm + __popc(m & lt)] = (uint16_t)slot;
-          atomicOr(&S.rbG[slot >> 5], 1u << (slot & 31));
-        }
-        nrm += __popc(m);
+  // ------------------------------------------------------------ emit: photons
+  const int ng_tot = ng;
+  int nrmG = 0, NPa = 0;
+  float pw_prod = 0.f;
+  int pK = 0, p_off = 0;
+  if (emitG && nflG > 0) {
+    for (int i = lane; i < (ng_tot + 31) / 32; i += 32) S.rbG[i] = 0u;
+    __syncwarp();
+    // decisions of the first 32 (products are written after the axion tail
+    // fill); longer lists are taken whole below
+    if (nflG <= 32) {
+      bool removed = false;
+      int slot = -1;
+      if (lane < nflG) {
+        slot = S.flG[lane];
+        const uint4 r = T.gr[lane];
+        pK = r.x & 0xFF;
+        pw_prod = __uint_as_float(r.y);
+        cnt.add(C_CAP, (r.x & DF_CAPPED) ? 1u : 0u);
+        cnt.add(C_CLAMP, (r.x & DF_OVER) ? 1u : 0u);
+        cnt.add(C_EV_P, (unsigned)pK);
+        removed = !(r.x & DF_KEEP);
+        if (pK && !removed) A.g.w[gbase + slot] = __uint_as_float(r.z);
       }
-      NPa = warp_sum_i(NPa);
+      int tot;
+      p_off = warp_excl_scan(pK, &tot);
+      NPa = tot;
+      const unsigned m = __ballot_sync(kFull, removed);
+      if (removed) {
+        S.rmG[__popc(m & lt)] = (uint16_t)slot;
+        atomicOr(&S.rbG[slot >> 5], 1u << (slot & 31));
+      }
+      nrmG = __popc(m);
+    }
+  }
+  __syncwarp();
+
+  // ------------------------------------------------------------ round trip 3
+  // tail-fill movers of both species (axion movers are read before any
+  // product is written over them)
+  int runA = 0, runG = 0, dA = -1, dG = -1;
+  const bool fillA = (PH & PH_ABSORB) && nrmA > 0;
+  const bool fillG = emitG && nflG <= 32 && nrmG > 0;
+  if (fillA) runA = mover_stage(A.a, abase, S.rmA, S.rbA, na, na_start, T.a, &dA);
+  if (fillG) runG = mover_stage(A.g, gbase, S.rmG, S.rbG, ng_tot - nrmG, ng_tot, T.mg, &dG);
+  if (fillA || fillG) {
+    cp_async_wait_all();
+    __syncwarp();
+  }
+  if (fillA) {
+    mover_commit(A.a, abase, T.a, dA);
+    if (na_start - na > 32) compact_rest(A.a, abase, S.rmA, runA, S.rbA, na, na_start);
+  }
+
+  if (PH & PH_EMIT) {
+    const int abase_new = na;
+    // (c) gamma->a products after the surviving axions
+    if (emitG && nflG > 0) {
+      if (nflG <= 32) {
+        if (pK) {
+          const float px = T.g.px[lane], py = T.g.py[lane], pz = T.g.pz[lane];
+          const float xx = T.g.x[lane], yy = T.g.y[lane], zz = T.g.z[lane];
+          const float om = sqrtf(px * px + py * py + pz * pz) * kMeC2f;
+          int off = p_off;
+          for (int k = 0; k < pK; ++k, ++off) {
+            const int dst = abase_new + off;
+            if (dst < A.a.cap) {
+              write_particle(A.a, abase + dst, pw_prod, px, py, pz, xx, yy, zz);
+              if (A.tally_enable) tally_add(A, 0, pw_prod, om);
+            } else {
+              cnt.add(C_DROP, 1);
+            }
+          }
+        }
+      } else {
+        int run = 0;
+        for (int i0 = 0; i0 < nflG; i0 += 32) {
+          const PhItem t = i0 == 0 ? ph_staged(T, S.flG, lane, nflG) : ph_load(A, gbase, S.flG, i0 + lane, nflG);
+          int K = 0;
+          bool removed = false;
+          float wprod = 0.f, om = 0.f;
+          if (t.slot >= 0) {
+            K = t.r.x & 0xFF;
+            wprod = __uint_as_float(t.r.y);
+            cnt.add(C_CAP, (t.r.x & DF_CAPPED) ? 1u : 0u);
+            cnt.add(C_CLAMP, (t.r.x & DF_OVER) ? 1u : 0u);
+            cnt.add(C_EV_P, (unsigned)K);
+            removed = !(t.r.x & DF_KEEP);
+            if (K) {
+              om = sqrtf(t.px * t.px + t.py * t.py + t.pz * t.pz) * kMeC2f;
+              if (!removed) A.g.w[gbase + t.slot] = __uint_as_float(t.r.z);
+            }
+          }
+          int tot;
+          int off = run + warp_excl_scan(K, &tot);
+          for (int k = 0; k < K; ++k, ++off) {
+            const int dst = abase_new + off;
+            if (dst < A.a.cap) {
+              write_particle(A.a, abase + dst, wprod, t.px, t.py, t.pz, t.x, t.y, t.z);
+              if (A.tally_enable) tally_add(A, 0, wprod, om);
+            } else {
+              cnt.add(C_DROP, 1);
+            }
+          }
+          run += tot;
+          NPa += K;
+          const unsigned m = __ballot_sync(kFull, removed);
+          if (removed) {
+            S.rmG[nrmG + __popc(m & lt)] = (uint16_t)t.slot;
+            atomicOr(&S.rbG[t.slot >> 5], 1u << (t.slot & 31));
+          }
+          nrmG += __popc(m);
+        }
+        NPa = warp_sum_i(NPa);
+      }
     }
     // (d) electron events, in electron then event order; event k of
     // electron i: cos theta, phi, energy and channel from one Philox block
     int NE = 0;
-    if (eC || eB) {
-      const float* rec = A.rec + (size_t)cell * kRecLen;
-      const float wu = A.mom[(size_t)cell * kMomLen + M_WU];
+    if (emitE) {
       if (wu > 0.f && lane == 0) {
         float fac;
         bool cc = false, cb = false;
-        if (eC) cap_lambda(wu * rec[R_CC], A.lam_cap, &fac, &cc);
-        if (eB) cap_lambda(wu * rec[R_CB], A.lam_cap, &fac, &cb);
+        if (eC) cap_lambda(wu * r_cc, A.lam_cap, &fac, &cc);
+        if (eB) cap_lambda(wu * r_cb, A.lam_cap, &fac, &cb);
         cnt.add(C_CAP, (unsigned)ne * ((unsigned)cc + (unsigned)cb));
       }
       if (nflE > 0) {
@@ -912,39 +1180,34 @@ __device__ __forceinline__ void event_cell(const StepArgs& A, int cell, EvScratc
         const float* tabB = A.tables + TAB_BREMS * kTableN;
         int run = 0;
         for (int i0 = 0; i0 < nflE; i0 += 32) {
-          const int i = i0 + lane;
-          int K = 0, slot = 0;
-          if (i < nflE) {
-            slot = S.flE[i];
-            const uint32_t f = A.recE[ebase + slot];
-            K = f & 0xFF;
-            if (wu <= 0.f) cnt.add(C_CAP, ((f & DF_CAPPED) ? 1u : 0u) + ((f & DF_CAPPED_B) ? 1u : 0u));
+          const ElItem t = el_load(A, ebase, S.flE, i0 + lane, nflE, wu);
+          int K = 0;
+          if (t.slot >= 0) {
+            K = t.f & 0xFF;
+            if (wu <= 0.f) cnt.add(C_CAP, ((t.f & DF_CAPPED) ? 1u : 0u) + ((t.f & DF_CAPPED_B) ? 1u : 0u));
           }
           int tot;
           int off = run + warp_excl_scan(K, &tot);
           if (K) {
-            const long src = ebase + slot;
-            const float w = wu > 0.f ? wu : A.e.w[src];
-            const float xx = A.e.x[src], yy = A.e.y[src], zz = A.e.z[src];
             float facC = 1.f, facB = 1.f;
             bool cc = false, cb = false;
-            const float lc = eC ? cap_lambda(w * rec[R_CC], A.lam_cap, &facC, &cc) : 0.f;
-            const float lb = eB ? cap_lambda(w * rec[R_CB], A.lam_cap, &facB, &cb) : 0.f;
+            const float lc = eC ? cap_lambda(t.w * r_cc, A.lam_cap, &facC, &cc) : 0.f;
+            const float lb = eB ? cap_lambda(t.w * r_cb, A.lam_cap, &facB, &cb) : 0.f;
             const float fracC = lc / (lc + lb);
             const float wvC = cc ? A.w_a * facC : A.w_a;
             const float wvB = cb ? A.w_a * facB : A.w_a;
             for (int k = 0; k < K; ++k, ++off) {
-              const uint4 r = philox4x32_10(make_uint4(A.step, gcell, (uint32_t)slot, (S_EV_E << 24) | (uint32_t)k),
-                                            A.key0, A.key1);
+              const uint4 r = philox4x32_10(make_uint4(A.step, gcell, (uint32_t)t.slot, (S_EV_E << 24) | (uint32_t)k),
+                                            A.rk);
               const bool isC = u23(r.w) < fracC;
               const float3 dv = iso_dir(u23(r.x), u23(r.y));
-              const float E = icdf_lookup(isC ? tabC : tabB, u23(r.z)) * rec[R_T];
+              const float E = icdf_lookup(isC ? tabC : tabB, u23(r.z)) * r_T;
               const float wv = isC ? wvC : wvB;
               const float pm = E * kInvMeC2f;
               const float px = pm * dv.x, py = pm * dv.y, pz = pm * dv.z;
               const int dst = abase_new + NPa + off;
               if (dst < A.a.cap) {
-                write_particle(A.a, abase + dst, wv, px, py, pz, xx, yy, zz);
+                write_particle(A.a, abase + dst, wv, px, py, pz, t.x, t.y, t.z);
                 if (A.tally_enable) tally_add(A, isC ? 1 : 2, wv, E);
               } else {
                 cnt.add(C_DROP, 1);
@@ -961,9 +1224,19 @@ __device__ __forceinline__ void event_cell(const StepArgs& A, int cell, EvScratc
     }
     na = min(na + NPa + NE, A.a.cap);
     __syncwarp();
-    // (e) tail-fill compaction of the photons (a->gamma products included)
-    if (nrm > 0) compact_removed(A.g, gbase, S.rmG, nrm, S.rbG, ng_tot);
-    ng = ng_tot - nrm;
+    // (e) tail fill of the photons (a->gamma products included)
+    if (fillG) {
+      mover_commit(A.g, gbase, T.mg, dG);
+      if (nrmG > 32) compact_rest(A.g, gbase, S.rmG, runG, S.rbG, ng_tot - nrmG, ng_tot);
+    } else if (emitG && nflG > 32 && nrmG > 0) {
+      int d = -1;
+      const int run0 = mover_stage(A.g, gbase, S.rmG, S.rbG, ng_tot - nrmG, ng_tot, T.mg, &d);
+      cp_async_wait_all();
+      __syncwarp();
+      mover_commit(A.g, gbase, T.mg, d);
+      if (nrmG > 32) compact_rest(A.g, gbase, S.rmG, run0, S.rbG, ng_tot - nrmG, ng_tot);
+    }
+    ng = ng_tot - nrmG;
   }
   if (lane == 0) {
     A.a.count[cell] = na;
@@ -982,20 +1255,13 @@ __device__ __forceinline__ void event_cell(const StepArgs& A, int cell, EvScratc
     xe[3] = warp_sum_d(x64.dPz);
     xe_any = true;
   }
-  if (lane == 0 && (xa_any || xe_any)) {
-    double* xb = A.xbuf + (size_t)cell * 4;
-    if (xa_any) {
-      xb[0] += xa[0];
-      xb[1] += xa[1];
-      xb[2] += xa[2];
-      xb[3] += xa[3];
-    }
-    if (xe_any) {
-      xb[0] += xe[0];
-      xb[1] += xe[1];
-      xb[2] += xe[2];
-      xb[3] += xe[3];
-    }
+  if (lane < 4 && (xa_any || xe_any)) {
+    const double a = lane == 0 ? xa[0] : (lane == 1 ? xa[1] : (lane == 2 ? xa[2] : xa[3]));
+    const double e = lane == 0 ? xe[0] : (lane == 1 ? xe[1] : (lane == 2 ? xe[2] : xe[3]));
+    double v = xb_old;
+    if (xa_any) v += a;
+    if (xe_any) v += e;
+    xb[lane] = v;
   }
 }
 
@@ -1033,12 +1299,29 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
 // electrons (Eqs. delta_def to b_def, affine_map), measuring what was applied;
 // then the temperature update (Eqs. Te_est, Te_relax) and the record's
 // temperature half.
-__global__ void __launch_bounds__(128) feedback_kernel(StepArgs A) {
-  const int lane = threadIdx.x & 31;
+struct RemapJob {
+  int cell, ne;
+  float s1, bx, by, bz;
+};
+
+// Thread per cell: every load it needs is issued first (exchange, carried
+// exchange, moments, count, T and the record); cells whose exchange needs an
+// affine remap go to a CTA list and the CTA's warps remap them side by side,
+// a warp per cell; then each thread finishes its cell (carry, diagnostics,
+// temperature update and the record's temperature half).
+constexpr int kFeedbackThreads = 128;
+
+__global__ void __launch_bounds__(kFeedbackThreads) feedback_kernel(StepArgs A) {
+  __shared__ RemapJob jobs[kFeedbackThreads];
+  __shared__ RemapOut outs[kFeedbackThreads];
+  __shared__ int njobs;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = cell < A.ncells;
-  double dE = 0.0, dPx = 0.0, dPy = 0.0, dPz = 0.0, rE = 0.0, rPx = 0.0, rPy = 0.0, rPz = 0.0;
+  if (threadIdx.x == 0) njobs = 0;
+  double dE = 0.0, dPx = 0.0, dPy = 0.0, dPz = 0.0, rE = 0.0, rPx = 0.0, rPy = 0.0, rPz = 0.0, T = 0.0;
   float W = 0.f, Px = 0.f, Py = 0.f, Pz = 0.f, U2 = 0.f, var = 0.f;
+  float4 rc0 = make_float4(0.f, 0.f, 0.f, 0.f), rc1 = rc0, rc2 = rc0, rc3 = rc0;
   bool has_x = false, has_res = false, need = false;
   int ne = 0;
   double qE = 0.0, qPx = 0.0, qPy = 0.0, qPz = 0.0, s1d = 0.0, bx = 0.0, by = 0.0, bz = 0.0, vnd = 0.0;
@@ -1048,19 +1331,11 @@ __global__ void __launch_bounds__(128) feedback_kernel(StepArgs A) {
     dPx = xb[1];
     dPy = xb[2];
     dPz = xb[3];
-    has_x = nz64(dE) || nz64(dPx) || nz64(dPy) || nz64(dPz);
-    if (has_x) {
-      xb[0] = 0.0;
-      xb[1] = 0.0;
-      xb[2] = 0.0;
-      xb[3] = 0.0;
-    }
     const double* rs = A.res + (size_t)cell * 4;
     rE = rs[0];
     rPx = rs[1];
     rPy = rs[2];
     rPz = rs[3];
-    has_res = nz64(rE) || nz64(rPx) || nz64(rPy) || nz64(rPz);
     const float* mom = A.mom + (size_t)cell * kMomLen;
     W = mom[M_W];
     Px = mom[M_PX];
@@ -1069,6 +1344,22 @@ __global__ void __launch_bounds__(128) feedback_kernel(StepArgs A) {
     U2 = mom[M_U2];
     var = mom[M_VAR];
     ne = min(max(A.e.count[cell], 0), A.e.cap);
+    if (A.T_mode == 2) {
+      T = A.T[cell];
+      const float4* r4 = reinterpret_cast<const float4*>(A.rec + (size_t)cell * kRecLen);
+      rc0 = r4[0];
+      rc1 = r4[1];
+      rc2 = r4[2];
+      rc3 = r4[3];
+    }
+    has_x = nz64(dE) || nz64(dPx) || nz64(dPy) || nz64(dPz);
+    if (has_x) {
+      xb[0] = 0.0;
+      xb[1] = 0.0;
+      xb[2] = 0.0;
+      xb[3] = 0.0;
+    }
+    has_res = nz64(rE) || nz64(rPx) || nz64(rPy) || nz64(rPz);
     if (has_x || has_res) {
       qE = dE + rE;
       qPx = dPx + rPx;
@@ -1098,37 +1389,39 @@ __global__ void __launch_bounds__(128) feedback_kernel(StepArgs A) {
       }
     }
   }
-  // the warp remaps each cell that needs it, one after the other
+  __syncthreads();
+  int job = -1;
+  if (need) {
+    job = atomicAdd(&njobs, 1);
+    jobs[job] = RemapJob{cell, ne, (float)s1d, (float)bx, (float)by, (float)bz};
+  }
+  __syncthreads();
+  const int nj = njobs;
+  for (int k = wid; k < nj; k += kFeedbackThreads / 32) {
+    const RemapJob J = jobs[k];
+    const RemapOut r = remap_electrons(A, (long)J.cell * A.e.cap, J.ne, J.s1, J.bx, J.by, J.bz);
+    if (lane == 0) outs[k] = r;
+  }
+  __syncthreads();
+  if (!valid) return;
   double nrE = qE, nrPx = qPx, nrPy = qPy, nrPz = qPz, applied_E = 0.0;
   float var_new = var;
-  unsigned m = __ballot_sync(kFull, need);
-  while (m) {
-    const int src = __ffs(m) - 1;
-    m &= m - 1u;
-    const int c_src = __shfl_sync(kFull, cell, src);
-    const int ne_src = __shfl_sync(kFull, ne, src);
-    const float s1 = __shfl_sync(kFull, (float)s1d, src);
-    const float fbx = __shfl_sync(kFull, (float)bx, src);
-    const float fby = __shfl_sync(kFull, (float)by, src);
-    const float fbz = __shfl_sync(kFull, (float)bz, src);
-    const RemapOut r = remap_electrons(A, (long)c_src * A.e.cap, ne_src, s1, fbx, fby, fbz);
-    if (lane == src) {
-      applied_E = r.applied_E;
-      nrE = qE - r.applied_E;
-      nrPx = qPx - r.apx;
-      nrPy = qPy - r.apy;
-      nrPz = qPz - r.apz;
-      var_new = (float)vnd;
-      float* mom = A.mom + (size_t)cell * kMomLen;
-      mom[M_W] = r.mW;
-      mom[M_PX] = r.mPx;
-      mom[M_PY] = r.mPy;
-      mom[M_PZ] = r.mPz;
-      mom[M_U2] = r.mU2;
-      mom[M_VAR] = fmaxf(0.f, r.mU2 - (r.mPx * r.mPx + r.mPy * r.mPy + r.mPz * r.mPz) / r.mW);
-    }
+  if (job >= 0) {
+    const RemapOut r = outs[job];
+    applied_E = r.applied_E;
+    nrE = qE - r.applied_E;
+    nrPx = qPx - r.apx;
+    nrPy = qPy - r.apy;
+    nrPz = qPz - r.apz;
+    var_new = (float)vnd;
+    float* mom = A.mom + (size_t)cell * kMomLen;
+    mom[M_W] = r.mW;
+    mom[M_PX] = r.mPx;
+    mom[M_PY] = r.mPy;
+    mom[M_PZ] = r.mPz;
+    mom[M_U2] = r.mU2;
+    mom[M_VAR] = fmaxf(0.f, r.mU2 - (r.mPx * r.mPx + r.mPy * r.mPy + r.mPz * r.mPz) / r.mW);
   }
-  if (!valid) return;
   if (has_x || has_res) {
     double* rs = A.res + (size_t)cell * 4;
     rs[0] = nrE;
@@ -1162,15 +1455,14 @@ __global__ void __launch_bounds__(128) feedback_kernel(StepArgs A) {
   // temperature (Eqs. Te_est, Te_relax), then the record's temperature half;
   // T stays FP64, the relaxation step is formed in binary32 and added once
   if (A.T_mode == 2 && W > 0.f) {
-    const double T = A.T[cell];
     const float Tf = (float)T;
     const float Test = (kMeC2f / 3.0f) * var_new / W;
     const float dT = A.relax_r * (Test - Tf);
     double Tn = T + (double)dT;
     const float Tnf = Tf + dT;
     if (Tnf <= A.T_floor_f || Tnf >= A.T_ceil_f) Tn = fmin(fmax(Tn, A.T_floor), A.T_ceil);
-    float rec[kRecLen];
-    load_rec(A, cell, rec);
+    float rec[kRecLen] = {rc0.x, rc0.y, rc0.z, rc0.w, rc1.x, rc1.y, rc1.z, rc1.w,
+                          rc2.x, rc2.y, rc2.z, rc2.w, rc3.x, rc3.y, rc3.z, rc3.w};
     compute_temperature(A.cc, (float)Tn, rec);
     A.T[cell] = Tn;
     float4* r4 = reinterpret_cast<float4*>(A.rec + (size_t)cell * kRecLen);
@@ -1178,6 +1470,7 @@ __global__ void __launch_bounds__(128) feedback_kernel(StepArgs A) {
     r4[1] = make_float4(rec[4], rec[5], rec[6], rec[7]);
   }
 }
+
 
 // ---------------------------------------------------------------- launchers
 size_t step_smem_per_warp(int acap, int gcap, int ecap) { return ev_scratch_bytes(acap, gcap, ecap); }
@@ -1190,23 +1483,45 @@ static cudaError_t launch_events(const StepArgs& A, int warps, cudaStream_t st) 
   return cudaGetLastError();
 }
 
-static int dec_blocks(const StepArgs& A) { return (A.ncells + A.dec_cells - 1) / A.dec_cells; }
-
-static cudaError_t launch_axion_decide(const StepArgs& A, cudaStream_t st) {
-  if (A.a.cap == 0 || A.ncells == 0) return cudaSuccess;
-  axion_decide_kernel<<<dec_blocks(A), kDecThreads, 0, st>>>(A);
-  return cudaGetLastError();
+// Persistent decision grid: as many CTAs as the device holds at once (at most
+// one warp per chunk).
+static int dec_blocks(const StepArgs& A) {
+  const int nchunks = (A.ncells + kChunk - 1) / kChunk;
+  const int need = (nchunks + kDecWarps - 1) / kDecWarps;
+  return max(1, min(need, A.dec_grid));
 }
 
-static cudaError_t launch_emit_decide(const StepArgs& A, cudaStream_t st) {
-  if ((A.g.cap == 0 && A.e.cap == 0) || A.ncells == 0) return cudaSuccess;
-  emit_decide_kernel<<<dim3(dec_blocks(A), 2), kDecThreads, 0, st>>>(A);
+// The decision passes a phase set needs, as DK_* bits.
+static int decide_kinds(const StepArgs& A, int phases) {
+  int k = 0;
+  if ((phases & PH_EMIT) && (A.mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS)) && A.e.cap > 0) k |= DK_ELECTRON;
+  if ((phases & PH_EMIT) && (A.mask & AXPIC_CH_PRIMAKOFF) && A.g.cap > 0) k |= DK_PHOTON;
+  if ((phases & PH_ABSORB) && A.a.cap > 0) k |= DK_AXION;
+  return k;
+}
+
+static cudaError_t launch_decide(const StepArgs& A, int phases, cudaStream_t st) {
+  const int kinds = decide_kinds(A, phases);
+  if (kinds == 0) return cudaSuccess;
+  decide_kernel<<<dec_blocks(A), kDecThreads, 0, st>>>(A, kinds);
   return cudaGetLastError();
 }
 
 static cudaError_t launch_feedback(const StepArgs& A, cudaStream_t st) {
-  feedback_kernel<<<(A.ncells + 127) / 128, 128, 0, st>>>(A);
+  feedback_kernel<<<(A.ncells + kFeedbackThreads - 1) / kFeedbackThreads, kFeedbackThreads, 0, st>>>(A);
   return cudaGetLastError();
+}
+
+const char* step_kernel_names() { return "decide_kernel,event_kernel,feedback_kernel"; }
+
+cudaError_t decide_resident_ctas(int* out) {
+  int dev = 0, sms = 0, nb = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, decide_kernel, kDecThreads, 0)))
+    return e;
+  *out = max(1, nb) * max(1, sms);
+  return cudaSuccess;
 }
 
 cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t st, cudaEvent_t* ev) {
@@ -1216,23 +1531,18 @@ cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t s
   auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], st) : cudaSuccess; };
   switch (phases) {
     case PH_ABSORB:
-      if ((e = launch_axion_decide(A, st))) return e;
+      if ((e = launch_decide(A, PH_ABSORB, st))) return e;
       return launch_events<PH_ABSORB>(A, warps, st);
     case PH_EMIT:
-      if ((e = launch_emit_decide(A, st))) return e;
+      if ((e = launch_decide(A, PH_EMIT, st))) return e;
       return launch_events<PH_EMIT>(A, warps, st);
     case PH_FEEDBACK:
       return launch_feedback(A, st);
-    case PH_ALL: {
-      // the photon decisions of the emit phase read the photons present at
-      // the start of the step, before the absorb phase appends a->gamma
-      // products, so both decision kernels run first
-      if ((e = mark(0)) || (e = launch_axion_decide(A, st)) || (e = mark(1))) return e;
-      if ((e = launch_emit_decide(A, st)) || (e = mark(2))) return e;
-      if ((e = launch_events<PH_ABSORB | PH_EMIT>(A, warps, st)) || (e = mark(3))) return e;
-      if ((e = launch_feedback(A, st)) || (e = mark(4))) return e;
+    case PH_ALL:
+      if ((e = mark(0)) || (e = launch_decide(A, PH_ABSORB | PH_EMIT, st)) || (e = mark(1))) return e;
+      if ((e = launch_events<PH_ABSORB | PH_EMIT>(A, warps, st)) || (e = mark(2))) return e;
+      if ((e = launch_feedback(A, st)) || (e = mark(3))) return e;
       return cudaSuccess;
-    }
     default:
       return cudaErrorInvalidValue;
   }
@@ -1240,12 +1550,12 @@ cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t s
 
 cudaError_t set_step_smem_limits(size_t bytes) {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(event_kernel<PH_ABSORB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)))
+  const int b = (int)bytes;
+  if ((e = cudaFuncSetAttribute(event_kernel<PH_ABSORB>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) ||
+      (e = cudaFuncSetAttribute(event_kernel<PH_EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) ||
+      (e = cudaFuncSetAttribute(event_kernel<PH_ABSORB | PH_EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
     return e;
-  if ((e = cudaFuncSetAttribute(event_kernel<PH_EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)))
-    return e;
-  return cudaFuncSetAttribute(event_kernel<PH_ABSORB | PH_EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)bytes);
+  return cudaSuccess;
 }
 
 }  // namespace axpic

@@ -7,9 +7,14 @@ namespace axpic {
 enum { PH_ABSORB = 1, PH_EMIT = 2, PH_FEEDBACK = 4, PH_ALL = 7 };
 
 size_t step_smem_per_warp(int acap, int gcap, int ecap);
-// ev: NULL, or 5 events recorded around the kernels of a PH_ALL step.
+// ev: NULL, or kStepKernels + 1 events recorded around the kernels of a
+// PH_ALL step.
 cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t st, cudaEvent_t* ev = nullptr);
-constexpr int kStepKernels = 4;
+constexpr int kStepKernels = 3;
+// Comma-separated names of the kernels a PH_ALL step launches, in order.
+const char* step_kernel_names();
 cudaError_t set_step_smem_limits(size_t bytes);
+// CTAs of the decision kernel that the current device holds at once.
+cudaError_t decide_resident_ctas(int* out);
 
 }  // namespace axpic
