@@ -1,22 +1,24 @@
 // The per-cell step: absorb -> emit -> feedback (Sec. II.D-II.J).
 //
-// A step is four kernels:
-//  * axion_decide_kernel and emit_decide_kernel: one thread per quad of
-//    consecutive slots (float4 loads from the SoA slabs, one Philox4x32-10
-//    block per quad and stream, word j for slot 4q+j). Each slot gets a cheap
-//    exact test that proves "no event this step"; slots it cannot clear are
-//    flagged in a per-cell bit mask. These kernels carry almost all the
-//    per-particle work and have no per-cell serialisation.
-//  * event_kernel: one warp per cell. It reads only the bit masks, takes the
-//    full decision for the flagged slots (few), writes products and compacts
-//    at offsets from warp prefix sums, so the output order is the
-//    deterministic one of the method's definition, and accumulates the FP64
-//    exchange (Delta E, Delta P).
-//  * feedback_kernel: one lane per cell for the temperature update; the rare
-//    cells whose exchange needs an affine remap are remapped by the whole warp.
-// The separate API calls run the same kernels with one phase each; the
-// exchange passes through an FP64 per-cell buffer in the same summation order,
-// so results do not depend on how a step is called.
+// A step is three kernels:
+//  * decide_kernel: persistent warps over chunks of consecutive cells, lane
+//    per quad of consecutive slots (float4 loads from the SoA slabs, one
+//    Philox4x32-10 block per quad and stream, word j for slot 4q+j). Each
+//    slot gets a cheap exact test that proves "no event this step"; slots it
+//    cannot clear are flagged in a per-cell bit mask and their full decision
+//    is taken from per-warp lists, 32 at a time, into slot-indexed records.
+//    This kernel carries almost all the per-particle work.
+//  * event_kernel: one warp per cell. It reads the bit masks and the records
+//    of the flagged slots, writes products and refills removed slots at
+//    offsets from warp prefix sums, so the output order is the deterministic
+//    one of the method's definition, and accumulates the FP64 exchange
+//    (Delta E, Delta P).
+//  * feedback_kernel: thread per cell for the temperature update; the rare
+//    cells whose exchange needs an affine remap are remapped by the CTA's
+//    warps side by side.
+// The separate API calls run the same kernels with a subset of the passes;
+// the exchange passes through an FP64 per-cell buffer in the same summation
+// order, so results do not depend on how a step is called.
 #include "common.cuh"
 #include "step.h"
 
