@@ -116,9 +116,11 @@ typedef struct {
   double tally_Emax_keV;    /* histogram range [0, Emax) (80 keV) */
   int32_t tally_enable;     /* 1: step calls accumulate the emitted spectrum */
   int32_t diag_enable;      /* 1: feedback writes per-cell diagnostics */
-  int32_t threads_per_block;/* threads per CTA of the step kernel (32..128, one warp
-                               per cell); 0: default 128 */
-  int32_t reserved[7];
+  int32_t threads_per_block;/* threads per CTA of the event kernel (32..128, one
+                               warp per cell); 0: default 128 */
+  int32_t decide_chunk;     /* cells per chunk of a decision warp: 2, 4 or 8;
+                               0: default 4 (launch shape, see axpic_autotune) */
+  int32_t reserved[6];
 } axpic_params;
 
 /* Number of doubles written by axpic_tally_spectrum into totals_out. */
@@ -270,6 +272,32 @@ axpic_status axpic_get_residuals(axpic_ctx *ctx, int32_t first, int32_t count, d
  * device. */
 axpic_status axpic_step_noalloc(const axpic_plasma_desc *desc, const axpic_params *params, int64_t step,
                                 int32_t channel_mask, double *carry, void *stream);
+
+/* Runs nsteps full steps (as axpic_step with steps first_step,
+ * first_step + 1, ...) by replaying a CUDA graph of one step: the decision,
+ * event and feedback kernels, with the step index read from a device counter
+ * that the feedback kernel advances. The graph is captured on first use for a
+ * channel mask (on a private stream of the context, ordered after the
+ * context's stream) and kept until the launch shape changes. Asynchronous;
+ * results are identical to nsteps calls of axpic_step. AXPIC_E_INVALID for
+ * nsteps < 0, a step range outside [0, 2^32 - 1) or unknown channel bits.
+ * Not part of the paper's method: batching of many small boxes in one
+ * context (each cell carries its own plasma record) and launch by graph. */
+axpic_status axpic_run_steps(axpic_ctx *ctx, int64_t first_step, int32_t nsteps, int32_t channel_mask);
+
+/* Picks the launch shape (cells per decision chunk, 2/4/8, and warps per
+ * event CTA, 2 or 4) by timing trial_steps steps of the context's own state
+ * for each shape (CUDA events, after one untimed step), with the step index
+ * `step` and channel_mask. The context's device state (the slabs and counts
+ * of the three species, T, rates, moments, exchange and carried buffers,
+ * tallies and counters) is saved to scratch first and restored after every
+ * trial, so the state afterwards is bit for bit what it was. Needs device
+ * memory for one copy of that state. Synchronises. Writes the best shape's
+ * ms per step to *best_ms_out (may be NULL) and its parameters to
+ * *chunk_out and *warps_out (may be NULL). AXPIC_E_INVALID for
+ * trial_steps < 1. Not part of the paper's method. */
+axpic_status axpic_autotune(axpic_ctx *ctx, int64_t step, int32_t trial_steps, int32_t channel_mask,
+                            double *best_ms_out, int32_t *chunk_out, int32_t *warps_out);
 
 /* Measurement of the step's kernels. axpic_profile_begin (synchronises)
  * prepares CUDA events for the next max_steps calls of axpic_step, which then

@@ -52,7 +52,8 @@ class Params(ctypes.Structure):
                 ("T_floor_keV", ctypes.c_double), ("T_ceil_keV", ctypes.c_double), ("T_mode", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("tally_nbins", ctypes.c_int32), ("tally_Emax_keV", ctypes.c_double),
                 ("tally_enable", ctypes.c_int32), ("diag_enable", ctypes.c_int32),
-                ("threads_per_block", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("threads_per_block", ctypes.c_int32), ("decide_chunk", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class AxpicError(RuntimeError):
@@ -73,6 +74,10 @@ EXPORTS = {
     "axpic_emit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]),
     "axpic_feedback": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "axpic_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]),
+    "axpic_run_steps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]),
+    "axpic_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32)]),
     "axpic_tally_spectrum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double)]),
     "axpic_eval_rates": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
@@ -154,6 +159,20 @@ def axpic_feedback(ctx, step):
 
 def axpic_step(ctx, step, mask):
     _check(ctx, lib().axpic_step(ctx, step, mask))
+
+
+def axpic_run_steps(ctx, first_step, nsteps, mask):
+    _check(ctx, lib().axpic_run_steps(ctx, first_step, nsteps, mask))
+
+
+def axpic_autotune(ctx, step, trial_steps, mask):
+    """(best ms per step, decide_chunk, event warps per CTA)."""
+    ms = ctypes.c_double()
+    chunk = ctypes.c_int32()
+    warps = ctypes.c_int32()
+    _check(ctx, lib().axpic_autotune(ctx, step, trial_steps, mask, ctypes.byref(ms), ctypes.byref(chunk),
+                                     ctypes.byref(warps)))
+    return ms.value, chunk.value, warps.value
 
 
 def axpic_tally_spectrum(ctx, nbins, H_out, totals_out):

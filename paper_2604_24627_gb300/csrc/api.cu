@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -52,8 +53,15 @@ struct axpic_ctx {
   uint32_t* recE = nullptr;   // event counts of flagged electrons
   CellConst cc;
   int warps = kDefaultWarps;
-  int grid = 0;      // event-kernel CTAs, also the rows of per-CTA counters
-  int dec_grid = 1;  // CTAs of the persistent decision kernel
+  int grid = 0;       // event-kernel CTAs
+  int max_warps = 4;  // largest event CTA (warps) whose scratch fits
+  int ctr_rows = 1;   // rows of per-CTA counters
+  int dec_grid = 1;   // CTAs of the persistent decision kernel
+  int dec_chunk = kDefaultDecChunk;
+  uint32_t* step_dev = nullptr;      // step counter of replayed graphs
+  cudaStream_t graph_stream = nullptr;
+  cudaEvent_t graph_ev[2] = {nullptr, nullptr};
+  std::map<int, cudaGraphExec_t> graphs;  // one-step graph per channel mask
   int64_t last_absorb_step = -1;
   std::string last_error;
   std::vector<cudaEvent_t> prof_events;  // 5 per recorded step, created by axpic_profile_begin
@@ -199,6 +207,9 @@ static StepArgs make_args(axpic_ctx* ctx, int64_t step, int mask) {
   A.recG = ctx->recG;
   A.recE = ctx->recE;
   A.dec_grid = ctx->dec_grid;
+  A.dec_chunk = ctx->dec_chunk;
+  A.ctr_rows = ctx->ctr_rows;
+  A.step_dev = nullptr;
   A.cc = ctx->cc;
   return A;
 }
@@ -209,11 +220,20 @@ static void free_events(axpic_ctx* ctx) {
   ctx->prof_max = ctx->prof_used = 0;
 }
 
+static void free_graphs(axpic_ctx* ctx) {
+  for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.second);
+  ctx->graphs.clear();
+}
+
 static void free_ctx(axpic_ctx* ctx) {
   free_events(ctx);
+  free_graphs(ctx);
+  for (cudaEvent_t e : ctx->graph_ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->graph_stream) cudaStreamDestroy(ctx->graph_stream);
   void* bufs[] = {ctx->rec,    ctx->mom,   ctx->xbuf,     ctx->res, ctx->diag,    ctx->photon_start,
                   ctx->tables, ctx->tally, ctx->counters, ctx->err, ctx->scratch, ctx->bits,
-                  ctx->recA,   ctx->recG,  ctx->recE};
+                  ctx->recA,   ctx->recG,  ctx->recE,     ctx->step_dev};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete ctx;
@@ -247,6 +267,7 @@ void axpic_default_params(axpic_params* p) {
   p->tally_enable = 1;
   p->diag_enable = 0;
   p->threads_per_block = 0;
+  p->decide_chunk = 0;
 }
 
 axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, const axpic_params* params,
@@ -300,8 +321,14 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
   const size_t smem_limit = 227 * 1024 - 128;
   while (warps > 1 && per_warp * warps > smem_limit) --warps;
   if (per_warp > smem_limit) return bad("slab capacities too large for shared-memory scratch");
+  ctx->max_warps = 4;
+  while (ctx->max_warps > 1 && per_warp * ctx->max_warps > smem_limit) --ctx->max_warps;
+  if (p.decide_chunk != 0 && p.decide_chunk != 2 && p.decide_chunk != 4 && p.decide_chunk != 8)
+    return bad("decide_chunk must be 0, 2, 4 or 8");
+  ctx->dec_chunk = p.decide_chunk ? p.decide_chunk : kDefaultDecChunk;
   ctx->warps = warps;
   ctx->grid = (d.ncells + warps - 1) / warps;
+  ctx->ctr_rows = std::max(1, std::min(kCounterRows, (d.ncells + 3) / 4));
   fold_constants(ctx);
 
   const int n = d.ncells;
@@ -320,7 +347,8 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
   ALLOC(ctx->photon_start, sizeof(int32_t) * (size_t)n);
   ALLOC(ctx->tables, sizeof(float) * kNumTables * kTableN);
   ALLOC(ctx->tally, sizeof(double) * (3 * (size_t)p.tally_nbins + 6));
-  ALLOC(ctx->counters, sizeof(unsigned long long) * kNumCounters * (size_t)ctx->grid);
+  ALLOC(ctx->counters, sizeof(unsigned long long) * kNumCounters * (size_t)ctx->ctr_rows);
+  ALLOC(ctx->step_dev, sizeof(uint32_t));
   ALLOC(ctx->err, sizeof(int));
   ALLOC(ctx->scratch, sizeof(double) * (8 + kNumCounters + (size_t)kInfoChunk * AXPIC_CELL_INFO_LEN));
   const size_t bit_words = (size_t)n * ((d.axions.capacity + 31) / 32 + (d.photons.capacity + 31) / 32 +
@@ -339,10 +367,11 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
       (e = cudaMemsetAsync(ctx->diag, 0, sizeof(double) * AXPIC_CELL_DIAG_LEN * (size_t)n, st)) ||
       (e = cudaMemsetAsync(ctx->photon_start, 0, sizeof(int32_t) * (size_t)n, st)) ||
       (e = cudaMemsetAsync(ctx->tally, 0, sizeof(double) * (3 * (size_t)p.tally_nbins + 6), st)) ||
-      (e = cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * kNumCounters * (size_t)ctx->grid, st)) ||
+      (e = cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * kNumCounters * (size_t)ctx->ctr_rows, st)) ||
       (e = cudaMemsetAsync(ctx->err, 0, sizeof(int), st)) ||
       (e = cudaMemsetAsync(ctx->bits, 0, sizeof(uint32_t) * (bit_words > 0 ? bit_words : 1), st)) ||
-      (e = set_step_smem_limits(per_warp * warps)) || (e = decide_resident_ctas(&ctx->dec_grid)) ||
+      (e = set_step_smem_limits(per_warp * ctx->max_warps)) ||
+      (e = decide_resident_ctas(ctx->dec_chunk, &ctx->dec_grid)) ||
       (e = launch_records(n, d.nspecies, ctx->cc, d.T_keV, d.n_ion, ctx->rec, ctx->err, st)) ||
       (e = launch_moments(n, to_ptrs(d.electrons), ctx->mom, st)) || (e = cudaStreamSynchronize(st))) {
     ctx->last_error = cudaGetErrorString(e);
@@ -439,13 +468,13 @@ axpic_status axpic_tally_spectrum(axpic_ctx* ctx, int32_t nbins, double* H_out, 
   std::vector<double> h(hn), tot(8 + kNumCounters);
   CK(cudaMemsetAsync(ctx->scratch, 0, sizeof(double) * (8 + kNumCounters), st), "memset");
   CK(launch_totals(d.ncells, to_ptrs(d.electrons), to_ptrs(d.photons), to_ptrs(d.axions), ctx->res, ctx->counters,
-                   ctx->grid, ctx->scratch, ctx->scratch + 8, st),
+                   ctx->ctr_rows, ctx->scratch, ctx->scratch + 8, st),
      "totals");
   CK(cudaMemcpyAsync(h.data(), ctx->tally, hn * sizeof(double), cudaMemcpyDeviceToHost, st), "copy tally");
   CK(cudaMemcpyAsync(tot.data(), ctx->scratch, tot.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
      "copy totals");
   CK(cudaMemsetAsync(ctx->tally, 0, hn * sizeof(double), st), "reset tally");
-  CK(cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * kNumCounters * (size_t)ctx->grid, st),
+  CK(cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned long long) * kNumCounters * (size_t)ctx->ctr_rows, st),
      "reset counters");
   CK(cudaStreamSynchronize(st), "synchronize");
   if (H_out) std::memcpy(H_out, h.data(), 3 * (size_t)nbins * sizeof(double));
@@ -560,6 +589,154 @@ axpic_status axpic_profile_end(axpic_ctx* ctx, double* ms_out, int32_t* steps_ou
   }
   if (steps_out) *steps_out = ctx->prof_used;
   free_events(ctx);
+  return AXPIC_OK;
+}
+
+axpic_status axpic_run_steps(axpic_ctx* ctx, int64_t first_step, int32_t nsteps, int32_t channel_mask) {
+  if (!ctx) return AXPIC_E_INVALID;
+  if (nsteps < 0 || first_step < 0 || first_step + (int64_t)nsteps >= (int64_t)0xFFFFFFFF)
+    return fail(ctx, AXPIC_E_INVALID, "axpic_run_steps: step range outside [0, 2^32 - 1)");
+  if (channel_mask & ~AXPIC_CH_ALL) return fail(ctx, AXPIC_E_INVALID, "axpic_run_steps: unknown channel bits");
+  if (nsteps == 0 || ctx->desc.ncells == 0) return AXPIC_OK;
+  if (!ctx->graph_stream) {
+    CK(cudaStreamCreateWithFlags(&ctx->graph_stream, cudaStreamNonBlocking), "stream create");
+    CK(cudaEventCreateWithFlags(&ctx->graph_ev[0], cudaEventDisableTiming), "event create");
+    CK(cudaEventCreateWithFlags(&ctx->graph_ev[1], cudaEventDisableTiming), "event create");
+  }
+  cudaStream_t gs = ctx->graph_stream;
+  // ordered after the work already queued on the context's stream
+  CK(cudaEventRecord(ctx->graph_ev[0], ctx->stream), "event record");
+  CK(cudaStreamWaitEvent(gs, ctx->graph_ev[0], 0), "stream wait");
+  auto it = ctx->graphs.find(channel_mask);
+  if (it == ctx->graphs.end()) {
+    StepArgs A = make_args(ctx, first_step, channel_mask);
+    A.step_dev = ctx->step_dev;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal), "begin capture");
+    const cudaError_t le = launch_step(PH_ALL, A, ctx->warps, gs);
+    const cudaError_t ce = cudaStreamEndCapture(gs, &g);
+    if (le != cudaSuccess || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(ctx, le != cudaSuccess ? le : ce, "axpic_run_steps: capture");
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return cuda_fail(ctx, ie, "axpic_run_steps: instantiate");
+    it = ctx->graphs.emplace(channel_mask, ex).first;
+  }
+  CK(launch_set_step(ctx->step_dev, (uint32_t)first_step, gs), "set step");
+  for (int32_t k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(it->second, gs), "graph launch");
+  CK(cudaEventRecord(ctx->graph_ev[1], gs), "event record");
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->graph_ev[1], 0), "stream wait");
+  return AXPIC_OK;
+}
+
+// The context's device state, as (pointer, bytes) pairs: what a step reads or
+// writes. The autotuner saves and restores exactly this.
+static std::vector<std::pair<void*, size_t>> state_buffers(axpic_ctx* ctx) {
+  const axpic_plasma_desc& d = ctx->desc;
+  const size_t n = (size_t)d.ncells;
+  std::vector<std::pair<void*, size_t>> b;
+  for (const axpic_species* s : {&d.electrons, &d.photons, &d.axions}) {
+    const size_t slots = n * (size_t)s->capacity * sizeof(float);
+    for (float* f : {s->w, s->px, s->py, s->pz, s->x, s->y, s->z}) b.emplace_back(f, slots);
+    b.emplace_back(s->count, n * sizeof(int32_t));
+  }
+  const size_t bit_words = n * ((d.axions.capacity + 31) / 32 + (d.photons.capacity + 31) / 32 +
+                                (d.electrons.capacity + 31) / 32);
+  b.emplace_back(d.T_keV, n * sizeof(double));
+  b.emplace_back(ctx->rec, n * kRecLen * sizeof(float));
+  b.emplace_back(ctx->mom, n * kMomLen * sizeof(float));
+  b.emplace_back(ctx->xbuf, n * 4 * sizeof(double));
+  b.emplace_back(ctx->res, n * 4 * sizeof(double));
+  b.emplace_back(ctx->diag, n * AXPIC_CELL_DIAG_LEN * sizeof(double));
+  b.emplace_back(ctx->photon_start, n * sizeof(int32_t));
+  b.emplace_back(ctx->tally, (3 * (size_t)ctx->prm.tally_nbins + 6) * sizeof(double));
+  b.emplace_back(ctx->counters, sizeof(unsigned long long) * kNumCounters * (size_t)ctx->ctr_rows);
+  b.emplace_back(ctx->err, sizeof(int));
+  b.emplace_back(ctx->bits, bit_words * sizeof(uint32_t));
+  return b;
+}
+
+static cudaError_t copy_state(axpic_ctx* ctx, unsigned char* save, bool to_save) {
+  size_t off = 0;
+  for (auto& b : state_buffers(ctx)) {
+    if (b.second == 0) continue;
+    void* dst = to_save ? (void*)(save + off) : b.first;
+    const void* src = to_save ? (const void*)b.first : (const void*)(save + off);
+    const cudaError_t e = cudaMemcpyAsync(dst, src, b.second, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) return e;
+    off += (b.second + 255) & ~size_t(255);
+  }
+  return cudaSuccess;
+}
+
+static void set_shape(axpic_ctx* ctx, int chunk, int warps, int dec_grid) {
+  ctx->dec_chunk = chunk;
+  ctx->dec_grid = dec_grid;
+  ctx->warps = warps;
+  ctx->grid = (ctx->desc.ncells + warps - 1) / warps;
+}
+
+axpic_status axpic_autotune(axpic_ctx* ctx, int64_t step, int32_t trial_steps, int32_t channel_mask,
+                            double* best_ms_out, int32_t* chunk_out, int32_t* warps_out) {
+  if (!ctx) return AXPIC_E_INVALID;
+  if (trial_steps < 1 || step < 0 || step + (int64_t)trial_steps >= (int64_t)0xFFFFFFFF)
+    return fail(ctx, AXPIC_E_INVALID, "axpic_autotune: trial_steps < 1 or step range outside [0, 2^32 - 1)");
+  if (channel_mask & ~AXPIC_CH_ALL) return fail(ctx, AXPIC_E_INVALID, "axpic_autotune: unknown channel bits");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  size_t total = 0;
+  for (auto& b : state_buffers(ctx)) total += (b.second + 255) & ~size_t(255);
+  unsigned char* save = nullptr;
+  CK(cudaMalloc((void**)&save, total > 0 ? total : 256), "autotune scratch");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const int keep_chunk = ctx->dec_chunk, keep_warps = ctx->warps, keep_grid = ctx->dec_grid;
+  int best_chunk = keep_chunk, best_warps = keep_warps, best_grid = keep_grid;
+  double best = -1.0;
+  cudaError_t e = copy_state(ctx, save, true);
+  if (!e) e = cudaEventCreate(&e0);
+  if (!e) e = cudaEventCreate(&e1);
+  for (int chunk : {2, 4, 8}) {
+    int dgrid = 1;
+    if (!e) e = decide_resident_ctas(chunk, &dgrid);
+    for (int warps : {2, 4}) {
+      if (e) break;
+      if (warps > ctx->max_warps) continue;
+      set_shape(ctx, chunk, warps, dgrid);
+      // one untimed step, then trial_steps timed ones, from the saved state
+      StepArgs A = make_args(ctx, step, channel_mask);
+      if ((e = launch_step(PH_ALL, A, ctx->warps, ctx->stream)) || (e = cudaEventRecord(e0, ctx->stream))) break;
+      for (int32_t k = 0; k < trial_steps && !e; ++k) {
+        A = make_args(ctx, step + 1 + k, channel_mask);
+        e = launch_step(PH_ALL, A, ctx->warps, ctx->stream);
+      }
+      float ms = 0.f;
+      if (e || (e = cudaEventRecord(e1, ctx->stream)) || (e = cudaEventSynchronize(e1)) ||
+          (e = cudaEventElapsedTime(&ms, e0, e1)) || (e = copy_state(ctx, save, false)))
+        break;
+      const double per = ms / trial_steps;
+      if (best < 0.0 || per < best) {
+        best = per;
+        best_chunk = chunk;
+        best_warps = warps;
+        best_grid = dgrid;
+      }
+    }
+  }
+  if (!e) e = cudaStreamSynchronize(ctx->stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(save);
+  if (e) {
+    set_shape(ctx, keep_chunk, keep_warps, keep_grid);
+    return cuda_fail(ctx, e, "axpic_autotune");
+  }
+  set_shape(ctx, best_chunk, best_warps, best_grid);
+  free_graphs(ctx);
+  if (best_ms_out) *best_ms_out = best;
+  if (chunk_out) *chunk_out = best_chunk;
+  if (warps_out) *warps_out = best_warps;
   return AXPIC_OK;
 }
 
@@ -686,15 +863,17 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc* desc, const axpic_param
   c.res = carry;
   c.warps = kNoAllocWarps;
   c.grid = (d.ncells + kNoAllocWarps - 1) / kNoAllocWarps;
+  c.ctr_rows = std::max(1, std::min(kCounterRows, (d.ncells + 3) / 4));
+  c.dec_chunk = kDefaultDecChunk;
   fold_constants(&c);
   const StepArgs A = make_args(&c, step, channel_mask);
   int h_err = 0;
   cudaError_t e;
   if ((e = cudaMemsetAsync(c.err, 0, sizeof(int), st)) ||
-      (e = cudaMemsetAsync(c.counters, 0, sizeof(unsigned long long) * kNumCounters * (size_t)c.grid, st)) ||
+      (e = cudaMemsetAsync(c.counters, 0, sizeof(unsigned long long) * kNumCounters * (size_t)c.ctr_rows, st)) ||
       (e = cudaMemsetAsync(c.xbuf, 0, sizeof(double) * 4 * (size_t)d.ncells, st)) ||
       (e = cudaMemsetAsync(c.bits, 0, bit_bytes > 0 ? bit_bytes : 4, st)) ||
-      (e = set_step_smem_limits(per_warp * kNoAllocWarps)) || (e = decide_resident_ctas(&c.dec_grid)) ||
+      (e = set_step_smem_limits(per_warp * kNoAllocWarps)) || (e = decide_resident_ctas(c.dec_chunk, &c.dec_grid)) ||
       (e = launch_records(d.ncells, d.nspecies, c.cc, d.T_keV, d.n_ion, c.rec, c.err, st)) ||
       (e = launch_moments(d.ncells, to_ptrs(d.electrons), c.mom, st)) ||
       (e = launch_step(PH_ALL, A, kNoAllocWarps, st)) ||

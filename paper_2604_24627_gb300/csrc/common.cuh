@@ -81,6 +81,9 @@ enum {
 // Device error flag bits.
 enum { ERR_CAPACITY = 1, ERR_NUMERIC = 2 };
 
+// Rows of per-CTA event counters (CTAs share rows beyond this).
+constexpr int kCounterRows = 4096;
+
 // Constants folded on the host (binary64) for the binary32 record.
 struct CellConst {
   int nspecies;
@@ -344,13 +347,16 @@ struct StepArgs {
   double* tally;          // [3 * nbins + 6]
   int nbins;
   float inv_dE_bin;
-  unsigned long long* counters;  // [gridDim * kNumCounters]
+  unsigned long long* counters;  // [ctr_rows * kNumCounters]
+  int ctr_rows;                  // CTA b adds to row b % ctr_rows
   uint32_t *bitsA, *bitsG, *bitsE;  // per-cell "needs a full decision" bit masks
   int Wa, Wg, We;                   // words per cell of each mask
   uint4 *recA, *recG;               // full decisions of flagged slots (slot-indexed)
   uint32_t* recE;
   int* err;
   int dec_grid;   // CTAs of the persistent decision kernel
+  int dec_chunk;  // cells per chunk of a decision warp: 2, 4 or 8
+  uint32_t* step_dev;  // NULL, or the device step counter of a replayed graph
   CellConst cc;
 };
 

@@ -329,7 +329,7 @@ __device__ __forceinline__ void flag_quad(uint32_t* bits, int W, int cell, int q
 }
 
 // A persistent grid of warps. Warp i owns the chunks i, i + nwarps, ... of
-// kChunk consecutive cells and, per chunk and species, gives the chunk's quads
+// C consecutive cells and, per chunk and species, gives the chunk's quads
 // to its lanes as one flat range (lane per quad, cell-major), so uneven counts
 // still fill the lanes. Slots that the guards cannot clear go to the warp's
 // own list in shared memory, which carries over from chunk to chunk and is
@@ -337,8 +337,9 @@ __device__ __forceinline__ void flag_quad(uint32_t* bits, int W, int cell, int q
 // barrier is needed. List order does not matter: records are indexed by slot.
 constexpr int kDecThreads = 256;
 constexpr int kDecWarps = kDecThreads / 32;
-constexpr int kChunk = AXPIC_DEC_CHUNK;
-static_assert(kChunk >= 1 && kChunk <= 32, "cells per decision chunk");
+// Cells per chunk: a launch-shape choice (2, 4 or 8), picked per context.
+constexpr int kChunkDefault = AXPIC_DEC_CHUNK;
+static_assert(kChunkDefault == 2 || kChunkDefault == 4 || kChunkDefault == 8, "cells per decision chunk");
 constexpr int kListCap = 32 + 4 * 32;  // < 32 pending + one pass of flags
 
 // Per-warp lists: {cell, slot, decision word(s)}.
@@ -349,29 +350,32 @@ struct DecLists {
 
 // Flat quad range of a chunk: lanes < nc hold their cell's slot count n; on
 // return every lane holds its cell's first quad (qoff), the starts of cells
-// 1..kChunk-1 (qo, cells beyond nc start at the total) and the total.
+// 1..C-1 (qo, cells beyond nc start at the total) and the total.
+template <int C>
 struct QuadRange {
   int qoff, total;
-  int qo[kChunk];
+  int qo[C];
 };
 
-__device__ __forceinline__ QuadRange quad_range(int n, int lane, int nc) {
-  QuadRange R;
+template <int C>
+__device__ __forceinline__ QuadRange<C> quad_range(int n, int lane, int nc) {
+  QuadRange<C> R;
   const int nq = lane < nc ? (n + 3) >> 2 : 0;
   R.qoff = warp_excl_scan(nq, &R.total);
 #pragma unroll
-  for (int c = 0; c < kChunk; ++c) R.qo[c] = __shfl_sync(kFull, R.qoff, c);
+  for (int c = 0; c < C; ++c) R.qo[c] = __shfl_sync(kFull, R.qoff, c);
 #pragma unroll
-  for (int c = 0; c < kChunk; ++c)
+  for (int c = 0; c < C; ++c)
     if (c >= nc) R.qo[c] = R.total;
   return R;
 }
 
 // Cell (in the chunk) of flat quad g.
-__device__ __forceinline__ int quad_cell(const QuadRange& R, int g) {
+template <int C>
+__device__ __forceinline__ int quad_cell(const QuadRange<C>& R, int g) {
   int lc = 0;
 #pragma unroll
-  for (int c = 1; c < kChunk; ++c) lc += g >= R.qo[c] ? 1 : 0;
+  for (int c = 1; c < C; ++c) lc += g >= R.qo[c] ? 1 : 0;
   return lc;
 }
 
@@ -428,7 +432,8 @@ __device__ __forceinline__ int list_drain(const StepArgs& A, const uint4* L, int
 // Electrons of a chunk (thermal-bath emission). With a common weight the
 // decision is u > exp(-lambda) with lambda shared by the cell; the full
 // decision of a flagged electron is a short Poisson inversion, taken here.
-__device__ __forceinline__ void electron_chunk(const StepArgs& A, int c0, int nc, int lane) {
+template <int C>
+__device__ __forceinline__ void electron_chunk(const StepArgs& A, uint32_t step, int c0, int nc, int lane) {
   const int mask = A.mask;
   const bool eC = mask & AXPIC_CH_COMPTON, eB = mask & AXPIC_CH_BREMS;
   int n = 0, thr = 0;
@@ -451,7 +456,7 @@ __device__ __forceinline__ void electron_chunk(const StepArgs& A, int c0, int nc
       thr = (int)floorf(__fsub_rn(__fmul_rn(expf(-lsum), 8388608.0f), 0.5f));
     }
   }
-  const QuadRange R = quad_range(n, lane, nc);
+  const QuadRange<C> R = quad_range<C>(n, lane, nc);
   for (int g0 = 0; g0 < R.total; g0 += 32) {
     const int g = g0 + lane;
     const int lc = quad_cell(R, g);
@@ -466,7 +471,7 @@ __device__ __forceinline__ void electron_chunk(const StepArgs& A, int c0, int nc
     const int cell = c0 + lc;
     const int q = g - qb;
     const int nj = min(4, nn - 4 * q);
-    const uint4 r = philox4x32_10(make_uint4(A.step, A.cell_base + (uint32_t)cell, (uint32_t)q, S_EMIT_E << 24), A.rk);
+    const uint4 r = philox4x32_10(make_uint4(step, A.cell_base + (uint32_t)cell, (uint32_t)q, S_EMIT_E << 24), A.rk);
     const long b = (long)cell * A.e.cap + 4 * q;
     uint32_t nib = 0;
     if (cwu > 0.f) {
@@ -503,7 +508,9 @@ __device__ __forceinline__ void electron_chunk(const StepArgs& A, int c0, int nc
 }
 
 // Photons of a chunk present at the start of the step (gamma->a).
-__device__ __forceinline__ int photon_chunk(const StepArgs& A, int c0, int nc, int lane, uint4* L, int pend) {
+template <int C>
+__device__ __forceinline__ int photon_chunk(const StepArgs& A, uint32_t step, int c0, int nc, int lane, uint4* L,
+                                            int pend) {
   int n = 0;
   float c_s = 0.f, ap = 0.f;
   if (lane < nc) {
@@ -514,7 +521,7 @@ __device__ __forceinline__ int photon_chunk(const StepArgs& A, int c0, int nc, i
     c_s = kMeC2f * kMeC2f * __ldg(rec + R_FOURK2);
     ap = __ldg(rec + R_AP);
   }
-  const QuadRange R = quad_range(n, lane, nc);
+  const QuadRange<C> R = quad_range<C>(n, lane, nc);
   for (int g0 = 0; g0 < R.total; g0 += 32) {
     const int g = g0 + lane;
     const int lc = quad_cell(R, g);
@@ -530,7 +537,7 @@ __device__ __forceinline__ int photon_chunk(const StepArgs& A, int c0, int nc, i
       const int nj = min(4, nn - 4 * q);
       const long b = (long)cell * A.g.cap + 4 * q;
       const float4 w4 = ld4(A.g.w + b), x4 = ld4(A.g.px + b), y4 = ld4(A.g.py + b), z4 = ld4(A.g.pz + b);
-      r = philox4x32_10(make_uint4(A.step, A.cell_base + (uint32_t)cell, (uint32_t)q, S_PRIM_FWD << 24), A.rk);
+      r = philox4x32_10(make_uint4(step, A.cell_base + (uint32_t)cell, (uint32_t)q, S_PRIM_FWD << 24), A.rk);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float px = f4(x4, j), py = f4(y4, j), pz = f4(z4, j);
@@ -546,7 +553,9 @@ __device__ __forceinline__ int photon_chunk(const StepArgs& A, int c0, int nc, i
 }
 
 // Axions of a chunk present at the start of the step: a->gamma and absorption.
-__device__ __forceinline__ int axion_chunk(const StepArgs& A, int c0, int nc, int lane, uint4* L, int pend) {
+template <int C>
+__device__ __forceinline__ int axion_chunk(const StepArgs& A, uint32_t step, int c0, int nc, int lane, uint4* L,
+                                           int pend) {
   const int mask = A.mask;
   const bool prim = mask & AXPIC_CH_PRIMAKOFF;
   const bool bath = mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS);
@@ -563,7 +572,7 @@ __device__ __forceinline__ int axion_chunk(const StepArgs& A, int c0, int nc, in
     r_bc = __ldg(rec + R_BC);
     r_bb = __ldg(rec + R_BB);
   }
-  const QuadRange R = quad_range(n, lane, nc);
+  const QuadRange<C> R = quad_range<C>(n, lane, nc);
   for (int g0 = 0; g0 < R.total; g0 += 32) {
     const int g = g0 + lane;
     const int lc = quad_cell(R, g);
@@ -583,8 +592,8 @@ __device__ __forceinline__ int axion_chunk(const StepArgs& A, int c0, int nc, in
       const uint32_t gcell = A.cell_base + (uint32_t)cell;
       const long b = (long)cell * A.a.cap + 4 * q;
       const float4 w4 = ld4(A.a.w + b), x4 = ld4(A.a.px + b), y4 = ld4(A.a.py + b), z4 = ld4(A.a.pz + b);
-      if (prim) rP = philox4x32_10(make_uint4(A.step, gcell, (uint32_t)q, S_PRIM_INV << 24), A.rk);
-      if (bath) rA = philox4x32_10(make_uint4(A.step, gcell, (uint32_t)q, S_ABSORB << 24), A.rk);
+      if (prim) rP = philox4x32_10(make_uint4(step, gcell, (uint32_t)q, S_PRIM_INV << 24), A.rk);
+      if (bath) rA = philox4x32_10(make_uint4(step, gcell, (uint32_t)q, S_ABSORB << 24), A.rk);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float px = f4(x4, j), py = f4(y4, j), pz = f4(z4, j);
@@ -611,18 +620,24 @@ enum : int { DK_ELECTRON = 1, DK_PHOTON = 2, DK_AXION = 4 };
 #define AXPIC_DEC_MIN_CTAS 4
 #endif
 
+// The step index of this call: from the device counter when the step runs
+// inside a replayed graph, else the launch argument.
+__device__ __forceinline__ uint32_t step_of(const StepArgs& A) { return A.step_dev ? *A.step_dev : A.step; }
+
+template <int C>
 __global__ void __launch_bounds__(kDecThreads, AXPIC_DEC_MIN_CTAS) decide_kernel(StepArgs A, int kinds) {
   __shared__ DecLists L;
   const int lane = lane_id(), wid = threadIdx.x >> 5;
+  const uint32_t step = step_of(A);
   const int nwarps = gridDim.x * kDecWarps;
-  const int nchunks = (A.ncells + kChunk - 1) / kChunk;
+  const int nchunks = (A.ncells + C - 1) / C;
   int pa = 0, pg = 0;
   for (int ch = blockIdx.x * kDecWarps + wid; ch < nchunks; ch += nwarps) {
-    const int c0 = ch * kChunk;
-    const int nc = min(kChunk, A.ncells - c0);
-    if (kinds & DK_ELECTRON) electron_chunk(A, c0, nc, lane);
-    if (kinds & DK_PHOTON) pg = photon_chunk(A, c0, nc, lane, L.g[wid], pg);
-    if (kinds & DK_AXION) pa = axion_chunk(A, c0, nc, lane, L.a[wid], pa);
+    const int c0 = ch * C;
+    const int nc = min(C, A.ncells - c0);
+    if (kinds & DK_ELECTRON) electron_chunk<C>(A, step, c0, nc, lane);
+    if (kinds & DK_PHOTON) pg = photon_chunk<C>(A, step, c0, nc, lane, L.g[wid], pg);
+    if (kinds & DK_AXION) pa = axion_chunk<C>(A, step, c0, nc, lane, L.a[wid], pa);
   }
   if (lane < pg) photon_full(A, L.g[wid][lane]);
   if (lane < pa) axion_full(A, L.a[wid][lane]);
@@ -892,7 +907,7 @@ __device__ __forceinline__ ElItem el_load(const StepArgs& A, long base, const ui
 // surviving axions, then the thermal-bath products in electron then event
 // order; removed slots are refilled from the tail.
 template <int PH>
-__device__ __forceinline__ void event_cell(const StepArgs& A, int cell, EvScratch& S, const Cnt& cnt) {
+__device__ __forceinline__ void event_cell(const StepArgs& A, uint32_t step, int cell, EvScratch& S, const Cnt& cnt) {
   const int lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t gcell = A.cell_base + (uint32_t)cell;
@@ -1199,7 +1214,7 @@ __device__ __forceinline__ void event_cell(const StepArgs& A, int cell, EvScratc
             const float wvC = cc ? A.w_a * facC : A.w_a;
             const float wvB = cb ? A.w_a * facB : A.w_a;
             for (int k = 0; k < K; ++k, ++off) {
-              const uint4 r = philox4x32_10(make_uint4(A.step, gcell, (uint32_t)t.slot, (S_EV_E << 24) | (uint32_t)k),
+              const uint4 r = philox4x32_10(make_uint4(step, gcell, (uint32_t)t.slot, (S_EV_E << 24) | (uint32_t)k),
                                             A.rk);
               const bool isC = u23(r.w) < fracC;
               const float3 dv = iso_dir(u23(r.x), u23(r.y));
@@ -1285,12 +1300,12 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
   if (cell < A.ncells) {
     const size_t bytes = ev_scratch_bytes(A.a.cap, A.g.cap, A.e.cap);
     EvScratch S = ev_carve(smem + wid * bytes, A.a.cap, A.g.cap, A.e.cap);
-    event_cell<PH>(A, cell, S, cnt);
+    event_cell<PH>(A, step_of(A), cell, S, cnt);
   }
   __syncwarp();
   if (lane < kNumCounters) {
     const unsigned long long v = warp_cnt[wid][lane];
-    if (v) atomicAdd(A.counters + (size_t)blockIdx.x * kNumCounters + lane, v);
+    if (v) atomicAdd(A.counters + (size_t)(blockIdx.x % A.ctr_rows) * kNumCounters + lane, v);
     if (lane == C_DROP && v) atomicOr(A.err, ERR_CAPACITY);
   }
 }
@@ -1314,6 +1329,9 @@ struct RemapJob {
 constexpr int kFeedbackThreads = 128;
 
 __global__ void __launch_bounds__(kFeedbackThreads) feedback_kernel(StepArgs A) {
+  // a replayed graph takes its step index from the device counter: the last
+  // kernel of the step advances it (no kernel of this launch reads it)
+  if (A.step_dev && blockIdx.x == 0 && threadIdx.x == 0) *A.step_dev += 1u;
   __shared__ RemapJob jobs[kFeedbackThreads];
   __shared__ RemapOut outs[kFeedbackThreads];
   __shared__ int njobs;
@@ -1485,10 +1503,10 @@ static cudaError_t launch_events(const StepArgs& A, int warps, cudaStream_t st) 
   return cudaGetLastError();
 }
 
-// Persistent decision grid: as many CTAs as the device holds at once (at most
-// one warp per chunk).
+// Persistent decision grid: A.dec_grid CTAs (what the device holds at once
+// for this chunk size), at most one warp per chunk.
 static int dec_blocks(const StepArgs& A) {
-  const int nchunks = (A.ncells + kChunk - 1) / kChunk;
+  const int nchunks = (A.ncells + A.dec_chunk - 1) / A.dec_chunk;
   const int need = (nchunks + kDecWarps - 1) / kDecWarps;
   return max(1, min(need, A.dec_grid));
 }
@@ -1505,7 +1523,17 @@ static int decide_kinds(const StepArgs& A, int phases) {
 static cudaError_t launch_decide(const StepArgs& A, int phases, cudaStream_t st) {
   const int kinds = decide_kinds(A, phases);
   if (kinds == 0) return cudaSuccess;
-  decide_kernel<<<dec_blocks(A), kDecThreads, 0, st>>>(A, kinds);
+  switch (A.dec_chunk) {
+    case 2:
+      decide_kernel<2><<<dec_blocks(A), kDecThreads, 0, st>>>(A, kinds);
+      break;
+    case 8:
+      decide_kernel<8><<<dec_blocks(A), kDecThreads, 0, st>>>(A, kinds);
+      break;
+    default:
+      decide_kernel<4><<<dec_blocks(A), kDecThreads, 0, st>>>(A, kinds);
+      break;
+  }
   return cudaGetLastError();
 }
 
@@ -1516,12 +1544,22 @@ static cudaError_t launch_feedback(const StepArgs& A, cudaStream_t st) {
 
 const char* step_kernel_names() { return "decide_kernel,event_kernel,feedback_kernel"; }
 
-cudaError_t decide_resident_ctas(int* out) {
+__global__ void set_step_kernel(uint32_t* p, uint32_t v) { *p = v; }
+
+cudaError_t launch_set_step(uint32_t* p, uint32_t v, cudaStream_t st) {
+  set_step_kernel<<<1, 1, 0, st>>>(p, v);
+  return cudaGetLastError();
+}
+
+cudaError_t decide_resident_ctas(int chunk, int* out) {
   int dev = 0, sms = 0, nb = 0;
   cudaError_t e;
-  if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) ||
-      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, decide_kernel, kDecThreads, 0)))
+  if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
     return e;
+  if (chunk == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, decide_kernel<2>, kDecThreads, 0);
+  else if (chunk == 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, decide_kernel<8>, kDecThreads, 0);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, decide_kernel<4>, kDecThreads, 0);
+  if (e) return e;
   *out = max(1, nb) * max(1, sms);
   return cudaSuccess;
 }

@@ -14,7 +14,11 @@ constexpr int kStepKernels = 3;
 // Comma-separated names of the kernels a PH_ALL step launches, in order.
 const char* step_kernel_names();
 cudaError_t set_step_smem_limits(size_t bytes);
-// CTAs of the decision kernel that the current device holds at once.
-cudaError_t decide_resident_ctas(int* out);
+// CTAs of the decision kernel (chunk of 2, 4 or 8 cells) that the current
+// device holds at once.
+cudaError_t decide_resident_ctas(int chunk, int* out);
+constexpr int kDefaultDecChunk = AXPIC_DEC_CHUNK;
+// Writes v to the device step counter *p (one thread).
+cudaError_t launch_set_step(uint32_t* p, uint32_t v, cudaStream_t st);
 
 }  // namespace axpic

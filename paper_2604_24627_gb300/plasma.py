@@ -111,6 +111,15 @@ class AxionPlasma:
     def step(self, step, mask=_lib.CH_ALL):
         _lib.axpic_step(self.ctx, step, mask)
 
+    def run_steps(self, first_step, nsteps, mask=_lib.CH_ALL):
+        """nsteps full steps by replaying a CUDA graph of one step."""
+        _lib.axpic_run_steps(self.ctx, first_step, nsteps, mask)
+
+    def autotune(self, step, trial_steps=3, mask=_lib.CH_ALL):
+        """Times the launch shapes on this state (restored afterwards) and keeps
+        the fastest; returns (ms per step, decide_chunk, event warps)."""
+        return _lib.axpic_autotune(self.ctx, step, trial_steps, mask)
+
     def tally(self):
         """(H [3, nbins] keV-weighted histogram, totals dict); clears the tally."""
         H = (ctypes.c_double * (3 * self.nbins))()

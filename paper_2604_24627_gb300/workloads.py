@@ -90,7 +90,12 @@ def config3(n=512, sigma=64.0):
 def config4(nboxes=4096, seed=0):
     """4096 independent uniform hydrogen boxes; cell counts log-normal (median
     256, sigma_ln = ln(16)/3) resampled into [16, 4096]; T ~ U[1, 5] keV;
-    n_e log-uniform in [1e24, 1e26]; 128 electrons + 64 photons per cell."""
+    n_e log-uniform in [1e24, 1e26]; 128 electrons + 64 photons per cell.
+    The boxes share one axion weight (the photon weight at 3 keV). In hot
+    boxes the photons are heavier than that weight: Primakoff exchange turns
+    them into axion macroparticles (up to about 0.42 * 64 * (5/3)^3 ~ 123 per
+    cell at equilibrium) and back into photons of the axion weight (up to
+    64 * (5/3)^3 ~ 296 per cell): slabs of 384 photon and 192 axion slots."""
     rng = np.random.default_rng(seed)
     counts = np.empty(nboxes, dtype=np.int64)
     for b in range(nboxes):
@@ -105,7 +110,7 @@ def config4(nboxes=4096, seed=0):
     ncells = int(counts.sum())
     n_ion = ne_box[box].reshape(ncells, 1)
     return Workload("c4-4096-boxes", ncells, (ncells,), T_box[box], n_ion, np.array([1.0]), np.array([A_H]),
-                    VOLUME_1UM3, 128, 64, 0, (128, 96, 96),
+                    VOLUME_1UM3, 128, 64, 0, (128, 384, 192),
                     params=dict(g_agg_GeV_inv=1e-10, g_ae=1e-13, dt_phys_s=9.93e11, T_mode=2, relax_r=0.1),
                     mask=7, steps=100, box_of_cell=box, w_a_over_w_gamma=1.0)
 

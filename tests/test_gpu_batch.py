@@ -1,0 +1,168 @@
+"""Batched boxes in one context, graph replay of the step and the launch-shape
+autotuner, through the C ABI: against the oracle and against plain step calls
+(needs a GB300 and the built library)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from parity_util import assert_species_close, oracle_step
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2604_24627_gb300 import AxionPlasma, _lib, workloads  # noqa: E402
+
+A_H, A_HE = 1.00794, 4.002602
+MIX_Z = np.array([1.0, 2.0])
+MIX_A = np.array([A_H, A_HE])
+
+
+def base_params(**kw):
+    prm = dict(g_agg_GeV_inv=1e-10, g_ae=1e-12, dt_phys_s=2e12, w_a=3.0e9, seed=0x1234_0000_0042,
+               T_mode=2, relax_r=0.1, diag_enable=1, tally_enable=1)
+    prm.update(kw)
+    return prm
+
+
+def make(ncells, prm, T=None, caps=(64, 192, 512), counts=(61, 37, 13)):
+    T = np.linspace(1.3, 5.0, ncells) if T is None else T
+    n = 6e25 / 1.1
+    n_ion = np.tile([[0.9 * n, 0.1 * n]], (ncells, 1))
+    pl = AxionPlasma(ncells, T, n_ion, MIX_Z, MIX_A, 1e-12, caps, prm)
+    pl.sample(*counts)
+    torch.cuda.synchronize()
+    return pl
+
+
+def state(pl):
+    """Host copy of everything a step changes: valid slots of every species,
+    counts, T, carried exchange."""
+    out = {}
+    for name, slab in pl.slabs.items():
+        cnt = slab.count[:pl.ncells].cpu().numpy()
+        out[name + ".count"] = cnt
+        valid = (np.arange(slab.capacity)[None, :] < cnt[:, None]).reshape(-1)
+        for f, t in slab.data.items():
+            out[name + "." + f] = t[:pl.ncells * slab.capacity].cpu().numpy()[valid]
+    out["T"] = pl.temperatures()
+    out["res"] = pl.residuals()
+    return out
+
+
+def assert_same(a, b, what):
+    assert a.keys() == b.keys()
+    for k in a:
+        assert a[k].shape == b[k].shape, (what, k, a[k].shape, b[k].shape)
+        diff = np.flatnonzero(a[k].view(np.uint8) != b[k].view(np.uint8))
+        assert diff.size == 0, (what, k, diff[:8])
+
+
+def test_run_steps_equals_step_calls():
+    prm = base_params()
+    a, b = make(40, prm), make(40, prm)
+    for s in range(5):
+        a.step(s, _lib.CH_ALL)
+    b.run_steps(0, 3, _lib.CH_ALL)   # captures the graph
+    b.run_steps(3, 2, _lib.CH_ALL)   # replays it from another first step
+    torch.cuda.synchronize()
+    assert_same(state(a), state(b), "graph replay")
+    _, ta = a.tally()
+    _, tb = b.tally()
+    for k in ta:  # FP64 tallies are sums by atomics: order-dependent rounding
+        assert abs(ta[k] - tb[k]) <= 1e-12 * abs(ta[k]), (k, ta[k], tb[k])
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("chunk,tpb", [(2, 32), (4, 64), (8, 128), (8, 64)])
+def test_launch_shapes_give_identical_results(chunk, tpb):
+    ref = make(29, base_params())
+    other = make(29, base_params(decide_chunk=chunk, threads_per_block=tpb))
+    for s in range(3):
+        ref.step(s, _lib.CH_ALL)
+        other.step(s, _lib.CH_ALL)
+    torch.cuda.synchronize()
+    assert_same(state(ref), state(other), "chunk %d tpb %d" % (chunk, tpb))
+    ref.close()
+    other.close()
+
+
+def test_autotune_restores_state_and_keeps_results():
+    prm = base_params()
+    a, b = make(48, prm), make(48, prm)
+    for s in range(2):
+        a.step(s, _lib.CH_ALL)
+        b.step(s, _lib.CH_ALL)
+    torch.cuda.synchronize()
+    before = state(a)
+    ms, chunk, warps = a.autotune(2, 2, _lib.CH_ALL)
+    assert ms > 0 and chunk in (2, 4, 8) and warps in (2, 4), (ms, chunk, warps)
+    assert_same(before, state(a), "after autotune")
+    for s in range(2, 4):
+        a.step(s, _lib.CH_ALL)
+        b.step(s, _lib.CH_ALL)
+    a.run_steps(4, 1, _lib.CH_ALL)
+    b.step(4, _lib.CH_ALL)
+    torch.cuda.synchronize()
+    assert_same(state(a), state(b), "tuned shape")
+    a.close()
+    b.close()
+
+
+def test_batched_boxes_match_oracle():
+    """Uneven hydrogen boxes with their own T and n_e concatenated in one
+    context: every cell's step equals the oracle's step of that cell."""
+    counts = np.array([1, 5, 2, 13, 3, 7])
+    T_box = np.array([1.2, 4.6, 2.5, 3.1, 1.8, 4.9])
+    ne_box = np.array([1e24, 8e25, 6e25, 2e25, 1e26, 5e24])
+    box = np.repeat(np.arange(len(counts)), counts)
+    ncells = int(counts.sum())
+    T = T_box[box]
+    n_ion = ne_box[box].reshape(ncells, 1)
+    Z, A = np.array([1.0]), np.array([A_H])
+    prm = base_params(g_ae=2e-12)
+    pl = AxionPlasma(ncells, T, n_ion, Z, A, 1e-12, (64, 192, 512), prm)
+    pl.sample(61, 37, 13)
+    pl.run_steps(0, 1, _lib.CH_ALL)
+    torch.cuda.synchronize()
+    before = [pl.cell(c) for c in range(ncells)]
+    T_before = pl.temperatures().copy()
+    res_before = pl.residuals()
+    pl.run_steps(1, 1, _lib.CH_ALL)
+    torch.cuda.synchronize()
+    diag = pl.cell_diag()
+    for c in range(ncells):
+        got = pl.cell(c)
+        parts, tally, fb = oracle_step(before[c], T_before[c], n_ion[c], Z, A, prm, 1, c, _lib.CH_ALL,
+                                       res=res_before[c])
+        what = "box %d cell %d" % (box[c], c)
+        assert_species_close(got["a"], parts["a"], what + " axions")
+        assert_species_close(got["g"], parts["g"], what + " photons")
+        assert abs(diag[c][0] - tally.dE) <= 1e-5 * tally.gross_E + 1e-30, (what, diag[c][0], tally.dE)
+    _, tot = pl.tally()
+    assert tot["dropped"] == 0
+    pl.close()
+
+
+def test_c4_workload_slice_runs():
+    """A slice of the 4096-box workload (first 12 boxes) through autotune and
+    graph replay: populations stay within the slabs and every cell keeps its
+    box's temperature range."""
+    w = workloads.config4(nboxes=12, seed=3)
+    prm = dict(w.params)
+    prm["w_a"] = float(np.float32(workloads.photon_weight(3.0, w.volume_cm3, w.n_ph)))
+    prm["tally_enable"] = 0
+    pl = AxionPlasma(w.ncells, w.T_keV, w.n_ion, w.Z, w.A, w.volume_cm3, w.caps, prm)
+    pl.sample(w.n_el, w.n_ph, w.n_ax)
+    pl.autotune(0, 2, w.mask)
+    pl.run_steps(0, 10, w.mask)
+    torch.cuda.synchronize()
+    _, tot = pl.tally()
+    assert tot["dropped"] == 0
+    cnt = pl.counts()
+    assert cnt["electrons"].min() == w.n_el and cnt["axions"].max() <= w.caps[2]
+    assert np.all(np.isfinite(pl.temperatures()))
+    pl.close()
