@@ -17,5 +17,8 @@ Parity status per function (details in each module's header):
 * poisson       - pinned (scipy Poisson CDF, pmf chi-square)
 * step          - pinned (conservation identities, steady states, unbiasedness)
 * tally         - pinned (normalisation, closed forms)
+* surrogate     - pinned (quantiles and emissivity integrals by scipy
+                  quadrature, Primakoff limits, Debye map, MLP gradients by
+                  finite differences, Adam's first step)
 """
-from . import constants, philox, spectra, plasma, poisson, step, tally  # noqa: F401
+from . import constants, philox, spectra, plasma, poisson, step, surrogate, tally  # noqa: F401

@@ -1,0 +1,219 @@
+"""The spectral surrogate's target function and its MLP, in FP64.
+
+Test infrastructure only (imported by tests/ and smoke()).
+
+What is approximated. For a single-ion plasma of charge Z (n_i = n_e / Z; A
+of hydrogen or helium-4), Debye screening, ions as Primakoff targets, and the
+axion couplings set to 1 (g_agg = 1 GeV^-1, g_ae = 1: the coupling squared is
+factored out), the state (T, n_e, Z) is fixed by (kappa/T, n_e, Z):
+T^3 = 4 pi alpha (hbar c)^3 n_e (1 + Z) / (kappa/T)^2 (Sec. II.F, Debye kappa
+with n_eff = n_e + Z^2 n_i). At x = omega / T the 96 outputs are, per channel
+c in (Primakoff, Compton-like, bremsstrahlung):
+* slot 0: ln(dQ_c/dx) in erg cm^-3 s^-1 per unit x, the energy emissivity
+  spectrum:
+  - Compton-like: Q_C x^5 / (e^x - 1) / (Gamma(6) zeta(6)) (Sec. II.G);
+  - bremsstrahlung: Q_B x^a e^-x / Gamma(a + 1) (Sec. II.H), with the two
+    [1 - c eta] brackets floored at 1e-3 (the paper's fit turns negative at
+    high eta; cells there are outside the trusted region);
+  - Primakoff: E Gamma(E) n_gamma(E) T with the screened rate of Eqs.
+    prim_xs, prim_rate and the Planck photon density of Sec. II.G.
+* slots 1..31: the quantiles x(u_j), u_j = j/32, of the channel's number
+  spectrum dQ_c/dx / x restricted to [0.05, 20] (the end points x(0) = 0.05
+  and x(1) = 20 are fixed and not outputs).
+
+The network (4 -> 64 -> 64 -> 96, tanh hidden layers) sees normalised features
+(ln x, ln(kappa/T), log10 n_e, Z) and predicts normalised outputs
+z = (y - mu) / sigma; mu and sigma are per-output constants.
+
+Pinned by: the Compton-like and bremsstrahlung quantiles against the
+closed-form inverse CDFs of the spectra module (Bose integrals, scipy's
+incomplete gamma), the emissivity integrals int dQ/dx dx = Q_C, Q_B (scipy
+quadrature), the Primakoff spectrum against a direct quadrature of
+E Gamma n_gamma, the temperature map against the Debye formula of
+plasma.cell_state, and the MLP gradients against central finite differences.
+"""
+import math
+
+import numpy as np
+from scipy import integrate, special
+
+from . import constants as K
+from . import plasma, spectra
+
+X_LO, X_HI = 0.05, 20.0
+KT_LO, KT_HI = 0.012, 41.0
+NE_LO, NE_HI = 1e23, 1e26
+T_LO, T_HI = 0.5, 10.0
+N_KNOTS = 31
+U_KNOTS = np.arange(1, 32) / 32.0
+N_OUT = 96
+CHANNELS = ("primakoff", "compton", "brems")
+LAYERS = (4, 64, 64, 96)
+
+
+# ------------------------------------------------------------------ domain
+
+def temperature(kT, ne, Z):
+    """T [keV] of a single-ion plasma with Debye kappa/T = kT."""
+    return (K.FOUR_PI * K.ALPHA_EM * K.HBARC_KEV_CM ** 3 * ne * (1.0 + Z) / kT ** 2) ** (1.0 / 3.0)
+
+
+def kappa_over_T(T, ne, Z):
+    return math.sqrt(K.FOUR_PI * K.ALPHA_EM * K.HBARC_KEV_CM ** 3 * ne * (1.0 + Z) / T ** 3)
+
+
+def cell(T, ne, Z, brems_shape=1.70):
+    """plasma.cell_state of the single-ion plasma with unit couplings."""
+    A = K.A_H if Z == 1 else K.A_HE
+    p = plasma.Params(g_agg_GeV_inv=1.0, g_ae=1.0, brems_gamma_shape=brems_shape)
+    return plasma.cell_state(T, np.array([ne / Z]), np.array([float(Z)]), np.array([A]), p), p
+
+
+def features(x, kT, ne, Z):
+    """Normalised network inputs, each in [-1, 1] on the domain."""
+    x, kT, ne, Z = (np.asarray(v, dtype=np.float64) for v in (x, kT, ne, Z))
+    f0 = np.log(x / X_LO) / math.log(X_HI / X_LO) * 2.0 - 1.0
+    f1 = np.log(kT / KT_LO) / math.log(KT_HI / KT_LO) * 2.0 - 1.0
+    f2 = (np.log10(ne) - 24.5) / 1.5
+    f3 = Z - 1.5
+    return np.stack(np.broadcast_arrays(f0, f1, f2, f3), axis=-1)
+
+
+# ------------------------------------------------------------------ targets
+
+def _brems_Q_floored(cs, a):
+    """Q_B with the [1 - c eta] brackets floored at 1e-3."""
+    T7, rho2, X = cs.T7, cs.rho2, cs.X_H
+    afac = (1.0 / K.FOUR_PI) / 1.60e-23
+    eZ = 0.150 * T7 ** 2.5 * rho2 * (1.0 + X) * afac * max(1e-3, 1.0 - 6.98e-2 * cs.eta)
+    ee = 0.150 * T7 ** 2.5 * rho2 * (1.0 + X) ** 2 / (2.0 * math.sqrt(2.0)) * afac * max(1e-3, 1.0 - 0.140 * cs.eta)
+    return cs.rho * (eZ + ee)
+
+
+def emissivity(channel, x, T, ne, Z, brems_shape=1.70):
+    """dQ_c/dx [erg cm^-3 s^-1 per unit x] at unit coupling."""
+    x = np.asarray(x, dtype=np.float64)
+    cs, p = cell(T, ne, Z, brems_shape)
+    if channel == "compton":
+        return cs.Q_C * x ** 5 / np.expm1(x) / (math.gamma(6.0) * special.zeta(6.0))
+    if channel == "brems":
+        a = brems_shape
+        return _brems_Q_floored(cs, a) * np.exp(a * np.log(x) - x - special.gammaln(a + 1.0))
+    if channel == "primakoff":
+        E = x * T
+        n_gamma = E ** 2 / (math.pi ** 2 * K.HBARC_KEV_CM ** 3) / np.expm1(x)     # per keV per cm^3
+        return E * plasma.primakoff_rate(cs, E) * n_gamma * T * K.KEV_ERG
+    raise ValueError(channel)
+
+
+def _number_quantiles(pdf_fn, n_grid=40001):
+    """Quantiles u_j of a number pdf on [X_LO, X_HI]: cumulative trapezoid
+    sums on a fine grid in ln x (40001 points), then linear inversion of the
+    monotone cumulative."""
+    t = np.linspace(math.log(X_LO), math.log(X_HI), n_grid)
+    x = np.exp(t)
+    f = pdf_fn(x) * x                      # d(number)/d(ln x)
+    h = t[1] - t[0]
+    cum = np.concatenate([[0.0], np.cumsum((f[:-1] + f[1:]) * 0.5 * h)])
+    cum /= cum[-1]
+    return np.interp(U_KNOTS, cum, x)
+
+
+def quantiles(channel, T, ne, Z, brems_shape=1.70):
+    """x(u_j), j = 1..31, of channel c's number spectrum on [X_LO, X_HI]."""
+    if channel == "compton":
+        F = spectra.compton_cdf
+        lo, hi = F(X_LO), F(X_HI)
+        return spectra.compton_icdf(lo + U_KNOTS * (hi - lo))
+    if channel == "brems":
+        a = brems_shape
+        lo, hi = spectra.gamma_cdf(a, X_LO), spectra.gamma_cdf(a, X_HI)
+        return spectra.gamma_icdf(a, lo + U_KNOTS * (hi - lo))
+    if channel == "primakoff":
+        return _number_quantiles(lambda x: emissivity("primakoff", x, T, ne, Z) / x)
+    raise ValueError(channel)
+
+
+def targets(x, kT, ne, Z, brems_shape=1.70):
+    """The 96 outputs at one (x, kappa/T, n_e, Z)."""
+    T = temperature(kT, ne, Z)
+    y = np.empty(N_OUT)
+    for c, ch in enumerate(CHANNELS):
+        y[32 * c] = math.log(float(emissivity(ch, x, T, ne, Z, brems_shape)))
+        y[32 * c + 1:32 * c + 32] = quantiles(ch, T, ne, Z, brems_shape)
+    return y
+
+
+def in_domain(kT, ne, Z):
+    T = temperature(kT, ne, Z)
+    return T_LO <= T <= T_HI and NE_LO <= ne <= NE_HI
+
+
+# ------------------------------------------------------------------ MLP
+
+def init_params(rng):
+    """Glorot-uniform weights, zero biases (FP64)."""
+    P = {}
+    for i, (a, b) in enumerate(zip(LAYERS[:-1], LAYERS[1:]), start=1):
+        lim = math.sqrt(6.0 / (a + b))
+        P["W%d" % i] = rng.uniform(-lim, lim, (a, b))
+        P["b%d" % i] = np.zeros(b)
+    return P
+
+
+def bf16(a):
+    """Round to bfloat16 (round to nearest, ties to even), returned as FP64."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(P, X, bf16_mma=False):
+    """Normalised outputs z and the cache for backward. With bf16_mma the
+    operands of layers 2 and 3 are rounded to bfloat16 (the GPU's tensor-core
+    inputs); accumulation stays FP64."""
+    q = bf16 if bf16_mma else (lambda a: a)
+    a1 = X @ P["W1"] + P["b1"]
+    h1 = np.tanh(a1)
+    a2 = q(h1) @ q(P["W2"]) + P["b2"]
+    h2 = np.tanh(a2)
+    z = q(h2) @ q(P["W3"]) + P["b3"]
+    return z, (X, h1, h2)
+
+
+def loss(P, X, Zt, bf16_mma=False):
+    """Mean over samples of the summed squared error of the normalised
+    outputs."""
+    z, _ = forward(P, X, bf16_mma)
+    return float(np.sum((z - Zt) ** 2) / len(X))
+
+
+def backward(P, X, Zt, bf16_mma=False):
+    """Gradients of loss() with respect to every parameter (the bfloat16
+    rounding, when on, is treated as identity in the derivative, as the GPU's
+    straight-through training does)."""
+    q = bf16 if bf16_mma else (lambda a: a)
+    z, (X, h1, h2) = forward(P, X, bf16_mma)
+    n = len(X)
+    dz = 2.0 * (z - Zt) / n
+    G = {"W3": q(h2).T @ q(dz), "b3": dz.sum(0)}
+    dh2 = q(dz) @ q(P["W3"]).T
+    da2 = dh2 * (1.0 - h2 ** 2)
+    G["W2"] = q(h1).T @ q(da2)
+    G["b2"] = da2.sum(0)
+    dh1 = q(da2) @ q(P["W2"]).T
+    da1 = dh1 * (1.0 - h1 ** 2)
+    G["W1"] = X.T @ da1
+    G["b1"] = da1.sum(0)
+    return G
+
+
+def adam(P, G, M, V, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step (bias-corrected moments) in place; t counts from 1."""
+    for k in P:
+        M[k] = b1 * M[k] + (1.0 - b1) * G[k]
+        V[k] = b2 * V[k] + (1.0 - b2) * G[k] ** 2
+        mh = M[k] / (1.0 - b1 ** t)
+        vh = V[k] / (1.0 - b2 ** t)
+        P[k] = P[k] - lr * mh / (np.sqrt(vh) + eps)
