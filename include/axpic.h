@@ -317,6 +317,40 @@ axpic_status axpic_profile_end(axpic_ctx *ctx, double *ms_out, int32_t *steps_ou
  * NULL context. */
 const char *axpic_step_kernel_names(const axpic_ctx *ctx);
 
+/* ---------------------------------------------------------------------------
+ * The spectral surrogate's network: MLP 4 -> 64 -> 64 -> 96 with tanh hidden
+ * layers, FP32 master parameters, bfloat16 tensor-core products with FP32
+ * accumulation (layers 2 and 3 and every backward product; layer 1, K = 4,
+ * on the CUDA cores). Not part of the paper's method: a learned stand-in for
+ * the per-channel spectral emissivity and inverse CDF (see
+ * axpic_surrogate_targets). Inputs are the normalised features
+ * (ln x, ln(kappa/T), log10 n_e, Z) of axpic_surrogate_features; outputs are
+ * normalised (z = (y - mu) / sigma). Calls are ordered on the stream given at
+ * creation; those that return host data synchronise it.
+ * ------------------------------------------------------------------------- */
+typedef struct axpic_mlp axpic_mlp;
+#define AXPIC_MLP_PARAMS 10720 /* W1[4][64], b1[64], W2[64][64], b2[64], W3[64][96], b3[96] */
+
+/* Creates a network with zero parameters on `stream` (a cudaStream_t). */
+axpic_status axpic_mlp_create(axpic_mlp **out, void *stream);
+/* Copies AXPIC_MLP_PARAMS host floats in (and resets the Adam state) or out. */
+axpic_status axpic_mlp_set_params(axpic_mlp *m, const float *params);
+axpic_status axpic_mlp_get_params(axpic_mlp *m, float *params);
+/* Z[n][96] (device) = network(X[n][4]) (device); asynchronous. */
+axpic_status axpic_mlp_forward(axpic_mlp *m, const float *X, int32_t n, float *Z);
+/* Gradients of loss = sum over samples and outputs of (z - Zt)^2 / n with
+ * respect to every parameter, written to grads (host, AXPIC_MLP_PARAMS, may
+ * be NULL) with the loss to *loss_out (may be NULL). X, Zt: device. */
+axpic_status axpic_mlp_gradients(axpic_mlp *m, const float *X, const float *Zt, int32_t n, double *loss_out,
+                                 float *grads);
+/* One training step: gradients on (X, Zt), then Adam (beta 0.9, 0.999,
+ * eps 1e-8, bias-corrected) with learning rate lr. *loss_out (may be NULL,
+ * which keeps the call asynchronous) gets the loss before the update. */
+axpic_status axpic_mlp_train_step(axpic_mlp *m, const float *X, const float *Zt, int32_t n, float lr,
+                                  double *loss_out);
+axpic_status axpic_mlp_destroy(axpic_mlp *m);
+const char *axpic_mlp_last_error(const axpic_mlp *m);
+
 /* Wait for the stream and return the first latched device error, if any. */
 axpic_status axpic_sync(axpic_ctx *ctx);
 

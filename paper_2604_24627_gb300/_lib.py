@@ -65,6 +65,16 @@ class AxpicError(RuntimeError):
 _lib = None
 
 EXPORTS = {
+    "axpic_mlp_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
+    "axpic_mlp_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    "axpic_mlp_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    "axpic_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "axpic_mlp_gradients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)]),
+    "axpic_mlp_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.c_float, ctypes.POINTER(ctypes.c_double)]),
+    "axpic_mlp_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "axpic_mlp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "axpic_default_params": (None, [ctypes.POINTER(Params)]),
     "axpic_init_plasma": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(PlasmaDesc),
                                          ctypes.POINTER(Params), ctypes.c_void_p]),
@@ -237,3 +247,61 @@ def axpic_destroy(ctx):
 
 def axpic_version():
     return lib().axpic_version().decode()
+
+
+# ---------------------------------------------------------------- surrogate network
+MLP_PARAMS = 10720
+
+
+def _mlp_check(h, status):
+    if status != AXPIC_OK:
+        msg = lib().axpic_mlp_last_error(h)
+        raise AxpicError(status, msg.decode() if msg else "")
+
+
+def axpic_mlp_create(stream):
+    h = ctypes.c_void_p()
+    st = lib().axpic_mlp_create(ctypes.byref(h), stream)
+    if st != AXPIC_OK:
+        raise AxpicError(st, "axpic_mlp_create failed")
+    return h
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def axpic_mlp_set_params(h, params):
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == MLP_PARAMS
+    _mlp_check(h, lib().axpic_mlp_set_params(h, _fptr(p)))
+
+
+def axpic_mlp_get_params(h):
+    import numpy as np
+    p = np.empty(MLP_PARAMS, dtype=np.float32)
+    _mlp_check(h, lib().axpic_mlp_get_params(h, _fptr(p)))
+    return p
+
+
+def axpic_mlp_forward(h, X_ptr, n, Z_ptr):
+    _mlp_check(h, lib().axpic_mlp_forward(h, X_ptr, n, Z_ptr))
+
+
+def axpic_mlp_gradients(h, X_ptr, Zt_ptr, n):
+    import numpy as np
+    g = np.empty(MLP_PARAMS, dtype=np.float32)
+    loss = ctypes.c_double()
+    _mlp_check(h, lib().axpic_mlp_gradients(h, X_ptr, Zt_ptr, n, ctypes.byref(loss), _fptr(g)))
+    return loss.value, g
+
+
+def axpic_mlp_train_step(h, X_ptr, Zt_ptr, n, lr, want_loss=True):
+    loss = ctypes.c_double()
+    _mlp_check(h, lib().axpic_mlp_train_step(h, X_ptr, Zt_ptr, n, lr, ctypes.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def axpic_mlp_destroy(h):
+    _mlp_check(h, lib().axpic_mlp_destroy(h))

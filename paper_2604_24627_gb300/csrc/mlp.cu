@@ -1,0 +1,510 @@
+// The spectral surrogate's MLP (4 -> 64 -> 64 -> 96, tanh hidden layers) on
+// the GPU: forward, backward and Adam. Layer 1 (K = 4) runs on the CUDA
+// cores; every other product, forward and backward, is a tile GEMM on the
+// 5th-generation tensor cores: operands staged by the CTA as bfloat16 in
+// shared memory (K-major, no swizzle), one elected thread issues
+// tcgen05.mma.kind::f16 with an FP32 accumulator in tensor memory, commits to
+// an mbarrier, and the CTA reads the tile back with tcgen05.ld.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "mlp.h"
+
+namespace axpic {
+
+// ---------------------------------------------------------------- tcgen05 primitives
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading (K)
+// and stride (M/N) byte offsets between 8x16-byte core matrices.
+__device__ __forceinline__ uint64_t mma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+  d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of this architecture
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B bfloat16, both K-major.
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Bounded wait on an mbarrier phase; false when the bound ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Core-matrix layout of a rows x kc bfloat16 tile (kc a multiple of 16):
+// element (r, k) of core matrix (r / 8, k / 8), 8 elements per 16-byte row.
+__device__ __forceinline__ int core_off(int r, int k, int kc) {
+  return ((r >> 3) * (kc >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+// ---------------------------------------------------------------- tile GEMM
+// C (M x N) = A (M x K) . B (K x N) on tiles of 128 rows, split along K into
+// chunks of kc. A(m, k) = transA ? A[k * lda + m] : A[m * lda + k], and
+// B(k, n) likewise. Store mode (accumulate = 0, one K chunk): C = AB + bias,
+// then tanh when act = 1. Accumulate mode: C += AB by atomics (split-K).
+struct GemmArgs {
+  const float* A;
+  long lda;
+  int transA;
+  const float* B;
+  long ldb;
+  int transB;
+  float* C;
+  long ldc;
+  const float* bias;
+  int M, N, K, kc, accumulate, act;
+  int* err;
+};
+
+constexpr int kGemmThreads = 128;
+constexpr int kGemmMaxN = 128;
+constexpr int kGemmMaxKc = 128;
+
+__global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(GemmArgs g) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(sm);
+  __nv_bfloat16* sB = sA + 128 * g.kc;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * 128;
+  const int k0 = blockIdx.y * g.kc;
+  const uint32_t ncols = g.N <= 32 ? 32u : (g.N <= 64 ? 64u : 128u);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  // stage A (128 x kc) and B^T (N x kc) as bfloat16, zero outside the matrix
+  for (int i = tid; i < 128 * g.kc; i += kGemmThreads) {
+    const int r = i / g.kc, k = i - r * g.kc;
+    const int m = m0 + r, kk = k0 + k;
+    float v = 0.f;
+    if (m < g.M && kk < g.K) v = g.transA ? g.A[(long)kk * g.lda + m] : g.A[(long)m * g.lda + kk];
+    sA[core_off(r, k, g.kc)] = __float2bfloat16_rn(v);
+  }
+  for (int i = tid; i < g.N * g.kc; i += kGemmThreads) {
+    const int n = i / g.kc, k = i - n * g.kc;
+    const int kk = k0 + k;
+    float v = 0.f;
+    if (kk < g.K) v = g.transB ? g.B[(long)n * g.ldb + kk] : g.B[(long)kk * g.ldb + n];
+    sB[core_off(n, k, g.kc)] = __float2bfloat16_rn(v);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  if (tid == 0) {
+    const uint32_t lbo = 128, sbo = (uint32_t)(g.kc >> 3) * 128u;
+    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+    const uint32_t idesc = mma_idesc(128, g.N);
+    for (int s = 0; s < g.kc / 16; ++s)
+      mma_bf16(tmem, mma_desc(a0 + s * 256, lbo, sbo), mma_desc(b0 + s * 256, lbo, sbo), idesc, s > 0 ? 1u : 0u);
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&bar))
+                 : "memory");
+  }
+  const bool ok = mbar_wait(&bar, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!ok) {
+    // flag it, give the tensor core a second bounded wait, then free the
+    // tensor memory and return
+    if (tid == 0) atomicOr(g.err, 1);
+    mbar_wait(&bar, 0);
+  } else {
+    const int m = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < g.N; c0 += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (m < g.M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = c0 + j;
+          float v = __uint_as_float(r[j]);
+          if (g.accumulate) {
+            atomicAdd(g.C + (long)m * g.ldc + n, v);
+          } else {
+            if (g.bias) v += g.bias[n];
+            if (g.act == 1) v = tanhf(v);
+            g.C[(long)m * g.ldc + n] = v;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
+static size_t gemm_smem(int N, int kc) { return (size_t)(128 + N) * kc * sizeof(__nv_bfloat16); }
+
+cudaError_t gemm_tc(const GemmArgs& g0, cudaStream_t st) {
+  GemmArgs g = g0;
+  if (g.M <= 0) return cudaSuccess;
+  if (g.N < 16 || g.N > kGemmMaxN || (g.N & 15) || g.K <= 0) return cudaErrorInvalidValue;
+  if (!g.accumulate) g.kc = ((g.K + 15) / 16) * 16;
+  if (g.kc < 16 || g.kc > kGemmMaxKc || (g.kc & 15)) return cudaErrorInvalidValue;
+  const dim3 grid((g.M + 127) / 128, (g.K + g.kc - 1) / g.kc);
+  gemm_tc_kernel<<<grid, kGemmThreads, gemm_smem(g.N, g.kc), st>>>(g);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- element-wise pieces
+// h1 = tanh(X W1 + b1): K = 4, on the CUDA cores; one thread per output.
+__global__ void layer1_kernel(const float* __restrict__ X, const float* __restrict__ W1, const float* __restrict__ b1,
+                              float* __restrict__ H1, int n) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)n * 64) return;
+  const int r = (int)(i >> 6), j = (int)(i & 63);
+  const float* x = X + (long)r * 4;
+  float a = b1[j];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a = fmaf(x[k], W1[k * 64 + j], a);
+  H1[i] = tanhf(a);
+}
+
+// dz = 2 (z - t) / n per element; the loss sum (z - t)^2 / n in FP64.
+__global__ void out_grad_kernel(const float* __restrict__ Zp, const float* __restrict__ Zt, float* __restrict__ dZ,
+                                long total, float inv_n, double* loss) {
+  double acc = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const float d = Zp[i] - Zt[i];
+    dZ[i] = 2.0f * d * inv_n;
+    acc += (double)d * (double)d;
+  }
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(loss, acc * (double)inv_n);
+}
+
+// d = d * (1 - h^2) (tanh derivative through its output).
+__global__ void tanh_back_kernel(float* __restrict__ D, const float* __restrict__ H, long total) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x)
+    D[i] *= 1.0f - H[i] * H[i];
+}
+
+// Column sums of an n x w matrix into g (bias gradients).
+__global__ void colsum_kernel(const float* __restrict__ D, int n, int w, float* __restrict__ g) {
+  const int j = blockIdx.x;
+  float acc = 0.f;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) acc += D[(long)r * w + j];
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+  __shared__ float part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += part[k];
+    g[j] += s;
+  }
+}
+
+// gW1 (4 x 64) += X^T dA1: one block per output column j, K = n.
+__global__ void w1_grad_kernel(const float* __restrict__ X, const float* __restrict__ dA1, int n,
+                               float* __restrict__ gW1) {
+  const int j = blockIdx.x;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const float d = dA1[(long)r * 64 + j];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = fmaf(X[(long)r * 4 + k], d, acc[k]);
+  }
+  __shared__ float part[4][32];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float a = acc[k];
+    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    if ((threadIdx.x & 31) == 0) part[k][threadIdx.x >> 5] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    float s = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[threadIdx.x][w];
+    gW1[threadIdx.x * 64 + j] += s;
+  }
+}
+
+// Adam with bias correction on the FP32 master parameters.
+__global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ M,
+                            float* __restrict__ V, int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float g = G[i];
+  const float m = b1 * M[i] + (1.f - b1) * g;
+  const float v = b2 * V[i] + (1.f - b2) * g * g;
+  M[i] = m;
+  V[i] = v;
+  P[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+}
+
+// ---------------------------------------------------------------- the network
+Mlp::~Mlp() {
+  void* bufs[] = {P, G, Ma, Va, h1, h2, z, dz, dh, err, loss};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+}
+
+cudaError_t Mlp::reserve(int n) {
+  if (n <= cap) return cudaSuccess;
+  void* bufs[] = {h1, h2, z, dz, dh};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  h1 = h2 = z = dz = dh = nullptr;
+  cudaError_t e;
+  if ((e = cudaMalloc(&h1, sizeof(float) * 64 * (size_t)n)) || (e = cudaMalloc(&h2, sizeof(float) * 64 * (size_t)n)) ||
+      (e = cudaMalloc(&z, sizeof(float) * 96 * (size_t)n)) || (e = cudaMalloc(&dz, sizeof(float) * 96 * (size_t)n)) ||
+      (e = cudaMalloc(&dh, sizeof(float) * 64 * (size_t)n)))
+    return e;
+  cap = n;
+  return cudaSuccess;
+}
+
+cudaError_t Mlp::init(cudaStream_t s) {
+  st = s;
+  cudaError_t e;
+  if ((e = cudaMalloc(&P, sizeof(float) * kMlpParams)) || (e = cudaMalloc(&G, sizeof(float) * kMlpParams)) ||
+      (e = cudaMalloc(&Ma, sizeof(float) * kMlpParams)) || (e = cudaMalloc(&Va, sizeof(float) * kMlpParams)) ||
+      (e = cudaMalloc(&err, sizeof(int))) || (e = cudaMalloc(&loss, sizeof(double))) ||
+      (e = cudaMemsetAsync(P, 0, sizeof(float) * kMlpParams, st)) ||
+      (e = cudaMemsetAsync(Ma, 0, sizeof(float) * kMlpParams, st)) ||
+      (e = cudaMemsetAsync(Va, 0, sizeof(float) * kMlpParams, st)) || (e = cudaMemsetAsync(err, 0, sizeof(int), st)))
+    return e;
+  const int smem = (int)gemm_smem(kGemmMaxN, kGemmMaxKc);
+  return cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+static GemmArgs store_gemm(const float* A, int K, const float* B, long ldb, int transB, float* C, int N,
+                           const float* bias, int act, int n, int* err) {
+  GemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.A = A;
+  g.lda = K;
+  g.B = B;
+  g.ldb = ldb;
+  g.transB = transB;
+  g.C = C;
+  g.ldc = N;
+  g.bias = bias;
+  g.M = n;
+  g.N = N;
+  g.K = K;
+  g.act = act;
+  g.err = err;
+  return g;
+}
+
+// C (rows x cols) += A^T B with A n x rows and B n x cols (weight gradients).
+static GemmArgs wgrad_gemm(const float* A, int rows, const float* B, int cols, float* C, int n, int* err) {
+  GemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.A = A;
+  g.lda = rows;
+  g.transA = 1;
+  g.B = B;
+  g.ldb = cols;
+  g.C = C;
+  g.ldc = cols;
+  g.M = rows;
+  g.N = cols;
+  g.K = n;
+  g.kc = 128;
+  g.accumulate = 1;
+  g.err = err;
+  return g;
+}
+
+cudaError_t Mlp::forward(const float* X, int n, float* out) {
+  cudaError_t e;
+  if ((e = reserve(n))) return e;
+  if (n == 0) return cudaSuccess;
+  const long t1 = (long)n * 64;
+  layer1_kernel<<<(unsigned)((t1 + 255) / 256), 256, 0, st>>>(X, W1(), b1(), h1, n);
+  if ((e = cudaGetLastError()) || (e = gemm_tc(store_gemm(h1, 64, W2(), 64, 0, h2, 64, b2(), 1, n, err), st)) ||
+      (e = gemm_tc(store_gemm(h2, 64, W3(), 96, 0, out ? out : z, 96, b3(), 0, n, err), st)))
+    return e;
+  return cudaSuccess;
+}
+
+cudaError_t Mlp::gradients(const float* X, const float* Zt, int n) {
+  cudaError_t e;
+  if ((e = forward(X, n, z))) return e;
+  if ((e = cudaMemsetAsync(G, 0, sizeof(float) * kMlpParams, st)) || (e = cudaMemsetAsync(loss, 0, sizeof(double), st)))
+    return e;
+  if (n == 0) return cudaSuccess;
+  const long tz = (long)n * 96, th = (long)n * 64;
+  out_grad_kernel<<<1024, 256, 0, st>>>(z, Zt, dz, tz, 1.0f / (float)n, loss);
+  // layer 3: gW3 = h2^T dz, gb3, dh2 = dz W3^T
+  if ((e = cudaGetLastError()) || (e = gemm_tc(wgrad_gemm(h2, 64, dz, 96, G + kOffW3, n, err), st))) return e;
+  colsum_kernel<<<96, 256, 0, st>>>(dz, n, 96, G + kOffB3);
+  if ((e = cudaGetLastError()) || (e = gemm_tc(store_gemm(dz, 96, W3(), 96, 1, dh, 64, nullptr, 0, n, err), st)))
+    return e;
+  // layer 2: da2 = dh2 (1 - h2^2), gW2 = h1^T da2, gb2, dh1 = da2 W2^T
+  tanh_back_kernel<<<1024, 256, 0, st>>>(dh, h2, th);
+  if ((e = cudaGetLastError()) || (e = gemm_tc(wgrad_gemm(h1, 64, dh, 64, G + kOffW2, n, err), st))) return e;
+  colsum_kernel<<<64, 256, 0, st>>>(dh, n, 64, G + kOffB2);
+  // h2 is free now: dh1 goes there
+  if ((e = cudaGetLastError()) || (e = gemm_tc(store_gemm(dh, 64, W2(), 64, 1, h2, 64, nullptr, 0, n, err), st)))
+    return e;
+  // layer 1: da1 = dh1 (1 - h1^2), gW1 = X^T da1, gb1
+  tanh_back_kernel<<<1024, 256, 0, st>>>(h2, h1, th);
+  w1_grad_kernel<<<64, 256, 0, st>>>(X, h2, n, G + kOffW1);
+  colsum_kernel<<<64, 256, 0, st>>>(h2, n, 64, G + kOffB1);
+  return cudaGetLastError();
+}
+
+cudaError_t Mlp::adam(float lr) {
+  ++t;
+  const float c1 = 1.0f - powf(0.9f, (float)t), c2 = 1.0f - powf(0.999f, (float)t);
+  adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, st>>>(P, G, Ma, Va, kMlpParams, lr, 0.9f, 0.999f, 1e-8f, c1, c2);
+  return cudaGetLastError();
+}
+
+}  // namespace axpic
+
+// ---------------------------------------------------------------- C ABI
+#include "axpic.h"
+#include <string>
+
+struct axpic_mlp {
+  axpic::Mlp m;
+  std::string last_error;
+};
+
+extern "C" {
+
+static axpic_status mlp_fail(axpic_mlp* h, cudaError_t e, const char* where) {
+  h->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return AXPIC_E_CUDA;
+}
+
+static axpic_status mlp_sync(axpic_mlp* h, const char* where) {
+  cudaError_t e = cudaStreamSynchronize(h->m.st);
+  if (e) return mlp_fail(h, e, where);
+  int herr = 0;
+  if ((e = cudaMemcpy(&herr, h->m.err, sizeof(int), cudaMemcpyDeviceToHost))) return mlp_fail(h, e, where);
+  if (herr) {
+    h->last_error = std::string(where) + ": a tensor-core wait ran out";
+    return AXPIC_E_TIMEOUT;
+  }
+  return AXPIC_OK;
+}
+
+axpic_status axpic_mlp_create(axpic_mlp** out, void* stream) {
+  if (!out) return AXPIC_E_INVALID;
+  *out = nullptr;
+  axpic_mlp* h = new axpic_mlp();
+  const cudaError_t e = h->m.init((cudaStream_t)stream);
+  if (e) {
+    fprintf(stderr, "axpic_mlp_create: %s\n", cudaGetErrorString(e));
+    delete h;
+    return AXPIC_E_CUDA;
+  }
+  *out = h;
+  return AXPIC_OK;
+}
+
+axpic_status axpic_mlp_set_params(axpic_mlp* h, const float* params) {
+  if (!h || !params) return AXPIC_E_INVALID;
+  cudaError_t e = cudaMemcpyAsync(h->m.P, params, sizeof(float) * axpic::kMlpParams, cudaMemcpyHostToDevice, h->m.st);
+  if (e) return mlp_fail(h, e, "axpic_mlp_set_params");
+  h->m.t = 0;
+  if ((e = cudaMemsetAsync(h->m.Ma, 0, sizeof(float) * axpic::kMlpParams, h->m.st)) ||
+      (e = cudaMemsetAsync(h->m.Va, 0, sizeof(float) * axpic::kMlpParams, h->m.st)))
+    return mlp_fail(h, e, "axpic_mlp_set_params");
+  return mlp_sync(h, "axpic_mlp_set_params");
+}
+
+axpic_status axpic_mlp_get_params(axpic_mlp* h, float* params) {
+  if (!h || !params) return AXPIC_E_INVALID;
+  const cudaError_t e =
+      cudaMemcpyAsync(params, h->m.P, sizeof(float) * axpic::kMlpParams, cudaMemcpyDeviceToHost, h->m.st);
+  if (e) return mlp_fail(h, e, "axpic_mlp_get_params");
+  return mlp_sync(h, "axpic_mlp_get_params");
+}
+
+axpic_status axpic_mlp_forward(axpic_mlp* h, const float* X, int32_t n, float* Z) {
+  if (!h || n < 0 || (n > 0 && (!X || !Z))) return AXPIC_E_INVALID;
+  const cudaError_t e = h->m.forward(X, n, Z);
+  if (e) return mlp_fail(h, e, "axpic_mlp_forward");
+  return AXPIC_OK;
+}
+
+axpic_status axpic_mlp_gradients(axpic_mlp* h, const float* X, const float* Zt, int32_t n, double* loss_out,
+                                 float* grads) {
+  if (!h || n < 0 || (n > 0 && (!X || !Zt))) return AXPIC_E_INVALID;
+  cudaError_t e = h->m.gradients(X, Zt, n);
+  if (e) return mlp_fail(h, e, "axpic_mlp_gradients");
+  if (grads && (e = cudaMemcpyAsync(grads, h->m.G, sizeof(float) * axpic::kMlpParams, cudaMemcpyDeviceToHost,
+                                    h->m.st)))
+    return mlp_fail(h, e, "axpic_mlp_gradients");
+  if (loss_out && (e = cudaMemcpyAsync(loss_out, h->m.loss, sizeof(double), cudaMemcpyDeviceToHost, h->m.st)))
+    return mlp_fail(h, e, "axpic_mlp_gradients");
+  return mlp_sync(h, "axpic_mlp_gradients");
+}
+
+axpic_status axpic_mlp_train_step(axpic_mlp* h, const float* X, const float* Zt, int32_t n, float lr,
+                                  double* loss_out) {
+  if (!h || n < 1 || !X || !Zt || !(lr > 0.f)) return AXPIC_E_INVALID;
+  cudaError_t e = h->m.gradients(X, Zt, n);
+  if (!e) e = h->m.adam(lr);
+  if (e) return mlp_fail(h, e, "axpic_mlp_train_step");
+  if (loss_out) {
+    if ((e = cudaMemcpyAsync(loss_out, h->m.loss, sizeof(double), cudaMemcpyDeviceToHost, h->m.st)))
+      return mlp_fail(h, e, "axpic_mlp_train_step");
+    return mlp_sync(h, "axpic_mlp_train_step");
+  }
+  return AXPIC_OK;
+}
+
+axpic_status axpic_mlp_destroy(axpic_mlp* h) {
+  if (!h) return AXPIC_E_INVALID;
+  const axpic_status s = mlp_sync(h, "axpic_mlp_destroy");
+  delete h;
+  return s;
+}
+
+const char* axpic_mlp_last_error(const axpic_mlp* h) { return h ? h->last_error.c_str() : "no network"; }
+
+}  // extern "C"
