@@ -120,7 +120,18 @@ typedef struct {
                                warp per cell); 0: default 128 */
   int32_t decide_chunk;     /* cells per chunk of a decision warp: 2, 4 or 8;
                                0: default 4 (launch shape, see axpic_autotune) */
-  int32_t reserved[6];
+  int32_t rate_model;       /* 0: closed forms (default); 1: exact FP32 table;
+                               2: surrogate network (axpic_set_surrogate) with
+                               the table where it is not trusted. Models 1 and
+                               2 take the full decisions' Primakoff and
+                               absorption rates and the emission energies from
+                               per-cell spectral records; they need one ion
+                               species with Z in {1, 2}, Debye screening and
+                               ions as Primakoff targets. Not part of the
+                               paper's method. */
+  int32_t sr_table_nkt;     /* table nodes in ln(kappa/T) (0: 64) */
+  int32_t sr_table_nne;     /* table nodes in log10 n_e (0: 32) */
+  int32_t reserved[3];
 } axpic_params;
 
 /* Number of doubles written by axpic_tally_spectrum into totals_out. */
@@ -350,6 +361,58 @@ axpic_status axpic_mlp_train_step(axpic_mlp *m, const float *X, const float *Zt,
                                   double *loss_out);
 axpic_status axpic_mlp_destroy(axpic_mlp *m);
 const char *axpic_mlp_last_error(const axpic_mlp *m);
+
+/* Output normalisation of the network (y = mu + sigma z), 96 floats each;
+ * set by axpic_surrogate_fit. */
+axpic_status axpic_mlp_set_norm(axpic_mlp *m, const float *mu, const float *sigma);
+axpic_status axpic_mlp_get_norm(axpic_mlp *m, float *mu, float *sigma);
+
+/* The function the surrogate stands in for, in binary64 on the host: for
+ * each of n rows (x = omega/T, kappa/T, n_e [cm^-3], Z in {1, 2}) of `in`,
+ * 96 values to `out`: per channel (Primakoff, Compton-like, bremsstrahlung)
+ * ln(dQ/dx) [erg cm^-3 s^-1 per unit x] at unit coupling (g_agg = 1 GeV^-1,
+ * g_ae = 1; Eqs. prim_xs/prim_rate with Planck photons, epsC, eps_eZ/eps_ee
+ * with the [1 - c eta] brackets floored at 1e-3), then the quantiles x(u_j),
+ * u_j = j/32, j = 1..31, of its number spectrum on [0.05, 20]. Single-ion
+ * plasma (n_i = n_e / Z), Debye screening, ions as Primakoff targets. */
+axpic_status axpic_surrogate_targets(const double *in, int32_t n, double brems_shape, double *out);
+/* The network's input features of n rows (x, kappa/T, n_e, Z): ln x,
+ * ln(kappa/T), log10 n_e and Z, each mapped onto [-1, 1] over the domain
+ * x in [0.05, 20], kappa/T in [0.012, 41], n_e in [1e23, 1e26]. */
+axpic_status axpic_surrogate_features(const double *in, int32_t n, float *out);
+/* Trains the network from scratch on the GPU: ncells random cells of the
+ * domain (T uniform in [0.5, 10] keV, n_e log-uniform in [1e23, 1e26],
+ * Z in {1, 2}) with x_per_cell log-uniform x each, targets from
+ * axpic_surrogate_targets, per-output normalisation set on the handle;
+ * `steps` Adam steps on consecutive batches of `batch` rows with a cosine
+ * learning rate from lr to lr / 100. *loss_out (may be NULL): final loss on
+ * the whole set (normalised units). Synchronises. */
+axpic_status axpic_surrogate_fit(axpic_mlp *m, int32_t ncells, int32_t x_per_cell, int32_t steps, int32_t batch,
+                                 float lr, uint64_t seed, double brems_shape, double *loss_out);
+/* Error of the trained network on a grid of nT temperatures (uniform in
+ * [0.5, 10] keV) x nne densities (log-uniform in [1e23, 1e26]) x Z in {1, 2}
+ * (node (Z-1, j, i) at index ((Z-1) nne + j) nT + i), each at 32 x values
+ * log-spaced on [0.05, 20]: err_out[2 node] = largest |ln(dQ/dx) error| over
+ * x and channels (the relative rate error), err_out[2 node + 1] = largest
+ * relative quantile error. Synchronises. */
+axpic_status axpic_surrogate_validate(axpic_mlp *m, int32_t nT, int32_t nne, double brems_shape, float *err_out);
+
+/* Gives a context with rate_model 2 its network: the parameters, output
+ * normalisation and a trust map from axpic_surrogate_validate's err_out
+ * (nT x nne x 2 nodes): a cell uses the network where the four nodes around
+ * its (T, n_e) at its Z have a rate error <= tol, the table elsewhere. Copies
+ * everything (the network may be destroyed afterwards) and rebuilds the
+ * spectral records. Synchronises. AXPIC_E_INVALID for another rate model or
+ * grid sizes below 2. */
+axpic_status axpic_set_surrogate(axpic_ctx *ctx, axpic_mlp *m, const float *err_map, int32_t nT, int32_t nne,
+                                 float tol);
+/* The spectral records of cells [first, first + count) (rate models 1 and 2):
+ * 192 floats per cell to out (host): ln(dQ_c/dx) at unit coupling on x_k =
+ * 0.05 400^(k/31) (c * 32 + k; c = Primakoff, Compton-like, brems), the
+ * quantiles x(j/32) (96 + c * 31 + j - 1), then ln(g_agg^2 dt pi^2 (hbar c)^3
+ * / (T^4 keV)), ln(g_ae^2 dt 2 pi^2 (hbar c)^3 / (T^4 keV)) and T.
+ * Synchronises. */
+axpic_status axpic_get_spectral_records(axpic_ctx *ctx, int32_t first, int32_t count, float *out);
 
 /* Wait for the stream and return the first latched device error, if any. */
 axpic_status axpic_sync(axpic_ctx *ctx);

@@ -40,6 +40,7 @@ from . import constants as K
 from . import spectra
 from .philox import philox4x32_10, uniform23, split_seed
 from .plasma import Params, CellState, primakoff_F, absorption_rate, cell_state
+from . import surrogate
 from .poisson import cap_lambda, poisson_count
 
 CH_PRIMAKOFF = 1
@@ -195,8 +196,14 @@ def _repeat_products(parent: Species, K, wprod, pos_from: Species = None):
                    src.x[idx], src.y[idx], src.z[idx])
 
 
-def absorb_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally):
-    """Inverse operators on the axions present at the start of the step."""
+def _in_records(x):
+    return (x >= 0.05) & (x <= 20.0)
+
+
+def absorb_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, rec=None):
+    """Inverse operators on the axions present at the start of the step. With
+    a spectral record (table or surrogate rate model) the Primakoff and
+    absorption rates at x = E/T in [0.05, 20] come from it."""
     a = parts["a"]
     tally.n_g0 = len(parts["g"])
     n = len(a)
@@ -204,8 +211,12 @@ def absorb_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTa
         return
     omega = a.pmag() * K.ME_C2_KEV
     w = a.w.copy()
+    x = omega / cs.T_keV
+    use = _in_records(x) if rec is not None else np.zeros(n, dtype=bool)
     if mask & CH_PRIMAKOFF:
         P = primakoff_prob(cs, p, omega, p.prim_inverse_mult)
+        if use.any():
+            P = np.where(use, -np.expm1(-p.prim_inverse_mult * surrogate.rec_prim_gdt(rec, np.where(use, x, 1.0))), P)
         lam = w * P / F32(p.w_gref).astype(np.float64)
         lam_eff, fac, capped = cap_lambda(lam, p.lambda_cap)
         u = decision_uniforms(p, step, cell, STREAM_PRIM_INV, n)
@@ -223,6 +234,12 @@ def absorb_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTa
         E = omega
         tau_c = absorption_rate(cs, "compton", E, p) * p.dt_phys_s if want_c else np.zeros(n)
         tau_b = absorption_rate(cs, "brems", E, p) * p.dt_phys_s if want_b else np.zeros(n)
+        if use.any():
+            xs = np.where(use, x, 1.0)
+            if want_c:
+                tau_c = np.where(use, surrogate.rec_tau(rec, 1, xs, p.eq_stats), tau_c)
+            if want_b:
+                tau_b = np.where(use, surrogate.rec_tau(rec, 2, xs, p.eq_stats), tau_b)
         tau = tau_c + tau_b
         if p.absorb_mode == 0:
             P_abs = -np.expm1(-tau)
@@ -254,9 +271,11 @@ def absorb_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTa
     parts["a"] = a2.take(tail_fill(keep))
 
 
-def emit_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, n_g0=None):
+def emit_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, n_g0=None, rec=None):
     """Forward operators: Primakoff on photons present at step start, then
-    thermal-bath emission on electrons; products are appended to the axions."""
+    thermal-bath emission on electrons; products are appended to the axions.
+    With a spectral record the Primakoff rate (x in [0.05, 20]) and the
+    emitted energies come from it."""
     if n_g0 is None:
         n_g0 = len(parts["g"])
     g = parts["g"]
@@ -268,6 +287,11 @@ def emit_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTall
         g0 = g.take(np.arange(n_g0))
         omega = g0.pmag() * K.ME_C2_KEV
         P = primakoff_prob(cs, p, omega)
+        if rec is not None:
+            x = omega / cs.T_keV
+            use = _in_records(x)
+            if use.any():
+                P = np.where(use, -np.expm1(-surrogate.rec_prim_gdt(rec, np.where(use, x, 1.0))), P)
         lam = g0.w * P / w_a
         lam_eff, fac, capped = cap_lambda(lam, p.lambda_cap)
         u = decision_uniforms(p, step, cell, STREAM_PRIM_FWD, n_g0)
@@ -309,8 +333,11 @@ def emit_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTall
             sub = np.concatenate([np.arange(k) for k in Kc])
             uu = event_uniforms(p, step, cell, STREAM_EV_E, parent, sub)
             is_c = f32(uu[:, 3]) < frac_c[parent]
-            xE = np.where(is_c, spectra.compton_icdf(uu[:, 2]),
-                          spectra.brems_icdf(p.brems_gamma_shape, uu[:, 2]))
+            if rec is None:
+                xE = np.where(is_c, spectra.compton_icdf(uu[:, 2]),
+                              spectra.brems_icdf(p.brems_gamma_shape, uu[:, 2]))
+            else:
+                xE = np.where(is_c, surrogate.rec_sample_x(rec, 1, uu[:, 2]), surrogate.rec_sample_x(rec, 2, uu[:, 2]))
             E = xE * cs.T_keV
             dx, dy, dz = isotropic(uu[:, 0], uu[:, 1])
             pm = E / K.ME_C2_KEV
@@ -401,12 +428,13 @@ class CellInput:
     A: np.ndarray
 
 
-def step_cell(ci: CellInput, parts, p: Params, step, cell, mask, res_E=0.0, res_P=None, feedback=True):
-    """absorb -> emit -> feedback for one cell; returns (tally, feedback result)."""
+def step_cell(ci: CellInput, parts, p: Params, step, cell, mask, res_E=0.0, res_P=None, feedback=True, rec=None):
+    """absorb -> emit -> feedback for one cell; returns (tally, feedback result).
+    rec: the cell's spectral record (table or surrogate rate model) or None."""
     cs = cell_state(ci.T_keV, ci.n_ion, ci.Z, ci.A, p)
     tally = StepTally()
-    absorb_cell(cs, parts, p, step, cell, mask, tally)
-    emit_cell(cs, parts, p, step, cell, mask, tally, n_g0=tally.n_g0)
+    absorb_cell(cs, parts, p, step, cell, mask, tally, rec)
+    emit_cell(cs, parts, p, step, cell, mask, tally, n_g0=tally.n_g0, rec=rec)
     fb = None
     if feedback:
         fb = feedback_cell(cs, parts, p, tally, res_E, res_P)

@@ -217,3 +217,94 @@ def adam(P, G, M, V, t, lr, b1=0.9, b2=0.999, eps=1e-8):
         mh = M[k] / (1.0 - b1 ** t)
         vh = V[k] / (1.0 - b2 ** t)
         P[k] = P[k] - lr * mh / (np.sqrt(vh) + eps)
+
+
+# ------------------------------------------------------------------ spectral records
+# A cell's spectral record under the table rate model: ln(dQ_c/dx) + x at unit
+# coupling (the Boltzmann factor taken out, so that the spline in ln x is
+# accurate to ~1e-4 at large x) on x_k = 0.05 e^((k - 1) h), h = ln(400) / 29, k = 0..31 (c * 32 +
+# k; x_1 = 0.05 and x_30 = 20, one point beyond each end so that the spline
+# has real neighbours everywhere in [0.05, 20]), the quantiles (96 +
+# c * 31 + j - 1), ln(g_agg^2 dt pi^2 (hbar c)^3 / (T^4 keV)),
+# ln(g_ae^2 dt 2 pi^2 (hbar c)^3 / (T^4 keV)) and T. The table holds the
+# targets at nodes uniform in ln(kappa/T) on [ln 0.012, ln 41] and in
+# log10 n_e on [23, 26], for Z = 1 and 2, stored in binary32; a cell's record
+# is bilinear in (ln kappa/T, log10 n_e) at its Z.
+
+SR_LEN = 192
+GRID_H = math.log(X_HI / X_LO) / 29.0
+X_GRID = np.exp(np.log(X_LO) + GRID_H * (np.arange(32) - 1.0))
+
+
+def build_table(nkt, nne, brems_shape=1.70):
+    tab = np.empty((2, nne, nkt, 189), dtype=np.float32)
+    for z in range(2):
+        for j in range(nne):
+            for i in range(nkt):
+                kT = math.exp(math.log(KT_LO) + math.log(KT_HI / KT_LO) * i / (nkt - 1))
+                ne = 10.0 ** (23.0 + 3.0 * j / (nne - 1))
+                Z = z + 1
+                T = temperature(kT, ne, Z)
+                for c, ch in enumerate(CHANNELS):
+                    tab[z, j, i, 32 * c:32 * c + 32] = np.log(emissivity(ch, X_GRID, T, ne, Z, brems_shape)) + X_GRID
+                    tab[z, j, i, 96 + 31 * c:96 + 31 * c + 31] = quantiles(ch, T, ne, Z, brems_shape)
+    return tab
+
+
+def table_record(tab, T, kappa, ne, Z, g_agg, g_ae, dt):
+    """The cell's record from the table (bilinear, clamped to the grid)."""
+    nne, nkt = tab.shape[1], tab.shape[2]
+    kT = kappa / T
+    u = (math.log(kT) - math.log(KT_LO)) / math.log(KT_HI / KT_LO) * (nkt - 1)
+    v = (math.log10(ne) - 23.0) / 3.0 * (nne - 1)
+    u = min(max(u, 0.0), nkt - 1.0)
+    v = min(max(v, 0.0), nne - 1.0)
+    i, j = min(int(u), nkt - 2), min(int(v), nne - 2)
+    fu, fv = u - i, v - j
+    t = tab[int(Z) - 1].astype(np.float64)
+    rec = np.empty(SR_LEN)
+    rec[:189] = ((1 - fv) * ((1 - fu) * t[j, i] + fu * t[j, i + 1]) + fv * ((1 - fu) * t[j + 1, i] + fu * t[j + 1, i + 1]))
+    hc3 = K.HBARC_KEV_CM ** 3
+    rec[189] = math.log(g_agg ** 2 * dt * math.pi ** 2 * hc3 / K.KEV_ERG) - 4.0 * math.log(T)
+    rec[190] = math.log(g_ae ** 2 * dt * 2.0 * math.pi ** 2 * hc3 / K.KEV_ERG) - 4.0 * math.log(T)
+    rec[191] = T
+    return rec
+
+
+def rec_lnL(rec, ch, x):
+    """ln(dQ_c/dx) at x in [0.05, 20] (clamped there): Catmull-Rom in ln x
+    through the record's 32 values of ln(dQ_c/dx) + x, minus x."""
+    x = np.asarray(x, dtype=np.float64)
+    u = (np.log(x) - math.log(X_LO)) / GRID_H + 1.0
+    u = np.clip(u, 1.0, 30.0)
+    k = np.minimum(u.astype(np.int64), 29)
+    f = u - k
+    g = rec[32 * ch:32 * ch + 32]
+    p0, p1, p2, p3 = g[k - 1], g[k], g[k + 1], g[k + 2]
+    s = p1 + 0.5 * f * (p2 - p0 + f * (2 * p0 - 5 * p1 + 4 * p2 - p3 + f * (3 * (p1 - p2) + p3 - p0)))
+    return s - np.clip(x, X_LO, X_HI)
+
+
+def rec_prim_gdt(rec, x):
+    """Gamma_{gamma->a} dt (multiplicity 1) from the record: the Primakoff
+    emissivity divided by E T n_gamma(E) (Eq. prim_rate with Planck photons)."""
+    x = np.asarray(x, dtype=np.float64)
+    return np.exp(rec_lnL(rec, 0, x) + rec[189] - 3 * np.log(x)) * np.expm1(x)
+
+
+def rec_tau(rec, ch, x, eq_stats):
+    """tau_c = Gamma_abs,c dt from the record (Eq. gamma_abs: the emission rate
+    per energy over the equilibrium density)."""
+    x = np.asarray(x, dtype=np.float64)
+    b = np.exp(rec_lnL(rec, ch, x) + rec[190] - 3 * np.log(x))
+    return b * (np.expm1(x) if eq_stats else np.exp(x))
+
+
+def rec_sample_x(rec, ch, u):
+    """x from the record's quantiles of channel ch, linear between quantiles
+    with the end points 0.05 and 20."""
+    u = np.asarray(u, dtype=np.float64)
+    q = np.concatenate([[X_LO], rec[96 + 31 * ch:96 + 31 * ch + 31], [X_HI]])
+    t = u * 32.0
+    j = np.minimum(t.astype(np.int64), 31)
+    return q[j] + (t - j) * (q[j + 1] - q[j])

@@ -53,7 +53,8 @@ class Params(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("tally_nbins", ctypes.c_int32), ("tally_Emax_keV", ctypes.c_double),
                 ("tally_enable", ctypes.c_int32), ("diag_enable", ctypes.c_int32),
                 ("threads_per_block", ctypes.c_int32), ("decide_chunk", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("rate_model", ctypes.c_int32), ("sr_table_nkt", ctypes.c_int32), ("sr_table_nne", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class AxpicError(RuntimeError):
@@ -74,6 +75,23 @@ EXPORTS = {
     "axpic_mlp_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                             ctypes.c_float, ctypes.POINTER(ctypes.c_double)]),
     "axpic_mlp_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "axpic_set_surrogate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
+                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_float]),
+    "axpic_get_spectral_records": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                                  ctypes.POINTER(ctypes.c_float)]),
+    "axpic_mlp_set_norm": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
+                                          ctypes.POINTER(ctypes.c_float)]),
+    "axpic_mlp_get_norm": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
+                                          ctypes.POINTER(ctypes.c_float)]),
+    "axpic_surrogate_targets": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
+                                               ctypes.POINTER(ctypes.c_double)]),
+    "axpic_surrogate_features": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_float)]),
+    "axpic_surrogate_fit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "axpic_surrogate_validate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                                ctypes.POINTER(ctypes.c_float)]),
     "axpic_mlp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "axpic_default_params": (None, [ctypes.POINTER(Params)]),
     "axpic_init_plasma": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(PlasmaDesc),
@@ -305,3 +323,73 @@ def axpic_mlp_train_step(h, X_ptr, Zt_ptr, n, lr, want_loss=True):
 
 def axpic_mlp_destroy(h):
     _mlp_check(h, lib().axpic_mlp_destroy(h))
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def axpic_surrogate_targets(rows, brems_shape=1.70):
+    """rows: (n, 4) of (x, kappa/T, n_e, Z) -> (n, 96) float64."""
+    import numpy as np
+    r = np.ascontiguousarray(rows, dtype=np.float64).reshape(-1, 4)
+    out = np.empty((len(r), 96))
+    st = lib().axpic_surrogate_targets(_dptr(r), len(r), brems_shape, _dptr(out))
+    if st != AXPIC_OK:
+        raise AxpicError(st, "axpic_surrogate_targets")
+    return out
+
+
+def axpic_surrogate_features(rows):
+    import numpy as np
+    r = np.ascontiguousarray(rows, dtype=np.float64).reshape(-1, 4)
+    out = np.empty((len(r), 4), dtype=np.float32)
+    st = lib().axpic_surrogate_features(_dptr(r), len(r), _fptr(out))
+    if st != AXPIC_OK:
+        raise AxpicError(st, "axpic_surrogate_features")
+    return out
+
+
+def axpic_mlp_set_norm(h, mu, sigma):
+    import numpy as np
+    m = np.ascontiguousarray(mu, dtype=np.float32)
+    s = np.ascontiguousarray(sigma, dtype=np.float32)
+    _mlp_check(h, lib().axpic_mlp_set_norm(h, _fptr(m), _fptr(s)))
+
+
+def axpic_mlp_get_norm(h):
+    import numpy as np
+    m = np.empty(96, dtype=np.float32)
+    s = np.empty(96, dtype=np.float32)
+    _mlp_check(h, lib().axpic_mlp_get_norm(h, _fptr(m), _fptr(s)))
+    return m, s
+
+
+def axpic_surrogate_fit(h, ncells, x_per_cell, steps, batch, lr, seed=0, brems_shape=1.70):
+    loss = ctypes.c_double()
+    _mlp_check(h, lib().axpic_surrogate_fit(h, ncells, x_per_cell, steps, batch, lr, seed, brems_shape,
+                                            ctypes.byref(loss)))
+    return loss.value
+
+
+def axpic_surrogate_validate(h, nT, nne, brems_shape=1.70):
+    """(2, nne, nT) arrays: largest ln-rate error and largest relative
+    quantile error per grid node, indexed [Z - 1, j, i]."""
+    import numpy as np
+    out = np.empty(nT * nne * 2 * 2, dtype=np.float32)
+    _mlp_check(h, lib().axpic_surrogate_validate(h, nT, nne, brems_shape, _fptr(out)))
+    out = out.reshape(2, nne, nT, 2)
+    return out[..., 0], out[..., 1]
+
+
+def axpic_set_surrogate(ctx, net_handle, err_map, nT, nne, tol):
+    import numpy as np
+    e = np.ascontiguousarray(err_map, dtype=np.float32)
+    _check(ctx, lib().axpic_set_surrogate(ctx, net_handle, _fptr(e), nT, nne, tol))
+
+
+def axpic_get_spectral_records(ctx, first, count):
+    import numpy as np
+    out = np.empty((max(count, 1), 192), dtype=np.float32)
+    _check(ctx, lib().axpic_get_spectral_records(ctx, first, count, _fptr(out)))
+    return out[:count]

@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "misc.h"
+#include "sr.h"
 #include "step.h"
 
 using namespace axpic;
@@ -62,6 +63,15 @@ struct axpic_ctx {
   cudaStream_t graph_stream = nullptr;
   cudaEvent_t graph_ev[2] = {nullptr, nullptr};
   std::map<int, cudaGraphExec_t> graphs;  // one-step graph per channel mask
+  // spectral records of rate models 1 and 2
+  float* sr = nullptr;      // [ncells * kSrLen]
+  float* srtab = nullptr;   // [2][nne][nkt][kSrTabOut]
+  float* sur_P = nullptr;   // network parameters, output affine and trust map
+  float* sur_mu = nullptr;
+  float* sur_sigma = nullptr;
+  uint8_t* sur_trust = nullptr;
+  int sr_nkt = 0, sr_nne = 0, tnT = 0, tnne = 0, sur_set = 0;
+  float ln_gP = 0.f, ln_gA = 0.f;
   int64_t last_absorb_step = -1;
   std::string last_error;
   std::vector<cudaEvent_t> prof_events;  // 5 per recorded step, created by axpic_profile_begin
@@ -210,8 +220,43 @@ static StepArgs make_args(axpic_ctx* ctx, int64_t step, int mask) {
   A.dec_chunk = ctx->dec_chunk;
   A.ctr_rows = ctx->ctr_rows;
   A.step_dev = nullptr;
+  A.rate_model = ctx->prm.rate_model;
+  A.sr = ctx->sr;
+  A.guard_margin = ctx->prm.rate_model ? 1.05f : 1.0f;
   A.cc = ctx->cc;
   return A;
+}
+
+static SrArgs make_sr_args(axpic_ctx* ctx) {
+  SrArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.ncells = ctx->desc.ncells;
+  a.rec = ctx->rec;
+  a.sr = ctx->sr;
+  a.tab = ctx->srtab;
+  a.nkt = ctx->sr_nkt;
+  a.nne = ctx->sr_nne;
+  a.Z = ctx->desc.nspecies > 0 ? (float)ctx->desc.Z[0] : 1.f;
+  a.ln_gP = ctx->ln_gP;
+  a.ln_gA = ctx->ln_gA;
+  a.P = ctx->sur_P;
+  a.mu = ctx->sur_mu;
+  a.sigma = ctx->sur_sigma;
+  a.trust = ctx->sur_set ? ctx->sur_trust : nullptr;
+  a.tnT = ctx->tnT;
+  a.tnne = ctx->tnne;
+  a.err = ctx->err;
+  return a;
+}
+
+// Rebuilds every cell's spectral record for its current T: the table, then
+// the network over the cells where it is trusted.
+static cudaError_t build_records(axpic_ctx* ctx, cudaStream_t st) {
+  if (!ctx->prm.rate_model) return cudaSuccess;
+  const SrArgs a = make_sr_args(ctx);
+  cudaError_t e = launch_sr_table(a, st);
+  if (!e && a.trust) e = launch_sr_mlp(a, st);
+  return e;
 }
 
 static void free_events(axpic_ctx* ctx) {
@@ -233,7 +278,8 @@ static void free_ctx(axpic_ctx* ctx) {
   if (ctx->graph_stream) cudaStreamDestroy(ctx->graph_stream);
   void* bufs[] = {ctx->rec,    ctx->mom,   ctx->xbuf,     ctx->res, ctx->diag,    ctx->photon_start,
                   ctx->tables, ctx->tally, ctx->counters, ctx->err, ctx->scratch, ctx->bits,
-                  ctx->recA,   ctx->recG,  ctx->recE,     ctx->step_dev};
+                  ctx->recA,   ctx->recG,  ctx->recE,     ctx->step_dev, ctx->sr, ctx->srtab,
+                  ctx->sur_P,  ctx->sur_mu, ctx->sur_sigma, ctx->sur_trust};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete ctx;
@@ -325,6 +371,19 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
   while (ctx->max_warps > 1 && per_warp * ctx->max_warps > smem_limit) --ctx->max_warps;
   if (p.decide_chunk != 0 && p.decide_chunk != 2 && p.decide_chunk != 4 && p.decide_chunk != 8)
     return bad("decide_chunk must be 0, 2, 4 or 8");
+  if (p.rate_model < 0 || p.rate_model > 2) return bad("rate_model must be 0, 1 or 2");
+  if (p.rate_model) {
+    if (d.nspecies != 1 || (d.Z[0] != 1.0 && d.Z[0] != 2.0) || p.kappa_mode != 0 || p.prim_targets != 0)
+      return bad("rate models 1 and 2 need one ion species with Z 1 or 2, Debye screening and ion targets");
+    ctx->sr_nkt = p.sr_table_nkt > 0 ? p.sr_table_nkt : 64;
+    ctx->sr_nne = p.sr_table_nne > 0 ? p.sr_table_nne : 32;
+    if (ctx->sr_nkt < 2 || ctx->sr_nne < 2 || ctx->sr_nkt > 4096 || ctx->sr_nne > 4096)
+      return bad("sr_table_nkt and sr_table_nne must be in [2, 4096]");
+    const double hc3 = kHbarcKeVcm * kHbarcKeVcm * kHbarcKeVcm;
+    const double gcm = p.g_agg_GeV_inv;  // the records are at g_agg = 1 GeV^-1
+    ctx->ln_gP = (float)std::log(gcm * gcm * p.dt_phys_s * kPi * kPi * hc3 / kKeVerg);
+    ctx->ln_gA = (float)std::log(p.g_ae * p.g_ae * p.dt_phys_s * 2.0 * kPi * kPi * hc3 / kKeVerg);
+  }
   ctx->dec_chunk = p.decide_chunk ? p.decide_chunk : kDefaultDecChunk;
   ctx->warps = warps;
   ctx->grid = (d.ncells + warps - 1) / warps;
@@ -349,6 +408,13 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
   ALLOC(ctx->tally, sizeof(double) * (3 * (size_t)p.tally_nbins + 6));
   ALLOC(ctx->counters, sizeof(unsigned long long) * kNumCounters * (size_t)ctx->ctr_rows);
   ALLOC(ctx->step_dev, sizeof(uint32_t));
+  if (p.rate_model) {
+    ALLOC(ctx->sr, sizeof(float) * kSrLen * (size_t)n);
+    ALLOC(ctx->srtab, sizeof(float) * kSrTabOut * 2 * (size_t)ctx->sr_nkt * ctx->sr_nne);
+    ALLOC(ctx->sur_P, sizeof(float) * AXPIC_MLP_PARAMS);
+    ALLOC(ctx->sur_mu, sizeof(float) * 96);
+    ALLOC(ctx->sur_sigma, sizeof(float) * 96);
+  }
   ALLOC(ctx->err, sizeof(int));
   ALLOC(ctx->scratch, sizeof(double) * (8 + kNumCounters + (size_t)kInfoChunk * AXPIC_CELL_INFO_LEN));
   const size_t bit_words = (size_t)n * ((d.axions.capacity + 31) / 32 + (d.photons.capacity + 31) / 32 +
@@ -360,6 +426,11 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
 #undef ALLOC
   std::vector<float> tab((size_t)kNumTables * kTableN);
   build_tables(p.brems_gamma_shape, tab.data());
+  std::vector<float> srtab;
+  if (p.rate_model) {
+    srtab.resize((size_t)kSrTabOut * 2 * ctx->sr_nkt * ctx->sr_nne);
+    build_sr_table(ctx->sr_nkt, ctx->sr_nne, p.brems_gamma_shape, srtab.data());
+  }
   cudaStream_t st = ctx->stream;
   if ((e = cudaMemcpyAsync(ctx->tables, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, st)) ||
       (e = cudaMemsetAsync(ctx->xbuf, 0, sizeof(double) * 4 * (size_t)n, st)) ||
@@ -373,7 +444,10 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
       (e = set_step_smem_limits(per_warp * ctx->max_warps)) ||
       (e = decide_resident_ctas(ctx->dec_chunk, &ctx->dec_grid)) ||
       (e = launch_records(n, d.nspecies, ctx->cc, d.T_keV, d.n_ion, ctx->rec, ctx->err, st)) ||
-      (e = launch_moments(n, to_ptrs(d.electrons), ctx->mom, st)) || (e = cudaStreamSynchronize(st))) {
+      (e = launch_moments(n, to_ptrs(d.electrons), ctx->mom, st)) ||
+      (p.rate_model && (e = cudaMemcpyAsync(ctx->srtab, srtab.data(), srtab.size() * sizeof(float),
+                                            cudaMemcpyHostToDevice, st))) ||
+      (p.rate_model && (e = sr_init_kernels())) || (e = build_records(ctx, st)) || (e = cudaStreamSynchronize(st))) {
     ctx->last_error = cudaGetErrorString(e);
     fprintf(stderr, "axpic_init_plasma: %s\n", ctx->last_error.c_str());
     free_ctx(ctx);
@@ -409,6 +483,7 @@ axpic_status axpic_sample_plasma(axpic_ctx* ctx, int32_t n_el, int32_t n_ph, int
   S.tables = ctx->tables;
   CK(launch_sample(S, ctx->stream), "sample");
   CK(launch_moments(d.ncells, to_ptrs(d.electrons), ctx->mom, ctx->stream), "moments");
+  CK(build_records(ctx, ctx->stream), "spectral records");
   return AXPIC_OK;
 }
 
@@ -417,6 +492,7 @@ axpic_status axpic_update_cells(axpic_ctx* ctx) {
   const axpic_plasma_desc& d = ctx->desc;
   CK(launch_records(d.ncells, d.nspecies, ctx->cc, d.T_keV, d.n_ion, ctx->rec, ctx->err, ctx->stream), "records");
   CK(launch_moments(d.ncells, to_ptrs(d.electrons), ctx->mom, ctx->stream), "moments");
+  CK(build_records(ctx, ctx->stream), "spectral records");
   return AXPIC_OK;
 }
 
@@ -429,7 +505,8 @@ static axpic_status run_phases(axpic_ctx* ctx, int phases, int64_t step, int32_t
   cudaEvent_t* ev = nullptr;
   if (phases == PH_ALL && ctx->prof_used < ctx->prof_max)
     ev = ctx->prof_events.data() + (kStepKernels + 1) * (ctx->prof_used++);
-  CK(launch_step(phases, A, ctx->warps, ctx->stream, ev), name);
+  const SrArgs sra = make_sr_args(ctx);
+  CK(launch_step(phases, A, ctx->warps, ctx->stream, ev, ctx->prm.rate_model ? &sra : nullptr), name);
   if (phases == PH_ABSORB) ctx->last_absorb_step = step;
   return AXPIC_OK;
 }
@@ -613,7 +690,8 @@ axpic_status axpic_run_steps(axpic_ctx* ctx, int64_t first_step, int32_t nsteps,
     A.step_dev = ctx->step_dev;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal), "begin capture");
-    const cudaError_t le = launch_step(PH_ALL, A, ctx->warps, gs);
+    const SrArgs sra = make_sr_args(ctx);
+    const cudaError_t le = launch_step(PH_ALL, A, ctx->warps, gs, nullptr, ctx->prm.rate_model ? &sra : nullptr);
     const cudaError_t ce = cudaStreamEndCapture(gs, &g);
     if (le != cudaSuccess || ce != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -656,6 +734,7 @@ static std::vector<std::pair<void*, size_t>> state_buffers(axpic_ctx* ctx) {
   b.emplace_back(ctx->counters, sizeof(unsigned long long) * kNumCounters * (size_t)ctx->ctr_rows);
   b.emplace_back(ctx->err, sizeof(int));
   b.emplace_back(ctx->bits, bit_words * sizeof(uint32_t));
+  if (ctx->sr) b.emplace_back(ctx->sr, n * kSrLen * sizeof(float));
   return b;
 }
 
@@ -706,10 +785,13 @@ axpic_status axpic_autotune(axpic_ctx* ctx, int64_t step, int32_t trial_steps, i
       set_shape(ctx, chunk, warps, dgrid);
       // one untimed step, then trial_steps timed ones, from the saved state
       StepArgs A = make_args(ctx, step, channel_mask);
-      if ((e = launch_step(PH_ALL, A, ctx->warps, ctx->stream)) || (e = cudaEventRecord(e0, ctx->stream))) break;
+      const SrArgs sra = make_sr_args(ctx);
+      const SrArgs* sp = ctx->prm.rate_model ? &sra : nullptr;
+      if ((e = launch_step(PH_ALL, A, ctx->warps, ctx->stream, nullptr, sp)) || (e = cudaEventRecord(e0, ctx->stream)))
+        break;
       for (int32_t k = 0; k < trial_steps && !e; ++k) {
         A = make_args(ctx, step + 1 + k, channel_mask);
-        e = launch_step(PH_ALL, A, ctx->warps, ctx->stream);
+        e = launch_step(PH_ALL, A, ctx->warps, ctx->stream, nullptr, sp);
       }
       float ms = 0.f;
       if (e || (e = cudaEventRecord(e1, ctx->stream)) || (e = cudaEventSynchronize(e1)) ||
@@ -737,6 +819,46 @@ axpic_status axpic_autotune(axpic_ctx* ctx, int64_t step, int32_t trial_steps, i
   if (best_ms_out) *best_ms_out = best;
   if (chunk_out) *chunk_out = best_chunk;
   if (warps_out) *warps_out = best_warps;
+  return AXPIC_OK;
+}
+
+axpic_status axpic_set_surrogate(axpic_ctx* ctx, axpic_mlp* m, const float* err_map, int32_t nT, int32_t nne,
+                                 float tol) {
+  if (!ctx || !m || !err_map) return AXPIC_E_INVALID;
+  if (ctx->prm.rate_model != 2) return fail(ctx, AXPIC_E_INVALID, "axpic_set_surrogate: rate_model is not 2");
+  if (nT < 2 || nne < 2 || nT > 4096 || nne > 4096) return fail(ctx, AXPIC_E_INVALID, "axpic_set_surrogate: grid");
+  std::vector<float> P(AXPIC_MLP_PARAMS), mu(96), sigma(96);
+  axpic_status s;
+  if ((s = axpic_mlp_get_params(m, P.data())) != AXPIC_OK || (s = axpic_mlp_get_norm(m, mu.data(), sigma.data())))
+    return fail(ctx, s, "axpic_set_surrogate: reading the network");
+  std::vector<uint8_t> trust((size_t)2 * nT * nne);
+  for (size_t i = 0; i < trust.size(); ++i) trust[i] = err_map[2 * i] <= tol ? 1 : 0;
+  cudaStream_t st = ctx->stream;
+  CK(cudaStreamSynchronize(st), "synchronize");
+  if (ctx->sur_trust) cudaFree(ctx->sur_trust);
+  ctx->sur_trust = nullptr;
+  CK(cudaMalloc((void**)&ctx->sur_trust, trust.size()), "trust map");
+  CK(cudaMemcpyAsync(ctx->sur_P, P.data(), sizeof(float) * P.size(), cudaMemcpyHostToDevice, st), "params");
+  CK(cudaMemcpyAsync(ctx->sur_mu, mu.data(), sizeof(float) * 96, cudaMemcpyHostToDevice, st), "norm");
+  CK(cudaMemcpyAsync(ctx->sur_sigma, sigma.data(), sizeof(float) * 96, cudaMemcpyHostToDevice, st), "norm");
+  CK(cudaMemcpyAsync(ctx->sur_trust, trust.data(), trust.size(), cudaMemcpyHostToDevice, st), "trust map");
+  ctx->tnT = nT;
+  ctx->tnne = nne;
+  ctx->sur_set = 1;
+  free_graphs(ctx);
+  CK(build_records(ctx, st), "spectral records");
+  CK(cudaStreamSynchronize(st), "synchronize");
+  return read_err(ctx);
+}
+
+axpic_status axpic_get_spectral_records(axpic_ctx* ctx, int32_t first, int32_t count, float* out) {
+  if (!ctx || !out || first < 0 || count < 0 || first + count > ctx->desc.ncells) return AXPIC_E_INVALID;
+  if (!ctx->sr) return fail(ctx, AXPIC_E_INVALID, "axpic_get_spectral_records: rate_model 0 keeps no records");
+  if (count == 0) return AXPIC_OK;
+  CK(cudaMemcpyAsync(out, ctx->sr + (size_t)first * kSrLen, sizeof(float) * kSrLen * count, cudaMemcpyDeviceToHost,
+                     ctx->stream),
+     "copy");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
   return AXPIC_OK;
 }
 
@@ -806,6 +928,7 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc* desc, const axpic_param
   if (p.T_mode < 0 || p.T_mode > 2 || p.eq_stats < 0 || p.eq_stats > 1 || p.absorb_mode < 0 || p.absorb_mode > 1)
     return bad("bad params");
   if (step < 0 || step >= (int64_t)0xFFFFFFFF || (channel_mask & ~AXPIC_CH_ALL)) return bad("bad step or mask");
+  if (p.rate_model != 0) return bad("rate_model must be 0 (the records need a context)");
   const size_t per_warp = step_smem_per_warp(d.axions.capacity, d.photons.capacity, d.electrons.capacity);
   if (per_warp * kNoAllocWarps > 227 * 1024 - 128) return bad("slab capacities too large");
   const size_t bit_bytes = sizeof(uint32_t) * (size_t)d.ncells *

@@ -357,6 +357,11 @@ struct StepArgs {
   int dec_grid;   // CTAs of the persistent decision kernel
   int dec_chunk;  // cells per chunk of a decision warp: 2, 4 or 8
   uint32_t* step_dev;  // NULL, or the device step counter of a replayed graph
+  // rate model: 0 the closed forms; 1 and 2 per-cell spectral records (table,
+  // surrogate) for the full decisions' rates and the emission energies
+  int rate_model;
+  const float* sr;     // [ncells * 192] spectral records
+  float guard_margin;  // factor on the no-event bounds (covers the records' error)
   CellConst cc;
 };
 

@@ -13,61 +13,10 @@
 #include <vector>
 
 #include "mlp.h"
+#include "tc.cuh"
+#include "surrogate.h"
 
 namespace axpic {
-
-// ---------------------------------------------------------------- tcgen05 primitives
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Shared-memory matrix descriptor, no swizzle: start address, leading (K)
-// and stride (M/N) byte offsets between 8x16-byte core matrices.
-__device__ __forceinline__ uint64_t mma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
-  d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version of this architecture
-  return d;
-}
-
-// Instruction descriptor, kind::f16: D FP32, A and B bfloat16, both K-major.
-__host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-// Bounded wait on an mbarrier phase; false when the bound ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = smem_u32(bar);
-  for (int it = 0; it < (1 << 22); ++it) {
-    uint32_t done = 0;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-// Core-matrix layout of a rows x kc bfloat16 tile (kc a multiple of 16):
-// element (r, k) of core matrix (r / 8, k / 8), 8 elements per 16-byte row.
-__device__ __forceinline__ int core_off(int r, int k, int kc) {
-  return ((r >> 3) * (kc >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
-}
 
 // ---------------------------------------------------------------- tile GEMM
 // C (M x N) = A (M x K) . B (K x N) on tiles of 128 rows, split along K into
@@ -357,7 +306,7 @@ static GemmArgs wgrad_gemm(const float* A, int rows, const float* B, int cols, f
 
 cudaError_t Mlp::forward(const float* X, int n, float* out) {
   cudaError_t e;
-  if ((e = reserve(n))) return e;
+  if ((e = reserve(n))) return e;  // may reallocate every work buffer, z included
   if (n == 0) return cudaSuccess;
   const long t1 = (long)n * 64;
   layer1_kernel<<<(unsigned)((t1 + 255) / 256), 256, 0, st>>>(X, W1(), b1(), h1, n);
@@ -369,7 +318,8 @@ cudaError_t Mlp::forward(const float* X, int n, float* out) {
 
 cudaError_t Mlp::gradients(const float* X, const float* Zt, int n) {
   cudaError_t e;
-  if ((e = forward(X, n, z))) return e;
+  // NULL: the output buffer is resolved after forward() has reserved it
+  if ((e = forward(X, n, nullptr))) return e;
   if ((e = cudaMemsetAsync(G, 0, sizeof(float) * kMlpParams, st)) || (e = cudaMemsetAsync(loss, 0, sizeof(double), st)))
     return e;
   if (n == 0) return cudaSuccess;
@@ -410,6 +360,7 @@ cudaError_t Mlp::adam(float lr) {
 struct axpic_mlp {
   axpic::Mlp m;
   std::string last_error;
+  std::vector<float> mu = std::vector<float>(96, 0.f), sigma = std::vector<float>(96, 1.f);
 };
 
 extern "C" {
@@ -506,5 +457,152 @@ axpic_status axpic_mlp_destroy(axpic_mlp* h) {
 }
 
 const char* axpic_mlp_last_error(const axpic_mlp* h) { return h ? h->last_error.c_str() : "no network"; }
+
+axpic_status axpic_mlp_set_norm(axpic_mlp* h, const float* mu, const float* sigma) {
+  if (!h || !mu || !sigma) return AXPIC_E_INVALID;
+  for (int k = 0; k < 96; ++k) {
+    if (!(sigma[k] > 0.f)) return AXPIC_E_INVALID;
+    h->mu[k] = mu[k];
+    h->sigma[k] = sigma[k];
+  }
+  return AXPIC_OK;
+}
+
+axpic_status axpic_mlp_get_norm(axpic_mlp* h, float* mu, float* sigma) {
+  if (!h || !mu || !sigma) return AXPIC_E_INVALID;
+  for (int k = 0; k < 96; ++k) {
+    mu[k] = h->mu[k];
+    sigma[k] = h->sigma[k];
+  }
+  return AXPIC_OK;
+}
+
+// Glorot-uniform weights and zero biases from a seeded stream.
+static void glorot(uint64_t seed, std::vector<float>& P) {
+  P.assign(axpic::kMlpParams, 0.f);
+  uint64_t s = seed;
+  auto u01 = [&s]() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  };
+  const int offs[3] = {axpic::kOffW1, axpic::kOffW2, axpic::kOffW3};
+  const int fin[3] = {4, 64, 64}, fout[3] = {64, 64, 96};
+  for (int l = 0; l < 3; ++l) {
+    const double lim = std::sqrt(6.0 / (fin[l] + fout[l]));
+    for (int i = 0; i < fin[l] * fout[l]; ++i) P[offs[l] + i] = (float)((2.0 * u01() - 1.0) * lim);
+  }
+}
+
+axpic_status axpic_surrogate_fit(axpic_mlp* h, int32_t ncells, int32_t x_per_cell, int32_t steps, int32_t batch,
+                                 float lr, uint64_t seed, double brems_shape, double* loss_out) {
+  if (!h || ncells < 1 || x_per_cell < 1 || steps < 1 || batch < 1 || !(lr > 0.f) || !(brems_shape > 0))
+    return AXPIC_E_INVALID;
+  std::vector<float> X;
+  std::vector<double> Y;
+  axpic::sur_training_set(ncells, x_per_cell, seed, brems_shape, X, Y);
+  const size_t n = (size_t)ncells * x_per_cell;
+  // per-output normalisation and the normalised targets
+  std::vector<double> mu(96, 0.0), var(96, 0.0);
+  for (size_t r = 0; r < n; ++r)
+    for (int k = 0; k < 96; ++k) mu[k] += Y[r * 96 + k];
+  for (int k = 0; k < 96; ++k) mu[k] /= (double)n;
+  for (size_t r = 0; r < n; ++r)
+    for (int k = 0; k < 96; ++k) var[k] += (Y[r * 96 + k] - mu[k]) * (Y[r * 96 + k] - mu[k]);
+  for (int k = 0; k < 96; ++k) {
+    h->mu[k] = (float)mu[k];
+    h->sigma[k] = (float)std::max(std::sqrt(var[k] / (double)n), 1e-6);
+  }
+  std::vector<float> Zt(n * 96);
+  for (size_t r = 0; r < n; ++r)
+    for (int k = 0; k < 96; ++k) Zt[r * 96 + k] = (float)((Y[r * 96 + k] - h->mu[k]) / h->sigma[k]);
+  std::vector<float> P;
+  glorot(seed ^ 0xA5A5A5A5u, P);
+  axpic_status s = axpic_mlp_set_params(h, P.data());
+  if (s != AXPIC_OK) return s;
+  float *dX = nullptr, *dZ = nullptr;
+  cudaError_t e;
+  if ((e = cudaMalloc(&dX, sizeof(float) * X.size())) || (e = cudaMalloc(&dZ, sizeof(float) * Zt.size()))) {
+    cudaFree(dX);
+    return mlp_fail(h, e, "axpic_surrogate_fit");
+  }
+  e = cudaMemcpyAsync(dX, X.data(), sizeof(float) * X.size(), cudaMemcpyHostToDevice, h->m.st);
+  if (!e) e = cudaMemcpyAsync(dZ, Zt.data(), sizeof(float) * Zt.size(), cudaMemcpyHostToDevice, h->m.st);
+  // rows were drawn independently: consecutive batches are random batches
+  const int nb = (int)std::max<size_t>(1, n / (size_t)batch);
+  for (int t = 0; t < steps && !e; ++t) {
+    const int b = t % nb;
+    const float lr_t = lr * (0.01f + 0.99f * 0.5f * (1.0f + cosf(3.14159265f * (float)t / (float)steps)));
+    e = h->m.gradients(dX + (size_t)b * batch * 4, dZ + (size_t)b * batch * 96, batch);
+    if (!e) e = h->m.adam(lr_t);
+  }
+  if (!e) e = h->m.gradients(dX, dZ, (int)n);
+  double loss = 0.0;
+  if (!e) e = cudaMemcpyAsync(&loss, h->m.loss, sizeof(double), cudaMemcpyDeviceToHost, h->m.st);
+  if (!e) e = cudaStreamSynchronize(h->m.st);
+  cudaFree(dX);
+  cudaFree(dZ);
+  if (e) return mlp_fail(h, e, "axpic_surrogate_fit");
+  if (loss_out) *loss_out = loss;
+  return mlp_sync(h, "axpic_surrogate_fit");
+}
+
+axpic_status axpic_surrogate_validate(axpic_mlp* h, int32_t nT, int32_t nne, double brems_shape, float* err_out) {
+  if (!h || nT < 2 || nne < 2 || !err_out || !(brems_shape > 0)) return AXPIC_E_INVALID;
+  const int nodes = nT * nne * 2, nx = 32;
+  std::vector<float> X((size_t)nodes * nx * 4);
+  std::vector<double> Y((size_t)nodes * nx * 96);
+  double knots[93];
+  for (int z = 0; z < 2; ++z)
+    for (int j = 0; j < nne; ++j)
+      for (int i = 0; i < nT; ++i) {
+        const int node = (z * nne + j) * nT + i;
+        const double T = axpic::kSurTLo + (axpic::kSurTHi - axpic::kSurTLo) * i / (nT - 1);
+        const double ne = std::pow(10.0, 23.0 + 3.0 * j / (nne - 1));
+        const double Z = z + 1.0;
+        const axpic::SurCell c = axpic::sur_cell(T, ne, Z, brems_shape);
+        axpic::sur_knots(c, knots);
+        for (int k = 0; k < nx; ++k) {
+          const double x = axpic::kSurXLo * std::pow(axpic::kSurXHi / axpic::kSurXLo, k / (double)(nx - 1));
+          const size_t r = (size_t)node * nx + k;
+          axpic::sur_features(x, c.kappa / T, ne, Z, &X[r * 4]);
+          axpic::sur_targets(x, c, knots, &Y[r * 96]);
+        }
+      }
+  const size_t n = (size_t)nodes * nx;
+  float *dX = nullptr, *dZ = nullptr;
+  cudaError_t e;
+  if ((e = cudaMalloc(&dX, sizeof(float) * X.size())) || (e = cudaMalloc(&dZ, sizeof(float) * n * 96))) {
+    cudaFree(dX);
+    return mlp_fail(h, e, "axpic_surrogate_validate");
+  }
+  std::vector<float> Z(n * 96);
+  e = cudaMemcpyAsync(dX, X.data(), sizeof(float) * X.size(), cudaMemcpyHostToDevice, h->m.st);
+  if (!e) e = h->m.forward(dX, (int)n, dZ);
+  if (!e) e = cudaMemcpyAsync(Z.data(), dZ, sizeof(float) * Z.size(), cudaMemcpyDeviceToHost, h->m.st);
+  if (!e) e = cudaStreamSynchronize(h->m.st);
+  cudaFree(dX);
+  cudaFree(dZ);
+  if (e) return mlp_fail(h, e, "axpic_surrogate_validate");
+  // per node: the largest error of ln(dQ/dx) over the x grid and channels
+  // (the relative rate error), and of the quantiles relative to x
+  for (int node = 0; node < nodes; ++node) {
+    double eL = 0.0, eQ = 0.0;
+    for (int k = 0; k < nx; ++k) {
+      const size_t r = (size_t)node * nx + k;
+      for (int o = 0; o < 96; ++o) {
+        const double y = h->mu[o] + h->sigma[o] * (double)Z[r * 96 + o];
+        const double d = std::fabs(y - Y[r * 96 + o]);
+        if (o % 32 == 0) eL = std::max(eL, d);
+        else eQ = std::max(eQ, d / Y[r * 96 + o]);
+      }
+    }
+    err_out[2 * node] = (float)eL;
+    err_out[2 * node + 1] = (float)eQ;
+  }
+  return AXPIC_OK;
+}
 
 }  // extern "C"

@@ -20,7 +20,9 @@ struct Mlp {
   ~Mlp();
   cudaError_t init(cudaStream_t s);
   cudaError_t reserve(int n);
-  // z[n][96] = network(X[n][4]) (normalised outputs); out may be NULL (own buffer)
+  // z[n][96] = network(X[n][4]) (normalised outputs); out NULL: the own
+  // buffer z, taken after the work buffers are reserved for n rows (never
+  // pass z itself: reserving may reallocate it)
   cudaError_t forward(const float* X, int n, float* out);
   // G = d loss / d P and *loss, loss = sum (z - Zt)^2 / n
   cudaError_t gradients(const float* X, const float* Zt, int n);

@@ -20,6 +20,7 @@
 // the exchange passes through an FP64 per-cell buffer in the same summation
 // order, so results do not depend on how a step is called.
 #include "common.cuh"
+#include "sr.h"
 #include "step.h"
 
 namespace axpic {
@@ -110,6 +111,50 @@ __device__ __noinline__ void tally_add(const StepArgs& A, int ch, float w, float
   atomicAdd(A.tally + 3 * A.nbins + 3 + ch, wE);
 }
 
+// ---------------------------------------------------------------- spectral records
+// Rates from a cell's spectral record (table or surrogate rate model): the
+// record holds ln(dQ_c/dx) + x at unit coupling on 32 points of ln x (step
+// ln(400)/29, one beyond each end of [0.05, 20]); a Catmull-Rom spline in
+// ln x interpolates it, the closed factors of Eqs. prim_rate and gamma_abs
+// turn it into a rate.
+__device__ __forceinline__ bool sr_in_range(float x) { return x >= 0.05f && x <= 20.0f; }
+
+__device__ __forceinline__ float sr_lnL(const float* sr, int ch, float lnx) {
+  float u = (lnx - kSrLnXLo) * (1.0f / kSrH) + 1.0f;
+  u = fminf(fmaxf(u, 1.f), 30.f);
+  const int k = min((int)u, 29);
+  const float f = u - (float)k;
+  const float* g = sr + ch * kSrGrid;
+  const float p0 = g[k - 1], p1 = g[k], p2 = g[k + 1], p3 = g[k + 2];
+  const float s = p1 + 0.5f * f * (p2 - p0 + f * (2.f * p0 - 5.f * p1 + 4.f * p2 - p3 + f * (3.f * (p1 - p2) + p3 - p0)));
+  return s - fminf(fmaxf(__expf(lnx), 0.05f), 20.0f);  // the stored values are ln(dQ/dx) + x
+}
+
+// Gamma_{gamma->a} dt at the cell's couplings (multiplicity 1).
+__device__ __forceinline__ float sr_prim_gdt(const float* sr, float x) {
+  const float lx = logf(x);
+  return expf((sr_lnL(sr, 0, lx) + sr[SR_LNKP]) - 3.f * lx) * expm1f(x);
+}
+
+// Absorption tau_c = Gamma_abs,c dt (c = 1 Compton-like, 2 bremsstrahlung).
+__device__ __forceinline__ float sr_tau(const float* sr, int ch, float x, int eq_stats) {
+  const float lx = logf(x);
+  const float b = expf((sr_lnL(sr, ch, lx) + sr[SR_LNKA]) - 3.f * lx);
+  return eq_stats ? b * expm1f(x) : b * expf(x);
+}
+
+// x from the record's 31 quantiles of channel c (end points 0.05 and 20),
+// linear between quantiles.
+__device__ __forceinline__ float sr_sample_x(const float* sr, int ch, float u) {
+  const float t = u * 32.f;
+  const int j = min((int)t, 31);
+  const float f = t - (float)j;
+  const float* q = sr + 96 + ch * kSrKnots;
+  const float x0 = j == 0 ? 0.05f : q[j - 1];
+  const float x1 = j == 31 ? 20.0f : q[j];
+  return fmaf(f, x1 - x0, x0);
+}
+
 // ---------------------------------------------------------------- decisions
 // One axion at the start of the step: a->gamma conversion (Sec. II.F.1, last
 // paragraph) then detailed-balance absorption of the thermal-bath channels
@@ -120,8 +165,9 @@ struct AxionDecision {
   bool keep, absorbed, capped, over, abs_c;
 };
 
-__device__ __forceinline__ AxionDecision axion_decide(const float* rec, const StepArgs& A, int mask, float w, float px,
-                                                      float py, float pz, uint32_t wP, uint32_t wA) {
+__device__ __forceinline__ AxionDecision axion_decide(const float* rec, const float* sr, const StepArgs& A, int mask,
+                                                      float w, float px, float py, float pz, uint32_t wP,
+                                                      uint32_t wA) {
   AxionDecision d;
   d.om = sqrtf(px * px + py * py + pz * pz) * kMeC2f;
   d.K = 0;
@@ -131,8 +177,10 @@ __device__ __forceinline__ AxionDecision axion_decide(const float* rec, const St
   d.absorbed = false;
   d.abs_c = false;
   float wrem = w;
+  const float xr = d.om * rec[R_INVT];
+  const bool use_sr = sr && sr_in_range(xr);
   if (mask & AXPIC_CH_PRIMAKOFF) {
-    const float P = prim_prob(rec, d.om, rec[R_APINV]);
+    const float P = use_sr ? -expm1f(-A.cc.prim_mult * sr_prim_gdt(sr, xr)) : prim_prob(rec, d.om, rec[R_APINV]);
     float fac;
     const float le = cap_lambda(w * P * A.inv_w_gref, A.lam_cap, &fac, &d.capped);
     d.K = poisson_inv(u23(wP), le);
@@ -141,9 +189,13 @@ __device__ __forceinline__ AxionDecision axion_decide(const float* rec, const St
   d.keep = wrem > 0.f;
   d.wnew = wrem;
   if (d.keep && (mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS))) {
-    const float x = d.om * rec[R_INVT];
-    const float tc = (mask & AXPIC_CH_COMPTON) ? tau_compton(rec, x, A.eq_stats) : 0.f;
-    const float tb = (mask & AXPIC_CH_BREMS) ? tau_brems(rec, x, A.brems_am3, A.eq_stats) : 0.f;
+    const float x = xr;
+    const float tc = !(mask & AXPIC_CH_COMPTON) ? 0.f
+                     : use_sr                   ? sr_tau(sr, 1, x, A.eq_stats)
+                                                : tau_compton(rec, x, A.eq_stats);
+    const float tb = !(mask & AXPIC_CH_BREMS) ? 0.f
+                     : use_sr                 ? sr_tau(sr, 2, x, A.eq_stats)
+                                              : tau_brems(rec, x, A.brems_am3, A.eq_stats);
     const float tau = tc + tb;
     if (A.absorb_mode == 0) {
       const float P = -expm1f(-tau);
@@ -179,7 +231,7 @@ __device__ __noinline__ AxionDecision axion_decide_slow(const StepArgs& A, int c
                                                         float py, float pz, uint32_t wP, uint32_t wA) {
   float rec[kRecLen];
   load_rec(A, cell, rec);
-  return axion_decide(rec, A, mask, w, px, py, pz, wP, wA);
+  return axion_decide(rec, A.rate_model ? A.sr + (size_t)cell * kSrLen : nullptr, A, mask, w, px, py, pz, wP, wA);
 }
 
 // One photon at the start of the step: gamma->a conversion (Sec. II.F,
@@ -190,11 +242,12 @@ struct PhotonDecision {
   bool capped, over;
 };
 
-__device__ __forceinline__ PhotonDecision photon_decide(const float* rec, const StepArgs& A, float w, float px,
-                                                        float py, float pz, uint32_t wd) {
+__device__ __forceinline__ PhotonDecision photon_decide(const float* rec, const float* sr, const StepArgs& A, float w,
+                                                        float px, float py, float pz, uint32_t wd) {
   PhotonDecision d;
   d.om = sqrtf(px * px + py * py + pz * pz) * kMeC2f;
-  const float P = prim_prob(rec, d.om, rec[R_AP]);
+  const float xr = d.om * rec[R_INVT];
+  const float P = sr && sr_in_range(xr) ? -expm1f(-sr_prim_gdt(sr, xr)) : prim_prob(rec, d.om, rec[R_AP]);
   float fac;
   const float le = cap_lambda(w * P * A.inv_w_a, A.lam_cap, &fac, &d.capped);
   d.K = poisson_inv(u23(wd), le);
@@ -209,7 +262,7 @@ __device__ __noinline__ PhotonDecision photon_decide_slow(const StepArgs& A, int
                                                           float pz, uint32_t wd) {
   float rec[kRecLen];
   load_rec(A, cell, rec);
-  return photon_decide(rec, A, w, px, py, pz, wd);
+  return photon_decide(rec, A.rate_model ? A.sr + (size_t)cell * kSrLen : nullptr, A, w, px, py, pz, wd);
 }
 
 // Guards: cheap upper bounds that prove, without the transcendental chain,
@@ -223,10 +276,10 @@ __device__ __noinline__ PhotonDecision photon_decide_slow(const StepArgs& A, int
 // A bound at or above the Poisson-mean cap also sends the slot to the full
 // decision, so that cap hits are counted exactly.
 __device__ __forceinline__ bool no_conversion(float w, float p2, float c_s, float Acoef, float inv_wref, float u,
-                                              float lam_cap) {
+                                              float lam_cap, float gm) {
   const float s = p2 * c_s;
   const float Fb = s < 2.5f ? 0.5f * s : __logf(1.0f + s);
-  const float lb = w * Acoef * Fb * inv_wref * 1.0001f;
+  const float lb = w * Acoef * Fb * inv_wref * (1.0001f * gm);
   return lb < lam_cap && u <= 1.0f - lb - 1e-6f;
 }
 
@@ -236,7 +289,7 @@ __device__ __forceinline__ bool no_absorption(float r_bc, float r_bb, const Step
   float tb = 0.f;
   if (mask & AXPIC_CH_COMPTON) tb += r_bc * x * (1.0f + x);
   if (mask & AXPIC_CH_BREMS) tb += r_bb * __expf(A.brems_am3 * __logf(x));
-  return u >= tb * 1.001f + 1e-6f;
+  return u >= tb * (1.001f * A.guard_margin) + 1e-6f;
 }
 
 // ---------------------------------------------------------------- feedback
@@ -542,7 +595,8 @@ __device__ __forceinline__ int photon_chunk(const StepArgs& A, uint32_t step, in
       for (int j = 0; j < 4; ++j) {
         const float px = f4(x4, j), py = f4(y4, j), pz = f4(z4, j);
         const float p2 = px * px + py * py + pz * pz;
-        if (j < nj && !no_conversion(f4(w4, j), p2, cs, ca, A.inv_w_a, u23(word(r, j)), A.lam_cap)) nib |= 1u << j;
+        if (j < nj && !no_conversion(f4(w4, j), p2, cs, ca, A.inv_w_a, u23(word(r, j)), A.lam_cap, A.guard_margin))
+          nib |= 1u << j;
       }
       flag_quad(A.bitsG, A.Wg, cell, q, nib);
     }
@@ -599,7 +653,8 @@ __device__ __forceinline__ int axion_chunk(const StepArgs& A, uint32_t step, int
         const float px = f4(x4, j), py = f4(y4, j), pz = f4(z4, j);
         const float p2 = px * px + py * py + pz * pz;
         bool fast = !all;
-        if (fast && prim) fast = no_conversion(f4(w4, j), p2, cs, cap_inv, A.inv_w_gref, u23(word(rP, j)), A.lam_cap);
+        if (fast && prim)
+          fast = no_conversion(f4(w4, j), p2, cs, cap_inv, A.inv_w_gref, u23(word(rP, j)), A.lam_cap, A.guard_margin);
         if (fast && bath) fast = no_absorption(cbc, cbb, A, mask, sqrtf(p2) * kMeC2f * cinvT, u23(word(rA, j)));
         if (j < nj && !fast) nib |= 1u << j;
       }
@@ -1218,7 +1273,9 @@ __device__ __forceinline__ void event_cell(const StepArgs& A, uint32_t step, int
                                             A.rk);
               const bool isC = u23(r.w) < fracC;
               const float3 dv = iso_dir(u23(r.x), u23(r.y));
-              const float E = icdf_lookup(isC ? tabC : tabB, u23(r.z)) * r_T;
+              const float E = (A.rate_model ? sr_sample_x(A.sr + (size_t)cell * kSrLen, isC ? 1 : 2, u23(r.z))
+                                            : icdf_lookup(isC ? tabC : tabB, u23(r.z))) *
+                              r_T;
               const float wv = isC ? wvC : wvB;
               const float pm = E * kInvMeC2f;
               const float px = pm * dv.x, py = pm * dv.y, pz = pm * dv.z;
@@ -1564,7 +1621,17 @@ cudaError_t decide_resident_ctas(int chunk, int* out) {
   return cudaSuccess;
 }
 
-cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t st, cudaEvent_t* ev) {
+// After the temperature update of an evolved-T step the spectral records are
+// rebuilt for the new T (rate models 1 and 2).
+static cudaError_t launch_records_update(const StepArgs& A, const SrArgs* sra, cudaStream_t st) {
+  if (!sra || A.T_mode != 2) return cudaSuccess;
+  cudaError_t e = launch_sr_table(*sra, st);
+  if (!e && sra->trust) e = launch_sr_mlp(*sra, st);
+  return e;
+}
+
+cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t st, cudaEvent_t* ev,
+                        const SrArgs* sra) {
   if (A.ncells == 0) return cudaSuccess;
   cudaError_t e;
   // optional measurement: events between the kernels of a full step
@@ -1577,11 +1644,12 @@ cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t s
       if ((e = launch_decide(A, PH_EMIT, st))) return e;
       return launch_events<PH_EMIT>(A, warps, st);
     case PH_FEEDBACK:
-      return launch_feedback(A, st);
+      if ((e = launch_feedback(A, st))) return e;
+      return launch_records_update(A, sra, st);
     case PH_ALL:
       if ((e = mark(0)) || (e = launch_decide(A, PH_ABSORB | PH_EMIT, st)) || (e = mark(1))) return e;
       if ((e = launch_events<PH_ABSORB | PH_EMIT>(A, warps, st)) || (e = mark(2))) return e;
-      if ((e = launch_feedback(A, st)) || (e = mark(3))) return e;
+      if ((e = launch_feedback(A, st)) || (e = launch_records_update(A, sra, st)) || (e = mark(3))) return e;
       return cudaSuccess;
     default:
       return cudaErrorInvalidValue;

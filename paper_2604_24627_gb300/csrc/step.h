@@ -1,6 +1,7 @@
 // Launch interface of the step kernels (internal to libaxpic).
 #pragma once
 #include "common.cuh"
+#include "sr.h"
 
 namespace axpic {
 
@@ -8,8 +9,11 @@ enum { PH_ABSORB = 1, PH_EMIT = 2, PH_FEEDBACK = 4, PH_ALL = 7 };
 
 size_t step_smem_per_warp(int acap, int gcap, int ecap);
 // ev: NULL, or kStepKernels + 1 events recorded around the kernels of a
-// PH_ALL step.
-cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t st, cudaEvent_t* ev = nullptr);
+// PH_ALL step (the third interval covers the feedback kernel and, with a rate
+// model, the records' rebuild). sra: the record kernels' arguments (rate
+// models 1 and 2), else NULL.
+cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t st, cudaEvent_t* ev = nullptr,
+                        const SrArgs* sra = nullptr);
 constexpr int kStepKernels = 3;
 // Comma-separated names of the kernels a PH_ALL step launches, in order.
 const char* step_kernel_names();

@@ -1,0 +1,33 @@
+// The spectral surrogate's target function on the host (internal to libaxpic).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace axpic {
+
+constexpr double kSurXLo = 0.05, kSurXHi = 20.0;     // x = omega / T
+constexpr double kSurKtLo = 0.012, kSurKtHi = 41.0;  // kappa / T
+constexpr double kSurTLo = 0.5, kSurTHi = 10.0;      // keV
+constexpr double kSurNeLo = 1e23, kSurNeHi = 1e26;   // cm^-3
+constexpr int kSurOut = 96;
+
+struct SurCell {
+  double T, ne, Z, a, kappa, Q_C, Q_B, Gamma0_P;
+};
+
+double sur_temperature(double kT, double ne, double Z);
+double sur_kappa_over_T(double T, double ne, double Z);
+SurCell sur_cell(double T, double ne, double Z, double brems_shape);
+// dQ_c/dx at unit coupling (c: 0 Primakoff, 1 Compton-like, 2 bremsstrahlung)
+double sur_emissivity(int ch, double x, const SurCell& c);
+// quantiles x(u_j), j = 1..31, of channel c's number spectrum on [0.05, 20]
+void sur_quantiles(int ch, const SurCell& c, double* out31);
+void sur_knots(const SurCell& c, double* knots93);
+void sur_targets(double x, const SurCell& c, const double* knots93, double* out96);
+void sur_features(double x, double kT, double ne, double Z, float* f4);
+// ncells random cells of the domain (T uniform, n_e log-uniform, Z in {1, 2})
+// with xpc log-uniform x each: features X (rows x 4) and targets Y (rows x 96)
+void sur_training_set(int ncells, int xpc, uint64_t seed, double brems_shape, std::vector<float>& X,
+                      std::vector<double>& Y);
+
+}  // namespace axpic

@@ -43,7 +43,7 @@ static const double kBern[21] = {1.0, -0.5, 1.0 / 6, 0, -1.0 / 30, 0, 1.0 / 42, 
                                  -174611.0 / 330};
 
 // CDF and complementary CDF of the number pdf x^n/(e^x-1)/(n! zeta(n+1)).
-static void bose_cdf(int n, double x, double* cdf, double* ccdf) {
+void bose_cdf(int n, double x, double* cdf, double* ccdf) {
   const double total = factorial(n) * zeta(n + 1.0);
   if (x < 1.0) {
     double acc = 0.0, fm = 1.0;
@@ -73,7 +73,7 @@ static void bose_cdf(int n, double x, double* cdf, double* ccdf) {
 }
 
 // Regularized incomplete gamma: P(a,x) and Q(a,x) = 1 - P.
-static void gamma_pq(double a, double x, double* P, double* Q) {
+void gamma_pq(double a, double x, double* P, double* Q) {
   if (x <= 0.0) {
     *P = 0.0;
     *Q = 1.0;

@@ -77,3 +77,20 @@ def test_training_reduces_loss():
     l1 = net.train_step(Xd, Zd, 3e-3, want_loss=True)
     assert l1 < 0.05 * l0, (l0, l1)
     net.close()
+
+
+def test_batches_that_grow_reuse_the_network():
+    """Work buffers are re-reserved when a batch outgrows them: every call,
+    small then larger, still matches the oracle."""
+    net = SurrogateNet()
+    for n in (200, 5000, 300, 9000):
+        P, X, Zt = seeded(10 + n, n)
+        net.set_params(P)
+        loss, G = net.gradients(dev(X), dev(Zt))
+        want = S.backward(P, X, Zt, bf16_mma=True)
+        for k in want:
+            assert np.linalg.norm(G[k] - want[k]) <= 5e-3 * np.linalg.norm(want[k]) + 1e-7, (n, k)
+        z = net.forward(dev(X)).cpu().numpy()
+        zw, _ = S.forward(P, X, bf16_mma=True)
+        assert np.median(np.abs(z - zw)) <= 2e-5 * max(1.0, np.abs(zw).max()), n
+    net.close()

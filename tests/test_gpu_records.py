@@ -1,0 +1,179 @@
+"""Rate models 1 (exact FP32 table) and 2 (surrogate network with the table
+as fallback): per-cell spectral records and the step, through the C ABI,
+against the oracle (needs a GB300)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import constants as K
+from oracle import surrogate as S
+from parity_util import assert_species_close, oracle_step
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2604_24627_gb300 import AxionPlasma, _lib  # noqa: E402
+from paper_2604_24627_gb300.mlp import SurrogateNet  # noqa: E402
+
+NKT, NNE = 6, 5
+_TAB = {}
+
+
+def oracle_table():
+    if "t" not in _TAB:
+        _TAB["t"] = S.build_table(NKT, NNE)
+    return _TAB["t"]
+
+
+def params(model, **kw):
+    prm = dict(g_agg_GeV_inv=1e-10, g_ae=2e-12, dt_phys_s=2e12, w_a=3.0e9, seed=0x77, T_mode=0, diag_enable=1,
+               tally_enable=0, rate_model=model, sr_table_nkt=NKT, sr_table_nne=NNE)
+    prm.update(kw)
+    return prm
+
+
+def make(T, ne, prm, Z=1, counts=(61, 37, 13), caps=(64, 192, 512)):
+    n = len(T)
+    A = K.A_H if Z == 1 else K.A_HE
+    pl = AxionPlasma(n, T, (np.asarray(ne) / Z).reshape(n, 1), [float(Z)], [A], 1e-12, caps, prm)
+    pl.sample(*counts)
+    torch.cuda.synchronize()
+    return pl
+
+
+def oracle_record(T, ne, Z, prm):
+    cs, _ = S.cell(T, ne, Z)
+    return S.table_record(oracle_table(), T, cs.kappa_keV, ne, Z, prm["g_agg_GeV_inv"], prm["g_ae"],
+                          prm["dt_phys_s"])
+
+
+CELLS = [(1.3, 6e25), (3.0, 6e25), (4.7, 2e24), (0.8, 9e25), (7.5, 3e23), (2.2, 1e26)]
+
+
+@pytest.mark.parametrize("Z", [1, 2])
+def test_table_records_match_oracle(Z):
+    T = np.array([c[0] for c in CELLS])
+    ne = np.array([c[1] for c in CELLS])
+    prm = params(1)
+    pl = make(T, ne, prm, Z=Z)
+    got = _lib.axpic_get_spectral_records(pl.ctx, 0, len(T))
+    for c in range(len(T)):
+        want = oracle_record(T[c], ne[c], Z, prm)
+        np.testing.assert_allclose(got[c, :96], want[:96], rtol=0, atol=5e-5, err_msg="ln dQ/dx, cell %d" % c)
+        np.testing.assert_allclose(got[c, 96:189], want[96:189], rtol=2e-5, atol=2e-5, err_msg="knots, cell %d" % c)
+        np.testing.assert_allclose(got[c, 189:192], want[189:192], rtol=2e-6, atol=2e-5, err_msg="consts %d" % c)
+    pl.close()
+
+
+def test_table_model_step_matches_oracle():
+    T = np.linspace(1.3, 5.0, 16)
+    ne = np.full(16, 6e25)
+    prm = params(1)
+    pl = make(T, ne, prm)
+    recs = [oracle_record(T[c], ne[c], 1, prm) for c in range(16)]
+    mism = 0
+    for step in range(2):
+        before = [pl.cell(c) for c in range(16)]
+        res = pl.residuals()
+        pl.step(step, _lib.CH_ALL)
+        diag = pl.cell_diag()
+        for c in range(16):
+            got = pl.cell(c)
+            parts, tally, _ = oracle_step(before[c], T[c], np.array([ne[c]]), np.array([1.0]), np.array([K.A_H]),
+                                          prm, step, c, _lib.CH_ALL, res=res[c], rec=recs[c])
+            if len(got["a"]["w"]) != len(parts["a"]) or len(got["g"]["w"]) != len(parts["g"]):
+                mism += 1
+                continue
+            assert_species_close(got["a"], parts["a"], "cell %d axions" % c)
+            assert_species_close(got["g"], parts["g"], "cell %d photons" % c)
+            assert abs(diag[c][0] - tally.dE) <= 1e-5 * tally.gross_E + 1e-30
+    # record values agree to binary32 rounding: a decision may flip only when
+    # its uniform falls within ~1e-6 of its threshold
+    assert mism <= 1, mism
+    pl.close()
+
+
+def seeded_net(seed):
+    rng = np.random.default_rng(seed)
+    P = S.init_params(rng)
+    for k in P:
+        if k.startswith("b"):
+            P[k] = rng.normal(0, 0.2, P[k].shape)
+    P = {k: np.asarray(v, np.float32).astype(np.float64) for k, v in P.items()}
+    mu = rng.normal(0, 3, 96).astype(np.float32)
+    sigma = rng.uniform(0.5, 2.0, 96).astype(np.float32)
+    return P, mu, sigma
+
+
+def test_surrogate_records_match_oracle_network():
+    """The fused per-cell inference (tensor cores) against the FP64 network
+    with the same (seeded) weights; trusted everywhere."""
+    T = np.array([c[0] for c in CELLS])
+    ne = np.array([c[1] for c in CELLS])
+    prm = params(2)
+    pl = make(T, ne, prm)
+    P, mu, sigma = seeded_net(4)
+    net = SurrogateNet()
+    net.set_params(P)
+    _lib.axpic_mlp_set_norm(net.h, mu, sigma)
+    err = np.zeros(2 * 4 * 4 * 2, dtype=np.float32)
+    _lib.axpic_set_surrogate(pl.ctx, net.h, err, 4, 4, 1.0)
+    got = _lib.axpic_get_spectral_records(pl.ctx, 0, len(T))
+    for c in range(len(T)):
+        cs, _ = S.cell(T[c], ne[c], 1)
+        X = S.features(S.X_GRID, cs.kappa_keV / T[c], ne[c], 1)
+        z, _ = S.forward(P, X, bf16_mma=True)
+        y = mu.astype(np.float64) + sigma.astype(np.float64) * z
+        for ch in range(3):
+            want = y[:, 32 * ch] + S.X_GRID
+            d = np.abs(got[c, 32 * ch:32 * ch + 32] - want)
+            assert np.median(d) <= 2e-4 * max(1.0, np.abs(want).max()), (c, ch, np.median(d))
+            assert d.max() <= 2e-2 * max(1.0, np.abs(want).max()), (c, ch, d.max())
+            kw = y[0, 32 * ch + 1:32 * ch + 32]
+            assert np.max(np.abs(got[c, 96 + 31 * ch:96 + 31 * ch + 31] - kw)) <= 2e-2 * max(1, np.abs(kw).max())
+    net.close()
+    pl.close()
+
+
+def test_untrusted_cells_keep_the_table():
+    T = np.array([c[0] for c in CELLS])
+    ne = np.array([c[1] for c in CELLS])
+    ref = make(T, ne, params(1))
+    pl = make(T, ne, params(2))
+    P, mu, sigma = seeded_net(5)
+    net = SurrogateNet()
+    net.set_params(P)
+    _lib.axpic_mlp_set_norm(net.h, mu, sigma)
+    err = np.ones(2 * 4 * 4 * 2, dtype=np.float32)       # every node above the bound
+    _lib.axpic_set_surrogate(pl.ctx, net.h, err, 4, 4, 1e-3)
+    a = _lib.axpic_get_spectral_records(pl.ctx, 0, len(T))
+    b = _lib.axpic_get_spectral_records(ref.ctx, 0, len(T))
+    assert np.array_equal(a, b)
+    net.close()
+    pl.close()
+    ref.close()
+
+
+def test_training_on_gpu_learns_the_targets():
+    """The network trained by the library's own kernels on the library's
+    quadrature targets: loss falls, and its quantile error beats the
+    untrained network's by a wide margin (what training gains)."""
+    net = SurrogateNet()
+    loss = _lib.axpic_surrogate_fit(net.h, 512, 16, 1500, 2048, 3e-3, 11)
+    eL, eQ = _lib.axpic_surrogate_validate(net.h, 5, 4)
+    P0 = S.init_params(np.random.default_rng(0))
+    net0 = SurrogateNet()
+    net0.set_params(P0)
+    mu, sigma = _lib.axpic_mlp_get_norm(net.h)
+    _lib.axpic_mlp_set_norm(net0.h, mu, sigma)
+    eL0, eQ0 = _lib.axpic_surrogate_validate(net0.h, 5, 4)
+    assert loss < 0.2, loss
+    assert np.median(eQ) < 0.1 * np.median(eQ0), (np.median(eQ), np.median(eQ0))
+    assert np.median(eL) < 0.1 * np.median(eL0), (np.median(eL), np.median(eL0))
+    net.close()
+    net0.close()
