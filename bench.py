@@ -44,9 +44,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=256, help="cells per side (256: the full workload)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4"],
-                    help="c2: the 256x256 relaxation (the reported line); c4: 4096 uneven boxes in one context, "
-                         "autotuned launch shape, steps replayed as a CUDA graph")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
+                    help="c2: the 256x256 relaxation (the reported line); c3: 512x512 temperature bump, surrogate "
+                         "vs table vs closed-form rates; c4: 4096 uneven boxes in one context, autotuned launch "
+                         "shape, steps replayed as a CUDA graph")
     ap.add_argument("--boxes", type=int, default=4096, help="boxes of the c4 workload")
     return ap.parse_args()
 
@@ -301,10 +302,104 @@ def run_batched(args):
     pl.close()
 
 
+def run_rate_models(args):
+    """The temperature-bump workload (512x512 hydrogen cells, T = 1 + 4
+    exp(-r^2 / 2 64^2) keV, 256 electrons + 128 photons per cell) under the
+    three rate models: closed forms, the exact FP32 table and the surrogate
+    network (trained first by the library's own GPU kernels on its FP64
+    targets; table where its validated error exceeds 1e-3). T evolves, so the
+    spectral records are rebuilt every step. Reports particle-steps/s per
+    model and each model's rate error against the exact targets on sampled
+    cells."""
+    import torch
+    from paper_2604_24627_gb300 import AxionPlasma, _lib, workloads
+    from paper_2604_24627_gb300.mlp import SurrogateNet
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = args.nx if args.nx != 256 else 512
+    w = workloads.config3(n)
+    w.params["w_a"] = float(np.float32(workloads.photon_weight(3.0, w.volume_cm3, w.n_ph)))
+    w.params.update(seed=0, tally_enable=0, T_mode=2, relax_r=0.1)
+    stream = torch.cuda.Stream(dev)
+    # the network: trained and validated on the GPU
+    t0 = time.time()
+    net = SurrogateNet(stream=stream)
+    fit_loss = _lib.axpic_surrogate_fit(net.h, 8192, 32, 12000, 8192, 2e-3, 7)
+    fit_s = time.time() - t0
+    nT, nne = 24, 16
+    eL, eQ = _lib.axpic_surrogate_validate(net.h, nT, nne)
+    err_map = np.stack([eL, eQ], axis=-1).astype(np.float32).reshape(-1)
+    sample = np.random.default_rng(0).choice(w.ncells, 64, replace=False)
+    out = {"surrogate": {"fit_seconds": fit_s, "fit_loss": fit_loss, "params": 10720,
+                         "validated_rate_err_median": float(np.median(eL)), "validated_rate_err_max": float(eL.max()),
+                         "validated_quantile_err_median": float(np.median(eQ)),
+                         "trusted_fraction_at_1e-3": float(np.mean(eL <= 1e-3))}}
+    lines = {}
+    for model in (0, 1, 2):
+        prm = dict(w.params, rate_model=model)
+        with torch.cuda.stream(stream):
+            pl = AxionPlasma(w.ncells, w.T_keV, w.n_ion, w.Z, w.A, w.volume_cm3, w.caps, prm, device=dev,
+                             stream=stream)
+            pl.sample(w.n_el, w.n_ph, w.n_ax)
+        if model == 2:
+            _lib.axpic_set_surrogate(pl.ctx, net.h, err_map, nT, nne, 1e-3)
+        for s in range(args.warmup):
+            pl.step(s, w.mask)
+        pl.tally()
+        pl.profile_begin(args.steps)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for k in range(args.steps):
+            pl.step(args.warmup + k, w.mask)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        kms, nrec = pl.profile_end()
+        _, tot = pl.tally()
+        parts = tot["part_e"] + tot["part_g"] + tot["part_a"]
+        entry = {"particle_steps_per_s": parts / (ms * 1e-3), "ms_per_step": ms / args.steps,
+                 "kernels_ms_per_step": {k: v / max(nrec, 1) for k, v in kms.items()}}
+        if model:
+            # records of sampled cells against the exact targets at the grid points
+            recs = [_lib.axpic_get_spectral_records(pl.ctx, int(c), 1)[0] for c in sample]
+            info = pl.cell_info()
+            errs = []
+            h = math.log(400.0) / 29.0
+            xk = 0.05 * np.exp(h * (np.arange(1, 31) - 1.0))
+            for r, c in zip(recs, sample):
+                T = float(info[c, 12])
+                kT = float(info[c, 5]) / T
+                ne = float(info[c, 2])
+                rows = np.stack([xk, np.full(30, kT), np.full(30, ne), np.ones(30)], 1)
+                y = _lib.axpic_surrogate_targets(rows)
+                for ch in range(3):
+                    errs.append(np.max(np.abs(r[32 * ch + 1:32 * ch + 31] - xk - y[:, 32 * ch])))
+            entry["rate_err_max_sampled"] = float(np.max(errs))
+            entry["rate_err_median_sampled"] = float(np.median(errs))
+        lines[("closed_forms", "table", "surrogate")[model]] = entry
+        pl.close()
+    net.close()
+    line = {"metric": METRIC, "value": lines["surrogate"]["particle_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": lines["surrogate"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (temperature bump, seeded)",
+            "config": {"workload": w.name, "cells": w.ncells, "electrons_per_cell": w.n_el,
+                       "photons_per_cell": w.n_ph, "T_mode": "evolved (records rebuilt every step)"},
+            "rate_models": lines, "surrogate_vs_table": lines["surrogate"]["particle_steps_per_s"]
+            / lines["table"]["particle_steps_per_s"], "network": out["surrogate"],
+            "gpu_launches": None}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "c3":
+        run_rate_models(args)
         return
     if args.workload == "c4":
         run_batched(args)

@@ -129,8 +129,8 @@ typedef struct {
                                species with Z in {1, 2}, Debye screening and
                                ions as Primakoff targets. Not part of the
                                paper's method. */
-  int32_t sr_table_nkt;     /* table nodes in ln(kappa/T) (0: 64) */
-  int32_t sr_table_nne;     /* table nodes in log10 n_e (0: 32) */
+  int32_t sr_table_nkt;     /* table nodes in ln(kappa/T) (0: 128) */
+  int32_t sr_table_nne;     /* table nodes in log10 n_e (0: 64) */
   int32_t reserved[3];
 } axpic_params;
 

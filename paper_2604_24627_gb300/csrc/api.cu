@@ -70,7 +70,8 @@ struct axpic_ctx {
   float* sur_mu = nullptr;
   float* sur_sigma = nullptr;
   uint8_t* sur_trust = nullptr;
-  int sr_nkt = 0, sr_nne = 0, tnT = 0, tnne = 0, sur_set = 0;
+  void* sur_W16 = nullptr;  // layers 2 and 3 laid out for the tensor cores
+  int sr_nkt = 0, sr_nne = 0, tnT = 0, tnne = 0, sur_set = 0, sur_any_trusted = 0;
   float ln_gP = 0.f, ln_gA = 0.f;
   int64_t last_absorb_step = -1;
   std::string last_error;
@@ -242,7 +243,9 @@ static SrArgs make_sr_args(axpic_ctx* ctx) {
   a.P = ctx->sur_P;
   a.mu = ctx->sur_mu;
   a.sigma = ctx->sur_sigma;
-  a.trust = ctx->sur_set ? ctx->sur_trust : nullptr;
+  // no trusted node: the network is never evaluated (every cell keeps the table)
+  a.trust = ctx->sur_set && ctx->sur_any_trusted ? ctx->sur_trust : nullptr;
+  a.W16 = ctx->sur_W16;
   a.tnT = ctx->tnT;
   a.tnne = ctx->tnne;
   a.err = ctx->err;
@@ -279,7 +282,7 @@ static void free_ctx(axpic_ctx* ctx) {
   void* bufs[] = {ctx->rec,    ctx->mom,   ctx->xbuf,     ctx->res, ctx->diag,    ctx->photon_start,
                   ctx->tables, ctx->tally, ctx->counters, ctx->err, ctx->scratch, ctx->bits,
                   ctx->recA,   ctx->recG,  ctx->recE,     ctx->step_dev, ctx->sr, ctx->srtab,
-                  ctx->sur_P,  ctx->sur_mu, ctx->sur_sigma, ctx->sur_trust};
+                  ctx->sur_P,  ctx->sur_mu, ctx->sur_sigma, ctx->sur_trust, ctx->sur_W16};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete ctx;
@@ -375,8 +378,8 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
   if (p.rate_model) {
     if (d.nspecies != 1 || (d.Z[0] != 1.0 && d.Z[0] != 2.0) || p.kappa_mode != 0 || p.prim_targets != 0)
       return bad("rate models 1 and 2 need one ion species with Z 1 or 2, Debye screening and ion targets");
-    ctx->sr_nkt = p.sr_table_nkt > 0 ? p.sr_table_nkt : 64;
-    ctx->sr_nne = p.sr_table_nne > 0 ? p.sr_table_nne : 32;
+    ctx->sr_nkt = p.sr_table_nkt > 0 ? p.sr_table_nkt : 128;
+    ctx->sr_nne = p.sr_table_nne > 0 ? p.sr_table_nne : 64;
     if (ctx->sr_nkt < 2 || ctx->sr_nne < 2 || ctx->sr_nkt > 4096 || ctx->sr_nne > 4096)
       return bad("sr_table_nkt and sr_table_nne must be in [2, 4096]");
     const double hc3 = kHbarcKeVcm * kHbarcKeVcm * kHbarcKeVcm;
@@ -414,6 +417,7 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
     ALLOC(ctx->sur_P, sizeof(float) * AXPIC_MLP_PARAMS);
     ALLOC(ctx->sur_mu, sizeof(float) * 96);
     ALLOC(ctx->sur_sigma, sizeof(float) * 96);
+    ALLOC(ctx->sur_W16, kSrW16Bytes);
   }
   ALLOC(ctx->err, sizeof(int));
   ALLOC(ctx->scratch, sizeof(double) * (8 + kNumCounters + (size_t)kInfoChunk * AXPIC_CELL_INFO_LEN));
@@ -832,7 +836,11 @@ axpic_status axpic_set_surrogate(axpic_ctx* ctx, axpic_mlp* m, const float* err_
   if ((s = axpic_mlp_get_params(m, P.data())) != AXPIC_OK || (s = axpic_mlp_get_norm(m, mu.data(), sigma.data())))
     return fail(ctx, s, "axpic_set_surrogate: reading the network");
   std::vector<uint8_t> trust((size_t)2 * nT * nne);
-  for (size_t i = 0; i < trust.size(); ++i) trust[i] = err_map[2 * i] <= tol ? 1 : 0;
+  int any = 0;
+  for (size_t i = 0; i < trust.size(); ++i) {
+    trust[i] = err_map[2 * i] <= tol ? 1 : 0;
+    any |= trust[i];
+  }
   cudaStream_t st = ctx->stream;
   CK(cudaStreamSynchronize(st), "synchronize");
   if (ctx->sur_trust) cudaFree(ctx->sur_trust);
@@ -842,9 +850,11 @@ axpic_status axpic_set_surrogate(axpic_ctx* ctx, axpic_mlp* m, const float* err_
   CK(cudaMemcpyAsync(ctx->sur_mu, mu.data(), sizeof(float) * 96, cudaMemcpyHostToDevice, st), "norm");
   CK(cudaMemcpyAsync(ctx->sur_sigma, sigma.data(), sizeof(float) * 96, cudaMemcpyHostToDevice, st), "norm");
   CK(cudaMemcpyAsync(ctx->sur_trust, trust.data(), trust.size(), cudaMemcpyHostToDevice, st), "trust map");
+  CK(launch_sr_weights(ctx->sur_P, ctx->sur_W16, st), "weights");
   ctx->tnT = nT;
   ctx->tnne = nne;
   ctx->sur_set = 1;
+  ctx->sur_any_trusted = any;
   free_graphs(ctx);
   CK(build_records(ctx, st), "spectral records");
   CK(cudaStreamSynchronize(st), "synchronize");

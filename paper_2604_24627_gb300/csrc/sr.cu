@@ -112,6 +112,24 @@ __device__ __forceinline__ bool sr_trusted(const SrArgs& a, float T, float ne, f
   return t[0] && t[1] && t[a.tnT] && t[a.tnT + 1];
 }
 
+// Layers 2 and 3 as B^T (N x K = 64) bfloat16 in the core-matrix layout, laid
+// out once per network: W2^T (64 x 64) then W3^T (96 x 64).
+__global__ void sr_weights_kernel(const float* __restrict__ P, __nv_bfloat16* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 64 * 64) {
+    const int n = i >> 6, kk = i & 63;
+    out[core_off(n, kk, 64)] = __float2bfloat16_rn(P[kOffW2 + kk * 64 + n]);
+  } else if (i < 64 * 64 + 96 * 64) {
+    const int j = i - 64 * 64, n = j >> 6, kk = j & 63;
+    out[64 * 64 + core_off(n, kk, 64)] = __float2bfloat16_rn(P[kOffW3 + kk * 96 + n]);
+  }
+}
+
+cudaError_t launch_sr_weights(const float* P, void* out, cudaStream_t st) {
+  sr_weights_kernel<<<(64 * 64 + 96 * 64 + 255) / 256, 256, 0, st>>>(P, static_cast<__nv_bfloat16*>(out));
+  return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(kSrMlpThreads) sr_mlp_kernel(SrArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint64_t bar;
@@ -128,21 +146,20 @@ __global__ void __launch_bounds__(kSrMlpThreads) sr_mlp_kernel(SrArgs a) {
   if (valid) sr_cell(a, cell, &T, &kT, &ne);
   const bool trusted = valid && sr_trusted(a, T, ne, a.Z);
   if (tid == 0) any_trusted = 0;
+  __syncthreads();
+  if (trusted) any_trusted = 1;
+  __syncthreads();
+  if (!any_trusted) return;  // the table record stays: nothing to evaluate here
   if (warp == 0) tmem_alloc(&tmem_base, 256);
   if (tid == 0) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  __syncthreads();
-  if (trusted) any_trusted = 1;
-  // weights of layers 2 and 3 as B^T (N x K = 64) in the core-matrix layout
-  for (int i = tid; i < 64 * 64; i += kSrMlpThreads) {
-    const int n = i >> 6, kk = i & 63;  // W2[kk][n]
-    sW2[core_off(n, kk, 64)] = __float2bfloat16_rn(a.P[kOffW2 + kk * 64 + n]);
-  }
-  for (int i = tid; i < 96 * 64; i += kSrMlpThreads) {
-    const int n = i >> 6, kk = i & 63;  // W3[kk][n]
-    sW3[core_off(n, kk, 64)] = __float2bfloat16_rn(a.P[kOffW3 + kk * 96 + n]);
+  // the pre-laid-out weights: 20 KB of 16-byte copies
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(a.W16);
+    uint4* dst = reinterpret_cast<uint4*>(sW2);
+    for (int i = tid; i < (64 * 64 + 96 * 64) / 8; i += kSrMlpThreads) dst[i] = src[i];
   }
   // features of row (cell, k) and layer 1 on the CUDA cores
   {

@@ -43,6 +43,7 @@ struct SrArgs {
   const float* mu;
   const float* sigma;
   const uint8_t* trust;  // [2][tnne][tnT], 1 = trusted node
+  const void* W16;       // W2^T, W3^T in bfloat16, core-matrix layout (launch_sr_weights)
   int tnT, tnne;
   int* err;
 };
@@ -54,6 +55,10 @@ void build_sr_table(int nkt, int nne, double brems_shape, float* out);
 
 cudaError_t launch_sr_table(const SrArgs& a, cudaStream_t st);
 cudaError_t launch_sr_mlp(const SrArgs& a, cudaStream_t st);
+// Lays out layers 2 and 3 of the parameters P (FP32, device) for sr_mlp:
+// out holds (64 * 64 + 96 * 64) bfloat16 values (20 KB, 16-byte aligned).
+cudaError_t launch_sr_weights(const float* P, void* out, cudaStream_t st);
+constexpr size_t kSrW16Bytes = (64 * 64 + 96 * 64) * 2;
 cudaError_t sr_init_kernels();
 
 }  // namespace axpic

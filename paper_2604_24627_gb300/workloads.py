@@ -76,13 +76,16 @@ def config2(nx=256, ny=256):
 def config3(n=512, sigma=64.0):
     """2-D 512x512 with a Gaussian temperature bump 1 -> 5 keV (sigma 64
     cells), hydrogen n_e = 6e25 cm^-3, 256 electrons + 128 photons per cell,
-    prescribed temperature field, dt = 9.93e11 s."""
+    prescribed temperature field, dt = 9.93e11 s. With one axion weight (the
+    photon weight at 3 keV) the hot cells turn their heavier photons into
+    axion-weight photons (up to 128 (5/3)^3 ~ 593 per cell) and hold up to
+    ~250 axion macroparticles at equilibrium: slabs of 768 and 384 slots."""
     i = np.arange(n) + 0.5 - n / 2
     r2 = i[:, None] ** 2 + i[None, :] ** 2
     T = (1.0 + 4.0 * np.exp(-r2 / (2 * sigma ** 2))).reshape(-1)
     n_ion, Z, A = _hydrogen(n * n, 6e25)
     return Workload("c3-2d-512x512-T-bump", n * n, (n, n), T, n_ion, Z, A, VOLUME_1UM3, 256, 128, 0,
-                    (256, 192, 192),
+                    (256, 768, 384),
                     params=dict(g_agg_GeV_inv=1e-10, g_ae=1e-13, dt_phys_s=9.93e11, T_mode=1),
                     mask=7, steps=100, w_a_over_w_gamma=1.0)
 
