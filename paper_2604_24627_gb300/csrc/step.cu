@@ -435,6 +435,7 @@ __device__ __forceinline__ int quad_cell(const QuadRange<C>& R, int g) {
 // Appends this lane's flagged slots (bits of nib; words w0/w1 rotate with the
 // slot) to a warp list of current length pend; returns the new length.
 __device__ __forceinline__ int list_append(uint4* L, int pend, int cell, int slot0, uint32_t nib, uint4 w0, uint4 w1) {
+  if (!__any_sync(kFull, nib != 0)) return pend;  // the common pass: nothing flagged
   int tot;
   int o = pend + warp_excl_scan(__popc(nib), &tot);
 #pragma unroll
@@ -510,6 +511,45 @@ __device__ __forceinline__ void electron_chunk(const StepArgs& A, uint32_t step,
     }
   }
   const QuadRange<C> R = quad_range<C>(n, lane, nc);
+  if (__all_sync(kFull, lane >= nc || wu > 0.f)) {
+    // every cell of the chunk has a common weight: the decision is the
+    // integer compare alone. Two quads per lane and pass, so that two
+    // independent Philox chains are in flight.
+    for (int g0 = 0; g0 < R.total; g0 += 64) {
+      int g[2], cell[2], q[2], nj[2], cthr[2];
+      float cls[2];
+      uint4 r[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        g[h] = g0 + 32 * h + lane;
+        const int lc = quad_cell(R, g[h]);
+        const int qb = __shfl_sync(kFull, R.qoff, lc);
+        const int nn = __shfl_sync(kFull, n, lc);
+        cthr[h] = __shfl_sync(kFull, thr, lc);
+        cls[h] = __shfl_sync(kFull, lsum, lc);
+        cell[h] = c0 + lc;
+        q[h] = g[h] - qb;
+        nj[h] = min(4, nn - 4 * q[h]);
+        r[h] = philox4x32_10(make_uint4(step, A.cell_base + (uint32_t)cell[h], (uint32_t)q[h], S_EMIT_E << 24), A.rk);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (g[h] >= R.total) continue;
+        const long b = (long)cell[h] * A.e.cap + 4 * q[h];
+        uint32_t nib = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t wj = word(r[h], j);
+          if (j < nj[h] && (int)(wj >> 9) > cthr[h]) {
+            A.recE[b + j] = (uint32_t)poisson_inv(u23(wj), cls[h]);
+            nib |= 1u << j;
+          }
+        }
+        flag_quad(A.bitsE, A.We, cell[h], q[h], nib);
+      }
+    }
+    return;
+  }
   for (int g0 = 0; g0 < R.total; g0 += 32) {
     const int g = g0 + lane;
     const int lc = quad_cell(R, g);
