@@ -375,7 +375,9 @@ enum : uint32_t {
 
 // ---------------------------------------------------------------- decision kernels
 // Bit masks: word (cell * W + s / 32), bit s % 32 flags slot s. Words are
-// set by atomicOr (rare) and cleared by the event kernel after reading.
+// set by atomicOr (rare: electrons whose draw passes, axions and photons
+// whose full decision changes something) and cleared by the event kernel
+// after reading.
 
 __device__ __forceinline__ void flag_quad(uint32_t* bits, int W, int cell, int q, uint32_t nib) {
   if (nib) atomicOr(bits + (size_t)cell * W + ((4 * q) >> 5), nib << ((4 * q) & 31));
@@ -445,18 +447,23 @@ __device__ __forceinline__ int list_append(uint4* L, int pend, int cell, int slo
   return pend + tot;
 }
 
+// A full decision that changes nothing (no event, no cap hit, weight kept
+// unchanged) leaves its slot unflagged: the event kernel never sees it.
 __device__ __forceinline__ void axion_full(const StepArgs& A, uint4 it) {
   const int cell = (int)it.x;
   const long idx = (long)cell * A.a.cap + it.y;
-  const AxionDecision d =
-      axion_decide_slow(A, cell, A.mask, A.a.w[idx], A.a.px[idx], A.a.py[idx], A.a.pz[idx], it.z, it.w);
+  const float w = A.a.w[idx];
+  const AxionDecision d = axion_decide_slow(A, cell, A.mask, w, A.a.px[idx], A.a.py[idx], A.a.pz[idx], it.z, it.w);
   uint32_t f = (uint32_t)d.K;
   if (d.keep) f |= DF_KEEP;
   if (d.absorbed) f |= DF_ABSORBED;
   if (d.abs_c) f |= DF_ABS_C;
   if (d.capped) f |= DF_CAPPED;
   if (d.over) f |= DF_OVER;
+  const bool reduce = A.absorb_mode == 1 && (A.mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS));
+  if (f == DF_KEEP && d.wnew == w && !reduce) return;
   A.recA[idx] = make_uint4(f, __float_as_uint(d.wprod), __float_as_uint(d.wnew), 0u);
+  atomicOr(A.bitsA + (size_t)cell * A.Wa + (it.y >> 5), 1u << (it.y & 31));
 }
 
 __device__ __forceinline__ void photon_full(const StepArgs& A, uint4 it) {
@@ -467,7 +474,9 @@ __device__ __forceinline__ void photon_full(const StepArgs& A, uint4 it) {
   if (d.wrem > 0.f) f |= DF_KEEP;
   if (d.capped) f |= DF_CAPPED;
   if (d.over) f |= DF_OVER;
+  if (f == DF_KEEP) return;
   A.recG[idx] = make_uint4(f, __float_as_uint(d.wprod), __float_as_uint(d.wrem), 0u);
+  atomicOr(A.bitsG + (size_t)cell * A.Wg + (it.y >> 5), 1u << (it.y & 31));
 }
 
 // Decides full batches of 32 from the top of a list; returns what is left.
@@ -638,7 +647,6 @@ __device__ __forceinline__ int photon_chunk(const StepArgs& A, uint32_t step, in
         if (j < nj && !no_conversion(f4(w4, j), p2, cs, ca, A.inv_w_a, u23(word(r, j)), A.lam_cap, A.guard_margin))
           nib |= 1u << j;
       }
-      flag_quad(A.bitsG, A.Wg, cell, q, nib);
     }
     pend = list_append(L, pend, cell, 4 * q, nib, r, r);
     pend = list_drain<false>(A, L, pend, lane);
@@ -698,7 +706,6 @@ __device__ __forceinline__ int axion_chunk(const StepArgs& A, uint32_t step, int
         if (fast && bath) fast = no_absorption(cbc, cbb, A, mask, sqrtf(p2) * kMeC2f * cinvT, u23(word(rA, j)));
         if (j < nj && !fast) nib |= 1u << j;
       }
-      flag_quad(A.bitsA, A.Wa, cell, q, nib);
     }
     pend = list_append(L, pend, cell, 4 * q, nib, rP, rA);
     pend = list_drain<true>(A, L, pend, lane);
@@ -738,38 +745,254 @@ __global__ void __launch_bounds__(kDecThreads, AXPIC_DEC_MIN_CTAS) decide_kernel
   if (lane < pa) axion_full(A, L.a[wid][lane]);
 }
 
-// ---------------------------------------------------------------- event kernel
-// Per-warp shared scratch: ascending lists of flagged slots and of removed
-// slots (u16), and removed-slot bit masks.
-// Flagged items staged in shared memory by asynchronous copies (no register
-// holds a load in flight): the first 32 flagged axions and photons of a cell,
-// and the first 32 tail positions of each species' tail fill.
-struct Fields7 {
-  float w[32], px[32], py[32], pz[32], x[32], y[32], z[32];
-};
-struct EvStage {
-  uint4 ar[32];
-  Fields7 a;  // flagged axions; then the axion tail-fill movers
-  uint4 gr[32];
-  Fields7 g;   // flagged photons (w unused)
-  Fields7 mg;  // photon tail-fill movers
+// ---------------------------------------------------------------- feedback kernel
+// Per cell: the exchange of this step plus the carried part; when it is
+// representable in binary32 momenta the cell's electrons get the affine remap
+// (Eqs. delta_def to b_def, affine_map) by a whole warp, measuring what was
+// applied; then the temperature update (Eqs. Te_est, Te_relax) and the
+// record's temperature half.
+struct FbCell {
+  double dE, dPx, dPy, dPz;  // this step's exchange
+  double rE, rPx, rPy, rPz;  // carried exchange
+  double T;
+  double qE, qPx, qPy, qPz, s1d, bx, by, bz, vnd;
+  float W, Px, Py, Pz, U2, var;
+  float4 rc[4];
+  int ne;
+  bool has_x, has_res, need;
 };
 
-// Per-warp scratch: flagged-slot lists (the removed lists reuse them: a
-// chunk's entries are read before removed entries at or below their index
-// are written), removed-slot bits and the stage.
+// What the feedback of a cell reads besides the exchange.
+__device__ __forceinline__ void fb_load(const StepArgs& A, int cell, FbCell& f) {
+  const double* rs = A.res + (size_t)cell * 4;
+  f.rE = rs[0];
+  f.rPx = rs[1];
+  f.rPy = rs[2];
+  f.rPz = rs[3];
+  const float* mom = A.mom + (size_t)cell * kMomLen;
+  f.W = mom[M_W];
+  f.Px = mom[M_PX];
+  f.Py = mom[M_PY];
+  f.Pz = mom[M_PZ];
+  f.U2 = mom[M_U2];
+  f.var = mom[M_VAR];
+  f.ne = min(max(A.e.count[cell], 0), A.e.cap);
+  f.T = 0.0;
+  f.rc[0] = f.rc[1] = f.rc[2] = f.rc[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (A.T_mode == 2) {
+    f.T = A.T[cell];
+    const float4* r4 = reinterpret_cast<const float4*>(A.rec + (size_t)cell * kRecLen);
+    f.rc[0] = r4[0];
+    f.rc[1] = r4[1];
+    f.rc[2] = r4[2];
+    f.rc[3] = r4[3];
+  }
+}
+
+// The pending exchange and, when it needs a remap now, the map's s - 1 and b.
+__device__ __forceinline__ void fb_prepare(FbCell& f) {
+  f.has_x = nz64(f.dE) || nz64(f.dPx) || nz64(f.dPy) || nz64(f.dPz);
+  f.has_res = nz64(f.rE) || nz64(f.rPx) || nz64(f.rPy) || nz64(f.rPz);
+  f.need = false;
+  f.qE = f.qPx = f.qPy = f.qPz = f.s1d = f.bx = f.by = f.bz = f.vnd = 0.0;
+  if (!(f.has_x || f.has_res)) return;
+  f.qE = f.dE + f.rE;
+  f.qPx = f.dPx + f.rPx;
+  f.qPy = f.dPy + f.rPy;
+  f.qPz = f.dPz + f.rPz;
+  // Exchanges below 2^-22 of the cell's kinetic energy (or momentum spread)
+  // cannot be represented by binary32 momenta; they stay pending.
+  const float ekin = 0.5f * f.U2 * kMeC2f;
+  const float prms = sqrtf(fmaxf(f.U2 * f.W, 0.f));
+  f.need = f.W > 0.f && (fabsf((float)f.qE) >= 2.384185791015625e-07f * ekin ||
+                         sqrtf((float)(f.qPx * f.qPx + f.qPy * f.qPy + f.qPz * f.qPz)) >=
+                             2.384185791015625e-07f * prms);
+  if (!f.need) return;
+  // Eqs. delta_def, dE_bulk, dE_th, var_new, s_def, b_def (mu = 1)
+  const double Wd = f.W;
+  const double dx = f.qPx / Wd, dy = f.qPy / Wd, dz = f.qPz / Wd;
+  const double dEb = (2.0 * (dx * f.Px + dy * f.Py + dz * f.Pz) + Wd * (dx * dx + dy * dy + dz * dz)) * 0.5;
+  const double dEth = f.qE / kMeC2 - dEb;
+  f.vnd = f.var;
+  if (f.var > 0.f) {
+    f.vnd = fmax(0.0, (double)f.var + 2.0 * dEth);
+    const double S = sqrt(f.vnd / (double)f.var);
+    f.s1d = ((f.vnd - (double)f.var) / (double)f.var) / (S + 1.0);
+  }
+  f.bx = -f.s1d * f.Px / Wd + dx;
+  f.by = -f.s1d * f.Py / Wd + dy;
+  f.bz = -f.s1d * f.Pz / Wd + dz;
+}
+
+// Carry, moments, diagnostics, temperature and record once the remap (r;
+// null when the cell was not remapped) is done.
+__device__ __forceinline__ void fb_finish(const StepArgs& A, int cell, const FbCell& f, const RemapOut* r) {
+  double nrE = f.qE, nrPx = f.qPx, nrPy = f.qPy, nrPz = f.qPz, applied_E = 0.0;
+  float var_new = f.var;
+  if (r) {
+    applied_E = r->applied_E;
+    nrE = f.qE - r->applied_E;
+    nrPx = f.qPx - r->apx;
+    nrPy = f.qPy - r->apy;
+    nrPz = f.qPz - r->apz;
+    var_new = (float)f.vnd;
+    float* mom = A.mom + (size_t)cell * kMomLen;
+    mom[M_W] = r->mW;
+    mom[M_PX] = r->mPx;
+    mom[M_PY] = r->mPy;
+    mom[M_PZ] = r->mPz;
+    mom[M_U2] = r->mU2;
+    mom[M_VAR] = fmaxf(0.f, r->mU2 - (r->mPx * r->mPx + r->mPy * r->mPy + r->mPz * r->mPz) / r->mW);
+  }
+  if (f.has_x || f.has_res) {
+    double* rs = A.res + (size_t)cell * 4;
+    rs[0] = nrE;
+    rs[1] = nrPx;
+    rs[2] = nrPy;
+    rs[3] = nrPz;
+  }
+  if (A.diag_enable) {
+    double* dg = A.diag + (size_t)cell * AXPIC_CELL_DIAG_LEN;
+    dg[AXPIC_CD_DE] = f.dE;
+    dg[AXPIC_CD_DPX] = f.dPx;
+    dg[AXPIC_CD_DPY] = f.dPy;
+    dg[AXPIC_CD_DPZ] = f.dPz;
+    dg[AXPIC_CD_S_MINUS_1] = f.s1d;
+    dg[AXPIC_CD_BX] = f.bx;
+    dg[AXPIC_CD_BY] = f.by;
+    dg[AXPIC_CD_BZ] = f.bz;
+    dg[AXPIC_CD_VAR] = f.var;
+    dg[AXPIC_CD_VAR_NEW] = f.need ? f.vnd : (double)f.var;
+    dg[AXPIC_CD_W] = f.W;
+    dg[AXPIC_CD_APPLIED_E] = applied_E;
+    dg[AXPIC_CD_RES_E] = f.has_x || f.has_res ? nrE : 0.0;
+    dg[AXPIC_CD_RES_PX] = f.has_x || f.has_res ? nrPx : 0.0;
+    dg[AXPIC_CD_RES_PY] = f.has_x || f.has_res ? nrPy : 0.0;
+    dg[AXPIC_CD_RES_PZ] = f.has_x || f.has_res ? nrPz : 0.0;
+  }
+  // temperature (Eqs. Te_est, Te_relax), then the record's temperature half;
+  // T stays FP64, the relaxation step is formed in binary32 and added once
+  if (A.T_mode == 2 && f.W > 0.f) {
+    const float Tf = (float)f.T;
+    const float Test = (kMeC2f / 3.0f) * var_new / f.W;
+    const float dT = A.relax_r * (Test - Tf);
+    double Tn = f.T + (double)dT;
+    const float Tnf = Tf + dT;
+    if (Tnf <= A.T_floor_f || Tnf >= A.T_ceil_f) Tn = fmin(fmax(Tn, A.T_floor), A.T_ceil);
+    float rec[kRecLen] = {f.rc[0].x, f.rc[0].y, f.rc[0].z, f.rc[0].w, f.rc[1].x, f.rc[1].y, f.rc[1].z, f.rc[1].w,
+                          f.rc[2].x, f.rc[2].y, f.rc[2].z, f.rc[2].w, f.rc[3].x, f.rc[3].y, f.rc[3].z, f.rc[3].w};
+    compute_temperature(A.cc, (float)Tn, rec);
+    A.T[cell] = Tn;
+    float4* r4 = reinterpret_cast<float4*>(A.rec + (size_t)cell * kRecLen);
+    r4[0] = make_float4(rec[0], rec[1], rec[2], rec[3]);
+    r4[1] = make_float4(rec[4], rec[5], rec[6], rec[7]);
+  }
+}
+
+// Thread per cell, every load issued first;
+// cells whose exchange needs an affine remap go to a CTA list and the CTA's
+// warps remap them side by side, a warp per cell; then each thread finishes
+// its cell.
+struct RemapJob {
+  int cell, ne;
+  float s1, bx, by, bz;
+};
+constexpr int kFeedbackThreads = 128;
+
+__global__ void __launch_bounds__(kFeedbackThreads) feedback_kernel(StepArgs A) {
+  // a replayed graph takes its step index from the device counter: the last
+  // kernel of the step advances it (no kernel of this launch reads it)
+  if (A.step_dev && blockIdx.x == 0 && threadIdx.x == 0) *A.step_dev += 1u;
+  __shared__ RemapJob jobs[kFeedbackThreads];
+  __shared__ RemapOut outs[kFeedbackThreads];
+  __shared__ int njobs;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = cell < A.ncells;
+  if (threadIdx.x == 0) njobs = 0;
+  FbCell f = {};
+  if (valid) {
+    double* xb = A.xbuf + (size_t)cell * 4;
+    f.dE = xb[0];
+    f.dPx = xb[1];
+    f.dPy = xb[2];
+    f.dPz = xb[3];
+    fb_load(A, cell, f);
+    fb_prepare(f);
+    if (f.has_x) {
+      xb[0] = 0.0;
+      xb[1] = 0.0;
+      xb[2] = 0.0;
+      xb[3] = 0.0;
+    }
+  }
+  __syncthreads();
+  int job = -1;
+  if (f.need) {
+    job = atomicAdd(&njobs, 1);
+    jobs[job] = RemapJob{cell, f.ne, (float)f.s1d, (float)f.bx, (float)f.by, (float)f.bz};
+  }
+  __syncthreads();
+  const int nj = njobs;
+  for (int k = wid; k < nj; k += kFeedbackThreads / 32) {
+    const RemapJob J = jobs[k];
+    const RemapOut r = remap_electrons(A, (long)J.cell * A.e.cap, J.ne, J.s1, J.bx, J.by, J.bz);
+    if (lane == 0) outs[k] = r;
+  }
+  __syncthreads();
+  if (!valid) return;
+  fb_finish(A, cell, f, job >= 0 ? &outs[job] : nullptr);
+  if (f.need) {
+    atomicAdd(A.counters + C_REMAP, 1ull);
+    atomicAdd(A.counters + C_REMAP_E, (unsigned long long)f.ne);
+  }
+}
+
+
+// ---------------------------------------------------------------- event kernel
+// Warp w takes cells [32 w, 32 w + 32), lane l cell 32 w + l. Most cells
+// have a handful of flagged slots: the lane then takes the cell alone, so the
+// per-cell scans, counts and stores are shared by 32 cells per instruction.
+// A cell with more flagged slots in a phase than a lane takes is done by the
+// whole warp for that phase.
+//
+// Per-warp shared scratch:
+//   flagged-slot lists of one heavy cell (u16, full capacities; the removed
+//   lists reuse them) and its removed-slot bits;
+//   the lanes' lists: kLight entries per species and lane, entry i of lane l
+//   at [32 i + l] (the removed list reuses it in place);
+//   the 32 cells' mask rows, copied in by cp.async (row stride W | 1 words,
+//   so that lanes reading their own rows hit distinct banks).
+
+// Flagged slots per species up to which one lane takes a cell's phase
+// (electrons: kLightE, each event with its own Philox block).
+constexpr int kLight = 8;
+constexpr int kLightE = 4;
+// Flagged slots and tail movers per species whose loads go out together.
+constexpr int kLoad = 2;
+constexpr size_t kLaneListBytes = 3 * kLight * 32 * sizeof(uint16_t);
+
 struct EvScratch {
   uint16_t *flA, *flG, *flE, *rmA, *rmG;
   uint32_t *rbA, *rbG;
-  EvStage* st;
+  uint16_t* lt;
+  uint32_t *rowA, *rowG, *rowE;  // null when some row is longer than 32 words
+  int sA, sG, sE;
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+__host__ __device__ inline int row_words(int cap) { return (cap + 31) / 32; }
+__host__ __device__ inline bool rows_staged(int acap, int gcap, int ecap) {
+  return row_words(acap) <= 32 && row_words(gcap) <= 32 && row_words(ecap) <= 32;
+}
 
 __host__ __device__ inline size_t ev_scratch_bytes(int acap, int gcap, int ecap) {
   size_t b = align16(2 * ((size_t)acap + (size_t)gcap + (size_t)ecap));
-  b = align16(b + 4 * (size_t)((acap + 31) / 32 + (gcap + 31) / 32));
-  return b + sizeof(EvStage);
+  b = align16(b + 4 * (size_t)(row_words(acap) + row_words(gcap)));
+  b += kLaneListBytes;
+  if (rows_staged(acap, gcap, ecap))
+    b += align16(4 * 32 * (size_t)((row_words(acap) | 1) + (row_words(gcap) | 1) + (row_words(ecap) | 1)));
+  return b;
 }
 
 __device__ inline EvScratch ev_carve(unsigned char* base, int acap, int gcap, int ecap) {
@@ -780,21 +1003,29 @@ __device__ inline EvScratch ev_carve(unsigned char* base, int acap, int gcap, in
   s.flE = h; h += ecap;
   s.rmA = s.flA;
   s.rmG = s.flG;
-  uint32_t* u = reinterpret_cast<uint32_t*>(base + align16(2 * ((size_t)acap + gcap + ecap)));
-  s.rbA = u; u += (acap + 31) / 32;
+  size_t off = align16(2 * ((size_t)acap + gcap + ecap));
+  uint32_t* u = reinterpret_cast<uint32_t*>(base + off);
+  s.rbA = u; u += row_words(acap);
   s.rbG = u;
-  s.st = reinterpret_cast<EvStage*>(base + align16(align16(2 * ((size_t)acap + gcap + ecap)) +
-                                                   4 * (size_t)((acap + 31) / 32 + (gcap + 31) / 32)));
+  off = align16(off + 4 * (size_t)(row_words(acap) + row_words(gcap)));
+  s.lt = reinterpret_cast<uint16_t*>(base + off);
+  off += kLaneListBytes;
+  s.sA = row_words(acap) | 1;
+  s.sG = row_words(gcap) | 1;
+  s.sE = row_words(ecap) | 1;
+  if (rows_staged(acap, gcap, ecap)) {
+    s.rowA = reinterpret_cast<uint32_t*>(base + off);
+    s.rowG = s.rowA + 32 * s.sA;
+    s.rowE = s.rowG + 32 * s.sG;
+  } else {
+    s.rowA = s.rowG = s.rowE = nullptr;
+  }
   return s;
 }
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 // Waits for this thread's copies; the warp then synchronises to see all.
 __device__ __forceinline__ void cp_async_wait_all() {
@@ -815,61 +1046,31 @@ __device__ __forceinline__ int list_flags(uint32_t v, int wi, int nw, int n, uin
   return total + tot;
 }
 
-// Reads and clears the cell's bit-mask words covering [0, n) and writes the
-// flagged slots in ascending order to `list`. Returns their number.
-__device__ __noinline__ int gather_flags(uint32_t* bits, int W, int cell, int n, uint16_t* list) {
+// Writes the flagged slots of a mask row covering [0, n) to `list` in
+// ascending order (warp-wide) and returns their number. The row is the
+// staged copy, or the global row itself, which is then cleared (clr).
+__device__ __noinline__ int gather_row(const uint32_t* row, uint32_t* clr, int n, uint16_t* list) {
   const int lane = lane_id();
   const int nw = (n + 31) >> 5;
-  uint32_t* row = bits + (size_t)cell * W;
   int total = 0;
   for (int w0 = 0; w0 < nw; w0 += 32) {
     const int wi = w0 + lane;
     const uint32_t v = wi < nw ? row[wi] : 0u;
-    if (v) row[wi] = 0u;
+    if (clr && v) clr[wi] = 0u;
     total = list_flags(v, wi, nw, n, list, total);
   }
   return total;
 }
 
-// Tail fill with the ascending removed list: holes are the removed slots
-// below n_surv, movers the kept slots at or beyond it, matched in order. The
-// movers of the first 32 positions of the tail [n_surv, n) are staged by
-// mover_stage (so that their copies are in flight with other work) and
-// written by mover_commit; compact_rest moves the positions from n_surv + 32
-// on.
-// Stages the movers of the first 32 tail positions; *dst is the slot this
-// lane's mover fills (or -1). Returns the number of movers staged.
-__device__ __forceinline__ int mover_stage(const SpeciesPtrs& s, long base, const uint16_t* rm, const uint32_t* rb,
-                                           int n_surv, int n, Fields7& F, int* dst) {
-  const int lane = lane_id();
-  const int i = n_surv + lane;
-  const bool mv = i < n && !bit(rb, i);
-  const unsigned msk = __ballot_sync(kFull, mv);
-  *dst = -1;
-  if (mv) {
-    const long src = base + i;
-    *dst = rm[__popc(msk & ((1u << lane) - 1u))];
-    cp_async4(&F.w[lane], s.w + src);
-    cp_async4(&F.px[lane], s.px + src);
-    cp_async4(&F.py[lane], s.py + src);
-    cp_async4(&F.pz[lane], s.pz + src);
-    cp_async4(&F.x[lane], s.x + src);
-    cp_async4(&F.y[lane], s.y + src);
-    cp_async4(&F.z[lane], s.z + src);
-  }
-  return __popc(msk);
-}
-
-__device__ __forceinline__ void mover_commit(const SpeciesPtrs& s, long base, const Fields7& F, int dst) {
-  const int lane = lane_id();
-  if (dst >= 0) write_particle(s, base + dst, F.w[lane], F.px[lane], F.py[lane], F.pz[lane], F.x[lane], F.y[lane], F.z[lane]);
-}
-
-__device__ __noinline__ void compact_rest(const SpeciesPtrs& s, long base, const uint16_t* rm, int run,
-                                          const uint32_t* rb, int n_surv, int n) {
+// Tail fill by the warp with the ascending removed list: holes are the
+// removed slots below n_surv, movers the kept slots at or beyond it, matched
+// in order.
+__device__ __noinline__ void compact_tail(const SpeciesPtrs& s, long base, const uint16_t* rm, const uint32_t* rb,
+                                          int n_surv, int n) {
   const int lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
-  for (int b0 = n_surv + 32; b0 < n; b0 += 32) {
+  int run = 0;
+  for (int b0 = n_surv; b0 < n; b0 += 32) {
     const int i = b0 + lane;
     const bool mv = i < n && !bit(rb, i);
     const unsigned m = __ballot_sync(kFull, mv);
@@ -900,14 +1101,13 @@ struct ElItem {
   int slot;
 };
 
-__device__ __forceinline__ AxItem ax_load(const StepArgs& A, long base, const uint16_t* fl, int i, int n) {
+__device__ __forceinline__ AxItem ax_load(const StepArgs& A, long base, int slot) {
   AxItem t;
-  t.slot = -1;
+  t.slot = slot;
   t.r = make_uint4(0, 0, 0, 0);
   t.w = t.px = t.py = t.pz = t.x = t.y = t.z = 0.f;
-  if (i < n) {
-    t.slot = fl[i];
-    const long src = base + t.slot;
+  if (slot >= 0) {
+    const long src = base + slot;
     t.r = A.recA[src];
     t.w = A.a.w[src];
     t.px = A.a.px[src];
@@ -920,14 +1120,13 @@ __device__ __forceinline__ AxItem ax_load(const StepArgs& A, long base, const ui
   return t;
 }
 
-__device__ __forceinline__ PhItem ph_load(const StepArgs& A, long base, const uint16_t* fl, int i, int n) {
+__device__ __forceinline__ PhItem ph_load(const StepArgs& A, long base, int slot) {
   PhItem t;
-  t.slot = -1;
+  t.slot = slot;
   t.r = make_uint4(0, 0, 0, 0);
   t.px = t.py = t.pz = t.x = t.y = t.z = 0.f;
-  if (i < n) {
-    t.slot = fl[i];
-    const long src = base + t.slot;
+  if (slot >= 0) {
+    const long src = base + slot;
     t.r = A.recG[src];
     t.px = A.g.px[src];
     t.py = A.g.py[src];
@@ -939,52 +1138,14 @@ __device__ __forceinline__ PhItem ph_load(const StepArgs& A, long base, const ui
   return t;
 }
 
-__device__ __forceinline__ AxItem ax_staged(const EvStage& T, const uint16_t* fl, int lane, int n) {
-  AxItem t;
-  t.slot = -1;
-  t.r = make_uint4(0, 0, 0, 0);
-  t.w = t.px = t.py = t.pz = t.x = t.y = t.z = 0.f;
-  if (lane < n) {
-    t.slot = fl[lane];
-    t.r = T.ar[lane];
-    t.w = T.a.w[lane];
-    t.px = T.a.px[lane];
-    t.py = T.a.py[lane];
-    t.pz = T.a.pz[lane];
-    t.x = T.a.x[lane];
-    t.y = T.a.y[lane];
-    t.z = T.a.z[lane];
-  }
-  return t;
-}
-
-__device__ __forceinline__ PhItem ph_staged(const EvStage& T, const uint16_t* fl, int lane, int n) {
-  PhItem t;
-  t.slot = -1;
-  t.r = make_uint4(0, 0, 0, 0);
-  t.px = t.py = t.pz = t.x = t.y = t.z = 0.f;
-  if (lane < n) {
-    t.slot = fl[lane];
-    t.r = T.gr[lane];
-    t.px = T.g.px[lane];
-    t.py = T.g.py[lane];
-    t.pz = T.g.pz[lane];
-    t.x = T.g.x[lane];
-    t.y = T.g.y[lane];
-    t.z = T.g.z[lane];
-  }
-  return t;
-}
-
-__device__ __forceinline__ ElItem el_load(const StepArgs& A, long base, const uint16_t* fl, int i, int n, float wu) {
+__device__ __forceinline__ ElItem el_load(const StepArgs& A, long base, int slot, float wu) {
   ElItem t;
-  t.slot = -1;
+  t.slot = slot;
   t.f = 0u;
   t.w = wu;
   t.x = t.y = t.z = 0.f;
-  if (i < n) {
-    t.slot = fl[i];
-    const long src = base + t.slot;
+  if (slot >= 0) {
+    const long src = base + slot;
     t.f = A.recE[src];
     t.x = A.e.x[src];
     t.y = A.e.y[src];
@@ -994,395 +1155,460 @@ __device__ __forceinline__ ElItem el_load(const StepArgs& A, long base, const ui
   return t;
 }
 
-// One cell's events, by one warp. Round trips: (1) counts, decision masks,
-// per-cell constants and the exchange buffer; (2) the records and fields of
-// the flagged slots of every species; (3) the tail-fill movers of both
-// species; then the stores. Output order is the method's: photon products of
-// a->gamma after the photons present, axion products of gamma->a after the
-// surviving axions, then the thermal-bath products in electron then event
-// order; removed slots are refilled from the tail.
-template <int PH>
-__device__ __forceinline__ void event_cell(const StepArgs& A, uint32_t step, int cell, EvScratch& S, const Cnt& cnt) {
-  const int lane = lane_id();
-  const unsigned lt = (1u << lane) - 1u;
-  const uint32_t gcell = A.cell_base + (uint32_t)cell;
-  const int mask = A.mask;
-  const bool prim = mask & AXPIC_CH_PRIMAKOFF;
-  const bool bath = mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS);
-  const bool eC = mask & AXPIC_CH_COMPTON, eB = mask & AXPIC_CH_BREMS;
-  const bool emitG = (PH & PH_EMIT) && prim;
-  const bool emitE = (PH & PH_EMIT) && (eC || eB);
-  const long abase = (long)cell * A.a.cap;
-  const long gbase = (long)cell * A.g.cap;
-  const long ebase = (long)cell * A.e.cap;
+// ---------------------------------------------------------------- per-slot outcomes
+// Shared by the lane and warp paths. Output order is the method's: photon
+// products of a->gamma after the photons present, axion products of gamma->a
+// after the surviving axions, then the thermal-bath products in electron then
+// event order; removed slots are refilled from the tail.
 
-  // ------------------------------------------------------------ round trip 1
-  const int ne = min(max(A.e.count[cell], 0), A.e.cap);
-  const int ng_start = min(max(A.g.count[cell], 0), A.g.cap);
-  const int na_start = min(max(A.a.count[cell], 0), A.a.cap);
-  const int pstart = (!(PH & PH_ABSORB) && A.use_snapshot) ? A.photon_start[cell] : 0;
-  float wu = 0.f, r_cc = 0.f, r_cb = 0.f, r_T = 0.f;
-  if (emitE) {
-    const float* rec = A.rec + (size_t)cell * kRecLen;
-    wu = A.mom[(size_t)cell * kMomLen + M_WU];
-    r_cc = rec[R_CC];
-    r_cb = rec[R_CB];
-    r_T = rec[R_T];
+// A flagged axion: counters, exchange, new weight. Returns K; *removed tells
+// whether the slot leaves the slab.
+__device__ __forceinline__ int axion_outcome(const StepArgs& A, const AxItem& t, long abase, bool bath,
+                                             const Cnt& cnt, Lane64& x64, bool* removed) {
+  const int K = t.r.x & 0xFF;
+  const float wprod = __uint_as_float(t.r.y);
+  const float wnew = __uint_as_float(t.r.z);
+  const float om = sqrtf(t.px * t.px + t.py * t.py + t.pz * t.pz) * kMeC2f;
+  cnt.add(C_CAP, (t.r.x & DF_CAPPED) ? 1u : 0u);
+  cnt.add(C_CLAMP, (t.r.x & DF_OVER) ? 1u : 0u);
+  cnt.add(C_EV_PINV, (unsigned)K);
+  if (t.r.x & DF_ABSORBED) {
+    x64.add((double)wnew, om, t.px, t.py, t.pz);
+    cnt.add((t.r.x & DF_ABS_C) ? C_ABS_C : C_ABS_B, 1);
+  } else if (A.absorb_mode == 1 && bath) {
+    // weight reduction: the lost weight's energy goes to the plasma
+    float wrem = t.w;
+    if (K > 0) wrem = (t.r.x & DF_OVER) ? 0.f : __fsub_rn(t.w, __fmul_rn((float)K, wprod));
+    x64.add((double)wrem - (double)wnew, om, t.px, t.py, t.pz);
   }
-  // lanes 0..3 hold one component each of the cell's exchange buffer
-  double* xb = A.xbuf + (size_t)cell * 4;
-  const double xb_old = lane < 4 ? xb[lane] : 0.0;
-  int nflA = 0, nflG = 0, nflE = 0;
-  const int ng0 = (PH & PH_ABSORB) ? ng_start : (A.use_snapshot ? min(pstart, ng_start) : ng_start);
-  {
-    // whole mask rows are loaded without waiting for the counts: bits beyond
-    // a count are never set
-    if (A.Wa <= 32 && A.Wg <= 32 && A.We <= 32) {
-      uint32_t* rA = A.bitsA + (size_t)cell * A.Wa;
-      uint32_t* rG = A.bitsG + (size_t)cell * A.Wg;
-      uint32_t* rE = A.bitsE + (size_t)cell * A.We;
-      const uint32_t vA = (PH & PH_ABSORB) && lane < A.Wa ? rA[lane] : 0u;
-      const uint32_t vG = emitG && lane < A.Wg ? rG[lane] : 0u;
-      const uint32_t vE = emitE && lane < A.We ? rE[lane] : 0u;
-      if (vA) rA[lane] = 0u;
-      if (vG) rG[lane] = 0u;
-      if (vE) rE[lane] = 0u;
-      if (__any_sync(kFull, vA != 0)) nflA = list_flags(vA, lane, (na_start + 31) >> 5, na_start, S.flA, 0);
-      if (__any_sync(kFull, vG != 0)) nflG = list_flags(vG, lane, (ng0 + 31) >> 5, ng0, S.flG, 0);
-      if (__any_sync(kFull, vE != 0)) nflE = list_flags(vE, lane, (ne + 31) >> 5, ne, S.flE, 0);
+  *removed = !(t.r.x & DF_KEEP);
+  if (!*removed && wnew != t.w) A.a.w[abase + t.slot] = wnew;
+  return K;
+}
+
+// A flagged photon: counters and the remaining weight. Returns K.
+__device__ __forceinline__ int photon_outcome(const StepArgs& A, const PhItem& t, long gbase, const Cnt& cnt,
+                                              bool* removed) {
+  const int K = t.r.x & 0xFF;
+  cnt.add(C_CAP, (t.r.x & DF_CAPPED) ? 1u : 0u);
+  cnt.add(C_CLAMP, (t.r.x & DF_OVER) ? 1u : 0u);
+  cnt.add(C_EV_P, (unsigned)K);
+  *removed = !(t.r.x & DF_KEEP);
+  if (K && !*removed) A.g.w[gbase + t.slot] = __uint_as_float(t.r.z);
+  return K;
+}
+
+// The K axion products of a gamma->a event, from position dst0 on.
+__device__ __forceinline__ void gamma_products(const StepArgs& A, const PhItem& t, long abase, int dst0, int K,
+                                               const Cnt& cnt) {
+  const float wprod = __uint_as_float(t.r.y);
+  const float om = sqrtf(t.px * t.px + t.py * t.py + t.pz * t.pz) * kMeC2f;
+  for (int k = 0; k < K; ++k) {
+    const int dst = dst0 + k;
+    if (dst < A.a.cap) {
+      write_particle(A.a, abase + dst, wprod, t.px, t.py, t.pz, t.x, t.y, t.z);
+      if (A.tally_enable) tally_add(A, 0, wprod, om);
     } else {
-      if (PH & PH_ABSORB) nflA = gather_flags(A.bitsA, A.Wa, cell, na_start, S.flA);
-      if (emitG) nflG = gather_flags(A.bitsG, A.Wg, cell, ng0, S.flG);
-      if (emitE) nflE = gather_flags(A.bitsE, A.We, cell, ne, S.flE);
+      cnt.add(C_DROP, 1);
     }
-    __syncwarp();
-  }
-  // particles present at the start of the step: counted by the absorb phase,
-  // or by the emit phase when no absorb ran this step
-  if (lane == 0 && ((PH & PH_ABSORB) || ((PH & PH_EMIT) && !A.use_snapshot))) {
-    cnt.add(C_NE, ne);
-    cnt.add(C_NG, ng_start);
-    cnt.add(C_NA, na_start);
-    cnt.add(C_CELLS, 1);
-  }
-  if ((PH & PH_ABSORB) && lane == 0) A.photon_start[cell] = ng_start;
-
-  // ------------------------------------------------------------ round trip 2
-  // records and fields of the first 32 flagged axions and photons, staged by
-  // asynchronous copies
-  EvStage& T = *S.st;
-  if ((PH & PH_ABSORB) && lane < nflA) {
-    const long src = abase + S.flA[lane];
-    cp_async16(&T.ar[lane], A.recA + src);
-    cp_async4(&T.a.w[lane], A.a.w + src);
-    cp_async4(&T.a.px[lane], A.a.px + src);
-    cp_async4(&T.a.py[lane], A.a.py + src);
-    cp_async4(&T.a.pz[lane], A.a.pz + src);
-    cp_async4(&T.a.x[lane], A.a.x + src);
-    cp_async4(&T.a.y[lane], A.a.y + src);
-    cp_async4(&T.a.z[lane], A.a.z + src);
-  }
-  if (emitG && lane < nflG) {
-    const long src = gbase + S.flG[lane];
-    cp_async16(&T.gr[lane], A.recG + src);
-    cp_async4(&T.g.px[lane], A.g.px + src);
-    cp_async4(&T.g.py[lane], A.g.py + src);
-    cp_async4(&T.g.pz[lane], A.g.pz + src);
-    cp_async4(&T.g.x[lane], A.g.x + src);
-    cp_async4(&T.g.y[lane], A.g.y + src);
-    cp_async4(&T.g.z[lane], A.g.z + src);
-  }
-  cp_async_wait_all();
-  __syncwarp();
-
-  Lane64 x64;
-  double xa[4] = {0.0, 0.0, 0.0, 0.0};
-  bool xa_any = false;
-  int ng = ng_start, na = na_start, nrmA = 0;
-
-  // ------------------------------------------------------------ absorb
-  if ((PH & PH_ABSORB) && nflA > 0) {
-    for (int i = lane; i < (na_start + 31) / 32; i += 32) S.rbA[i] = 0u;
-    __syncwarp();
-    int run = 0, NPg = 0;
-    for (int i0 = 0; i0 < nflA; i0 += 32) {
-      const AxItem t = i0 == 0 ? ax_staged(T, S.flA, lane, nflA) : ax_load(A, abase, S.flA, i0 + lane, nflA);
-      int K = 0;
-      bool removed = false;
-      float wprod = 0.f;
-      if (t.slot >= 0) {
-        K = t.r.x & 0xFF;
-        wprod = __uint_as_float(t.r.y);
-        const float wnew = __uint_as_float(t.r.z);
-        const float om = sqrtf(t.px * t.px + t.py * t.py + t.pz * t.pz) * kMeC2f;
-        cnt.add(C_CAP, (t.r.x & DF_CAPPED) ? 1u : 0u);
-        cnt.add(C_CLAMP, (t.r.x & DF_OVER) ? 1u : 0u);
-        cnt.add(C_EV_PINV, (unsigned)K);
-        if (t.r.x & DF_ABSORBED) {
-          x64.add((double)wnew, om, t.px, t.py, t.pz);
-          cnt.add((t.r.x & DF_ABS_C) ? C_ABS_C : C_ABS_B, 1);
-        } else if (A.absorb_mode == 1 && bath) {
-          // weight reduction: the lost weight's energy goes to the plasma
-          float wrem = t.w;
-          if (K > 0) wrem = (t.r.x & DF_OVER) ? 0.f : __fsub_rn(t.w, __fmul_rn((float)K, wprod));
-          x64.add((double)wrem - (double)wnew, om, t.px, t.py, t.pz);
-        }
-        removed = !(t.r.x & DF_KEEP);
-        if (!removed && wnew != t.w) A.a.w[abase + t.slot] = wnew;
-      }
-      // photon products of a->gamma after the photons present
-      int tot;
-      int off = run + warp_excl_scan(K, &tot);
-      for (int k = 0; k < K; ++k, ++off) {
-        const int dst = ng + off;
-        if (dst < A.g.cap) write_particle(A.g, gbase + dst, wprod, t.px, t.py, t.pz, t.x, t.y, t.z);
-        else cnt.add(C_DROP, 1);
-      }
-      run += tot;
-      NPg += K;
-      const unsigned m = __ballot_sync(kFull, removed);
-      if (removed) {
-        S.rmA[nrmA + __popc(m & lt)] = (uint16_t)t.slot;
-        atomicOr(&S.rbA[t.slot >> 5], 1u << (t.slot & 31));
-      }
-      nrmA += __popc(m);
-    }
-    NPg = warp_sum_i(NPg);
-    ng = min(ng + NPg, A.g.cap);
-    if (__any_sync(kFull, x64.any)) {
-      xa[0] = warp_sum_d(x64.dE);
-      xa[1] = warp_sum_d(x64.dPx);
-      xa[2] = warp_sum_d(x64.dPy);
-      xa[3] = warp_sum_d(x64.dPz);
-      xa_any = true;
-    }
-    x64 = Lane64();
-    na = na_start - nrmA;
-  }
-
-  // ------------------------------------------------------------ emit: photons
-  const int ng_tot = ng;
-  int nrmG = 0, NPa = 0;
-  float pw_prod = 0.f;
-  int pK = 0, p_off = 0;
-  if (emitG && nflG > 0) {
-    for (int i = lane; i < (ng_tot + 31) / 32; i += 32) S.rbG[i] = 0u;
-    __syncwarp();
-    // decisions of the first 32 (products are written after the axion tail
-    // fill); longer lists are taken whole below
-    if (nflG <= 32) {
-      bool removed = false;
-      int slot = -1;
-      if (lane < nflG) {
-        slot = S.flG[lane];
-        const uint4 r = T.gr[lane];
-        pK = r.x & 0xFF;
-        pw_prod = __uint_as_float(r.y);
-        cnt.add(C_CAP, (r.x & DF_CAPPED) ? 1u : 0u);
-        cnt.add(C_CLAMP, (r.x & DF_OVER) ? 1u : 0u);
-        cnt.add(C_EV_P, (unsigned)pK);
-        removed = !(r.x & DF_KEEP);
-        if (pK && !removed) A.g.w[gbase + slot] = __uint_as_float(r.z);
-      }
-      int tot;
-      p_off = warp_excl_scan(pK, &tot);
-      NPa = tot;
-      const unsigned m = __ballot_sync(kFull, removed);
-      if (removed) {
-        S.rmG[__popc(m & lt)] = (uint16_t)slot;
-        atomicOr(&S.rbG[slot >> 5], 1u << (slot & 31));
-      }
-      nrmG = __popc(m);
-    }
-  }
-  __syncwarp();
-
-  // ------------------------------------------------------------ round trip 3
-  // tail-fill movers of both species (axion movers are read before any
-  // product is written over them)
-  int runA = 0, runG = 0, dA = -1, dG = -1;
-  const bool fillA = (PH & PH_ABSORB) && nrmA > 0;
-  const bool fillG = emitG && nflG <= 32 && nrmG > 0;
-  if (fillA) runA = mover_stage(A.a, abase, S.rmA, S.rbA, na, na_start, T.a, &dA);
-  if (fillG) runG = mover_stage(A.g, gbase, S.rmG, S.rbG, ng_tot - nrmG, ng_tot, T.mg, &dG);
-  if (fillA || fillG) {
-    cp_async_wait_all();
-    __syncwarp();
-  }
-  if (fillA) {
-    mover_commit(A.a, abase, T.a, dA);
-    if (na_start - na > 32) compact_rest(A.a, abase, S.rmA, runA, S.rbA, na, na_start);
-  }
-
-  if (PH & PH_EMIT) {
-    const int abase_new = na;
-    // (c) gamma->a products after the surviving axions
-    if (emitG && nflG > 0) {
-      if (nflG <= 32) {
-        if (pK) {
-          const float px = T.g.px[lane], py = T.g.py[lane], pz = T.g.pz[lane];
-          const float xx = T.g.x[lane], yy = T.g.y[lane], zz = T.g.z[lane];
-          const float om = sqrtf(px * px + py * py + pz * pz) * kMeC2f;
-          int off = p_off;
-          for (int k = 0; k < pK; ++k, ++off) {
-            const int dst = abase_new + off;
-            if (dst < A.a.cap) {
-              write_particle(A.a, abase + dst, pw_prod, px, py, pz, xx, yy, zz);
-              if (A.tally_enable) tally_add(A, 0, pw_prod, om);
-            } else {
-              cnt.add(C_DROP, 1);
-            }
-          }
-        }
-      } else {
-        int run = 0;
-        for (int i0 = 0; i0 < nflG; i0 += 32) {
-          const PhItem t = i0 == 0 ? ph_staged(T, S.flG, lane, nflG) : ph_load(A, gbase, S.flG, i0 + lane, nflG);
-          int K = 0;
-          bool removed = false;
-          float wprod = 0.f, om = 0.f;
-          if (t.slot >= 0) {
-            K = t.r.x & 0xFF;
-            wprod = __uint_as_float(t.r.y);
-            cnt.add(C_CAP, (t.r.x & DF_CAPPED) ? 1u : 0u);
-            cnt.add(C_CLAMP, (t.r.x & DF_OVER) ? 1u : 0u);
-            cnt.add(C_EV_P, (unsigned)K);
-            removed = !(t.r.x & DF_KEEP);
-            if (K) {
-              om = sqrtf(t.px * t.px + t.py * t.py + t.pz * t.pz) * kMeC2f;
-              if (!removed) A.g.w[gbase + t.slot] = __uint_as_float(t.r.z);
-            }
-          }
-          int tot;
-          int off = run + warp_excl_scan(K, &tot);
-          for (int k = 0; k < K; ++k, ++off) {
-            const int dst = abase_new + off;
-            if (dst < A.a.cap) {
-              write_particle(A.a, abase + dst, wprod, t.px, t.py, t.pz, t.x, t.y, t.z);
-              if (A.tally_enable) tally_add(A, 0, wprod, om);
-            } else {
-              cnt.add(C_DROP, 1);
-            }
-          }
-          run += tot;
-          NPa += K;
-          const unsigned m = __ballot_sync(kFull, removed);
-          if (removed) {
-            S.rmG[nrmG + __popc(m & lt)] = (uint16_t)t.slot;
-            atomicOr(&S.rbG[t.slot >> 5], 1u << (t.slot & 31));
-          }
-          nrmG += __popc(m);
-        }
-        NPa = warp_sum_i(NPa);
-      }
-    }
-    // (d) electron events, in electron then event order; event k of
-    // electron i: cos theta, phi, energy and channel from one Philox block
-    int NE = 0;
-    if (emitE) {
-      if (wu > 0.f && lane == 0) {
-        float fac;
-        bool cc = false, cb = false;
-        if (eC) cap_lambda(wu * r_cc, A.lam_cap, &fac, &cc);
-        if (eB) cap_lambda(wu * r_cb, A.lam_cap, &fac, &cb);
-        cnt.add(C_CAP, (unsigned)ne * ((unsigned)cc + (unsigned)cb));
-      }
-      if (nflE > 0) {
-        const float* tabC = A.tables + TAB_COMPTON * kTableN;
-        const float* tabB = A.tables + TAB_BREMS * kTableN;
-        int run = 0;
-        for (int i0 = 0; i0 < nflE; i0 += 32) {
-          const ElItem t = el_load(A, ebase, S.flE, i0 + lane, nflE, wu);
-          int K = 0;
-          if (t.slot >= 0) {
-            K = t.f & 0xFF;
-            if (wu <= 0.f) cnt.add(C_CAP, ((t.f & DF_CAPPED) ? 1u : 0u) + ((t.f & DF_CAPPED_B) ? 1u : 0u));
-          }
-          int tot;
-          int off = run + warp_excl_scan(K, &tot);
-          if (K) {
-            float facC = 1.f, facB = 1.f;
-            bool cc = false, cb = false;
-            const float lc = eC ? cap_lambda(t.w * r_cc, A.lam_cap, &facC, &cc) : 0.f;
-            const float lb = eB ? cap_lambda(t.w * r_cb, A.lam_cap, &facB, &cb) : 0.f;
-            const float fracC = lc / (lc + lb);
-            const float wvC = cc ? A.w_a * facC : A.w_a;
-            const float wvB = cb ? A.w_a * facB : A.w_a;
-            for (int k = 0; k < K; ++k, ++off) {
-              const uint4 r = philox4x32_10(make_uint4(step, gcell, (uint32_t)t.slot, (S_EV_E << 24) | (uint32_t)k),
-                                            A.rk);
-              const bool isC = u23(r.w) < fracC;
-              const float3 dv = iso_dir(u23(r.x), u23(r.y));
-              const float E = (A.rate_model ? sr_sample_x(A.sr + (size_t)cell * kSrLen, isC ? 1 : 2, u23(r.z))
-                                            : icdf_lookup(isC ? tabC : tabB, u23(r.z))) *
-                              r_T;
-              const float wv = isC ? wvC : wvB;
-              const float pm = E * kInvMeC2f;
-              const float px = pm * dv.x, py = pm * dv.y, pz = pm * dv.z;
-              const int dst = abase_new + NPa + off;
-              if (dst < A.a.cap) {
-                write_particle(A.a, abase + dst, wv, px, py, pz, t.x, t.y, t.z);
-                if (A.tally_enable) tally_add(A, isC ? 1 : 2, wv, E);
-              } else {
-                cnt.add(C_DROP, 1);
-              }
-              x64.add(-(double)wv, E, px, py, pz);
-              cnt.add(isC ? C_EV_C : C_EV_B, 1);
-            }
-          }
-          run += tot;
-          NE += K;
-        }
-        NE = warp_sum_i(NE);
-      }
-    }
-    na = min(na + NPa + NE, A.a.cap);
-    __syncwarp();
-    // (e) tail fill of the photons (a->gamma products included)
-    if (fillG) {
-      mover_commit(A.g, gbase, T.mg, dG);
-      if (nrmG > 32) compact_rest(A.g, gbase, S.rmG, runG, S.rbG, ng_tot - nrmG, ng_tot);
-    } else if (emitG && nflG > 32 && nrmG > 0) {
-      int d = -1;
-      const int run0 = mover_stage(A.g, gbase, S.rmG, S.rbG, ng_tot - nrmG, ng_tot, T.mg, &d);
-      cp_async_wait_all();
-      __syncwarp();
-      mover_commit(A.g, gbase, T.mg, d);
-      if (nrmG > 32) compact_rest(A.g, gbase, S.rmG, run0, S.rbG, ng_tot - nrmG, ng_tot);
-    }
-    ng = ng_tot - nrmG;
-  }
-  if (lane == 0) {
-    A.a.count[cell] = na;
-    A.g.count[cell] = ng;
-  }
-
-  // ------------------------------------------------------------ exchange
-  // the absorb and emit contributions are reduced separately and added to the
-  // cell's buffer in that order, whichever way the step was called
-  bool xe_any = false;
-  double xe[4] = {0.0, 0.0, 0.0, 0.0};
-  if (__any_sync(kFull, x64.any)) {
-    xe[0] = warp_sum_d(x64.dE);
-    xe[1] = warp_sum_d(x64.dPx);
-    xe[2] = warp_sum_d(x64.dPy);
-    xe[3] = warp_sum_d(x64.dPz);
-    xe_any = true;
-  }
-  if (lane < 4 && (xa_any || xe_any)) {
-    const double a = lane == 0 ? xa[0] : (lane == 1 ? xa[1] : (lane == 2 ? xa[2] : xa[3]));
-    const double e = lane == 0 ? xe[0] : (lane == 1 ? xe[1] : (lane == 2 ? xe[2] : xe[3]));
-    double v = xb_old;
-    if (xa_any) v += a;
-    if (xe_any) v += e;
-    xb[lane] = v;
   }
 }
 
+// The events of a flagged electron (thermal-bath emission), from position
+// dst0 on: event k takes cos theta, phi, energy and channel from one Philox
+// block. Returns K.
+__device__ __forceinline__ int electron_events(const StepArgs& A, uint32_t step, int cell, const ElItem& t,
+                                               long abase, int dst0, float r_cc, float r_cb, float r_T,
+                                               float wu, const Cnt& cnt, Lane64& x64) {
+  const int K = t.f & 0xFF;
+  if (wu <= 0.f) cnt.add(C_CAP, ((t.f & DF_CAPPED) ? 1u : 0u) + ((t.f & DF_CAPPED_B) ? 1u : 0u));
+  if (!K) return 0;
+  const bool eC = A.mask & AXPIC_CH_COMPTON, eB = A.mask & AXPIC_CH_BREMS;
+  float facC = 1.f, facB = 1.f;
+  bool cc = false, cb = false;
+  const float lc = eC ? cap_lambda(t.w * r_cc, A.lam_cap, &facC, &cc) : 0.f;
+  const float lb = eB ? cap_lambda(t.w * r_cb, A.lam_cap, &facB, &cb) : 0.f;
+  const float fracC = lc / (lc + lb);
+  const float wvC = cc ? A.w_a * facC : A.w_a;
+  const float wvB = cb ? A.w_a * facB : A.w_a;
+  const uint32_t gcell = A.cell_base + (uint32_t)cell;
+  for (int k = 0; k < K; ++k) {
+    const uint4 r = philox4x32_10(make_uint4(step, gcell, (uint32_t)t.slot, (S_EV_E << 24) | (uint32_t)k), A.rk);
+    const bool isC = u23(r.w) < fracC;
+    const float3 dv = iso_dir(u23(r.x), u23(r.y));
+    const float E = (A.rate_model ? sr_sample_x(A.sr + (size_t)cell * kSrLen, isC ? 1 : 2, u23(r.z))
+                                  : icdf_lookup(A.tables + (isC ? TAB_COMPTON : TAB_BREMS) * kTableN, u23(r.z))) *
+                    r_T;
+    const float wv = isC ? wvC : wvB;
+    const float pm = E * kInvMeC2f;
+    const float px = pm * dv.x, py = pm * dv.y, pz = pm * dv.z;
+    const int dst = dst0 + k;
+    if (dst < A.a.cap) {
+      write_particle(A.a, abase + dst, wv, px, py, pz, t.x, t.y, t.z);
+      if (A.tally_enable) tally_add(A, isC ? 1 : 2, wv, E);
+    } else {
+      cnt.add(C_DROP, 1);
+    }
+    x64.add(-(double)wv, E, px, py, pz);
+    cnt.add(isC ? C_EV_C : C_EV_B, 1);
+  }
+  return K;
+}
+
+// ---------------------------------------------------------------- warp path
+struct PhaseOut {
+  int na, ng;
+  double x[4];
+  bool any;
+};
+
+__device__ __forceinline__ void reduce_out(const Lane64& x64, PhaseOut* out) {
+  out->any = __any_sync(kFull, x64.any);
+  out->x[0] = out->x[1] = out->x[2] = out->x[3] = 0.0;
+  if (out->any) {
+    out->x[0] = warp_sum_d(x64.dE);
+    out->x[1] = warp_sum_d(x64.dPx);
+    out->x[2] = warp_sum_d(x64.dPy);
+    out->x[3] = warp_sum_d(x64.dPz);
+  }
+}
+
+// Absorb phase of one cell by the warp: a->gamma products, absorption and
+// weight reduction, then the axion tail fill.
+__device__ __noinline__ void absorb_warp(const StepArgs& A, int cell, EvScratch& S, const uint32_t* row,
+                                         uint32_t* clr, const Cnt& cnt, int na_start, int ng_start,
+                                         PhaseOut* out) {
+  const int lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  const bool bath = A.mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS);
+  const long abase = (long)cell * A.a.cap;
+  const long gbase = (long)cell * A.g.cap;
+  const int nfl = gather_row(row, clr, na_start, S.flA);
+  for (int i = lane; i < (na_start + 31) / 32; i += 32) S.rbA[i] = 0u;
+  __syncwarp();
+  Lane64 x64;
+  int run = 0, nrm = 0;
+  for (int i0 = 0; i0 < nfl; i0 += 32) {
+    const AxItem t = ax_load(A, abase, i0 + lane < nfl ? (int)S.flA[i0 + lane] : -1);
+    int K = 0;
+    bool removed = false;
+    if (t.slot >= 0) K = axion_outcome(A, t, abase, bath, cnt, x64, &removed);
+    int tot;
+    int off = run + warp_excl_scan(K, &tot);
+    const float wprod = __uint_as_float(t.r.y);
+    for (int k = 0; k < K; ++k, ++off) {
+      const int dst = ng_start + off;
+      if (dst < A.g.cap) write_particle(A.g, gbase + dst, wprod, t.px, t.py, t.pz, t.x, t.y, t.z);
+      else cnt.add(C_DROP, 1);
+    }
+    run += tot;
+    const unsigned m = __ballot_sync(kFull, removed);
+    if (removed) {
+      S.rmA[nrm + __popc(m & lt)] = (uint16_t)t.slot;
+      atomicOr(&S.rbA[t.slot >> 5], 1u << (t.slot & 31));
+    }
+    nrm += __popc(m);
+  }
+  reduce_out(x64, out);
+  __syncwarp();
+  if (nrm > 0) compact_tail(A.a, abase, S.rmA, S.rbA, na_start - nrm, na_start);
+  out->na = na_start - nrm;
+  out->ng = min(ng_start + run, A.g.cap);
+}
+
+// Emit phase of one cell by the warp: gamma->a, the thermal-bath events, then
+// the photon tail fill (a->gamma products included).
+__device__ __noinline__ void emit_warp(const StepArgs& A, uint32_t step, int cell, EvScratch& S,
+                                       const uint32_t* rowG, uint32_t* clrG, const uint32_t* rowE, uint32_t* clrE,
+                                       const Cnt& cnt, int na, int ng_tot, int ng0, int ne, float wu, float r_cc,
+                                       float r_cb, float r_T, PhaseOut* out) {
+  const int lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  const long abase = (long)cell * A.a.cap;
+  const long gbase = (long)cell * A.g.cap;
+  const long ebase = (long)cell * A.e.cap;
+  const int nflG = rowG ? gather_row(rowG, clrG, ng0, S.flG) : 0;
+  const int nflE = rowE ? gather_row(rowE, clrE, ne, S.flE) : 0;
+  for (int i = lane; i < (ng_tot + 31) / 32; i += 32) S.rbG[i] = 0u;
+  __syncwarp();
+  int run = 0, nrm = 0;
+  for (int i0 = 0; i0 < nflG; i0 += 32) {
+    const PhItem t = ph_load(A, gbase, i0 + lane < nflG ? (int)S.flG[i0 + lane] : -1);
+    int K = 0;
+    bool removed = false;
+    if (t.slot >= 0) K = photon_outcome(A, t, gbase, cnt, &removed);
+    int tot;
+    const int off = run + warp_excl_scan(K, &tot);
+    if (K) gamma_products(A, t, abase, na + off, K, cnt);
+    run += tot;
+    const unsigned m = __ballot_sync(kFull, removed);
+    if (removed) {
+      S.rmG[nrm + __popc(m & lt)] = (uint16_t)t.slot;
+      atomicOr(&S.rbG[t.slot >> 5], 1u << (t.slot & 31));
+    }
+    nrm += __popc(m);
+  }
+  Lane64 x64;
+  for (int i0 = 0; i0 < nflE; i0 += 32) {
+    const ElItem t = el_load(A, ebase, i0 + lane < nflE ? (int)S.flE[i0 + lane] : -1, wu);
+    const int K = t.slot >= 0 ? (int)(t.f & 0xFF) : 0;
+    int tot;
+    const int off = run + warp_excl_scan(K, &tot);
+    if (t.slot >= 0) electron_events(A, step, cell, t, abase, na + off, r_cc, r_cb, r_T, wu, cnt, x64);
+    run += tot;
+  }
+  reduce_out(x64, out);
+  __syncwarp();
+  if (nrm > 0) compact_tail(A.g, gbase, S.rmG, S.rbG, ng_tot - nrm, ng_tot);
+  out->na = min(na + run, A.a.cap);
+  out->ng = ng_tot - nrm;
+}
+
+// ---------------------------------------------------------------- lane path
+// Counts the flagged slots of a staged mask row in [0, n) and lists the
+// first kLight of them (ascending, stride 32); *nz gets the nonzero words.
+__device__ __forceinline__ int scan_row(const uint32_t* row, int n, uint16_t* list, uint32_t* nz) {
+  const int nw = (n + 31) >> 5;
+  int c = 0;
+  uint32_t m = 0u;
+  for (int w = 0; w < nw; ++w) {
+    uint32_t v = row[w];
+    if (v) {
+      m |= 1u << w;
+      if (w == nw - 1 && (n & 31)) v &= (1u << (n & 31)) - 1u;
+      while (v) {
+        if (c < kLight) list[32 * c] = (uint16_t)(32 * w + __ffs(v) - 1);
+        ++c;
+        v &= v - 1u;
+      }
+    }
+  }
+  *nz = m;
+  return c;
+}
+
+// Clears the nonzero words of a cell's global mask row.
+__device__ __forceinline__ void clear_row(uint32_t* bits, int W, int cell, uint32_t nz) {
+  uint32_t* row = bits + (size_t)cell * W;
+  while (nz) {
+    row[__ffs(nz) - 1] = 0u;
+    nz &= nz - 1u;
+  }
+}
+
+// Tail fill by one lane: the removed slots rm[0, nrm) (ascending) below
+// n_surv are refilled, in order, by the kept slots of [n_surv, n). The first
+// kLoad movers can be loaded ahead (fill_load) and written later
+// (fill_store); fill_rest moves the others.
+struct FillIt {
+  int h, j, i, m;  // holes, next removed entry at or past the scan, scan position, movers done
+};
+struct Mover {
+  float w, px, py, pz, x, y, z;
+  int dst;
+};
+
+__device__ __forceinline__ FillIt fill_begin(const uint16_t* rm, int nrm, int n_surv) {
+  FillIt it;
+  it.h = 0;
+  while (it.h < nrm && rm[32 * it.h] < n_surv) ++it.h;
+  it.j = it.h;
+  it.i = n_surv;
+  it.m = 0;
+  return it;
+}
+
+// Source slot of the next mover (the caller checks it.m < it.h).
+__device__ __forceinline__ int fill_next(const uint16_t* rm, int nrm, FillIt& it) {
+  while (it.j < nrm && rm[32 * it.j] == it.i) {
+    ++it.j;
+    ++it.i;
+  }
+  return it.i++;
+}
+
+__device__ __forceinline__ Mover mover_load(const SpeciesPtrs& sp, long base, int src, int dst) {
+  Mover v;
+  v.dst = dst;
+  if (dst >= 0) {
+    const long q = base + src;
+    v.w = sp.w[q];
+    v.px = sp.px[q];
+    v.py = sp.py[q];
+    v.pz = sp.pz[q];
+    v.x = sp.x[q];
+    v.y = sp.y[q];
+    v.z = sp.z[q];
+  }
+  return v;
+}
+
+__device__ __forceinline__ void mover_store(const SpeciesPtrs& sp, long base, const Mover& v) {
+  if (v.dst >= 0) write_particle(sp, base + v.dst, v.w, v.px, v.py, v.pz, v.x, v.y, v.z);
+}
+
+// Loads the next kLoad movers.
+__device__ __forceinline__ void fill_load(const SpeciesPtrs& sp, long base, const uint16_t* rm, int nrm, FillIt& it,
+                                          Mover* v) {
+#pragma unroll
+  for (int t = 0; t < kLoad; ++t) {
+    int src = 0, dst = -1;
+    if (it.m < it.h) {
+      src = fill_next(rm, nrm, it);
+      dst = rm[32 * it.m++];
+    }
+    v[t] = mover_load(sp, base, src, dst);
+  }
+}
+
+__device__ __forceinline__ void fill_rest(const SpeciesPtrs& sp, long base, const uint16_t* rm, int nrm, FillIt& it) {
+  while (it.m < it.h) {
+    Mover v[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      int src = 0, dst = -1;
+      if (it.m < it.h) {
+        src = fill_next(rm, nrm, it);
+        dst = rm[32 * it.m++];
+      }
+      v[t] = mover_load(sp, base, src, dst);
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) mover_store(sp, base, v[t]);
+  }
+}
+
+// One cell by one lane: its absorb phase (doA), its emit phase (doE) or
+// both. Round trips: the first kLoad flagged axions and photons together;
+// the first kLoad tail movers of both species together; then the stores.
+// Longer lists take further round trips. Axion movers are read before any
+// gamma->a product is written over their slots.
+struct LaneCell {
+  int na, ng;       // in: counts at the start of the phase(s); out: final counts
+  int ng0, ne;      // photons eligible for gamma->a, electrons
+  int nflA, nflG, nflE;
+  float wu, r_cc, r_cb, r_T;
+};
+
+__device__ __forceinline__ void cell_lane(const StepArgs& A, uint32_t step, int cell, bool doA, bool doE,
+                                          uint16_t* lA, uint16_t* lG, const uint16_t* lE, LaneCell& L,
+                                          const Cnt& cnt, Lane64& xa, Lane64& xe) {
+  const bool bath = A.mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS);
+  const long abase = (long)cell * A.a.cap;
+  const long gbase = (long)cell * A.g.cap;
+  const long ebase = (long)cell * A.e.cap;
+  const int nA = doA ? L.nflA : 0;
+  const int nG = doE ? L.nflG : 0;
+  const int nE = doE ? L.nflE : 0;
+  AxItem ta[kLoad];
+  PhItem tg[kLoad];
+#pragma unroll
+  for (int j = 0; j < kLoad; ++j) ta[j] = ax_load(A, abase, j < nA ? (int)lA[32 * j] : -1);
+#pragma unroll
+  for (int j = 0; j < kLoad; ++j) tg[j] = ph_load(A, gbase, j < nG ? (int)lG[32 * j] : -1);
+
+  // absorb: a->gamma products after the photons present
+  int na = L.na, ng = L.ng, nrmA = 0;
+  if (doA) {
+    int run = 0;
+#pragma unroll
+    for (int j = 0; j < kLoad; ++j) {
+      if (ta[j].slot < 0) break;
+      bool removed;
+      const int K = axion_outcome(A, ta[j], abase, bath, cnt, xa, &removed);
+      const float wprod = __uint_as_float(ta[j].r.y);
+      for (int k = 0; k < K; ++k) {
+        const int dst = L.ng + run + k;
+        if (dst < A.g.cap) write_particle(A.g, gbase + dst, wprod, ta[j].px, ta[j].py, ta[j].pz, ta[j].x, ta[j].y, ta[j].z);
+        else cnt.add(C_DROP, 1);
+      }
+      run += K;
+      if (removed) lA[32 * nrmA++] = (uint16_t)ta[j].slot;
+    }
+    for (int i = kLoad; i < nA; ++i) {
+      const AxItem t = ax_load(A, abase, lA[32 * i]);
+      bool removed;
+      const int K = axion_outcome(A, t, abase, bath, cnt, xa, &removed);
+      const float wprod = __uint_as_float(t.r.y);
+      for (int k = 0; k < K; ++k) {
+        const int dst = L.ng + run + k;
+        if (dst < A.g.cap) write_particle(A.g, gbase + dst, wprod, t.px, t.py, t.pz, t.x, t.y, t.z);
+        else cnt.add(C_DROP, 1);
+      }
+      run += K;
+      if (removed) lA[32 * nrmA++] = (uint16_t)t.slot;
+    }
+    na = L.na - nrmA;
+    ng = min(L.ng + run, A.g.cap);
+  }
+
+  // emit: gamma->a decisions of the loaded photons (products after the fill)
+  int nrmG = 0, Kg[kLoad];
+#pragma unroll
+  for (int j = 0; j < kLoad; ++j) {
+    Kg[j] = 0;
+    if (tg[j].slot >= 0) {
+      bool removed;
+      Kg[j] = photon_outcome(A, tg[j], gbase, cnt, &removed);
+      if (removed) lG[32 * nrmG++] = (uint16_t)tg[j].slot;
+    }
+  }
+
+  // tail movers of both species, loaded together
+  FillIt fa = fill_begin(lA, nrmA, na);
+  Mover ma[kLoad], mg[kLoad];
+  fill_load(A.a, abase, lA, nrmA, fa, ma);
+  const bool gFill = nG <= kLoad;  // every photon removal is known
+  FillIt fg = fill_begin(lG, nrmG, ng - nrmG);
+  if (gFill) fill_load(A.g, gbase, lG, nrmG, fg, mg);
+#pragma unroll
+  for (int t = 0; t < kLoad; ++t) mover_store(A.a, abase, ma[t]);
+  fill_rest(A.a, abase, lA, nrmA, fa);
+
+  if (doE) {
+    int NP = 0;
+#pragma unroll
+    for (int j = 0; j < kLoad; ++j) {
+      if (Kg[j]) gamma_products(A, tg[j], abase, na + NP, Kg[j], cnt);
+      NP += Kg[j];
+    }
+    for (int i = kLoad; i < nG; ++i) {
+      const PhItem t = ph_load(A, gbase, lG[32 * i]);
+      bool removed;
+      const int K = photon_outcome(A, t, gbase, cnt, &removed);
+      if (K) gamma_products(A, t, abase, na + NP, K, cnt);
+      NP += K;
+      if (removed) lG[32 * nrmG++] = (uint16_t)t.slot;
+    }
+    for (int i = 0; i < nE; ++i) {
+      const ElItem t = el_load(A, ebase, lE[32 * i], L.wu);
+      NP += electron_events(A, step, cell, t, abase, na + NP, L.r_cc, L.r_cb, L.r_T, L.wu, cnt, xe);
+    }
+    na = min(na + NP, A.a.cap);
+    // photon tail fill (a->gamma products included)
+    if (gFill) {
+#pragma unroll
+      for (int t = 0; t < kLoad; ++t) mover_store(A.g, gbase, mg[t]);
+    } else {
+      fg = fill_begin(lG, nrmG, ng - nrmG);
+    }
+    fill_rest(A.g, gbase, lG, nrmG, fg);
+    ng -= nrmG;
+  }
+  L.na = na;
+  L.ng = ng;
+}
+
 #ifndef AXPIC_EVENT_MIN_CTAS
-#define AXPIC_EVENT_MIN_CTAS 8
+#define AXPIC_EVENT_MIN_CTAS 4
 #endif
 
+// Round trip 1: counts, per-cell constants, the exchange buffer and the mask
+// rows (staged by cp.async; cleared for the next step as soon as they are
+// read). Each phase runs first in the lanes whose cell is light for it, then
+// warp-wide for the heavy cells one by one; a cell's absorb phase ends before
+// its emit phase starts. The absorb and emit exchanges are added to the
+// cell's buffer in that order, whichever way the step was called.
 template <int PH>
 __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1390,14 +1616,184 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
   const int wid = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int cell = blockIdx.x * nw + wid;
+  const int cell = (blockIdx.x * nw + wid) * 32 + lane;
+  const bool valid = cell < A.ncells;
   if (lane < kNumCounters) warp_cnt[wid][lane] = 0ull;
   __syncwarp();
   const Cnt cnt{warp_cnt[wid]};
-  if (cell < A.ncells) {
-    const size_t bytes = ev_scratch_bytes(A.a.cap, A.g.cap, A.e.cap);
-    EvScratch S = ev_carve(smem + wid * bytes, A.a.cap, A.g.cap, A.e.cap);
-    event_cell<PH>(A, step_of(A), cell, S, cnt);
+  EvScratch S = ev_carve(smem + wid * ev_scratch_bytes(A.a.cap, A.g.cap, A.e.cap), A.a.cap, A.g.cap, A.e.cap);
+  uint16_t* lA = S.lt + lane;
+  uint16_t* lG = lA + 32 * kLight;
+  uint16_t* lE = lG + 32 * kLight;
+  const uint32_t step = step_of(A);
+  const int mask = A.mask;
+  const bool emitG = (PH & PH_EMIT) && (mask & AXPIC_CH_PRIMAKOFF);
+  const bool emitE = (PH & PH_EMIT) && (mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS));
+  const bool staged = S.rowA != nullptr;
+  uint32_t* rA = staged ? S.rowA + lane * S.sA : nullptr;
+  uint32_t* rG = staged ? S.rowG + lane * S.sG : nullptr;
+  uint32_t* rE = staged ? S.rowE + lane * S.sE : nullptr;
+
+  // ------------------------------------------------------------ round trip 1
+  LaneCell L;
+  L.na = L.ng = L.ng0 = L.ne = 0;
+  L.nflA = L.nflG = L.nflE = 0;
+  L.wu = L.r_cc = L.r_cb = L.r_T = 0.f;
+  int pstart = 0;
+  double xb[4] = {0.0, 0.0, 0.0, 0.0};
+  if (valid) {
+    if (staged) {
+      if (PH & PH_ABSORB)
+        for (int w = 0; w < A.Wa; ++w) cp_async4(rA + w, A.bitsA + (size_t)cell * A.Wa + w);
+      if (emitG)
+        for (int w = 0; w < A.Wg; ++w) cp_async4(rG + w, A.bitsG + (size_t)cell * A.Wg + w);
+      if (emitE)
+        for (int w = 0; w < A.We; ++w) cp_async4(rE + w, A.bitsE + (size_t)cell * A.We + w);
+    }
+    L.ne = min(max(A.e.count[cell], 0), A.e.cap);
+    L.ng = min(max(A.g.count[cell], 0), A.g.cap);
+    L.na = min(max(A.a.count[cell], 0), A.a.cap);
+    if (!(PH & PH_ABSORB) && A.use_snapshot) pstart = A.photon_start[cell];
+    if (emitE) {
+      const float* rec = A.rec + (size_t)cell * kRecLen;
+      L.wu = A.mom[(size_t)cell * kMomLen + M_WU];
+      L.r_cc = rec[R_CC];
+      L.r_cb = rec[R_CB];
+      L.r_T = rec[R_T];
+    }
+    const double2* x2 = reinterpret_cast<const double2*>(A.xbuf + (size_t)cell * 4);
+    const double2 a = x2[0], b = x2[1];
+    xb[0] = a.x;
+    xb[1] = a.y;
+    xb[2] = b.x;
+    xb[3] = b.y;
+  }
+  const int ne = L.ne, ng_start = L.ng, na_start = L.na;
+  L.ng0 = (PH & PH_ABSORB) ? ng_start : (A.use_snapshot ? min(pstart, ng_start) : ng_start);
+  // particles present at the start of the step: counted by the absorb phase,
+  // or by the emit phase when no absorb ran this step
+  if ((PH & PH_ABSORB) || ((PH & PH_EMIT) && !A.use_snapshot)) {
+    const int sne = warp_sum_i(ne), sng = warp_sum_i(ng_start), sna = warp_sum_i(na_start);
+    const unsigned nv = __popc(__ballot_sync(kFull, valid));
+    if (lane == 0) {
+      cnt.add(C_NE, (unsigned)sne);
+      cnt.add(C_NG, (unsigned)sng);
+      cnt.add(C_NA, (unsigned)sna);
+      cnt.add(C_CELLS, nv);
+    }
+  }
+  if (staged) cp_async_wait_all();
+  __syncwarp();
+
+  bool hA = false, hE = false;
+  if (valid) {
+    if (staged) {
+      uint32_t nz;
+      if (PH & PH_ABSORB) {
+        L.nflA = scan_row(rA, na_start, lA, &nz);
+        clear_row(A.bitsA, A.Wa, cell, nz);
+      }
+      if (emitG) {
+        L.nflG = scan_row(rG, L.ng0, lG, &nz);
+        clear_row(A.bitsG, A.Wg, cell, nz);
+      }
+      if (emitE) {
+        L.nflE = scan_row(rE, ne, lE, &nz);
+        clear_row(A.bitsE, A.We, cell, nz);
+      }
+      hA = L.nflA > kLight;
+      hE = L.nflG > kLight || L.nflE > kLightE;
+    } else {
+      hA = (PH & PH_ABSORB) != 0;
+      hE = (PH & PH_EMIT) != 0;
+    }
+    if (PH & PH_ABSORB) A.photon_start[cell] = ng_start;
+    if (emitE && L.wu > 0.f) {
+      float fac;
+      bool cc = false, cb = false;
+      if (mask & AXPIC_CH_COMPTON) cap_lambda(L.wu * L.r_cc, A.lam_cap, &fac, &cc);
+      if (mask & AXPIC_CH_BREMS) cap_lambda(L.wu * L.r_cb, A.lam_cap, &fac, &cb);
+      cnt.add(C_CAP, (unsigned)ne * ((unsigned)cc + (unsigned)cb));
+    }
+  }
+
+  Lane64 xa, xe;
+  const bool doA = (PH & PH_ABSORB) && valid && !hA;
+  const bool doE = (PH & PH_EMIT) && valid && !hE;
+  // light in every phase of the call: the lane takes the whole cell now
+  if (doA && ((PH & PH_EMIT) ? doE : true) && (L.nflA | L.nflG | L.nflE))
+    cell_lane(A, step, cell, true, (PH & PH_EMIT) != 0, lA, lG, lE, L, cnt, xa, xe);
+  else if (doA && L.nflA)
+    cell_lane(A, step, cell, true, false, lA, lG, lE, L, cnt, xa, xe);
+  __syncwarp();
+  if (PH & PH_ABSORB) {
+    for (unsigned hm = __ballot_sync(kFull, valid && hA); hm; hm &= hm - 1u) {
+      const int j = __ffs(hm) - 1;
+      const int c = __shfl_sync(kFull, cell, j);
+      PhaseOut o;
+      absorb_warp(A, c, S, staged ? S.rowA + j * S.sA : A.bitsA + (size_t)c * A.Wa,
+                  staged ? nullptr : A.bitsA + (size_t)c * A.Wa, cnt, __shfl_sync(kFull, na_start, j),
+                  __shfl_sync(kFull, ng_start, j), &o);
+      if (lane == j) {
+        L.na = o.na;
+        L.ng = o.ng;
+        xa.dE = o.x[0];
+        xa.dPx = o.x[1];
+        xa.dPy = o.x[2];
+        xa.dPz = o.x[3];
+        xa.any = o.any;
+      }
+    }
+  }
+  if (PH & PH_EMIT) {
+    // the emit phase of cells heavy for absorb only
+    if (doE && (PH & PH_ABSORB) && hA && (L.nflG | L.nflE))
+      cell_lane(A, step, cell, false, true, lA, lG, lE, L, cnt, xa, xe);
+    if (doE && !(PH & PH_ABSORB) && (L.nflG | L.nflE))
+      cell_lane(A, step, cell, false, true, lA, lG, lE, L, cnt, xa, xe);
+    __syncwarp();
+    for (unsigned hm = __ballot_sync(kFull, valid && hE); hm; hm &= hm - 1u) {
+      const int j = __ffs(hm) - 1;
+      const int c = __shfl_sync(kFull, cell, j);
+      PhaseOut o;
+      const uint32_t* gG = emitG ? (staged ? S.rowG + j * S.sG : A.bitsG + (size_t)c * A.Wg) : nullptr;
+      const uint32_t* gE = emitE ? (staged ? S.rowE + j * S.sE : A.bitsE + (size_t)c * A.We) : nullptr;
+      emit_warp(A, step, c, S, gG, (emitG && !staged) ? A.bitsG + (size_t)c * A.Wg : nullptr, gE,
+                (emitE && !staged) ? A.bitsE + (size_t)c * A.We : nullptr, cnt, __shfl_sync(kFull, L.na, j),
+                __shfl_sync(kFull, L.ng, j), __shfl_sync(kFull, L.ng0, j), __shfl_sync(kFull, ne, j),
+                __shfl_sync(kFull, L.wu, j), __shfl_sync(kFull, L.r_cc, j), __shfl_sync(kFull, L.r_cb, j),
+                __shfl_sync(kFull, L.r_T, j), &o);
+      if (lane == j) {
+        L.na = o.na;
+        L.ng = o.ng;
+        xe.dE = o.x[0];
+        xe.dPx = o.x[1];
+        xe.dPy = o.x[2];
+        xe.dPz = o.x[3];
+        xe.any = o.any;
+      }
+    }
+  }
+  if (valid) {
+    A.a.count[cell] = L.na;
+    A.g.count[cell] = L.ng;
+    if (xa.any || xe.any) {
+      if (xa.any) {
+        xb[0] += xa.dE;
+        xb[1] += xa.dPx;
+        xb[2] += xa.dPy;
+        xb[3] += xa.dPz;
+      }
+      if (xe.any) {
+        xb[0] += xe.dE;
+        xb[1] += xe.dPx;
+        xb[2] += xe.dPy;
+        xb[3] += xe.dPz;
+      }
+      double2* xo = reinterpret_cast<double2*>(A.xbuf + (size_t)cell * 4);
+      xo[0] = make_double2(xb[0], xb[1]);
+      xo[1] = make_double2(xb[2], xb[3]);
+    }
   }
   __syncwarp();
   if (lane < kNumCounters) {
@@ -1407,195 +1803,13 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
   }
 }
 
-// ---------------------------------------------------------------- feedback kernel
-// One lane per cell: the exchange of this step plus the carried part; when it
-// is representable in binary32 momenta the whole warp remaps that cell's
-// electrons (Eqs. delta_def to b_def, affine_map), measuring what was applied;
-// then the temperature update (Eqs. Te_est, Te_relax) and the record's
-// temperature half.
-struct RemapJob {
-  int cell, ne;
-  float s1, bx, by, bz;
-};
-
-// Thread per cell: every load it needs is issued first (exchange, carried
-// exchange, moments, count, T and the record); cells whose exchange needs an
-// affine remap go to a CTA list and the CTA's warps remap them side by side,
-// a warp per cell; then each thread finishes its cell (carry, diagnostics,
-// temperature update and the record's temperature half).
-constexpr int kFeedbackThreads = 128;
-
-__global__ void __launch_bounds__(kFeedbackThreads) feedback_kernel(StepArgs A) {
-  // a replayed graph takes its step index from the device counter: the last
-  // kernel of the step advances it (no kernel of this launch reads it)
-  if (A.step_dev && blockIdx.x == 0 && threadIdx.x == 0) *A.step_dev += 1u;
-  __shared__ RemapJob jobs[kFeedbackThreads];
-  __shared__ RemapOut outs[kFeedbackThreads];
-  __shared__ int njobs;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = cell < A.ncells;
-  if (threadIdx.x == 0) njobs = 0;
-  double dE = 0.0, dPx = 0.0, dPy = 0.0, dPz = 0.0, rE = 0.0, rPx = 0.0, rPy = 0.0, rPz = 0.0, T = 0.0;
-  float W = 0.f, Px = 0.f, Py = 0.f, Pz = 0.f, U2 = 0.f, var = 0.f;
-  float4 rc0 = make_float4(0.f, 0.f, 0.f, 0.f), rc1 = rc0, rc2 = rc0, rc3 = rc0;
-  bool has_x = false, has_res = false, need = false;
-  int ne = 0;
-  double qE = 0.0, qPx = 0.0, qPy = 0.0, qPz = 0.0, s1d = 0.0, bx = 0.0, by = 0.0, bz = 0.0, vnd = 0.0;
-  if (valid) {
-    double* xb = A.xbuf + (size_t)cell * 4;
-    dE = xb[0];
-    dPx = xb[1];
-    dPy = xb[2];
-    dPz = xb[3];
-    const double* rs = A.res + (size_t)cell * 4;
-    rE = rs[0];
-    rPx = rs[1];
-    rPy = rs[2];
-    rPz = rs[3];
-    const float* mom = A.mom + (size_t)cell * kMomLen;
-    W = mom[M_W];
-    Px = mom[M_PX];
-    Py = mom[M_PY];
-    Pz = mom[M_PZ];
-    U2 = mom[M_U2];
-    var = mom[M_VAR];
-    ne = min(max(A.e.count[cell], 0), A.e.cap);
-    if (A.T_mode == 2) {
-      T = A.T[cell];
-      const float4* r4 = reinterpret_cast<const float4*>(A.rec + (size_t)cell * kRecLen);
-      rc0 = r4[0];
-      rc1 = r4[1];
-      rc2 = r4[2];
-      rc3 = r4[3];
-    }
-    has_x = nz64(dE) || nz64(dPx) || nz64(dPy) || nz64(dPz);
-    if (has_x) {
-      xb[0] = 0.0;
-      xb[1] = 0.0;
-      xb[2] = 0.0;
-      xb[3] = 0.0;
-    }
-    has_res = nz64(rE) || nz64(rPx) || nz64(rPy) || nz64(rPz);
-    if (has_x || has_res) {
-      qE = dE + rE;
-      qPx = dPx + rPx;
-      qPy = dPy + rPy;
-      qPz = dPz + rPz;
-      // Exchanges below 2^-22 of the cell's kinetic energy (or momentum
-      // spread) cannot be represented by binary32 momenta; they stay pending.
-      const float ekin = 0.5f * U2 * kMeC2f;
-      const float prms = sqrtf(fmaxf(U2 * W, 0.f));
-      need = W > 0.f && (fabsf((float)qE) >= 2.384185791015625e-07f * ekin ||
-                         sqrtf((float)(qPx * qPx + qPy * qPy + qPz * qPz)) >= 2.384185791015625e-07f * prms);
-      if (need) {
-        // Eqs. delta_def, dE_bulk, dE_th, var_new, s_def, b_def (mu = 1)
-        const double Wd = W;
-        const double dx = qPx / Wd, dy = qPy / Wd, dz = qPz / Wd;
-        const double dEb = (2.0 * (dx * Px + dy * Py + dz * Pz) + Wd * (dx * dx + dy * dy + dz * dz)) * 0.5;
-        const double dEth = qE / kMeC2 - dEb;
-        vnd = var;
-        if (var > 0.f) {
-          vnd = fmax(0.0, (double)var + 2.0 * dEth);
-          const double S = sqrt(vnd / (double)var);
-          s1d = ((vnd - (double)var) / (double)var) / (S + 1.0);
-        }
-        bx = -s1d * Px / Wd + dx;
-        by = -s1d * Py / Wd + dy;
-        bz = -s1d * Pz / Wd + dz;
-      }
-    }
-  }
-  __syncthreads();
-  int job = -1;
-  if (need) {
-    job = atomicAdd(&njobs, 1);
-    jobs[job] = RemapJob{cell, ne, (float)s1d, (float)bx, (float)by, (float)bz};
-  }
-  __syncthreads();
-  const int nj = njobs;
-  for (int k = wid; k < nj; k += kFeedbackThreads / 32) {
-    const RemapJob J = jobs[k];
-    const RemapOut r = remap_electrons(A, (long)J.cell * A.e.cap, J.ne, J.s1, J.bx, J.by, J.bz);
-    if (lane == 0) outs[k] = r;
-  }
-  __syncthreads();
-  if (!valid) return;
-  double nrE = qE, nrPx = qPx, nrPy = qPy, nrPz = qPz, applied_E = 0.0;
-  float var_new = var;
-  if (job >= 0) {
-    const RemapOut r = outs[job];
-    applied_E = r.applied_E;
-    nrE = qE - r.applied_E;
-    nrPx = qPx - r.apx;
-    nrPy = qPy - r.apy;
-    nrPz = qPz - r.apz;
-    var_new = (float)vnd;
-    float* mom = A.mom + (size_t)cell * kMomLen;
-    mom[M_W] = r.mW;
-    mom[M_PX] = r.mPx;
-    mom[M_PY] = r.mPy;
-    mom[M_PZ] = r.mPz;
-    mom[M_U2] = r.mU2;
-    mom[M_VAR] = fmaxf(0.f, r.mU2 - (r.mPx * r.mPx + r.mPy * r.mPy + r.mPz * r.mPz) / r.mW);
-  }
-  if (has_x || has_res) {
-    double* rs = A.res + (size_t)cell * 4;
-    rs[0] = nrE;
-    rs[1] = nrPx;
-    rs[2] = nrPy;
-    rs[3] = nrPz;
-  }
-  if (need) {
-    atomicAdd(A.counters + C_REMAP, 1ull);
-    atomicAdd(A.counters + C_REMAP_E, (unsigned long long)ne);
-  }
-  if (A.diag_enable) {
-    double* dg = A.diag + (size_t)cell * AXPIC_CELL_DIAG_LEN;
-    dg[AXPIC_CD_DE] = dE;
-    dg[AXPIC_CD_DPX] = dPx;
-    dg[AXPIC_CD_DPY] = dPy;
-    dg[AXPIC_CD_DPZ] = dPz;
-    dg[AXPIC_CD_S_MINUS_1] = s1d;
-    dg[AXPIC_CD_BX] = bx;
-    dg[AXPIC_CD_BY] = by;
-    dg[AXPIC_CD_BZ] = bz;
-    dg[AXPIC_CD_VAR] = var;
-    dg[AXPIC_CD_VAR_NEW] = need ? vnd : (double)var;
-    dg[AXPIC_CD_W] = W;
-    dg[AXPIC_CD_APPLIED_E] = applied_E;
-    dg[AXPIC_CD_RES_E] = has_x || has_res ? nrE : 0.0;
-    dg[AXPIC_CD_RES_PX] = has_x || has_res ? nrPx : 0.0;
-    dg[AXPIC_CD_RES_PY] = has_x || has_res ? nrPy : 0.0;
-    dg[AXPIC_CD_RES_PZ] = has_x || has_res ? nrPz : 0.0;
-  }
-  // temperature (Eqs. Te_est, Te_relax), then the record's temperature half;
-  // T stays FP64, the relaxation step is formed in binary32 and added once
-  if (A.T_mode == 2 && W > 0.f) {
-    const float Tf = (float)T;
-    const float Test = (kMeC2f / 3.0f) * var_new / W;
-    const float dT = A.relax_r * (Test - Tf);
-    double Tn = T + (double)dT;
-    const float Tnf = Tf + dT;
-    if (Tnf <= A.T_floor_f || Tnf >= A.T_ceil_f) Tn = fmin(fmax(Tn, A.T_floor), A.T_ceil);
-    float rec[kRecLen] = {rc0.x, rc0.y, rc0.z, rc0.w, rc1.x, rc1.y, rc1.z, rc1.w,
-                          rc2.x, rc2.y, rc2.z, rc2.w, rc3.x, rc3.y, rc3.z, rc3.w};
-    compute_temperature(A.cc, (float)Tn, rec);
-    A.T[cell] = Tn;
-    float4* r4 = reinterpret_cast<float4*>(A.rec + (size_t)cell * kRecLen);
-    r4[0] = make_float4(rec[0], rec[1], rec[2], rec[3]);
-    r4[1] = make_float4(rec[4], rec[5], rec[6], rec[7]);
-  }
-}
-
-
 // ---------------------------------------------------------------- launchers
 size_t step_smem_per_warp(int acap, int gcap, int ecap) { return ev_scratch_bytes(acap, gcap, ecap); }
 
 template <int PH>
 static cudaError_t launch_events(const StepArgs& A, int warps, cudaStream_t st) {
   const size_t per = ev_scratch_bytes(A.a.cap, A.g.cap, A.e.cap);
-  const int grid = (A.ncells + warps - 1) / warps;
+  const int grid = (A.ncells + 32 * warps - 1) / (32 * warps);
   event_kernel<PH><<<grid, warps * 32, per * warps, st>>>(A);
   return cudaGetLastError();
 }
