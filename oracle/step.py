@@ -22,13 +22,23 @@ each): step order absorb -> emit -> feedback; Philox4x32-10 counters
 (step, cell, particle, stream<<24 | sub); decisions use one 32-bit word per
 particle, word (i & 3) of block (i >> 2); event j of particle i uses block
 (step, cell, i, stream<<24 | j) with words (cos theta, phi, energy); new axions
-are appended after the survivors, photon products first (photon order), then
-electron products (electron order, then event order; an electron's two
-thermal-bath channels are drawn as one superposed Poisson process and each
-event is attributed to a channel by a further uniform); removed particles leave holes that are filled by the survivors found
-beyond the new count, in ascending order ("tail fill"); weights are binary32
-quantities and depletion is evaluated in binary32 because it decides whether
-the parent survives.
+are made photon products first (photon order), then electron products
+(electron order, then event order; an electron's two thermal-bath channels are
+drawn as one superposed Poisson process and each event is attributed to a
+channel by a further uniform); weights are binary32 quantities and depletion
+is evaluated in binary32 because it decides whether the parent survives.
+
+Slot order (the paper fixes none; both implementations share this one):
+* a separate absorb or emit call (absorb_cell, emit_cell) appends its new
+  particles after the survivors and closes its holes by the tail fill (holes
+  below the survivor count take, in ascending order, the survivors found at or
+  beyond it);
+* a full step (step_cell) does the same for the photons (a->gamma products
+  appended in the absorb phase, holes of the emit phase closed by the tail
+  fill), while the axion slots freed in the absorb phase are reused by the
+  axions made in the emit phase: the freed slots, in ascending order, take the
+  new axions in the order they are made; new axions beyond them are appended
+  after the old count, and freed slots left over are closed by the tail fill.
 """
 import math
 from dataclasses import dataclass, field
@@ -161,6 +171,24 @@ def tail_fill(keep):
     return order
 
 
+def recycle(s: Species, keep, new: Species):
+    """Axion slots after a full step: the slots freed earlier in the step
+    (~keep, ascending) take the new particles in order; new particles beyond
+    them are appended after the old count; freed slots left over are closed by
+    the tail fill."""
+    keep = np.asarray(keep, dtype=bool)
+    holes = np.flatnonzero(~keep)
+    k = min(len(holes), len(new))
+    out = s.copy()
+    for f_out, f_new in zip(out.fields(), new.fields()):
+        f_out[holes[:k]] = f_new[:k]
+    if len(new) >= len(holes):
+        return out.concat(new.take(np.arange(k, len(new))))
+    keep2 = keep.copy()
+    keep2[holes[:k]] = True
+    return out.take(tail_fill(keep2))
+
+
 def f32(a):
     return np.asarray(a, dtype=np.float64).astype(F32)
 
@@ -200,15 +228,17 @@ def _in_records(x):
     return (x >= 0.05) & (x <= 20.0)
 
 
-def absorb_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, rec=None):
+def _absorb(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, rec=None):
     """Inverse operators on the axions present at the start of the step. With
     a spectral record (table or surrogate rate model) the Primakoff and
-    absorption rates at x = E/T in [0.05, 20] come from it."""
+    absorption rates at x = E/T in [0.05, 20] come from it. Returns the axions
+    with their new weights, which of them stay, and the photon products."""
     a = parts["a"]
     tally.n_g0 = len(parts["g"])
     n = len(a)
+    new_g = Species.empty()
     if n == 0:
-        return
+        return a, np.ones(0, dtype=bool), new_g
     omega = a.pmag() * K.ME_C2_KEV
     w = a.w.copy()
     x = omega / cs.T_keV
@@ -226,7 +256,7 @@ def absorb_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTa
         tally.cap_hits += int(capped.sum())
         tally.clamp_hits += int(over.sum())
         if Kc.sum() > 0:
-            parts["g"] = parts["g"].concat(_repeat_products(a, Kc, wprod))
+            new_g = _repeat_products(a, Kc, wprod)
     keep = w > 0
     want_c = bool(mask & CH_COMPTON)
     want_b = bool(mask & CH_BREMS)
@@ -268,14 +298,24 @@ def absorb_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTa
             keep = keep & (w > 0)
     a2 = a.copy()
     a2.w = w
+    return a2, keep, new_g
+
+
+def absorb_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, rec=None):
+    """Absorb phase of a separate call: photon products appended, axion holes
+    closed by the tail fill."""
+    a2, keep, new_g = _absorb(cs, parts, p, step, cell, mask, tally, rec)
     parts["a"] = a2.take(tail_fill(keep))
+    if len(new_g):
+        parts["g"] = parts["g"].concat(new_g)
 
 
-def emit_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, n_g0=None, rec=None):
+def _emit(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, n_g0=None, rec=None):
     """Forward operators: Primakoff on photons present at step start, then
-    thermal-bath emission on electrons; products are appended to the axions.
-    With a spectral record the Primakoff rate (x in [0.05, 20]) and the
-    emitted energies come from it."""
+    thermal-bath emission on electrons. With a spectral record the Primakoff
+    rate (x in [0.05, 20]) and the emitted energies come from it. Returns the
+    photons with their remaining weights, which of them stay, and the new
+    axions."""
     if n_g0 is None:
         n_g0 = len(parts["g"])
     g = parts["g"]
@@ -306,7 +346,7 @@ def emit_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTall
         energy_blocks.append(np.repeat(omega, Kc))
         g = g.copy()
         g.w[:n_g0] = wrem
-    parts["g"] = g.take(tail_fill(g.w > 0))
+    keep_g = g.w > 0
     e = parts["e"]
     ne = len(e)
     if (mask & (CH_COMPTON | CH_BREMS)) and ne > 0:
@@ -353,13 +393,22 @@ def emit_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTall
             new_blocks.append(prods)
             chan_blocks.append(np.where(is_c, CH_COMPTON, CH_BREMS))
             energy_blocks.append(E)
+    new = Species.empty()
+    for b in new_blocks:
+        new = new.concat(b)
     if new_blocks:
-        new = new_blocks[0]
-        for b in new_blocks[1:]:
-            new = new.concat(b)
-        parts["a"] = parts["a"].concat(new)
         tally.new_axion_channel = np.concatenate(chan_blocks)
         tally.new_axion_E = np.concatenate(energy_blocks)
+    return g, keep_g, new
+
+
+def emit_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, n_g0=None, rec=None):
+    """Emit phase of a separate call: photon holes closed by the tail fill,
+    new axions appended."""
+    g, keep_g, new_a = _emit(cs, parts, p, step, cell, mask, tally, n_g0, rec)
+    parts["g"] = g.take(tail_fill(keep_g))
+    if len(new_a):
+        parts["a"] = parts["a"].concat(new_a)
 
 
 @dataclass
@@ -430,11 +479,17 @@ class CellInput:
 
 def step_cell(ci: CellInput, parts, p: Params, step, cell, mask, res_E=0.0, res_P=None, feedback=True, rec=None):
     """absorb -> emit -> feedback for one cell; returns (tally, feedback result).
-    rec: the cell's spectral record (table or surrogate rate model) or None."""
+    The axions made in the emit phase reuse the axion slots freed in the
+    absorb phase (recycle). rec: the cell's spectral record (table or
+    surrogate rate model) or None."""
     cs = cell_state(ci.T_keV, ci.n_ion, ci.Z, ci.A, p)
     tally = StepTally()
-    absorb_cell(cs, parts, p, step, cell, mask, tally, rec)
-    emit_cell(cs, parts, p, step, cell, mask, tally, n_g0=tally.n_g0, rec=rec)
+    a2, keep_a, new_g = _absorb(cs, parts, p, step, cell, mask, tally, rec)
+    if len(new_g):
+        parts["g"] = parts["g"].concat(new_g)
+    g2, keep_g, new_a = _emit(cs, parts, p, step, cell, mask, tally, n_g0=tally.n_g0, rec=rec)
+    parts["g"] = g2.take(tail_fill(keep_g))
+    parts["a"] = recycle(a2, keep_a, new_a)
     fb = None
     if feedback:
         fb = feedback_cell(cs, parts, p, tally, res_E, res_P)

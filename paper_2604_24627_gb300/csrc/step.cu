@@ -1198,13 +1198,25 @@ __device__ __forceinline__ int photon_outcome(const StepArgs& A, const PhItem& t
   return K;
 }
 
-// The K axion products of a gamma->a event, from position dst0 on.
-__device__ __forceinline__ void gamma_products(const StepArgs& A, const PhItem& t, long abase, int dst0, int K,
-                                               const Cnt& cnt) {
+// Slot of the i-th new axion of an emit phase: the freed slots holes[0,
+// nholes) (ascending, entries `stride` apart) first, then from base on. A
+// separate emit call has no freed slots (base: the axion count); a full step
+// reuses the slots its absorb phase freed (base: the count at its start).
+struct AxDest {
+  const uint16_t* holes;
+  int nholes, stride, base;
+  __device__ __forceinline__ int at(int i) const {
+    return i < nholes ? (int)holes[stride * i] : base + (i - nholes);
+  }
+};
+
+// The K axion products of a gamma->a event, new axions i0 .. i0 + K - 1.
+__device__ __forceinline__ void gamma_products(const StepArgs& A, const PhItem& t, long abase, const AxDest& D,
+                                               int i0, int K, const Cnt& cnt) {
   const float wprod = __uint_as_float(t.r.y);
   const float om = sqrtf(t.px * t.px + t.py * t.py + t.pz * t.pz) * kMeC2f;
   for (int k = 0; k < K; ++k) {
-    const int dst = dst0 + k;
+    const int dst = D.at(i0 + k);
     if (dst < A.a.cap) {
       write_particle(A.a, abase + dst, wprod, t.px, t.py, t.pz, t.x, t.y, t.z);
       if (A.tally_enable) tally_add(A, 0, wprod, om);
@@ -1214,12 +1226,12 @@ __device__ __forceinline__ void gamma_products(const StepArgs& A, const PhItem& 
   }
 }
 
-// The events of a flagged electron (thermal-bath emission), from position
-// dst0 on: event k takes cos theta, phi, energy and channel from one Philox
+// The events of a flagged electron (thermal-bath emission), new axions i0
+// on: event k takes cos theta, phi, energy and channel from one Philox
 // block. Returns K.
 __device__ __forceinline__ int electron_events(const StepArgs& A, uint32_t step, int cell, const ElItem& t,
-                                               long abase, int dst0, float r_cc, float r_cb, float r_T,
-                                               float wu, const Cnt& cnt, Lane64& x64) {
+                                               long abase, const AxDest& D, int i0, float r_cc, float r_cb,
+                                               float r_T, float wu, const Cnt& cnt, Lane64& x64) {
   const int K = t.f & 0xFF;
   if (wu <= 0.f) cnt.add(C_CAP, ((t.f & DF_CAPPED) ? 1u : 0u) + ((t.f & DF_CAPPED_B) ? 1u : 0u));
   if (!K) return 0;
@@ -1242,7 +1254,7 @@ __device__ __forceinline__ int electron_events(const StepArgs& A, uint32_t step,
     const float wv = isC ? wvC : wvB;
     const float pm = E * kInvMeC2f;
     const float px = pm * dv.x, py = pm * dv.y, pz = pm * dv.z;
-    const int dst = dst0 + k;
+    const int dst = D.at(i0 + k);
     if (dst < A.a.cap) {
       write_particle(A.a, abase + dst, wv, px, py, pz, t.x, t.y, t.z);
       if (A.tally_enable) tally_add(A, isC ? 1 : 2, wv, E);
@@ -1257,7 +1269,7 @@ __device__ __forceinline__ int electron_events(const StepArgs& A, uint32_t step,
 
 // ---------------------------------------------------------------- warp path
 struct PhaseOut {
-  int na, ng;
+  int na, ng, np;  // axion and photon counts, new axions
   double x[4];
   bool any;
 };
@@ -1274,9 +1286,10 @@ __device__ __forceinline__ void reduce_out(const Lane64& x64, PhaseOut* out) {
 }
 
 // Absorb phase of one cell by the warp: a->gamma products, absorption and
-// weight reduction, then the axion tail fill.
+// weight reduction, then (fill) the axion tail fill; without it the freed
+// slots stay listed, ascending, in S.rmA (marked in S.rbA).
 __device__ __noinline__ void absorb_warp(const StepArgs& A, int cell, EvScratch& S, const uint32_t* row,
-                                         uint32_t* clr, const Cnt& cnt, int na_start, int ng_start,
+                                         uint32_t* clr, const Cnt& cnt, int na_start, int ng_start, bool fill,
                                          PhaseOut* out) {
   const int lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
@@ -1311,16 +1324,18 @@ __device__ __noinline__ void absorb_warp(const StepArgs& A, int cell, EvScratch&
   }
   reduce_out(x64, out);
   __syncwarp();
-  if (nrm > 0) compact_tail(A.a, abase, S.rmA, S.rbA, na_start - nrm, na_start);
+  if (fill && nrm > 0) compact_tail(A.a, abase, S.rmA, S.rbA, na_start - nrm, na_start);
   out->na = na_start - nrm;
   out->ng = min(ng_start + run, A.g.cap);
+  out->np = 0;
 }
 
-// Emit phase of one cell by the warp: gamma->a, the thermal-bath events, then
-// the photon tail fill (a->gamma products included).
+// Emit phase of one cell by the warp: gamma->a, the thermal-bath events (new
+// axions placed by D), then the photon tail fill (a->gamma products
+// included).
 __device__ __noinline__ void emit_warp(const StepArgs& A, uint32_t step, int cell, EvScratch& S,
                                        const uint32_t* rowG, uint32_t* clrG, const uint32_t* rowE, uint32_t* clrE,
-                                       const Cnt& cnt, int na, int ng_tot, int ng0, int ne, float wu, float r_cc,
+                                       const Cnt& cnt, AxDest D, int ng_tot, int ng0, int ne, float wu, float r_cc,
                                        float r_cb, float r_T, PhaseOut* out) {
   const int lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
@@ -1339,7 +1354,7 @@ __device__ __noinline__ void emit_warp(const StepArgs& A, uint32_t step, int cel
     if (t.slot >= 0) K = photon_outcome(A, t, gbase, cnt, &removed);
     int tot;
     const int off = run + warp_excl_scan(K, &tot);
-    if (K) gamma_products(A, t, abase, na + off, K, cnt);
+    if (K) gamma_products(A, t, abase, D, off, K, cnt);
     run += tot;
     const unsigned m = __ballot_sync(kFull, removed);
     if (removed) {
@@ -1354,14 +1369,15 @@ __device__ __noinline__ void emit_warp(const StepArgs& A, uint32_t step, int cel
     const int K = t.slot >= 0 ? (int)(t.f & 0xFF) : 0;
     int tot;
     const int off = run + warp_excl_scan(K, &tot);
-    if (t.slot >= 0) electron_events(A, step, cell, t, abase, na + off, r_cc, r_cb, r_T, wu, cnt, x64);
+    if (t.slot >= 0) electron_events(A, step, cell, t, abase, D, off, r_cc, r_cb, r_T, wu, cnt, x64);
     run += tot;
   }
   reduce_out(x64, out);
   __syncwarp();
   if (nrm > 0) compact_tail(A.g, gbase, S.rmG, S.rbG, ng_tot - nrm, ng_tot);
-  out->na = min(na + run, A.a.cap);
+  out->na = min(D.base - D.nholes + run, A.a.cap);
   out->ng = ng_tot - nrm;
+  out->np = run;
 }
 
 // ---------------------------------------------------------------- lane path
@@ -1478,11 +1494,13 @@ __device__ __forceinline__ void fill_rest(const SpeciesPtrs& sp, long base, cons
   }
 }
 
-// One cell by one lane: its absorb phase (doA), its emit phase (doE) or
-// both. Round trips: the first kLoad flagged axions and photons together;
-// the first kLoad tail movers of both species together; then the stores.
-// Longer lists take further round trips. Axion movers are read before any
-// gamma->a product is written over their slots.
+// One cell by one lane: its absorb phase (doA), its emit phase (doE) or the
+// full step (both: the new axions of the emit phase reuse the axion slots the
+// absorb phase freed). Round trips: the first kLoad flagged axions and
+// photons together; the first kLoad tail movers together; then the stores.
+// Longer lists take further round trips. Every flagged axion is read before
+// a new axion is written over a freed slot, and axion movers before any new
+// axion is written.
 struct LaneCell {
   int na, ng;       // in: counts at the start of the phase(s); out: final counts
   int ng0, ne;      // photons eligible for gamma->a, electrons
@@ -1554,37 +1572,49 @@ __device__ __forceinline__ void cell_lane(const StepArgs& A, uint32_t step, int 
     }
   }
 
-  // tail movers of both species, loaded together
-  FillIt fa = fill_begin(lA, nrmA, na);
+  // tail movers, loaded together: the axions' unless the step reuses the
+  // freed slots, the photons' when every photon removal is known
+  const bool reuse = doA && doE;
+  FillIt fa = fill_begin(lA, reuse ? 0 : nrmA, na);
   Mover ma[kLoad], mg[kLoad];
-  fill_load(A.a, abase, lA, nrmA, fa, ma);
-  const bool gFill = nG <= kLoad;  // every photon removal is known
+  fill_load(A.a, abase, lA, reuse ? 0 : nrmA, fa, ma);
+  const bool gFill = nG <= kLoad;
   FillIt fg = fill_begin(lG, nrmG, ng - nrmG);
   if (gFill) fill_load(A.g, gbase, lG, nrmG, fg, mg);
+  if (!reuse) {
 #pragma unroll
-  for (int t = 0; t < kLoad; ++t) mover_store(A.a, abase, ma[t]);
-  fill_rest(A.a, abase, lA, nrmA, fa);
+    for (int t = 0; t < kLoad; ++t) mover_store(A.a, abase, ma[t]);
+    fill_rest(A.a, abase, lA, nrmA, fa);
+  }
 
   if (doE) {
+    // new axions: gamma->a products, then thermal-bath events
+    const AxDest D{lA, reuse ? nrmA : 0, 32, reuse ? L.na : na};
     int NP = 0;
 #pragma unroll
     for (int j = 0; j < kLoad; ++j) {
-      if (Kg[j]) gamma_products(A, tg[j], abase, na + NP, Kg[j], cnt);
+      if (Kg[j]) gamma_products(A, tg[j], abase, D, NP, Kg[j], cnt);
       NP += Kg[j];
     }
     for (int i = kLoad; i < nG; ++i) {
       const PhItem t = ph_load(A, gbase, lG[32 * i]);
       bool removed;
       const int K = photon_outcome(A, t, gbase, cnt, &removed);
-      if (K) gamma_products(A, t, abase, na + NP, K, cnt);
+      if (K) gamma_products(A, t, abase, D, NP, K, cnt);
       NP += K;
       if (removed) lG[32 * nrmG++] = (uint16_t)t.slot;
     }
     for (int i = 0; i < nE; ++i) {
       const ElItem t = el_load(A, ebase, lE[32 * i], L.wu);
-      NP += electron_events(A, step, cell, t, abase, na + NP, L.r_cc, L.r_cb, L.r_T, L.wu, cnt, xe);
+      NP += electron_events(A, step, cell, t, abase, D, NP, L.r_cc, L.r_cb, L.r_T, L.wu, cnt, xe);
     }
-    na = min(na + NP, A.a.cap);
+    na = min(D.base - D.nholes + NP, A.a.cap);
+    if (reuse && NP < nrmA) {
+      // freed slots left over: closed from the tail (their movers lie beyond
+      // every slot a new axion took)
+      FillIt fr = fill_begin(lA + 32 * NP, nrmA - NP, na);
+      fill_rest(A.a, abase, lA + 32 * NP, nrmA - NP, fr);
+    }
     // photon tail fill (a->gamma products included)
     if (gFill) {
 #pragma unroll
@@ -1718,22 +1748,55 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
   }
 
   Lane64 xa, xe;
-  const bool doA = (PH & PH_ABSORB) && valid && !hA;
-  const bool doE = (PH & PH_EMIT) && valid && !hE;
-  // light in every phase of the call: the lane takes the whole cell now
-  if (doA && ((PH & PH_EMIT) ? doE : true) && (L.nflA | L.nflG | L.nflE))
-    cell_lane(A, step, cell, true, (PH & PH_EMIT) != 0, lA, lG, lE, L, cnt, xa, xe);
-  else if (doA && L.nflA)
-    cell_lane(A, step, cell, true, false, lA, lG, lE, L, cnt, xa, xe);
-  __syncwarp();
-  if (PH & PH_ABSORB) {
+  if (PH == (PH_ABSORB | PH_EMIT)) {
+    // full step: a cell light in both phases is taken by its lane, any other
+    // by the whole warp; either way the new axions reuse the freed slots
+    const bool heavy = valid && (hA || hE);
+    if (valid && !heavy && (L.nflA | L.nflG | L.nflE))
+      cell_lane(A, step, cell, true, true, lA, lG, lE, L, cnt, xa, xe);
+    __syncwarp();
+    for (unsigned hm = __ballot_sync(kFull, heavy); hm; hm &= hm - 1u) {
+      const int j = __ffs(hm) - 1;
+      const int c = __shfl_sync(kFull, cell, j);
+      const int na0 = __shfl_sync(kFull, na_start, j);
+      PhaseOut oa, oe;
+      absorb_warp(A, c, S, staged ? S.rowA + j * S.sA : A.bitsA + (size_t)c * A.Wa,
+                  staged ? nullptr : A.bitsA + (size_t)c * A.Wa, cnt, na0, __shfl_sync(kFull, ng_start, j), false,
+                  &oa);
+      const int nrmA = na0 - oa.na;
+      const uint32_t* gG = emitG ? (staged ? S.rowG + j * S.sG : A.bitsG + (size_t)c * A.Wg) : nullptr;
+      const uint32_t* gE = emitE ? (staged ? S.rowE + j * S.sE : A.bitsE + (size_t)c * A.We) : nullptr;
+      emit_warp(A, step, c, S, gG, (emitG && !staged) ? A.bitsG + (size_t)c * A.Wg : nullptr, gE,
+                (emitE && !staged) ? A.bitsE + (size_t)c * A.We : nullptr, cnt, AxDest{S.rmA, nrmA, 1, na0},
+                oa.ng, __shfl_sync(kFull, L.ng0, j), __shfl_sync(kFull, ne, j), __shfl_sync(kFull, L.wu, j),
+                __shfl_sync(kFull, L.r_cc, j), __shfl_sync(kFull, L.r_cb, j), __shfl_sync(kFull, L.r_T, j), &oe);
+      // freed slots left over: closed from the tail
+      if (oe.np < nrmA) compact_tail(A.a, (long)c * A.a.cap, S.rmA + oe.np, S.rbA, oe.na, na0);
+      if (lane == j) {
+        L.na = oe.na;
+        L.ng = oe.ng;
+        xa.dE = oa.x[0];
+        xa.dPx = oa.x[1];
+        xa.dPy = oa.x[2];
+        xa.dPz = oa.x[3];
+        xa.any = oa.any;
+        xe.dE = oe.x[0];
+        xe.dPx = oe.x[1];
+        xe.dPy = oe.x[2];
+        xe.dPz = oe.x[3];
+        xe.any = oe.any;
+      }
+    }
+  } else if (PH == PH_ABSORB) {
+    if (valid && !hA && L.nflA) cell_lane(A, step, cell, true, false, lA, lG, lE, L, cnt, xa, xe);
+    __syncwarp();
     for (unsigned hm = __ballot_sync(kFull, valid && hA); hm; hm &= hm - 1u) {
       const int j = __ffs(hm) - 1;
       const int c = __shfl_sync(kFull, cell, j);
       PhaseOut o;
       absorb_warp(A, c, S, staged ? S.rowA + j * S.sA : A.bitsA + (size_t)c * A.Wa,
                   staged ? nullptr : A.bitsA + (size_t)c * A.Wa, cnt, __shfl_sync(kFull, na_start, j),
-                  __shfl_sync(kFull, ng_start, j), &o);
+                  __shfl_sync(kFull, ng_start, j), true, &o);
       if (lane == j) {
         L.na = o.na;
         L.ng = o.ng;
@@ -1744,13 +1807,8 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
         xa.any = o.any;
       }
     }
-  }
-  if (PH & PH_EMIT) {
-    // the emit phase of cells heavy for absorb only
-    if (doE && (PH & PH_ABSORB) && hA && (L.nflG | L.nflE))
-      cell_lane(A, step, cell, false, true, lA, lG, lE, L, cnt, xa, xe);
-    if (doE && !(PH & PH_ABSORB) && (L.nflG | L.nflE))
-      cell_lane(A, step, cell, false, true, lA, lG, lE, L, cnt, xa, xe);
+  } else {
+    if (valid && !hE && (L.nflG | L.nflE)) cell_lane(A, step, cell, false, true, lA, lG, lE, L, cnt, xa, xe);
     __syncwarp();
     for (unsigned hm = __ballot_sync(kFull, valid && hE); hm; hm &= hm - 1u) {
       const int j = __ffs(hm) - 1;
@@ -1759,10 +1817,10 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
       const uint32_t* gG = emitG ? (staged ? S.rowG + j * S.sG : A.bitsG + (size_t)c * A.Wg) : nullptr;
       const uint32_t* gE = emitE ? (staged ? S.rowE + j * S.sE : A.bitsE + (size_t)c * A.We) : nullptr;
       emit_warp(A, step, c, S, gG, (emitG && !staged) ? A.bitsG + (size_t)c * A.Wg : nullptr, gE,
-                (emitE && !staged) ? A.bitsE + (size_t)c * A.We : nullptr, cnt, __shfl_sync(kFull, L.na, j),
-                __shfl_sync(kFull, L.ng, j), __shfl_sync(kFull, L.ng0, j), __shfl_sync(kFull, ne, j),
-                __shfl_sync(kFull, L.wu, j), __shfl_sync(kFull, L.r_cc, j), __shfl_sync(kFull, L.r_cb, j),
-                __shfl_sync(kFull, L.r_T, j), &o);
+                (emitE && !staged) ? A.bitsE + (size_t)c * A.We : nullptr, cnt,
+                AxDest{nullptr, 0, 1, __shfl_sync(kFull, L.na, j)}, __shfl_sync(kFull, L.ng, j),
+                __shfl_sync(kFull, L.ng0, j), __shfl_sync(kFull, ne, j), __shfl_sync(kFull, L.wu, j),
+                __shfl_sync(kFull, L.r_cc, j), __shfl_sync(kFull, L.r_cb, j), __shfl_sync(kFull, L.r_T, j), &o);
       if (lane == j) {
         L.na = o.na;
         L.ng = o.ng;

@@ -41,6 +41,63 @@ def test_tail_fill_against_list_algorithm():
         assert sorted(order) == sorted(np.flatnonzero(keep))
 
 
+def test_recycle_against_list_algorithm():
+    """Full-step slots: lost slots take the new particles in order, the rest
+    are appended or the leftover holes closed by the tail fill; written out
+    with plain lists."""
+    rng = np.random.default_rng(1)
+    for trial in range(400):
+        n = int(rng.integers(0, 30))
+        m = int(rng.integers(0, 12))
+        keep = rng.uniform(size=n) < rng.uniform()
+        old = S.Species(*[np.arange(n, dtype=float) + 100.0 * k for k in range(7)])
+        new = S.Species(*[-1.0 - np.arange(m, dtype=float) - 100.0 * k for k in range(7)])
+        got = S.recycle(old, keep, new)
+        slots = [i if keep[i] else None for i in range(n)]   # survivors by old index
+        fresh = [-1.0 - j for j in range(m)]
+        for i in range(n):
+            if slots[i] is None and fresh:
+                slots[i] = fresh.pop(0)
+        vals = [(float(v) if v is not None and v < 0 else v) for v in slots]
+        if fresh:
+            out = vals + fresh
+        else:
+            # close the remaining holes from the tail, in ascending order
+            live = [v for v in vals if v is not None]
+            ns = len(live)
+            movers = [vals[i] for i in range(ns, n) if vals[i] is not None]
+            out = [vals[i] if vals[i] is not None else movers.pop(0) for i in range(ns)]
+        want = [float(v) for v in out]
+        assert list(got.w) == want, (keep, m, list(got.w), want)
+        assert list(got.z) == [v - 600.0 if v < 0 else v + 600.0 for v in want]
+        assert len(got) == int(keep.sum()) + m
+
+
+def test_full_step_holds_the_particles_of_separate_calls():
+    """One full step and absorb + emit calls from the same state give the same
+    particles (decisions do not depend on slot order within a step): photons
+    slot for slot, axions in other slots (the full step reuses freed ones)."""
+    p = Params(g_agg_GeV_inv=1e-10, g_ae=2e-12, dt_phys_s=4e12, seed=5)
+    for cell in range(6):
+        init = S.init_cell(p, cell, 3.0, 6e25, 1e-12, 96, 128, 80)
+        p.w_a = init["g"].w[0]
+        p.w_gamma_ref = p.w_a
+        ci = S.CellInput(3.0, *_hyd())
+        fused = {k: v.copy() for k, v in init.items()}
+        sep = {k: v.copy() for k, v in init.items()}
+        t1, _ = S.step_cell(ci, fused, p, 4, cell, 7, feedback=False)
+        cs = cell_state(3.0, *_hyd(), p)
+        t2 = S.StepTally()
+        S.absorb_cell(cs, sep, p, 4, cell, 7, t2)
+        S.emit_cell(cs, sep, p, 4, cell, 7, t2, n_g0=t2.n_g0)
+        assert t1.events == t2.events and abs(t1.dE - t2.dE) <= 1e-12 * max(t1.gross_E, 1e-300)
+        assert np.array_equal(np.stack(fused["g"].fields()), np.stack(sep["g"].fields()))
+        a = np.stack(fused["a"].fields(), 1)
+        b = np.stack(sep["a"].fields(), 1)
+        assert a.shape == b.shape
+        assert np.array_equal(a[np.lexsort(a.T[::-1])], b[np.lexsort(b.T[::-1])])
+
+
 # ---------------------------------------------------------------- feedback
 
 def _fb(parts, dE, dP, T=3.0, p=None):
