@@ -519,6 +519,44 @@ __device__ __forceinline__ void electron_chunk(const StepArgs& A, uint32_t step,
       thr = (int)floorf(__fsub_rn(__fmul_rn(expf(-lsum), 8388608.0f), 0.5f));
     }
   }
+  if (__all_sync(kFull, lane >= nc || (wu > 0.f && (((n + 3) >> 2) & 63) == 0))) {
+    // every cell of the chunk has a common weight and whole passes of 64
+    // quads: cell by cell, two quads per lane and pass (two independent
+    // Philox chains in flight), the decision the integer compare alone
+    for (int lc = 0; lc < nc; ++lc) {
+      const int nn = __shfl_sync(kFull, n, lc);
+      const int cthr = __shfl_sync(kFull, thr, lc);
+      const float cls = __shfl_sync(kFull, lsum, lc);
+      const int cell = c0 + lc;
+      const uint32_t gcell = A.cell_base + (uint32_t)cell;
+      const long cb = (long)cell * A.e.cap;
+      const int nq = (nn + 3) >> 2;
+      for (int q0 = 0; q0 < nq; q0 += 64) {
+        uint4 r[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          r[h] = philox4x32_10(make_uint4(step, gcell, (uint32_t)(q0 + 32 * h + lane), S_EMIT_E << 24), A.rk);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int q = q0 + 32 * h + lane;
+          const uint32_t m = max(max(r[h].x, r[h].y), max(r[h].z, r[h].w));
+          if ((int)(m >> 9) <= cthr) continue;  // no slot of the quad emits
+          const int nj = min(4, nn - 4 * q);
+          uint32_t nib = 0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint32_t wj = word(r[h], j);
+            if (j < nj && (int)(wj >> 9) > cthr) {
+              A.recE[cb + 4 * q + j] = (uint32_t)poisson_inv(u23(wj), cls);
+              nib |= 1u << j;
+            }
+          }
+          flag_quad(A.bitsE, A.We, cell, q, nib);
+        }
+      }
+    }
+    return;
+  }
   const QuadRange<C> R = quad_range<C>(n, lane, nc);
   if (__all_sync(kFull, lane >= nc || wu > 0.f)) {
     // every cell of the chunk has a common weight: the decision is the

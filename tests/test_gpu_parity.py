@@ -189,6 +189,24 @@ def test_fused_step_matches_oracle(case):
     pl.close()
 
 
+@pytest.mark.parametrize("n_el", [256, 512])
+def test_whole_electron_passes_match_oracle(n_el):
+    """Cells whose electrons fill whole passes of 64 quads take the
+    cell-by-cell electron decisions; every chunk here does."""
+    prm = base_params()
+    ncells = 12
+    pl = make(ncells, np.linspace(1.5, 4.5, ncells), prm, caps=(n_el, 192, 512), counts=(n_el, 37, 13))
+    for step in range(3):
+        before = [pl.cell(c) for c in range(ncells)]
+        T_before = pl.temperatures().copy()
+        res_before = pl.residuals()
+        pl.step(step, _lib.CH_ALL)
+        _compare_step(pl, before, T_before, prm, step, _lib.CH_ALL, res_before, "%d e- step %d" % (n_el, step))
+    _, tot = pl.tally()
+    assert tot["events_c"] > 0 and tot["events_b"] > 0, tot
+    pl.close()
+
+
 def test_channel_masks_each_alone():
     prm = base_params()
     for mask in (1, 2, 4, 3, 6):
