@@ -306,45 +306,64 @@ __device__ __noinline__ RemapOut remap_electrons(const StepArgs& A, long ebase, 
   float aE = 0.f, aPx = 0.f, aPy = 0.f, aPz = 0.f;
   float mW = 0.f, mPx = 0.f, mPy = 0.f, mPz = 0.f, mU2 = 0.f;
   const int nqe = (ne + 3) >> 2;
-  for (int q = lane; q < nqe; q += 32) {
-    const long b = ebase + 4 * q;
-    const float4 w4 = ld4(A.e.w + b);
-    float4 x4 = ld4(A.e.px + b), y4 = ld4(A.e.py + b), z4 = ld4(A.e.pz + b);
-    float* xs = reinterpret_cast<float*>(&x4);
-    float* ys = reinterpret_cast<float*>(&y4);
-    float* zs = reinterpret_cast<float*>(&z4);
-    const float* ws = reinterpret_cast<const float*>(&w4);
-    const int nj = min(4, ne - 4 * q);
+  // two quads per lane and pass, both loaded before either is stored; each
+  // lane still sums its quads in ascending order
+  for (int q0 = lane; q0 < nqe; q0 += 64) {
+    float4 wq[2], xq[2], yq[2], zq[2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (j >= nj) break;
-      const float w = ws[j];
-      const float nx = xs[j] + fmaf(s1, xs[j], fbx);
-      const float ny = ys[j] + fmaf(s1, ys[j], fby);
-      const float nz = zs[j] + fmaf(s1, zs[j], fbz);
-      const float ddx = nx - xs[j], ddy = ny - ys[j], ddz = nz - zs[j];
-      aE += w * (ddx * (2.f * xs[j] + ddx) + ddy * (2.f * ys[j] + ddy) + ddz * (2.f * zs[j] + ddz));
-      aPx += w * ddx;
-      aPy += w * ddy;
-      aPz += w * ddz;
-      mW += w;
-      mPx += w * nx;
-      mPy += w * ny;
-      mPz += w * nz;
-      mU2 += w * (nx * nx + ny * ny + nz * nz);
-      xs[j] = nx;
-      ys[j] = ny;
-      zs[j] = nz;
+    for (int h = 0; h < 2; ++h) {
+      const int q = q0 + 32 * h;
+      if (q < nqe) {
+        const long b = ebase + 4 * q;
+        wq[h] = ld4(A.e.w + b);
+        xq[h] = ld4(A.e.px + b);
+        yq[h] = ld4(A.e.py + b);
+        zq[h] = ld4(A.e.pz + b);
+      }
     }
-    if (nj == 4) {
-      *reinterpret_cast<float4*>(A.e.px + b) = x4;
-      *reinterpret_cast<float4*>(A.e.py + b) = y4;
-      *reinterpret_cast<float4*>(A.e.pz + b) = z4;
-    } else {
-      for (int j = 0; j < nj; ++j) {
-        A.e.px[b + j] = xs[j];
-        A.e.py[b + j] = ys[j];
-        A.e.pz[b + j] = zs[j];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = q0 + 32 * h;
+      if (q >= nqe) break;
+      const long b = ebase + 4 * q;
+      const float4 w4 = wq[h];
+      float4 x4 = xq[h], y4 = yq[h], z4 = zq[h];
+      float* xs = reinterpret_cast<float*>(&x4);
+      float* ys = reinterpret_cast<float*>(&y4);
+      float* zs = reinterpret_cast<float*>(&z4);
+      const float* ws = reinterpret_cast<const float*>(&w4);
+      const int nj = min(4, ne - 4 * q);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (j >= nj) break;
+        const float w = ws[j];
+        const float nx = xs[j] + fmaf(s1, xs[j], fbx);
+        const float ny = ys[j] + fmaf(s1, ys[j], fby);
+        const float nz = zs[j] + fmaf(s1, zs[j], fbz);
+        const float ddx = nx - xs[j], ddy = ny - ys[j], ddz = nz - zs[j];
+        aE += w * (ddx * (2.f * xs[j] + ddx) + ddy * (2.f * ys[j] + ddy) + ddz * (2.f * zs[j] + ddz));
+        aPx += w * ddx;
+        aPy += w * ddy;
+        aPz += w * ddz;
+        mW += w;
+        mPx += w * nx;
+        mPy += w * ny;
+        mPz += w * nz;
+        mU2 += w * (nx * nx + ny * ny + nz * nz);
+        xs[j] = nx;
+        ys[j] = ny;
+        zs[j] = nz;
+      }
+      if (nj == 4) {
+        *reinterpret_cast<float4*>(A.e.px + b) = x4;
+        *reinterpret_cast<float4*>(A.e.py + b) = y4;
+        *reinterpret_cast<float4*>(A.e.pz + b) = z4;
+      } else {
+        for (int j = 0; j < nj; ++j) {
+          A.e.px[b + j] = xs[j];
+          A.e.py[b + j] = ys[j];
+          A.e.pz[b + j] = zs[j];
+        }
       }
     }
   }
@@ -846,20 +865,26 @@ __device__ __forceinline__ void fb_prepare(FbCell& f) {
                          sqrtf((float)(f.qPx * f.qPx + f.qPy * f.qPy + f.qPz * f.qPz)) >=
                              2.384185791015625e-07f * prms);
   if (!f.need) return;
-  // Eqs. delta_def, dE_bulk, dE_th, var_new, s_def, b_def (mu = 1)
+  // Eqs. delta_def, dE_bulk, dE_th, var_new, s_def, b_def (mu = 1). Three
+  // FP64 divisions and one square root (FP64 runs at a small fraction of the
+  // FP32 rate): 1/W once, and S - 1 = t / (S + 1) with t = var_new / var - 1
+  // formed from 2 dE_th without cancellation.
   const double Wd = f.W;
-  const double dx = f.qPx / Wd, dy = f.qPy / Wd, dz = f.qPz / Wd;
+  const double iW = 1.0 / Wd;
+  const double dx = f.qPx * iW, dy = f.qPy * iW, dz = f.qPz * iW;
   const double dEb = (2.0 * (dx * f.Px + dy * f.Py + dz * f.Pz) + Wd * (dx * dx + dy * dy + dz * dz)) * 0.5;
-  const double dEth = f.qE / kMeC2 - dEb;
+  const double dEth = f.qE * (1.0 / kMeC2) - dEb;
   f.vnd = f.var;
   if (f.var > 0.f) {
-    f.vnd = fmax(0.0, (double)f.var + 2.0 * dEth);
-    const double S = sqrt(f.vnd / (double)f.var);
-    f.s1d = ((f.vnd - (double)f.var) / (double)f.var) / (S + 1.0);
+    const double var = f.var;
+    f.vnd = fmax(0.0, var + 2.0 * dEth);
+    const double t = (f.vnd > 0.0 ? 2.0 * dEth : -var) / var;
+    const double S = sqrt(1.0 + t);
+    f.s1d = t / (S + 1.0);
   }
-  f.bx = -f.s1d * f.Px / Wd + dx;
-  f.by = -f.s1d * f.Py / Wd + dy;
-  f.bz = -f.s1d * f.Pz / Wd + dz;
+  f.bx = -f.s1d * f.Px * iW + dx;
+  f.by = -f.s1d * f.Py * iW + dy;
+  f.bz = -f.s1d * f.Pz * iW + dz;
 }
 
 // Carry, moments, diagnostics, temperature and record once the remap (r;
