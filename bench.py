@@ -292,7 +292,8 @@ def run_batched(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (uniform thermal boxes, seeded)",
             "config": {"workload": w.name, "boxes": args.boxes, "cells": w.ncells,
                        "electrons_per_cell": w.n_el, "photons_per_cell": w.n_ph, "channels": "all, fwd+inv",
-                       "T_mode": "evolved", "launch": "CUDA graph of one step, replayed",
+                       "T_mode": "evolved",
+                       "launch": "CUDA graphs of 16 steps replayed, %d branch(es)" % pl.launch_shape()[2],
                        "autotuned": {"decide_chunk": chunk, "event_warps": warps, "trial_ms_per_step": tuned_ms,
                                      "seconds": tune_s},
                        "l2": "inputs larger than L2"},
@@ -301,7 +302,7 @@ def run_batched(args):
                          "kernel": "step (%s), graph replay" % " + ".join(kms),
                          "basis": "28 B per electron, 16 B per photon and axion per step",
                          "kernels_ms_per_step": {k: v / max(nrec, 1) for k, v in kms.items()}},
-            "gpu_launches": len(kms) * args.steps + 1, "clocks": clk}
+            "gpu_launches": len(kms) * pl.launch_shape()[2] * args.steps + 1, "clocks": clk}
     print(json.dumps(line))
     pl.close()
 
@@ -536,7 +537,9 @@ def main():
                            "photons_per_cell": w.n_ph, "axions_at_start": w.n_ax, "channels": "all, fwd+inv",
                            "T_mode": "evolved", "l2": "inputs larger than L2 (%.2f GB per step at the fused-pass minimum)"
                            % (kernel_bytes(tot, w.params.get("T_mode", 0))["step"] / args.steps / 1e9),
-                           "parallelism": "cells sharded per GPU" if world > 1 else "single GPU"},
+                           "parallelism": "cells sharded per GPU" if world > 1 else "single GPU",
+                           "launch": "CUDA graphs of 16 steps replayed, %d branches of cells on forked streams"
+                           % pl.launch_shape()[2]},
                 # the step's kernels as one pass of the hot path, against the
                 # fused-pass minimum of 28 B per electron, 16 B per photon and
                 # axion; the kernel with the largest device time is named
@@ -547,7 +550,7 @@ def main():
                              "algorithmic_bytes_per_launch": kernel_bytes(tot, w.params.get("T_mode", 0))["step"]
                              / args.steps,
                              "dominant_kernel": "axpic::" + dom, "kernels": per_kernel},
-                "gpu_launches": len(kms) * args.steps + 1, "clocks": clk,
+                "gpu_launches": len(kms) * pl.launch_shape()[2] * args.steps + 1, "clocks": clk,
                 "counts": {"particle_steps": particles, "events_primakoff": tot["events_p"],
                            "events_compton": tot["events_c"], "events_brems": tot["events_b"],
                            "events_inverse": tot["events_pinv"], "remapped_cells": tot["remaps"]}}

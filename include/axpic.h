@@ -131,7 +131,14 @@ typedef struct {
                                paper's method. */
   int32_t sr_table_nkt;     /* table nodes in ln(kappa/T) (0: 128) */
   int32_t sr_table_nne;     /* table nodes in log10 n_e (0: 64) */
-  int32_t reserved[3];
+  int32_t step_branches;    /* axpic_run_steps: the cells run as 1, 2, 4 or
+                               8 independent ranges on forked streams of the
+                               graph, each chaining 16 steps with its own step
+                               counter, so that one range's decisions overlap
+                               another's events (0: 8 up to 2^20 cells, else
+                               1; rate models 1 and 2 use 1). Results do not
+                               depend on it. Not part of the paper's method. */
+  int32_t reserved[2];
 } axpic_params;
 
 /* Number of doubles written by axpic_tally_spectrum into totals_out. */
@@ -285,16 +292,27 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc *desc, const axpic_param
                                 int32_t channel_mask, double *carry, void *stream);
 
 /* Runs nsteps full steps (as axpic_step with steps first_step,
- * first_step + 1, ...) by replaying a CUDA graph of one step: the decision,
- * event and feedback kernels, with the step index read from a device counter
- * that the feedback kernel advances. The graph is captured on first use for a
- * channel mask (on a private stream of the context, ordered after the
- * context's stream) and kept until the launch shape changes. Asynchronous;
- * results are identical to nsteps calls of axpic_step. AXPIC_E_INVALID for
+ * first_step + 1, ...) by replaying CUDA graphs of 16 steps and of one step
+ * (for the remainder): the decision, event and feedback kernels, with the
+ * step index read from device counters that the feedback kernels advance.
+ * Inside a graph the cells run as step_branches independent ranges on forked
+ * streams, each range with its own counter, joined at the graph's end. The
+ * graphs are captured on first use for a channel mask (on private streams of
+ * the context, ordered after the context's stream) and kept until the launch
+ * shape changes. Asynchronous; results are identical to nsteps calls of
+ * axpic_step. AXPIC_E_INVALID for
  * nsteps < 0, a step range outside [0, 2^32 - 1) or unknown channel bits.
  * Not part of the paper's method: batching of many small boxes in one
  * context (each cell carries its own plasma record) and launch by graph. */
 axpic_status axpic_run_steps(axpic_ctx *ctx, int64_t first_step, int32_t nsteps, int32_t channel_mask);
+
+/* The context's launch shape: cells per decision chunk, warps per event CTA
+ * and the branches a replayed step runs its cells as (each may be NULL).
+ * A replayed step launches 3 x branches kernels (decision, event, feedback
+ * per branch). AXPIC_E_INVALID for a NULL context. Not part of the paper's
+ * method. */
+axpic_status axpic_launch_shape(const axpic_ctx *ctx, int32_t *decide_chunk, int32_t *event_warps,
+                                int32_t *step_branches);
 
 /* Picks the launch shape (cells per decision chunk, 2/4/8, and warps per
  * event CTA, 2 or 4) by timing trial_steps steps of the context's own state

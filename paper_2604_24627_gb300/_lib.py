@@ -54,7 +54,7 @@ class Params(ctypes.Structure):
                 ("tally_enable", ctypes.c_int32), ("diag_enable", ctypes.c_int32),
                 ("threads_per_block", ctypes.c_int32), ("decide_chunk", ctypes.c_int32),
                 ("rate_model", ctypes.c_int32), ("sr_table_nkt", ctypes.c_int32), ("sr_table_nne", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("step_branches", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class AxpicError(RuntimeError):
@@ -103,6 +103,8 @@ EXPORTS = {
     "axpic_feedback": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "axpic_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]),
     "axpic_run_steps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]),
+    "axpic_launch_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "axpic_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32)]),
@@ -191,6 +193,13 @@ def axpic_step(ctx, step, mask):
 
 def axpic_run_steps(ctx, first_step, nsteps, mask):
     _check(ctx, lib().axpic_run_steps(ctx, first_step, nsteps, mask))
+
+
+def axpic_launch_shape(ctx):
+    """(decide_chunk, event warps per CTA, branches of a replayed step)."""
+    v = [ctypes.c_int32() for _ in range(3)]
+    _check(ctx, lib().axpic_launch_shape(ctx, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def axpic_autotune(ctx, step, trial_steps, mask):

@@ -322,7 +322,8 @@ __device__ __forceinline__ float tau_brems(const float* rec, float x, float am3,
 // Kernel parameters shared by the step kernels (passed by value).
 struct StepArgs {
   SpeciesPtrs e, g, a;
-  int ncells;
+  int ncells;             // cells of this launch: [cell0, cell0 + ncells)
+  int cell0;              // first cell of this launch (a branch of a replayed step)
   uint32_t cell_base;     // global index of cell 0 (low 32 bits)
   uint32_t step;
   uint32_t key0, key1;

@@ -790,10 +790,11 @@ __global__ void __launch_bounds__(kDecThreads, AXPIC_DEC_MIN_CTAS) decide_kernel
   const uint32_t step = step_of(A);
   const int nwarps = gridDim.x * kDecWarps;
   const int nchunks = (A.ncells + C - 1) / C;
+  const int cend = A.cell0 + A.ncells;
   int pa = 0, pg = 0;
   for (int ch = blockIdx.x * kDecWarps + wid; ch < nchunks; ch += nwarps) {
-    const int c0 = ch * C;
-    const int nc = min(C, A.ncells - c0);
+    const int c0 = A.cell0 + ch * C;
+    const int nc = min(C, cend - c0);
     if (kinds & DK_ELECTRON) electron_chunk<C>(A, step, c0, nc, lane);
     if (kinds & DK_PHOTON) pg = photon_chunk<C>(A, step, c0, nc, lane, L.g[wid], pg);
     if (kinds & DK_AXION) pa = axion_chunk<C>(A, step, c0, nc, lane, L.a[wid], pa);
@@ -970,8 +971,8 @@ __global__ void __launch_bounds__(kFeedbackThreads) feedback_kernel(StepArgs A) 
   __shared__ RemapOut outs[kFeedbackThreads];
   __shared__ int njobs;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = cell < A.ncells;
+  const int cell = A.cell0 + blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = cell < A.cell0 + A.ncells;
   if (threadIdx.x == 0) njobs = 0;
   FbCell f = {};
   if (valid) {
@@ -1709,8 +1710,8 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
   const int wid = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int cell = (blockIdx.x * nw + wid) * 32 + lane;
-  const bool valid = cell < A.ncells;
+  const int cell = A.cell0 + (blockIdx.x * nw + wid) * 32 + lane;
+  const bool valid = cell < A.cell0 + A.ncells;
   if (lane < kNumCounters) warp_cnt[wid][lane] = 0ull;
   __syncwarp();
   const Cnt cnt{warp_cnt[wid]};
@@ -1976,10 +1977,12 @@ static cudaError_t launch_feedback(const StepArgs& A, cudaStream_t st) {
 
 const char* step_kernel_names() { return "decide_kernel,event_kernel,feedback_kernel"; }
 
-__global__ void set_step_kernel(uint32_t* p, uint32_t v) { *p = v; }
+__global__ void set_step_kernel(uint32_t* p, uint32_t v, int n) {
+  for (int i = 0; i < n; ++i) p[i] = v;
+}
 
-cudaError_t launch_set_step(uint32_t* p, uint32_t v, cudaStream_t st) {
-  set_step_kernel<<<1, 1, 0, st>>>(p, v);
+cudaError_t launch_set_step(uint32_t* p, uint32_t v, int n, cudaStream_t st) {
+  set_step_kernel<<<1, 1, 0, st>>>(p, v, n);
   return cudaGetLastError();
 }
 

@@ -22,7 +22,7 @@ cudaError_t set_step_smem_limits(size_t bytes);
 // device holds at once.
 cudaError_t decide_resident_ctas(int chunk, int* out);
 constexpr int kDefaultDecChunk = AXPIC_DEC_CHUNK;
-// Writes v to the device step counter *p (one thread).
-cudaError_t launch_set_step(uint32_t* p, uint32_t v, cudaStream_t st);
+// Writes v to the n device step counters p[0, n) (one thread).
+cudaError_t launch_set_step(uint32_t* p, uint32_t v, int n, cudaStream_t st);
 
 }  // namespace axpic

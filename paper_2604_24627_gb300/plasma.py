@@ -115,6 +115,10 @@ class AxionPlasma:
         """nsteps full steps by replaying a CUDA graph of one step."""
         _lib.axpic_run_steps(self.ctx, first_step, nsteps, mask)
 
+    def launch_shape(self):
+        """(decide_chunk, event warps per CTA, branches of a replayed step)."""
+        return _lib.axpic_launch_shape(self.ctx)
+
     def autotune(self, step, trial_steps=3, mask=_lib.CH_ALL):
         """Times the launch shapes on this state (restored afterwards) and keeps
         the fastest; returns (ms per step, decide_chunk, event warps)."""

@@ -64,7 +64,7 @@ int main(void) {
   P(axpic_plasma_desc, electrons) P(axpic_plasma_desc, axions) P(axpic_plasma_desc, cell_volume_cm3)
   P(axpic_params, kappa_fixed_keV) P(axpic_params, seed) P(axpic_params, tally_Emax_keV)
   P(axpic_params, threads_per_block) P(axpic_params, decide_chunk) P(axpic_params, T_mode)
-  P(axpic_params, rate_model) P(axpic_params, sr_table_nne)
+  P(axpic_params, rate_model) P(axpic_params, sr_table_nne) P(axpic_params, step_branches)
   P(axpic_params, brems_gamma_shape)
   return 0;
 }
