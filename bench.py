@@ -293,7 +293,7 @@ def run_batched(args):
             "config": {"workload": w.name, "boxes": args.boxes, "cells": w.ncells,
                        "electrons_per_cell": w.n_el, "photons_per_cell": w.n_ph, "channels": "all, fwd+inv",
                        "T_mode": "evolved",
-                       "launch": "CUDA graphs of 16 steps replayed, %d branch(es)" % pl.launch_shape()[2],
+                       "launch": "CUDA graphs of 32 steps replayed, %d branch(es)" % pl.launch_shape()[2],
                        "autotuned": {"decide_chunk": chunk, "event_warps": warps, "trial_ms_per_step": tuned_ms,
                                      "seconds": tune_s},
                        "l2": "inputs larger than L2"},
@@ -538,7 +538,7 @@ def main():
                            "T_mode": "evolved", "l2": "inputs larger than L2 (%.2f GB per step at the fused-pass minimum)"
                            % (kernel_bytes(tot, w.params.get("T_mode", 0))["step"] / args.steps / 1e9),
                            "parallelism": "cells sharded per GPU" if world > 1 else "single GPU",
-                           "launch": "CUDA graphs of 16 steps replayed, %d branches of cells on forked streams"
+                           "launch": "CUDA graphs of 32 steps replayed, %d branches of cells on forked streams"
                            % pl.launch_shape()[2]},
                 # the step's kernels as one pass of the hot path, against the
                 # fused-pass minimum of 28 B per electron, 16 B per photon and

@@ -133,7 +133,7 @@ typedef struct {
   int32_t sr_table_nne;     /* table nodes in log10 n_e (0: 64) */
   int32_t step_branches;    /* axpic_run_steps: the cells run as 1, 2, 4 or
                                8 independent ranges on forked streams of the
-                               graph, each chaining 16 steps with its own step
+                               graph, each chaining 32 steps with its own step
                                counter, so that one range's decisions overlap
                                another's events (0: 8 up to 2^20 cells, else
                                1; rate models 1 and 2 use 1). Results do not
@@ -292,7 +292,7 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc *desc, const axpic_param
                                 int32_t channel_mask, double *carry, void *stream);
 
 /* Runs nsteps full steps (as axpic_step with steps first_step,
- * first_step + 1, ...) by replaying CUDA graphs of 16 steps and of one step
+ * first_step + 1, ...) by replaying CUDA graphs of 32 steps and of one step
  * (for the remainder): the decision, event and feedback kernels, with the
  * step index read from device counters that the feedback kernels advance.
  * Inside a graph the cells run as step_branches independent ranges on forked

@@ -33,13 +33,17 @@ constexpr int kDefaultWarps = 4;
 // branch's events and feedback. Each branch chains kGraphSteps steps with
 // its own device step counter and the branches join only at the graph's end,
 // so they drift apart within it. Default: 8 branches up to kBranchCells
-// cells (c2, 65,536 cells: 0.190 ms per step against 0.236 with one), one
-// above (1.57 M cells fill the GPU alone: branching measured 1 % slower).
+// cells (c2, 65,536 cells, graphs of 32 steps: 0.1875 ms per step against
+// 0.236 with one branch; 16 branches 0.1925), one above (1.57 M cells fill
+// the GPU alone: branching measured 1 % slower).
 #ifndef AXPIC_GRAPH_STEPS
-#define AXPIC_GRAPH_STEPS 16
+#define AXPIC_GRAPH_STEPS 32
 #endif
-constexpr int kMaxBranches = 8;
-constexpr int kDefaultBranches = 8;
+#ifndef AXPIC_MAX_BRANCHES
+#define AXPIC_MAX_BRANCHES 8
+#endif
+constexpr int kMaxBranches = AXPIC_MAX_BRANCHES;
+constexpr int kDefaultBranches = AXPIC_MAX_BRANCHES;
 constexpr int kBranchCells = 1 << 20;
 constexpr int kGraphSteps = AXPIC_GRAPH_STEPS;
 constexpr int kInfoChunk = 4096;
@@ -396,9 +400,8 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
   while (ctx->max_warps > 1 && per_warp * ctx->max_warps > smem_limit) --ctx->max_warps;
   if (p.decide_chunk != 0 && p.decide_chunk != 2 && p.decide_chunk != 4 && p.decide_chunk != 8)
     return bad("decide_chunk must be 0, 2, 4 or 8");
-  if (p.step_branches != 0 && p.step_branches != 1 && p.step_branches != 2 && p.step_branches != 4 &&
-      p.step_branches != 8)
-    return bad("step_branches must be 0, 1, 2, 4 or 8");
+  if (p.step_branches < 0 || p.step_branches > kMaxBranches || (p.step_branches & (p.step_branches - 1)))
+    return bad("step_branches must be 0 or a power of two up to 8");
   if (p.rate_model < 0 || p.rate_model > 2) return bad("rate_model must be 0, 1 or 2");
   if (p.rate_model) {
     if (d.nspecies != 1 || (d.Z[0] != 1.0 && d.Z[0] != 2.0) || p.kappa_mode != 0 || p.prim_targets != 0)
@@ -743,7 +746,7 @@ static cudaError_t capture_steps(axpic_ctx* ctx, StepArgs A, int nsteps, cudaStr
 // The graph of nsteps steps for channel_mask, captured on first use.
 static axpic_status step_graph(axpic_ctx* ctx, int64_t first_step, int nsteps, int32_t channel_mask,
                                cudaGraphExec_t* out) {
-  const int key = channel_mask * 64 + nsteps;
+  const int key = channel_mask * 1024 + nsteps;
   auto it = ctx->graphs.find(key);
   if (it == ctx->graphs.end()) {
     StepArgs A = make_args(ctx, first_step, channel_mask);

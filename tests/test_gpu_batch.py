@@ -81,14 +81,14 @@ def test_run_steps_equals_step_calls():
 def test_branched_replay_equals_step_calls(branches):
     """Replayed steps whose cells run as several branches (ranges of whole
     event CTAs on forked streams, each with its own step counter, joined
-    every 16 steps) give what plain step calls give: 19 steps take one graph
-    of 16 steps and three of one step."""
+    every 32 steps) give what plain step calls give: 35 steps take one graph
+    of 32 steps and three of one step."""
     prm = base_params(step_branches=branches)
-    caps = (64, 768, 1024)  # no product dropped in 19 steps at these rates
+    caps = (64, 1024, 2048)  # no product dropped in 35 steps at these rates
     a, b = make(600, prm, caps=caps), make(600, prm, caps=caps)
-    for s in range(19):
+    for s in range(35):
         a.step(s, _lib.CH_ALL)
-    b.run_steps(0, 19, _lib.CH_ALL)
+    b.run_steps(0, 35, _lib.CH_ALL)
     torch.cuda.synchronize()
     assert_same(state(a), state(b), "%d branches" % branches)
     assert a.tally()[1]["dropped"] == 0
