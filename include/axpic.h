@@ -353,9 +353,18 @@ const char *axpic_step_kernel_names(const axpic_ctx *ctx);
  * on the CUDA cores). Not part of the paper's method: a learned stand-in for
  * the per-channel spectral emissivity and inverse CDF (see
  * axpic_surrogate_targets). Inputs are the normalised features
- * (ln x, ln(kappa/T), log10 n_e, Z) of axpic_surrogate_features; outputs are
- * normalised (z = (y - mu) / sigma). Calls are ordered on the stream given at
- * creation; those that return host data synchronise it.
+ * (ln x, ln(kappa/T), log10 n_e, Z) of axpic_surrogate_features. The
+ * network's output z is a normalised residual: the model's output o is
+ *   y_o = shape_o(x, kappa/T) + mu_o + sum_i S_oi f_i + sigma_o z_o
+ * with f the features, S an FP32 linear map (axpic_mlp_set_skip) and shape_o
+ * fixed: for the ln-emissivity outputs (o = 0, 32, 64) the channel's x-shape,
+ *   Primakoff      3 ln x - ln(e^x - 1) + ln min(s/2, ln(1 + s)),
+ *                  s = 4 x^2 / (kappa/T)^2 (an upper bound of the screening
+ *                  function F),
+ *   Compton-like   5 ln x - ln(e^x - 1),
+ *   bremsstrahlung a ln x - x (a = brems_gamma_shape);
+ * zero for the quantiles. Calls are ordered on the stream given at creation;
+ * those that return host data synchronise it.
  * ------------------------------------------------------------------------- */
 typedef struct axpic_mlp axpic_mlp;
 #define AXPIC_MLP_PARAMS 10720 /* W1[4][64], b1[64], W2[64][64], b2[64], W3[64][96], b3[96] */
@@ -380,10 +389,15 @@ axpic_status axpic_mlp_train_step(axpic_mlp *m, const float *X, const float *Zt,
 axpic_status axpic_mlp_destroy(axpic_mlp *m);
 const char *axpic_mlp_last_error(const axpic_mlp *m);
 
-/* Output normalisation of the network (y = mu + sigma z), 96 floats each;
- * set by axpic_surrogate_fit. */
+/* Output normalisation of the network (mu, sigma of the model above), 96
+ * floats each; set by axpic_surrogate_fit. sigma must be > 0. */
 axpic_status axpic_mlp_set_norm(axpic_mlp *m, const float *mu, const float *sigma);
 axpic_status axpic_mlp_get_norm(axpic_mlp *m, float *mu, float *sigma);
+/* The linear map S of the model above, 96 x 4 floats, S[o][i] at o * 4 + i
+ * (zero on creation; fitted by least squares in axpic_surrogate_fit).
+ * AXPIC_E_INVALID for a non-finite entry. */
+axpic_status axpic_mlp_set_skip(axpic_mlp *m, const float *skip);
+axpic_status axpic_mlp_get_skip(axpic_mlp *m, float *skip);
 
 /* The function the surrogate stands in for, in binary64 on the host: for
  * each of n rows (x = omega/T, kappa/T, n_e [cm^-3], Z in {1, 2}) of `in`,

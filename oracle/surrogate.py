@@ -22,8 +22,10 @@ c in (Primakoff, Compton-like, bremsstrahlung):
   and x(1) = 20 are fixed and not outputs).
 
 The network (4 -> 64 -> 64 -> 96, tanh hidden layers) sees normalised features
-(ln x, ln(kappa/T), log10 n_e, Z) and predicts normalised outputs
-z = (y - mu) / sigma; mu and sigma are per-output constants.
+f = (ln x, ln(kappa/T), log10 n_e, Z) and predicts a normalised residual z;
+the model's output is y = shape(x, kappa/T) + mu + S f + sigma z with
+per-output constants mu, sigma, an FP32 linear map S (96 x 4) and fixed
+x-shapes on the ln-emissivity outputs (model_output below).
 
 Pinned by: the Compton-like and bremsstrahlung quantiles against the
 closed-form inverse CDFs of the spectra module (Bose integrals, scipy's
@@ -77,6 +79,31 @@ def features(x, kT, ne, Z):
     f2 = (np.log10(ne) - 24.5) / 1.5
     f3 = Z - 1.5
     return np.stack(np.broadcast_arrays(f0, f1, f2, f3), axis=-1)
+
+
+def shape(X, brems_shape=1.70):
+    """The fixed part of the model's 96 outputs at feature rows X: on the
+    ln-emissivity outputs the channel's x-shape (Primakoff: Planck factor
+    x^3/(e^x - 1) times min(s/2, ln(1 + s)), s = 4 x^2/(kappa/T)^2, which
+    bounds the screening function F from above; Compton-like x^5/(e^x - 1);
+    bremsstrahlung x^a e^-x), in ln; zero on the quantiles. x and kappa/T are
+    recovered from the features."""
+    X = np.atleast_2d(np.asarray(X, dtype=np.float64))
+    x = X_LO * (X_HI / X_LO) ** (0.5 * (X[:, 0] + 1.0))
+    kT = KT_LO * (KT_HI / KT_LO) ** (0.5 * (X[:, 1] + 1.0))
+    s = 4.0 * x ** 2 / kT ** 2
+    out = np.zeros((len(X), N_OUT))
+    out[:, 0] = 3.0 * np.log(x) - np.log(np.expm1(x)) + np.log(np.minimum(0.5 * s, np.log1p(s)))
+    out[:, 32] = 5.0 * np.log(x) - np.log(np.expm1(x))
+    out[:, 64] = brems_shape * np.log(x) - x
+    return out
+
+
+def model_output(z, X, mu, sigma, skip, brems_shape=1.70):
+    """y = shape + mu + S f + sigma z for normalised outputs z at features X."""
+    X = np.atleast_2d(np.asarray(X, dtype=np.float64))
+    return (shape(X, brems_shape) + np.asarray(mu, np.float64) + X @ np.asarray(skip, np.float64).T
+            + np.asarray(sigma, np.float64) * z)
 
 
 # ------------------------------------------------------------------ targets

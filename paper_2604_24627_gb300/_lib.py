@@ -83,6 +83,8 @@ EXPORTS = {
                                           ctypes.POINTER(ctypes.c_float)]),
     "axpic_mlp_get_norm": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
                                           ctypes.POINTER(ctypes.c_float)]),
+    "axpic_mlp_set_skip": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    "axpic_mlp_get_skip": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
     "axpic_surrogate_targets": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double,
                                                ctypes.POINTER(ctypes.c_double)]),
     "axpic_surrogate_features": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
@@ -372,6 +374,20 @@ def axpic_mlp_get_norm(h):
     s = np.empty(96, dtype=np.float32)
     _mlp_check(h, lib().axpic_mlp_get_norm(h, _fptr(m), _fptr(s)))
     return m, s
+
+
+def axpic_mlp_set_skip(h, skip):
+    """The model's FP32 linear map S[96][4]."""
+    import numpy as np
+    a = np.ascontiguousarray(skip, dtype=np.float32).reshape(96 * 4)
+    _mlp_check(h, lib().axpic_mlp_set_skip(h, _fptr(a)))
+
+
+def axpic_mlp_get_skip(h):
+    import numpy as np
+    a = np.empty(96 * 4, dtype=np.float32)
+    _mlp_check(h, lib().axpic_mlp_get_skip(h, _fptr(a)))
+    return a.reshape(96, 4)
 
 
 def axpic_surrogate_fit(h, ncells, x_per_cell, steps, batch, lr, seed=0, brems_shape=1.70):

@@ -90,6 +90,7 @@ struct axpic_ctx {
   float* sur_P = nullptr;   // network parameters, output affine and trust map
   float* sur_mu = nullptr;
   float* sur_sigma = nullptr;
+  float* sur_skip = nullptr;
   uint8_t* sur_trust = nullptr;
   void* sur_W16 = nullptr;  // layers 2 and 3 laid out for the tensor cores
   int sr_nkt = 0, sr_nne = 0, tnT = 0, tnne = 0, sur_set = 0, sur_any_trusted = 0;
@@ -265,6 +266,8 @@ static SrArgs make_sr_args(axpic_ctx* ctx) {
   a.P = ctx->sur_P;
   a.mu = ctx->sur_mu;
   a.sigma = ctx->sur_sigma;
+  a.skip = ctx->sur_skip;
+  a.brems_a = (float)ctx->prm.brems_gamma_shape;
   // no trusted node: the network is never evaluated (every cell keeps the table)
   a.trust = ctx->sur_set && ctx->sur_any_trusted ? ctx->sur_trust : nullptr;
   a.W16 = ctx->sur_W16;
@@ -308,7 +311,7 @@ static void free_ctx(axpic_ctx* ctx) {
   void* bufs[] = {ctx->rec,    ctx->mom,   ctx->xbuf,     ctx->res, ctx->diag,    ctx->photon_start,
                   ctx->tables, ctx->tally, ctx->counters, ctx->err, ctx->scratch, ctx->bits,
                   ctx->recA,   ctx->recG,  ctx->recE,     ctx->step_dev, ctx->sr, ctx->srtab,
-                  ctx->sur_P,  ctx->sur_mu, ctx->sur_sigma, ctx->sur_trust, ctx->sur_W16};
+                  ctx->sur_P,  ctx->sur_mu, ctx->sur_sigma, ctx->sur_trust, ctx->sur_W16, ctx->sur_skip};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete ctx;
@@ -449,6 +452,7 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
     ALLOC(ctx->sur_P, sizeof(float) * AXPIC_MLP_PARAMS);
     ALLOC(ctx->sur_mu, sizeof(float) * 96);
     ALLOC(ctx->sur_sigma, sizeof(float) * 96);
+    ALLOC(ctx->sur_skip, sizeof(float) * 96 * 4);
     ALLOC(ctx->sur_W16, kSrW16Bytes);
   }
   ALLOC(ctx->err, sizeof(int));
@@ -928,9 +932,10 @@ axpic_status axpic_set_surrogate(axpic_ctx* ctx, axpic_mlp* m, const float* err_
   if (!ctx || !m || !err_map) return AXPIC_E_INVALID;
   if (ctx->prm.rate_model != 2) return fail(ctx, AXPIC_E_INVALID, "axpic_set_surrogate: rate_model is not 2");
   if (nT < 2 || nne < 2 || nT > 4096 || nne > 4096) return fail(ctx, AXPIC_E_INVALID, "axpic_set_surrogate: grid");
-  std::vector<float> P(AXPIC_MLP_PARAMS), mu(96), sigma(96);
+  std::vector<float> P(AXPIC_MLP_PARAMS), mu(96), sigma(96), skip(96 * 4);
   axpic_status s;
-  if ((s = axpic_mlp_get_params(m, P.data())) != AXPIC_OK || (s = axpic_mlp_get_norm(m, mu.data(), sigma.data())))
+  if ((s = axpic_mlp_get_params(m, P.data())) != AXPIC_OK || (s = axpic_mlp_get_norm(m, mu.data(), sigma.data())) ||
+      (s = axpic_mlp_get_skip(m, skip.data())))
     return fail(ctx, s, "axpic_set_surrogate: reading the network");
   std::vector<uint8_t> trust((size_t)2 * nT * nne);
   int any = 0;
@@ -946,6 +951,7 @@ axpic_status axpic_set_surrogate(axpic_ctx* ctx, axpic_mlp* m, const float* err_
   CK(cudaMemcpyAsync(ctx->sur_P, P.data(), sizeof(float) * P.size(), cudaMemcpyHostToDevice, st), "params");
   CK(cudaMemcpyAsync(ctx->sur_mu, mu.data(), sizeof(float) * 96, cudaMemcpyHostToDevice, st), "norm");
   CK(cudaMemcpyAsync(ctx->sur_sigma, sigma.data(), sizeof(float) * 96, cudaMemcpyHostToDevice, st), "norm");
+  CK(cudaMemcpyAsync(ctx->sur_skip, skip.data(), sizeof(float) * 96 * 4, cudaMemcpyHostToDevice, st), "skip");
   CK(cudaMemcpyAsync(ctx->sur_trust, trust.data(), trust.size(), cudaMemcpyHostToDevice, st), "trust map");
   CK(launch_sr_weights(ctx->sur_P, ctx->sur_W16, st), "weights");
   ctx->tnT = nT;

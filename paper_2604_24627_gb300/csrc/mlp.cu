@@ -7,6 +7,8 @@
 // an mbarrier, and the CTA reads the tile back with tcgen05.ld.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -361,7 +363,18 @@ struct axpic_mlp {
   axpic::Mlp m;
   std::string last_error;
   std::vector<float> mu = std::vector<float>(96, 0.f), sigma = std::vector<float>(96, 1.f);
+  std::vector<float> skip = std::vector<float>(96 * 4, 0.f);  // S[o][i]
 };
+
+// The output model y = shape(x, kappa/T) + mu + S f + sigma z for the
+// network's normalised output z (double).
+static double model_output(const axpic_mlp* h, int o, const float* f, double z, double brems_shape) {
+  double x, kT;
+  axpic::sur_feature_xkt(f, &x, &kT);
+  double y = axpic::sur_shape(o, x, kT, brems_shape) + (double)h->mu[o] + (double)h->sigma[o] * z;
+  for (int i = 0; i < 4; ++i) y += (double)h->skip[o * 4 + i] * (double)f[i];
+  return y;
+}
 
 extern "C" {
 
@@ -468,6 +481,21 @@ axpic_status axpic_mlp_set_norm(axpic_mlp* h, const float* mu, const float* sigm
   return AXPIC_OK;
 }
 
+axpic_status axpic_mlp_set_skip(axpic_mlp* h, const float* skip) {
+  if (!h || !skip) return AXPIC_E_INVALID;
+  for (int k = 0; k < 96 * 4; ++k) {
+    if (!std::isfinite(skip[k])) return AXPIC_E_INVALID;
+    h->skip[k] = skip[k];
+  }
+  return AXPIC_OK;
+}
+
+axpic_status axpic_mlp_get_skip(axpic_mlp* h, float* skip) {
+  if (!h || !skip) return AXPIC_E_INVALID;
+  for (int k = 0; k < 96 * 4; ++k) skip[k] = h->skip[k];
+  return AXPIC_OK;
+}
+
 axpic_status axpic_mlp_get_norm(axpic_mlp* h, float* mu, float* sigma) {
   if (!h || !mu || !sigma) return AXPIC_E_INVALID;
   for (int k = 0; k < 96; ++k) {
@@ -504,20 +532,59 @@ axpic_status axpic_surrogate_fit(axpic_mlp* h, int32_t ncells, int32_t x_per_cel
   std::vector<double> Y;
   axpic::sur_training_set(ncells, x_per_cell, seed, brems_shape, X, Y);
   const size_t n = (size_t)ncells * x_per_cell;
-  // per-output normalisation and the normalised targets
-  std::vector<double> mu(96, 0.0), var(96, 0.0);
-  for (size_t r = 0; r < n; ++r)
-    for (int k = 0; k < 96; ++k) mu[k] += Y[r * 96 + k];
-  for (int k = 0; k < 96; ++k) mu[k] /= (double)n;
-  for (size_t r = 0; r < n; ++r)
-    for (int k = 0; k < 96; ++k) var[k] += (Y[r * 96 + k] - mu[k]) * (Y[r * 96 + k] - mu[k]);
-  for (int k = 0; k < 96; ++k) {
-    h->mu[k] = (float)mu[k];
-    h->sigma[k] = (float)std::max(std::sqrt(var[k] / (double)n), 1e-6);
+  // The output model y = shape(x, kappa/T) + mu + S f + sigma z: the network
+  // learns only what the fixed x-shapes and an FP32 linear map of the
+  // features leave over. mu and S by least squares over the rows (5 x 5
+  // normal equations in FP64, 96 right-hand sides); sigma is the residual's
+  // spread, divided by kRateWeight on the ln-emissivity outputs so that their
+  // errors weigh more in the loss.
+#ifndef AXPIC_RATE_WEIGHT
+#define AXPIC_RATE_WEIGHT 4.0
+#endif
+  constexpr double kRateWeight = AXPIC_RATE_WEIGHT;
+  for (size_t r = 0; r < n; ++r) {
+    double x, kT;
+    axpic::sur_feature_xkt(&X[r * 4], &x, &kT);
+    for (int k = 0; k < 96; ++k) Y[r * 96 + k] -= axpic::sur_shape(k, x, kT, brems_shape);
   }
+  double M[5][5 + 96] = {};
+  for (size_t r = 0; r < n; ++r) {
+    const double d[5] = {1.0, X[r * 4], X[r * 4 + 1], X[r * 4 + 2], X[r * 4 + 3]};
+    for (int i = 0; i < 5; ++i) {
+      for (int j = 0; j < 5; ++j) M[i][j] += d[i] * d[j];
+      for (int k = 0; k < 96; ++k) M[i][5 + k] += d[i] * Y[r * 96 + k];
+    }
+  }
+  for (int c = 0; c < 5; ++c) {  // Gauss-Jordan with partial pivoting
+    int p = c;
+    for (int i = c + 1; i < 5; ++i)
+      if (std::fabs(M[i][c]) > std::fabs(M[p][c])) p = i;
+    if (!(std::fabs(M[p][c]) > 0.0)) return AXPIC_E_INVALID;  // degenerate feature draw
+    for (int j = 0; j < 5 + 96; ++j) std::swap(M[c][j], M[p][j]);
+    for (int i = 0; i < 5; ++i) {
+      if (i == c) continue;
+      const double g = M[i][c] / M[c][c];
+      for (int j = c; j < 5 + 96; ++j) M[i][j] -= g * M[c][j];
+    }
+  }
+  for (int k = 0; k < 96; ++k) {
+    h->mu[k] = (float)(M[0][5 + k] / M[0][0]);
+    for (int i = 0; i < 4; ++i) h->skip[k * 4 + i] = (float)(M[i + 1][5 + k] / M[i + 1][i + 1]);
+  }
+  // residuals with the binary32 coefficients the model keeps
+  std::vector<double> var(96, 0.0);
+  for (size_t r = 0; r < n; ++r)
+    for (int k = 0; k < 96; ++k) {
+      double lin = h->mu[k];
+      for (int i = 0; i < 4; ++i) lin += (double)h->skip[k * 4 + i] * (double)X[r * 4 + i];
+      Y[r * 96 + k] -= lin;
+      var[k] += Y[r * 96 + k] * Y[r * 96 + k];
+    }
+  for (int k = 0; k < 96; ++k)
+    h->sigma[k] = (float)(std::max(std::sqrt(var[k] / (double)n), 1e-6) / (k % 32 == 0 ? kRateWeight : 1.0));
   std::vector<float> Zt(n * 96);
   for (size_t r = 0; r < n; ++r)
-    for (int k = 0; k < 96; ++k) Zt[r * 96 + k] = (float)((Y[r * 96 + k] - h->mu[k]) / h->sigma[k]);
+    for (int k = 0; k < 96; ++k) Zt[r * 96 + k] = (float)(Y[r * 96 + k] / h->sigma[k]);
   std::vector<float> P;
   glorot(seed ^ 0xA5A5A5A5u, P);
   axpic_status s = axpic_mlp_set_params(h, P.data());
@@ -593,7 +660,7 @@ axpic_status axpic_surrogate_validate(axpic_mlp* h, int32_t nT, int32_t nne, dou
     for (int k = 0; k < nx; ++k) {
       const size_t r = (size_t)node * nx + k;
       for (int o = 0; o < 96; ++o) {
-        const double y = h->mu[o] + h->sigma[o] * (double)Z[r * 96 + o];
+        const double y = model_output(h, o, &X[r * 4], (double)Z[r * 96 + o], brems_shape);
         const double d = std::fabs(y - Y[r * 96 + o]);
         if (o % 32 == 0) eL = std::max(eL, d);
         else eQ = std::max(eQ, d / Y[r * 96 + o]);

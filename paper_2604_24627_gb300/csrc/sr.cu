@@ -112,6 +112,18 @@ __device__ __forceinline__ bool sr_trusted(const SrArgs& a, float T, float ne, f
   return t[0] && t[1] && t[a.tnT] && t[a.tnT + 1];
 }
 
+// The fixed x-shape of channel ch's ln-emissivity output (Primakoff: the
+// Planck factor and min(s/2, ln(1 + s)), an upper bound of the screening
+// function; Compton-like: x^5 / (e^x - 1); bremsstrahlung: x^a e^-x).
+__device__ __forceinline__ float sr_shape(int ch, float x, float kT, float a) {
+  if (ch == 0) {
+    const float s = 4.0f * x * x / (kT * kT);
+    return 3.0f * logf(x) - logf(expm1f(x)) + logf(fminf(0.5f * s, log1pf(s)));
+  }
+  if (ch == 1) return 5.0f * logf(x) - logf(expm1f(x));
+  return a * logf(x) - x;
+}
+
 // Layers 2 and 3 as B^T (N x K = 64) bfloat16 in the core-matrix layout, laid
 // out once per network: W2^T (64 x 64) then W3^T (96 x 64).
 __global__ void sr_weights_kernel(const float* __restrict__ P, __nv_bfloat16* __restrict__ out) {
@@ -162,8 +174,8 @@ __global__ void __launch_bounds__(kSrMlpThreads) sr_mlp_kernel(SrArgs a) {
     for (int i = tid; i < (64 * 64 + 96 * 64) / 8; i += kSrMlpThreads) dst[i] = src[i];
   }
   // features of row (cell, k) and layer 1 on the CUDA cores
+  float f[4];
   {
-    float f[4];
     f[0] = 2.0f * (k - 1) / 29.0f - 1.0f;  // ln x_k on the feature scale (x_1 -> -1, x_30 -> 1)
     f[1] = (__logf(kT) - kSrLnKt0) / kSrLnKtSpan * 2.0f - 1.0f;
     f[2] = (log10f(ne) - 24.5f) / 1.5f;
@@ -232,9 +244,11 @@ __global__ void __launch_bounds__(kSrMlpThreads) sr_mlp_kernel(SrArgs a) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int o = c0 + j;
-            const float y = a.mu[o] + a.sigma[o] * (v[j] + a.P[kOffB3 + o]);
+            float y = a.mu[o] + a.sigma[o] * (v[j] + a.P[kOffB3 + o]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) y = fmaf(a.skip[o * 4 + i], f[i], y);
             const int ch = o >> 5, slot = o & 31;
-            if (slot == 0) out[ch * 32 + k] = y + xk;
+            if (slot == 0) out[ch * 32 + k] = y + sr_shape(ch, xk, kT, a.brems_a) + xk;
             else if (k == 0) out[96 + ch * 31 + slot - 1] = y;
           }
         }

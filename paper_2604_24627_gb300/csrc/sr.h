@@ -42,6 +42,8 @@ struct SrArgs {
   const float* P;
   const float* mu;
   const float* sigma;
+  const float* skip;     // S[96][4]: y = shape(x, kappa/T) + mu + S f + sigma z
+  float brems_a;         // the bremsstrahlung shape's exponent a
   const uint8_t* trust;  // [2][tnne][tnT], 1 = trusted node
   const void* W16;       // W2^T, W3^T in bfloat16, core-matrix layout (launch_sr_weights)
   int tnT, tnne;

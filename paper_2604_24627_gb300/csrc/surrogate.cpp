@@ -158,6 +158,21 @@ void sur_features(double x, double kT, double ne, double Z, float* f) {
   f[3] = (float)(Z - 1.5);
 }
 
+void sur_feature_xkt(const float* f, double* x, double* kT) {
+  *x = kSurXLo * std::pow(kSurXHi / kSurXLo, 0.5 * ((double)f[0] + 1.0));
+  *kT = kSurKtLo * std::pow(kSurKtHi / kSurKtLo, 0.5 * ((double)f[1] + 1.0));
+}
+
+double sur_shape(int o, double x, double kT, double a) {
+  if (o == 0) {
+    const double s = 4.0 * x * x / (kT * kT);
+    return 3.0 * std::log(x) - std::log(std::expm1(x)) + std::log(std::min(0.5 * s, std::log1p(s)));
+  }
+  if (o == 32) return 5.0 * std::log(x) - std::log(std::expm1(x));
+  if (o == 64) return a * std::log(x) - x;
+  return 0.0;
+}
+
 // splitmix64: a seeded stream for the training-set draws
 static uint64_t mix(uint64_t& s) {
   uint64_t z = (s += 0x9E3779B97F4A7C15ull);

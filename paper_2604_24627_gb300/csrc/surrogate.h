@@ -25,6 +25,16 @@ void sur_quantiles(int ch, const SurCell& c, double* out31);
 void sur_knots(const SurCell& c, double* knots93);
 void sur_targets(double x, const SurCell& c, const double* knots93, double* out96);
 void sur_features(double x, double kT, double ne, double Z, float* f4);
+// x and kappa/T back from the features (inverse of the maps of sur_features)
+void sur_feature_xkt(const float* f4, double* x, double* kT);
+// The fixed part of output o of the network's model: for the ln-emissivity
+// outputs (o = 0, 32, 64) the channel's x-shape, zero for the quantiles:
+//   Primakoff      3 ln x - ln(e^x - 1) + ln min(s/2, ln(1 + s)), s = 4 x^2 / (kappa/T)^2
+//   Compton-like   5 ln x - ln(e^x - 1)
+//   bremsstrahlung a ln x - x
+// (the Planck / Boltzmann factors and the small- and large-s limits of the
+// screening function F, an upper bound of F).
+double sur_shape(int o, double x, double kT, double a);
 // ncells random cells of the domain (T uniform, n_e log-uniform, Z in {1, 2})
 // with xpc log-uniform x each: features X (rows x 4) and targets Y (rows x 96)
 void sur_training_set(int ncells, int xpc, uint64_t seed, double brems_shape, std::vector<float>& X,

@@ -94,6 +94,48 @@ def test_targets_layout():
     np.testing.assert_allclose(y[33:96][np.r_[0:31, 32:63]], y2[33:96][np.r_[0:31, 32:63]], rtol=1e-12)
 
 
+def _residual(ch, x, T, ne, Z):
+    """ln-emissivity of a channel minus the model's fixed x-shape."""
+    kT = S.kappa_over_T(T, ne, Z)
+    X = S.features(x, kT, ne, Z)
+    o = {"primakoff": 0, "compton": 32, "brems": 64}[ch]
+    return np.log(S.emissivity(ch, x, T, ne, Z)) - S.shape(X)[:, o], X
+
+
+def test_shapes_leave_cell_constants():
+    """The Compton-like and bremsstrahlung x-shapes are the spectra's exact
+    x-dependence: what they leave is constant in x, and for Compton-like it
+    is linear in the features (ln Q_C = ln n_e + 6 ln T + const, ln T linear
+    in ln n_e and ln(kappa/T)), so the FP32 linear map carries it exactly."""
+    x = np.geomspace(S.X_LO, S.X_HI, 40)
+    rows, Yc = [], []
+    for T, ne, Z in ((0.7, 2e23, 1), (3.0, 6e25, 1), (9.0, 1e24, 2), (1.5, 5e25, 2), (5.0, 3e23, 1),
+                     (2.2, 8e24, 2), (6.5, 2e25, 1)):
+        for ch in ("compton", "brems"):
+            r, X = _residual(ch, x, T, ne, Z)
+            assert np.ptp(r) < 1e-12 * max(1.0, np.abs(r).max()), (ch, T, ne, Z, np.ptp(r))
+        r, X = _residual("compton", x[:1], T, ne, Z)
+        rows.append(np.r_[1.0, X[0]])
+        Yc.append(r[0])
+    c, *_ = np.linalg.lstsq(np.array(rows), np.array(Yc), rcond=None)
+    assert np.abs(np.array(rows) @ c - np.array(Yc)).max() < 1e-9
+
+
+@pytest.mark.parametrize("T,ne,Z", [(0.5, 1e26, 2), (3.0, 6e25, 1), (10.0, 1e23, 1)])
+def test_primakoff_shape_bounds_the_screening_function(T, ne, Z):
+    """Primakoff: what the x-shape leaves is ln F(s) - ln min(s/2, ln(1+s))
+    plus a cell constant; F <= min(s/2, ln(1+s)) with equality in both limits
+    and ratio at least 0.6 (its minimum, near s = 2.5), so the residual spans
+    at most ln(0.6) ~ -0.51 in x."""
+    x = np.geomspace(S.X_LO, S.X_HI, 400)
+    r, _ = _residual("primakoff", x, T, ne, Z)
+    kT = S.kappa_over_T(T, ne, Z)
+    s = 4 * x ** 2 / kT ** 2
+    ratio = np.log(plasma.primakoff_F(s) / np.minimum(s / 2, np.log1p(s)))
+    assert np.all(ratio <= 1e-12) and ratio.min() > math.log(0.59)
+    np.testing.assert_allclose(r - ratio, (r - ratio)[0], atol=1e-9)
+
+
 def test_features_span_the_domain():
     f = S.features([S.X_LO, S.X_HI], [S.KT_LO, S.KT_HI], [S.NE_LO, S.NE_HI], [1, 2])
     np.testing.assert_allclose(f[:, :3], [[-1, -1, -1], [1, 1, 1]], atol=1e-12)
