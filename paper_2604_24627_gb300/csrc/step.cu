@@ -275,21 +275,28 @@ __device__ __noinline__ PhotonDecision photon_decide_slow(const StepArgs& A, int
 // u <= 1 - lb <= exp(-lambda).
 // A bound at or above the Poisson-mean cap also sends the slot to the full
 // decision, so that cap hits are counted exactly.
-__device__ __forceinline__ bool no_conversion(float w, float p2, float c_s, float Acoef, float inv_wref, float u,
-                                              float lam_cap, float gm) {
+// kb is the cell's A / w_ref with the margin 1.0001 (times the rate model's
+// guard margin) folded in.
+__device__ __forceinline__ bool no_conversion(float w, float p2, float c_s, float kb, float u, float lam_cap) {
   const float s = p2 * c_s;
   const float Fb = s < 2.5f ? 0.5f * s : __logf(1.0f + s);
-  const float lb = w * Acoef * Fb * inv_wref * (1.0001f * gm);
+  const float lb = w * kb * Fb;
   return lb < lam_cap && u <= 1.0f - lb - 1e-6f;
+}
+__device__ __forceinline__ float conversion_kb(float Acoef, float inv_wref, float gm) {
+  return Acoef * inv_wref * (1.0001f * gm);
 }
 
 // Absorption: P_abs <= tau; x/(1-e^-x) <= 1 + x bounds the Compton-like
-// factor, (1 - e^-x) <= 1 the Bose-Einstein one.
-__device__ __forceinline__ bool no_absorption(float r_bc, float r_bb, const StepArgs& A, int mask, float x, float u) {
+// factor, (1 - e^-x) <= 1 the Bose-Einstein one. b_c, b_b: the cell's
+// coefficients with the margin 1.001 (times the guard margin) folded in; x
+// = |p| m_e c^2 / T from p2 by a reciprocal square root (p2 = 0 gives NaN,
+// which clears nothing).
+__device__ __forceinline__ bool no_absorption(float b_c, float b_b, const StepArgs& A, int mask, float x, float u) {
   float tb = 0.f;
-  if (mask & AXPIC_CH_COMPTON) tb += r_bc * x * (1.0f + x);
-  if (mask & AXPIC_CH_BREMS) tb += r_bb * __expf(A.brems_am3 * __logf(x));
-  return u >= tb * (1.001f * A.guard_margin) + 1e-6f;
+  if (mask & AXPIC_CH_COMPTON) tb += b_c * x * (1.0f + x);
+  if (mask & AXPIC_CH_BREMS) tb += b_b * __expf(A.brems_am3 * __logf(x));
+  return u >= tb + 1e-6f;
 }
 
 // ---------------------------------------------------------------- feedback
@@ -678,7 +685,7 @@ __device__ __forceinline__ int photon_chunk(const StepArgs& A, uint32_t step, in
     const int cnt = min(max(A.g.count[c], 0), A.g.cap);
     n = A.use_snapshot ? min(A.photon_start[c], cnt) : cnt;
     c_s = kMeC2f * kMeC2f * __ldg(rec + R_FOURK2);
-    ap = __ldg(rec + R_AP);
+    ap = conversion_kb(__ldg(rec + R_AP), A.inv_w_a, A.guard_margin);
   }
   const QuadRange<C> R = quad_range<C>(n, lane, nc);
   for (int g0 = 0; g0 < R.total; g0 += 32) {
@@ -701,7 +708,7 @@ __device__ __forceinline__ int photon_chunk(const StepArgs& A, uint32_t step, in
       for (int j = 0; j < 4; ++j) {
         const float px = f4(x4, j), py = f4(y4, j), pz = f4(z4, j);
         const float p2 = px * px + py * py + pz * pz;
-        if (j < nj && !no_conversion(f4(w4, j), p2, cs, ca, A.inv_w_a, u23(word(r, j)), A.lam_cap, A.guard_margin))
+        if (j < nj && !no_conversion(f4(w4, j), p2, cs, ca, u23(word(r, j)), A.lam_cap))
           nib |= 1u << j;
       }
     }
@@ -726,10 +733,10 @@ __device__ __forceinline__ int axion_chunk(const StepArgs& A, uint32_t step, int
     const float* rec = A.rec + (size_t)c * kRecLen;
     n = min(max(A.a.count[c], 0), A.a.cap);
     c_s = kMeC2f * kMeC2f * __ldg(rec + R_FOURK2);
-    apinv = __ldg(rec + R_APINV);
-    invT = __ldg(rec + R_INVT);
-    r_bc = __ldg(rec + R_BC);
-    r_bb = __ldg(rec + R_BB);
+    apinv = conversion_kb(__ldg(rec + R_APINV), A.inv_w_gref, A.guard_margin);
+    invT = kMeC2f * __ldg(rec + R_INVT);
+    r_bc = __ldg(rec + R_BC) * (1.001f * A.guard_margin);
+    r_bb = __ldg(rec + R_BB) * (1.001f * A.guard_margin);
   }
   const QuadRange<C> R = quad_range<C>(n, lane, nc);
   for (int g0 = 0; g0 < R.total; g0 += 32) {
@@ -759,8 +766,8 @@ __device__ __forceinline__ int axion_chunk(const StepArgs& A, uint32_t step, int
         const float p2 = px * px + py * py + pz * pz;
         bool fast = !all;
         if (fast && prim)
-          fast = no_conversion(f4(w4, j), p2, cs, cap_inv, A.inv_w_gref, u23(word(rP, j)), A.lam_cap, A.guard_margin);
-        if (fast && bath) fast = no_absorption(cbc, cbb, A, mask, sqrtf(p2) * kMeC2f * cinvT, u23(word(rA, j)));
+          fast = no_conversion(f4(w4, j), p2, cs, cap_inv, u23(word(rP, j)), A.lam_cap);
+        if (fast && bath) fast = no_absorption(cbc, cbb, A, mask, p2 * rsqrtf(p2) * cinvT, u23(word(rA, j)));
         if (j < nj && !fast) nib |= 1u << j;
       }
     }
