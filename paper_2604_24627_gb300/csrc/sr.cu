@@ -56,38 +56,55 @@ __device__ __forceinline__ void sr_cell(const SrArgs& a, int cell, float* T, flo
   *ne = rec[R_NE] * 1e24f;
 }
 
-// Thread per (cell, output): bilinear in (ln kappa/T, log10 n_e) at the
-// cell's Z, plus the per-cell constants.
-__global__ void sr_table_kernel(SrArgs a) {
-  const int cell = blockIdx.x, o = threadIdx.x;
-  if (cell >= a.ncells || o >= kSrLen) return;
-  float T, kT, ne;
-  sr_cell(a, cell, &T, &kT, &ne);
-  float* out = a.sr + (size_t)cell * kSrLen;
-  if (o < kSrTabOut) {
+// A CTA takes 32 cells: warp 0 forms each cell's interpolation constants
+// (lane per cell) in shared memory, then the CTA's threads stream the 32 x
+// 192 record entries (consecutive threads, consecutive entries of a cell):
+// bilinear in (ln kappa/T, log10 n_e) at the cell's Z, plus the per-cell
+// constants.
+constexpr int kSrTableThreads = 256;
+__global__ void __launch_bounds__(kSrTableThreads) sr_table_kernel(SrArgs a) {
+  struct Interp {
+    const float* t00;
+    float fu, fv, lnKP, lnKA, T;
+  };
+  __shared__ Interp ip[32];
+  const int c0 = blockIdx.x * 32;
+  const int nc = min(32, a.ncells - c0);
+  if (threadIdx.x < 32 && (int)threadIdx.x < nc) {
+    float T, kT, ne;
+    sr_cell(a, c0 + threadIdx.x, &T, &kT, &ne);
     float u = (__logf(kT) - kSrLnKt0) / kSrLnKtSpan * (a.nkt - 1);
     float v = (log10f(ne) - 23.0f) / 3.0f * (a.nne - 1);
     u = fminf(fmaxf(u, 0.f), (float)(a.nkt - 1));
     v = fminf(fmaxf(v, 0.f), (float)(a.nne - 1));
     const int i = min((int)u, a.nkt - 2), j = min((int)v, a.nne - 2);
-    const float fu = u - i, fv = v - j;
     const int z = a.Z > 1.5f ? 1 : 0;
-    const float* t00 = a.tab + ((size_t)(z * a.nne + j) * a.nkt + i) * kSrTabOut;
-    const float* t01 = t00 + (size_t)a.nkt * kSrTabOut;  // j + 1
-    const float v00 = t00[o], v10 = t00[kSrTabOut + o], v01 = t01[o], v11 = t01[kSrTabOut + o];
-    out[o] = (1.f - fv) * ((1.f - fu) * v00 + fu * v10) + fv * ((1.f - fu) * v01 + fu * v11);
-  } else if (o == SR_LNKP) {
-    out[o] = a.ln_gP - 4.0f * __logf(T);
-  } else if (o == SR_LNKA) {
-    out[o] = a.ln_gA - 4.0f * __logf(T);
-  } else {
-    out[o] = T;
+    Interp& q = ip[threadIdx.x];
+    q.t00 = a.tab + ((size_t)(z * a.nne + j) * a.nkt + i) * kSrTabOut;
+    q.fu = u - i;
+    q.fv = v - j;
+    q.lnKP = a.ln_gP - 4.0f * __logf(T);
+    q.lnKA = a.ln_gA - 4.0f * __logf(T);
+    q.T = T;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nc * kSrLen; e += kSrTableThreads) {
+    const int c = e / kSrLen, o = e - c * kSrLen;
+    const Interp& q = ip[c];
+    float* out = a.sr + (size_t)(c0 + c) * kSrLen;
+    if (o < kSrTabOut) {
+      const float* t01 = q.t00 + (size_t)a.nkt * kSrTabOut;  // j + 1
+      const float v00 = q.t00[o], v10 = q.t00[kSrTabOut + o], v01 = t01[o], v11 = t01[kSrTabOut + o];
+      out[o] = (1.f - q.fv) * ((1.f - q.fu) * v00 + q.fu * v10) + q.fv * ((1.f - q.fu) * v01 + q.fu * v11);
+    } else {
+      out[o] = o == SR_LNKP ? q.lnKP : (o == SR_LNKA ? q.lnKA : q.T);
+    }
   }
 }
 
 cudaError_t launch_sr_table(const SrArgs& a, cudaStream_t st) {
   if (a.ncells <= 0) return cudaSuccess;
-  sr_table_kernel<<<a.ncells, kSrLen, 0, st>>>(a);
+  sr_table_kernel<<<(a.ncells + 31) / 32, kSrTableThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
