@@ -119,7 +119,7 @@ typedef struct {
   int32_t threads_per_block;/* threads per CTA of the event kernel (32..128, one
                                warp per cell); 0: default 128 */
   int32_t decide_chunk;     /* cells per chunk of a decision warp: 2, 4 or 8;
-                               0: default 4 (launch shape, see axpic_autotune) */
+                               0: default 8 (launch shape, see axpic_autotune) */
   int32_t rate_model;       /* 0: closed forms (default); 1: exact FP32 table;
                                2: surrogate network (axpic_set_surrogate) with
                                the table where it is not trusted. Models 1 and
