@@ -329,7 +329,7 @@ def run_rate_models(args):
     # the network: trained and validated on the GPU
     t0 = time.time()
     net = SurrogateNet(stream=stream)
-    fit_loss = _lib.axpic_surrogate_fit(net.h, 8192, 32, 40000, 8192, 2e-3, 7)
+    fit_loss = _lib.axpic_surrogate_fit(net.h, 65536, 1, 40000, 8192, 2e-3, 7)
     fit_s = time.time() - t0
     nT, nne = 24, 16
     eL, eQ = _lib.axpic_surrogate_validate(net.h, nT, nne)

@@ -21,11 +21,13 @@ c in (Primakoff, Compton-like, bremsstrahlung):
   spectrum dQ_c/dx / x restricted to [0.05, 20] (the end points x(0) = 0.05
   and x(1) = 20 are fixed and not outputs).
 
-The network (4 -> 64 -> 64 -> 96, tanh hidden layers) sees normalised features
-f = (ln x, ln(kappa/T), log10 n_e, Z) and predicts a normalised residual z;
-the model's output is y = shape(x, kappa/T) + mu + S f + sigma z with
-per-output constants mu, sigma, an FP32 linear map S (96 x 4) and fixed
-x-shapes on the ln-emissivity outputs (model_output below).
+The model's output is y = shape(x, kappa/T) + mu + S f_c + sigma z
+(model_output below). shape is each channel's exact x-dependence on the
+ln-emissivity outputs, so the rest is a function of the cell alone: the
+network (4 -> 64 -> 64 -> 96, tanh hidden layers) and the FP32 linear map S
+(96 x 4) see the cell features f_c = (0, ln(kappa/T), log10 n_e, Z), the
+normalised features of the row with the ln x column held at zero, and mu,
+sigma are per-output constants.
 
 Pinned by: the Compton-like and bremsstrahlung quantiles against the
 closed-form inverse CDFs of the spectra module (Bose integrals, scipy's
@@ -81,28 +83,37 @@ def features(x, kT, ne, Z):
     return np.stack(np.broadcast_arrays(f0, f1, f2, f3), axis=-1)
 
 
+def cell_features(X):
+    """The features the network and the linear map see: the rows' features
+    with the ln x column held at zero."""
+    X = np.array(np.atleast_2d(X), dtype=np.float64)
+    X[:, 0] = 0.0
+    return X
+
+
 def shape(X, brems_shape=1.70):
     """The fixed part of the model's 96 outputs at feature rows X: on the
-    ln-emissivity outputs the channel's x-shape (Primakoff: Planck factor
-    x^3/(e^x - 1) times min(s/2, ln(1 + s)), s = 4 x^2/(kappa/T)^2, which
-    bounds the screening function F from above; Compton-like x^5/(e^x - 1);
-    bremsstrahlung x^a e^-x), in ln; zero on the quantiles. x and kappa/T are
-    recovered from the features."""
+    ln-emissivity outputs the channel's x-dependence at fixed cell, in ln
+    (Primakoff: x^3/(e^x - 1) F(s), s = 4 x^2/(kappa/T)^2, with the screening
+    function F of Eq. prim_F; Compton-like x^5/(e^x - 1); bremsstrahlung
+    x^a e^-x); zero on the quantiles. x and kappa/T are recovered from the
+    features."""
     X = np.atleast_2d(np.asarray(X, dtype=np.float64))
     x = X_LO * (X_HI / X_LO) ** (0.5 * (X[:, 0] + 1.0))
     kT = KT_LO * (KT_HI / KT_LO) ** (0.5 * (X[:, 1] + 1.0))
     s = 4.0 * x ** 2 / kT ** 2
     out = np.zeros((len(X), N_OUT))
-    out[:, 0] = 3.0 * np.log(x) - np.log(np.expm1(x)) + np.log(np.minimum(0.5 * s, np.log1p(s)))
+    out[:, 0] = 3.0 * np.log(x) - np.log(np.expm1(x)) + np.log(plasma.primakoff_F(s))
     out[:, 32] = 5.0 * np.log(x) - np.log(np.expm1(x))
     out[:, 64] = brems_shape * np.log(x) - x
     return out
 
 
 def model_output(z, X, mu, sigma, skip, brems_shape=1.70):
-    """y = shape + mu + S f + sigma z for normalised outputs z at features X."""
+    """y = shape + mu + S f_c + sigma z for normalised network outputs z (the
+    network evaluated at cell_features(X)) at feature rows X."""
     X = np.atleast_2d(np.asarray(X, dtype=np.float64))
-    return (shape(X, brems_shape) + np.asarray(mu, np.float64) + X @ np.asarray(skip, np.float64).T
+    return (shape(X, brems_shape) + np.asarray(mu, np.float64) + cell_features(X) @ np.asarray(skip, np.float64).T
             + np.asarray(sigma, np.float64) * z)
 
 

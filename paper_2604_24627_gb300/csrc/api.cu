@@ -277,8 +277,9 @@ static SrArgs make_sr_args(axpic_ctx* ctx) {
   return a;
 }
 
-// Rebuilds every cell's spectral record for its current T: the table, then
-// the network over the cells where it is trusted.
+// Rebuilds every cell's spectral record for its current T: the table kernel
+// and, once a network is trusted somewhere, the fused network kernel; each
+// writes the cells the other skips (trusted: network).
 static cudaError_t build_records(axpic_ctx* ctx, cudaStream_t st) {
   if (!ctx->prm.rate_model) return cudaSuccess;
   const SrArgs a = make_sr_args(ctx);

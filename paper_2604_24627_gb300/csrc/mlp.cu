@@ -366,14 +366,25 @@ struct axpic_mlp {
   std::vector<float> skip = std::vector<float>(96 * 4, 0.f);  // S[o][i]
 };
 
-// The output model y = shape(x, kappa/T) + mu + S f + sigma z for the
-// network's normalised output z (double).
+// The output model y = shape(x, kappa/T) + mu + S f_c + sigma z for the
+// network's normalised output z (double) at the row's features f. shape
+// carries each channel's exact x-dependence, so the learned part sees the
+// cell features f_c = (0, f1, f2, f3): the network is evaluated at f_c and
+// the ln x column of S multiplies zero.
 static double model_output(const axpic_mlp* h, int o, const float* f, double z, double brems_shape) {
   double x, kT;
   axpic::sur_feature_xkt(f, &x, &kT);
   double y = axpic::sur_shape(o, x, kT, brems_shape) + (double)h->mu[o] + (double)h->sigma[o] * z;
-  for (int i = 0; i < 4; ++i) y += (double)h->skip[o * 4 + i] * (double)f[i];
+  for (int i = 1; i < 4; ++i) y += (double)h->skip[o * 4 + i] * (double)f[i];
   return y;
+}
+
+// The network's inputs for feature rows X: the cell features (ln x column
+// zeroed).
+static std::vector<float> cell_features(const std::vector<float>& X) {
+  std::vector<float> Xc(X);
+  for (size_t r = 0; r < Xc.size() / 4; ++r) Xc[r * 4] = 0.f;
+  return Xc;
 }
 
 extern "C" {
@@ -532,12 +543,13 @@ axpic_status axpic_surrogate_fit(axpic_mlp* h, int32_t ncells, int32_t x_per_cel
   std::vector<double> Y;
   axpic::sur_training_set(ncells, x_per_cell, seed, brems_shape, X, Y);
   const size_t n = (size_t)ncells * x_per_cell;
-  // The output model y = shape(x, kappa/T) + mu + S f + sigma z: the network
-  // learns only what the fixed x-shapes and an FP32 linear map of the
-  // features leave over. mu and S by least squares over the rows (5 x 5
-  // normal equations in FP64, 96 right-hand sides); sigma is the residual's
-  // spread, divided by kRateWeight on the ln-emissivity outputs so that their
-  // errors weigh more in the loss.
+  // The output model y = shape(x, kappa/T) + mu + S f_c + sigma z: the
+  // network learns only what the exact x-shapes and an FP32 linear map of the
+  // cell features leave over. mu and S by least squares over the rows (4 x 4
+  // normal equations in FP64 over (1, f1, f2, f3), 96 right-hand sides; the
+  // ln x column of S is zero); sigma is the residual's spread, divided by
+  // kRateWeight on the ln-emissivity outputs so that their errors weigh more
+  // in the loss.
 #ifndef AXPIC_RATE_WEIGHT
 #define AXPIC_RATE_WEIGHT 4.0
 #endif
@@ -547,36 +559,38 @@ axpic_status axpic_surrogate_fit(axpic_mlp* h, int32_t ncells, int32_t x_per_cel
     axpic::sur_feature_xkt(&X[r * 4], &x, &kT);
     for (int k = 0; k < 96; ++k) Y[r * 96 + k] -= axpic::sur_shape(k, x, kT, brems_shape);
   }
-  double M[5][5 + 96] = {};
+  constexpr int kD = 4;  // 1, f1, f2, f3
+  double M[kD][kD + 96] = {};
   for (size_t r = 0; r < n; ++r) {
-    const double d[5] = {1.0, X[r * 4], X[r * 4 + 1], X[r * 4 + 2], X[r * 4 + 3]};
-    for (int i = 0; i < 5; ++i) {
-      for (int j = 0; j < 5; ++j) M[i][j] += d[i] * d[j];
-      for (int k = 0; k < 96; ++k) M[i][5 + k] += d[i] * Y[r * 96 + k];
+    const double d[kD] = {1.0, X[r * 4 + 1], X[r * 4 + 2], X[r * 4 + 3]};
+    for (int i = 0; i < kD; ++i) {
+      for (int j = 0; j < kD; ++j) M[i][j] += d[i] * d[j];
+      for (int k = 0; k < 96; ++k) M[i][kD + k] += d[i] * Y[r * 96 + k];
     }
   }
-  for (int c = 0; c < 5; ++c) {  // Gauss-Jordan with partial pivoting
+  for (int c = 0; c < kD; ++c) {  // Gauss-Jordan with partial pivoting
     int p = c;
-    for (int i = c + 1; i < 5; ++i)
+    for (int i = c + 1; i < kD; ++i)
       if (std::fabs(M[i][c]) > std::fabs(M[p][c])) p = i;
     if (!(std::fabs(M[p][c]) > 0.0)) return AXPIC_E_INVALID;  // degenerate feature draw
-    for (int j = 0; j < 5 + 96; ++j) std::swap(M[c][j], M[p][j]);
-    for (int i = 0; i < 5; ++i) {
+    for (int j = 0; j < kD + 96; ++j) std::swap(M[c][j], M[p][j]);
+    for (int i = 0; i < kD; ++i) {
       if (i == c) continue;
       const double g = M[i][c] / M[c][c];
-      for (int j = c; j < 5 + 96; ++j) M[i][j] -= g * M[c][j];
+      for (int j = c; j < kD + 96; ++j) M[i][j] -= g * M[c][j];
     }
   }
   for (int k = 0; k < 96; ++k) {
-    h->mu[k] = (float)(M[0][5 + k] / M[0][0]);
-    for (int i = 0; i < 4; ++i) h->skip[k * 4 + i] = (float)(M[i + 1][5 + k] / M[i + 1][i + 1]);
+    h->mu[k] = (float)(M[0][kD + k] / M[0][0]);
+    h->skip[k * 4] = 0.f;
+    for (int i = 1; i < kD; ++i) h->skip[k * 4 + i] = (float)(M[i][kD + k] / M[i][i]);
   }
   // residuals with the binary32 coefficients the model keeps
   std::vector<double> var(96, 0.0);
   for (size_t r = 0; r < n; ++r)
     for (int k = 0; k < 96; ++k) {
       double lin = h->mu[k];
-      for (int i = 0; i < 4; ++i) lin += (double)h->skip[k * 4 + i] * (double)X[r * 4 + i];
+      for (int i = 1; i < 4; ++i) lin += (double)h->skip[k * 4 + i] * (double)X[r * 4 + i];
       Y[r * 96 + k] -= lin;
       var[k] += Y[r * 96 + k] * Y[r * 96 + k];
     }
@@ -585,6 +599,7 @@ axpic_status axpic_surrogate_fit(axpic_mlp* h, int32_t ncells, int32_t x_per_cel
   std::vector<float> Zt(n * 96);
   for (size_t r = 0; r < n; ++r)
     for (int k = 0; k < 96; ++k) Zt[r * 96 + k] = (float)(Y[r * 96 + k] / h->sigma[k]);
+  X = cell_features(X);  // the network's inputs
   std::vector<float> P;
   glorot(seed ^ 0xA5A5A5A5u, P);
   axpic_status s = axpic_mlp_set_params(h, P.data());
@@ -621,7 +636,8 @@ axpic_status axpic_surrogate_validate(axpic_mlp* h, int32_t nT, int32_t nne, dou
   const int nodes = nT * nne * 2, nx = 32;
   std::vector<float> X((size_t)nodes * nx * 4);
   std::vector<double> Y((size_t)nodes * nx * 96);
-  double knots[93];
+  double knots[93], uni[93];
+  axpic::sur_universal_knots(brems_shape, uni);
   for (int z = 0; z < 2; ++z)
     for (int j = 0; j < nne; ++j)
       for (int i = 0; i < nT; ++i) {
@@ -630,7 +646,7 @@ axpic_status axpic_surrogate_validate(axpic_mlp* h, int32_t nT, int32_t nne, dou
         const double ne = std::pow(10.0, 23.0 + 3.0 * j / (nne - 1));
         const double Z = z + 1.0;
         const axpic::SurCell c = axpic::sur_cell(T, ne, Z, brems_shape);
-        axpic::sur_knots(c, knots);
+        axpic::sur_knots(c, knots, uni);
         for (int k = 0; k < nx; ++k) {
           const double x = axpic::kSurXLo * std::pow(axpic::kSurXHi / axpic::kSurXLo, k / (double)(nx - 1));
           const size_t r = (size_t)node * nx + k;
@@ -646,7 +662,8 @@ axpic_status axpic_surrogate_validate(axpic_mlp* h, int32_t nT, int32_t nne, dou
     return mlp_fail(h, e, "axpic_surrogate_validate");
   }
   std::vector<float> Z(n * 96);
-  e = cudaMemcpyAsync(dX, X.data(), sizeof(float) * X.size(), cudaMemcpyHostToDevice, h->m.st);
+  const std::vector<float> Xc = cell_features(X);
+  e = cudaMemcpyAsync(dX, Xc.data(), sizeof(float) * Xc.size(), cudaMemcpyHostToDevice, h->m.st);
   if (!e) e = h->m.forward(dX, (int)n, dZ);
   if (!e) e = cudaMemcpyAsync(Z.data(), dZ, sizeof(float) * Z.size(), cudaMemcpyDeviceToHost, h->m.st);
   if (!e) e = cudaStreamSynchronize(h->m.st);

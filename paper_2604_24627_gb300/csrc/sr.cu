@@ -2,11 +2,13 @@
 //
 // Table model: the exact targets tabulated on the host over (ln kappa/T,
 // log10 n_e, Z) and interpolated bilinearly per cell. Surrogate model: the
-// network evaluated per cell at the 32 grid points x_k in one fused kernel
-// (features and layer 1 on the CUDA cores, layers 2 and 3 as tcgen05 MMAs
-// with FP32 accumulators in tensor memory, output affine in FP32), written
-// over the table record of every cell whose (T, n_e, Z) lies in the region
-// where the network's validated error is within the bound.
+// network evaluated once per cell (its inputs are the cell features; every
+// x-dependence is in the exact shapes) in one fused kernel: features and
+// layer 1 on the CUDA cores, layers 2 and 3 as tcgen05 MMAs with FP32
+// accumulators in tensor memory, the output affine in FP32, the shapes added
+// at the 32 grid points x_k. Cells whose (T, n_e, Z) lies outside the region
+// where the network's validated error is within the bound get the table
+// record (the table kernel, which then skips the others).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -23,10 +25,12 @@ namespace axpic {
 
 void build_sr_table(int nkt, int nne, double brems_shape, float* out) {
   const int nodes = 2 * nne * nkt;
+  double uni[93];
+  sur_universal_knots(brems_shape, uni);
   const int nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
   std::vector<std::thread> th;
   for (int t = 0; t < nth; ++t) {
-    th.emplace_back([=]() {
+    th.emplace_back([=, &uni]() {
       double knots[93], y[96];
       for (int node = t; node < nodes; node += nth) {
         const int i = node % nkt, j = (node / nkt) % nne, z = node / (nkt * nne);
@@ -34,7 +38,7 @@ void build_sr_table(int nkt, int nne, double brems_shape, float* out) {
         const double ne = std::pow(10.0, 23.0 + 3.0 * j / (nne - 1));
         const double Z = z + 1.0;
         const SurCell c = sur_cell(sur_temperature(kT, ne, Z), ne, Z, brems_shape);
-        sur_knots(c, knots);
+        sur_knots(c, knots, uni);
         float* o = out + (size_t)node * kSrTabOut;
         for (int k = 0; k < kSrGrid; ++k) {
           const double x = std::exp(std::log(kSurXLo) + std::log(kSurXHi / kSurXLo) / 29.0 * (k - 1));
@@ -56,65 +60,42 @@ __device__ __forceinline__ void sr_cell(const SrArgs& a, int cell, float* T, flo
   *ne = rec[R_NE] * 1e24f;
 }
 
-// A CTA takes 32 cells: warp 0 forms each cell's interpolation constants
-// (lane per cell) in shared memory, then the CTA's threads stream the 32 x
-// 192 record entries (consecutive threads, consecutive entries of a cell):
-// bilinear in (ln kappa/T, log10 n_e) at the cell's Z, plus the per-cell
-// constants.
-constexpr int kSrTableThreads = 256;
-__global__ void __launch_bounds__(kSrTableThreads) sr_table_kernel(SrArgs a) {
-  struct Interp {
-    const float* t00;
-    float fu, fv, lnKP, lnKA, T;
-  };
-  __shared__ Interp ip[32];
-  const int c0 = blockIdx.x * 32;
-  const int nc = min(32, a.ncells - c0);
-  if (threadIdx.x < 32 && (int)threadIdx.x < nc) {
-    float T, kT, ne;
-    sr_cell(a, c0 + threadIdx.x, &T, &kT, &ne);
-    float u = (__logf(kT) - kSrLnKt0) / kSrLnKtSpan * (a.nkt - 1);
-    float v = (log10f(ne) - 23.0f) / 3.0f * (a.nne - 1);
-    u = fminf(fmaxf(u, 0.f), (float)(a.nkt - 1));
-    v = fminf(fmaxf(v, 0.f), (float)(a.nne - 1));
-    const int i = min((int)u, a.nkt - 2), j = min((int)v, a.nne - 2);
-    const int z = a.Z > 1.5f ? 1 : 0;
-    Interp& q = ip[threadIdx.x];
-    q.t00 = a.tab + ((size_t)(z * a.nne + j) * a.nkt + i) * kSrTabOut;
-    q.fu = u - i;
-    q.fv = v - j;
-    q.lnKP = a.ln_gP - 4.0f * __logf(T);
-    q.lnKA = a.ln_gA - 4.0f * __logf(T);
-    q.T = T;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < nc * kSrLen; e += kSrTableThreads) {
-    const int c = e / kSrLen, o = e - c * kSrLen;
-    const Interp& q = ip[c];
-    float* out = a.sr + (size_t)(c0 + c) * kSrLen;
-    if (o < kSrTabOut) {
-      const float* t01 = q.t00 + (size_t)a.nkt * kSrTabOut;  // j + 1
-      const float v00 = q.t00[o], v10 = q.t00[kSrTabOut + o], v01 = t01[o], v11 = t01[kSrTabOut + o];
-      out[o] = (1.f - q.fv) * ((1.f - q.fu) * v00 + q.fu * v10) + q.fv * ((1.f - q.fu) * v01 + q.fu * v11);
-    } else {
-      out[o] = o == SR_LNKP ? q.lnKP : (o == SR_LNKA ? q.lnKA : q.T);
-    }
-  }
+// A cell's table interpolation constants: the corner node (i, j) at the
+// cell's Z, the weights in (ln kappa/T, log10 n_e), and the record's
+// per-cell constants.
+struct SrInterp {
+  const float* t00;
+  float fu, fv, lnKP, lnKA, T;
+};
+
+__device__ __forceinline__ void sr_interp(const SrArgs& a, float T, float kT, float ne, SrInterp* q) {
+  float u = (__logf(kT) - kSrLnKt0) / kSrLnKtSpan * (a.nkt - 1);
+  float v = (log10f(ne) - 23.0f) / 3.0f * (a.nne - 1);
+  u = fminf(fmaxf(u, 0.f), (float)(a.nkt - 1));
+  v = fminf(fmaxf(v, 0.f), (float)(a.nne - 1));
+  const int i = min((int)u, a.nkt - 2), j = min((int)v, a.nne - 2);
+  const int z = a.Z > 1.5f ? 1 : 0;
+  q->t00 = a.tab + ((size_t)(z * a.nne + j) * a.nkt + i) * kSrTabOut;
+  q->fu = u - i;
+  q->fv = v - j;
+  q->lnKP = fmaf(-4.0f, __logf(T), a.ln_gP);
+  q->lnKA = fmaf(-4.0f, __logf(T), a.ln_gA);
+  q->T = T;
 }
 
-cudaError_t launch_sr_table(const SrArgs& a, cudaStream_t st) {
-  if (a.ncells <= 0) return cudaSuccess;
-  sr_table_kernel<<<(a.ncells + 31) / 32, kSrTableThreads, 0, st>>>(a);
-  return cudaGetLastError();
+// Entry o of the table record (bilinear, each rounding step explicit so that
+// both record kernels give the same bits).
+__device__ __forceinline__ float sr_table_entry(const SrArgs& a, const SrInterp& q, int o) {
+  if (o >= kSrTabOut) return o == SR_LNKP ? q.lnKP : (o == SR_LNKA ? q.lnKA : q.T);
+  const float* t01 = q.t00 + (size_t)a.nkt * kSrTabOut;  // j + 1
+  const float v00 = q.t00[o], v10 = q.t00[kSrTabOut + o], v01 = t01[o], v11 = t01[kSrTabOut + o];
+  const float u0 = fmaf(q.fu, v10, __fmul_rn(1.f - q.fu, v00));
+  const float u1 = fmaf(q.fu, v11, __fmul_rn(1.f - q.fu, v01));
+  return fmaf(q.fv, u1, __fmul_rn(1.f - q.fv, u0));
 }
 
-// ---------------------------------------------------------------- fused network
-// CTA = 4 cells x 32 grid points = 128 rows (thread = row). Shared memory:
-// A1, A2 (128 x 64 bfloat16, core-matrix layout), W2^T (64 x 64), W3^T
-// (96 x 64); tensor memory: 64 columns for layer 2, 96 for layer 3.
-constexpr int kSrMlpThreads = 128;
-constexpr size_t kSrMlpSmem = (size_t)(128 * 64 * 2 + 64 * 64 + 96 * 64) * sizeof(__nv_bfloat16);
-
+// Whether the network is trusted at (T, n_e, Z): the four validation nodes
+// around it all passed.
 __device__ __forceinline__ bool sr_trusted(const SrArgs& a, float T, float ne, float Z) {
   float fu = (T - (float)kSurTLo) / (float)(kSurTHi - kSurTLo) * (a.tnT - 1);
   float fv = (log10f(ne) - 23.0f) / 3.0f * (a.tnne - 1);
@@ -129,16 +110,68 @@ __device__ __forceinline__ bool sr_trusted(const SrArgs& a, float T, float ne, f
   return t[0] && t[1] && t[a.tnT] && t[a.tnT + 1];
 }
 
-// The fixed x-shape of channel ch's ln-emissivity output (Primakoff: the
-// Planck factor and min(s/2, ln(1 + s)), an upper bound of the screening
-// function; Compton-like: x^5 / (e^x - 1); bremsstrahlung: x^a e^-x).
-__device__ __forceinline__ float sr_shape(int ch, float x, float kT, float a) {
-  if (ch == 0) {
-    const float s = 4.0f * x * x / (kT * kT);
-    return 3.0f * logf(x) - logf(expm1f(x)) + logf(fminf(0.5f * s, log1pf(s)));
+// A CTA takes 32 cells: warp 0 forms each cell's interpolation constants
+// (lane per cell) in shared memory, then the CTA's threads stream the 32 x
+// 192 record entries (consecutive threads, consecutive entries of a cell).
+// With a trust map (surrogate model) the cells where the network is trusted
+// are left to the network kernel.
+constexpr int kSrTableThreads = 256;
+__global__ void __launch_bounds__(kSrTableThreads) sr_table_kernel(SrArgs a) {
+  __shared__ SrInterp ip[32];
+  __shared__ int skip[32];
+  const int c0 = blockIdx.x * 32;
+  const int nc = min(32, a.ncells - c0);
+  if (threadIdx.x < 32 && (int)threadIdx.x < nc) {
+    float T, kT, ne;
+    sr_cell(a, c0 + threadIdx.x, &T, &kT, &ne);
+    sr_interp(a, T, kT, ne, &ip[threadIdx.x]);
+    skip[threadIdx.x] = a.trust && sr_trusted(a, T, ne, a.Z);
   }
-  if (ch == 1) return 5.0f * logf(x) - logf(expm1f(x));
-  return a * logf(x) - x;
+  __syncthreads();
+  for (int e = threadIdx.x; e < nc * kSrLen; e += kSrTableThreads) {
+    const int c = e / kSrLen, o = e - c * kSrLen;
+    if (!skip[c]) a.sr[(size_t)(c0 + c) * kSrLen + o] = sr_table_entry(a, ip[c], o);
+  }
+}
+
+cudaError_t launch_sr_table(const SrArgs& a, cudaStream_t st) {
+  if (a.ncells <= 0) return cudaSuccess;
+  sr_table_kernel<<<(a.ncells + 31) / 32, kSrTableThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- fused network
+// CTA = 128 cells (thread = cell = MMA row); it writes the records of the
+// cells where the network is trusted (the table kernel skips them) and exits
+// at once when it has none. Shared memory: A1, A2 (128 x 64
+// bfloat16, core-matrix layout), W2^T (64 x 64), W3^T (96 x 64); once layer
+// 3 has run, the same bytes hold the 128 cells' 96 outputs (FP32, row stride
+// 97, so that a column is conflict-free), from which each warp writes whole
+// records with coalesced stores. Tensor memory: 128 columns, layer 2 in
+// [0, 64), then layer 3 in [0, 96) after layer 2's values were read out.
+constexpr int kSrMlpThreads = 128;
+constexpr int kSrOutStride = 97;
+constexpr size_t kSrMlpOperands = (size_t)(128 * 64 * 2 + 64 * 64 + 96 * 64) * sizeof(__nv_bfloat16);
+constexpr size_t kSrMlpStage = (size_t)128 * kSrOutStride * sizeof(float);
+constexpr size_t kSrMlpSmem = kSrMlpOperands > kSrMlpStage ? kSrMlpOperands : kSrMlpStage;
+
+// ln F(s), F(s) = (1 + 1/s) ln(1 + s) - 1 the screening function of Sec.
+// II.F, in binary32: below s = 1/2 the alternating series
+// sum_n (-1)^(n+1) s^n / (n (n + 1)) to n = 12 (truncation under 4e-6
+// relative), above it the closed form, whose cancellation costs at most a
+// factor 6 on the rounding of its logarithm.
+__device__ __forceinline__ float sr_prim_lnF(float s) {
+  float F;
+  if (s < 0.5f) {
+    float p = -1.0f / 156.0f;  // n = 12
+#pragma unroll
+    for (int n = 11; n >= 1; --n) p = fmaf(p, s, ((n & 1) ? 1.0f : -1.0f) / (float)(n * (n + 1)));
+    F = p * s;
+  } else {
+    const float L = __logf(1.0f + s);
+    F = fmaf(L, __frcp_rn(s), L) - 1.0f;
+  }
+  return __logf(F);
 }
 
 // Layers 2 and 3 as B^T (N x K = 64) bfloat16 in the core-matrix layout, laid
@@ -159,59 +192,101 @@ cudaError_t launch_sr_weights(const float* P, void* out, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Per-cell state of the fused kernel.
+struct SrCellSlot {
+  SrInterp q;
+  float s_per_x2;  // 4 / (kappa/T)^2: s = x^2 times this
+  int mode;        // 0: not trusted (the table kernel's), 1: network, 2: table (no network outputs)
+};
+
+// A cell's six record entries of this lane (entry lane + 32 it): from the
+// network's outputs y (shared memory), or from the table (mode 2).
+// shx: the lane's fixed shape terms (Primakoff and Compton-like Planck
+// factors, bremsstrahlung power, each plus x_k); qsrc: the network output of
+// the lane's quantile entries (-1: a per-cell constant).
+__device__ __forceinline__ void sr_record_entries(const SrArgs& a, const SrCellSlot& c, const float* y, float x2,
+                                                  const float* shx, const int* qsrc, int lane, float* v) {
+  if (c.mode == 1) {
+    v[0] = y[0] + shx[0] + sr_prim_lnF(x2 * c.s_per_x2);
+    v[1] = y[32] + shx[1];
+    v[2] = y[64] + shx[2];
+#pragma unroll
+    for (int it = 0; it < 3; ++it) v[3 + it] = qsrc[it] >= 0 ? y[qsrc[it]] : sr_table_entry(a, c.q, 96 + lane + 32 * it);
+  } else {
+#pragma unroll
+    for (int it = 0; it < 6; ++it) v[it] = sr_table_entry(a, c.q, lane + 32 * it);
+  }
+}
+
 __global__ void __launch_bounds__(kSrMlpThreads) sr_mlp_kernel(SrArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ SrCellSlot cs[128];
+  // network constants: layer 1 (b1, W1 rows of f1..f3), b2, and the output
+  // affine (mu + sigma b3, sigma, S columns of f1..f3)
+  __shared__ float sL1[4][64], sB2[64], sC3[96], sSig[96], sS[3][96];
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_base;
-  __shared__ int any_trusted;
   __nv_bfloat16* sA1 = reinterpret_cast<__nv_bfloat16*>(sm);
   __nv_bfloat16* sA2 = sA1 + 128 * 64;
   __nv_bfloat16* sW2 = sA2 + 128 * 64;
   __nv_bfloat16* sW3 = sW2 + 64 * 64;
+  float* sOut = reinterpret_cast<float*>(sm);  // after layer 3: [128][kSrOutStride]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int cell = blockIdx.x * 4 + warp, k = lane;
-  const bool valid = cell < a.ncells;
+  const int c0 = blockIdx.x * 128;
+  const int nc = min(128, a.ncells - c0);
+  const bool valid = tid < nc;
   float T = 1.f, kT = 1.f, ne = 1e24f;
-  if (valid) sr_cell(a, cell, &T, &kT, &ne);
+  if (valid) sr_cell(a, c0 + tid, &T, &kT, &ne);
   const bool trusted = valid && sr_trusted(a, T, ne, a.Z);
-  if (tid == 0) any_trusted = 0;
-  __syncthreads();
-  if (trusted) any_trusted = 1;
-  __syncthreads();
-  if (!any_trusted) return;  // the table record stays: nothing to evaluate here
-  if (warp == 0) tmem_alloc(&tmem_base, 256);
-  if (tid == 0) {
-    mbar_init(&bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;");
+  if (valid) {
+    sr_interp(a, T, kT, ne, &cs[tid].q);
+    cs[tid].s_per_x2 = 4.0f / (kT * kT);
+    cs[tid].mode = trusted ? 1 : 0;
   }
-  // the pre-laid-out weights: 20 KB of 16-byte copies
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(a.W16);
-    uint4* dst = reinterpret_cast<uint4*>(sW2);
-    for (int i = tid; i < (64 * 64 + 96 * 64) / 8; i += kSrMlpThreads) dst[i] = src[i];
-  }
-  // features of row (cell, k) and layer 1 on the CUDA cores
-  float f[4];
-  {
-    f[0] = 2.0f * (k - 1) / 29.0f - 1.0f;  // ln x_k on the feature scale (x_1 -> -1, x_30 -> 1)
-    f[1] = (__logf(kT) - kSrLnKt0) / kSrLnKtSpan * 2.0f - 1.0f;
-    f[2] = (log10f(ne) - 24.5f) / 1.5f;
-    f[3] = a.Z - 1.5f;
-    for (int j = 0; j < 64; ++j) {
-      float s = a.P[kOffB1 + j];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) s = fmaf(f[q], a.P[kOffW1 + q * 64 + j], s);
-      sA1[core_off(tid, j, 64)] = __float2bfloat16_rn(tanhf(s));
-    }
-  }
-  smem_to_async_proxy();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tmem_base;
-  const uint32_t lbo = 128, sbo = 8 * 128;
+  // no trusted cell here: the table kernel writes all of them
+  if (!__syncthreads_or(trusted)) return;
   bool ok = true;
-  if (any_trusted) {
+  {
+    if (warp == 0) tmem_alloc(&tmem_base, 128);
+    if (tid == 0) {
+      mbar_init(&bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    // the pre-laid-out weights: 20 KB of 16-byte copies
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(a.W16);
+      uint4* dst = reinterpret_cast<uint4*>(sW2);
+      for (int i = tid; i < (64 * 64 + 96 * 64) / 8; i += kSrMlpThreads) dst[i] = src[i];
+    }
+    if (tid < 64) {
+      sL1[0][tid] = a.P[kOffB1 + tid];
+#pragma unroll
+      for (int q = 1; q < 4; ++q) sL1[q][tid] = a.P[kOffW1 + q * 64 + tid];
+      sB2[tid] = a.P[kOffB2 + tid];
+    }
+    if (tid < 96) {
+      sC3[tid] = fmaf(a.sigma[tid], a.P[kOffB3 + tid], a.mu[tid]);
+      sSig[tid] = a.sigma[tid];
+#pragma unroll
+      for (int i = 1; i < 4; ++i) sS[i - 1][tid] = a.skip[tid * 4 + i];
+    }
+    __syncthreads();
+    // cell features (the ln x input held at zero) and layer 1 on the CUDA cores
+    const float f1 = (__logf(kT) - kSrLnKt0) / kSrLnKtSpan * 2.0f - 1.0f;
+    const float f2 = (log10f(ne) - 24.5f) / 1.5f;
+    const float f3 = a.Z - 1.5f;
+#pragma unroll 16
+    for (int j = 0; j < 64; ++j) {
+      const float h = fmaf(f3, sL1[3][j], fmaf(f2, sL1[2][j], fmaf(f1, sL1[1][j], sL1[0][j])));
+      sA1[core_off(tid, j, 64)] = __float2bfloat16_rn(tanhf(h));
+    }
+    smem_to_async_proxy();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t lbo = 128, sbo = 8 * 128;
     // layer 2: D[0, 64) = A1 . W2
     if (tid == 0) {
       for (int s = 0; s < 4; ++s)
@@ -219,63 +294,92 @@ __global__ void __launch_bounds__(kSrMlpThreads) sr_mlp_kernel(SrArgs a) {
                  mma_idesc(128, 64), s > 0);
       tc_commit(&bar);
     }
-    ok = mbar_wait(&bar, 0);
+    // warp-uniform, as the tensor-memory loads below are warp-collective
+    ok = __all_sync(0xFFFFFFFFu, mbar_wait(&bar, 0));
     tc_fence_after();
     if (ok) {
-      const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
-      for (int c0 = 0; c0 < 64; c0 += 16) {
+      for (int j0 = 0; j0 < 64; j0 += 16) {
         float v[16];
-        tmem_ld16(row + c0, v);
+        tmem_ld16(row + j0, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          sA2[core_off(tid, c0 + j, 64)] = __float2bfloat16_rn(tanhf(v[j] + a.P[kOffB2 + c0 + j]));
+        for (int j = 0; j < 16; ++j) sA2[core_off(tid, j0 + j, 64)] = __float2bfloat16_rn(tanhf(v[j] + sB2[j0 + j]));
       }
     }
     smem_to_async_proxy();
     tc_fence_before();
-    __syncthreads();
+    ok = __syncthreads_and(ok) != 0;
     tc_fence_after();
-    // layer 3: D[64, 160) = A2 . W3
+    // layer 3: D[0, 96) = A2 . W3 (layer 2's columns have been read out)
     if (ok && tid == 0) {
       for (int s = 0; s < 4; ++s)
-        mma_bf16(tmem + 64, mma_desc(smem_u32(sA2) + s * 256, lbo, sbo),
-                 mma_desc(smem_u32(sW3) + s * 256, lbo, sbo), mma_idesc(128, 96), s > 0);
+        mma_bf16(tmem, mma_desc(smem_u32(sA2) + s * 256, lbo, sbo), mma_desc(smem_u32(sW3) + s * 256, lbo, sbo),
+                 mma_idesc(128, 96), s > 0);
       tc_commit(&bar);
     }
-    bool issued3 = ok;
-    if (ok) ok = mbar_wait(&bar, 1);
+    const bool issued3 = ok;
+    if (ok) ok = __all_sync(0xFFFFFFFFu, mbar_wait(&bar, 1));
     tc_fence_after();
     if (!ok) {
       // flag it and give the tensor core a second bounded wait on whatever
-      // it may still be doing before the tensor memory is released
+      // it may still be doing before the tensor memory is released (the
+      // records then come from the table)
       if (tid == 0) atomicOr(a.err, 2);
       mbar_wait(&bar, issued3 ? 1u : 0u);
-    } else {
-      const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16) + 64;
-      float* out = a.sr + (size_t)cell * kSrLen;
-      const float xk = __expf(kSrLnX0 + kSrH * (float)k);
-      for (int c0 = 0; c0 < 96; c0 += 16) {
-        float v[16];
-        tmem_ld16(row + c0, v);
-        if (trusted) {
+    }
+    // every thread's loads of layer 3 are in registers before the operands'
+    // bytes are overwritten with the outputs
+    float y[96];
+    if (ok) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int o = c0 + j;
-            float y = a.mu[o] + a.sigma[o] * (v[j] + a.P[kOffB3 + o]);
+      for (int j0 = 0; j0 < 96; j0 += 16) tmem_ld16(row + j0, y + j0);
+    }
+    tc_fence_before();
+    ok = __syncthreads_and(ok) != 0;
+    tc_fence_after();
+    if (warp == 0) tmem_free(tmem, 128);
+    if (ok) {
+      float* out = sOut + tid * kSrOutStride;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) y = fmaf(a.skip[o * 4 + i], f[i], y);
-            const int ch = o >> 5, slot = o & 31;
-            if (slot == 0) out[ch * 32 + k] = y + sr_shape(ch, xk, kT, a.brems_a) + xk;
-            else if (k == 0) out[96 + ch * 31 + slot - 1] = y;
-          }
-        }
-      }
+      for (int o = 0; o < 96; ++o)
+        out[o] = fmaf(sS[2][o], f3, fmaf(sS[1][o], f2, fmaf(sS[0][o], f1, fmaf(sSig[o], y[o], sC3[o]))));
+    } else if (trusted) {
+      cs[tid].mode = 2;  // no network outputs: the table record
+    }
+    __syncthreads();
+  }
+  // records: warp w writes cells w, w + 4, ..., two at a time, a cell's 192
+  // entries by its 32 lanes (lane k takes grid point x_k of the three rate
+  // rows). A trusted cell's ln-emissivity row is the network's cell constant
+  // plus the exact shape plus x_k; its quantiles are outputs 1..31 of each
+  // channel.
+  const float lnxk = kSrLnX0 + kSrH * (float)lane;
+  const float xk = __expf(lnxk);
+  const float planck = logf(expm1f(xk));
+  const float shx[3] = {3.0f * lnxk - planck + xk, 5.0f * lnxk - planck + xk, a.brems_a * lnxk};
+  int qsrc[3];
+#pragma unroll
+  for (int it = 0; it < 3; ++it) {
+    const int e = lane + 32 * it;  // entry 96 + e
+    qsrc[it] = e < 93 ? 32 * (e / 31) + 1 + e % 31 : -1;
+  }
+  const float x2 = xk * xk;
+  for (int c = warp; c < nc; c += 2 * (kSrMlpThreads / 32)) {
+    const int c1 = c + kSrMlpThreads / 32;
+    const bool w0 = cs[c].mode != 0, w1 = c1 < nc && cs[c1].mode != 0;
+    float v0[6], v1[6];
+    if (w0) sr_record_entries(a, cs[c], sOut + c * kSrOutStride, x2, shx, qsrc, lane, v0);
+    if (w1) sr_record_entries(a, cs[c1], sOut + c1 * kSrOutStride, x2, shx, qsrc, lane, v1);
+    if (w0) {
+      float* r0 = a.sr + (size_t)(c0 + c) * kSrLen;
+#pragma unroll
+      for (int it = 0; it < 6; ++it) r0[lane + 32 * it] = v0[it];
+    }
+    if (w1) {
+      float* r1 = a.sr + (size_t)(c0 + c1) * kSrLen;
+#pragma unroll
+      for (int it = 0; it < 6; ++it) r1[lane + 32 * it] = v1[it];
     }
   }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (warp == 0) tmem_free(tmem, 256);
 }
 
 cudaError_t sr_init_kernels() {
@@ -284,7 +388,7 @@ cudaError_t sr_init_kernels() {
 
 cudaError_t launch_sr_mlp(const SrArgs& a, cudaStream_t st) {
   if (a.ncells <= 0) return cudaSuccess;
-  sr_mlp_kernel<<<(a.ncells + 3) / 4, kSrMlpThreads, kSrMlpSmem, st>>>(a);
+  sr_mlp_kernel<<<(a.ncells + 127) / 128, kSrMlpThreads, kSrMlpSmem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -147,8 +147,19 @@ void sur_targets(double x, const SurCell& c, const double* knots93, double* out9
   }
 }
 
-void sur_knots(const SurCell& c, double* knots93) {
-  for (int ch = 0; ch < 3; ++ch) sur_quantiles(ch, c, knots93 + 31 * ch);
+void sur_knots(const SurCell& c, double* knots93, const double* universal) {
+  sur_quantiles(0, c, knots93);
+  if (universal) {
+    for (int q = 31; q < 93; ++q) knots93[q] = universal[q];
+    return;
+  }
+  for (int ch = 1; ch < 3; ++ch) sur_quantiles(ch, c, knots93 + 31 * ch);
+}
+
+void sur_universal_knots(double brems_shape, double* knots93) {
+  // the Compton-like and bremsstrahlung number spectra in x do not depend on
+  // the cell: any cell gives their quantiles
+  sur_knots(sur_cell(1.0, 1e24, 1.0, brems_shape), knots93, nullptr);
 }
 
 void sur_features(double x, double kT, double ne, double Z, float* f) {
@@ -164,10 +175,7 @@ void sur_feature_xkt(const float* f, double* x, double* kT) {
 }
 
 double sur_shape(int o, double x, double kT, double a) {
-  if (o == 0) {
-    const double s = 4.0 * x * x / (kT * kT);
-    return 3.0 * std::log(x) - std::log(std::expm1(x)) + std::log(std::min(0.5 * s, std::log1p(s)));
-  }
+  if (o == 0) return 3.0 * std::log(x) - std::log(std::expm1(x)) + std::log(prim_F(4.0 * x * x / (kT * kT)));
   if (o == 32) return 5.0 * std::log(x) - std::log(std::expm1(x));
   if (o == 64) return a * std::log(x) - x;
   return 0.0;
@@ -199,6 +207,8 @@ void sur_training_set(int ncells, int xpc, uint64_t seed, double brems_shape, st
   }
   X.assign((size_t)ncells * xpc * 4, 0.f);
   Y.assign((size_t)ncells * xpc * 96, 0.0);
+  double uni[93];
+  sur_universal_knots(brems_shape, uni);
   const int nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
   std::vector<std::thread> th;
   for (int t = 0; t < nth; ++t) {
@@ -207,7 +217,7 @@ void sur_training_set(int ncells, int xpc, uint64_t seed, double brems_shape, st
       for (int i = t; i < ncells; i += nth) {
         const Draw& d = cells[i];
         const SurCell c = sur_cell(d.T, d.ne, d.Z, brems_shape);
-        sur_knots(c, knots);
+        sur_knots(c, knots, uni);
         const double kT = c.kappa / d.T;
         for (int k = 0; k < xpc; ++k) {
           const size_t r = (size_t)i * xpc + k;
@@ -229,12 +239,13 @@ extern "C" {
 
 axpic_status axpic_surrogate_targets(const double* in, int32_t n, double brems_shape, double* out) {
   if (n < 0 || (n > 0 && (!in || !out)) || !(brems_shape > 0)) return AXPIC_E_INVALID;
-  double knots[93];
+  double knots[93], uni[93];
+  if (n > 0) axpic::sur_universal_knots(brems_shape, uni);
   for (int32_t r = 0; r < n; ++r) {
     const double x = in[4 * r], kT = in[4 * r + 1], ne = in[4 * r + 2], Z = in[4 * r + 3];
     if (!(x > 0) || !(kT > 0) || !(ne > 0) || (Z != 1.0 && Z != 2.0)) return AXPIC_E_INVALID;
     const axpic::SurCell c = axpic::sur_cell(axpic::sur_temperature(kT, ne, Z), ne, Z, brems_shape);
-    axpic::sur_knots(c, knots);
+    axpic::sur_knots(c, knots, uni);
     axpic::sur_targets(x, c, knots, out + 96 * (size_t)r);
   }
   return AXPIC_OK;

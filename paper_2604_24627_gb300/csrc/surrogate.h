@@ -22,18 +22,22 @@ SurCell sur_cell(double T, double ne, double Z, double brems_shape);
 double sur_emissivity(int ch, double x, const SurCell& c);
 // quantiles x(u_j), j = 1..31, of channel c's number spectrum on [0.05, 20]
 void sur_quantiles(int ch, const SurCell& c, double* out31);
-void sur_knots(const SurCell& c, double* knots93);
+// all 93 quantiles of a cell; universal (from sur_universal_knots, or NULL)
+// supplies the cell-independent Compton-like and bremsstrahlung ones
+void sur_knots(const SurCell& c, double* knots93, const double* universal = nullptr);
+void sur_universal_knots(double brems_shape, double* knots93);
 void sur_targets(double x, const SurCell& c, const double* knots93, double* out96);
 void sur_features(double x, double kT, double ne, double Z, float* f4);
 // x and kappa/T back from the features (inverse of the maps of sur_features)
 void sur_feature_xkt(const float* f4, double* x, double* kT);
 // The fixed part of output o of the network's model: for the ln-emissivity
-// outputs (o = 0, 32, 64) the channel's x-shape, zero for the quantiles:
-//   Primakoff      3 ln x - ln(e^x - 1) + ln min(s/2, ln(1 + s)), s = 4 x^2 / (kappa/T)^2
+// outputs (o = 0, 32, 64) the channel's exact x-dependence at fixed cell,
+// zero for the quantiles:
+//   Primakoff      3 ln x - ln(e^x - 1) + ln F(s), s = 4 x^2 / (kappa/T)^2
 //   Compton-like   5 ln x - ln(e^x - 1)
 //   bremsstrahlung a ln x - x
-// (the Planck / Boltzmann factors and the small- and large-s limits of the
-// screening function F, an upper bound of F).
+// with F the screening function of Sec. II.F. What is left of each
+// ln-emissivity is a function of the cell alone.
 double sur_shape(int o, double x, double kT, double a);
 // ncells random cells of the domain (T uniform, n_e log-uniform, Z in {1, 2})
 // with xpc log-uniform x each: features X (rows x 4) and targets Y (rows x 96)

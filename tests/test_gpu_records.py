@@ -130,7 +130,7 @@ def test_surrogate_records_match_oracle_network():
     for c in range(len(T)):
         cs, _ = S.cell(T[c], ne[c], 1)
         X = S.features(S.X_GRID, cs.kappa_keV / T[c], ne[c], 1)
-        z, _ = S.forward(P, X, bf16_mma=True)
+        z, _ = S.forward(P, S.cell_features(X), bf16_mma=True)
         y = S.model_output(z, X, mu, sigma, skip)
         for ch in range(3):
             want = y[:, 32 * ch] + S.X_GRID
@@ -163,13 +163,56 @@ def test_untrusted_cells_keep_the_table():
     ref.close()
 
 
+def test_mixed_trust_records():
+    """One fused launch over three CTAs of 128 cells (the last one ragged):
+    cells whose four trust nodes pass get the network's record, the others
+    the table's, bit for bit as the table model writes it, and every cell's
+    constants (couplings, T) are the table model's."""
+    rng = np.random.default_rng(21)
+    n = 300
+    T = rng.uniform(0.6, 9.5, n)
+    ne = 10 ** rng.uniform(23.3, 25.9, n)
+    kw = dict(counts=(8, 8, 4), caps=(16, 64, 64))
+    ref = make(T, ne, params(1), **kw)
+    pl = make(T, ne, params(2), **kw)
+    P, mu, sigma, skip = seeded_net(6)
+    net = SurrogateNet()
+    net.set_params(P)
+    _lib.axpic_mlp_set_norm(net.h, mu, sigma)
+    _lib.axpic_mlp_set_skip(net.h, skip)
+    nT = nne = 4
+    err = np.ones((2, nne, nT, 2), dtype=np.float32)
+    err[:, :, :2, 0] = 0.0  # the nodes at the two lowest temperatures pass
+    _lib.axpic_set_surrogate(pl.ctx, net.h, err.ravel(), nT, nne, 1e-3)
+    a = _lib.axpic_get_spectral_records(pl.ctx, 0, n)
+    b = _lib.axpic_get_spectral_records(ref.ctx, 0, n)
+    t1 = S.T_LO + (S.T_HI - S.T_LO) / (nT - 1)
+    trusted, untrusted = T < t1 - 1e-3, T > t1 + 1e-3
+    assert trusted.sum() > 40 and untrusted.sum() > 150
+    assert np.array_equal(a[untrusted], b[untrusted])
+    assert np.array_equal(a[:, 189:], b[:, 189:])
+    assert not np.array_equal(a[trusted, :189], b[trusted, :189])
+    for c in np.flatnonzero(trusted)[::9]:
+        cs, _ = S.cell(T[c], ne[c], 1)
+        X = S.features(S.X_GRID, cs.kappa_keV / T[c], ne[c], 1)
+        z, _ = S.forward(P, S.cell_features(X), bf16_mma=True)
+        y = S.model_output(z, X, mu, sigma, skip)
+        for ch in range(3):
+            want = y[:, 32 * ch] + S.X_GRID
+            d = np.abs(a[c, 32 * ch:32 * ch + 32] - want)
+            assert d.max() <= 2e-2 * max(1.0, np.abs(want).max()), (c, ch, d.max())
+    net.close()
+    pl.close()
+    ref.close()
+
+
 def test_training_on_gpu_learns_the_targets():
     """The network trained by the library's own kernels on the library's
     quadrature targets: its rate and quantile errors beat those of an
     untrained network with the same output model (shape, linear map and
     normalisation) by a wide margin (what training gains)."""
     net = SurrogateNet()
-    loss = _lib.axpic_surrogate_fit(net.h, 512, 16, 1500, 2048, 3e-3, 11)
+    loss = _lib.axpic_surrogate_fit(net.h, 4096, 1, 1500, 2048, 3e-3, 11)
     eL, eQ = _lib.axpic_surrogate_validate(net.h, 5, 4)
     P0 = S.init_params(np.random.default_rng(0))
     net0 = SurrogateNet()

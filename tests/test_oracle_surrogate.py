@@ -103,37 +103,54 @@ def _residual(ch, x, T, ne, Z):
 
 
 def test_shapes_leave_cell_constants():
-    """The Compton-like and bremsstrahlung x-shapes are the spectra's exact
-    x-dependence: what they leave is constant in x, and for Compton-like it
-    is linear in the features (ln Q_C = ln n_e + 6 ln T + const, ln T linear
-    in ln n_e and ln(kappa/T)), so the FP32 linear map carries it exactly."""
-    x = np.geomspace(S.X_LO, S.X_HI, 40)
-    rows, Yc = [], []
-    for T, ne, Z in ((0.7, 2e23, 1), (3.0, 6e25, 1), (9.0, 1e24, 2), (1.5, 5e25, 2), (5.0, 3e23, 1),
-                     (2.2, 8e24, 2), (6.5, 2e25, 1)):
-        for ch in ("compton", "brems"):
-            r, X = _residual(ch, x, T, ne, Z)
-            assert np.ptp(r) < 1e-12 * max(1.0, np.abs(r).max()), (ch, T, ne, Z, np.ptp(r))
-        r, X = _residual("compton", x[:1], T, ne, Z)
-        rows.append(np.r_[1.0, X[0]])
-        Yc.append(r[0])
-    c, *_ = np.linalg.lstsq(np.array(rows), np.array(Yc), rcond=None)
-    assert np.abs(np.array(rows) @ c - np.array(Yc)).max() < 1e-9
-
-
-@pytest.mark.parametrize("T,ne,Z", [(0.5, 1e26, 2), (3.0, 6e25, 1), (10.0, 1e23, 1)])
-def test_primakoff_shape_bounds_the_screening_function(T, ne, Z):
-    """Primakoff: what the x-shape leaves is ln F(s) - ln min(s/2, ln(1+s))
-    plus a cell constant; F <= min(s/2, ln(1+s)) with equality in both limits
-    and ratio at least 0.6 (its minimum, near s = 2.5), so the residual spans
-    at most ln(0.6) ~ -0.51 in x."""
+    """Each channel's x-shape is its spectrum's exact x-dependence: what it
+    leaves is constant in x (for Primakoff over s = 4x^2/(kappa/T)^2 from
+    below 1e-5 to above 1e6, both limits of F and its series branch). For
+    Compton-like and Primakoff that constant is linear in the cell features
+    (ln Q_C = ln n_e + 6 ln T + const; the Primakoff factor is n_i Z^2 T^4
+    times constants; ln T is linear in ln n_e and ln(kappa/T), and Z takes two
+    values), so the FP32 linear map carries both rates exactly."""
     x = np.geomspace(S.X_LO, S.X_HI, 400)
-    r, _ = _residual("primakoff", x, T, ne, Z)
-    kT = S.kappa_over_T(T, ne, Z)
+    rows, Yc, Yp = [], [], []
+    for T, ne, Z in ((0.7, 2e23, 1), (3.0, 6e25, 1), (9.0, 1e24, 2), (1.5, 5e25, 2), (5.0, 3e23, 1),
+                     (2.2, 8e24, 2), (6.5, 2e25, 1), (0.5, 1e26, 2), (10.0, 1e23, 1)):
+        for ch in ("primakoff", "compton", "brems"):
+            r, X = _residual(ch, x, T, ne, Z)
+            assert np.ptp(r) < 1e-11 * max(1.0, np.abs(r).max()), (ch, T, ne, Z, np.ptp(r))
+        rows.append(np.r_[1.0, S.cell_features(X[:1])[0, 1:]])
+        Yc.append(_residual("compton", x[:1], T, ne, Z)[0][0])
+        Yp.append(_residual("primakoff", x[:1], T, ne, Z)[0][0])
+    A = np.array(rows)
+    for Y in (Yc, Yp):
+        c, *_ = np.linalg.lstsq(A, np.array(Y), rcond=None)
+        assert np.abs(A @ c - np.array(Y)).max() < 1e-9
+
+
+def test_primakoff_shape_spans_both_screening_limits():
+    """The s range of the domain's rows reaches both limits of F: s/2 (weak
+    screening) and ln s - 1 (strong), where a bound such as min(s/2, ln(1+s))
+    would leave an x-dependent residual of up to ln 0.6."""
+    X = S.features(np.array([S.X_LO, S.X_HI]), np.array([S.KT_HI, S.KT_LO]), 1e25, 1)
+    x = S.X_LO * (S.X_HI / S.X_LO) ** (0.5 * (X[:, 0] + 1.0))
+    kT = S.KT_LO * (S.KT_HI / S.KT_LO) ** (0.5 * (X[:, 1] + 1.0))
     s = 4 * x ** 2 / kT ** 2
-    ratio = np.log(plasma.primakoff_F(s) / np.minimum(s / 2, np.log1p(s)))
-    assert np.all(ratio <= 1e-12) and ratio.min() > math.log(0.59)
-    np.testing.assert_allclose(r - ratio, (r - ratio)[0], atol=1e-9)
+    assert s[0] < 1e-5 and s[1] > 1e6
+    F = plasma.primakoff_F(s)
+    assert abs(F[0] / (s[0] / 2) - 1) < 1e-5 and abs(F[1] / (np.log(s[1]) - 1) - 1) < 1e-5
+
+
+def test_model_output_depends_on_x_only_through_the_shape():
+    """The learned part (mu + S f_c + sigma z) sees the cell features: rows of
+    one cell at different x differ by the shapes alone, whatever S holds in
+    its ln x column."""
+    rng = np.random.default_rng(3)
+    X = S.features(np.array([0.1, 2.0, 15.0]), 0.9, 3e24, 2)
+    mu, sigma, skip = rng.normal(size=96), rng.uniform(0.5, 2, 96), rng.normal(size=(96, 4))
+    P = S.init_params(rng)
+    z, _ = S.forward(P, S.cell_features(X))
+    assert np.ptp(z, axis=0).max() == 0.0
+    y = S.model_output(z, X, mu, sigma, skip) - S.shape(X)
+    assert np.ptp(y, axis=0).max() < 1e-12
 
 
 def test_features_span_the_domain():
