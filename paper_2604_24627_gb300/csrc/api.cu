@@ -92,6 +92,7 @@ struct axpic_ctx {
   float* sur_sigma = nullptr;
   float* sur_skip = nullptr;
   uint8_t* sur_trust = nullptr;
+  uint8_t* sr_grp = nullptr;  // [ceil(ncells / 32)]: 1 where the network kernel wrote all 32 records
   void* sur_W16 = nullptr;  // layers 2 and 3 laid out for the tensor cores
   int sr_nkt = 0, sr_nne = 0, tnT = 0, tnne = 0, sur_set = 0, sur_any_trusted = 0;
   float ln_gP = 0.f, ln_gA = 0.f;
@@ -271,20 +272,22 @@ static SrArgs make_sr_args(axpic_ctx* ctx) {
   // no trusted node: the network is never evaluated (every cell keeps the table)
   a.trust = ctx->sur_set && ctx->sur_any_trusted ? ctx->sur_trust : nullptr;
   a.W16 = ctx->sur_W16;
+  a.grp = ctx->sr_grp;
   a.tnT = ctx->tnT;
   a.tnne = ctx->tnne;
   a.err = ctx->err;
   return a;
 }
 
-// Rebuilds every cell's spectral record for its current T: the table kernel
-// and, once a network is trusted somewhere, the fused network kernel; each
-// writes the cells the other skips (trusted: network).
+// Rebuilds every cell's spectral record for its current T: once a network is
+// trusted somewhere, the fused network kernel writes the cells where it is
+// trusted and marks the 32-cell groups it wrote whole; the table kernel then
+// writes the rest (its CTAs of marked groups exit at once).
 static cudaError_t build_records(axpic_ctx* ctx, cudaStream_t st) {
   if (!ctx->prm.rate_model) return cudaSuccess;
   const SrArgs a = make_sr_args(ctx);
-  cudaError_t e = launch_sr_table(a, st);
-  if (!e && a.trust) e = launch_sr_mlp(a, st);
+  cudaError_t e = a.trust ? launch_sr_mlp(a, st) : cudaSuccess;
+  if (!e) e = launch_sr_table(a, st);
   return e;
 }
 
@@ -312,7 +315,8 @@ static void free_ctx(axpic_ctx* ctx) {
   void* bufs[] = {ctx->rec,    ctx->mom,   ctx->xbuf,     ctx->res, ctx->diag,    ctx->photon_start,
                   ctx->tables, ctx->tally, ctx->counters, ctx->err, ctx->scratch, ctx->bits,
                   ctx->recA,   ctx->recG,  ctx->recE,     ctx->step_dev, ctx->sr, ctx->srtab,
-                  ctx->sur_P,  ctx->sur_mu, ctx->sur_sigma, ctx->sur_trust, ctx->sur_W16, ctx->sur_skip};
+                  ctx->sur_P,  ctx->sur_mu, ctx->sur_sigma, ctx->sur_trust, ctx->sur_W16, ctx->sur_skip,
+                  ctx->sr_grp};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete ctx;
@@ -449,6 +453,7 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
   ALLOC(ctx->step_dev, sizeof(uint32_t) * kMaxBranches);
   if (p.rate_model) {
     ALLOC(ctx->sr, sizeof(float) * kSrLen * (size_t)n);
+    ALLOC(ctx->sr_grp, (size_t)(n + 31) / 32);
     ALLOC(ctx->srtab, sizeof(float) * kSrTabOut * 2 * (size_t)ctx->sr_nkt * ctx->sr_nne);
     ALLOC(ctx->sur_P, sizeof(float) * AXPIC_MLP_PARAMS);
     ALLOC(ctx->sur_mu, sizeof(float) * 96);

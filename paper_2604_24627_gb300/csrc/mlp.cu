@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(GemmArgs g) {
             atomicAdd(g.C + (long)m * g.ldc + n, v);
           } else {
             if (g.bias) v += g.bias[n];
-            if (g.act == 1) v = tanhf(v);
+            if (g.act == 1) v = act_tanh(v);
             g.C[(long)m * g.ldc + n] = v;
           }
         }
@@ -154,7 +154,7 @@ __global__ void layer1_kernel(const float* __restrict__ X, const float* __restri
   float a = b1[j];
 #pragma unroll
   for (int k = 0; k < 4; ++k) a = fmaf(x[k], W1[k * 64 + j], a);
-  H1[i] = tanhf(a);
+  H1[i] = act_tanh(a);
 }
 
 // dz = 2 (z - t) / n per element; the loss sum (z - t)^2 / n in FP64.
@@ -551,7 +551,7 @@ axpic_status axpic_surrogate_fit(axpic_mlp* h, int32_t ncells, int32_t x_per_cel
   // kRateWeight on the ln-emissivity outputs so that their errors weigh more
   // in the loss.
 #ifndef AXPIC_RATE_WEIGHT
-#define AXPIC_RATE_WEIGHT 4.0
+#define AXPIC_RATE_WEIGHT 16.0
 #endif
   constexpr double kRateWeight = AXPIC_RATE_WEIGHT;
   for (size_t r = 0; r < n; ++r) {
@@ -594,8 +594,21 @@ axpic_status axpic_surrogate_fit(axpic_mlp* h, int32_t ncells, int32_t x_per_cel
       Y[r * 96 + k] -= lin;
       var[k] += Y[r * 96 + k] * Y[r * 96 + k];
     }
-  for (int k = 0; k < 96; ++k)
-    h->sigma[k] = (float)(std::max(std::sqrt(var[k] / (double)n), 1e-6) / (k % 32 == 0 ? kRateWeight : 1.0));
+  // Floors on sigma: what is left below them (the binary32 rounding of mu + S
+  // f on the outputs the linear map already carries exactly) is not the
+  // network's to learn. 1e-4 in ln rate (a tenth of the rate bound), 1e-5 in
+  // x on the quantiles.
+#ifndef AXPIC_SIGMA_FLOOR_RATE
+#define AXPIC_SIGMA_FLOOR_RATE 1e-4
+#endif
+#ifndef AXPIC_SIGMA_FLOOR_Q
+#define AXPIC_SIGMA_FLOOR_Q 1e-5
+#endif
+  for (int k = 0; k < 96; ++k) {
+    const bool rate = k % 32 == 0;
+    const double floor = rate ? AXPIC_SIGMA_FLOOR_RATE : AXPIC_SIGMA_FLOOR_Q;
+    h->sigma[k] = (float)(std::max(std::sqrt(var[k] / (double)n), floor) / (rate ? kRateWeight : 1.0));
+  }
   std::vector<float> Zt(n * 96);
   for (size_t r = 0; r < n; ++r)
     for (int k = 0; k < 96; ++k) Zt[r * 96 + k] = (float)(Y[r * 96 + k] / h->sigma[k]);

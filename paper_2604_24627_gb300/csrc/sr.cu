@@ -53,12 +53,21 @@ void build_sr_table(int nkt, int nne, double brems_shape, float* out) {
 }
 
 // Cell quantities the records need: T, kappa/T, n_e.
-__device__ __forceinline__ void sr_cell(const SrArgs& a, int cell, float* T, float* kT, float* ne) {
+struct SrCellIn {
+  float T, kT;
+  float lkT, lne;  // ln(kappa/T), log10 n_e
+};
+__device__ __forceinline__ SrCellIn sr_cell(const SrArgs& a, int cell) {
   const float* rec = a.rec + (size_t)cell * kRecLen;
-  *T = rec[R_T];
-  *kT = 2.0f * rsqrtf(rec[R_FOURK2]) / *T;
-  *ne = rec[R_NE] * 1e24f;
+  SrCellIn c;
+  c.T = rec[R_T];
+  c.kT = 2.0f * rsqrtf(rec[R_FOURK2]) / c.T;
+  c.lkT = __logf(c.kT);
+  c.lne = log10f(rec[R_NE] * 1e24f);
+  return c;
 }
+// a cell beyond the launch's cells (its values are never used)
+__device__ __forceinline__ SrCellIn sr_cell_none() { return SrCellIn{1.f, 1.f, 0.f, 24.f}; }
 
 // A cell's table interpolation constants: the corner node (i, j) at the
 // cell's Z, the weights in (ln kappa/T, log10 n_e), and the record's
@@ -68,9 +77,10 @@ struct SrInterp {
   float fu, fv, lnKP, lnKA, T;
 };
 
-__device__ __forceinline__ void sr_interp(const SrArgs& a, float T, float kT, float ne, SrInterp* q) {
-  float u = (__logf(kT) - kSrLnKt0) / kSrLnKtSpan * (a.nkt - 1);
-  float v = (log10f(ne) - 23.0f) / 3.0f * (a.nne - 1);
+__device__ __forceinline__ void sr_interp(const SrArgs& a, const SrCellIn& c, SrInterp* q) {
+  const float T = c.T;
+  float u = (c.lkT - kSrLnKt0) / kSrLnKtSpan * (a.nkt - 1);
+  float v = (c.lne - 23.0f) / 3.0f * (a.nne - 1);
   u = fminf(fmaxf(u, 0.f), (float)(a.nkt - 1));
   v = fminf(fmaxf(v, 0.f), (float)(a.nne - 1));
   const int i = min((int)u, a.nkt - 2), j = min((int)v, a.nne - 2);
@@ -96,9 +106,9 @@ __device__ __forceinline__ float sr_table_entry(const SrArgs& a, const SrInterp&
 
 // Whether the network is trusted at (T, n_e, Z): the four validation nodes
 // around it all passed.
-__device__ __forceinline__ bool sr_trusted(const SrArgs& a, float T, float ne, float Z) {
-  float fu = (T - (float)kSurTLo) / (float)(kSurTHi - kSurTLo) * (a.tnT - 1);
-  float fv = (log10f(ne) - 23.0f) / 3.0f * (a.tnne - 1);
+__device__ __forceinline__ bool sr_trusted(const SrArgs& a, const SrCellIn& c, float Z) {
+  float fu = (c.T - (float)kSurTLo) / (float)(kSurTHi - kSurTLo) * (a.tnT - 1);
+  float fv = (c.lne - 23.0f) / 3.0f * (a.tnne - 1);
   // inside the validated grid (binary32 rounding at its edges tolerated)
   const float tol = 1e-4f;
   if (!(fu >= -tol && fu <= (float)(a.tnT - 1) + tol && fv >= -tol && fv <= (float)(a.tnne - 1) + tol)) return false;
@@ -114,18 +124,19 @@ __device__ __forceinline__ bool sr_trusted(const SrArgs& a, float T, float ne, f
 // (lane per cell) in shared memory, then the CTA's threads stream the 32 x
 // 192 record entries (consecutive threads, consecutive entries of a cell).
 // With a trust map (surrogate model) the cells where the network is trusted
-// are left to the network kernel.
+// are left to the network kernel, which ran before: a group it wrote whole
+// exits at once.
 constexpr int kSrTableThreads = 256;
 __global__ void __launch_bounds__(kSrTableThreads) sr_table_kernel(SrArgs a) {
   __shared__ SrInterp ip[32];
   __shared__ int skip[32];
+  if (a.trust && a.grp[blockIdx.x]) return;
   const int c0 = blockIdx.x * 32;
   const int nc = min(32, a.ncells - c0);
   if (threadIdx.x < 32 && (int)threadIdx.x < nc) {
-    float T, kT, ne;
-    sr_cell(a, c0 + threadIdx.x, &T, &kT, &ne);
-    sr_interp(a, T, kT, ne, &ip[threadIdx.x]);
-    skip[threadIdx.x] = a.trust && sr_trusted(a, T, ne, a.Z);
+    const SrCellIn c = sr_cell(a, c0 + threadIdx.x);
+    sr_interp(a, c, &ip[threadIdx.x]);
+    skip[threadIdx.x] = a.trust && sr_trusted(a, c, a.Z);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < nc * kSrLen; e += kSrTableThreads) {
@@ -141,15 +152,17 @@ cudaError_t launch_sr_table(const SrArgs& a, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- fused network
-// CTA = 128 cells (thread = cell = MMA row); it writes the records of the
-// cells where the network is trusted (the table kernel skips them) and exits
-// at once when it has none. Shared memory: A1, A2 (128 x 64
-// bfloat16, core-matrix layout), W2^T (64 x 64), W3^T (96 x 64); once layer
-// 3 has run, the same bytes hold the 128 cells' 96 outputs (FP32, row stride
-// 97, so that a column is conflict-free), from which each warp writes whole
-// records with coalesced stores. Tensor memory: 128 columns, layer 2 in
-// [0, 64), then layer 3 in [0, 96) after layer 2's values were read out.
-constexpr int kSrMlpThreads = 128;
+// CTA = 128 cells (MMA row r = cell) and 256 threads: thread t takes row
+// t % 128 and half t / 128 of each layer's columns (the warps w and w + 4 read
+// the same tensor-memory lanes). It writes the records of the cells where
+// the network is trusted (the table kernel skips them) and exits at once
+// when it has none. Shared memory: A1, A2 (128 x 64 bfloat16, core-matrix
+// layout), W2^T (64 x 64), W3^T (96 x 64); once layer 3 has run, the same
+// bytes hold the 128 cells' 96 outputs (FP32, row stride 97, so that a column
+// is conflict-free), from which each warp writes whole records with
+// coalesced stores. Tensor memory: 128 columns, layer 2 in [0, 64), then
+// layer 3 in [0, 96) after layer 2's values were read out.
+constexpr int kSrMlpThreads = 256;
 constexpr int kSrOutStride = 97;
 constexpr size_t kSrMlpOperands = (size_t)(128 * 64 * 2 + 64 * 64 + 96 * 64) * sizeof(__nv_bfloat16);
 constexpr size_t kSrMlpStage = (size_t)128 * kSrOutStride * sizeof(float);
@@ -159,19 +172,15 @@ constexpr size_t kSrMlpSmem = kSrMlpOperands > kSrMlpStage ? kSrMlpOperands : kS
 // II.F, in binary32: below s = 1/2 the alternating series
 // sum_n (-1)^(n+1) s^n / (n (n + 1)) to n = 12 (truncation under 4e-6
 // relative), above it the closed form, whose cancellation costs at most a
-// factor 6 on the rounding of its logarithm.
+// factor 6 on the rounding of its logarithm. Both forms are taken and one
+// selected: the 32 lanes of a record row span both sides.
 __device__ __forceinline__ float sr_prim_lnF(float s) {
-  float F;
-  if (s < 0.5f) {
-    float p = -1.0f / 156.0f;  // n = 12
+  float p = -1.0f / 156.0f;  // n = 12
 #pragma unroll
-    for (int n = 11; n >= 1; --n) p = fmaf(p, s, ((n & 1) ? 1.0f : -1.0f) / (float)(n * (n + 1)));
-    F = p * s;
-  } else {
-    const float L = __logf(1.0f + s);
-    F = fmaf(L, __frcp_rn(s), L) - 1.0f;
-  }
-  return __logf(F);
+  for (int n = 11; n >= 1; --n) p = fmaf(p, s, ((n & 1) ? 1.0f : -1.0f) / (float)(n * (n + 1)));
+  const float L = __logf(1.0f + s);
+  const float closed = L + __fdividef(L, s) - 1.0f;
+  return __logf(s < 0.5f ? p * s : closed);
 }
 
 // Layers 2 and 3 as B^T (N x K = 64) bfloat16 in the core-matrix layout, laid
@@ -203,27 +212,48 @@ struct SrCellSlot {
 // network's outputs y (shared memory), or from the table (mode 2).
 // shx: the lane's fixed shape terms (Primakoff and Compton-like Planck
 // factors, bremsstrahlung power, each plus x_k); qsrc: the network output of
-// the lane's quantile entries (-1: a per-cell constant).
+// the lane's quantile entries (-1 on lanes 29..31 of the last row: the
+// per-cell constants).
 __device__ __forceinline__ void sr_record_entries(const SrArgs& a, const SrCellSlot& c, const float* y, float x2,
                                                   const float* shx, const int* qsrc, int lane, float* v) {
   if (c.mode == 1) {
     v[0] = y[0] + shx[0] + sr_prim_lnF(x2 * c.s_per_x2);
     v[1] = y[32] + shx[1];
     v[2] = y[64] + shx[2];
-#pragma unroll
-    for (int it = 0; it < 3; ++it) v[3 + it] = qsrc[it] >= 0 ? y[qsrc[it]] : sr_table_entry(a, c.q, 96 + lane + 32 * it);
+    v[3] = y[qsrc[0]];
+    v[4] = y[qsrc[1]];
+    const float k = lane == 29 ? c.q.lnKP : (lane == 30 ? c.q.lnKA : c.q.T);
+    v[5] = qsrc[2] >= 0 ? y[qsrc[2]] : k;
   } else {
 #pragma unroll
     for (int it = 0; it < 6; ++it) v[it] = sr_table_entry(a, c.q, lane + 32 * it);
   }
 }
 
+// Eight activations (columns j0..j0+7 of row r) as bfloat16 into one 16-byte
+// row of a core matrix.
+__device__ __forceinline__ void store8_bf16(__nv_bfloat16* base, int r, int j0, const float* v) {
+  uint4 u;
+  uint32_t* w = reinterpret_cast<uint32_t*>(&u);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    w[i] = *reinterpret_cast<const uint32_t*>(&h);
+  }
+  *reinterpret_cast<uint4*>(base + core_off(r, j0, 64)) = u;
+}
+
 __global__ void __launch_bounds__(kSrMlpThreads) sr_mlp_kernel(SrArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ SrCellSlot cs[128];
-  // network constants: layer 1 (b1, W1 rows of f1..f3), b2, and the output
-  // affine (mu + sigma b3, sigma, S columns of f1..f3)
-  __shared__ float sL1[4][64], sB2[64], sC3[96], sSig[96], sS[3][96];
+  __shared__ float sF[2][128];  // features f1, f2 of each row
+  // network constants: layer 1 per unit (b1, W1 rows of f1..f3), b2, and the
+  // output affine (mu + sigma b3, sigma, S columns of f1..f3), read as float4
+  __shared__ float4 sL1[64];
+  __shared__ __align__(16) float sB2[64];
+  __shared__ __align__(16) float sC3[96];
+  __shared__ __align__(16) float sSig[96];
+  __shared__ __align__(16) float sS[3][96];
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_base;
   __nv_bfloat16* sA1 = reinterpret_cast<__nv_bfloat16*>(sm);
@@ -232,16 +262,25 @@ __global__ void __launch_bounds__(kSrMlpThreads) sr_mlp_kernel(SrArgs a) {
   __nv_bfloat16* sW3 = sW2 + 64 * 64;
   float* sOut = reinterpret_cast<float*>(sm);  // after layer 3: [128][kSrOutStride]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r = tid & 127, half = tid >> 7;
   const int c0 = blockIdx.x * 128;
   const int nc = min(128, a.ncells - c0);
-  const bool valid = tid < nc;
-  float T = 1.f, kT = 1.f, ne = 1e24f;
-  if (valid) sr_cell(a, c0 + tid, &T, &kT, &ne);
-  const bool trusted = valid && sr_trusted(a, T, ne, a.Z);
-  if (valid) {
-    sr_interp(a, T, kT, ne, &cs[tid].q);
-    cs[tid].s_per_x2 = 4.0f / (kT * kT);
-    cs[tid].mode = trusted ? 1 : 0;
+  bool trusted = false;
+  if (half == 0) {
+    const bool valid = r < nc;
+    const SrCellIn c = valid ? sr_cell(a, c0 + r) : sr_cell_none();
+    trusted = valid && sr_trusted(a, c, a.Z);
+    if (valid) {
+      sr_interp(a, c, &cs[r].q);
+      cs[r].s_per_x2 = 4.0f / (c.kT * c.kT);
+      cs[r].mode = trusted ? 1 : 0;
+    }
+    sF[0][r] = (c.lkT - kSrLnKt0) / kSrLnKtSpan * 2.0f - 1.0f;
+    sF[1][r] = (c.lne - 24.5f) / 1.5f;
+    // the group of 32 cells of this warp: written whole here (the table
+    // kernel's CTA for it exits)
+    const bool whole = __all_sync(0xFFFFFFFFu, trusted || !valid);
+    if (lane == 0 && 32 * warp < nc) a.grp[(c0 >> 5) + warp] = whole ? 1 : 0;
   }
   // no trusted cell here: the table kernel writes all of them
   if (!__syncthreads_or(trusted)) return;
@@ -259,33 +298,36 @@ __global__ void __launch_bounds__(kSrMlpThreads) sr_mlp_kernel(SrArgs a) {
       for (int i = tid; i < (64 * 64 + 96 * 64) / 8; i += kSrMlpThreads) dst[i] = src[i];
     }
     if (tid < 64) {
-      sL1[0][tid] = a.P[kOffB1 + tid];
-#pragma unroll
-      for (int q = 1; q < 4; ++q) sL1[q][tid] = a.P[kOffW1 + q * 64 + tid];
+      sL1[tid] = make_float4(a.P[kOffB1 + tid], a.P[kOffW1 + 64 + tid], a.P[kOffW1 + 128 + tid],
+                             a.P[kOffW1 + 192 + tid]);
       sB2[tid] = a.P[kOffB2 + tid];
-    }
-    if (tid < 96) {
-      sC3[tid] = fmaf(a.sigma[tid], a.P[kOffB3 + tid], a.mu[tid]);
-      sSig[tid] = a.sigma[tid];
+    } else if (tid >= 128 && tid < 128 + 96) {
+      const int o = tid - 128;
+      sC3[o] = fmaf(a.sigma[o], a.P[kOffB3 + o], a.mu[o]);
+      sSig[o] = a.sigma[o];
 #pragma unroll
-      for (int i = 1; i < 4; ++i) sS[i - 1][tid] = a.skip[tid * 4 + i];
+      for (int i = 1; i < 4; ++i) sS[i - 1][o] = a.skip[o * 4 + i];
     }
     __syncthreads();
-    // cell features (the ln x input held at zero) and layer 1 on the CUDA cores
-    const float f1 = (__logf(kT) - kSrLnKt0) / kSrLnKtSpan * 2.0f - 1.0f;
-    const float f2 = (log10f(ne) - 24.5f) / 1.5f;
-    const float f3 = a.Z - 1.5f;
-#pragma unroll 16
-    for (int j = 0; j < 64; ++j) {
-      const float h = fmaf(f3, sL1[3][j], fmaf(f2, sL1[2][j], fmaf(f1, sL1[1][j], sL1[0][j])));
-      sA1[core_off(tid, j, 64)] = __float2bfloat16_rn(tanhf(h));
+    // cell features (the ln x input held at zero) and layer 1 on the CUDA
+    // cores: this thread's 32 of the 64 units
+    const float f1 = sF[0][r], f2 = sF[1][r], f3 = a.Z - 1.5f;
+#pragma unroll
+    for (int j0 = 32 * half; j0 < 32 * half + 32; j0 += 8) {
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float4 w = sL1[j0 + j];
+        v[j] = act_tanh(fmaf(f3, w.w, fmaf(f2, w.z, fmaf(f1, w.y, w.x))));
+      }
+      store8_bf16(sA1, r, j0, v);
     }
     smem_to_async_proxy();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t row = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     const uint32_t lbo = 128, sbo = 8 * 128;
     // layer 2: D[0, 64) = A1 . W2
     if (tid == 0) {
@@ -294,15 +336,29 @@ __global__ void __launch_bounds__(kSrMlpThreads) sr_mlp_kernel(SrArgs a) {
                  mma_idesc(128, 64), s > 0);
       tc_commit(&bar);
     }
-    // warp-uniform, as the tensor-memory loads below are warp-collective
-    ok = __all_sync(0xFFFFFFFFu, mbar_wait(&bar, 0));
+    // warp 0 waits; the others park in the barrier (no issue slots spent
+    // spinning), and the verdict is CTA-uniform
+    {
+      bool w = true;
+      if (warp == 0) w = __all_sync(0xFFFFFFFFu, mbar_wait(&bar, 0));
+      ok = __syncthreads_and(w) != 0;
+    }
     tc_fence_after();
     if (ok) {
-      for (int j0 = 0; j0 < 64; j0 += 16) {
+#pragma unroll
+      for (int j0 = 32 * half; j0 < 32 * half + 32; j0 += 16) {
         float v[16];
         tmem_ld16(row + j0, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) sA2[core_off(tid, j0 + j, 64)] = __float2bfloat16_rn(tanhf(v[j] + sB2[j0 + j]));
+        for (int j = 0; j < 16; j += 4) {
+          const float4 b = *reinterpret_cast<const float4*>(sB2 + j0 + j);
+          v[j] = act_tanh(v[j] + b.x);
+          v[j + 1] = act_tanh(v[j + 1] + b.y);
+          v[j + 2] = act_tanh(v[j + 2] + b.z);
+          v[j + 3] = act_tanh(v[j + 3] + b.w);
+        }
+        store8_bf16(sA2, r, j0, v);
+        store8_bf16(sA2, r, j0 + 8, v + 8);
       }
     }
     smem_to_async_proxy();
@@ -317,41 +373,56 @@ __global__ void __launch_bounds__(kSrMlpThreads) sr_mlp_kernel(SrArgs a) {
       tc_commit(&bar);
     }
     const bool issued3 = ok;
-    if (ok) ok = __all_sync(0xFFFFFFFFu, mbar_wait(&bar, 1));
+    if (ok) {
+      bool w = true;
+      if (warp == 0) w = __all_sync(0xFFFFFFFFu, mbar_wait(&bar, 1));
+      ok = __syncthreads_and(w) != 0;
+    }
     tc_fence_after();
-    if (!ok) {
+    if (!ok && warp == 0) {
       // flag it and give the tensor core a second bounded wait on whatever
       // it may still be doing before the tensor memory is released (the
       // records then come from the table)
-      if (tid == 0) atomicOr(a.err, 2);
+      if (lane == 0) atomicOr(a.err, 2);
       mbar_wait(&bar, issued3 ? 1u : 0u);
     }
-    // every thread's loads of layer 3 are in registers before the operands'
-    // bytes are overwritten with the outputs
-    float y[96];
+    // this thread's 48 outputs in registers before the operands' bytes are
+    // overwritten with the outputs
+    float y[48];
     if (ok) {
 #pragma unroll
-      for (int j0 = 0; j0 < 96; j0 += 16) tmem_ld16(row + j0, y + j0);
+      for (int j0 = 0; j0 < 48; j0 += 16) tmem_ld16(row + 48 * half + j0, y + j0);
     }
     tc_fence_before();
     ok = __syncthreads_and(ok) != 0;
     tc_fence_after();
     if (warp == 0) tmem_free(tmem, 128);
     if (ok) {
-      float* out = sOut + tid * kSrOutStride;
+      float* out = sOut + r * kSrOutStride + 48 * half;
 #pragma unroll
-      for (int o = 0; o < 96; ++o)
-        out[o] = fmaf(sS[2][o], f3, fmaf(sS[1][o], f2, fmaf(sS[0][o], f1, fmaf(sSig[o], y[o], sC3[o]))));
-    } else if (trusted) {
-      cs[tid].mode = 2;  // no network outputs: the table record
+      for (int i = 0; i < 48; i += 4) {
+        const int o = 48 * half + i;
+        const float4 c = *reinterpret_cast<const float4*>(sC3 + o);
+        const float4 g = *reinterpret_cast<const float4*>(sSig + o);
+        const float4 s1 = *reinterpret_cast<const float4*>(sS[0] + o);
+        const float4 s2 = *reinterpret_cast<const float4*>(sS[1] + o);
+        const float4 s3 = *reinterpret_cast<const float4*>(sS[2] + o);
+        out[i] = fmaf(s3.x, f3, fmaf(s2.x, f2, fmaf(s1.x, f1, fmaf(g.x, y[i], c.x))));
+        out[i + 1] = fmaf(s3.y, f3, fmaf(s2.y, f2, fmaf(s1.y, f1, fmaf(g.y, y[i + 1], c.y))));
+        out[i + 2] = fmaf(s3.z, f3, fmaf(s2.z, f2, fmaf(s1.z, f1, fmaf(g.z, y[i + 2], c.z))));
+        out[i + 3] = fmaf(s3.w, f3, fmaf(s2.w, f2, fmaf(s1.w, f1, fmaf(g.w, y[i + 3], c.w))));
+      }
+    } else if (half == 0 && trusted) {
+      cs[r].mode = 2;  // no network outputs: the table record
     }
     __syncthreads();
   }
-  // records: warp w writes cells w, w + 4, ..., two at a time, a cell's 192
+  // records: warp w writes cells w, w + 8, ..., two at a time, a cell's 192
   // entries by its 32 lanes (lane k takes grid point x_k of the three rate
   // rows). A trusted cell's ln-emissivity row is the network's cell constant
   // plus the exact shape plus x_k; its quantiles are outputs 1..31 of each
   // channel.
+  constexpr int kW = kSrMlpThreads / 32;
   const float lnxk = kSrLnX0 + kSrH * (float)lane;
   const float xk = __expf(lnxk);
   const float planck = logf(expm1f(xk));
@@ -359,12 +430,12 @@ __global__ void __launch_bounds__(kSrMlpThreads) sr_mlp_kernel(SrArgs a) {
   int qsrc[3];
 #pragma unroll
   for (int it = 0; it < 3; ++it) {
-    const int e = lane + 32 * it;  // entry 96 + e
+    const int e = lane + 32 * it;  // entry 96 + e: quantile e (e < 93) or a constant
     qsrc[it] = e < 93 ? 32 * (e / 31) + 1 + e % 31 : -1;
   }
   const float x2 = xk * xk;
-  for (int c = warp; c < nc; c += 2 * (kSrMlpThreads / 32)) {
-    const int c1 = c + kSrMlpThreads / 32;
+  for (int c = warp; c < nc; c += 2 * kW) {
+    const int c1 = c + kW;
     const bool w0 = cs[c].mode != 0, w1 = c1 < nc && cs[c1].mode != 0;
     float v0[6], v1[6];
     if (w0) sr_record_entries(a, cs[c], sOut + c * kSrOutStride, x2, shx, qsrc, lane, v0);

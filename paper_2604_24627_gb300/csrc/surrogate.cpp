@@ -60,9 +60,11 @@ SurCell sur_cell(double T, double ne, double Z, double brems_shape) {
   const double eta = (3.0 + XH) * rho2 / (T7 * T7);
   const double afac = (1.0 / (4.0 * kPI)) / 1.60e-23;
   const double epsC = 2.67e-2 * (1.0 + XH) * std::pow(T7, 6.0) * afac;
-  const double epsZ = 0.150 * std::pow(T7, 2.5) * rho2 * (1.0 + XH) * afac * std::max(1e-3, 1.0 - 6.98e-2 * eta);
+  c.bZ = 1.0 - 6.98e-2 * eta;
+  c.bE = 1.0 - 0.140 * eta;
+  const double epsZ = 0.150 * std::pow(T7, 2.5) * rho2 * (1.0 + XH) * afac * std::max(1e-3, c.bZ);
   const double epsE = 0.150 * std::pow(T7, 2.5) * rho2 * (1.0 + XH) * (1.0 + XH) / (2.0 * std::sqrt(2.0)) * afac *
-                      std::max(1e-3, 1.0 - 0.140 * eta);
+                      std::max(1e-3, c.bE);
   c.Q_C = rho * epsC;
   c.Q_B = rho * (epsZ + epsE);
   c.Gamma0_P = kAl * kHcGeV * kHcGeV / 8.0 * zsq * kCl;
@@ -199,9 +201,16 @@ void sur_training_set(int ncells, int xpc, uint64_t seed, double brems_shape, st
   std::vector<Draw> cells(ncells);
   uint64_t s = seed;
   for (auto& d : cells) {
-    d.T = kSurTLo + (kSurTHi - kSurTLo) * unif(s);
-    d.ne = std::pow(10.0, 23.0 + 3.0 * unif(s));
-    d.Z = (mix(s) & 1) ? 2.0 : 1.0;
+    // the network is trained where the bremsstrahlung fit holds (both of its
+    // brackets well above their floor); cells beyond fail validation there
+    // and keep the table
+    do {
+      d.T = kSurTLo + (kSurTHi - kSurTLo) * unif(s);
+      d.ne = std::pow(10.0, 23.0 + 3.0 * unif(s));
+      d.Z = (mix(s) & 1) ? 2.0 : 1.0;
+      const SurCell c = sur_cell(d.T, d.ne, d.Z, brems_shape);
+      if (std::min(c.bZ, c.bE) >= kSurBracketMin) break;
+    } while (true);
     d.x.resize(xpc);
     for (int k = 0; k < xpc; ++k) d.x[k] = kSurXLo * std::pow(kSurXHi / kSurXLo, unif(s));
   }

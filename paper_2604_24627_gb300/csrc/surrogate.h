@@ -13,6 +13,7 @@ constexpr int kSurOut = 96;
 
 struct SurCell {
   double T, ne, Z, a, kappa, Q_C, Q_B, Gamma0_P;
+  double bZ, bE;  // the bremsstrahlung fit's [1 - c eta] brackets before the 1e-3 floor
 };
 
 double sur_temperature(double kT, double ne, double Z);
@@ -39,8 +40,10 @@ void sur_feature_xkt(const float* f4, double* x, double* kT);
 // with F the screening function of Sec. II.F. What is left of each
 // ln-emissivity is a function of the cell alone.
 double sur_shape(int o, double x, double kT, double a);
-// ncells random cells of the domain (T uniform, n_e log-uniform, Z in {1, 2})
-// with xpc log-uniform x each: features X (rows x 4) and targets Y (rows x 96)
+// ncells random cells of the domain (T uniform, n_e log-uniform, Z in {1, 2};
+// only where both bremsstrahlung brackets are at least kSurBracketMin) with
+// xpc log-uniform x each: features X (rows x 4) and targets Y (rows x 96)
+constexpr double kSurBracketMin = 0.05;
 void sur_training_set(int ncells, int xpc, uint64_t seed, double brems_shape, std::vector<float>& X,
                       std::vector<double>& Y);
 
