@@ -348,23 +348,28 @@ const char *axpic_step_kernel_names(const axpic_ctx *ctx);
 
 /* ---------------------------------------------------------------------------
  * The spectral surrogate's network: MLP 4 -> 64 -> 64 -> 96 with tanh hidden
- * layers, FP32 master parameters, bfloat16 tensor-core products with FP32
+ * layers (tanh(v) = 1 - 2 / (e^(2v) + 1) in binary32, absolute error below
+ * 7e-7), FP32 master parameters, bfloat16 tensor-core products with FP32
  * accumulation (layers 2 and 3 and every backward product; layer 1, K = 4,
  * on the CUDA cores). Not part of the paper's method: a learned stand-in for
  * the per-channel spectral emissivity and inverse CDF (see
- * axpic_surrogate_targets). Inputs are the normalised features
- * (ln x, ln(kappa/T), log10 n_e, Z) of axpic_surrogate_features. The
- * network's output z is a normalised residual: the model's output o is
- *   y_o = shape_o(x, kappa/T) + mu_o + sum_i S_oi f_i + sigma_o z_o
- * with f the features, S an FP32 linear map (axpic_mlp_set_skip) and shape_o
- * fixed: for the ln-emissivity outputs (o = 0, 32, 64) the channel's x-shape,
- *   Primakoff      3 ln x - ln(e^x - 1) + ln min(s/2, ln(1 + s)),
- *                  s = 4 x^2 / (kappa/T)^2 (an upper bound of the screening
- *                  function F),
+ * axpic_surrogate_targets). The model's output o at the normalised features
+ * f = (ln x, ln(kappa/T), log10 n_e, Z) of axpic_surrogate_features is
+ *   y_o = shape_o(x, kappa/T) + mu_o + sum_{i=1..3} S_oi f_i + sigma_o z_o,
+ * z the network's output at the cell features (0, f_1, f_2, f_3): shape_o
+ * carries every x-dependence, so the learned part is a function of the cell.
+ * S is an FP32 linear map (axpic_mlp_set_skip; its column i = 0 multiplies
+ * zero) and shape_o is fixed: for the ln-emissivity outputs (o = 0, 32, 64)
+ * the channel's exact x-dependence at fixed cell,
+ *   Primakoff      3 ln x - ln(e^x - 1) + ln F(s), s = 4 x^2 / (kappa/T)^2,
+ *                  F the screening function of Sec. II.F,
  *   Compton-like   5 ln x - ln(e^x - 1),
  *   bremsstrahlung a ln x - x (a = brems_gamma_shape);
- * zero for the quantiles. Calls are ordered on the stream given at creation;
- * those that return host data synchronise it.
+ * zero for the quantiles. After S the Primakoff and Compton-like rates are
+ * exact; the network carries the bremsstrahlung brackets and the Primakoff
+ * quantiles. axpic_mlp_forward and axpic_mlp_gradients take the network's
+ * own inputs (callers pass cell features). Calls are ordered on the stream
+ * given at creation; those that return host data synchronise it.
  * ------------------------------------------------------------------------- */
 typedef struct axpic_mlp axpic_mlp;
 #define AXPIC_MLP_PARAMS 10720 /* W1[4][64], b1[64], W2[64][64], b2[64], W3[64][96], b3[96] */
@@ -414,11 +419,15 @@ axpic_status axpic_surrogate_targets(const double *in, int32_t n, double brems_s
 axpic_status axpic_surrogate_features(const double *in, int32_t n, float *out);
 /* Trains the network from scratch on the GPU: ncells random cells of the
  * domain (T uniform in [0.5, 10] keV, n_e log-uniform in [1e23, 1e26],
- * Z in {1, 2}) with x_per_cell log-uniform x each, targets from
- * axpic_surrogate_targets, per-output normalisation set on the handle;
- * `steps` Adam steps on consecutive batches of `batch` rows with a cosine
- * learning rate from lr to lr / 100. *loss_out (may be NULL): final loss on
- * the whole set (normalised units). Synchronises. */
+ * Z in {1, 2}; only cells where both bremsstrahlung brackets 1 - c eta are
+ * at least 0.05, the region where that fit holds) with x_per_cell
+ * log-uniform x each (the learned part does not depend on x: 1 suffices),
+ * targets from axpic_surrogate_targets. mu and S by least squares, sigma
+ * the residual spread (floors 1e-4 on rates, 1e-5 on quantiles; rates
+ * weighted 16 in the loss) set on the handle; `steps` Adam steps on
+ * consecutive batches of `batch` rows with a cosine learning rate from lr to
+ * lr / 100. *loss_out (may be NULL): final loss on the whole set
+ * (normalised units). Synchronises. */
 axpic_status axpic_surrogate_fit(axpic_mlp *m, int32_t ncells, int32_t x_per_cell, int32_t steps, int32_t batch,
                                  float lr, uint64_t seed, double brems_shape, double *loss_out);
 /* Error of the trained network on a grid of nT temperatures (uniform in
@@ -432,10 +441,13 @@ axpic_status axpic_surrogate_validate(axpic_mlp *m, int32_t nT, int32_t nne, dou
 /* Gives a context with rate_model 2 its network: the parameters, output
  * normalisation and a trust map from axpic_surrogate_validate's err_out
  * (nT x nne x 2 nodes): a cell uses the network where the four nodes around
- * its (T, n_e) at its Z have a rate error <= tol, the table elsewhere. Copies
- * everything (the network may be destroyed afterwards) and rebuilds the
- * spectral records. Synchronises. AXPIC_E_INVALID for another rate model or
- * grid sizes below 2. */
+ * its (T, n_e) at its Z have a rate error <= tol, the table elsewhere (the
+ * error between nodes can exceed the nodes': a tol below the bound wanted
+ * leaves a margin). Copies everything (the network may be destroyed
+ * afterwards) and rebuilds the spectral records: the network kernel writes
+ * the trusted cells (one tensor-core row per cell), the table kernel the
+ * others. Synchronises. AXPIC_E_INVALID for another rate model or grid sizes
+ * below 2. */
 axpic_status axpic_set_surrogate(axpic_ctx *ctx, axpic_mlp *m, const float *err_map, int32_t nT, int32_t nne,
                                  float tol);
 /* The spectral records of cells [first, first + count) (rate models 1 and 2):
