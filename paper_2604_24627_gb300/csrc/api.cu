@@ -92,7 +92,7 @@ struct axpic_ctx {
   float* sur_sigma = nullptr;
   float* sur_skip = nullptr;
   uint8_t* sur_trust = nullptr;
-  uint8_t* sr_grp = nullptr;  // [ceil(ncells / 32)]: 1 where the network kernel wrote all 32 records
+  uint8_t* sr_net = nullptr;  // [ncells]: 1 where the network kernel wrote the record
   void* sur_W16 = nullptr;  // layers 2 and 3 laid out for the tensor cores
   int sr_nkt = 0, sr_nne = 0, tnT = 0, tnne = 0, sur_set = 0, sur_any_trusted = 0;
   float ln_gP = 0.f, ln_gA = 0.f;
@@ -272,7 +272,7 @@ static SrArgs make_sr_args(axpic_ctx* ctx) {
   // no trusted node: the network is never evaluated (every cell keeps the table)
   a.trust = ctx->sur_set && ctx->sur_any_trusted ? ctx->sur_trust : nullptr;
   a.W16 = ctx->sur_W16;
-  a.grp = ctx->sr_grp;
+  a.net = ctx->sr_net;
   a.tnT = ctx->tnT;
   a.tnne = ctx->tnne;
   a.err = ctx->err;
@@ -281,8 +281,8 @@ static SrArgs make_sr_args(axpic_ctx* ctx) {
 
 // Rebuilds every cell's spectral record for its current T: once a network is
 // trusted somewhere, the fused network kernel writes the cells where it is
-// trusted and marks the 32-cell groups it wrote whole; the table kernel then
-// writes the rest (its CTAs of marked groups exit at once).
+// trusted and flags them; the table kernel then writes the rest (its CTAs
+// whose 32 cells are all flagged exit at once).
 static cudaError_t build_records(axpic_ctx* ctx, cudaStream_t st) {
   if (!ctx->prm.rate_model) return cudaSuccess;
   const SrArgs a = make_sr_args(ctx);
@@ -316,7 +316,7 @@ static void free_ctx(axpic_ctx* ctx) {
                   ctx->tables, ctx->tally, ctx->counters, ctx->err, ctx->scratch, ctx->bits,
                   ctx->recA,   ctx->recG,  ctx->recE,     ctx->step_dev, ctx->sr, ctx->srtab,
                   ctx->sur_P,  ctx->sur_mu, ctx->sur_sigma, ctx->sur_trust, ctx->sur_W16, ctx->sur_skip,
-                  ctx->sr_grp};
+                  ctx->sr_net};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete ctx;
@@ -453,7 +453,7 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
   ALLOC(ctx->step_dev, sizeof(uint32_t) * kMaxBranches);
   if (p.rate_model) {
     ALLOC(ctx->sr, sizeof(float) * kSrLen * (size_t)n);
-    ALLOC(ctx->sr_grp, (size_t)(n + 31) / 32);
+    ALLOC(ctx->sr_net, (size_t)n);
     ALLOC(ctx->srtab, sizeof(float) * kSrTabOut * 2 * (size_t)ctx->sr_nkt * ctx->sr_nne);
     ALLOC(ctx->sur_P, sizeof(float) * AXPIC_MLP_PARAMS);
     ALLOC(ctx->sur_mu, sizeof(float) * 96);

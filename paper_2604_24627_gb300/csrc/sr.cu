@@ -77,6 +77,12 @@ struct SrInterp {
   float fu, fv, lnKP, lnKA, T;
 };
 
+// The record's per-cell constants (entries 189, 190).
+__device__ __forceinline__ void sr_consts(const SrArgs& a, float T, float* lnKP, float* lnKA) {
+  *lnKP = fmaf(-4.0f, __logf(T), a.ln_gP);
+  *lnKA = fmaf(-4.0f, __logf(T), a.ln_gA);
+}
+
 __device__ __forceinline__ void sr_interp(const SrArgs& a, const SrCellIn& c, SrInterp* q) {
   const float T = c.T;
   float u = (c.lkT - kSrLnKt0) / kSrLnKtSpan * (a.nkt - 1);
@@ -88,8 +94,7 @@ __device__ __forceinline__ void sr_interp(const SrArgs& a, const SrCellIn& c, Sr
   q->t00 = a.tab + ((size_t)(z * a.nne + j) * a.nkt + i) * kSrTabOut;
   q->fu = u - i;
   q->fv = v - j;
-  q->lnKP = fmaf(-4.0f, __logf(T), a.ln_gP);
-  q->lnKA = fmaf(-4.0f, __logf(T), a.ln_gA);
+  sr_consts(a, T, &q->lnKP, &q->lnKA);
   q->T = T;
 }
 
@@ -123,22 +128,25 @@ __device__ __forceinline__ bool sr_trusted(const SrArgs& a, const SrCellIn& c, f
 // A CTA takes 32 cells: warp 0 forms each cell's interpolation constants
 // (lane per cell) in shared memory, then the CTA's threads stream the 32 x
 // 192 record entries (consecutive threads, consecutive entries of a cell).
-// With a trust map (surrogate model) the cells where the network is trusted
-// are left to the network kernel, which ran before: a group it wrote whole
-// exits at once.
+// With a trust map (surrogate model) the network kernel ran before and
+// flagged the cells it wrote: those are skipped, and a CTA with none left
+// exits.
 constexpr int kSrTableThreads = 256;
 __global__ void __launch_bounds__(kSrTableThreads) sr_table_kernel(SrArgs a) {
   __shared__ SrInterp ip[32];
   __shared__ int skip[32];
-  if (a.trust && a.grp[blockIdx.x]) return;
   const int c0 = blockIdx.x * 32;
   const int nc = min(32, a.ncells - c0);
+  int need = 0;
   if (threadIdx.x < 32 && (int)threadIdx.x < nc) {
-    const SrCellIn c = sr_cell(a, c0 + threadIdx.x);
-    sr_interp(a, c, &ip[threadIdx.x]);
-    skip[threadIdx.x] = a.trust && sr_trusted(a, c, a.Z);
+    const int sk = a.trust ? a.net[c0 + threadIdx.x] : 0;
+    skip[threadIdx.x] = sk;
+    if (!sk) {
+      sr_interp(a, sr_cell(a, c0 + threadIdx.x), &ip[threadIdx.x]);
+      need = 1;
+    }
   }
-  __syncthreads();
+  if (!__syncthreads_or(need)) return;
   for (int e = threadIdx.x; e < nc * kSrLen; e += kSrTableThreads) {
     const int c = e / kSrLen, o = e - c * kSrLen;
     if (!skip[c]) a.sr[(size_t)(c0 + c) * kSrLen + o] = sr_table_entry(a, ip[c], o);
@@ -155,18 +163,23 @@ cudaError_t launch_sr_table(const SrArgs& a, cudaStream_t st) {
 // CTA = 128 cells (MMA row r = cell) and 256 threads: thread t takes row
 // t % 128 and half t / 128 of each layer's columns (the warps w and w + 4 read
 // the same tensor-memory lanes). It writes the records of the cells where
-// the network is trusted (the table kernel skips them) and exits at once
-// when it has none. Shared memory: A1, A2 (128 x 64 bfloat16, core-matrix
-// layout), W2^T (64 x 64), W3^T (96 x 64); once layer 3 has run, the same
-// bytes hold the 128 cells' 96 outputs (FP32, row stride 97, so that a column
-// is conflict-free), from which each warp writes whole records with
-// coalesced stores. Tensor memory: 128 columns, layer 2 in [0, 64), then
-// layer 3 in [0, 96) after layer 2's values were read out.
+// the network is trusted and flags them for the table kernel, which runs
+// next and writes the others; a CTA with no trusted cell exits at once.
+// Dynamic shared memory: A (128 x 64 bfloat16, core-matrix layout: layer 1's
+// activations, then layer 2's over them once layer 2 has run), W2^T
+// (64 x 64), W3^T (96 x 64), layer 1's constants and the rows' features;
+// once layer 3 has run, the same bytes hold the 128 cells' 96 outputs (FP32,
+// row stride 97, so that a column is conflict-free), from which each warp
+// writes whole records with coalesced stores. Four CTAs fit an SM (shared
+// memory, 64 registers a thread, 4 x 128 tensor-memory columns). Tensor
+// memory: 128 columns, layer 2 in [0, 64), then layer 3 in [0, 96) after
+// layer 2's values were read out.
 constexpr int kSrMlpThreads = 256;
 constexpr int kSrOutStride = 97;
-constexpr size_t kSrMlpOperands = (size_t)(128 * 64 * 2 + 64 * 64 + 96 * 64) * sizeof(__nv_bfloat16);
+constexpr size_t kSrOffW2 = 128 * 64 * 2, kSrOffW3 = kSrOffW2 + 64 * 64 * 2, kSrOffL1 = kSrOffW3 + 96 * 64 * 2,
+                 kSrOffB2 = kSrOffL1 + 64 * 16, kSrOffF = kSrOffB2 + 64 * 4, kSrMlpLayers = kSrOffF + 2 * 128 * 4;
 constexpr size_t kSrMlpStage = (size_t)128 * kSrOutStride * sizeof(float);
-constexpr size_t kSrMlpSmem = kSrMlpOperands > kSrMlpStage ? kSrMlpOperands : kSrMlpStage;
+constexpr size_t kSrMlpSmem = kSrMlpLayers > kSrMlpStage ? kSrMlpLayers : kSrMlpStage;
 
 // ln F(s), F(s) = (1 + 1/s) ln(1 + s) - 1 the screening function of Sec.
 // II.F, in binary32: below s = 1/2 the alternating series
@@ -203,31 +216,25 @@ cudaError_t launch_sr_weights(const float* P, void* out, cudaStream_t st) {
 
 // Per-cell state of the fused kernel.
 struct SrCellSlot {
-  SrInterp q;
-  float s_per_x2;  // 4 / (kappa/T)^2: s = x^2 times this
-  int mode;        // 0: not trusted (the table kernel's), 1: network, 2: table (no network outputs)
+  float lnKP, lnKA, T;  // the record's per-cell constants
+  float s_per_x2;       // 4 / (kappa/T)^2: s = x^2 times this
+  int mode;             // 1: the network writes this cell's record
 };
 
-// A cell's six record entries of this lane (entry lane + 32 it): from the
-// network's outputs y (shared memory), or from the table (mode 2).
-// shx: the lane's fixed shape terms (Primakoff and Compton-like Planck
-// factors, bremsstrahlung power, each plus x_k); qsrc: the network output of
-// the lane's quantile entries (-1 on lanes 29..31 of the last row: the
-// per-cell constants).
-__device__ __forceinline__ void sr_record_entries(const SrArgs& a, const SrCellSlot& c, const float* y, float x2,
-                                                  const float* shx, const int* qsrc, int lane, float* v) {
-  if (c.mode == 1) {
-    v[0] = y[0] + shx[0] + sr_prim_lnF(x2 * c.s_per_x2);
-    v[1] = y[32] + shx[1];
-    v[2] = y[64] + shx[2];
-    v[3] = y[qsrc[0]];
-    v[4] = y[qsrc[1]];
-    const float k = lane == 29 ? c.q.lnKP : (lane == 30 ? c.q.lnKA : c.q.T);
-    v[5] = qsrc[2] >= 0 ? y[qsrc[2]] : k;
-  } else {
-#pragma unroll
-    for (int it = 0; it < 6; ++it) v[it] = sr_table_entry(a, c.q, lane + 32 * it);
-  }
+// A trusted cell's six record entries of this lane (entry lane + 32 it) from
+// the network's outputs y (shared memory). shx: the lane's fixed shape
+// terms (Primakoff and Compton-like Planck factors, bremsstrahlung power,
+// each plus x_k); qsrc: the network output of the lane's quantile entries
+// (-1 on lanes 29..31 of the last row: the per-cell constants).
+__device__ __forceinline__ void sr_record_entries(const SrCellSlot& c, const float* y, float x2, const float* shx,
+                                                  const int* qsrc, int lane, float* v) {
+  v[0] = y[0] + shx[0] + sr_prim_lnF(x2 * c.s_per_x2);
+  v[1] = y[32] + shx[1];
+  v[2] = y[64] + shx[2];
+  v[3] = y[qsrc[0]];
+  v[4] = y[qsrc[1]];
+  const float k = lane == 29 ? c.lnKP : (lane == 30 ? c.lnKA : c.T);
+  v[5] = qsrc[2] >= 0 ? y[qsrc[2]] : k;
 }
 
 // Eight activations (columns j0..j0+7 of row r) as bfloat16 into one 16-byte
@@ -243,180 +250,175 @@ __device__ __forceinline__ void store8_bf16(__nv_bfloat16* base, int r, int j0, 
   *reinterpret_cast<uint4*>(base + core_off(r, j0, 64)) = u;
 }
 
-__global__ void __launch_bounds__(kSrMlpThreads) sr_mlp_kernel(SrArgs a) {
+__global__ void __launch_bounds__(kSrMlpThreads, 4) sr_mlp_kernel(SrArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ SrCellSlot cs[128];
-  __shared__ float sF[2][128];  // features f1, f2 of each row
-  // network constants: layer 1 per unit (b1, W1 rows of f1..f3), b2, and the
-  // output affine (mu + sigma b3, sigma, S columns of f1..f3), read as float4
-  __shared__ float4 sL1[64];
-  __shared__ __align__(16) float sB2[64];
+  // the output affine (mu + sigma b3, sigma, S columns of f1..f3), read as float4
   __shared__ __align__(16) float sC3[96];
   __shared__ __align__(16) float sSig[96];
   __shared__ __align__(16) float sS[3][96];
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_base;
-  __nv_bfloat16* sA1 = reinterpret_cast<__nv_bfloat16*>(sm);
-  __nv_bfloat16* sA2 = sA1 + 128 * 64;
-  __nv_bfloat16* sW2 = sA2 + 128 * 64;
-  __nv_bfloat16* sW3 = sW2 + 64 * 64;
-  float* sOut = reinterpret_cast<float*>(sm);  // after layer 3: [128][kSrOutStride]
+  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(sm);
+  __nv_bfloat16* sW2 = reinterpret_cast<__nv_bfloat16*>(sm + kSrOffW2);
+  __nv_bfloat16* sW3 = reinterpret_cast<__nv_bfloat16*>(sm + kSrOffW3);
+  float4* sL1 = reinterpret_cast<float4*>(sm + kSrOffL1);  // per unit: b1, W1 rows of f1..f3
+  float* sB2 = reinterpret_cast<float*>(sm + kSrOffB2);
+  float* sF = reinterpret_cast<float*>(sm + kSrOffF);      // [2][128]: f1, f2 of each row
+  float* sOut = reinterpret_cast<float*>(sm);              // after layer 3: [128][kSrOutStride]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int r = tid & 127, half = tid >> 7;
   const int c0 = blockIdx.x * 128;
   const int nc = min(128, a.ncells - c0);
+  const bool valid = r < nc;
   bool trusted = false;
   if (half == 0) {
-    const bool valid = r < nc;
     const SrCellIn c = valid ? sr_cell(a, c0 + r) : sr_cell_none();
     trusted = valid && sr_trusted(a, c, a.Z);
-    if (valid) {
-      sr_interp(a, c, &cs[r].q);
-      cs[r].s_per_x2 = 4.0f / (c.kT * c.kT);
-      cs[r].mode = trusted ? 1 : 0;
-    }
-    sF[0][r] = (c.lkT - kSrLnKt0) / kSrLnKtSpan * 2.0f - 1.0f;
-    sF[1][r] = (c.lne - 24.5f) / 1.5f;
-    // the group of 32 cells of this warp: written whole here (the table
-    // kernel's CTA for it exits)
-    const bool whole = __all_sync(0xFFFFFFFFu, trusted || !valid);
-    if (lane == 0 && 32 * warp < nc) a.grp[(c0 >> 5) + warp] = whole ? 1 : 0;
+    sr_consts(a, c.T, &cs[r].lnKP, &cs[r].lnKA);
+    cs[r].T = c.T;
+    cs[r].s_per_x2 = 4.0f / (c.kT * c.kT);
+    cs[r].mode = trusted ? 1 : 0;
+    sF[r] = (c.lkT - kSrLnKt0) / kSrLnKtSpan * 2.0f - 1.0f;
+    sF[128 + r] = (c.lne - 24.5f) / 1.5f;
   }
   // no trusted cell here: the table kernel writes all of them
-  if (!__syncthreads_or(trusted)) return;
+  if (!__syncthreads_or(trusted)) {
+    if (half == 0 && valid) a.net[c0 + r] = 0;
+    return;
+  }
   bool ok = true;
+  if (warp == 0) tmem_alloc(&tmem_base, 128);
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  // the pre-laid-out weights: 20 KB of 16-byte copies
   {
-    if (warp == 0) tmem_alloc(&tmem_base, 128);
-    if (tid == 0) {
-      mbar_init(&bar, 1);
-      asm volatile("fence.mbarrier_init.release.cluster;");
-    }
-    // the pre-laid-out weights: 20 KB of 16-byte copies
-    {
-      const uint4* src = reinterpret_cast<const uint4*>(a.W16);
-      uint4* dst = reinterpret_cast<uint4*>(sW2);
-      for (int i = tid; i < (64 * 64 + 96 * 64) / 8; i += kSrMlpThreads) dst[i] = src[i];
-    }
-    if (tid < 64) {
-      sL1[tid] = make_float4(a.P[kOffB1 + tid], a.P[kOffW1 + 64 + tid], a.P[kOffW1 + 128 + tid],
-                             a.P[kOffW1 + 192 + tid]);
-      sB2[tid] = a.P[kOffB2 + tid];
-    } else if (tid >= 128 && tid < 128 + 96) {
-      const int o = tid - 128;
-      sC3[o] = fmaf(a.sigma[o], a.P[kOffB3 + o], a.mu[o]);
-      sSig[o] = a.sigma[o];
+    const uint4* src = reinterpret_cast<const uint4*>(a.W16);
+    uint4* dst = reinterpret_cast<uint4*>(sW2);
+    for (int i = tid; i < (64 * 64 + 96 * 64) / 8; i += kSrMlpThreads) dst[i] = src[i];
+  }
+  if (tid < 64) {
+    sL1[tid] = make_float4(a.P[kOffB1 + tid], a.P[kOffW1 + 64 + tid], a.P[kOffW1 + 128 + tid],
+                           a.P[kOffW1 + 192 + tid]);
+    sB2[tid] = a.P[kOffB2 + tid];
+  } else if (tid >= 128 && tid < 128 + 96) {
+    const int o = tid - 128;
+    sC3[o] = fmaf(a.sigma[o], a.P[kOffB3 + o], a.mu[o]);
+    sSig[o] = a.sigma[o];
 #pragma unroll
-      for (int i = 1; i < 4; ++i) sS[i - 1][o] = a.skip[o * 4 + i];
+    for (int i = 1; i < 4; ++i) sS[i - 1][o] = a.skip[o * 4 + i];
+  }
+  __syncthreads();
+  // cell features (the ln x input held at zero) and layer 1 on the CUDA
+  // cores: this thread's 32 of the 64 units
+  const float f1 = sF[r], f2 = sF[128 + r], f3 = a.Z - 1.5f;
+#pragma unroll
+  for (int j0 = 32 * half; j0 < 32 * half + 32; j0 += 8) {
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float4 w = sL1[j0 + j];
+      v[j] = act_tanh(fmaf(f3, w.w, fmaf(f2, w.z, fmaf(f1, w.y, w.x))));
     }
-    __syncthreads();
-    // cell features (the ln x input held at zero) and layer 1 on the CUDA
-    // cores: this thread's 32 of the 64 units
-    const float f1 = sF[0][r], f2 = sF[1][r], f3 = a.Z - 1.5f;
+    store8_bf16(sA, r, j0, v);
+  }
+  smem_to_async_proxy();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t row = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  const uint32_t lbo = 128, sbo = 8 * 128;
+  // layer 2: D[0, 64) = A1 . W2
+  if (tid == 0) {
+    for (int s = 0; s < 4; ++s)
+      mma_bf16(tmem, mma_desc(smem_u32(sA) + s * 256, lbo, sbo), mma_desc(smem_u32(sW2) + s * 256, lbo, sbo),
+               mma_idesc(128, 64), s > 0);
+    tc_commit(&bar);
+  }
+  // warp 0 waits; the others park in the barrier (no issue slots spent
+  // spinning), and the verdict is CTA-uniform
+  {
+    bool w = true;
+    if (warp == 0) w = __all_sync(0xFFFFFFFFu, mbar_wait(&bar, 0));
+    ok = __syncthreads_and(w) != 0;
+  }
+  tc_fence_after();
+  // layer 2's activations over layer 1's (the MMA that read them is done)
+  if (ok) {
 #pragma unroll
-    for (int j0 = 32 * half; j0 < 32 * half + 32; j0 += 8) {
-      float v[8];
+    for (int j0 = 32 * half; j0 < 32 * half + 32; j0 += 16) {
+      float v[16];
+      tmem_ld16(row + j0, v);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float4 w = sL1[j0 + j];
-        v[j] = act_tanh(fmaf(f3, w.w, fmaf(f2, w.z, fmaf(f1, w.y, w.x))));
+      for (int j = 0; j < 16; j += 4) {
+        const float4 b = *reinterpret_cast<const float4*>(sB2 + j0 + j);
+        v[j] = act_tanh(v[j] + b.x);
+        v[j + 1] = act_tanh(v[j + 1] + b.y);
+        v[j + 2] = act_tanh(v[j + 2] + b.z);
+        v[j + 3] = act_tanh(v[j + 3] + b.w);
       }
-      store8_bf16(sA1, r, j0, v);
+      store8_bf16(sA, r, j0, v);
+      store8_bf16(sA, r, j0 + 8, v + 8);
     }
-    smem_to_async_proxy();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = tmem_base;
-    const uint32_t row = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    const uint32_t lbo = 128, sbo = 8 * 128;
-    // layer 2: D[0, 64) = A1 . W2
-    if (tid == 0) {
-      for (int s = 0; s < 4; ++s)
-        mma_bf16(tmem, mma_desc(smem_u32(sA1) + s * 256, lbo, sbo), mma_desc(smem_u32(sW2) + s * 256, lbo, sbo),
-                 mma_idesc(128, 64), s > 0);
-      tc_commit(&bar);
-    }
-    // warp 0 waits; the others park in the barrier (no issue slots spent
-    // spinning), and the verdict is CTA-uniform
-    {
-      bool w = true;
-      if (warp == 0) w = __all_sync(0xFFFFFFFFu, mbar_wait(&bar, 0));
-      ok = __syncthreads_and(w) != 0;
-    }
-    tc_fence_after();
-    if (ok) {
+  }
+  smem_to_async_proxy();
+  tc_fence_before();
+  ok = __syncthreads_and(ok) != 0;
+  tc_fence_after();
+  // layer 3: D[0, 96) = A2 . W3 (layer 2's columns have been read out)
+  if (ok && tid == 0) {
+    for (int s = 0; s < 4; ++s)
+      mma_bf16(tmem, mma_desc(smem_u32(sA) + s * 256, lbo, sbo), mma_desc(smem_u32(sW3) + s * 256, lbo, sbo),
+               mma_idesc(128, 96), s > 0);
+    tc_commit(&bar);
+  }
+  const bool issued3 = ok;
+  if (ok) {
+    bool w = true;
+    if (warp == 0) w = __all_sync(0xFFFFFFFFu, mbar_wait(&bar, 1));
+    ok = __syncthreads_and(w) != 0;
+  }
+  tc_fence_after();
+  if (!ok && warp == 0) {
+    // flag it and give the tensor core a second bounded wait on whatever it
+    // may still be doing before the tensor memory is released; no record is
+    // written here and the table kernel writes them all
+    if (lane == 0) atomicOr(a.err, 2);
+    mbar_wait(&bar, issued3 ? 1u : 0u);
+  }
+  if (ok) {
+    // this thread's 48 outputs, 16 at a time, through the FP32 output affine
+    // into the stage (the operands' bytes: the MMA that read them is done)
+    float* out = sOut + r * kSrOutStride + 48 * half;
 #pragma unroll
-      for (int j0 = 32 * half; j0 < 32 * half + 32; j0 += 16) {
-        float v[16];
-        tmem_ld16(row + j0, v);
+    for (int j0 = 0; j0 < 48; j0 += 16) {
+      float y[16];
+      tmem_ld16(row + 48 * half + j0, y);
 #pragma unroll
-        for (int j = 0; j < 16; j += 4) {
-          const float4 b = *reinterpret_cast<const float4*>(sB2 + j0 + j);
-          v[j] = act_tanh(v[j] + b.x);
-          v[j + 1] = act_tanh(v[j + 1] + b.y);
-          v[j + 2] = act_tanh(v[j + 2] + b.z);
-          v[j + 3] = act_tanh(v[j + 3] + b.w);
-        }
-        store8_bf16(sA2, r, j0, v);
-        store8_bf16(sA2, r, j0 + 8, v + 8);
-      }
-    }
-    smem_to_async_proxy();
-    tc_fence_before();
-    ok = __syncthreads_and(ok) != 0;
-    tc_fence_after();
-    // layer 3: D[0, 96) = A2 . W3 (layer 2's columns have been read out)
-    if (ok && tid == 0) {
-      for (int s = 0; s < 4; ++s)
-        mma_bf16(tmem, mma_desc(smem_u32(sA2) + s * 256, lbo, sbo), mma_desc(smem_u32(sW3) + s * 256, lbo, sbo),
-                 mma_idesc(128, 96), s > 0);
-      tc_commit(&bar);
-    }
-    const bool issued3 = ok;
-    if (ok) {
-      bool w = true;
-      if (warp == 0) w = __all_sync(0xFFFFFFFFu, mbar_wait(&bar, 1));
-      ok = __syncthreads_and(w) != 0;
-    }
-    tc_fence_after();
-    if (!ok && warp == 0) {
-      // flag it and give the tensor core a second bounded wait on whatever
-      // it may still be doing before the tensor memory is released (the
-      // records then come from the table)
-      if (lane == 0) atomicOr(a.err, 2);
-      mbar_wait(&bar, issued3 ? 1u : 0u);
-    }
-    // this thread's 48 outputs in registers before the operands' bytes are
-    // overwritten with the outputs
-    float y[48];
-    if (ok) {
-#pragma unroll
-      for (int j0 = 0; j0 < 48; j0 += 16) tmem_ld16(row + 48 * half + j0, y + j0);
-    }
-    tc_fence_before();
-    ok = __syncthreads_and(ok) != 0;
-    tc_fence_after();
-    if (warp == 0) tmem_free(tmem, 128);
-    if (ok) {
-      float* out = sOut + r * kSrOutStride + 48 * half;
-#pragma unroll
-      for (int i = 0; i < 48; i += 4) {
-        const int o = 48 * half + i;
+      for (int i = 0; i < 16; i += 4) {
+        const int o = 48 * half + j0 + i;
         const float4 c = *reinterpret_cast<const float4*>(sC3 + o);
         const float4 g = *reinterpret_cast<const float4*>(sSig + o);
         const float4 s1 = *reinterpret_cast<const float4*>(sS[0] + o);
         const float4 s2 = *reinterpret_cast<const float4*>(sS[1] + o);
         const float4 s3 = *reinterpret_cast<const float4*>(sS[2] + o);
-        out[i] = fmaf(s3.x, f3, fmaf(s2.x, f2, fmaf(s1.x, f1, fmaf(g.x, y[i], c.x))));
-        out[i + 1] = fmaf(s3.y, f3, fmaf(s2.y, f2, fmaf(s1.y, f1, fmaf(g.y, y[i + 1], c.y))));
-        out[i + 2] = fmaf(s3.z, f3, fmaf(s2.z, f2, fmaf(s1.z, f1, fmaf(g.z, y[i + 2], c.z))));
-        out[i + 3] = fmaf(s3.w, f3, fmaf(s2.w, f2, fmaf(s1.w, f1, fmaf(g.w, y[i + 3], c.w))));
+        out[j0 + i] = fmaf(s3.x, f3, fmaf(s2.x, f2, fmaf(s1.x, f1, fmaf(g.x, y[i], c.x))));
+        out[j0 + i + 1] = fmaf(s3.y, f3, fmaf(s2.y, f2, fmaf(s1.y, f1, fmaf(g.y, y[i + 1], c.y))));
+        out[j0 + i + 2] = fmaf(s3.z, f3, fmaf(s2.z, f2, fmaf(s1.z, f1, fmaf(g.z, y[i + 2], c.z))));
+        out[j0 + i + 3] = fmaf(s3.w, f3, fmaf(s2.w, f2, fmaf(s1.w, f1, fmaf(g.w, y[i + 3], c.w))));
       }
-    } else if (half == 0 && trusted) {
-      cs[r].mode = 2;  // no network outputs: the table record
     }
-    __syncthreads();
+  } else if (half == 0) {
+    cs[r].mode = 0;  // no network outputs: the table kernel writes this cell
   }
+  if (half == 0 && valid) a.net[c0 + r] = cs[r].mode;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_free(tmem, 128);
   // records: warp w writes cells w, w + 8, ..., two at a time, a cell's 192
   // entries by its 32 lanes (lane k takes grid point x_k of the three rate
   // rows). A trusted cell's ln-emissivity row is the network's cell constant
@@ -438,8 +440,8 @@ __global__ void __launch_bounds__(kSrMlpThreads) sr_mlp_kernel(SrArgs a) {
     const int c1 = c + kW;
     const bool w0 = cs[c].mode != 0, w1 = c1 < nc && cs[c1].mode != 0;
     float v0[6], v1[6];
-    if (w0) sr_record_entries(a, cs[c], sOut + c * kSrOutStride, x2, shx, qsrc, lane, v0);
-    if (w1) sr_record_entries(a, cs[c1], sOut + c1 * kSrOutStride, x2, shx, qsrc, lane, v1);
+    if (w0) sr_record_entries(cs[c], sOut + c * kSrOutStride, x2, shx, qsrc, lane, v0);
+    if (w1) sr_record_entries(cs[c1], sOut + c1 * kSrOutStride, x2, shx, qsrc, lane, v1);
     if (w0) {
       float* r0 = a.sr + (size_t)(c0 + c) * kSrLen;
 #pragma unroll
@@ -454,7 +456,9 @@ __global__ void __launch_bounds__(kSrMlpThreads) sr_mlp_kernel(SrArgs a) {
 }
 
 cudaError_t sr_init_kernels() {
-  return cudaFuncSetAttribute(sr_mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSrMlpSmem);
+  cudaError_t e = cudaFuncSetAttribute(sr_mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSrMlpSmem);
+  if (!e) e = cudaFuncSetAttribute(sr_mlp_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
 }
 
 cudaError_t launch_sr_mlp(const SrArgs& a, cudaStream_t st) {

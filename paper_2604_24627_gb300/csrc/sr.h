@@ -47,7 +47,7 @@ struct SrArgs {
   const uint8_t* trust;  // [2][tnne][tnT], 1 = trusted node
   const void* W16;       // W2^T, W3^T in bfloat16, core-matrix layout (launch_sr_weights)
   int tnT, tnne;
-  uint8_t* grp;          // [ceil(ncells / 32)]: 1 = the network kernel wrote all 32 cells of the group
+  uint8_t* net;          // [ncells]: 1 = the network kernel wrote this cell's record (surrogate model)
   int* err;
 };
 
