@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--stream-calls", type=int, default=20,
+                    help="timed axion streaming calls after the other legs (0: none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=256, help="cells per side (256: the full workload)")
@@ -512,8 +514,39 @@ def main():
         e2e = {"value": p_e / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
 
+    # axion free streaming and cell migration (axpic_stream_axions) on the
+    # same plasma after the legs above: the workload's grid as a periodic box
+    # of cubic cells (edge from the cell volume), c dt = 0.6 of the edge. The
+    # algorithmic bytes of a call: every axion's seven fields read and
+    # written once (56 B).
+    stream_leg = None
+    if args.stream_calls > 0 and len(w.shape) >= 1:
+        dims = tuple(list(w.shape) + [1] * (3 - len(w.shape)))
+        if int(np.prod(dims)) == w.ncells:
+            h = w.volume_cm3 ** (1.0 / 3.0)
+            dt_s = 0.6 * h / 2.99792458e10
+            pl.stream_axions(dims, h, dt_s, True)  # the first call makes the scratch
+            torch.cuda.synchronize(dev)
+            n_ax = int(pl.slabs["axions"].count[:w.ncells].sum())
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            for _ in range(args.stream_calls):
+                pl.stream_axions(dims, h, dt_s, True)
+            s1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = s0.elapsed_time(s1) / args.stream_calls
+            gbps = 56.0 * n_ax / (ms * 1e-3) / 1e9
+            stream_leg = {"call": "axpic_stream_axions", "grid": list(dims), "boundary": "periodic",
+                          "c_dt_over_h": 0.6, "axions": n_ax, "calls": args.stream_calls, "ms_per_call": ms,
+                          "axion_moves_per_s": n_ax / (ms * 1e-3), "algorithmic_bytes_per_axion": 56,
+                          "GBps": gbps}
+
     if rank == 0:
         peak, peak_kind = measured_peaks()
+        if stream_leg:
+            stream_leg["frac"] = stream_leg["GBps"] / peak
+            stream_leg["peak_kind"] = peak_kind
         # per kernel: device time from events around each launch, and the
         # minimum bytes that kernel has to move (kernel_bytes)
         dom = max(kms, key=kms.get)
@@ -564,6 +597,8 @@ def main():
                            "events_inverse": tot["events_pinv"], "remapped_cells": tot["remaps"]}}
         if e2e:
             line["e2e"] = e2e
+        if stream_leg:
+            line["axion_streaming"] = stream_leg
         if world == 1 and not args.no_cpu_baseline:
             cells = [pl.cell(c) for c in range(64)]
             from oracle import step as ostep

@@ -206,6 +206,35 @@ axpic_status axpic_sample_plasma(axpic_ctx *ctx, int32_t n_el, int32_t n_ph, int
  * n_ion (temperature mode "prescribed field", Sec. II.E). */
 axpic_status axpic_update_cells(axpic_ctx *ctx);
 
+/* Axion free streaming and cell migration: every axion moves by
+ * (p / |p|) c dt_s (Sec. II, the axions' transport between steps) on a
+ * regular grid of nx x ny x nz cubic cells of edge h_cm [cm], cell index
+ * (k ny + j) nx + i (nx ny nz must equal ncells). Positions are fractions of
+ * the cell; a dimension of one cell is not streamed. c dt_s must stay below
+ * h_cm (at most one cell per dimension and step). boundary 0: periodic;
+ * 1: open (axions leaving the box are removed and counted, see
+ * axpic_stream_stats). The position update is binary32 with each rounding
+ * fixed: |p| = sqrt((px px + py py) + pz pz), d = (kappa / |p|) p_dim with
+ * kappa = binary32(c dt / h), t = x + d, shift floor(t), fraction t -
+ * shift (the largest binary32 below 1 where that rounds up to 1); |p| = 0
+ * does not move. Each cell's slab is then rebuilt: its staying axions in
+ * slot order, then the arrivals ordered by the source cell's position
+ * relative to it ((dz, dy, dx) ascending lexicographic over {-1, 0, 1}^3),
+ * then by source slot. Axions beyond the capacity are dropped, counted and
+ * latch AXPIC_E_CAPACITY. Asynchronous on the context's stream; the first
+ * call allocates scratch (33 bytes per axion slot plus 108 per cell), later
+ * calls allocate nothing. AXPIC_E_INVALID (nothing launched) for a grid
+ * that does not match, h_cm <= 0, dt_s < 0, c dt_s >= h_cm or another
+ * boundary value. */
+axpic_status axpic_stream_axions(axpic_ctx *ctx, int32_t nx, int32_t ny, int32_t nz, double h_cm, double dt_s,
+                                 int32_t boundary);
+
+/* Totals of every axpic_stream_axions call so far, to out (host, 4
+ * doubles): axions that left an open box (number, weight, weight x energy
+ * [keV]) and axions dropped at a full slab (number). Zeros before the first
+ * call. Synchronises. */
+axpic_status axpic_stream_stats(axpic_ctx *ctx, double *out);
+
 /* Inverse operators on the axions present when the call starts (Sec. II.F.1
  * last paragraph; Sec. II.I): Primakoff a->gamma conversion with weight
  * depletion (photon products appended) and detailed-balance absorption of the

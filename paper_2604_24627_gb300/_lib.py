@@ -126,6 +126,9 @@ EXPORTS = {
     "axpic_profile_end": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int32)]),
     "axpic_step_kernel_names": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "axpic_stream_axions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_int32]),
+    "axpic_stream_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "axpic_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "axpic_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "axpic_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -411,6 +414,18 @@ def axpic_set_surrogate(ctx, net_handle, err_map, nT, nne, tol):
     import numpy as np
     e = np.ascontiguousarray(err_map, dtype=np.float32)
     _check(ctx, lib().axpic_set_surrogate(ctx, net_handle, _fptr(e), nT, nne, tol))
+
+
+def axpic_stream_axions(ctx, dims, h_cm, dt_s, boundary):
+    nx, ny, nz = dims
+    _check(ctx, lib().axpic_stream_axions(ctx, nx, ny, nz, h_cm, dt_s, boundary))
+
+
+def axpic_stream_stats(ctx):
+    import numpy as np
+    out = np.zeros(4, dtype=np.float64)
+    _check(ctx, lib().axpic_stream_stats(ctx, _dptr(out)))
+    return out
 
 
 def axpic_get_spectral_records(ctx, first, count):

@@ -13,6 +13,7 @@
 #include "misc.h"
 #include "sr.h"
 #include "step.h"
+#include "stream.h"
 
 using namespace axpic;
 
@@ -93,6 +94,11 @@ struct axpic_ctx {
   float* sur_skip = nullptr;
   uint8_t* sur_trust = nullptr;
   uint8_t* sr_net = nullptr;  // [ncells]: 1 where the network kernel wrote the record
+  // axion streaming scratch, made by the first axpic_stream_axions call
+  uint8_t* st_dir = nullptr;  // [ncells * axion capacity]
+  int32_t* st_cnt = nullptr;  // [ncells * 27]
+  float* st_buf = nullptr;    // [ncells * axion capacity * 8]
+  double* st_stats = nullptr; // [4]
   void* sur_W16 = nullptr;  // layers 2 and 3 laid out for the tensor cores
   int sr_nkt = 0, sr_nne = 0, tnT = 0, tnne = 0, sur_set = 0, sur_any_trusted = 0;
   float ln_gP = 0.f, ln_gA = 0.f;
@@ -316,7 +322,7 @@ static void free_ctx(axpic_ctx* ctx) {
                   ctx->tables, ctx->tally, ctx->counters, ctx->err, ctx->scratch, ctx->bits,
                   ctx->recA,   ctx->recG,  ctx->recE,     ctx->step_dev, ctx->sr, ctx->srtab,
                   ctx->sur_P,  ctx->sur_mu, ctx->sur_sigma, ctx->sur_trust, ctx->sur_W16, ctx->sur_skip,
-                  ctx->sr_net};
+                  ctx->sr_net, ctx->st_dir, ctx->st_cnt, ctx->st_buf, ctx->st_stats};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete ctx;
@@ -968,6 +974,51 @@ axpic_status axpic_set_surrogate(axpic_ctx* ctx, axpic_mlp* m, const float* err_
   CK(build_records(ctx, st), "spectral records");
   CK(cudaStreamSynchronize(st), "synchronize");
   return read_err(ctx);
+}
+
+axpic_status axpic_stream_axions(axpic_ctx* ctx, int32_t nx, int32_t ny, int32_t nz, double h_cm, double dt_s,
+                                 int32_t boundary) {
+  if (!ctx) return AXPIC_E_INVALID;
+  const axpic_plasma_desc& d = ctx->desc;
+  if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz != d.ncells)
+    return fail(ctx, AXPIC_E_INVALID, "axpic_stream_axions: nx ny nz must give the context's cells");
+  if (!(h_cm > 0) || !std::isfinite(h_cm) || !(dt_s >= 0) || !std::isfinite(dt_s) || (boundary != 0 && boundary != 1))
+    return fail(ctx, AXPIC_E_INVALID, "axpic_stream_axions: h, dt or boundary");
+  const float kappa = (float)(2.99792458e10 * dt_s / h_cm);
+  if (!(kappa < 1.0f - 0x1p-20f))
+    return fail(ctx, AXPIC_E_INVALID, "axpic_stream_axions: c dt must stay below the cell edge");
+  const size_t slots = (size_t)d.ncells * d.axions.capacity;
+  if (!ctx->st_dir) {
+    CK(cudaMalloc((void**)&ctx->st_dir, std::max<size_t>(slots, 1)), "streaming scratch");
+    CK(cudaMalloc((void**)&ctx->st_cnt, sizeof(int32_t) * kStreamDirs * (size_t)d.ncells), "streaming scratch");
+    CK(cudaMalloc((void**)&ctx->st_buf, sizeof(float) * 8 * std::max<size_t>(slots, 1)), "streaming scratch");
+    CK(cudaMalloc((void**)&ctx->st_stats, sizeof(double) * 4), "streaming scratch");
+    CK(cudaMemsetAsync(ctx->st_stats, 0, sizeof(double) * 4, ctx->stream), "memset");
+  }
+  StreamArgs a;
+  a.s = to_ptrs(d.axions);
+  a.ncells = d.ncells;
+  a.nx = nx;
+  a.ny = ny;
+  a.nz = nz;
+  a.kappa = kappa;
+  a.periodic = boundary == 0;
+  a.dir = ctx->st_dir;
+  a.cnt = ctx->st_cnt;
+  a.buf = ctx->st_buf;
+  a.stats = ctx->st_stats;
+  a.err = ctx->err;
+  CK(launch_stream(a, ctx->stream), "stream kernels");
+  return AXPIC_OK;
+}
+
+axpic_status axpic_stream_stats(axpic_ctx* ctx, double* out) {
+  if (!ctx || !out) return AXPIC_E_INVALID;
+  for (int i = 0; i < 4; ++i) out[i] = 0.0;
+  if (!ctx->st_stats) return AXPIC_OK;
+  CK(cudaMemcpyAsync(out, ctx->st_stats, sizeof(double) * 4, cudaMemcpyDeviceToHost, ctx->stream), "copy");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  return AXPIC_OK;
 }
 
 axpic_status axpic_get_spectral_records(axpic_ctx* ctx, int32_t first, int32_t count, float* out) {

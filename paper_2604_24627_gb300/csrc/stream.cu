@@ -1,0 +1,200 @@
+// Axion free streaming and cell migration: x += (p / |p|) c dt (Sec. II, the
+// transport of the axion macroparticles between steps) on the cell-sorted
+// slabs, positions being fractions of the cell.
+//
+// Two kernels, a warp per cell each (grid-stride):
+//  * stream_move_kernel moves every axion of its cell, in binary32 with each
+//    rounding fixed (the result decides the destination cell), writes the
+//    new position in place, the direction of each slot and the count per
+//    direction, and copies the leaving axions into the cell's staging rows,
+//    grouped by direction in slot order.
+//  * stream_place_kernel compacts the cell's staying axions in place (slot
+//    order), then appends the arrivals from its neighbours' staging rows,
+//    ordered by the neighbour's position relative to it, (dz, dy, dx)
+//    ascending, then by source slot. Slots beyond the capacity are dropped,
+//    counted, and latch ERR_CAPACITY.
+// The first kernel writes only its own cell's slots and rows; the second
+// reads the neighbours' rows and writes only its own slab, so neither needs
+// a barrier across cells.
+#include "stream.h"
+
+namespace axpic {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr unsigned kAll = 0xFFFFFFFFu;
+constexpr float kBelowOne = 0x1.fffffep-1f;
+
+// New fraction of one position component and the cell shift in {-1, 0, 1}:
+// t = q + d, s = floor(t), t - s (the largest binary32 below 1 where that
+// rounds up to 1).
+__device__ __forceinline__ float advance(float q, float d, int* shift) {
+  const float t = __fadd_rn(q, d);
+  const float s = floorf(t);
+  float r = __fsub_rn(t, s);
+  if (r >= 1.0f) r = kBelowOne;
+  // in {-1, 0, 1} for positions in [0, 1) and kappa < 1; clamped so that no
+  // input can index beyond the 27 directions
+  *shift = max(-1, min(1, (int)s));
+  return r;
+}
+
+__global__ void __launch_bounds__(kThreads) stream_move_kernel(StreamArgs a) {
+  __shared__ int cnt[kWarps][32];
+  __shared__ int run[kWarps][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int c = blockIdx.x * kWarps + wid; c < a.ncells; c += gridDim.x * kWarps) {
+    cnt[wid][lane] = 0;
+    run[wid][lane] = 0;
+    __syncwarp();
+    const int n = min(max(a.s.count[c], 0), a.s.cap);
+    const long base = (long)c * a.s.cap;
+    const int ci = c % a.nx, cj = (c / a.nx) % a.ny, ck = c / (a.nx * a.ny);
+    for (int s0 = 0; s0 < n; s0 += 32) {
+      const int slot = s0 + lane;
+      if (slot < n) {
+        const long q = base + slot;
+        const float px = a.s.px[q], py = a.s.py[q], pz = a.s.pz[q];
+        const float pn = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(px, px), __fmul_rn(py, py)), __fmul_rn(pz, pz)));
+        int sx = 0, sy = 0, sz = 0;
+        if (pn > 0.f) {
+          const float k = __fdiv_rn(a.kappa, pn);
+          if (a.nx > 1) a.s.x[q] = advance(a.s.x[q], __fmul_rn(k, px), &sx);
+          if (a.ny > 1) a.s.y[q] = advance(a.s.y[q], __fmul_rn(k, py), &sy);
+          if (a.nz > 1) a.s.z[q] = advance(a.s.z[q], __fmul_rn(k, pz), &sz);
+        }
+        int o = (sz + 1) * 9 + (sy + 1) * 3 + (sx + 1);
+        if (!a.periodic) {
+          const int ii = ci + sx, jj = cj + sy, kk = ck + sz;
+          if (ii < 0 || ii >= a.nx || jj < 0 || jj >= a.ny || kk < 0 || kk >= a.nz) {
+            o = kStreamEscaped;
+            const double w = (double)a.s.w[q];
+            const double pm = sqrt((double)px * px + (double)py * py + (double)pz * pz);
+            atomicAdd(a.stats + 0, 1.0);
+            atomicAdd(a.stats + 1, w);
+            atomicAdd(a.stats + 2, w * pm * kMeC2);
+          }
+        }
+        a.dir[q] = (uint8_t)o;
+        atomicAdd(&cnt[wid][o], 1);
+      }
+    }
+    __syncwarp();
+    if (lane < kStreamDirs) a.cnt[(size_t)c * kStreamDirs + lane] = cnt[wid][lane];
+    // staging offset of each direction's group: the leavers of the lower
+    // directions (13 stays and 27 escaped hold none)
+    const int v = (lane < kStreamDirs && lane != kStreamStay) ? cnt[wid][lane] : 0;
+    int incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(kAll, incl, d);
+      if (lane >= d) incl += t;
+    }
+    const int off = incl - v;
+    for (int s0 = 0; s0 < n; s0 += 32) {
+      const int slot = s0 + lane;
+      const int o = slot < n ? (int)a.dir[base + slot] : 31;
+      const bool leave = o < kStreamDirs && o != kStreamStay;
+      const unsigned m = __match_any_sync(kAll, o);
+      const int goff = __shfl_sync(kAll, off, o);
+      if (leave) {
+        const int pos = goff + run[wid][o] + __popc(m & lt);
+        const long q = base + slot;
+        float4* dst = reinterpret_cast<float4*>(a.buf + ((size_t)c * a.s.cap + pos) * 8);
+        dst[0] = make_float4(a.s.w[q], a.s.px[q], a.s.py[q], a.s.pz[q]);
+        dst[1] = make_float4(a.s.x[q], a.s.y[q], a.s.z[q], 0.f);
+      }
+      __syncwarp();
+      if (leave && (m & lt) == 0) run[wid][o] += __popc(m);  // the group's first lane
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) stream_place_kernel(StreamArgs a) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const SpeciesPtrs& s = a.s;
+  for (int c = blockIdx.x * kWarps + wid; c < a.ncells; c += gridDim.x * kWarps) {
+    const int n = min(max(s.count[c], 0), s.cap);
+    const long base = (long)c * s.cap;
+    const int ci = c % a.nx, cj = (c / a.nx) % a.ny, ck = c / (a.nx * a.ny);
+    // the staying axions, in slot order, in place (a slot moves only down)
+    int total = 0;
+    for (int s0 = 0; s0 < n; s0 += 32) {
+      const int slot = s0 + lane;
+      const bool stay = slot < n && a.dir[base + slot] == kStreamStay;
+      const unsigned b = __ballot_sync(kAll, stay);
+      float f[7];
+      if (stay) {
+        const long q = base + slot;
+        f[0] = s.w[q], f[1] = s.px[q], f[2] = s.py[q], f[3] = s.pz[q], f[4] = s.x[q], f[5] = s.y[q], f[6] = s.z[q];
+      }
+      __syncwarp();
+      if (stay) {
+        const long q = base + total + __popc(b & lt);
+        s.w[q] = f[0], s.px[q] = f[1], s.py[q] = f[2], s.pz[q] = f[3], s.x[q] = f[4], s.y[q] = f[5], s.z[q] = f[6];
+      }
+      total += __popc(b);
+      __syncwarp();
+    }
+    // arrivals: neighbour at (dz, dy, dx) = r's digits - 1, r ascending; its
+    // axions that moved here have the shift -(dz, dy, dx), direction 26 - r
+    for (int r = 0; r < kStreamDirs; ++r) {
+      if (r == kStreamStay) continue;
+      const int dz = r / 9 - 1, dy = (r / 3) % 3 - 1, dx = r % 3 - 1;
+      if ((dx && a.nx == 1) || (dy && a.ny == 1) || (dz && a.nz == 1)) continue;
+      int si = ci + dx, sj = cj + dy, sk = ck + dz;
+      if (a.periodic) {
+        si = (si + a.nx) % a.nx;
+        sj = (sj + a.ny) % a.ny;
+        sk = (sk + a.nz) % a.nz;
+      } else if (si < 0 || si >= a.nx || sj < 0 || sj >= a.ny || sk < 0 || sk >= a.nz) {
+        continue;
+      }
+      const int src = (sk * a.ny + sj) * a.nx + si;
+      const int o = kStreamDirs - 1 - r;
+      const int32_t* sc = a.cnt + (size_t)src * kStreamDirs;
+      const int m = sc[o];
+      if (m == 0) continue;
+      int v = (lane < o && lane != kStreamStay) ? sc[lane] : 0;
+#pragma unroll
+      for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(kAll, v, d);
+      const float* rows = a.buf + ((size_t)src * s.cap + v) * 8;
+      for (int t0 = 0; t0 < m; t0 += 32) {
+        const int i = t0 + lane, dst = total + i;
+        if (i < m && dst < s.cap) {
+          const float4 u0 = reinterpret_cast<const float4*>(rows + (size_t)i * 8)[0];
+          const float4 u1 = reinterpret_cast<const float4*>(rows + (size_t)i * 8)[1];
+          const long q = base + dst;
+          s.w[q] = u0.x, s.px[q] = u0.y, s.py[q] = u0.z, s.pz[q] = u0.w, s.x[q] = u1.x, s.y[q] = u1.y, s.z[q] = u1.z;
+        }
+      }
+      total += m;
+    }
+    if (lane == 0) {
+      s.count[c] = min(total, s.cap);
+      if (total > s.cap) {
+        atomicAdd(a.stats + 3, (double)(total - s.cap));
+        atomicOr(a.err, ERR_CAPACITY);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_stream(const StreamArgs& a, cudaStream_t st) {
+  if (a.ncells <= 0) return cudaSuccess;
+  const int grid = (a.ncells + kWarps - 1) / kWarps;
+  stream_move_kernel<<<grid, kThreads, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e) return e;
+  stream_place_kernel<<<grid, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace axpic

@@ -156,6 +156,16 @@ class AxionPlasma:
         _lib.axpic_get_residuals(self.ctx, first, count, buf)
         return np.array(buf)[:4 * count].reshape(count, 4)
 
+    def stream_axions(self, dims, h_cm, dt_s, periodic=True):
+        """Axion free streaming and cell migration on an nx x ny x nz grid
+        (axpic_stream_axions); asynchronous."""
+        _lib.axpic_stream_axions(self.ctx, dims, h_cm, dt_s, 0 if periodic else 1)
+
+    def stream_stats(self):
+        """[escaped number, escaped weight, escaped weight x energy (keV),
+        dropped number] over every streaming call so far."""
+        return _lib.axpic_stream_stats(self.ctx)
+
     def profile_begin(self, max_steps):
         _lib.axpic_profile_begin(self.ctx, max_steps)
 
