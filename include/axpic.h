@@ -222,7 +222,7 @@ axpic_status axpic_update_cells(axpic_ctx *ctx);
  * relative to it ((dz, dy, dx) ascending lexicographic over {-1, 0, 1}^3),
  * then by source slot. Axions beyond the capacity are dropped, counted and
  * latch AXPIC_E_CAPACITY. Asynchronous on the context's stream; the first
- * call allocates scratch (33 bytes per axion slot plus 108 per cell), later
+ * call allocates scratch (33 bytes per axion slot plus 216 per cell), later
  * calls allocate nothing. AXPIC_E_INVALID (nothing launched) for a grid
  * that does not match, h_cm <= 0, dt_s < 0, c dt_s >= h_cm or another
  * boundary value. */

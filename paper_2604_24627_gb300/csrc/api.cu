@@ -96,7 +96,7 @@ struct axpic_ctx {
   uint8_t* sr_net = nullptr;  // [ncells]: 1 where the network kernel wrote the record
   // axion streaming scratch, made by the first axpic_stream_axions call
   uint8_t* st_dir = nullptr;  // [ncells * axion capacity]
-  int32_t* st_cnt = nullptr;  // [ncells * 27]
+  int32_t* st_cnt = nullptr;  // [ncells * 27 * 2]: counts, then group offsets
   float* st_buf = nullptr;    // [ncells * axion capacity * 8]
   double* st_stats = nullptr; // [4]
   void* sur_W16 = nullptr;  // layers 2 and 3 laid out for the tensor cores
@@ -990,7 +990,7 @@ axpic_status axpic_stream_axions(axpic_ctx* ctx, int32_t nx, int32_t ny, int32_t
   const size_t slots = (size_t)d.ncells * d.axions.capacity;
   if (!ctx->st_dir) {
     CK(cudaMalloc((void**)&ctx->st_dir, std::max<size_t>(slots, 1)), "streaming scratch");
-    CK(cudaMalloc((void**)&ctx->st_cnt, sizeof(int32_t) * kStreamDirs * (size_t)d.ncells), "streaming scratch");
+    CK(cudaMalloc((void**)&ctx->st_cnt, sizeof(int32_t) * 2 * kStreamDirs * (size_t)d.ncells), "streaming scratch");
     CK(cudaMalloc((void**)&ctx->st_buf, sizeof(float) * 8 * std::max<size_t>(slots, 1)), "streaming scratch");
     CK(cudaMalloc((void**)&ctx->st_stats, sizeof(double) * 4), "streaming scratch");
     CK(cudaMemsetAsync(ctx->st_stats, 0, sizeof(double) * 4, ctx->stream), "memset");
@@ -1005,6 +1005,7 @@ axpic_status axpic_stream_axions(axpic_ctx* ctx, int32_t nx, int32_t ny, int32_t
   a.periodic = boundary == 0;
   a.dir = ctx->st_dir;
   a.cnt = ctx->st_cnt;
+  a.goff = ctx->st_cnt + (size_t)kStreamDirs * d.ncells;
   a.buf = ctx->st_buf;
   a.stats = ctx->st_stats;
   a.err = ctx->err;

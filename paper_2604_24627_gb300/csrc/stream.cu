@@ -53,18 +53,33 @@ __global__ void __launch_bounds__(kThreads) stream_move_kernel(StreamArgs a) {
     const int n = min(max(a.s.count[c], 0), a.s.cap);
     const long base = (long)c * a.s.cap;
     const int ci = c % a.nx, cj = (c / a.nx) % a.ny, ck = c / (a.nx * a.ny);
-    for (int s0 = 0; s0 < n; s0 += 32) {
-      const int slot = s0 + lane;
-      if (slot < n) {
+    // two chunks of 32 slots per pass: both chunks' loads are issued before
+    // either is stored
+    for (int s0 = 0; s0 < n; s0 += 64) {
+      float px[2], py[2], pz[2], x[2], y[2], z[2];
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int slot = s0 + 32 * hh + lane;
+        px[hh] = py[hh] = pz[hh] = x[hh] = y[hh] = z[hh] = 0.f;
+        if (slot < n) {
+          const long q = base + slot;
+          px[hh] = a.s.px[q], py[hh] = a.s.py[q], pz[hh] = a.s.pz[q];
+          x[hh] = a.s.x[q], y[hh] = a.s.y[q], z[hh] = a.s.z[q];
+        }
+      }
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int slot = s0 + 32 * hh + lane;
+        if (slot >= n) continue;
         const long q = base + slot;
-        const float px = a.s.px[q], py = a.s.py[q], pz = a.s.pz[q];
-        const float pn = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(px, px), __fmul_rn(py, py)), __fmul_rn(pz, pz)));
+        const float pn = __fsqrt_rn(
+            __fadd_rn(__fadd_rn(__fmul_rn(px[hh], px[hh]), __fmul_rn(py[hh], py[hh])), __fmul_rn(pz[hh], pz[hh])));
         int sx = 0, sy = 0, sz = 0;
         if (pn > 0.f) {
           const float k = __fdiv_rn(a.kappa, pn);
-          if (a.nx > 1) a.s.x[q] = advance(a.s.x[q], __fmul_rn(k, px), &sx);
-          if (a.ny > 1) a.s.y[q] = advance(a.s.y[q], __fmul_rn(k, py), &sy);
-          if (a.nz > 1) a.s.z[q] = advance(a.s.z[q], __fmul_rn(k, pz), &sz);
+          if (a.nx > 1) a.s.x[q] = advance(x[hh], __fmul_rn(k, px[hh]), &sx);
+          if (a.ny > 1) a.s.y[q] = advance(y[hh], __fmul_rn(k, py[hh]), &sy);
+          if (a.nz > 1) a.s.z[q] = advance(z[hh], __fmul_rn(k, pz[hh]), &sz);
         }
         int o = (sz + 1) * 9 + (sy + 1) * 3 + (sx + 1);
         if (!a.periodic) {
@@ -72,7 +87,7 @@ __global__ void __launch_bounds__(kThreads) stream_move_kernel(StreamArgs a) {
           if (ii < 0 || ii >= a.nx || jj < 0 || jj >= a.ny || kk < 0 || kk >= a.nz) {
             o = kStreamEscaped;
             const double w = (double)a.s.w[q];
-            const double pm = sqrt((double)px * px + (double)py * py + (double)pz * pz);
+            const double pm = sqrt((double)px[hh] * px[hh] + (double)py[hh] * py[hh] + (double)pz[hh] * pz[hh]);
             atomicAdd(a.stats + 0, 1.0);
             atomicAdd(a.stats + 1, w);
             atomicAdd(a.stats + 2, w * pm * kMeC2);
@@ -94,6 +109,7 @@ __global__ void __launch_bounds__(kThreads) stream_move_kernel(StreamArgs a) {
       if (lane >= d) incl += t;
     }
     const int off = incl - v;
+    if (lane < kStreamDirs) a.goff[(size_t)c * kStreamDirs + lane] = off;
     for (int s0 = 0; s0 < n; s0 += 32) {
       const int slot = s0 + lane;
       const int o = slot < n ? (int)a.dir[base + slot] : 31;
@@ -141,40 +157,59 @@ __global__ void __launch_bounds__(kThreads) stream_place_kernel(StreamArgs a) {
       total += __popc(b);
       __syncwarp();
     }
-    // arrivals: neighbour at (dz, dy, dx) = r's digits - 1, r ascending; its
-    // axions that moved here have the shift -(dz, dy, dx), direction 26 - r
-    for (int r = 0; r < kStreamDirs; ++r) {
-      if (r == kStreamStay) continue;
+    // arrivals: lane r (r < 27, r != 13) takes the neighbour at (dz, dy, dx)
+    // = r's digits - 1, lanes ascending in r; that neighbour's axions that
+    // moved here have the shift -(dz, dy, dx), direction 26 - r. Every
+    // lane's group is found at once; a scan places the groups in r order.
+    int m = 0, src = 0, g = 0;
+    if (lane < kStreamDirs && lane != kStreamStay) {
+      const int r = lane;
       const int dz = r / 9 - 1, dy = (r / 3) % 3 - 1, dx = r % 3 - 1;
-      if ((dx && a.nx == 1) || (dy && a.ny == 1) || (dz && a.nz == 1)) continue;
       int si = ci + dx, sj = cj + dy, sk = ck + dz;
+      bool ok = !((dx && a.nx == 1) || (dy && a.ny == 1) || (dz && a.nz == 1));
       if (a.periodic) {
         si = (si + a.nx) % a.nx;
         sj = (sj + a.ny) % a.ny;
         sk = (sk + a.nz) % a.nz;
       } else if (si < 0 || si >= a.nx || sj < 0 || sj >= a.ny || sk < 0 || sk >= a.nz) {
-        continue;
+        ok = false;
       }
-      const int src = (sk * a.ny + sj) * a.nx + si;
-      const int o = kStreamDirs - 1 - r;
-      const int32_t* sc = a.cnt + (size_t)src * kStreamDirs;
-      const int m = sc[o];
-      if (m == 0) continue;
-      int v = (lane < o && lane != kStreamStay) ? sc[lane] : 0;
-#pragma unroll
-      for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(kAll, v, d);
-      const float* rows = a.buf + ((size_t)src * s.cap + v) * 8;
-      for (int t0 = 0; t0 < m; t0 += 32) {
-        const int i = t0 + lane, dst = total + i;
-        if (i < m && dst < s.cap) {
-          const float4 u0 = reinterpret_cast<const float4*>(rows + (size_t)i * 8)[0];
-          const float4 u1 = reinterpret_cast<const float4*>(rows + (size_t)i * 8)[1];
-          const long q = base + dst;
-          s.w[q] = u0.x, s.px[q] = u0.y, s.py[q] = u0.z, s.pz[q] = u0.w, s.x[q] = u1.x, s.y[q] = u1.y, s.z[q] = u1.z;
-        }
+      if (ok) {
+        src = (sk * a.ny + sj) * a.nx + si;
+        const size_t k = (size_t)src * kStreamDirs + (kStreamDirs - 1 - r);
+        m = a.cnt[k];
+        g = a.goff[k];
       }
-      total += m;
     }
+    int incl = m;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(kAll, incl, d);
+      if (lane >= d) incl += t;
+    }
+    const int arrivals = __shfl_sync(kAll, incl, 31);
+    const int excl = incl - m;
+    for (int t0 = 0; t0 < arrivals; t0 += 32) {
+      const int t = t0 + lane;
+      // the group holding arrival t: the last lane whose first arrival is <= t
+      int sel = 0;
+#pragma unroll
+      for (int r = 1; r < kStreamDirs; ++r) {
+        const int e = __shfl_sync(kAll, excl, r), mr = __shfl_sync(kAll, m, r);
+        if (mr > 0 && e <= t) sel = r;
+      }
+      const int e = __shfl_sync(kAll, excl, sel);
+      const int gs = __shfl_sync(kAll, g, sel), ss = __shfl_sync(kAll, src, sel);
+      const int dst = total + t;
+      if (t < arrivals && dst < s.cap) {
+        const float* row = a.buf + ((size_t)ss * s.cap + gs + (t - e)) * 8;
+        const float4 u0 = reinterpret_cast<const float4*>(row)[0];
+        const float4 u1 = reinterpret_cast<const float4*>(row)[1];
+        const long q = base + dst;
+        s.w[q] = u0.x, s.px[q] = u0.y, s.py[q] = u0.z, s.pz[q] = u0.w, s.x[q] = u1.x, s.y[q] = u1.y, s.z[q] = u1.z;
+      }
+    }
+    total += arrivals;
     if (lane == 0) {
       s.count[c] = min(total, s.cap);
       if (total > s.cap) {

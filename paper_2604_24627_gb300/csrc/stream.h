@@ -18,6 +18,7 @@ struct StreamArgs {
   int periodic;        // 1 periodic, 0 open
   uint8_t* dir;        // [ncells * cap]: direction of each slot
   int32_t* cnt;        // [ncells * 27]: slots per direction
+  int32_t* goff;       // [ncells * 27]: the direction's first row in the cell's staging rows
   float* buf;          // [ncells * cap * 8]: the cell's leaving axions, grouped by direction
   double* stats;       // [4]: escaped number, weight, weight x energy [keV]; dropped number
   int* err;            // latched error flags (ERR_CAPACITY)
