@@ -217,11 +217,13 @@ axpic_status axpic_update_cells(axpic_ctx *ctx);
  * fixed: |p| = sqrt((px px + py py) + pz pz), d = (kappa / |p|) p_dim with
  * kappa = binary32(c dt / h), t = x + d, shift floor(t), fraction t -
  * shift (the largest binary32 below 1 where that rounds up to 1); |p| = 0
- * does not move. Each cell's slab is then rebuilt: its staying axions in
- * slot order, then the arrivals ordered by the source cell's position
- * relative to it ((dz, dy, dx) ascending lexicographic over {-1, 0, 1}^3),
- * then by source slot. Axions beyond the capacity are dropped, counted and
- * latch AXPIC_E_CAPACITY. Asynchronous on the context's stream; the first
+ * does not move. Each cell's arrivals, ordered by the source cell's position
+ * relative to it ((dz, dy, dx) ascending lexicographic over {-1, 0, 1}^3)
+ * and then by source slot, take the slots its leaving axions freed
+ * (ascending), then the slots after the old count; freed slots left over are
+ * closed by the tail fill (the slot rule of a full step's axions). Staying
+ * axions keep their slots unless the tail fill moves them. Axions beyond the
+ * capacity are dropped, counted and latch AXPIC_E_CAPACITY. Asynchronous on the context's stream; the first
  * call allocates scratch (33 bytes per axion slot plus 216 per cell), later
  * calls allocate nothing. AXPIC_E_INVALID (nothing launched) for a grid
  * that does not match, h_cm <= 0, dt_s < 0, c dt_s >= h_cm or another

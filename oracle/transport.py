@@ -22,15 +22,19 @@ Readings of the paper (it is silent on each):
   d = (kappa / |p|) p_dim with kappa = binary32(c dt / h);
   t = x + d; s = floor(t) in {-1, 0, 1}; t = t - s, and t = the largest
   binary32 below 1 where that rounds up to 1. |p| = 0 does not move.
-* Re-binning: a cell keeps its staying axions in slot order, then takes the
-  arrivals ordered by the position of their source cell relative to it,
-  (dz, dy, dx) in ascending lexicographic order over {-1, 0, 1}^3, then by
-  source slot. Axions beyond the slab capacity are dropped and counted.
+* Re-binning: the arrivals of a cell are ordered by the position of their
+  source cell relative to it, (dz, dy, dx) in ascending lexicographic order
+  over {-1, 0, 1}^3, then by source slot. They take the slots the cell's
+  leaving axions freed, in ascending order; arrivals beyond those are
+  appended after the old count, and freed slots left over are closed by the
+  tail fill (step.recycle, the slot rule of a full step's axions). Staying
+  axions keep their slots unless the tail fill moves them. Axions beyond the
+  slab capacity are dropped and counted.
 """
 import numpy as np
 
 from . import constants as K
-from .step import Species
+from .step import Species, recycle
 
 C_CM_S = 2.99792458e10
 _ONE_BELOW = np.nextafter(np.float32(1.0), np.float32(0.0))
@@ -95,7 +99,8 @@ def stream(cells, dims, h_cm, dt_s, periodic, cap):
     for d in range(len(cells)):
         i, j, k = d % nx, (d // nx) % ny, d // (nx * ny)
         m, sh = moved[d]
-        parts = [m.take(np.flatnonzero((dest[d] == d) & np.all(sh == 0, axis=1)))]
+        stay = (dest[d] == d) & np.all(sh == 0, axis=1)
+        parts = []
         for dz, dy, dx in offsets():
             si, sj, sk = i + dx, j + dy, k + dz
             if periodic:
@@ -109,9 +114,10 @@ def stream(cells, dims, h_cm, dt_s, periodic, cap):
             # the axions of src that moved by (-dx, -dy, -dz) into d
             sel = np.flatnonzero((dest[src] == d) & (shs[:, 0] == -dx) & (shs[:, 1] == -dy) & (shs[:, 2] == -dz))
             parts.append(ms.take(sel))
-        cell = parts[0]
-        for p in parts[1:]:
-            cell = cell.concat(p)
+        arrivals = Species.empty()
+        for p in parts:
+            arrivals = arrivals.concat(p)
+        cell = recycle(m, stay, arrivals)
         if len(cell) > cap:
             dropped += len(cell) - cap
             cell = cell.take(np.arange(cap))

@@ -8,11 +8,13 @@
 //    new position in place, the direction of each slot and the count per
 //    direction, and copies the leaving axions into the cell's staging rows,
 //    grouped by direction in slot order.
-//  * stream_place_kernel compacts the cell's staying axions in place (slot
-//    order), then appends the arrivals from its neighbours' staging rows,
-//    ordered by the neighbour's position relative to it, (dz, dy, dx)
-//    ascending, then by source slot. Slots beyond the capacity are dropped,
-//    counted, and latch ERR_CAPACITY.
+//  * stream_place_kernel takes the arrivals from its neighbours' staging
+//    rows, ordered by the neighbour's position relative to it, (dz, dy, dx)
+//    ascending, then by source slot, into the slots its own leavers freed
+//    (ascending), then after the old count; freed slots left over are closed
+//    by the tail fill. Staying axions keep their slots unless the tail fill
+//    moves them. Slots beyond the capacity are dropped, counted, and latch
+//    ERR_CAPACITY.
 // The first kernel writes only its own cell's slots and rows; the second
 // reads the neighbours' rows and writes only its own slab, so neither needs
 // a barrier across cells.
@@ -138,29 +140,12 @@ __global__ void __launch_bounds__(kThreads) stream_place_kernel(StreamArgs a) {
     const int n = min(max(s.count[c], 0), s.cap);
     const long base = (long)c * s.cap;
     const int ci = c % a.nx, cj = (c / a.nx) % a.ny, ck = c / (a.nx * a.ny);
-    // the staying axions, in slot order, in place (a slot moves only down)
-    int total = 0;
-    for (int s0 = 0; s0 < n; s0 += 32) {
-      const int slot = s0 + lane;
-      const bool stay = slot < n && a.dir[base + slot] == kStreamStay;
-      const unsigned b = __ballot_sync(kAll, stay);
-      float f[7];
-      if (stay) {
-        const long q = base + slot;
-        f[0] = s.w[q], f[1] = s.px[q], f[2] = s.py[q], f[3] = s.pz[q], f[4] = s.x[q], f[5] = s.y[q], f[6] = s.z[q];
-      }
-      __syncwarp();
-      if (stay) {
-        const long q = base + total + __popc(b & lt);
-        s.w[q] = f[0], s.px[q] = f[1], s.py[q] = f[2], s.pz[q] = f[3], s.x[q] = f[4], s.y[q] = f[5], s.z[q] = f[6];
-      }
-      total += __popc(b);
-      __syncwarp();
-    }
+    // freed slots: every slot of the cell that did not stay
+    const int H = n - a.cnt[(size_t)c * kStreamDirs + kStreamStay];
     // arrivals: lane r (r < 27, r != 13) takes the neighbour at (dz, dy, dx)
     // = r's digits - 1, lanes ascending in r; that neighbour's axions that
     // moved here have the shift -(dz, dy, dx), direction 26 - r. Every
-    // lane's group is found at once; a scan places the groups in r order.
+    // lane's group is found at once; a scan orders the groups by r.
     int m = 0, src = 0, g = 0;
     if (lane < kStreamDirs && lane != kStreamStay) {
       const int r = lane;
@@ -187,11 +172,12 @@ __global__ void __launch_bounds__(kThreads) stream_place_kernel(StreamArgs a) {
       const int t = __shfl_up_sync(kAll, incl, d);
       if (lane >= d) incl += t;
     }
-    const int arrivals = __shfl_sync(kAll, incl, 31);
+    const int A = __shfl_sync(kAll, incl, 31);
     const int excl = incl - m;
-    for (int t0 = 0; t0 < arrivals; t0 += 32) {
+    // arrival t takes freed slot t (ascending) while there are any, then
+    // slot n + (t - H)
+    for (int t0 = 0; t0 < A; t0 += 32) {
       const int t = t0 + lane;
-      // the group holding arrival t: the last lane whose first arrival is <= t
       int sel = 0;
 #pragma unroll
       for (int r = 1; r < kStreamDirs; ++r) {
@@ -200,8 +186,19 @@ __global__ void __launch_bounds__(kThreads) stream_place_kernel(StreamArgs a) {
       }
       const int e = __shfl_sync(kAll, excl, sel);
       const int gs = __shfl_sync(kAll, g, sel), ss = __shfl_sync(kAll, src, sel);
-      const int dst = total + t;
-      if (t < arrivals && dst < s.cap) {
+      int dst = n + (t - H);
+      const int need = min(t0 + 32, H);  // freed slots this round: indices t0 .. need - 1
+      if (t0 < need) {
+        int run = 0;
+        for (int s0 = 0; s0 < n && run < need; s0 += 32) {
+          const int slot = s0 + lane;
+          const unsigned hm = __ballot_sync(kAll, slot < n && a.dir[base + slot] != kStreamStay);
+          const int k = t - run;
+          if (t < H && k >= 0 && k < __popc(hm)) dst = s0 + (int)__fns(hm, 0, k + 1);
+          run += __popc(hm);
+        }
+      }
+      if (t < A && dst < s.cap) {
         const float* row = a.buf + ((size_t)ss * s.cap + gs + (t - e)) * 8;
         const float4 u0 = reinterpret_cast<const float4*>(row)[0];
         const float4 u1 = reinterpret_cast<const float4*>(row)[1];
@@ -209,7 +206,40 @@ __global__ void __launch_bounds__(kThreads) stream_place_kernel(StreamArgs a) {
         s.w[q] = u0.x, s.px[q] = u0.y, s.py[q] = u0.z, s.pz[q] = u0.w, s.x[q] = u1.x, s.y[q] = u1.y, s.z[q] = u1.z;
       }
     }
-    total += arrivals;
+    __syncwarp();
+    // fewer arrivals than freed slots: the freed slots left over (indices A
+    // .. H - 1) below the new count ns take, in ascending order, the kept
+    // slots at or beyond ns (stayers and filled slots), in ascending order
+    if (A < H) {
+      const int ns = n - (H - A);
+      for (int j0 = 0;; j0 += 32) {
+        const int j = j0 + lane;
+        int from = -1, to = -1, runH = 0, runTo = 0, runFrom = 0;
+        for (int s0 = 0; s0 < n; s0 += 32) {
+          const int slot = s0 + lane;
+          const bool freed = slot < n && a.dir[base + slot] != kStreamStay;
+          const unsigned hm = __ballot_sync(kAll, freed);
+          const bool left = freed && runH + __popc(hm & lt) >= A;  // freed and not filled
+          const unsigned tm = __ballot_sync(kAll, left && slot < ns);
+          const unsigned fm = __ballot_sync(kAll, slot < n && slot >= ns && !left);
+          int k = j - runTo;
+          if (k >= 0 && k < __popc(tm)) to = s0 + (int)__fns(tm, 0, k + 1);
+          k = j - runFrom;
+          if (k >= 0 && k < __popc(fm)) from = s0 + (int)__fns(fm, 0, k + 1);
+          runH += __popc(hm);
+          runTo += __popc(tm);
+          runFrom += __popc(fm);
+        }
+        if (j < runTo && from >= 0 && to >= 0) {
+          const long qf = base + from, qt = base + to;
+          const float w = s.w[qf], px = s.px[qf], py = s.py[qf], pz = s.pz[qf], x = s.x[qf], y = s.y[qf],
+                      z = s.z[qf];
+          s.w[qt] = w, s.px[qt] = px, s.py[qt] = py, s.pz[qt] = pz, s.x[qt] = x, s.y[qt] = y, s.z[qt] = z;
+        }
+        if (j0 + 32 >= runTo) break;
+      }
+    }
+    const int total = n - H + A;
     if (lane == 0) {
       s.count[c] = min(total, s.cap);
       if (total > s.cap) {

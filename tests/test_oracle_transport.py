@@ -130,8 +130,9 @@ def test_open_box_escapes_count_weight_and_energy():
 
 
 def test_arrival_order():
-    """A cell keeps its stayers in slot order, then takes arrivals by the
-    (dz, dy, dx) of their source relative to it, ascending, then source slot."""
+    """Arrivals are ordered by the (dz, dy, dx) of their source relative to
+    the cell, ascending, then by source slot (here all appended after the
+    cell's stayers, which keep their slots)."""
     f = np.float32
     dims = (3, 3, 1)
     h = 1e-4
@@ -151,6 +152,37 @@ def test_arrival_order():
     put(1, 6.0, 0.0, 1e-3, 0.5, 0.9)        # second from (1, 0), later slot
     new, _, _ = TR.stream(cells, dims, h, dt, True, 16)
     assert [float(v) for v in new[centre].w] == [1.0, 3.0, 4.0, 6.0, 5.0, 2.0]
+
+
+def test_arrivals_fill_the_freed_slots():
+    """Arrivals take the slots of the cell's leavers in ascending order,
+    extras are appended; with fewer arrivals than freed slots the tail fill
+    closes the rest (survivors at or beyond the new count move down, in
+    order)."""
+    f = np.float32
+    dims = (3, 1, 1)
+    h = 1e-4
+    dt = 0.5 * h / C
+
+    def sp(ws, pxs, xs):
+        n = len(ws)
+        return Species(np.array(ws, f), np.array(pxs, f), np.zeros(n, f), np.zeros(n, f), np.array(xs, f),
+                       np.full(n, 0.5, f), np.full(n, 0.5, f))
+
+    # cell 1: slots 0 and 2 leave (+x), 1 and 3 stay; cell 0 sends one arrival
+    cells = [sp([10.0], [1e-3], [0.8]), sp([1.0, 2.0, 3.0, 4.0], [1e-3, 0.0, 1e-3, 0.0], [0.7, 0.5, 0.9, 0.5]),
+             Species.empty()]
+    new, _, _ = TR.stream(cells, dims, h, dt, False, 8)
+    # slot 0 takes the arrival (w 10); slot 2 is left over: the survivor count
+    # is 3, so slot 2 stays a hole below it and takes slot 3 (w 4)
+    assert [float(v) for v in new[1].w] == [10.0, 2.0, 4.0]
+    # cell 2: no freed slots, two arrivals appended in source-slot order
+    assert [float(v) for v in new[2].w] == [1.0, 3.0]
+    # more arrivals than freed slots
+    cells = [sp([10.0, 11.0], [1e-3, 1e-3], [0.8, 0.9]), sp([1.0, 2.0], [1e-3, 0.0], [0.7, 0.5]),
+             Species.empty()]
+    new, _, _ = TR.stream(cells, dims, h, dt, False, 8)
+    assert [float(v) for v in new[1].w] == [10.0, 2.0, 11.0]
 
 
 def test_one_cell_dimension_is_not_streamed():
