@@ -226,3 +226,42 @@ def test_training_on_gpu_learns_the_targets():
     assert np.median(eL) < 0.25 * np.median(eL0), (np.median(eL), np.median(eL0))
     net.close()
     net0.close()
+
+
+def test_trained_network_within_the_bound_where_trusted():
+    """The network as the c3 measurement trains it, trusted where its four
+    validation nodes are within 5e-4: at least 90 % of the nodes pass, and
+    on 160 random cells of the domain every record the network writes has
+    its three ln-emissivity rows within 1e-3 of the exact targets at the 30
+    grid points inside [0.05, 20] (cells it does not trust keep the table)."""
+    net = SurrogateNet()
+    _lib.axpic_surrogate_fit(net.h, 65536, 1, 40000, 8192, 2e-3, 7)
+    nT, nne = 24, 16
+    eL, eQ = _lib.axpic_surrogate_validate(net.h, nT, nne)
+    assert np.mean(eL <= 5e-4) >= 0.9, np.mean(eL <= 5e-4)
+    rng = np.random.default_rng(31)
+    n = 160
+    T = rng.uniform(0.6, 9.5, n)
+    ne = 10 ** rng.uniform(23.1, 25.9, n)
+    kw = dict(counts=(8, 8, 4), caps=(16, 64, 64))
+    pl = make(T, ne, params(2), **kw)
+    ref = make(T, ne, params(1), **kw)
+    err_map = np.stack([eL, eQ], axis=-1).astype(np.float32).reshape(-1)
+    _lib.axpic_set_surrogate(pl.ctx, net.h, err_map, nT, nne, 5e-4)
+    a = _lib.axpic_get_spectral_records(pl.ctx, 0, n)
+    b = _lib.axpic_get_spectral_records(ref.ctx, 0, n)
+    on_net = np.any(a[:, :189] != b[:, :189], axis=1)
+    assert on_net.sum() >= 0.7 * n, on_net.sum()
+    h = math.log(400.0) / 29.0
+    xk = 0.05 * np.exp(h * (np.arange(1, 31) - 1.0))
+    worst = 0.0
+    for c in np.flatnonzero(on_net):
+        cs, _ = S.cell(T[c], ne[c], 1)
+        rows = np.stack([xk, np.full(30, cs.kappa_keV / T[c]), np.full(30, ne[c]), np.ones(30)], 1)
+        y = _lib.axpic_surrogate_targets(rows)
+        for ch in range(3):
+            worst = max(worst, float(np.max(np.abs(a[c, 32 * ch + 1:32 * ch + 31] - xk - y[:, 32 * ch]))))
+    assert worst <= 1e-3, worst
+    net.close()
+    pl.close()
+    ref.close()
