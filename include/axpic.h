@@ -207,17 +207,19 @@ axpic_status axpic_sample_plasma(axpic_ctx *ctx, int32_t n_el, int32_t n_ph, int
 axpic_status axpic_update_cells(axpic_ctx *ctx);
 
 /* Axion free streaming and cell migration: every axion moves by
- * (p / |p|) c dt_s (Sec. II, the axions' transport between steps) on a
+ * (p / E) c dt_s, E = sqrt(p^2 + m_a^2) with m_a c^2 = mass_keV (Sec. II.B:
+ * massless axions at c, massive ones sub-luminal; the axions' transport
+ * between steps) on a
  * regular grid of nx x ny x nz cubic cells of edge h_cm [cm], cell index
  * (k ny + j) nx + i (nx ny nz must equal ncells). Positions are fractions of
  * the cell; a dimension of one cell is not streamed. c dt_s must stay below
  * h_cm (at most one cell per dimension and step). boundary 0: periodic;
  * 1: open (axions leaving the box are removed and counted, see
  * axpic_stream_stats). The position update is binary32 with each rounding
- * fixed: |p| = sqrt((px px + py py) + pz pz), d = (kappa / |p|) p_dim with
- * kappa = binary32(c dt / h), t = x + d, shift floor(t), fraction t -
- * shift (the largest binary32 below 1 where that rounds up to 1); |p| = 0
- * does not move. Each cell's arrivals, ordered by the source cell's position
+ * fixed: E = sqrt(((px px + py py) + pz pz) + mu mu) with mu =
+ * binary32(mass_keV / m_e c^2), d = (kappa / E) p_dim with kappa =
+ * binary32(c dt / h), t = x + d, shift floor(t), fraction t - shift (the
+ * largest binary32 below 1 where that rounds up to 1); E = 0 does not move. Each cell's arrivals, ordered by the source cell's position
  * relative to it ((dz, dy, dx) ascending lexicographic over {-1, 0, 1}^3)
  * and then by source slot, take the slots its leaving axions freed
  * (ascending), then the slots after the old count; freed slots left over are
@@ -227,13 +229,14 @@ axpic_status axpic_update_cells(axpic_ctx *ctx);
  * call allocates scratch (33 bytes per axion slot plus 216 per cell), later
  * calls allocate nothing. AXPIC_E_INVALID (nothing launched) for a grid
  * that does not match, h_cm <= 0, dt_s < 0, c dt_s >= h_cm or another
- * boundary value. */
+ * boundary value, or a negative mass. */
 axpic_status axpic_stream_axions(axpic_ctx *ctx, int32_t nx, int32_t ny, int32_t nz, double h_cm, double dt_s,
-                                 int32_t boundary);
+                                 double mass_keV, int32_t boundary);
 
 /* Totals of every axpic_stream_axions call so far, to out (host, 4
  * doubles): axions that left an open box (number, weight, weight x energy
- * [keV]) and axions dropped at a full slab (number). Zeros before the first
+ * [keV], the total energy sqrt(p^2 + m_a^2)) and axions dropped at a full
+ * slab (number). Zeros before the first
  * call. Synchronises. */
 axpic_status axpic_stream_stats(axpic_ctx *ctx, double *out);
 

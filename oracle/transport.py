@@ -4,10 +4,11 @@ Test infrastructure only (imported by tests/). Nothing here is blocked or
 fused: each axion is moved, then every cell's slots are rebuilt from the
 moved axions in the order defined below.
 
-What it computes. Massless axions move at the speed of light along their
-momentum, x += (p / |p|) c dt (Sec. II, the free-streaming transport of the
-axion macroparticles between the emission and absorption steps). Positions
-are fractions of the cell in [0, 1).
+What it computes. Axions move along their momentum at v = p / E c with
+E = sqrt(p^2 + m_a^2) (Sec. II.B: massless axions at c, v = p / |p|;
+massive ones sub-luminal): x += (p / E) c dt, the free-streaming transport
+of the axion macroparticles between the emission and absorption steps.
+Positions are fractions of the cell in [0, 1).
 
 Readings of the paper (it is silent on each):
 * The grid is regular: nx x ny x nz cubic cells of edge h [cm], cell index
@@ -18,10 +19,13 @@ Readings of the paper (it is silent on each):
 * Boundaries are periodic (leaving one side enters the other) or open (an
   axion leaving the box is removed and counted).
 * The position update is binary32, since it decides the destination cell:
-  |p| = sqrt((px px + py py) + pz pz), each operation rounded;
-  d = (kappa / |p|) p_dim with kappa = binary32(c dt / h);
+  E = sqrt(((px px + py py) + pz pz) + mu mu), each operation rounded, with
+  mu = binary32(m_a c^2 / m_e c^2) (momenta are in m_e c);
+  d = (kappa / E) p_dim with kappa = binary32(c dt / h);
   t = x + d; s = floor(t) in {-1, 0, 1}; t = t - s, and t = the largest
-  binary32 below 1 where that rounds up to 1. |p| = 0 does not move.
+  binary32 below 1 where that rounds up to 1. E = 0 does not move.
+* The energy counted for an axion leaving an open box is its total energy
+  sqrt(p^2 + m_a^2) (in keV, times its weight).
 * Re-binning: the arrivals of a cell are ordered by the position of their
   source cell relative to it, (dz, dy, dx) in ascending lexicographic order
   over {-1, 0, 1}^3, then by source slot. They take the slots the cell's
@@ -46,20 +50,21 @@ def offsets():
             if (dz, dy, dx) != (0, 0, 0)]
 
 
-def stream(cells, dims, h_cm, dt_s, periodic, cap):
-    """cells: list of Species (axions, slot order) indexed (k ny + j) nx + i.
-    Returns (new cells, escaped [number, weight, weight x energy keV],
-    dropped number)."""
+def stream(cells, dims, h_cm, dt_s, periodic, cap, mass_keV=0.0):
+    """cells: list of Species (axions, slot order) indexed (k ny + j) nx + i;
+    mass_keV: the axion mass m_a c^2. Returns (new cells, escaped [number,
+    weight, weight x energy keV], dropped number)."""
     nx, ny, nz = dims
     assert len(cells) == nx * ny * nz
     f = np.float32
     kappa = f(C_CM_S * dt_s / h_cm)
     assert kappa <= 1.0, "a step may move an axion at most one cell"
+    mu = f(mass_keV / K.ME_C2_KEV)
     n_dim = (nx, ny, nz)
     moved = []  # per source cell: (Species with new positions, shift per axion [n, 3] as (sx, sy, sz))
     for s in cells:
         px, py, pz = (np.asarray(v, dtype=np.float32) for v in (s.px, s.py, s.pz))
-        pn = np.sqrt((px * px + py * py) + pz * pz)
+        en = np.sqrt(((px * px + py * py) + pz * pz) + mu * mu)
         newpos, shifts = [], []
         for dim, (pc, q) in enumerate(zip((px, py, pz), (s.x, s.y, s.z))):
             q = np.asarray(q, dtype=np.float32)
@@ -68,7 +73,7 @@ def stream(cells, dims, h_cm, dt_s, periodic, cap):
                 shifts.append(np.zeros(len(q), dtype=np.int64))
                 continue
             with np.errstate(divide="ignore", invalid="ignore"):
-                d = np.where(pn > 0, (kappa / pn) * pc, f(0.0)).astype(np.float32)
+                d = np.where(en > 0, (kappa / en) * pc, f(0.0)).astype(np.float32)
             t = (q + d).astype(np.float32)
             sh = np.floor(t).astype(np.float32)
             t = (t - sh).astype(np.float32)
@@ -89,7 +94,8 @@ def stream(cells, dims, h_cm, dt_s, periodic, cap):
                 ii, jj, kk = ii % nx, jj % ny, kk % nz
             elif not (0 <= ii < nx and 0 <= jj < ny and 0 <= kk < nz):
                 out[a] = -1
-                E = float(np.sqrt(float(m.px[a]) ** 2 + float(m.py[a]) ** 2 + float(m.pz[a]) ** 2)) * K.ME_C2_KEV
+                E = float(np.sqrt(float(m.px[a]) ** 2 + float(m.py[a]) ** 2 + float(m.pz[a]) ** 2
+                                  + float(mu) ** 2)) * K.ME_C2_KEV
                 escaped += (1.0, float(m.w[a]), float(m.w[a]) * E)
                 continue
             out[a] = (kk * ny + jj) * nx + ii

@@ -127,7 +127,7 @@ EXPORTS = {
                                          ctypes.POINTER(ctypes.c_int32)]),
     "axpic_step_kernel_names": (ctypes.c_char_p, [ctypes.c_void_p]),
     "axpic_stream_axions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                           ctypes.c_double, ctypes.c_double, ctypes.c_int32]),
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32]),
     "axpic_stream_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "axpic_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "axpic_destroy": (ctypes.c_int, [ctypes.c_void_p]),
@@ -416,9 +416,9 @@ def axpic_set_surrogate(ctx, net_handle, err_map, nT, nne, tol):
     _check(ctx, lib().axpic_set_surrogate(ctx, net_handle, _fptr(e), nT, nne, tol))
 
 
-def axpic_stream_axions(ctx, dims, h_cm, dt_s, boundary):
+def axpic_stream_axions(ctx, dims, h_cm, dt_s, boundary, mass_keV=0.0):
     nx, ny, nz = dims
-    _check(ctx, lib().axpic_stream_axions(ctx, nx, ny, nz, h_cm, dt_s, boundary))
+    _check(ctx, lib().axpic_stream_axions(ctx, nx, ny, nz, h_cm, dt_s, mass_keV, boundary))
 
 
 def axpic_stream_stats(ctx):

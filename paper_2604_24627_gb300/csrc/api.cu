@@ -977,13 +977,14 @@ axpic_status axpic_set_surrogate(axpic_ctx* ctx, axpic_mlp* m, const float* err_
 }
 
 axpic_status axpic_stream_axions(axpic_ctx* ctx, int32_t nx, int32_t ny, int32_t nz, double h_cm, double dt_s,
-                                 int32_t boundary) {
+                                 double mass_keV, int32_t boundary) {
   if (!ctx) return AXPIC_E_INVALID;
   const axpic_plasma_desc& d = ctx->desc;
   if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz != d.ncells)
     return fail(ctx, AXPIC_E_INVALID, "axpic_stream_axions: nx ny nz must give the context's cells");
-  if (!(h_cm > 0) || !std::isfinite(h_cm) || !(dt_s >= 0) || !std::isfinite(dt_s) || (boundary != 0 && boundary != 1))
-    return fail(ctx, AXPIC_E_INVALID, "axpic_stream_axions: h, dt or boundary");
+  if (!(h_cm > 0) || !std::isfinite(h_cm) || !(dt_s >= 0) || !std::isfinite(dt_s) || !(mass_keV >= 0) ||
+      !std::isfinite(mass_keV) || (boundary != 0 && boundary != 1))
+    return fail(ctx, AXPIC_E_INVALID, "axpic_stream_axions: h, dt, mass or boundary");
   const float kappa = (float)(2.99792458e10 * dt_s / h_cm);
   if (!(kappa < 1.0f - 0x1p-20f))
     return fail(ctx, AXPIC_E_INVALID, "axpic_stream_axions: c dt must stay below the cell edge");
@@ -1002,6 +1003,7 @@ axpic_status axpic_stream_axions(axpic_ctx* ctx, int32_t nx, int32_t ny, int32_t
   a.ny = ny;
   a.nz = nz;
   a.kappa = kappa;
+  a.mu = (float)(mass_keV / kMeC2);
   a.periodic = boundary == 0;
   a.dir = ctx->st_dir;
   a.cnt = ctx->st_cnt;

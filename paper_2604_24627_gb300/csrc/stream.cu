@@ -1,6 +1,7 @@
-// Axion free streaming and cell migration: x += (p / |p|) c dt (Sec. II, the
-// transport of the axion macroparticles between steps) on the cell-sorted
-// slabs, positions being fractions of the cell.
+// Axion free streaming and cell migration: x += (p / E) c dt with E =
+// sqrt(p^2 + m_a^2) (Sec. II.B: massless axions at c, massive ones
+// sub-luminal; the transport of the axion macroparticles between steps) on
+// the cell-sorted slabs, positions being fractions of the cell.
 //
 // Two kernels, a warp per cell each (grid-stride):
 //  * stream_move_kernel moves every axion of its cell, in binary32 with each
@@ -74,11 +75,13 @@ __global__ void __launch_bounds__(kThreads) stream_move_kernel(StreamArgs a) {
         const int slot = s0 + 32 * hh + lane;
         if (slot >= n) continue;
         const long q = base + slot;
-        const float pn = __fsqrt_rn(
-            __fadd_rn(__fadd_rn(__fmul_rn(px[hh], px[hh]), __fmul_rn(py[hh], py[hh])), __fmul_rn(pz[hh], pz[hh])));
+        // E = sqrt(p^2 + mu^2): v = p / E in units of c
+        const float en = __fsqrt_rn(__fadd_rn(
+            __fadd_rn(__fadd_rn(__fmul_rn(px[hh], px[hh]), __fmul_rn(py[hh], py[hh])), __fmul_rn(pz[hh], pz[hh])),
+            __fmul_rn(a.mu, a.mu)));
         int sx = 0, sy = 0, sz = 0;
-        if (pn > 0.f) {
-          const float k = __fdiv_rn(a.kappa, pn);
+        if (en > 0.f) {
+          const float k = __fdiv_rn(a.kappa, en);
           if (a.nx > 1) a.s.x[q] = advance(x[hh], __fmul_rn(k, px[hh]), &sx);
           if (a.ny > 1) a.s.y[q] = advance(y[hh], __fmul_rn(k, py[hh]), &sy);
           if (a.nz > 1) a.s.z[q] = advance(z[hh], __fmul_rn(k, pz[hh]), &sz);
@@ -89,7 +92,8 @@ __global__ void __launch_bounds__(kThreads) stream_move_kernel(StreamArgs a) {
           if (ii < 0 || ii >= a.nx || jj < 0 || jj >= a.ny || kk < 0 || kk >= a.nz) {
             o = kStreamEscaped;
             const double w = (double)a.s.w[q];
-            const double pm = sqrt((double)px[hh] * px[hh] + (double)py[hh] * py[hh] + (double)pz[hh] * pz[hh]);
+            const double pm = sqrt((double)px[hh] * px[hh] + (double)py[hh] * py[hh] + (double)pz[hh] * pz[hh] +
+                                   (double)a.mu * a.mu);
             atomicAdd(a.stats + 0, 1.0);
             atomicAdd(a.stats + 1, w);
             atomicAdd(a.stats + 2, w * pm * kMeC2);

@@ -15,6 +15,7 @@ struct StreamArgs {
   SpeciesPtrs s;       // the axion slabs (positions rewritten, slots re-binned)
   int ncells, nx, ny, nz;
   float kappa;         // binary32(c dt / h): the cell fraction moved at |v| = c
+  float mu;            // binary32(m_a c^2 / m_e c^2): the axion mass in units of the momenta
   int periodic;        // 1 periodic, 0 open
   uint8_t* dir;        // [ncells * cap]: direction of each slot
   int32_t* cnt;        // [ncells * 27]: slots per direction

@@ -156,10 +156,11 @@ class AxionPlasma:
         _lib.axpic_get_residuals(self.ctx, first, count, buf)
         return np.array(buf)[:4 * count].reshape(count, 4)
 
-    def stream_axions(self, dims, h_cm, dt_s, periodic=True):
+    def stream_axions(self, dims, h_cm, dt_s, periodic=True, mass_keV=0.0):
         """Axion free streaming and cell migration on an nx x ny x nz grid
-        (axpic_stream_axions); asynchronous."""
-        _lib.axpic_stream_axions(self.ctx, dims, h_cm, dt_s, 0 if periodic else 1)
+        (axpic_stream_axions); mass_keV: the axion mass (0: massless, at c);
+        asynchronous."""
+        _lib.axpic_stream_axions(self.ctx, dims, h_cm, dt_s, 0 if periodic else 1, mass_keV)
 
     def stream_stats(self):
         """[escaped number, escaped weight, escaped weight x energy (keV),

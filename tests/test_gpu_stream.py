@@ -71,10 +71,12 @@ def assert_cells_equal(got, want):
             assert np.array_equal(getattr(g, f), np.asarray(getattr(w, f), dtype=np.float32)), (c, f)
 
 
-@pytest.mark.parametrize("dims,periodic", [((5, 4, 3), True), ((5, 4, 3), False), ((9, 7, 1), True),
-                                           ((9, 7, 1), False), ((33, 1, 1), True)])
-def test_streaming_matches_oracle(dims, periodic):
-    rng = np.random.default_rng(hash((dims, periodic)) % 2 ** 32)
+@pytest.mark.parametrize("dims,periodic,mass", [((5, 4, 3), True, 0.0), ((5, 4, 3), False, 0.0),
+                                                ((9, 7, 1), True, 0.0), ((9, 7, 1), False, 0.0),
+                                                ((33, 1, 1), True, 0.0), ((5, 4, 3), False, 4.0),
+                                                ((9, 7, 1), True, 12.0)])
+def test_streaming_matches_oracle(dims, periodic, mass):
+    rng = np.random.default_rng(hash((dims, periodic, mass)) % 2 ** 32)
     n = int(np.prod(dims))
     cap = 96
     cells = [random_axions(rng, int(rng.integers(0, 40))) if rng.uniform() > 0.1 else random_axions(rng, 0)
@@ -85,8 +87,8 @@ def test_streaming_matches_oracle(dims, periodic):
     dt = kappa * h / C
     esc_total = np.zeros(3)
     for _ in range(5):
-        pl.stream_axions(dims, h, dt, periodic)
-        cells, esc, dropped = TR.stream(cells, dims, h, dt, periodic, cap)
+        pl.stream_axions(dims, h, dt, periodic, mass_keV=mass)
+        cells, esc, dropped = TR.stream(cells, dims, h, dt, periodic, cap, mass_keV=mass)
         esc_total += esc
         assert dropped == 0
     torch.cuda.synchronize()
@@ -125,6 +127,8 @@ def test_invalid_grid_or_step_launches_nothing():
         pl.stream_axions((4, 3, 1), 1e-4, 1e-4 / C, True)  # c dt = h
     with pytest.raises(_lib.AxpicError):
         pl.stream_axions((4, 3, 1), -1.0, 1e-15, True)
+    with pytest.raises(_lib.AxpicError):
+        pl.stream_axions((4, 3, 1), 1e-4, 1e-15, True, mass_keV=-1.0)
     assert list(pl.stream_stats()) == [0, 0, 0, 0]
     pl.close()
 

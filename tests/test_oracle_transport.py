@@ -49,9 +49,31 @@ def test_straight_line_closed_form():
         assert float(cells[where[0]].y[0]) == 0.5 and float(cells[where[0]].w[0]) == f(1.5)
 
 
+def test_massive_axion_moves_at_p_over_E():
+    """A massive axion along +x moves kappa p / sqrt(p^2 + m^2) cells a step
+    (sub-luminal); a massless one with the same momentum moves kappa."""
+    dims = (11, 1, 1)
+    h, kappa = 1e-4, 0.5
+    dt = kappa * h / C
+    f = np.float32
+    p = 4.0 / 511.0
+    m_keV = 3.0
+    beta = p / math.sqrt(p * p + (m_keV / 510.99895) ** 2)
+    cells = [Species.empty() for _ in range(11)]
+    cells[0] = Species(np.array([1.0], f), np.array([p], f), np.zeros(1, f), np.zeros(1, f), np.array([0.0], f),
+                       np.array([0.5], f), np.array([0.5], f))
+    for n in range(1, 31):
+        cells, _, _ = TR.stream(cells, dims, h, dt, True, 8, mass_keV=m_keV)
+        where = [c for c in range(11) if len(cells[c])]
+        X = (n * kappa * beta) % 11
+        assert where == [int(X)] and abs(float(cells[where[0]].x[0]) - (X - int(X))) < 2e-5
+    assert 0.7 < beta < 0.9
+
+
+@pytest.mark.parametrize("mass", [0.0, 5.0])
 @pytest.mark.parametrize("periodic", [True, False])
 @pytest.mark.parametrize("dims", [(5, 4, 3), (6, 5, 1)])
-def test_brute_force_global_coordinates(periodic, dims):
+def test_brute_force_global_coordinates(periodic, dims, mass):
     """Every axion's new cell and fraction from its global coordinate
     X = i + x + kappa p_x / |p| in FP64 (per dimension), wrapped or dropped at
     the box; a dimension of one cell is not moved. The oracle's binary32
@@ -62,9 +84,10 @@ def test_brute_force_global_coordinates(periodic, dims):
     h, kappa = 1e-4, 0.8
     dt = kappa * h / C
     cells = grid_cells(rng, dims, 12)
-    new, esc, dropped = TR.stream(cells, dims, h, dt, periodic, 64)
+    new, esc, dropped = TR.stream(cells, dims, h, dt, periodic, 64, mass_keV=mass)
     assert dropped == 0
     want, n_esc = {}, 0
+    mu = mass / 510.99895
     for c, s in enumerate(cells):
         i, j, k = c % nx, (c // nx) % ny, c // (nx * ny)
         for a in range(len(s)):
@@ -72,7 +95,7 @@ def test_brute_force_global_coordinates(periodic, dims):
             X = np.array([i + s.x[a], j + s.y[a], k + s.z[a]], dtype=np.float64)
             for d, n in enumerate(dims):
                 if n > 1:
-                    X[d] += kappa * p[d] / np.linalg.norm(p)
+                    X[d] += kappa * p[d] / math.sqrt(float(p @ p) + mu * mu)
             if periodic:
                 X = np.mod(X, dims)
             elif np.any(X < 0) or np.any(X >= dims):
