@@ -306,7 +306,8 @@ def run_batched(args):
                          "traffic": None, "peak_kind": peak_kind,
                          "kernel": "step (%s), graph replay" % " + ".join(kms),
                          "basis": "28 B per electron, 16 B per photon and axion per step",
-                         "kernels_ms_per_step": {k: v / max(nrec, 1) for k, v in kms.items()}},
+                         "kernels_ms_per_step": {k: v / max(nrec, 1) for k, v in kms.items()},
+                 "launch": "CUDA graphs of 32 steps replayed, %d branch(es)" % pl.launch_shape()[2]},
             "gpu_launches": len(kms) * pl.launch_shape()[2] * args.steps + 1, "clocks": clk}
     print(json.dumps(line))
     pl.close()
@@ -358,21 +359,25 @@ def run_rate_models(args):
         for s in range(args.warmup):
             pl.step(s, w.mask)
         pl.tally()
-        pl.profile_begin(args.steps)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
+        # the timed steps: CUDA graphs of 32 steps, replayed (axpic_run_steps)
         e0.record(stream)
-        for k in range(args.steps):
-            pl.step(args.warmup + k, w.mask)
+        pl.run_steps(args.warmup, args.steps, w.mask)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1)
-        kms, nrec = pl.profile_end()
         _, tot = pl.tally()
         parts = tot["part_e"] + tot["part_g"] + tot["part_a"]
+        # the kernel split: events around each kernel of 10 further steps
+        pl.profile_begin(10)
+        for k in range(10):
+            pl.step(args.warmup + args.steps + k, w.mask)
+        kms, nrec = pl.profile_end()
         entry = {"particle_steps_per_s": parts / (ms * 1e-3), "ms_per_step": ms / args.steps,
-                 "kernels_ms_per_step": {k: v / max(nrec, 1) for k, v in kms.items()}}
+                 "kernels_ms_per_step": {k: v / max(nrec, 1) for k, v in kms.items()},
+                 "launch": "CUDA graphs of 32 steps replayed, %d branch(es)" % pl.launch_shape()[2]}
         if model:
             # records of sampled cells against the exact targets at the grid points
             recs = [_lib.axpic_get_spectral_records(pl.ctx, int(c), 1)[0] for c in sample]

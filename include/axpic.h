@@ -136,7 +136,8 @@ typedef struct {
                                graph, each chaining 32 steps with its own step
                                counter, so that one range's decisions overlap
                                another's events (0: 8 up to 2^20 cells, else
-                               1; rate models 1 and 2 use 1). Results do not
+                               1; with rate models 1 and 2 each range also
+                               rebuilds its own records). Results do not
                                depend on it. Not part of the paper's method. */
   int32_t reserved[2];
 } axpic_params;

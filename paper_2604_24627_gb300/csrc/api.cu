@@ -262,6 +262,7 @@ static SrArgs make_sr_args(axpic_ctx* ctx) {
   SrArgs a;
   std::memset(&a, 0, sizeof(a));
   a.ncells = ctx->desc.ncells;
+  a.cell0 = 0;
   a.rec = ctx->rec;
   a.sr = ctx->sr;
   a.tab = ctx->srtab;
@@ -291,10 +292,7 @@ static SrArgs make_sr_args(axpic_ctx* ctx) {
 // whose 32 cells are all flagged exit at once).
 static cudaError_t build_records(axpic_ctx* ctx, cudaStream_t st) {
   if (!ctx->prm.rate_model) return cudaSuccess;
-  const SrArgs a = make_sr_args(ctx);
-  cudaError_t e = a.trust ? launch_sr_mlp(a, st) : cudaSuccess;
-  if (!e) e = launch_sr_table(a, st);
-  return e;
+  return launch_sr_records(make_sr_args(ctx), st);
 }
 
 static void free_events(axpic_ctx* ctx) {
@@ -430,8 +428,7 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
     ctx->ln_gA = (float)std::log(p.g_ae * p.g_ae * p.dt_phys_s * 2.0 * kPi * kPi * hc3 / kKeVerg);
   }
   ctx->dec_chunk = p.decide_chunk ? p.decide_chunk : kDefaultDecChunk;
-  ctx->branches = p.rate_model                       ? 1
-                  : p.step_branches                  ? p.step_branches
+  ctx->branches = p.step_branches                    ? p.step_branches
                   : d.ncells <= kBranchCells         ? kDefaultBranches
                                                      : 1;
   ctx->warps = warps;
@@ -730,7 +727,7 @@ static cudaError_t capture_steps(axpic_ctx* ctx, StepArgs A, int nsteps, cudaStr
   const int n = ctx->desc.ncells;
   const int part = ((n + ctx->branches - 1) / ctx->branches + 127) / 128 * 128;
   cudaError_t e;
-  if (ctx->branches == 1 || sra || part >= n) {
+  if (ctx->branches == 1 || part >= n) {
     for (int k = 0; k < nsteps; ++k)
       if ((e = launch_step(PH_ALL, A, ctx->warps, gs, nullptr, sra))) return e;
     return cudaSuccess;
@@ -748,10 +745,16 @@ static cudaError_t capture_steps(axpic_ctx* ctx, StepArgs A, int nsteps, cudaStr
     B.cell0 = c0;
     B.ncells = std::min(part, n - c0);
     B.step_dev = ctx->step_dev + nb;
+    SrArgs Bsr;
+    if (sra) {  // the branch's records, rebuilt after its temperature update
+      Bsr = *sra;
+      Bsr.cell0 = B.cell0;
+      Bsr.ncells = B.ncells;
+    }
     cudaStream_t bs = ctx->br_stream[nb];
     if ((e = cudaStreamWaitEvent(bs, ctx->br_ev[kMaxBranches], 0))) return e;
     for (int k = 0; k < nsteps; ++k)
-      if ((e = launch_step(PH_ALL, B, ctx->warps, bs, nullptr, nullptr))) return e;
+      if ((e = launch_step(PH_ALL, B, ctx->warps, bs, nullptr, sra ? &Bsr : nullptr))) return e;
     if ((e = cudaEventRecord(ctx->br_ev[nb], bs))) return e;
   }
   for (int b = 0; b < nb; ++b)
@@ -870,7 +873,7 @@ axpic_status axpic_launch_shape(const axpic_ctx* ctx, int32_t* decide_chunk, int
   if (step_branches) {
     const int n = ctx->desc.ncells;
     const int part = ((n + ctx->branches - 1) / ctx->branches + 127) / 128 * 128;
-    *step_branches = (ctx->branches == 1 || ctx->prm.rate_model || part >= n) ? 1 : (n + part - 1) / part;
+    *step_branches = (ctx->branches == 1 || part >= n) ? 1 : (n + part - 1) / part;
   }
   return AXPIC_OK;
 }

@@ -135,8 +135,8 @@ constexpr int kSrTableThreads = 256;
 __global__ void __launch_bounds__(kSrTableThreads) sr_table_kernel(SrArgs a) {
   __shared__ SrInterp ip[32];
   __shared__ int skip[32];
-  const int c0 = blockIdx.x * 32;
-  const int nc = min(32, a.ncells - c0);
+  const int c0 = a.cell0 + blockIdx.x * 32;
+  const int nc = min(32, a.cell0 + a.ncells - c0);
   int need = 0;
   if (threadIdx.x < 32 && (int)threadIdx.x < nc) {
     const int sk = a.trust ? a.net[c0 + threadIdx.x] : 0;
@@ -268,8 +268,8 @@ __global__ void __launch_bounds__(kSrMlpThreads, 4) sr_mlp_kernel(SrArgs a) {
   float* sOut = reinterpret_cast<float*>(sm);              // after layer 3: [128][kSrOutStride]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int r = tid & 127, half = tid >> 7;
-  const int c0 = blockIdx.x * 128;
-  const int nc = min(128, a.ncells - c0);
+  const int c0 = a.cell0 + blockIdx.x * 128;
+  const int nc = min(128, a.cell0 + a.ncells - c0);
   const bool valid = r < nc;
   bool trusted = false;
   if (half == 0) {
@@ -458,6 +458,12 @@ __global__ void __launch_bounds__(kSrMlpThreads, 4) sr_mlp_kernel(SrArgs a) {
 cudaError_t sr_init_kernels() {
   cudaError_t e = cudaFuncSetAttribute(sr_mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSrMlpSmem);
   if (!e) e = cudaFuncSetAttribute(sr_mlp_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
+}
+
+cudaError_t launch_sr_records(const SrArgs& a, cudaStream_t st) {
+  cudaError_t e = a.trust ? launch_sr_mlp(a, st) : cudaSuccess;
+  if (!e) e = launch_sr_table(a, st);
   return e;
 }
 

@@ -31,7 +31,8 @@ constexpr int kSrTabOut = 189;                      // table outputs per node
 
 // Rate-model inputs of the record kernels.
 struct SrArgs {
-  int ncells;
+  int ncells;            // cells of this launch: [cell0, cell0 + ncells)
+  int cell0;             // first cell (a branch of a replayed step: a multiple of 128)
   const float* rec;      // [ncells * kRecLen]
   float* sr;             // [ncells * kSrLen]
   const float* tab;      // [2][nne][nkt][kSrTabOut]
@@ -58,6 +59,10 @@ void build_sr_table(int nkt, int nne, double brems_shape, float* out);
 
 cudaError_t launch_sr_table(const SrArgs& a, cudaStream_t st);
 cudaError_t launch_sr_mlp(const SrArgs& a, cudaStream_t st);
+// The records of cells [cell0, cell0 + ncells) for their current T: the
+// network kernel over the cells where it is trusted (when a trust map is
+// set), then the table kernel over the others.
+cudaError_t launch_sr_records(const SrArgs& a, cudaStream_t st);
 // Lays out layers 2 and 3 of the parameters P (FP32, device) for sr_mlp:
 // out holds (64 * 64 + 96 * 64) bfloat16 values (20 KB, 16-byte aligned).
 cudaError_t launch_sr_weights(const float* P, void* out, cudaStream_t st);

@@ -2010,9 +2010,7 @@ cudaError_t decide_resident_ctas(int chunk, int* out) {
 // rebuilt for the new T (rate models 1 and 2).
 static cudaError_t launch_records_update(const StepArgs& A, const SrArgs* sra, cudaStream_t st) {
   if (!sra || A.T_mode != 2) return cudaSuccess;
-  cudaError_t e = launch_sr_table(*sra, st);
-  if (!e && sra->trust) e = launch_sr_mlp(*sra, st);
-  return e;
+  return launch_sr_records(*sra, st);
 }
 
 cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t st, cudaEvent_t* ev,

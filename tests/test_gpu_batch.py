@@ -96,6 +96,69 @@ def test_branched_replay_equals_step_calls(branches):
     b.close()
 
 
+def make_h(ncells, prm, T=None, caps=(64, 1024, 2048), counts=(61, 37, 13)):
+    """A hydrogen plasma (the rate models' records need one ion species)."""
+    T = np.linspace(1.3, 5.0, ncells) if T is None else T
+    pl = AxionPlasma(ncells, T, np.full((ncells, 1), 6e25), [1.0], [A_H], 1e-12, caps, prm)
+    pl.sample(*counts)
+    torch.cuda.synchronize()
+    return pl
+
+
+@pytest.mark.parametrize("model", [1, 2])
+def test_branched_replay_with_records_equals_step_calls(model):
+    """Evolved-T steps with spectral records (exact table; network trusted
+    everywhere, table nowhere): a replay in branches (4 asked, 3 formed), each rebuilding its
+    own cells' records after its temperature update, gives what plain step
+    calls give, records included."""
+    from paper_2604_24627_gb300.mlp import SurrogateNet
+    prm = base_params(step_branches=4, rate_model=model, sr_table_nkt=24, sr_table_nne=12)
+    a, b = make_h(600, prm), make_h(600, prm)
+    if model == 2:
+        net = SurrogateNet()
+        _lib.axpic_surrogate_fit(net.h, 2048, 1, 400, 2048, 2e-3, 5)
+        err = np.zeros(2 * 4 * 4 * 2, dtype=np.float32)
+        for pl in (a, b):
+            _lib.axpic_set_surrogate(pl.ctx, net.h, err, 4, 4, 1.0)
+        net.close()
+    for s in range(35):
+        a.step(s, _lib.CH_ALL)
+    b.run_steps(0, 35, _lib.CH_ALL)
+    torch.cuda.synchronize()
+    assert_same(state(a), state(b), "records of model %d" % model)
+    ra = _lib.axpic_get_spectral_records(a.ctx, 0, 600)
+    rb = _lib.axpic_get_spectral_records(b.ctx, 0, 600)
+    assert np.array_equal(ra, rb)
+    assert b.launch_shape()[2] == 3  # 600 cells in ranges of whole 128-cell CTAs: 256, 256, 88
+    a.close()
+    b.close()
+
+
+def test_records_rebuilt_in_a_step_equal_a_rebuild_from_scratch():
+    """Cells whose trust changes as T evolves: the records the step rebuilds
+    (network first, then the table over the cells it left) equal the ones a
+    rebuild from scratch gives for the same temperatures."""
+    from paper_2604_24627_gb300.mlp import SurrogateNet
+    prm = base_params(rate_model=2, relax_r=1.0, sr_table_nkt=24, sr_table_nne=12)
+    T = np.linspace(1.0, 7.0, 300)
+    pl = make_h(300, prm, T=T, caps=(64, 4096, 4096))
+    net = SurrogateNet()
+    _lib.axpic_surrogate_fit(net.h, 2048, 1, 400, 2048, 2e-3, 5)
+    nT, nne = 8, 4
+    err = np.zeros((2, nne, nT, 2), dtype=np.float32)
+    err[:, :, 3:5, 0] = 1.0  # an untrusted band of temperatures between two trusted ones: cells cross its borders
+    _lib.axpic_set_surrogate(pl.ctx, net.h, err.ravel(), nT, nne, 1e-3)
+    net.close()
+    for s in range(4):
+        pl.step(s, _lib.CH_ALL)
+    torch.cuda.synchronize()
+    in_step = _lib.axpic_get_spectral_records(pl.ctx, 0, 300)
+    _lib.axpic_update_cells(pl.ctx)
+    fresh = _lib.axpic_get_spectral_records(pl.ctx, 0, 300)
+    assert np.array_equal(in_step, fresh)
+    pl.close()
+
+
 @pytest.mark.parametrize("chunk,tpb", [(2, 32), (4, 64), (8, 128), (8, 64)])
 def test_launch_shapes_give_identical_results(chunk, tpb):
     ref = make(29, base_params())
