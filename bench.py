@@ -401,6 +401,37 @@ def run_rate_models(args):
         lines[("closed_forms", "table", "surrogate")[model]] = entry
         pl.close()
     net.close()
+    # transport on: the closed-form model with the axions' free streaming
+    # after every step (axpic_run_steps_streamed), the workload's grid as a
+    # periodic box of cubic cells, c dt = 0.6 of the edge
+    dims = tuple(list(w.shape) + [1] * (3 - len(w.shape)))
+    if int(np.prod(dims)) == w.ncells:
+        h = w.volume_cm3 ** (1.0 / 3.0)
+        dt_s = 0.6 * h / 2.99792458e10
+        with torch.cuda.stream(stream):
+            pl = AxionPlasma(w.ncells, w.T_keV, w.n_ion, w.Z, w.A, w.volume_cm3, w.caps, dict(w.params, rate_model=0),
+                             device=dev, stream=stream)
+            pl.sample(w.n_el, w.n_ph, w.n_ax)
+        for s in range(args.warmup):
+            pl.step(s, w.mask)
+            pl.stream_axions(dims, h, dt_s, True)
+        pl.tally()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        pl.run_steps_streamed(args.warmup, args.steps, w.mask, dims, h, dt_s, True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        _, tot = pl.tally()
+        parts = tot["part_e"] + tot["part_g"] + tot["part_a"]
+        lines["closed_forms_with_transport"] = {
+            "particle_steps_per_s": parts / (ms * 1e-3), "ms_per_step": ms / args.steps,
+            "launch": "CUDA graphs of 32 steps replayed, each step's %d branch(es) joined before the streaming"
+                      % pl.launch_shape()[2],
+            "transport": {"grid": list(dims), "boundary": "periodic", "c_dt_over_h": 0.6}}
+        pl.close()
     line = {"metric": METRIC, "value": lines["surrogate"]["particle_steps_per_s"], "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": lines["surrogate"]["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

@@ -234,7 +234,19 @@ axpic_status axpic_update_cells(axpic_ctx *ctx);
 axpic_status axpic_stream_axions(axpic_ctx *ctx, int32_t nx, int32_t ny, int32_t nz, double h_cm, double dt_s,
                                  double mass_keV, int32_t boundary);
 
-/* Totals of every axpic_stream_axions call so far, to out (host, 4
+/* nsteps steps as axpic_run_steps runs them, each followed by the axions'
+ * streaming of axpic_stream_axions with these parameters (the transport
+ * between steps, Sec. II.B), replayed from CUDA graphs of 32 steps. Each
+ * step's cell branches are joined before the streaming, which crosses
+ * them. Graphs are kept per channel mask for the last streaming parameters.
+ * Asynchronous; results are identical to nsteps pairs of axpic_step and
+ * axpic_stream_axions. AXPIC_E_INVALID as for either call. */
+axpic_status axpic_run_steps_streamed(axpic_ctx *ctx, int64_t first_step, int32_t nsteps, int32_t channel_mask,
+                                      int32_t nx, int32_t ny, int32_t nz, double h_cm, double dt_stream_s,
+                                      double mass_keV, int32_t boundary);
+
+/* Totals of every streaming so far (axpic_stream_axions and the streaming of
+ * axpic_run_steps_streamed), to out (host, 4
  * doubles): axions that left an open box (number, weight, weight x energy
  * [keV], the total energy sqrt(p^2 + m_a^2)) and axions dropped at a full
  * slab (number). Zeros before the first

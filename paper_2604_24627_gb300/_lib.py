@@ -129,6 +129,9 @@ EXPORTS = {
     "axpic_stream_axions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32]),
     "axpic_stream_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "axpic_run_steps_streamed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_int32]),
     "axpic_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "axpic_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "axpic_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -419,6 +422,11 @@ def axpic_set_surrogate(ctx, net_handle, err_map, nT, nne, tol):
 def axpic_stream_axions(ctx, dims, h_cm, dt_s, boundary, mass_keV=0.0):
     nx, ny, nz = dims
     _check(ctx, lib().axpic_stream_axions(ctx, nx, ny, nz, h_cm, dt_s, mass_keV, boundary))
+
+
+def axpic_run_steps_streamed(ctx, first, nsteps, mask, dims, h_cm, dt_s, boundary, mass_keV=0.0):
+    nx, ny, nz = dims
+    _check(ctx, lib().axpic_run_steps_streamed(ctx, first, nsteps, mask, nx, ny, nz, h_cm, dt_s, mass_keV, boundary))
 
 
 def axpic_stream_stats(ctx):

@@ -85,6 +85,8 @@ struct axpic_ctx {
   cudaStream_t br_stream[kMaxBranches] = {};
   cudaEvent_t br_ev[kMaxBranches + 1] = {};
   std::map<int, cudaGraphExec_t> graphs;  // per (channel mask, steps in the graph)
+  std::map<int, cudaGraphExec_t> sgraphs;  // steps followed by axion streaming, for stream_sig
+  std::vector<int64_t> stream_sig;         // the streaming parameters sgraphs were captured for
   // spectral records of rate models 1 and 2
   float* sr = nullptr;      // [ncells * kSrLen]
   float* srtab = nullptr;   // [2][nne][nkt][kSrTabOut]
@@ -304,6 +306,8 @@ static void free_events(axpic_ctx* ctx) {
 static void free_graphs(axpic_ctx* ctx) {
   for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.second);
   ctx->graphs.clear();
+  for (auto& g : ctx->sgraphs) cudaGraphExecDestroy(g.second);
+  ctx->sgraphs.clear();
 }
 
 static void free_ctx(axpic_ctx* ctx) {
@@ -763,18 +767,32 @@ static cudaError_t capture_steps(axpic_ctx* ctx, StepArgs A, int nsteps, cudaStr
 }
 
 // The graph of nsteps steps for channel_mask, captured on first use.
+static axpic_status stream_setup(axpic_ctx* ctx, int32_t nx, int32_t ny, int32_t nz, double h_cm, double dt_s,
+                                 double mass_keV, int32_t boundary, StreamArgs* out);
+
 static axpic_status step_graph(axpic_ctx* ctx, int64_t first_step, int nsteps, int32_t channel_mask,
-                               cudaGraphExec_t* out) {
+                               cudaGraphExec_t* out, const StreamArgs* sa = nullptr) {
   const int key = channel_mask * 1024 + nsteps;
-  auto it = ctx->graphs.find(key);
-  if (it == ctx->graphs.end()) {
+  std::map<int, cudaGraphExec_t>& cache = sa ? ctx->sgraphs : ctx->graphs;
+  auto it = cache.find(key);
+  if (it == cache.end()) {
     StepArgs A = make_args(ctx, first_step, channel_mask);
     A.step_dev = ctx->step_dev;
     cudaStream_t gs = ctx->graph_stream;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal), "begin capture");
     const SrArgs sra = make_sr_args(ctx);
-    const cudaError_t le = capture_steps(ctx, A, nsteps, gs, ctx->prm.rate_model ? &sra : nullptr);
+    cudaError_t le = cudaSuccess;
+    if (!sa) {
+      le = capture_steps(ctx, A, nsteps, gs, ctx->prm.rate_model ? &sra : nullptr);
+    } else {
+      // each step (its branches joined: migration crosses them), then the
+      // axions' streaming over all cells
+      for (int k = 0; k < nsteps && le == cudaSuccess; ++k) {
+        le = capture_steps(ctx, A, 1, gs, ctx->prm.rate_model ? &sra : nullptr);
+        if (le == cudaSuccess) le = launch_stream(*sa, gs);
+      }
+    }
     const cudaError_t ce = cudaStreamEndCapture(gs, &g);
     if (le != cudaSuccess || ce != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -784,7 +802,7 @@ static axpic_status step_graph(axpic_ctx* ctx, int64_t first_step, int nsteps, i
     const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
     if (ie != cudaSuccess) return cuda_fail(ctx, ie, "axpic_run_steps: instantiate");
-    it = ctx->graphs.emplace(key, ex).first;
+    it = cache.emplace(key, ex).first;
   }
   *out = it->second;
   return AXPIC_OK;
@@ -809,6 +827,47 @@ axpic_status axpic_run_steps(axpic_ctx* ctx, int64_t first_step, int32_t nsteps,
   axpic_status st;
   if (nsteps >= kGraphSteps && (st = step_graph(ctx, first_step, kGraphSteps, channel_mask, &many))) return st;
   if (nsteps % kGraphSteps && (st = step_graph(ctx, first_step, 1, channel_mask, &one))) return st;
+  CK(launch_set_step(ctx->step_dev, (uint32_t)first_step, kMaxBranches, gs), "set step");
+  for (int32_t k = 0; k < nsteps / kGraphSteps; ++k) CK(cudaGraphLaunch(many, gs), "graph launch");
+  for (int32_t k = 0; k < nsteps % kGraphSteps; ++k) CK(cudaGraphLaunch(one, gs), "graph launch");
+  CK(cudaEventRecord(ctx->graph_ev[1], gs), "event record");
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->graph_ev[1], 0), "stream wait");
+  return AXPIC_OK;
+}
+
+axpic_status axpic_run_steps_streamed(axpic_ctx* ctx, int64_t first_step, int32_t nsteps, int32_t channel_mask,
+                                      int32_t nx, int32_t ny, int32_t nz, double h_cm, double dt_stream_s,
+                                      double mass_keV, int32_t boundary) {
+  if (!ctx) return AXPIC_E_INVALID;
+  if (nsteps < 0 || first_step < 0 || first_step + (int64_t)nsteps >= (int64_t)0xFFFFFFFF)
+    return fail(ctx, AXPIC_E_INVALID, "axpic_run_steps_streamed: step range outside [0, 2^32 - 1)");
+  if (channel_mask & ~AXPIC_CH_ALL)
+    return fail(ctx, AXPIC_E_INVALID, "axpic_run_steps_streamed: unknown channel bits");
+  StreamArgs sa;
+  axpic_status st = stream_setup(ctx, nx, ny, nz, h_cm, dt_stream_s, mass_keV, boundary, &sa);
+  if (st != AXPIC_OK) return st;
+  if (nsteps == 0 || ctx->desc.ncells == 0) return AXPIC_OK;
+  // graphs captured for other streaming parameters are dropped
+  int32_t kbits, mbits;
+  std::memcpy(&kbits, &sa.kappa, 4);
+  std::memcpy(&mbits, &sa.mu, 4);
+  const std::vector<int64_t> sig = {nx, ny, nz, kbits, mbits, sa.periodic};
+  if (sig != ctx->stream_sig) {
+    for (auto& g : ctx->sgraphs) cudaGraphExecDestroy(g.second);
+    ctx->sgraphs.clear();
+    ctx->stream_sig = sig;
+  }
+  if (!ctx->graph_stream) {
+    CK(cudaStreamCreateWithFlags(&ctx->graph_stream, cudaStreamNonBlocking), "stream create");
+    CK(cudaEventCreateWithFlags(&ctx->graph_ev[0], cudaEventDisableTiming), "event create");
+    CK(cudaEventCreateWithFlags(&ctx->graph_ev[1], cudaEventDisableTiming), "event create");
+  }
+  cudaStream_t gs = ctx->graph_stream;
+  CK(cudaEventRecord(ctx->graph_ev[0], ctx->stream), "event record");
+  CK(cudaStreamWaitEvent(gs, ctx->graph_ev[0], 0), "stream wait");
+  cudaGraphExec_t many = nullptr, one = nullptr;
+  if (nsteps >= kGraphSteps && (st = step_graph(ctx, first_step, kGraphSteps, channel_mask, &many, &sa))) return st;
+  if (nsteps % kGraphSteps && (st = step_graph(ctx, first_step, 1, channel_mask, &one, &sa))) return st;
   CK(launch_set_step(ctx->step_dev, (uint32_t)first_step, kMaxBranches, gs), "set step");
   for (int32_t k = 0; k < nsteps / kGraphSteps; ++k) CK(cudaGraphLaunch(many, gs), "graph launch");
   for (int32_t k = 0; k < nsteps % kGraphSteps; ++k) CK(cudaGraphLaunch(one, gs), "graph launch");
@@ -979,9 +1038,10 @@ axpic_status axpic_set_surrogate(axpic_ctx* ctx, axpic_mlp* m, const float* err_
   return read_err(ctx);
 }
 
-axpic_status axpic_stream_axions(axpic_ctx* ctx, int32_t nx, int32_t ny, int32_t nz, double h_cm, double dt_s,
-                                 double mass_keV, int32_t boundary) {
-  if (!ctx) return AXPIC_E_INVALID;
+// Validates the streaming parameters, makes the scratch on first use and fills
+// the kernels' arguments (nothing is launched).
+static axpic_status stream_setup(axpic_ctx* ctx, int32_t nx, int32_t ny, int32_t nz, double h_cm, double dt_s,
+                                 double mass_keV, int32_t boundary, StreamArgs* out) {
   const axpic_plasma_desc& d = ctx->desc;
   if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz != d.ncells)
     return fail(ctx, AXPIC_E_INVALID, "axpic_stream_axions: nx ny nz must give the context's cells");
@@ -1000,6 +1060,7 @@ axpic_status axpic_stream_axions(axpic_ctx* ctx, int32_t nx, int32_t ny, int32_t
     CK(cudaMemsetAsync(ctx->st_stats, 0, sizeof(double) * 4, ctx->stream), "memset");
   }
   StreamArgs a;
+  std::memset(&a, 0, sizeof(a));
   a.s = to_ptrs(d.axions);
   a.ncells = d.ncells;
   a.nx = nx;
@@ -1014,6 +1075,16 @@ axpic_status axpic_stream_axions(axpic_ctx* ctx, int32_t nx, int32_t ny, int32_t
   a.buf = ctx->st_buf;
   a.stats = ctx->st_stats;
   a.err = ctx->err;
+  *out = a;
+  return AXPIC_OK;
+}
+
+axpic_status axpic_stream_axions(axpic_ctx* ctx, int32_t nx, int32_t ny, int32_t nz, double h_cm, double dt_s,
+                                 double mass_keV, int32_t boundary) {
+  if (!ctx) return AXPIC_E_INVALID;
+  StreamArgs a;
+  const axpic_status st = stream_setup(ctx, nx, ny, nz, h_cm, dt_s, mass_keV, boundary, &a);
+  if (st != AXPIC_OK) return st;
   CK(launch_stream(a, ctx->stream), "stream kernels");
   return AXPIC_OK;
 }

@@ -162,6 +162,12 @@ class AxionPlasma:
         asynchronous."""
         _lib.axpic_stream_axions(self.ctx, dims, h_cm, dt_s, 0 if periodic else 1, mass_keV)
 
+    def run_steps_streamed(self, first, nsteps, mask, dims, h_cm, dt_s, periodic=True, mass_keV=0.0):
+        """nsteps steps, each followed by the axions' streaming, replayed from
+        CUDA graphs (axpic_run_steps_streamed); asynchronous."""
+        _lib.axpic_run_steps_streamed(self.ctx, first, nsteps, mask, dims, h_cm, dt_s, 0 if periodic else 1,
+                                      mass_keV)
+
     def stream_stats(self):
         """[escaped number, escaped weight, escaped weight x energy (keV),
         dropped number] over every streaming call so far."""

@@ -178,3 +178,45 @@ def test_relaxation_size_sampled_cells_and_invariants():
         got = Species(*[d[f].astype(np.float32) for f in FIELDS])
         assert_cells_equal([got], [want[4]])
     pl.close()
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_streamed_replay_equals_step_and_stream_calls(periodic):
+    """35 steps of the full method, each followed by the axions' streaming on
+    a 24 x 25 grid, replayed from graphs (8 branches asked for the steps):
+    the same particles, slots and counters as plain step and stream calls."""
+    prm = dict(g_agg_GeV_inv=1e-10, g_ae=1e-12, dt_phys_s=2e12, w_a=3.0e9, seed=0x1234_0000_0042, T_mode=2,
+               relax_r=0.1, diag_enable=0, tally_enable=0, step_branches=8)
+    dims, h = (24, 25, 1), 1e-4
+    dt = 0.6 * h / C
+
+    def make_pl():
+        n = 600
+        pl = AxionPlasma(n, np.linspace(1.3, 5.0, n), np.full((n, 1), 6e25), [1.0], [1.00794], 1e-12,
+                         (64, 1024, 2048), prm)
+        pl.sample(61, 37, 13)
+        torch.cuda.synchronize()
+        return pl
+
+    a, b = make_pl(), make_pl()
+    for s in range(35):
+        a.step(s, _lib.CH_ALL)
+        a.stream_axions(dims, h, dt, periodic)
+    b.run_steps_streamed(0, 35, _lib.CH_ALL, dims, h, dt, periodic)
+    torch.cuda.synchronize()
+    for name in ("electrons", "photons", "axions"):
+        sa_, sb_ = a.slabs[name], b.slabs[name]
+        assert torch.equal(sa_.count, sb_.count), name
+        cap = sa_.capacity
+        idx = (torch.arange(cap, device=sa_.count.device)[None, :] < sa_.count[:, None].long()).reshape(-1)
+        for f in FIELDS:
+            assert torch.equal(sa_.data[f][:idx.numel()][idx], sb_.data[f][:idx.numel()][idx]), (name, f)
+    assert torch.equal(a.T, b.T)
+    sa, sb = a.stream_stats(), b.stream_stats()
+    # counts exactly; the escaped weight and energy are FP64 atomic sums,
+    # whose order varies
+    assert sa[0] == sb[0] and sa[3] == sb[3]
+    assert np.allclose(sa[1:3], sb[1:3], rtol=1e-12, atol=0)
+    assert b.launch_shape()[2] > 1
+    a.close()
+    b.close()
