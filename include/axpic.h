@@ -234,6 +234,21 @@ axpic_status axpic_update_cells(axpic_ctx *ctx);
 axpic_status axpic_stream_axions(axpic_ctx *ctx, int32_t nx, int32_t ny, int32_t nz, double h_cm, double dt_s,
                                  double mass_keV, int32_t boundary);
 
+/* Checkpoint and resume. The state a context owns between steps, besides
+ * the caller's slabs and T_keV: the cells' rate records and cached electron
+ * moments, the FP64 exchange and residual-carry buffers, the per-cell
+ * diagnostics, the tallies and counters, the decision masks, the latched
+ * error flag and, for rate models 1 and 2, the spectral records (not the
+ * surrogate's network or trust map: axpic_set_surrogate sets those). Philox
+ * is stateless, so a context of the same geometry and parameters whose
+ * caller arrays and loaded state are a save's continues bit for bit from
+ * the next step index. axpic_state_bytes gives the size; save and load copy
+ * it to and from host memory (bytes must equal it, else AXPIC_E_INVALID).
+ * Save and load synchronise. */
+axpic_status axpic_state_bytes(axpic_ctx *ctx, uint64_t *bytes);
+axpic_status axpic_save_state(axpic_ctx *ctx, void *host_out, uint64_t bytes);
+axpic_status axpic_load_state(axpic_ctx *ctx, const void *host_in, uint64_t bytes);
+
 /* nsteps steps as axpic_run_steps runs them, each followed by the axions'
  * streaming of axpic_stream_axions with these parameters (the transport
  * between steps, Sec. II.B), replayed from CUDA graphs of 32 steps. Each

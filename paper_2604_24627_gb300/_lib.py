@@ -129,6 +129,9 @@ EXPORTS = {
     "axpic_stream_axions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32]),
     "axpic_stream_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "axpic_state_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "axpic_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
+    "axpic_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
     "axpic_run_steps_streamed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                                 ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                                 ctypes.c_double, ctypes.c_double, ctypes.c_int32]),
@@ -427,6 +430,21 @@ def axpic_stream_axions(ctx, dims, h_cm, dt_s, boundary, mass_keV=0.0):
 def axpic_run_steps_streamed(ctx, first, nsteps, mask, dims, h_cm, dt_s, boundary, mass_keV=0.0):
     nx, ny, nz = dims
     _check(ctx, lib().axpic_run_steps_streamed(ctx, first, nsteps, mask, nx, ny, nz, h_cm, dt_s, mass_keV, boundary))
+
+
+def axpic_save_state(ctx):
+    import numpy as np
+    n = ctypes.c_uint64()
+    _check(ctx, lib().axpic_state_bytes(ctx, ctypes.byref(n)))
+    out = np.empty(max(n.value, 1), dtype=np.uint8)
+    _check(ctx, lib().axpic_save_state(ctx, out.ctypes.data_as(ctypes.c_void_p), n.value))
+    return out[:n.value]
+
+
+def axpic_load_state(ctx, buf):
+    import numpy as np
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(ctx, lib().axpic_load_state(ctx, buf.ctypes.data_as(ctypes.c_void_p), buf.size))
 
 
 def axpic_stream_stats(ctx):

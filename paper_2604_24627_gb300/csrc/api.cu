@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "misc.h"
 #include "sr.h"
@@ -18,6 +20,14 @@
 using namespace axpic;
 
 namespace {
+
+// An NVTX range over each public call, named for it (a no-op unless a
+// profiler is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+#define AXPIC_RANGE(name) NvtxRange axpic_range_(name)
 
 // CODATA 2018 constants (binary64), folded into the binary32 record.
 constexpr double kHbarcKeVcm = 1.973269804e-8;
@@ -363,6 +373,7 @@ void axpic_default_params(axpic_params* p) {
 
 axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, const axpic_params* params,
                                void* stream) {
+  AXPIC_RANGE("axpic_init_plasma");
   if (!out || !desc || !params) return AXPIC_E_INVALID;
   *out = nullptr;
   const axpic_plasma_desc& d = *desc;
@@ -511,6 +522,7 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
 }
 
 axpic_status axpic_sample_plasma(axpic_ctx* ctx, int32_t n_el, int32_t n_ph, int32_t n_ax) {
+  AXPIC_RANGE("axpic_sample_plasma");
   if (!ctx) return AXPIC_E_INVALID;
   const axpic_plasma_desc& d = ctx->desc;
   if (n_el < 0 || n_ph < 0 || n_ax < 0 || n_el > d.electrons.capacity || n_ph > d.photons.capacity ||
@@ -541,6 +553,7 @@ axpic_status axpic_sample_plasma(axpic_ctx* ctx, int32_t n_el, int32_t n_ph, int
 }
 
 axpic_status axpic_update_cells(axpic_ctx* ctx) {
+  AXPIC_RANGE("axpic_update_cells");
   if (!ctx) return AXPIC_E_INVALID;
   const axpic_plasma_desc& d = ctx->desc;
   CK(launch_records(d.ncells, d.nspecies, ctx->cc, d.T_keV, d.n_ion, ctx->rec, ctx->err, ctx->stream), "records");
@@ -565,18 +578,22 @@ static axpic_status run_phases(axpic_ctx* ctx, int phases, int64_t step, int32_t
 }
 
 axpic_status axpic_absorb(axpic_ctx* ctx, int64_t step, int32_t channel_mask) {
+  AXPIC_RANGE("axpic_absorb");
   return run_phases(ctx, PH_ABSORB, step, channel_mask, "axpic_absorb");
 }
 
 axpic_status axpic_emit(axpic_ctx* ctx, int64_t step, int32_t channel_mask) {
+  AXPIC_RANGE("axpic_emit");
   return run_phases(ctx, PH_EMIT, step, channel_mask, "axpic_emit");
 }
 
 axpic_status axpic_feedback(axpic_ctx* ctx, int64_t step) {
+  AXPIC_RANGE("axpic_feedback");
   return run_phases(ctx, PH_FEEDBACK, step, 0, "axpic_feedback");
 }
 
 axpic_status axpic_step(axpic_ctx* ctx, int64_t step, int32_t channel_mask) {
+  AXPIC_RANGE("axpic_step");
   return run_phases(ctx, PH_ALL, step, channel_mask, "axpic_step");
 }
 
@@ -590,6 +607,7 @@ static axpic_status read_err(axpic_ctx* ctx) {
 }
 
 axpic_status axpic_tally_spectrum(axpic_ctx* ctx, int32_t nbins, double* H_out, double* totals_out) {
+  AXPIC_RANGE("axpic_tally_spectrum");
   if (!ctx) return AXPIC_E_INVALID;
   if (nbins != ctx->prm.tally_nbins) return fail(ctx, AXPIC_E_INVALID, "axpic_tally_spectrum: nbins mismatch");
   const axpic_plasma_desc& d = ctx->desc;
@@ -809,6 +827,7 @@ static axpic_status step_graph(axpic_ctx* ctx, int64_t first_step, int nsteps, i
 }
 
 axpic_status axpic_run_steps(axpic_ctx* ctx, int64_t first_step, int32_t nsteps, int32_t channel_mask) {
+  AXPIC_RANGE("axpic_run_steps");
   if (!ctx) return AXPIC_E_INVALID;
   if (nsteps < 0 || first_step < 0 || first_step + (int64_t)nsteps >= (int64_t)0xFFFFFFFF)
     return fail(ctx, AXPIC_E_INVALID, "axpic_run_steps: step range outside [0, 2^32 - 1)");
@@ -838,6 +857,7 @@ axpic_status axpic_run_steps(axpic_ctx* ctx, int64_t first_step, int32_t nsteps,
 axpic_status axpic_run_steps_streamed(axpic_ctx* ctx, int64_t first_step, int32_t nsteps, int32_t channel_mask,
                                       int32_t nx, int32_t ny, int32_t nz, double h_cm, double dt_stream_s,
                                       double mass_keV, int32_t boundary) {
+  AXPIC_RANGE("axpic_run_steps_streamed");
   if (!ctx) return AXPIC_E_INVALID;
   if (nsteps < 0 || first_step < 0 || first_step + (int64_t)nsteps >= (int64_t)0xFFFFFFFF)
     return fail(ctx, AXPIC_E_INVALID, "axpic_run_steps_streamed: step range outside [0, 2^32 - 1)");
@@ -878,18 +898,20 @@ axpic_status axpic_run_steps_streamed(axpic_ctx* ctx, int64_t first_step, int32_
 
 // The context's device state, as (pointer, bytes) pairs: what a step reads or
 // writes. The autotuner saves and restores exactly this.
-static std::vector<std::pair<void*, size_t>> state_buffers(axpic_ctx* ctx) {
+static std::vector<std::pair<void*, size_t>> state_buffers(axpic_ctx* ctx, bool with_caller = true) {
   const axpic_plasma_desc& d = ctx->desc;
   const size_t n = (size_t)d.ncells;
   std::vector<std::pair<void*, size_t>> b;
-  for (const axpic_species* s : {&d.electrons, &d.photons, &d.axions}) {
-    const size_t slots = n * (size_t)s->capacity * sizeof(float);
-    for (float* f : {s->w, s->px, s->py, s->pz, s->x, s->y, s->z}) b.emplace_back(f, slots);
-    b.emplace_back(s->count, n * sizeof(int32_t));
+  if (with_caller) {  // the caller's slabs and T
+    for (const axpic_species* s : {&d.electrons, &d.photons, &d.axions}) {
+      const size_t slots = n * (size_t)s->capacity * sizeof(float);
+      for (float* f : {s->w, s->px, s->py, s->pz, s->x, s->y, s->z}) b.emplace_back(f, slots);
+      b.emplace_back(s->count, n * sizeof(int32_t));
+    }
+    b.emplace_back(d.T_keV, n * sizeof(double));
   }
   const size_t bit_words = n * ((d.axions.capacity + 31) / 32 + (d.photons.capacity + 31) / 32 +
                                 (d.electrons.capacity + 31) / 32);
-  b.emplace_back(d.T_keV, n * sizeof(double));
   b.emplace_back(ctx->rec, n * kRecLen * sizeof(float));
   b.emplace_back(ctx->mom, n * kMomLen * sizeof(float));
   b.emplace_back(ctx->xbuf, n * 4 * sizeof(double));
@@ -939,6 +961,7 @@ axpic_status axpic_launch_shape(const axpic_ctx* ctx, int32_t* decide_chunk, int
 
 axpic_status axpic_autotune(axpic_ctx* ctx, int64_t step, int32_t trial_steps, int32_t channel_mask,
                             double* best_ms_out, int32_t* chunk_out, int32_t* warps_out) {
+  AXPIC_RANGE("axpic_autotune");
   if (!ctx) return AXPIC_E_INVALID;
   if (trial_steps < 1 || step < 0 || step + (int64_t)trial_steps >= (int64_t)0xFFFFFFFF)
     return fail(ctx, AXPIC_E_INVALID, "axpic_autotune: trial_steps < 1 or step range outside [0, 2^32 - 1)");
@@ -1003,6 +1026,7 @@ axpic_status axpic_autotune(axpic_ctx* ctx, int64_t step, int32_t trial_steps, i
 
 axpic_status axpic_set_surrogate(axpic_ctx* ctx, axpic_mlp* m, const float* err_map, int32_t nT, int32_t nne,
                                  float tol) {
+  AXPIC_RANGE("axpic_set_surrogate");
   if (!ctx || !m || !err_map) return AXPIC_E_INVALID;
   if (ctx->prm.rate_model != 2) return fail(ctx, AXPIC_E_INVALID, "axpic_set_surrogate: rate_model is not 2");
   if (nT < 2 || nne < 2 || nT > 4096 || nne > 4096) return fail(ctx, AXPIC_E_INVALID, "axpic_set_surrogate: grid");
@@ -1081,11 +1105,48 @@ static axpic_status stream_setup(axpic_ctx* ctx, int32_t nx, int32_t ny, int32_t
 
 axpic_status axpic_stream_axions(axpic_ctx* ctx, int32_t nx, int32_t ny, int32_t nz, double h_cm, double dt_s,
                                  double mass_keV, int32_t boundary) {
+  AXPIC_RANGE("axpic_stream_axions");
   if (!ctx) return AXPIC_E_INVALID;
   StreamArgs a;
   const axpic_status st = stream_setup(ctx, nx, ny, nz, h_cm, dt_s, mass_keV, boundary, &a);
   if (st != AXPIC_OK) return st;
   CK(launch_stream(a, ctx->stream), "stream kernels");
+  return AXPIC_OK;
+}
+
+axpic_status axpic_state_bytes(axpic_ctx* ctx, uint64_t* bytes) {
+  if (!ctx || !bytes) return AXPIC_E_INVALID;
+  uint64_t t = 0;
+  for (auto& b : state_buffers(ctx, false)) t += b.second;
+  *bytes = t;
+  return AXPIC_OK;
+}
+
+axpic_status axpic_save_state(axpic_ctx* ctx, void* host_out, uint64_t bytes) {
+  AXPIC_RANGE("axpic_save_state");
+  uint64_t need = 0;
+  if (!ctx || !host_out || axpic_state_bytes(ctx, &need) != AXPIC_OK || bytes != need)
+    return ctx ? fail(ctx, AXPIC_E_INVALID, "axpic_save_state: buffer size") : AXPIC_E_INVALID;
+  unsigned char* p = static_cast<unsigned char*>(host_out);
+  for (auto& b : state_buffers(ctx, false)) {
+    CK(cudaMemcpyAsync(p, b.first, b.second, cudaMemcpyDeviceToHost, ctx->stream), "copy");
+    p += b.second;
+  }
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  return AXPIC_OK;
+}
+
+axpic_status axpic_load_state(axpic_ctx* ctx, const void* host_in, uint64_t bytes) {
+  AXPIC_RANGE("axpic_load_state");
+  uint64_t need = 0;
+  if (!ctx || !host_in || axpic_state_bytes(ctx, &need) != AXPIC_OK || bytes != need)
+    return ctx ? fail(ctx, AXPIC_E_INVALID, "axpic_load_state: buffer size") : AXPIC_E_INVALID;
+  const unsigned char* p = static_cast<const unsigned char*>(host_in);
+  for (auto& b : state_buffers(ctx, false)) {
+    CK(cudaMemcpyAsync(b.first, p, b.second, cudaMemcpyHostToDevice, ctx->stream), "copy");
+    p += b.second;
+  }
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
   return AXPIC_OK;
 }
 
@@ -1158,6 +1219,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 axpic_status axpic_step_noalloc(const axpic_plasma_desc* desc, const axpic_params* params, int64_t step,
                                 int32_t channel_mask, double* carry, void* stream) {
+  AXPIC_RANGE("axpic_step_noalloc");
   if (!desc || !params || !carry) return AXPIC_E_INVALID;
   const axpic_plasma_desc& d = *desc;
   const axpic_params& p = *params;

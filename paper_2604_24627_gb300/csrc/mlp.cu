@@ -14,6 +14,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mlp.h"
 #include "tc.cuh"
 #include "surrogate.h"
@@ -537,6 +539,10 @@ static void glorot(uint64_t seed, std::vector<float>& P) {
 
 axpic_status axpic_surrogate_fit(axpic_mlp* h, int32_t ncells, int32_t x_per_cell, int32_t steps, int32_t batch,
                                  float lr, uint64_t seed, double brems_shape, double* loss_out) {
+  nvtxRangePushA("axpic_surrogate_fit");
+  struct Pop {
+    ~Pop() { nvtxRangePop(); }
+  } pop_range_;
   if (!h || ncells < 1 || x_per_cell < 1 || steps < 1 || batch < 1 || !(lr > 0.f) || !(brems_shape > 0))
     return AXPIC_E_INVALID;
   std::vector<float> X;
@@ -645,6 +651,10 @@ axpic_status axpic_surrogate_fit(axpic_mlp* h, int32_t ncells, int32_t x_per_cel
 }
 
 axpic_status axpic_surrogate_validate(axpic_mlp* h, int32_t nT, int32_t nne, double brems_shape, float* err_out) {
+  nvtxRangePushA("axpic_surrogate_validate");
+  struct Pop {
+    ~Pop() { nvtxRangePop(); }
+  } pop_range_;
   if (!h || nT < 2 || nne < 2 || !err_out || !(brems_shape > 0)) return AXPIC_E_INVALID;
   const int nodes = nT * nne * 2, nx = 32;
   std::vector<float> X((size_t)nodes * nx * 4);

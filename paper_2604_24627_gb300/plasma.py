@@ -168,6 +168,15 @@ class AxionPlasma:
         _lib.axpic_run_steps_streamed(self.ctx, first, nsteps, mask, dims, h_cm, dt_s, 0 if periodic else 1,
                                       mass_keV)
 
+    def save_state(self):
+        """The library-owned state (axpic_save_state) as a uint8 array; the
+        slabs and T are the caller's (this object's tensors)."""
+        return _lib.axpic_save_state(self.ctx)
+
+    def load_state(self, buf):
+        """Loads a save_state array into this context (axpic_load_state)."""
+        _lib.axpic_load_state(self.ctx, buf)
+
     def stream_stats(self):
         """[escaped number, escaped weight, escaped weight x energy (keV),
         dropped number] over every streaming call so far."""

@@ -159,6 +159,42 @@ def test_records_rebuilt_in_a_step_equal_a_rebuild_from_scratch():
     pl.close()
 
 
+def test_checkpoint_and_resume_continue_bit_for_bit():
+    """10 steps in one context equal 5 steps, a save (the caller's slabs and
+    T, the library's state), a load into a new context and 5 more steps
+    (evolved T, residual carry, cached moments, counters)."""
+    prm = base_params()
+    a, b = make(48, prm), make(48, prm)
+    for s in range(10):
+        a.step(s, _lib.CH_ALL)
+    for s in range(5):
+        b.step(s, _lib.CH_ALL)
+    torch.cuda.synchronize()
+    slabs = {name: ({f: t.clone() for f, t in slab.data.items()}, slab.count.clone()) for name, slab in b.slabs.items()}
+    T = b.T.clone()
+    saved = b.save_state()
+    assert saved.size > 0
+    b.close()
+    c = make(48, prm, T=np.full(48, 2.0))  # another start: everything is overwritten
+    for name, (data, count) in slabs.items():
+        for f, t in data.items():
+            c.slabs[name].data[f].copy_(t)
+        c.slabs[name].count.copy_(count)
+    c.T.copy_(T)
+    c.load_state(saved)
+    with pytest.raises(_lib.AxpicError):
+        c.load_state(saved[:-8])
+    for s in range(5, 10):
+        c.step(s, _lib.CH_ALL)
+    torch.cuda.synchronize()
+    assert_same(state(a), state(c), "resumed")
+    ta, tc = a.tally()[1], c.tally()[1]
+    for k in ta:  # counts exactly, FP64 atomic sums (order-dependent) to 1e-12
+        assert abs(ta[k] - tc[k]) <= 1e-12 * max(1.0, abs(ta[k])), (k, ta[k], tc[k])
+    a.close()
+    c.close()
+
+
 @pytest.mark.parametrize("chunk,tpb", [(2, 32), (4, 64), (8, 128), (8, 64)])
 def test_launch_shapes_give_identical_results(chunk, tpb):
     ref = make(29, base_params())
