@@ -306,6 +306,21 @@ def test_empty_and_full_cells():
     pl.ctx = None
 
 
+def test_non_finite_temperature_is_reported():
+    """Host-side fault injection: a NaN temperature handed in by the caller
+    is caught when the cell records are rebuilt (no step is run) and the next
+    synchronising call returns AXPIC_E_NUMERIC; destroying the context
+    reports it again."""
+    pl = make(4, 3.0, base_params())
+    pl.T[2] = float("nan")
+    pl.update_cells()
+    with pytest.raises(_lib.AxpicError) as e:
+        pl.sync()
+    assert e.value.status == _lib.AXPIC_E_NUMERIC
+    with pytest.raises(_lib.AxpicError):
+        pl.close()
+
+
 def test_invalid_arguments_rejected():
     prm = base_params()
     with pytest.raises(_lib.AxpicError):
