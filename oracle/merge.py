@@ -21,9 +21,13 @@ Readings (the paper is silent on each):
   thresholds at or below |p|^2 = (px px + py py) + pz pz in binary32 (so the
   group is decided by comparisons alone). A group of three or more axions is
   merged.
-* Sums in FP64 in slot order, each operation rounded: w_i p_i and
-  |p_i| = sqrt((px px + py py) + pz pz) of the binary32 values. The
-  position is the weighted mean sum w_i x_i / W.
+* Arithmetic in binary32, each operation rounded: the sums over a group
+  run in slot order with Kahan compensation (y = v - c; t = s + y;
+  c = (t - s) - y; s = t), of w_i, w_i p_i, w_i |p_i| with
+  |p_i| = sqrt((px px + py py) + pz pz), and w_i x_i; the position is the
+  weighted mean sum w_i x_i / W. The merged axions are binary32 anyway, and
+  the compensation keeps the sums' error near one rounding whatever the
+  group's size.
 * Directions: e_P = P / |P| (e_z when P = 0); the perpendicular e_perp is
   e_P x e_a, normalised, with e_a the axis of e_P's smallest |component|
   (the lowest index on ties); p_a = (E/W)(cos theta e_P + sin theta e_perp)
@@ -32,8 +36,6 @@ Readings (the paper is silent on each):
 * The two new axions take the group's first two slots (p_a the first); the
   group's other slots are freed and closed by the tail fill (step.tail_fill).
 """
-import math
-
 import numpy as np
 
 from .step import Species, tail_fill
@@ -51,46 +53,57 @@ def group_of(px, py, pz, edges_p2):
     return e * 8 + octant
 
 
+def _kahan(values):
+    """Compensated binary32 sum in the order given."""
+    f = np.float32
+    s = f(0.0)
+    c = f(0.0)
+    for v in values:
+        y = f(v) - c
+        t = s + y
+        c = (t - s) - y
+        s = t
+    return s
+
+
 def merge_group(w, px, py, pz, x, y, z):
-    """The two axions that replace one group (FP64 with each step rounded as
-    written, results in binary32): ((w, px, py, pz, x, y, z) of a, of b)."""
-    W = Px = Py = Pz = E = X = Y = Zs = 0.0
-    for i in range(len(w)):
-        wi = float(w[i])
-        a, b, c = float(px[i]), float(py[i]), float(pz[i])
-        W += wi
-        Px += wi * a
-        Py += wi * b
-        Pz += wi * c
-        E += wi * math.sqrt((a * a + b * b) + c * c)
-        X += wi * float(x[i])
-        Y += wi * float(y[i])
-        Zs += wi * float(z[i])
+    """The two axions that replace one group (binary32, each step rounded as
+    written): ((w, px, py, pz, x, y, z) of a, of b)."""
+    f = np.float32
+    w, px, py, pz, x, y, z = (np.asarray(v, dtype=f) for v in (w, px, py, pz, x, y, z))
+    pn = [np.sqrt((px[i] * px[i] + py[i] * py[i]) + pz[i] * pz[i]) for i in range(len(w))]
+    W = _kahan(w)
+    Px = _kahan([w[i] * px[i] for i in range(len(w))])
+    Py = _kahan([w[i] * py[i] for i in range(len(w))])
+    Pz = _kahan([w[i] * pz[i] for i in range(len(w))])
+    E = _kahan([w[i] * pn[i] for i in range(len(w))])
+    X = _kahan([w[i] * x[i] for i in range(len(w))])
+    Y = _kahan([w[i] * y[i] for i in range(len(w))])
+    Zs = _kahan([w[i] * z[i] for i in range(len(w))])
     pm = E / W
-    Pn = math.sqrt((Px * Px + Py * Py) + Pz * Pz)
-    if Pn > 0.0:
+    Pn = np.sqrt((Px * Px + Py * Py) + Pz * Pz)
+    if Pn > f(0.0):
         e = (Px / Pn, Py / Pn, Pz / Pn)
-        ct = min(Pn / E, 1.0)
+        ct = min(Pn / E, f(1.0))
     else:
-        e = (0.0, 0.0, 1.0)
-        ct = 0.0
-    st = math.sqrt(1.0 - ct * ct)
+        e = (f(0.0), f(0.0), f(1.0))
+        ct = f(0.0)
+    st = np.sqrt(f(1.0) - ct * ct)
     ae = [abs(v) for v in e]
     k = 0
     for j in (1, 2):
         if ae[j] < ae[k]:
             k = j
-    ax = [0.0, 0.0, 0.0]
-    ax[k] = 1.0
+    ax = [f(0.0), f(0.0), f(0.0)]
+    ax[k] = f(1.0)
     u = (e[1] * ax[2] - e[2] * ax[1], e[2] * ax[0] - e[0] * ax[2], e[0] * ax[1] - e[1] * ax[0])
-    un = math.sqrt((u[0] * u[0] + u[1] * u[1]) + u[2] * u[2])
+    un = np.sqrt((u[0] * u[0] + u[1] * u[1]) + u[2] * u[2])
     q = (u[0] / un, u[1] / un, u[2] / un)
-    f = np.float32
-    wh = f(W / 2.0)
-    pos = (f(X / W), f(Y / W), f(Zs / W))
-    pa = tuple(f(pm * (ct * e[j] + st * q[j])) for j in range(3))
-    pb = tuple(f(pm * (ct * e[j] - st * q[j])) for j in range(3))
-    return (wh,) + pa + pos, (wh,) + pb + pos
+    wh = W * f(0.5)
+    pos = (X / W, Y / W, Zs / W)
+    pa = tuple(pm * (ct * e[j] + st * q[j]) for j in range(3))
+    pb = tuple(pm * (ct * e[j] - st * q[j]) for j in range(3))
+    return tuple(f(v) for v in (wh,) + pa + pos), tuple(f(v) for v in (wh,) + pb + pos)
 
 
 def merge_cell(s: Species, n_target, edges_p2):
