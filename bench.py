@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--stream-calls", type=int, default=20,
                     help="timed axion streaming calls after the other legs (0: none)")
+    ap.add_argument("--merge-n-target", type=int, default=64,
+                    help="timed axion merging call after the other legs, toward this many a cell (0: none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=256, help="cells per side (256: the full workload)")
@@ -578,8 +580,35 @@ def main():
                           "axion_moves_per_s": n_ax / (ms * 1e-3), "algorithmic_bytes_per_axion": 56,
                           "GBps": gbps}
 
+    # axion merging (axpic_merge_axions) on the same plasma after the other
+    # legs: every cell above 64 axions, 16 |p| thresholds from 0.5 to 50 keV.
+    # Algorithmic bytes: the seven fields of every axion in a merged cell
+    # read and written once (56 B).
+    merge_leg = None
+    if args.merge_n_target > 0:
+        edges = (np.geomspace(0.5, 50.0, 16) / 510.99895).astype(np.float32) ** 2
+        pl.merge_axions(1 << 30, edges)  # the first call makes the scratch; nothing is merged
+        torch.cuda.synchronize(dev)
+        cnt = pl.slabs["axions"].count[:w.ncells]
+        n_before = int(cnt.sum())
+        n_in_merged = int(cnt[cnt > args.merge_n_target].sum())
+        m0 = torch.cuda.Event(enable_timing=True)
+        m1 = torch.cuda.Event(enable_timing=True)
+        m0.record(stream)
+        pl.merge_axions(args.merge_n_target, edges)
+        m1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = m0.elapsed_time(m1)
+        n_after = int(pl.slabs["axions"].count[:w.ncells].sum())
+        merge_leg = {"call": "axpic_merge_axions", "n_target": args.merge_n_target, "p_bins": 17, "octants": 8,
+                     "axions_before": n_before, "axions_after": n_after, "axions_in_merged_cells": n_in_merged,
+                     "ms_per_call": ms, "axions_per_s": n_in_merged / (ms * 1e-3),
+                     "algorithmic_bytes_per_axion": 56, "GBps": 56.0 * n_in_merged / (ms * 1e-3) / 1e9}
+
     if rank == 0:
         peak, peak_kind = measured_peaks()
+        if merge_leg:
+            merge_leg["frac"] = merge_leg["GBps"] / peak
         if stream_leg:
             stream_leg["frac"] = stream_leg["GBps"] / peak
             stream_leg["peak_kind"] = peak_kind
@@ -635,6 +664,8 @@ def main():
             line["e2e"] = e2e
         if stream_leg:
             line["axion_streaming"] = stream_leg
+        if merge_leg:
+            line["axion_merging"] = merge_leg
         if world == 1 and not args.no_cpu_baseline:
             cells = [pl.cell(c) for c in range(64)]
             from oracle import step as ostep

@@ -234,6 +234,26 @@ axpic_status axpic_update_cells(axpic_ctx *ctx);
 axpic_status axpic_stream_axions(axpic_ctx *ctx, int32_t nx, int32_t ny, int32_t nz, double h_cm, double dt_s,
                                  double mass_keV, int32_t boundary);
 
+/* Axion merging for population control: in every cell holding more than
+ * n_target axions, each group of three or more axions with the same octant
+ * of p (signs of px, py, pz; zero counts as positive) and the same |p|^2 bin
+ * becomes two axions with the group's weight W, momentum P and energy E
+ * (massless: each of weight W/2 and |p| = E/W, on either side of P at
+ * cos theta = |P|/E; Vranic et al., Comput. Phys. Commun. 191, 65 (2015);
+ * the method merges axions as a species of the PIC code, Sec. II.A, and names
+ * no algorithm). The bin of an axion is the number of the nedges (<= 30)
+ * ascending binary32 thresholds edges_p2 [(m_e c)^2] at or below
+ * |p|^2 = (px px + py py) + pz pz in binary32. Arithmetic is binary32 with
+ * every step rounded, the sums compensated (Kahan) in slot order;
+ * the new axions take the group's first two slots at the weighted mean
+ * position, the other slots are freed and closed by the tail fill. One pass;
+ * a cell may stay above n_target. Asynchronous; the first call allocates 1
+ * byte per axion slot. AXPIC_E_INVALID (nothing launched) for n_target < 0,
+ * more than 30 thresholds, or thresholds not finite, >= 0 and ascending. */
+axpic_status axpic_merge_axions(axpic_ctx *ctx, int32_t n_target, int32_t nedges, const float *edges_p2);
+/* Axions removed by every merge so far (host, 1 double). Synchronises. */
+axpic_status axpic_merge_stats(axpic_ctx *ctx, double *removed);
+
 /* Checkpoint and resume. The state a context owns between steps, besides
  * the caller's slabs and T_keV: the cells' rate records and cached electron
  * moments, the FP64 exchange and residual-carry buffers, the per-cell

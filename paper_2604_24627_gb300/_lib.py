@@ -129,6 +129,9 @@ EXPORTS = {
     "axpic_stream_axions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32]),
     "axpic_stream_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "axpic_merge_axions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_float)]),
+    "axpic_merge_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "axpic_state_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     "axpic_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
     "axpic_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
@@ -430,6 +433,18 @@ def axpic_stream_axions(ctx, dims, h_cm, dt_s, boundary, mass_keV=0.0):
 def axpic_run_steps_streamed(ctx, first, nsteps, mask, dims, h_cm, dt_s, boundary, mass_keV=0.0):
     nx, ny, nz = dims
     _check(ctx, lib().axpic_run_steps_streamed(ctx, first, nsteps, mask, nx, ny, nz, h_cm, dt_s, mass_keV, boundary))
+
+
+def axpic_merge_axions(ctx, n_target, edges_p2):
+    import numpy as np
+    e = np.ascontiguousarray(edges_p2, dtype=np.float32)
+    _check(ctx, lib().axpic_merge_axions(ctx, n_target, e.size, _fptr(e) if e.size else None))
+
+
+def axpic_merge_stats(ctx):
+    out = ctypes.c_double()
+    _check(ctx, lib().axpic_merge_stats(ctx, ctypes.byref(out)))
+    return out.value
 
 
 def axpic_save_state(ctx):

@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libaxpic.so")
-SOURCES = ["api.cu", "step.cu", "misc.cu", "mlp.cu", "sr.cu", "stream.cu", "tables.cpp", "surrogate.cpp"]
+SOURCES = ["api.cu", "step.cu", "misc.cu", "mlp.cu", "sr.cu", "stream.cu", "merge.cu", "tables.cpp", "surrogate.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include")]
 

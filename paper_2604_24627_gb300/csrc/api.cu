@@ -15,6 +15,7 @@
 #include "misc.h"
 #include "sr.h"
 #include "step.h"
+#include "merge.h"
 #include "stream.h"
 
 using namespace axpic;
@@ -111,6 +112,9 @@ struct axpic_ctx {
   int32_t* st_cnt = nullptr;  // [ncells * 27 * 2]: counts, then group offsets
   float* st_buf = nullptr;    // [ncells * axion capacity * 8]
   double* st_stats = nullptr; // [4]
+  // axion merging scratch, made by the first axpic_merge_axions call
+  uint8_t* mg_grp = nullptr;  // [ncells * axion capacity]
+  double* mg_removed = nullptr;
   void* sur_W16 = nullptr;  // layers 2 and 3 laid out for the tensor cores
   int sr_nkt = 0, sr_nne = 0, tnT = 0, tnne = 0, sur_set = 0, sur_any_trusted = 0;
   float ln_gP = 0.f, ln_gA = 0.f;
@@ -334,7 +338,8 @@ static void free_ctx(axpic_ctx* ctx) {
                   ctx->tables, ctx->tally, ctx->counters, ctx->err, ctx->scratch, ctx->bits,
                   ctx->recA,   ctx->recG,  ctx->recE,     ctx->step_dev, ctx->sr, ctx->srtab,
                   ctx->sur_P,  ctx->sur_mu, ctx->sur_sigma, ctx->sur_trust, ctx->sur_W16, ctx->sur_skip,
-                  ctx->sr_net, ctx->st_dir, ctx->st_cnt, ctx->st_buf, ctx->st_stats};
+                  ctx->sr_net, ctx->st_dir, ctx->st_cnt, ctx->st_buf, ctx->st_stats, ctx->mg_grp,
+                  ctx->mg_removed};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete ctx;
@@ -1146,6 +1151,42 @@ axpic_status axpic_load_state(axpic_ctx* ctx, const void* host_in, uint64_t byte
     CK(cudaMemcpyAsync(b.first, p, b.second, cudaMemcpyHostToDevice, ctx->stream), "copy");
     p += b.second;
   }
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  return AXPIC_OK;
+}
+
+axpic_status axpic_merge_axions(axpic_ctx* ctx, int32_t n_target, int32_t nedges, const float* edges_p2) {
+  AXPIC_RANGE("axpic_merge_axions");
+  if (!ctx) return AXPIC_E_INVALID;
+  if (n_target < 0 || nedges < 0 || nedges > kMergeMaxEdges || (nedges > 0 && !edges_p2))
+    return fail(ctx, AXPIC_E_INVALID, "axpic_merge_axions: n_target or thresholds");
+  for (int k = 0; k < nedges; ++k)
+    if (!std::isfinite(edges_p2[k]) || edges_p2[k] < 0.f || (k > 0 && !(edges_p2[k] > edges_p2[k - 1])))
+      return fail(ctx, AXPIC_E_INVALID, "axpic_merge_axions: thresholds must be finite, >= 0 and ascending");
+  const axpic_plasma_desc& d = ctx->desc;
+  if (!ctx->mg_grp) {
+    CK(cudaMalloc((void**)&ctx->mg_grp, std::max<size_t>((size_t)d.ncells * d.axions.capacity, 1)), "merge scratch");
+    CK(cudaMalloc((void**)&ctx->mg_removed, sizeof(double)), "merge scratch");
+    CK(cudaMemsetAsync(ctx->mg_removed, 0, sizeof(double), ctx->stream), "memset");
+  }
+  MergeArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.s = to_ptrs(d.axions);
+  a.ncells = d.ncells;
+  a.n_target = n_target;
+  a.nedges = nedges;
+  for (int k = 0; k < nedges; ++k) a.edges[k] = edges_p2[k];
+  a.grp = ctx->mg_grp;
+  a.removed = ctx->mg_removed;
+  CK(launch_merge(a, ctx->stream), "merge kernel");
+  return AXPIC_OK;
+}
+
+axpic_status axpic_merge_stats(axpic_ctx* ctx, double* removed) {
+  if (!ctx || !removed) return AXPIC_E_INVALID;
+  *removed = 0.0;
+  if (!ctx->mg_removed) return AXPIC_OK;
+  CK(cudaMemcpyAsync(removed, ctx->mg_removed, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "copy");
   CK(cudaStreamSynchronize(ctx->stream), "synchronize");
   return AXPIC_OK;
 }

@@ -1,0 +1,184 @@
+// Axion merging for population control: in every cell holding more than
+// n_target axions, each group of three or more axions of one momentum
+// octant and |p|^2 bin becomes two, with the group's weight, momentum and
+// energy (the N -> 2 merging of Vranic et al., Comput. Phys. Commun. 191, 65
+// (2015), for massless particles; the method merges axions as a species of
+// the PIC code, Sec. II.A, and names no algorithm).
+//
+// A warp per cell: each slot's group (comparisons of binary32 |p|^2 with the
+// thresholds, and the sign bits), the group sizes, then lanes take groups 32
+// at a time: a lane whose group has three or more members scans the cell in
+// slot order and forms the binary32 compensated sums, every rounding
+// explicit (the results match the oracle bit for bit), writes the two new
+// axions into the group's first two slots and frees the others, which the
+// tail fill closes.
+#include "merge.h"
+
+namespace axpic {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr unsigned kAll = 0xFFFFFFFFu;
+constexpr int kGroupsMax = (kMergeMaxEdges + 1) * 8;
+
+__device__ __forceinline__ float fsum3(float a, float b, float c) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)), __fmul_rn(c, c));
+}
+
+// A compensated (Kahan) binary32 sum, every step rounded as written.
+struct Kahan {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+};
+
+// The two axions replacing group g of the cell at base (n slots): binary32
+// compensated sums in slot order, then p_a and p_b on either side of P at
+// cos theta = |P| / E. Members after the first two are freed.
+__device__ void merge_group(const MergeArgs& a, long base, int n, int g) {
+  const SpeciesPtrs& s = a.s;
+  Kahan W, Px, Py, Pz, E, X, Y, Z;
+  int sa = -1, sb = -1, seen = 0;
+  for (int i = 0; i < n; ++i) {
+    if (a.grp[base + i] != g) continue;
+    const long q = base + i;
+    const float w = s.w[q], px = s.px[q], py = s.py[q], pz = s.pz[q];
+    W.add(w);
+    Px.add(__fmul_rn(w, px));
+    Py.add(__fmul_rn(w, py));
+    Pz.add(__fmul_rn(w, pz));
+    E.add(__fmul_rn(w, __fsqrt_rn(fsum3(px, py, pz))));
+    X.add(__fmul_rn(w, s.x[q]));
+    Y.add(__fmul_rn(w, s.y[q]));
+    Z.add(__fmul_rn(w, s.z[q]));
+    if (seen == 0) sa = i;
+    else if (seen == 1) sb = i;
+    else a.grp[q] = kMergeFreed;
+    ++seen;
+  }
+  const float pm = __fdiv_rn(E.s, W.s);
+  const float Pn = __fsqrt_rn(fsum3(Px.s, Py.s, Pz.s));
+  float e[3], ct;
+  if (Pn > 0.f) {
+    e[0] = __fdiv_rn(Px.s, Pn);
+    e[1] = __fdiv_rn(Py.s, Pn);
+    e[2] = __fdiv_rn(Pz.s, Pn);
+    ct = fminf(__fdiv_rn(Pn, E.s), 1.0f);
+  } else {
+    e[0] = 0.f, e[1] = 0.f, e[2] = 1.f;
+    ct = 0.f;
+  }
+  const float st = __fsqrt_rn(__fsub_rn(1.0f, __fmul_rn(ct, ct)));
+  int k = 0;
+  if (fabsf(e[1]) < fabsf(e[k])) k = 1;
+  if (fabsf(e[2]) < fabsf(e[k])) k = 2;
+  float ax[3] = {0.f, 0.f, 0.f};
+  ax[k] = 1.f;
+  const float u[3] = {__fsub_rn(__fmul_rn(e[1], ax[2]), __fmul_rn(e[2], ax[1])),
+                      __fsub_rn(__fmul_rn(e[2], ax[0]), __fmul_rn(e[0], ax[2])),
+                      __fsub_rn(__fmul_rn(e[0], ax[1]), __fmul_rn(e[1], ax[0]))};
+  const float un = __fsqrt_rn(fsum3(u[0], u[1], u[2]));
+  const float qv[3] = {__fdiv_rn(u[0], un), __fdiv_rn(u[1], un), __fdiv_rn(u[2], un)};
+  const float wh = __fmul_rn(W.s, 0.5f);
+  const float x = __fdiv_rn(X.s, W.s), y = __fdiv_rn(Y.s, W.s), z = __fdiv_rn(Z.s, W.s);
+  float pa[3], pb[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    pa[j] = __fmul_rn(pm, __fadd_rn(__fmul_rn(ct, e[j]), __fmul_rn(st, qv[j])));
+    pb[j] = __fmul_rn(pm, __fsub_rn(__fmul_rn(ct, e[j]), __fmul_rn(st, qv[j])));
+  }
+  const long qa = base + sa, qb = base + sb;
+  s.w[qa] = wh, s.px[qa] = pa[0], s.py[qa] = pa[1], s.pz[qa] = pa[2], s.x[qa] = x, s.y[qa] = y, s.z[qa] = z;
+  s.w[qb] = wh, s.px[qb] = pb[0], s.py[qb] = pb[1], s.pz[qb] = pb[2], s.x[qb] = x, s.y[qb] = y, s.z[qb] = z;
+}
+
+__global__ void __launch_bounds__(kThreads) merge_kernel(MergeArgs a) {
+  __shared__ int gcnt[kWarps][kGroupsMax];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const SpeciesPtrs& s = a.s;
+  const int ngroups = (a.nedges + 1) * 8;
+  for (int c = blockIdx.x * kWarps + wid; c < a.ncells; c += gridDim.x * kWarps) {
+    const int n = min(max(s.count[c], 0), s.cap);
+    if (n <= a.n_target) continue;
+    const long base = (long)c * s.cap;
+    for (int g = lane; g < ngroups; g += 32) gcnt[wid][g] = 0;
+    __syncwarp();
+    // each slot's group: the number of thresholds at or below |p|^2, times
+    // 8, plus the octant of p
+    for (int s0 = 0; s0 < n; s0 += 32) {
+      const int slot = s0 + lane;
+      if (slot < n) {
+        const long q = base + slot;
+        const float px = s.px[q], py = s.py[q], pz = s.pz[q];
+        const float p2 = __fadd_rn(__fadd_rn(__fmul_rn(px, px), __fmul_rn(py, py)), __fmul_rn(pz, pz));
+        int e = 0;
+        for (int k = 0; k < a.nedges; ++k) e += p2 >= a.edges[k] ? 1 : 0;
+        const int g = e * 8 + (px < 0.f ? 1 : 0) + (py < 0.f ? 2 : 0) + (pz < 0.f ? 4 : 0);
+        a.grp[q] = (uint8_t)g;
+        atomicAdd(&gcnt[wid][g], 1);
+      }
+    }
+    __syncwarp();
+    // groups of three or more, 32 at a time, a lane each; removed count
+    int removed = 0;
+    for (int g0 = 0; g0 < ngroups; g0 += 32) {
+      const int g = g0 + lane;
+      const int m = g < ngroups ? gcnt[wid][g] : 0;
+      if (!__any_sync(kAll, m >= 3)) continue;
+      if (m >= 3) {
+        merge_group(a, base, n, g);
+        removed += m - 2;
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) removed += __shfl_xor_sync(kAll, removed, d);
+    if (removed == 0) continue;
+    // the tail fill: the freed slots below the new count ns take, in
+    // ascending order, the kept slots at or beyond it, in ascending order
+    const int ns = n - removed;
+    for (int j0 = 0;; j0 += 32) {
+      const int j = j0 + lane;
+      int from = -1, to = -1, runTo = 0, runFrom = 0;
+      for (int s0 = 0; s0 < n; s0 += 32) {
+        const int slot = s0 + lane;
+        const bool freed = slot < n && a.grp[base + slot] == kMergeFreed;
+        const unsigned tm = __ballot_sync(kAll, freed && slot < ns);
+        const unsigned fm = __ballot_sync(kAll, slot < n && slot >= ns && !freed);
+        int k = j - runTo;
+        if (k >= 0 && k < __popc(tm)) to = s0 + (int)__fns(tm, 0, k + 1);
+        k = j - runFrom;
+        if (k >= 0 && k < __popc(fm)) from = s0 + (int)__fns(fm, 0, k + 1);
+        runTo += __popc(tm);
+        runFrom += __popc(fm);
+      }
+      if (j < runTo && from >= 0 && to >= 0) {
+        const long qf = base + from, qt = base + to;
+        const float w = s.w[qf], px = s.px[qf], py = s.py[qf], pz = s.pz[qf], x = s.x[qf], y = s.y[qf],
+                    z = s.z[qf];
+        s.w[qt] = w, s.px[qt] = px, s.py[qt] = py, s.pz[qt] = pz, s.x[qt] = x, s.y[qt] = y, s.z[qt] = z;
+      }
+      if (j0 + 32 >= runTo) break;
+    }
+    if (lane == 0) {
+      s.count[c] = ns;
+      atomicAdd(a.removed, (double)removed);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_merge(const MergeArgs& a, cudaStream_t st) {
+  if (a.ncells <= 0) return cudaSuccess;
+  merge_kernel<<<(a.ncells + kWarps - 1) / kWarps, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace axpic

@@ -168,6 +168,15 @@ class AxionPlasma:
         _lib.axpic_run_steps_streamed(self.ctx, first, nsteps, mask, dims, h_cm, dt_s, 0 if periodic else 1,
                                       mass_keV)
 
+    def merge_axions(self, n_target, edges_p2):
+        """Merging of the axions of every cell above n_target (axpic_merge_axions);
+        edges_p2: ascending |p|^2 thresholds in (m_e c)^2; asynchronous."""
+        _lib.axpic_merge_axions(self.ctx, n_target, edges_p2)
+
+    def merge_stats(self):
+        """Axions removed by merging so far."""
+        return _lib.axpic_merge_stats(self.ctx)
+
     def save_state(self):
         """The library-owned state (axpic_save_state) as a uint8 array; the
         slabs and T are the caller's (this object's tensors)."""
