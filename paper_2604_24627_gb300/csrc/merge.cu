@@ -5,21 +5,25 @@
 // (2015), for massless particles; the method merges axions as a species of
 // the PIC code, Sec. II.A, and names no algorithm).
 //
-// A warp per cell: each slot's group (comparisons of binary32 |p|^2 with the
-// thresholds, and the sign bits), the group sizes, then lanes take groups 32
-// at a time: a lane whose group has three or more members scans the cell in
-// slot order and forms the binary32 compensated sums, every rounding
-// explicit (the results match the oracle bit for bit), writes the two new
-// axions into the group's first two slots and frees the others, which the
-// tail fill closes.
+// A warp per cell:
+// * each slot's group (comparisons of binary32 |p|^2 with the thresholds,
+//   and the sign bits) and the group sizes;
+// * the groups of three or more in a list, and their members' slots in
+//   shared memory, grouped and in slot order (a stable counting sort);
+// * a lane per listed group forms the binary32 compensated sums over its
+//   members in slot order, every rounding explicit (the results match the
+//   oracle bit for bit), writes the two new axions into the group's first
+//   two slots and frees the others;
+// * the tail fill closes the freed slots.
 #include "merge.h"
+
+#include <algorithm>
 
 namespace axpic {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+constexpr int kWarpsMax = 8;
 constexpr unsigned kAll = 0xFFFFFFFFu;
 constexpr int kGroupsMax = (kMergeMaxEdges + 1) * 8;
 
@@ -38,15 +42,16 @@ struct Kahan {
   }
 };
 
-// The two axions replacing group g of the cell at base (n slots): binary32
-// compensated sums in slot order, then p_a and p_b on either side of P at
-// cos theta = |P| / E. Members after the first two are freed.
-__device__ void merge_group(const MergeArgs& a, long base, int n, int g) {
+// The two axions replacing the group whose m member slots, ascending, are
+// mem[0..m) of the cell at base: binary32 compensated sums in slot order,
+// then p_a and p_b on either side of P at cos theta = |P| / E. Members after
+// the first two are freed.
+__device__ void merge_group(const MergeArgs& a, long base, const uint16_t* mem, int m) {
   const SpeciesPtrs& s = a.s;
   Kahan W, Px, Py, Pz, E, X, Y, Z;
   int sa = -1, sb = -1, seen = 0;
-  for (int i = 0; i < n; ++i) {
-    if (a.grp[base + i] != g) continue;
+  for (int k = 0; k < m; ++k) {
+    const int i = mem[k];
     const long q = base + i;
     const float w = s.w[q], px = s.px[q], py = s.py[q], pz = s.pz[q];
     W.add(w);
@@ -64,27 +69,29 @@ __device__ void merge_group(const MergeArgs& a, long base, int n, int g) {
   }
   const float pm = __fdiv_rn(E.s, W.s);
   const float Pn = __fsqrt_rn(fsum3(Px.s, Py.s, Pz.s));
-  float e[3], ct;
+  float e0, e1, e2, ct;
   if (Pn > 0.f) {
-    e[0] = __fdiv_rn(Px.s, Pn);
-    e[1] = __fdiv_rn(Py.s, Pn);
-    e[2] = __fdiv_rn(Pz.s, Pn);
+    e0 = __fdiv_rn(Px.s, Pn);
+    e1 = __fdiv_rn(Py.s, Pn);
+    e2 = __fdiv_rn(Pz.s, Pn);
     ct = fminf(__fdiv_rn(Pn, E.s), 1.0f);
   } else {
-    e[0] = 0.f, e[1] = 0.f, e[2] = 1.f;
+    e0 = 0.f, e1 = 0.f, e2 = 1.f;
     ct = 0.f;
   }
   const float st = __fsqrt_rn(__fsub_rn(1.0f, __fmul_rn(ct, ct)));
+  // the axis of e_P's smallest |component|, the lowest index on ties
   int k = 0;
-  if (fabsf(e[1]) < fabsf(e[k])) k = 1;
-  if (fabsf(e[2]) < fabsf(e[k])) k = 2;
-  float ax[3] = {0.f, 0.f, 0.f};
-  ax[k] = 1.f;
-  const float u[3] = {__fsub_rn(__fmul_rn(e[1], ax[2]), __fmul_rn(e[2], ax[1])),
-                      __fsub_rn(__fmul_rn(e[2], ax[0]), __fmul_rn(e[0], ax[2])),
-                      __fsub_rn(__fmul_rn(e[0], ax[1]), __fmul_rn(e[1], ax[0]))};
-  const float un = __fsqrt_rn(fsum3(u[0], u[1], u[2]));
-  const float qv[3] = {__fdiv_rn(u[0], un), __fdiv_rn(u[1], un), __fdiv_rn(u[2], un)};
+  float amin = fabsf(e0);
+  if (fabsf(e1) < amin) k = 1, amin = fabsf(e1);
+  if (fabsf(e2) < amin) k = 2;
+  const float ax0 = k == 0 ? 1.f : 0.f, ax1 = k == 1 ? 1.f : 0.f, ax2 = k == 2 ? 1.f : 0.f;
+  const float u0 = __fsub_rn(__fmul_rn(e1, ax2), __fmul_rn(e2, ax1));
+  const float u1 = __fsub_rn(__fmul_rn(e2, ax0), __fmul_rn(e0, ax2));
+  const float u2 = __fsub_rn(__fmul_rn(e0, ax1), __fmul_rn(e1, ax0));
+  const float un = __fsqrt_rn(fsum3(u0, u1, u2));
+  const float e[3] = {e0, e1, e2};
+  const float qv[3] = {__fdiv_rn(u0, un), __fdiv_rn(u1, un), __fdiv_rn(u2, un)};
   const float wh = __fmul_rn(W.s, 0.5f);
   const float x = __fdiv_rn(X.s, W.s), y = __fdiv_rn(Y.s, W.s), z = __fdiv_rn(Z.s, W.s);
   float pa[3], pb[3];
@@ -98,23 +105,34 @@ __device__ void merge_group(const MergeArgs& a, long base, int n, int g) {
   s.w[qb] = wh, s.px[qb] = pb[0], s.py[qb] = pb[1], s.pz[qb] = pb[2], s.x[qb] = x, s.y[qb] = y, s.z[qb] = z;
 }
 
-__global__ void __launch_bounds__(kThreads) merge_kernel(MergeArgs a) {
-  __shared__ int gcnt[kWarps][kGroupsMax];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// Dynamic shared memory: cap slot indices (u16) per warp.
+__global__ void __launch_bounds__(kWarpsMax * 32) merge_kernel(MergeArgs a) {
+  extern __shared__ uint16_t smem_members[];
+  __shared__ int gcnt[kWarpsMax][kGroupsMax];  // group sizes
+  __shared__ int gpos[kWarpsMax][kGroupsMax];  // next member position of a listed group
+  __shared__ uint8_t glist[kWarpsMax][kGroupsMax];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const SpeciesPtrs& s = a.s;
+  uint16_t* mem = smem_members + (size_t)wid * s.cap;
   const int ngroups = (a.nedges + 1) * 8;
-  for (int c = blockIdx.x * kWarps + wid; c < a.ncells; c += gridDim.x * kWarps) {
+  const unsigned lt = (1u << lane) - 1u;
+  for (int c = blockIdx.x * nw + wid; c < a.ncells; c += gridDim.x * nw) {
     const int n = min(max(s.count[c], 0), s.cap);
     if (n <= a.n_target) continue;
     const long base = (long)c * s.cap;
     for (int g = lane; g < ngroups; g += 32) gcnt[wid][g] = 0;
     __syncwarp();
     // each slot's group: the number of thresholds at or below |p|^2, times
-    // 8, plus the octant of p
+    // 8, plus the octant of p; the other fields' lines go to L1 meanwhile
     for (int s0 = 0; s0 < n; s0 += 32) {
       const int slot = s0 + lane;
       if (slot < n) {
         const long q = base + slot;
+        prefetch_l1(s.w + q), prefetch_l1(s.x + q), prefetch_l1(s.y + q), prefetch_l1(s.z + q);
         const float px = s.px[q], py = s.py[q], pz = s.pz[q];
         const float p2 = __fadd_rn(__fadd_rn(__fmul_rn(px, px), __fmul_rn(py, py)), __fmul_rn(pz, pz));
         int e = 0;
@@ -125,21 +143,57 @@ __global__ void __launch_bounds__(kThreads) merge_kernel(MergeArgs a) {
       }
     }
     __syncwarp();
-    // groups of three or more, 32 at a time, a lane each; removed count
-    int removed = 0;
+    // the groups of three or more: a list, and each one's first member
+    // position (exclusive prefix of their sizes)
+    int nm = 0, run = 0;
     for (int g0 = 0; g0 < ngroups; g0 += 32) {
       const int g = g0 + lane;
       const int m = g < ngroups ? gcnt[wid][g] : 0;
-      if (!__any_sync(kAll, m >= 3)) continue;
-      if (m >= 3) {
-        merge_group(a, base, n, g);
-        removed += m - 2;
+      const bool listed = m >= 3;
+      const int v = listed ? m : 0;
+      int incl = v;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(kAll, incl, d);
+        if (lane >= d) incl += t;
+      }
+      const unsigned bm = __ballot_sync(kAll, listed);
+      if (listed) {
+        gpos[wid][g] = run + incl - v;
+        glist[wid][nm + __popc(bm & lt)] = (uint8_t)g;
+      }
+      nm += __popc(bm);
+      run += __shfl_sync(kAll, incl, 31);
+    }
+    if (nm == 0) continue;
+    __syncwarp();
+    // members of listed groups in slot order: rank among the chunk's lanes
+    // of the same group, after the group's members of earlier chunks
+    for (int s0 = 0; s0 < n; s0 += 32) {
+      const int slot = s0 + lane;
+      const int g = slot < n ? a.grp[base + slot] : 0;
+      const bool take = slot < n && gcnt[wid][g] >= 3;
+      const unsigned peers = __match_any_sync(kAll, take ? g : kGroupsMax + lane);
+      const int rank = __popc(peers & lt);
+      const int p0 = take ? gpos[wid][g] : 0;
+      __syncwarp();
+      if (take) {
+        mem[p0 + rank] = (uint16_t)slot;
+        if (rank == 0) gpos[wid][g] = p0 + __popc(peers);
       }
       __syncwarp();
     }
+    // a lane per listed group
+    int removed = 0;
+    for (int t = lane; t < nm; t += 32) {
+      const int g = glist[wid][t];
+      const int m = gcnt[wid][g];
+      merge_group(a, base, mem + (gpos[wid][g] - m), m);
+      removed += m - 2;
+    }
+    __syncwarp();
 #pragma unroll
     for (int d = 16; d; d >>= 1) removed += __shfl_xor_sync(kAll, removed, d);
-    if (removed == 0) continue;
     // the tail fill: the freed slots below the new count ns take, in
     // ascending order, the kept slots at or beyond it, in ascending order
     const int ns = n - removed;
@@ -177,7 +231,19 @@ __global__ void __launch_bounds__(kThreads) merge_kernel(MergeArgs a) {
 
 cudaError_t launch_merge(const MergeArgs& a, cudaStream_t st) {
   if (a.ncells <= 0) return cudaSuccess;
-  merge_kernel<<<(a.ncells + kWarps - 1) / kWarps, kThreads, 0, st>>>(a);
+  if (a.s.cap > kMergeMaxCap) return cudaErrorInvalidValue;
+  // warps per CTA: as many as fit the members' shared memory, at most 8
+  constexpr int kDynMax = 160 * 1024;
+  const size_t per_warp = (size_t)std::max(a.s.cap, 1) * sizeof(uint16_t);
+  const int nw = (int)std::max<size_t>(1, std::min<size_t>(kWarpsMax, kDynMax / per_warp));
+  const size_t dyn = per_warp * nw;
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynMax);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  merge_kernel<<<(a.ncells + nw - 1) / nw, nw * 32, dyn, st>>>(a);
   return cudaGetLastError();
 }
 

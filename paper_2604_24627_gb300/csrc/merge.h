@@ -9,6 +9,7 @@ namespace axpic {
 
 constexpr int kMergeMaxEdges = 30;  // |p|^2 thresholds: (30 + 1) bins x 8 octants = 248 groups
 constexpr int kMergeFreed = 255;    // group byte of a freed slot
+constexpr int kMergeMaxCap = 65535; // slots per cell, u16 member indices (slabs hold at most 65532)
 
 struct MergeArgs {
   SpeciesPtrs s;     // the axion slabs

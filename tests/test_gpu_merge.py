@@ -76,6 +76,26 @@ def test_merging_matches_oracle(n_target):
     pl.close()
 
 
+def test_large_cells_fewer_warps_per_block():
+    """Capacities of 12000 and 40000 slots leave room for six and two warps'
+    member lists in a block; cells of thousands of axions, groups of
+    hundreds, equal the oracle bit for bit."""
+    for cap, counts in ((12000, [0, 11000, 12000, 37]), (40000, [40000, 25000])):
+        rng = np.random.default_rng(cap)
+        cells = [random_axions(rng, k) for k in counts]
+        pl = make(len(counts), cap)
+        for c, sp in enumerate(cells):
+            pl.slabs["axions"].set_cell(c, {f: getattr(sp, f) for f in FIELDS})
+        torch.cuda.synchronize()
+        pl.merge_axions(30, EDGES)
+        want, removed = MG.merge(cells, 30, EDGES)
+        torch.cuda.synchronize()
+        for c in range(len(counts)):
+            assert_cell_equal(gpu_cell(pl.slabs["axions"], c), want[c], c)
+        assert pl.merge_stats() == removed
+        pl.close()
+
+
 def test_invalid_merge_arguments_launch_nothing():
     pl = make(4, 8)
     for args in ((-1, EDGES), (4, EDGES[::-1]), (4, np.array([np.nan], np.float32)),
