@@ -23,7 +23,7 @@ namespace axpic {
 
 namespace {
 
-constexpr int kWarpsMax = 8;
+constexpr int kWarpsMax = 2;  // small blocks: a cell that finishes early frees its slot
 constexpr unsigned kAll = 0xFFFFFFFFu;
 constexpr int kGroupsMax = (kMergeMaxEdges + 1) * 8;
 
@@ -49,24 +49,25 @@ struct Kahan {
 __device__ void merge_group(const MergeArgs& a, long base, const uint16_t* mem, int m) {
   const SpeciesPtrs& s = a.s;
   Kahan W, Px, Py, Pz, E, X, Y, Z;
-  int sa = -1, sb = -1, seen = 0;
+  // member k + 1's fields are loaded before member k's sums (m >= 3)
+  long q = base + mem[0];
+  float w = s.w[q], px = s.px[q], py = s.py[q], pz = s.pz[q], x = s.x[q], y = s.y[q], z = s.z[q];
   for (int k = 0; k < m; ++k) {
-    const int i = mem[k];
-    const long q = base + i;
-    const float w = s.w[q], px = s.px[q], py = s.py[q], pz = s.pz[q];
+    const long qn = base + mem[min(k + 1, m - 1)];
+    const float wn = s.w[qn], pxn = s.px[qn], pyn = s.py[qn], pzn = s.pz[qn], xn = s.x[qn], yn = s.y[qn],
+                zn = s.z[qn];
     W.add(w);
     Px.add(__fmul_rn(w, px));
     Py.add(__fmul_rn(w, py));
     Pz.add(__fmul_rn(w, pz));
     E.add(__fmul_rn(w, __fsqrt_rn(fsum3(px, py, pz))));
-    X.add(__fmul_rn(w, s.x[q]));
-    Y.add(__fmul_rn(w, s.y[q]));
-    Z.add(__fmul_rn(w, s.z[q]));
-    if (seen == 0) sa = i;
-    else if (seen == 1) sb = i;
-    else a.grp[q] = kMergeFreed;
-    ++seen;
+    X.add(__fmul_rn(w, x));
+    Y.add(__fmul_rn(w, y));
+    Z.add(__fmul_rn(w, z));
+    if (k >= 2) a.grp[q] = kMergeFreed;
+    q = qn, w = wn, px = pxn, py = pyn, pz = pzn, x = xn, y = yn, z = zn;
   }
+  const int sa = mem[0], sb = mem[1];
   const float pm = __fdiv_rn(E.s, W.s);
   const float Pn = __fsqrt_rn(fsum3(Px.s, Py.s, Pz.s));
   float e0, e1, e2, ct;
@@ -93,7 +94,7 @@ __device__ void merge_group(const MergeArgs& a, long base, const uint16_t* mem, 
   const float e[3] = {e0, e1, e2};
   const float qv[3] = {__fdiv_rn(u0, un), __fdiv_rn(u1, un), __fdiv_rn(u2, un)};
   const float wh = __fmul_rn(W.s, 0.5f);
-  const float x = __fdiv_rn(X.s, W.s), y = __fdiv_rn(Y.s, W.s), z = __fdiv_rn(Z.s, W.s);
+  const float mx = __fdiv_rn(X.s, W.s), my = __fdiv_rn(Y.s, W.s), mz = __fdiv_rn(Z.s, W.s);
   float pa[3], pb[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
@@ -101,8 +102,8 @@ __device__ void merge_group(const MergeArgs& a, long base, const uint16_t* mem, 
     pb[j] = __fmul_rn(pm, __fsub_rn(__fmul_rn(ct, e[j]), __fmul_rn(st, qv[j])));
   }
   const long qa = base + sa, qb = base + sb;
-  s.w[qa] = wh, s.px[qa] = pa[0], s.py[qa] = pa[1], s.pz[qa] = pa[2], s.x[qa] = x, s.y[qa] = y, s.z[qa] = z;
-  s.w[qb] = wh, s.px[qb] = pb[0], s.py[qb] = pb[1], s.pz[qb] = pb[2], s.x[qb] = x, s.y[qb] = y, s.z[qb] = z;
+  s.w[qa] = wh, s.px[qa] = pa[0], s.py[qa] = pa[1], s.pz[qa] = pa[2], s.x[qa] = mx, s.y[qa] = my, s.z[qa] = mz;
+  s.w[qb] = wh, s.px[qb] = pb[0], s.py[qb] = pb[1], s.pz[qb] = pb[2], s.x[qb] = mx, s.y[qb] = my, s.z[qb] = mz;
 }
 
 __device__ __forceinline__ void prefetch_l1(const void* p) {
@@ -110,7 +111,7 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
 }
 
 // Dynamic shared memory: cap slot indices (u16) per warp.
-__global__ void __launch_bounds__(kWarpsMax * 32) merge_kernel(MergeArgs a) {
+__global__ void __launch_bounds__(kWarpsMax * 32, 16) merge_kernel(MergeArgs a) {
   extern __shared__ uint16_t smem_members[];
   __shared__ int gcnt[kWarpsMax][kGroupsMax];  // group sizes
   __shared__ int gpos[kWarpsMax][kGroupsMax];  // next member position of a listed group
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(kWarpsMax * 32) merge_kernel(MergeArgs a) {
 cudaError_t launch_merge(const MergeArgs& a, cudaStream_t st) {
   if (a.ncells <= 0) return cudaSuccess;
   if (a.s.cap > kMergeMaxCap) return cudaErrorInvalidValue;
-  // warps per CTA: as many as fit the members' shared memory, at most 8
+  // warps per CTA: as many as fit the members' shared memory, at most 2
   constexpr int kDynMax = 160 * 1024;
   const size_t per_warp = (size_t)std::max(a.s.cap, 1) * sizeof(uint16_t);
   const int nw = (int)std::max<size_t>(1, std::min<size_t>(kWarpsMax, kDynMax / per_warp));
