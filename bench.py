@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--merge-n-target", type=int, default=64,
                     help="timed axion merging call after the other legs, toward this many a cell (0: none)")
     ap.add_argument("--merge-calls", type=int, default=10, help="timed merging calls, each on the same state")
+    ap.add_argument("--deposit-calls", type=int, default=10, help="timed composition deposits (0: none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=256, help="cells per side (256: the full workload)")
@@ -620,8 +621,35 @@ def main():
                      "axions_per_s": n_in_merged / (ms * 1e-3),
                      "algorithmic_bytes_per_axion": 56, "GBps": 56.0 * n_in_merged / (ms * 1e-3) / 1e9}
 
+    # composition from the deposited electron density
+    # (axpic_deposit_composition) into a scratch array, 10 calls. Algorithmic
+    # bytes: each electron's weight read (4 B) and each cell's count and ion
+    # densities (4 + 8 nspecies B).
+    comp_leg = None
+    if args.deposit_calls > 0:
+        XH = 0.9 * 1.00794 / (0.9 * 1.00794 + 0.1 * 4.002602)
+        out = torch.empty(w.ncells * len(w.Z), dtype=torch.float64, device=dev)
+        pl.deposit_composition([XH, 1 - XH], -1, out)
+        torch.cuda.synchronize(dev)
+        n_el = int(pl.slabs["electrons"].count[:w.ncells].sum())
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(args.deposit_calls):
+            pl.deposit_composition([XH, 1 - XH], -1, out)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = c0.elapsed_time(c1) / args.deposit_calls
+        nbytes = 4.0 * n_el + (4.0 + 8.0 * len(w.Z)) * w.ncells
+        comp_leg = {"call": "axpic_deposit_composition", "mode": "mass fractions (X_H)", "electrons": n_el,
+                    "calls": args.deposit_calls, "ms_per_call": ms, "algorithmic_bytes": nbytes,
+                    "GBps": nbytes / (ms * 1e-3) / 1e9}
+        del out
+
     if rank == 0:
         peak, peak_kind = measured_peaks()
+        if comp_leg:
+            comp_leg["frac"] = comp_leg["GBps"] / peak
         if merge_leg:
             merge_leg["frac"] = merge_leg["GBps"] / peak
         if stream_leg:
@@ -681,6 +709,8 @@ def main():
             line["axion_streaming"] = stream_leg
         if merge_leg:
             line["axion_merging"] = merge_leg
+        if comp_leg:
+            line["composition_deposit"] = comp_leg
         if world == 1 and not args.no_cpu_baseline:
             cells = [pl.cell(c) for c in range(64)]
             from oracle import step as ostep

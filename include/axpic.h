@@ -207,6 +207,27 @@ axpic_status axpic_sample_plasma(axpic_ctx *ctx, int32_t n_el, int32_t n_ph, int
  * n_ion (temperature mode "prescribed field", Sec. II.E). */
 axpic_status axpic_update_cells(axpic_ctx *ctx);
 
+/* Composition from the deposited electron density (Sec. II.E, Eqs. rho_def
+ * and qn_def: n_e and rho inferred from the deposited charge density with
+ * the hydrogen mass fraction under quasi-neutrality, or the densities bound
+ * to one ion species). Each cell's free-electron density is that of its own
+ * electron macroparticles, n_e = sum w / cell_volume_cm3 (FP64 sums). Then,
+ * for every cell:
+ * - bind_species = -1: mass fractions mass_frac (host [nspecies], finite,
+ *   >= 0, summing to 1 within 1e-9; X_H and 1 - X_H for hydrogen-helium)
+ *   with n_e = sum_i Z_i n_i: n_i = X_i (rho/m_u) / A_i,
+ *   rho/m_u = n_e / sum_i Z_i X_i / A_i;
+ * - bind_species = k in [0, nspecies): n_k = n_e / Z_k, the others 0
+ *   (mass_frac unused).
+ * Writes n_ion_out (device [ncells*nspecies], cm^-3). When n_ion_out is the
+ * context's own n_ion array, the rate records are then rebuilt from it as by
+ * axpic_update_cells; the cached electron moments are unchanged, since the
+ * deposit moves no electron. Asynchronous. AXPIC_E_INVALID (nothing written)
+ * for a bad bind_species, a bound species with Z <= 0, missing or invalid
+ * mass fractions, or a null n_ion_out with cells. */
+axpic_status axpic_deposit_composition(axpic_ctx *ctx, int32_t bind_species, const double *mass_frac,
+                                       double *n_ion_out);
+
 /* Axion free streaming and cell migration: every axion moves by
  * (p / E) c dt_s, E = sqrt(p^2 + m_a^2) with m_a c^2 = mass_keV (Sec. II.B:
  * massless axions at c, massive ones sub-luminal; the axions' transport

@@ -132,6 +132,8 @@ EXPORTS = {
     "axpic_merge_axions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_float)]),
     "axpic_merge_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "axpic_deposit_composition": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.c_void_p]),
     "axpic_state_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     "axpic_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
     "axpic_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
@@ -439,6 +441,13 @@ def axpic_merge_axions(ctx, n_target, edges_p2):
     import numpy as np
     e = np.ascontiguousarray(edges_p2, dtype=np.float32)
     _check(ctx, lib().axpic_merge_axions(ctx, n_target, e.size, _fptr(e) if e.size else None))
+
+
+def axpic_deposit_composition(ctx, bind_species, mass_frac, n_ion_out_ptr):
+    import numpy as np
+    x = None if mass_frac is None else np.ascontiguousarray(mass_frac, dtype=np.float64)
+    xp = None if x is None else x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _check(ctx, lib().axpic_deposit_composition(ctx, bind_species, xp, n_ion_out_ptr))
 
 
 def axpic_merge_stats(ctx):

@@ -567,6 +567,44 @@ axpic_status axpic_update_cells(axpic_ctx* ctx) {
   return AXPIC_OK;
 }
 
+axpic_status axpic_deposit_composition(axpic_ctx* ctx, int32_t bind_species, const double* mass_frac,
+                                       double* n_ion_out) {
+  AXPIC_RANGE("axpic_deposit_composition");
+  if (!ctx) return AXPIC_E_INVALID;
+  const axpic_plasma_desc& d = ctx->desc;
+  const int ns = d.nspecies;
+  if (!n_ion_out && d.ncells > 0) return fail(ctx, AXPIC_E_INVALID, "axpic_deposit_composition: n_ion_out");
+  DepositCoef k;
+  std::memset(&k, 0, sizeof(k));
+  k.volume_cm3 = d.cell_volume_cm3;
+  if (bind_species >= 0) {
+    if (bind_species >= ns || !(d.Z[bind_species] > 0.0))
+      return fail(ctx, AXPIC_E_INVALID, "axpic_deposit_composition: bound species out of range or Z <= 0");
+    k.coef[bind_species] = 1.0 / d.Z[bind_species];
+  } else if (bind_species == -1) {
+    if (!mass_frac) return fail(ctx, AXPIC_E_INVALID, "axpic_deposit_composition: mass fractions missing");
+    double sum = 0.0, zxa = 0.0;
+    for (int i = 0; i < ns; ++i) {
+      if (!std::isfinite(mass_frac[i]) || mass_frac[i] < 0.0)
+        return fail(ctx, AXPIC_E_INVALID, "axpic_deposit_composition: mass fractions must be finite and >= 0");
+      sum += mass_frac[i];
+      zxa += d.Z[i] * mass_frac[i] / d.A[i];
+    }
+    if (std::fabs(sum - 1.0) > 1e-9 || !(zxa > 0.0))
+      return fail(ctx, AXPIC_E_INVALID, "axpic_deposit_composition: mass fractions must sum to 1 and carry charge");
+    // n_i = X_i (rho / m_u) / A_i with rho / m_u = n_e / sum_i Z_i X_i / A_i
+    for (int i = 0; i < ns; ++i) k.coef[i] = mass_frac[i] / d.A[i] / zxa;
+  } else {
+    return fail(ctx, AXPIC_E_INVALID, "axpic_deposit_composition: bind_species must be -1 or a species");
+  }
+  CK(launch_deposit(d.ncells, ns, to_ptrs(d.electrons), k, n_ion_out, ctx->stream), "deposit");
+  if (n_ion_out == d.n_ion) {
+    CK(launch_records(d.ncells, ns, ctx->cc, d.T_keV, d.n_ion, ctx->rec, ctx->err, ctx->stream), "records");
+    CK(build_records(ctx, ctx->stream), "spectral records");
+  }
+  return AXPIC_OK;
+}
+
 static axpic_status run_phases(axpic_ctx* ctx, int phases, int64_t step, int32_t mask, const char* name) {
   if (!ctx) return AXPIC_E_INVALID;
   if (step < 0 || step >= (int64_t)0xFFFFFFFF) return fail(ctx, AXPIC_E_INVALID, std::string(name) + ": step out of range");

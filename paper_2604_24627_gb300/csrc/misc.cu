@@ -67,6 +67,30 @@ cudaError_t launch_info(int first, int count, const CellConst& cc, double k_gamm
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- deposit
+// Composition from the deposited electron density (Sec. II.E, Eqs. rho_def,
+// qn_def): n_e = sum w / V over the cell's electron macroparticles (FP64,
+// one warp per cell), then n_i = n_e * coef_i with the host's coefficients.
+__global__ void deposit_kernel(int ncells, int nspecies, SpeciesPtrs e, DepositCoef k, double* __restrict__ n_ion) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c >= ncells) return;
+  const int n = min(max(e.count[c], 0), e.cap);
+  const long b = (long)c * e.cap;
+  double W = 0.0;
+  for (int i = lane; i < n; i += 32) W += (double)e.w[b + i];
+  for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(kFullMask, W, o);
+  const double n_e = W / k.volume_cm3;
+  if (lane < nspecies) n_ion[(size_t)c * nspecies + lane] = n_e * k.coef[lane];
+}
+
+cudaError_t launch_deposit(int ncells, int nspecies, const SpeciesPtrs& e, const DepositCoef& k, double* n_ion,
+                           cudaStream_t st) {
+  if (ncells == 0) return cudaSuccess;
+  deposit_kernel<<<(ncells + 7) / 8, 256, 0, st>>>(ncells, nspecies, e, k, n_ion);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- moments
 // Cached electron moments W, P, U2 and var = U2 - |P|^2 / W (Eqs.
 // cell_moments, var_unnormalized), one warp per cell.

@@ -15,6 +15,14 @@ struct SampleArgs {
   const float* tables;
 };
 
+// n_i = (sum of the cell's electron weights / V) * coef[i]
+struct DepositCoef {
+  double volume_cm3;
+  double coef[kMaxSpecies];
+};
+
+cudaError_t launch_deposit(int ncells, int nspecies, const SpeciesPtrs& e, const DepositCoef& k, double* n_ion,
+                           cudaStream_t st);
 cudaError_t launch_records(int ncells, int nspecies, const CellConst& cc, const double* T, const double* n_ion,
                            float* rec, int* err, cudaStream_t st);
 cudaError_t launch_info(int first, int count, const CellConst& cc, double k_gamma, const float* rec, double* out,

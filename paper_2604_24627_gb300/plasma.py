@@ -168,6 +168,16 @@ class AxionPlasma:
         _lib.axpic_run_steps_streamed(self.ctx, first, nsteps, mask, dims, h_cm, dt_s, 0 if periodic else 1,
                                       mass_keV)
 
+    def deposit_composition(self, mass_frac=None, bind_species=-1, out=None):
+        """Ion densities from the deposited electron density
+        (axpic_deposit_composition): mass fractions under quasi-neutrality, or
+        the whole density on bind_species. out: a device float64 tensor of
+        ncells * nspecies (default: the context's own n_ion, whose records are
+        then rebuilt); asynchronous; returns out."""
+        out = self.n_ion if out is None else out
+        _lib.axpic_deposit_composition(self.ctx, bind_species, mass_frac, out.data_ptr())
+        return out
+
     def merge_axions(self, n_target, edges_p2):
         """Merging of the axions of every cell above n_target (axpic_merge_axions);
         edges_p2: ascending |p|^2 thresholds in (m_e c)^2; asynchronous."""
