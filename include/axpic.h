@@ -211,7 +211,9 @@ axpic_status axpic_update_cells(axpic_ctx *ctx);
  * and qn_def: n_e and rho inferred from the deposited charge density with
  * the hydrogen mass fraction under quasi-neutrality, or the densities bound
  * to one ion species). Each cell's free-electron density is that of its own
- * electron macroparticles, n_e = sum w / cell_volume_cm3 (FP64 sums). Then,
+ * electron macroparticles, n_e = sum w / cell_volume_cm3 (summed in
+ * compensated binary32 pairs per lane, then in FP64: within about
+ * (count/32) 2^-48 of the exact sum). Then,
  * for every cell:
  * - bind_species = -1: mass fractions mass_frac (host [nspecies], finite,
  *   >= 0, summing to 1 within 1e-9; X_H and 1 - X_H for hydrogen-helium)

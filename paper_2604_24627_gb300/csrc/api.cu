@@ -576,11 +576,10 @@ axpic_status axpic_deposit_composition(axpic_ctx* ctx, int32_t bind_species, con
   if (!n_ion_out && d.ncells > 0) return fail(ctx, AXPIC_E_INVALID, "axpic_deposit_composition: n_ion_out");
   DepositCoef k;
   std::memset(&k, 0, sizeof(k));
-  k.volume_cm3 = d.cell_volume_cm3;
   if (bind_species >= 0) {
     if (bind_species >= ns || !(d.Z[bind_species] > 0.0))
       return fail(ctx, AXPIC_E_INVALID, "axpic_deposit_composition: bound species out of range or Z <= 0");
-    k.coef[bind_species] = 1.0 / d.Z[bind_species];
+    k.coef[bind_species] = 1.0 / d.Z[bind_species] / d.cell_volume_cm3;
   } else if (bind_species == -1) {
     if (!mass_frac) return fail(ctx, AXPIC_E_INVALID, "axpic_deposit_composition: mass fractions missing");
     double sum = 0.0, zxa = 0.0;
@@ -593,7 +592,7 @@ axpic_status axpic_deposit_composition(axpic_ctx* ctx, int32_t bind_species, con
     if (std::fabs(sum - 1.0) > 1e-9 || !(zxa > 0.0))
       return fail(ctx, AXPIC_E_INVALID, "axpic_deposit_composition: mass fractions must sum to 1 and carry charge");
     // n_i = X_i (rho / m_u) / A_i with rho / m_u = n_e / sum_i Z_i X_i / A_i
-    for (int i = 0; i < ns; ++i) k.coef[i] = mass_frac[i] / d.A[i] / zxa;
+    for (int i = 0; i < ns; ++i) k.coef[i] = mass_frac[i] / d.A[i] / zxa / d.cell_volume_cm3;
   } else {
     return fail(ctx, AXPIC_E_INVALID, "axpic_deposit_composition: bind_species must be -1 or a species");
   }

@@ -69,19 +69,62 @@ cudaError_t launch_info(int first, int count, const CellConst& cc, double k_gamm
 
 // ---------------------------------------------------------------- deposit
 // Composition from the deposited electron density (Sec. II.E, Eqs. rho_def,
-// qn_def): n_e = sum w / V over the cell's electron macroparticles (FP64,
-// one warp per cell), then n_i = n_e * coef_i with the host's coefficients.
+// qn_def): n_e = sum w / V over the cell's electron macroparticles, then
+// n_i = n_e * coef_i: the host's coefficients hold coef_i / V, so the device
+// does no FP64 division. One warp per cell, the
+// sum kept as an unevaluated binary32 pair (hi, lo): Knuth's TwoSum gives
+// the exact rounding error of each hi + w, accumulated in lo, so the pair is
+// within about (terms) 2^-48 of the exact sum without the FP64 pipe. The
+// lanes' pairs are combined the same way; one FP64 add per cell evaluates
+// the pair.
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float w) {
+  const float s = __fadd_rn(hi, w);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(w, bb));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
 __global__ void deposit_kernel(int ncells, int nspecies, SpeciesPtrs e, DepositCoef k, double* __restrict__ n_ion) {
+  constexpr int kU = 4;  // quads in flight per lane
   const int lane = threadIdx.x & 31;
   const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (c >= ncells) return;
   const int n = min(max(e.count[c], 0), e.cap);
-  const long b = (long)c * e.cap;
-  double W = 0.0;
-  for (int i = lane; i < n; i += 32) W += (double)e.w[b + i];
-  for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(kFullMask, W, o);
-  const double n_e = W / k.volume_cm3;
-  if (lane < nspecies) n_ion[(size_t)c * nspecies + lane] = n_e * k.coef[lane];
+  // cap is a multiple of 4 and the slab 16-byte aligned: quads of slots
+  const float4* w4 = reinterpret_cast<const float4*>(e.w + (long)c * e.cap);
+  float hi = 0.f, lo = 0.f;
+  for (int q0 = lane; 4 * q0 < n; q0 += 32 * kU) {
+    float4 v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int q = q0 + 32 * u;
+      v[u] = 4 * q < n ? __ldcs(w4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int j = 4 * (q0 + 32 * u);  // slots past the count add +0
+      two_sum_add(hi, lo, v[u].x);
+      two_sum_add(hi, lo, j + 1 < n ? v[u].y : 0.f);
+      two_sum_add(hi, lo, j + 2 < n ? v[u].z : 0.f);
+      two_sum_add(hi, lo, j + 3 < n ? v[u].w : 0.f);
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    const float h2 = __shfl_xor_sync(kFullMask, hi, o), l2 = __shfl_xor_sync(kFullMask, lo, o);
+    two_sum_add(hi, lo, h2);
+    lo = __fadd_rn(lo, l2);
+  }
+  // lane 0's pair for every species (the lanes combined in different orders)
+  hi = __shfl_sync(kFullMask, hi, 0);
+  lo = __shfl_sync(kFullMask, lo, 0);
+  if (lane < nspecies) {  // the FP64 work, in these lanes only
+    double cf = 0.0;      // coef[lane], read with constant indices (no local copy)
+#pragma unroll
+    for (int i = 0; i < kMaxSpecies; ++i)
+      if (lane == i) cf = k.coef[i];
+    n_ion[(size_t)c * nspecies + lane] = ((double)hi + (double)lo) * cf;
+  }
 }
 
 cudaError_t launch_deposit(int ncells, int nspecies, const SpeciesPtrs& e, const DepositCoef& k, double* n_ion,

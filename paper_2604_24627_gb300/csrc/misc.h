@@ -15,9 +15,8 @@ struct SampleArgs {
   const float* tables;
 };
 
-// n_i = (sum of the cell's electron weights / V) * coef[i]
+// n_i = (sum of the cell's electron weights) * coef[i], coef[i] including 1/V
 struct DepositCoef {
-  double volume_cm3;
   double coef[kMaxSpecies];
 };
 
