@@ -111,7 +111,7 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
 }
 
 // Dynamic shared memory: cap slot indices (u16) per warp.
-__global__ void __launch_bounds__(kWarpsMax * 32, 16) merge_kernel(MergeArgs a) {
+__global__ void __launch_bounds__(kWarpsMax * 32, 20) merge_kernel(MergeArgs a) {
   extern __shared__ uint16_t smem_members[];
   __shared__ int gcnt[kWarpsMax][kGroupsMax];  // group sizes
   __shared__ int gpos[kWarpsMax][kGroupsMax];  // next member position of a listed group
