@@ -61,6 +61,12 @@ def test_merging_matches_oracle(n_target):
     n, cap = 90, 192
     counts = [0, 1, 2, 3, cap] + [int(v) for v in rng.integers(0, 160, n - 5)]
     cells = [random_axions(rng, k) for k in counts]
+    # degenerate groups: zero momenta (P = 0) and identical axions (cos theta = 1)
+    f = np.float32
+    z = np.zeros(40, f)
+    cells[5] = Species(np.full(40, 1.25, f), z, z, z, np.full(40, .5, f), np.full(40, .5, f), np.full(40, .5, f))
+    same = random_axions(rng, 1)
+    cells[6] = Species(*[np.repeat(v, 60) for v in same.fields()])
     pl = make(n, cap)
     for c, sp in enumerate(cells):
         pl.slabs["axions"].set_cell(c, {f: getattr(sp, f) for f in FIELDS})

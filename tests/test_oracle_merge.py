@@ -93,3 +93,24 @@ def test_group_thresholds_are_inclusive_and_slots_follow_the_rule():
     # the survivor count is 4, so slot 3 takes slot 4 (w 8)
     assert removed == 2
     assert [float(v) for v in new.w] == [2.0, 9.0, 2.0, 8.0]
+
+
+def test_degenerate_groups():
+    """Zero momenta: P = 0, so e_P = e_z, cos theta = 0 and both products
+    carry p = 0. Identical axions: |P| = E up to rounding, so cos theta is 1
+    within a few binary32 roundings and sin theta = sqrt(1 - cos^2 theta) at
+    most about sqrt(2 * 4 * 2^-24) ~ 1e-3: the products sit symmetrically
+    about p, with |p| and the doubled-up weight."""
+    a, b = MG.merge_group(*sp([(1, 0, 0, 0, .1, .2, .3)] * 4).fields())
+    assert a == b and a[:4] == (f(2.0), f(0.0), f(0.0), f(0.0))
+    row = (1.5, 1e-3, 2e-3, -3e-3, .25, .5, .75)
+    a, b = MG.merge_group(*sp([row] * 5).fields())
+    want = np.array(row, dtype=f).astype(float)
+    pa, pb = np.array(a[1:4], float), np.array(b[1:4], float)
+    pn = np.linalg.norm(want[1:4])
+    assert a[0] == b[0] == f(3.75)
+    np.testing.assert_allclose((pa + pb) / 2, want[1:4], rtol=0, atol=1e-6 * pn)
+    for q in (pa, pb):
+        assert abs(np.linalg.norm(q) - pn) <= 1e-6 * pn
+        assert np.linalg.norm(q - want[1:4]) <= 1e-3 * pn
+    np.testing.assert_allclose(np.array(a[4:], float), want[4:], rtol=1e-6)
