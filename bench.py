@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-ranges", type=int, default=4, help="cell ranges pipelined in the end-to-end leg")
     ap.add_argument("--stream-calls", type=int, default=20,
                     help="timed axion streaming calls after the other legs (0: none)")
     ap.add_argument("--merge-n-target", type=int, default=64,
@@ -517,29 +518,73 @@ def main():
         elapsed_ms, particles = float(mx[0]), float(t[1])
 
     # end to end through the public API with host buffers: every step copies
-    # the whole plasma state host -> device, runs the step, copies it back
+    # the whole plasma state host -> device, runs the step, copies it back.
+    # The cells are split into ranges (whole event CTAs of 128 cells); each
+    # range's copy in, step (axpic_step_cells) and copy out are chained by
+    # events on three streams, so one range's copies overlap another's step
+    # and the two copy directions overlap each other. A range's next copy in
+    # waits for its previous copy out: the host buffers hold the state.
     e2e = None
     if args.e2e_steps > 0:
-        tensors = []
-        for slab in pl.slabs.values():
-            tensors += list(slab.data.values()) + [slab.count]
-        tensors += [pl.T]
-        host = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in tensors]
-        for h, t in zip(host, tensors):
-            h.copy_(t)
-        nbytes = sum(t.numel() * t.element_size() for t in tensors)
+        caps = {name: slab.capacity for name, slab in pl.slabs.items()}
+        fields = [(name, f) for name, slab in pl.slabs.items() for f in slab.data]
+        host = {(name, f): torch.empty(pl.slabs[name].data[f].shape, dtype=torch.float32, pin_memory=True)
+                for name, f in fields}
+        host_cnt = {name: torch.empty(slab.count.shape, dtype=torch.int32, pin_memory=True)
+                    for name, slab in pl.slabs.items()}
+        host_T = torch.empty(pl.T.shape, dtype=torch.float64, pin_memory=True)
+        for (name, f), h in host.items():
+            h.copy_(pl.slabs[name].data[f])
+        for name, h in host_cnt.items():
+            h.copy_(pl.slabs[name].count)
+        host_T.copy_(pl.T)
+        nbytes = sum(h.numel() * h.element_size() for h in list(host.values()) + list(host_cnt.values()))
+        nbytes += host_T.numel() * host_T.element_size()
+        n = w.ncells
+        part = ((n + args.e2e_ranges - 1) // args.e2e_ranges + 127) // 128 * 128 if args.e2e_ranges > 1 else n
+        ranges = [(c0, min(part, n - c0)) for c0 in range(0, n, part)]
+
+        def pairs(c0, nc):
+            out = []
+            for name, f in fields:
+                cap = caps[name]
+                out.append((host[(name, f)][c0 * cap:(c0 + nc) * cap],
+                            pl.slabs[name].data[f][c0 * cap:(c0 + nc) * cap]))
+            for name in caps:
+                out.append((host_cnt[name][c0:c0 + nc], pl.slabs[name].count[c0:c0 + nc]))
+            out.append((host_T[c0:c0 + nc], pl.T[c0:c0 + nc]))
+            return out
+
+        rpairs = [pairs(c0, nc) for c0, nc in ranges]
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         pl.tally()
+        out_done = [None] * len(ranges)
         e0.record(stream)
-        with torch.cuda.stream(stream):
-            for k in range(args.e2e_steps):
-                for h, t in zip(host, tensors):
-                    t.copy_(h, non_blocking=True)
-                pl.step(args.warmup + args.steps + nk + k, w.mask)
-                for h, t in zip(host, tensors):
-                    h.copy_(t, non_blocking=True)
+        s_in.wait_event(e0)
+        for k in range(args.e2e_steps):
+            for r, (c0, nc) in enumerate(ranges):
+                if out_done[r] is not None:
+                    s_in.wait_event(out_done[r])
+                with torch.cuda.stream(s_in):
+                    for h, t in rpairs[r]:
+                        t.copy_(h, non_blocking=True)
+                ev_in = torch.cuda.Event()
+                ev_in.record(s_in)
+                stream.wait_event(ev_in)
+                pl.step_cells(args.warmup + args.steps + nk + k, c0, nc, w.mask)
+                ev_c = torch.cuda.Event()
+                ev_c.record(stream)
+                s_out.wait_event(ev_c)
+                with torch.cuda.stream(s_out):
+                    for h, t in rpairs[r]:
+                        h.copy_(t, non_blocking=True)
+                out_done[r] = torch.cuda.Event()
+                out_done[r].record(s_out)
+        for ev in out_done:
+            stream.wait_event(ev)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         _, tot_e = pl.tally()
@@ -552,7 +597,9 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.SUM)
             e_ms, p_e = float(mx[0]), float(t[1])
         e2e = {"value": p_e / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
+               "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps, "cell_ranges": len(ranges),
+               "overlap": "copies of one cell range overlap the step of another (axpic_step_cells)"}
+        del host, host_cnt, host_T, rpairs
 
     # axion free streaming and cell migration (axpic_stream_axions) on the
     # same plasma after the legs above: the workload's grid as a periodic box

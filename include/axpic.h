@@ -334,6 +334,17 @@ axpic_status axpic_feedback(axpic_ctx *ctx, int64_t step);
 /* One step, absorb -> emit -> feedback: the three calls above enqueued
  * together (identical results). */
 axpic_status axpic_step(axpic_ctx *ctx, int64_t step, int32_t channel_mask);
+/* One full step, as axpic_step, over the cells [first_cell, first_cell +
+ * ncells) only. Cells are independent within a step (every operator is
+ * cell-local, Sec. II.D), so steps of one index over disjoint ranges that
+ * cover the context, in any order, leave the particles, temperatures and
+ * records bit for bit as one axpic_step does (tallies are FP64 sums whose
+ * rounding follows the order). This lets a caller overlap the copies of
+ * one range with the step of another. Asynchronous on the context's
+ * stream. AXPIC_E_INVALID (nothing launched) for a range outside the
+ * context, a step index outside [0, 2^32 - 1) or unknown channel bits. */
+axpic_status axpic_step_cells(axpic_ctx *ctx, int64_t step, int32_t channel_mask, int32_t first_cell,
+                              int32_t ncells);
 
 /* Emitted-spectrum tally (App. B): H_out (host, 3*nbins doubles, channel-
  * major: Primakoff, Compton-like, bremsstrahlung) receives

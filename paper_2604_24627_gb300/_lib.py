@@ -100,6 +100,8 @@ EXPORTS = {
                                          ctypes.POINTER(Params), ctypes.c_void_p]),
     "axpic_sample_plasma": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "axpic_update_cells": (ctypes.c_int, [ctypes.c_void_p]),
+    "axpic_step_cells": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int32]),
     "axpic_absorb": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]),
     "axpic_emit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]),
     "axpic_feedback": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
@@ -185,6 +187,10 @@ def axpic_init_plasma(desc, params, stream=0):
 
 def axpic_sample_plasma(ctx, n_el, n_ph, n_ax):
     _check(ctx, lib().axpic_sample_plasma(ctx, n_el, n_ph, n_ax))
+
+
+def axpic_step_cells(ctx, step, mask, first_cell, ncells):
+    _check(ctx, lib().axpic_step_cells(ctx, step, mask, first_cell, ncells))
 
 
 def axpic_update_cells(ctx):

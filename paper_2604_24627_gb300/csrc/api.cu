@@ -639,6 +639,26 @@ axpic_status axpic_step(axpic_ctx* ctx, int64_t step, int32_t channel_mask) {
   return run_phases(ctx, PH_ALL, step, channel_mask, "axpic_step");
 }
 
+axpic_status axpic_step_cells(axpic_ctx* ctx, int64_t step, int32_t channel_mask, int32_t first_cell,
+                              int32_t ncells) {
+  AXPIC_RANGE("axpic_step_cells");
+  if (!ctx) return AXPIC_E_INVALID;
+  if (step < 0 || step >= (int64_t)0xFFFFFFFF) return fail(ctx, AXPIC_E_INVALID, "axpic_step_cells: step out of range");
+  if (channel_mask & ~AXPIC_CH_ALL) return fail(ctx, AXPIC_E_INVALID, "axpic_step_cells: unknown channel bits");
+  if (first_cell < 0 || ncells < 0 || first_cell > ctx->desc.ncells - ncells)
+    return fail(ctx, AXPIC_E_INVALID, "axpic_step_cells: cell range outside the context");
+  if (ncells == 0) return AXPIC_OK;
+  StepArgs A = make_args(ctx, step, channel_mask);
+  A.cell0 = first_cell;
+  A.ncells = ncells;
+  SrArgs sra = make_sr_args(ctx);
+  sra.cell0 = first_cell;
+  sra.ncells = ncells;
+  CK(launch_step(PH_ALL, A, ctx->warps, ctx->stream, nullptr, ctx->prm.rate_model ? &sra : nullptr),
+     "axpic_step_cells");
+  return AXPIC_OK;
+}
+
 static axpic_status read_err(axpic_ctx* ctx) {
   int h = 0;
   CK(cudaMemcpyAsync(&h, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "read error flag");
@@ -1202,6 +1222,7 @@ axpic_status axpic_merge_axions(axpic_ctx* ctx, int32_t n_target, int32_t nedges
       return fail(ctx, AXPIC_E_INVALID, "axpic_merge_axions: thresholds must be finite, >= 0 and ascending");
   const axpic_plasma_desc& d = ctx->desc;
   if (!ctx->mg_grp) {
+    CK(merge_init_kernels(), "merge kernel attributes");
     CK(cudaMalloc((void**)&ctx->mg_grp, std::max<size_t>((size_t)d.ncells * d.axions.capacity, 1)), "merge scratch");
     CK(cudaMalloc((void**)&ctx->mg_removed, sizeof(double)), "merge scratch");
     CK(cudaMemsetAsync(ctx->mg_removed, 0, sizeof(double), ctx->stream), "memset");

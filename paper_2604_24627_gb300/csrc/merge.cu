@@ -230,21 +230,19 @@ __global__ void __launch_bounds__(kWarpsMax * 32, 20) merge_kernel(MergeArgs a) 
 
 }  // namespace
 
+constexpr int kDynMax = 160 * 1024;  // the members' dynamic shared memory, at most
+
+cudaError_t merge_init_kernels() {
+  return cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynMax);
+}
+
 cudaError_t launch_merge(const MergeArgs& a, cudaStream_t st) {
   if (a.ncells <= 0) return cudaSuccess;
   if (a.s.cap > kMergeMaxCap) return cudaErrorInvalidValue;
   // warps per CTA: as many as fit the members' shared memory, at most 2
-  constexpr int kDynMax = 160 * 1024;
   const size_t per_warp = (size_t)std::max(a.s.cap, 1) * sizeof(uint16_t);
   const int nw = (int)std::max<size_t>(1, std::min<size_t>(kWarpsMax, kDynMax / per_warp));
-  const size_t dyn = per_warp * nw;
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynMax);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  merge_kernel<<<(a.ncells + nw - 1) / nw, nw * 32, dyn, st>>>(a);
+  merge_kernel<<<(a.ncells + nw - 1) / nw, nw * 32, per_warp * nw, st>>>(a);
   return cudaGetLastError();
 }
 

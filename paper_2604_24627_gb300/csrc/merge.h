@@ -21,6 +21,8 @@ struct MergeArgs {
   double* removed;   // [1]: axions removed so far
 };
 
+// Sets the merge kernel's shared-memory limit; called before its first launch.
+cudaError_t merge_init_kernels();
 cudaError_t launch_merge(const MergeArgs& a, cudaStream_t st);
 
 }  // namespace axpic

@@ -111,6 +111,11 @@ class AxionPlasma:
     def step(self, step, mask=_lib.CH_ALL):
         _lib.axpic_step(self.ctx, step, mask)
 
+    def step_cells(self, step, first_cell, ncells, mask=_lib.CH_ALL):
+        """One full step over cells [first_cell, first_cell + ncells) only
+        (axpic_step_cells); asynchronous."""
+        _lib.axpic_step_cells(self.ctx, step, mask, first_cell, ncells)
+
     def run_steps(self, first_step, nsteps, mask=_lib.CH_ALL):
         """nsteps full steps by replaying a CUDA graph of one step."""
         _lib.axpic_run_steps(self.ctx, first_step, nsteps, mask)

@@ -284,3 +284,27 @@ def test_c4_workload_slice_runs():
     assert cnt["electrons"].min() == w.n_el and cnt["axions"].max() <= w.caps[2]
     assert np.all(np.isfinite(pl.temperatures()))
     pl.close()
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_steps_over_cell_ranges_equal_step_calls(model):
+    """Each step run as ragged, disjoint cell ranges in a shuffled order
+    (axpic_step_cells; closed-form and exact-table rate models) gives what
+    plain step calls give; a range outside the context launches nothing."""
+    prm = base_params(rate_model=model)
+    caps = (64, 1024, 2048)
+    a, b = make_h(300, prm, caps=caps), make_h(300, prm, caps=caps)
+    cuts = [0, 1, 128, 131, 257, 300]
+    order = np.random.default_rng(5).permutation(len(cuts) - 1)
+    for s in range(6):
+        a.step(s, _lib.CH_ALL)
+        for r in order:
+            b.step_cells(s, cuts[r], cuts[r + 1] - cuts[r])
+        b.step_cells(s, 300, 0)
+    torch.cuda.synchronize()
+    assert_same(state(a), state(b), "cell ranges")
+    for args in ((0, 250, 51), (0, -1, 2), (-1, 0, 4)):
+        with pytest.raises(_lib.AxpicError):
+            b.step_cells(args[0], args[1], args[2])
+    a.close()
+    b.close()
