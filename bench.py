@@ -60,6 +60,8 @@ def parse():
                          "vs table vs closed-form rates; c4: 4096 uneven boxes in one context, autotuned launch "
                          "shape, steps replayed as a CUDA graph")
     ap.add_argument("--boxes", type=int, default=4096, help="boxes of the c4 workload")
+    ap.add_argument("--branches", type=int, default=0,
+                    help="c3: cell branches of a replayed step (1, 2, 4 or 8; 0: the library's choice)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 1000 if args.workload == "c2" else 100
@@ -355,6 +357,8 @@ def run_rate_models(args):
     lines = {}
     for model in (0, 1, 2):
         prm = dict(w.params, rate_model=model)
+        if args.branches:
+            prm["step_branches"] = args.branches
         with torch.cuda.stream(stream):
             pl = AxionPlasma(w.ncells, w.T_keV, w.n_ion, w.Z, w.A, w.volume_cm3, w.caps, prm, device=dev,
                              stream=stream)
