@@ -388,12 +388,14 @@ axpic_status axpic_get_residuals(axpic_ctx *ctx, int32_t first, int32_t count, d
  * bit masks and to ncells * (16 (axion + photon capacity) + 4 electron
  * capacity) <= 16 MiB of decision records (about 1300 cells with capacities
  * 512/384/384); larger requests return AXPIC_E_INVALID without launching.
- * The first call on a device looks up the array's device address with that
- * device current and uploads the sampling tables; make that first call
- * before any stream capture. Later calls reupload the tables only when
- * brems_gamma_shape changes.
+ * The first call on a device does a set-up: with that device current it
+ * looks up the array's device address and uploads the sampling tables; make
+ * that first call before any stream capture. Later calls reupload the tables
+ * only when brems_gamma_shape changes.
  *
- * desc, params: as for axpic_init_plasma (read during the call).
+ * desc, params: as for axpic_init_plasma (read during the call, and checked
+ *   the same way: AXPIC_E_INVALID, nothing launched, for what
+ *   axpic_init_plasma rejects; rate_model must be 0).
  * carry: device [ncells*4] FP64, owned by the caller, read and written: the
  *   energy (keV) and momentum (m_e c) not yet applied by the remap, which
  *   axpic_step keeps inside its context; zero it before the first step.
@@ -401,9 +403,9 @@ axpic_status axpic_get_residuals(axpic_ctx *ctx, int32_t first, int32_t count, d
  * electrons, on every call; no tally or per-cell diagnostics are produced.
  * Every call shares the one scratch array (it keeps the last call's
  * contents; what must start at zero is cleared by each call), so calls that
- * overlap on the GPU, on different streams or threads, race. Synchronises
- * the stream and returns AXPIC_E_CAPACITY or AXPIC_E_NUMERIC found on the
- * device. */
+ * overlap on the GPU, on different streams or threads, race. Every call
+ * waits for the stream before it returns, and returns AXPIC_E_CAPACITY or
+ * AXPIC_E_NUMERIC found on the device. */
 axpic_status axpic_step_noalloc(const axpic_plasma_desc *desc, const axpic_params *params, int64_t step,
                                 int32_t channel_mask, double *carry, void *stream);
 

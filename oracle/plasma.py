@@ -18,8 +18,7 @@ the paper's order:
   Gamma_B = rho (eps_eZ+eps_ee)/(n_e <E>).
 * Eq. gamma_abs: Gamma_abs(E) = (d ndot/dE) / (d n_eq/dE), MB or BE target.
 
-Readings where the paper is silent (each listed in the design notes):
-<E> is the number mean of the channel's sampling kernel; the fit brackets
+Readings where the paper is silent: <E> is the number mean of the channel's sampling kernel; the fit brackets
 [1-0.0698 eta] and [1-0.140 eta] are clamped at zero; Primakoff targets are
 the ions (option: all charges, n_eff).
 

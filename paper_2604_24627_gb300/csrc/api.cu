@@ -170,6 +170,39 @@ static std::string check_species(const axpic_species& s, const char* name) {
   return "";
 }
 
+// The checks every entry point that takes a plasma description and options
+// makes before launching anything: an empty string when they hold, else
+// what failed.
+static std::string check_plasma(const axpic_plasma_desc& d, const axpic_params& p) {
+  if (d.ncells < 0) return "ncells < 0";
+  if (d.nspecies < 1 || d.nspecies > kMaxSpecies) return "nspecies must be in 1..8";
+  if (d.cell_index_base < 0 || d.cell_index_base + d.ncells > (int64_t)0xFFFFFFFF)
+    return "global cell indices must fit in 32 bits";
+  if (d.ncells > 0 && (!d.T_keV || !d.n_ion)) return "T_keV or n_ion is NULL";
+  if (!d.Z || !d.A) return "Z or A is NULL";
+  if (!(d.cell_volume_cm3 > 0)) return "cell_volume_cm3 must be > 0";
+  for (auto sp : {std::make_pair(&d.electrons, "electrons"), std::make_pair(&d.photons, "photons"),
+                  std::make_pair(&d.axions, "axions")}) {
+    const std::string m = check_species(*sp.first, sp.second);
+    if (!m.empty()) return m;
+  }
+  for (int s = 0; s < d.nspecies; ++s)
+    if (!(d.Z[s] > 0) || !(d.A[s] > 0)) return "Z and A must be > 0";
+  if (!(p.dt_phys_s > 0) || !(p.w_a > 0)) return "dt_phys_s and w_a must be > 0";
+  if (!((float)p.w_a > 0) || !std::isfinite((float)p.w_a)) return "w_a must be representable in binary32";
+  if (!(p.relax_r >= 0 && p.relax_r <= 1)) return "relax_r must be in [0, 1]";
+  if (!(p.brems_gamma_shape > 0)) return "brems_gamma_shape must be > 0";
+  if (p.kappa_mode != 0 && p.kappa_mode != 1) return "kappa_mode must be 0 or 1";
+  if (p.kappa_mode == 1 && !(p.kappa_fixed_keV > 0)) return "kappa_fixed_keV must be > 0";
+  if (p.eq_stats != 0 && p.eq_stats != 1) return "eq_stats must be 0 or 1";
+  if (p.absorb_mode != 0 && p.absorb_mode != 1) return "absorb_mode must be 0 or 1";
+  if (p.T_mode < 0 || p.T_mode > 2) return "T_mode must be 0, 1 or 2";
+  if (!(p.T_floor_keV <= p.T_ceil_keV)) return "T_floor_keV > T_ceil_keV";
+  if (p.tally_nbins < 1 || !(p.tally_Emax_keV > 0)) return "tally_nbins >= 1 and tally_Emax_keV > 0";
+  if (!(p.prim_inverse_mult >= 0)) return "prim_inverse_mult must be >= 0";
+  return "";
+}
+
 static double w_gref(const axpic_params& p) { return p.w_gamma_ref > 0 ? p.w_gamma_ref : p.w_a; }
 
 static void fold_constants(axpic_ctx* ctx) {
@@ -392,32 +425,9 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
     delete ctx;
     return AXPIC_E_INVALID;
   };
-  if (d.ncells < 0) return bad("ncells < 0");
-  if (d.nspecies < 1 || d.nspecies > kMaxSpecies) return bad("nspecies must be in 1..8");
-  if (d.cell_index_base < 0 || d.cell_index_base + d.ncells > (int64_t)0xFFFFFFFF)
-    return bad("global cell indices must fit in 32 bits");
-  if (d.ncells > 0 && (!d.T_keV || !d.n_ion)) return bad("T_keV or n_ion is NULL");
-  if (!d.Z || !d.A) return bad("Z or A is NULL");
-  if (!(d.cell_volume_cm3 > 0)) return bad("cell_volume_cm3 must be > 0");
-  for (auto sp : {std::make_pair(&d.electrons, "electrons"), std::make_pair(&d.photons, "photons"),
-                  std::make_pair(&d.axions, "axions")}) {
-    const std::string m = check_species(*sp.first, sp.second);
-    if (!m.empty()) return bad(m);
-  }
-  if (!(p.dt_phys_s > 0) || !(p.w_a > 0)) return bad("dt_phys_s and w_a must be > 0");
-  if (!((float)p.w_a > 0) || !std::isfinite((float)p.w_a)) return bad("w_a must be representable in binary32");
-  if (!(p.relax_r >= 0 && p.relax_r <= 1)) return bad("relax_r must be in [0, 1]");
-  if (!(p.brems_gamma_shape > 0)) return bad("brems_gamma_shape must be > 0");
-  if (p.kappa_mode != 0 && p.kappa_mode != 1) return bad("kappa_mode must be 0 or 1");
-  if (p.kappa_mode == 1 && !(p.kappa_fixed_keV > 0)) return bad("kappa_fixed_keV must be > 0");
-  if (p.eq_stats != 0 && p.eq_stats != 1) return bad("eq_stats must be 0 or 1");
-  if (p.absorb_mode != 0 && p.absorb_mode != 1) return bad("absorb_mode must be 0 or 1");
-  if (p.T_mode < 0 || p.T_mode > 2) return bad("T_mode must be 0, 1 or 2");
-  if (!(p.T_floor_keV <= p.T_ceil_keV)) return bad("T_floor_keV > T_ceil_keV");
-  if (p.tally_nbins < 1 || !(p.tally_Emax_keV > 0)) return bad("tally_nbins >= 1 and tally_Emax_keV > 0");
-  if (!(p.prim_inverse_mult >= 0)) return bad("prim_inverse_mult must be >= 0");
+  const std::string why = check_plasma(d, p);
+  if (!why.empty()) return bad(why);
   for (int s = 0; s < d.nspecies; ++s) {
-    if (!(d.Z[s] > 0) || !(d.A[s] > 0)) return bad("Z and A must be > 0");
     ctx->Z.push_back(d.Z[s]);
     ctx->A.push_back(d.A[s]);
   }
@@ -1326,15 +1336,9 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc* desc, const axpic_param
     fprintf(stderr, "axpic_step_noalloc: %s\n", m);
     return AXPIC_E_INVALID;
   };
-  if (d.ncells < 0 || d.ncells > kNoAllocMaxCells) return bad("ncells outside [0, 16384], the scratch maximum");
-  if (d.nspecies < 1 || d.nspecies > kMaxSpecies || !d.Z || !d.A) return bad("bad ion species");
-  if (d.ncells > 0 && (!d.T_keV || !d.n_ion)) return bad("T_keV or n_ion is NULL");
-  if (d.cell_index_base < 0 || d.cell_index_base + d.ncells > (int64_t)0xFFFFFFFF) return bad("cell indices");
-  for (auto sp : {&d.electrons, &d.photons, &d.axions})
-    if (!check_species(*sp, "species").empty()) return bad("bad species slab");
-  if (!(p.dt_phys_s > 0) || !(p.w_a > 0) || !(p.brems_gamma_shape > 0)) return bad("bad params");
-  if (p.T_mode < 0 || p.T_mode > 2 || p.eq_stats < 0 || p.eq_stats > 1 || p.absorb_mode < 0 || p.absorb_mode > 1)
-    return bad("bad params");
+  if (d.ncells > kNoAllocMaxCells) return bad("ncells above 16384, the scratch maximum");
+  const std::string why = check_plasma(d, p);
+  if (!why.empty()) return bad(why.c_str());
   if (step < 0 || step >= (int64_t)0xFFFFFFFF || (channel_mask & ~AXPIC_CH_ALL)) return bad("bad step or mask");
   if (p.rate_model != 0) return bad("rate_model must be 0 (the records need a context)");
   const size_t per_warp = step_smem_per_warp(d.axions.capacity, d.photons.capacity, d.electrons.capacity);

@@ -26,7 +26,9 @@ namespace axpic {
 // C (M x N) = A (M x K) . B (K x N) on tiles of 128 rows, split along K into
 // chunks of kc. A(m, k) = transA ? A[k * lda + m] : A[m * lda + k], and
 // B(k, n) likewise. Store mode (accumulate = 0, one K chunk): C = AB + bias,
-// then tanh when act = 1. Accumulate mode: C += AB by atomics (split-K).
+// then tanh when act = 1. Accumulate mode (split-K): K chunk s writes its
+// partial product to part[s][M][N]; a second kernel adds the partials to C
+// in chunk order, so the sum (and training) does not depend on scheduling.
 struct GemmArgs {
   const float* A;
   long lda;
@@ -38,6 +40,7 @@ struct GemmArgs {
   long ldc;
   const float* bias;
   int M, N, K, kc, accumulate, act;
+  float* part;  // accumulate mode: [ceil(K / kc)][M][N]
   int* err;
 };
 
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(GemmArgs g) {
           const int n = c0 + j;
           float v = __uint_as_float(r[j]);
           if (g.accumulate) {
-            atomicAdd(g.C + (long)m * g.ldc + n, v);
+            g.part[((long)blockIdx.y * g.M + m) * g.N + n] = v;
           } else {
             if (g.bias) v += g.bias[n];
             if (g.act == 1) v = act_tanh(v);
@@ -134,14 +137,30 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_tc_kernel(GemmArgs g) {
 
 static size_t gemm_smem(int N, int kc) { return (size_t)(128 + N) * kc * sizeof(__nv_bfloat16); }
 
+// C[m][n] += sum over s = 0, 1, ... of part[s][m][n], in that order.
+__global__ void splitk_sum_kernel(const float* __restrict__ part, int splits, int M, int N, float* __restrict__ C,
+                                  long ldc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M * N) return;
+  const long mn = (long)M * N;
+  float acc = 0.f;
+  for (int s = 0; s < splits; ++s) acc += part[s * mn + i];
+  const int m = i / N, n = i - m * N;
+  C[(long)m * ldc + n] += acc;
+}
+
 cudaError_t gemm_tc(const GemmArgs& g0, cudaStream_t st) {
   GemmArgs g = g0;
   if (g.M <= 0) return cudaSuccess;
   if (g.N < 16 || g.N > kGemmMaxN || (g.N & 15) || g.K <= 0) return cudaErrorInvalidValue;
   if (!g.accumulate) g.kc = ((g.K + 15) / 16) * 16;
   if (g.kc < 16 || g.kc > kGemmMaxKc || (g.kc & 15)) return cudaErrorInvalidValue;
+  if (g.accumulate && (!g.part || g.M > 128)) return cudaErrorInvalidValue;
   const dim3 grid((g.M + 127) / 128, (g.K + g.kc - 1) / g.kc);
   gemm_tc_kernel<<<grid, kGemmThreads, gemm_smem(g.N, g.kc), st>>>(g);
+  cudaError_t e = cudaGetLastError();
+  if (e || !g.accumulate) return e;
+  splitk_sum_kernel<<<(g.M * g.N + 255) / 256, 256, 0, st>>>(g.part, (int)grid.y, g.M, g.N, g.C, g.ldc);
   return cudaGetLastError();
 }
 
@@ -234,21 +253,25 @@ __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, 
 
 // ---------------------------------------------------------------- the network
 Mlp::~Mlp() {
-  void* bufs[] = {P, G, Ma, Va, h1, h2, z, dz, dh, err, loss};
+  void* bufs[] = {P, G, Ma, Va, h1, h2, z, dz, dh, part, err, loss};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }
 
 cudaError_t Mlp::reserve(int n) {
   if (n <= cap) return cudaSuccess;
-  void* bufs[] = {h1, h2, z, dz, dh};
+  void* bufs[] = {h1, h2, z, dz, dh, part};
   for (void* b : bufs)
     if (b) cudaFree(b);
-  h1 = h2 = z = dz = dh = nullptr;
+  h1 = h2 = z = dz = dh = part = nullptr;
   cudaError_t e;
+  // split-K partials of the weight gradients: K = n rows in chunks of 128,
+  // at most 64 x 96 outputs each
+  const size_t splits = ((size_t)n + 127) / 128;
   if ((e = cudaMalloc(&h1, sizeof(float) * 64 * (size_t)n)) || (e = cudaMalloc(&h2, sizeof(float) * 64 * (size_t)n)) ||
       (e = cudaMalloc(&z, sizeof(float) * 96 * (size_t)n)) || (e = cudaMalloc(&dz, sizeof(float) * 96 * (size_t)n)) ||
-      (e = cudaMalloc(&dh, sizeof(float) * 64 * (size_t)n)))
+      (e = cudaMalloc(&dh, sizeof(float) * 64 * (size_t)n)) ||
+      (e = cudaMalloc(&part, sizeof(float) * 64 * 96 * (splits > 0 ? splits : 1))))
     return e;
   cap = n;
   return cudaSuccess;
@@ -289,7 +312,8 @@ static GemmArgs store_gemm(const float* A, int K, const float* B, long ldb, int 
 }
 
 // C (rows x cols) += A^T B with A n x rows and B n x cols (weight gradients).
-static GemmArgs wgrad_gemm(const float* A, int rows, const float* B, int cols, float* C, int n, int* err) {
+static GemmArgs wgrad_gemm(const float* A, int rows, const float* B, int cols, float* C, int n, float* part,
+                           int* err) {
   GemmArgs g;
   std::memset(&g, 0, sizeof(g));
   g.A = A;
@@ -304,6 +328,7 @@ static GemmArgs wgrad_gemm(const float* A, int rows, const float* B, int cols, f
   g.K = n;
   g.kc = 128;
   g.accumulate = 1;
+  g.part = part;
   g.err = err;
   return g;
 }
@@ -330,13 +355,13 @@ cudaError_t Mlp::gradients(const float* X, const float* Zt, int n) {
   const long tz = (long)n * 96, th = (long)n * 64;
   out_grad_kernel<<<1024, 256, 0, st>>>(z, Zt, dz, tz, 1.0f / (float)n, loss);
   // layer 3: gW3 = h2^T dz, gb3, dh2 = dz W3^T
-  if ((e = cudaGetLastError()) || (e = gemm_tc(wgrad_gemm(h2, 64, dz, 96, G + kOffW3, n, err), st))) return e;
+  if ((e = cudaGetLastError()) || (e = gemm_tc(wgrad_gemm(h2, 64, dz, 96, G + kOffW3, n, part, err), st))) return e;
   colsum_kernel<<<96, 256, 0, st>>>(dz, n, 96, G + kOffB3);
   if ((e = cudaGetLastError()) || (e = gemm_tc(store_gemm(dz, 96, W3(), 96, 1, dh, 64, nullptr, 0, n, err), st)))
     return e;
   // layer 2: da2 = dh2 (1 - h2^2), gW2 = h1^T da2, gb2, dh1 = da2 W2^T
   tanh_back_kernel<<<1024, 256, 0, st>>>(dh, h2, th);
-  if ((e = cudaGetLastError()) || (e = gemm_tc(wgrad_gemm(h1, 64, dh, 64, G + kOffW2, n, err), st))) return e;
+  if ((e = cudaGetLastError()) || (e = gemm_tc(wgrad_gemm(h1, 64, dh, 64, G + kOffW2, n, part, err), st))) return e;
   colsum_kernel<<<64, 256, 0, st>>>(dh, n, 64, G + kOffB2);
   // h2 is free now: dh1 goes there
   if ((e = cudaGetLastError()) || (e = gemm_tc(store_gemm(dh, 64, W2(), 64, 1, h2, 64, nullptr, 0, n, err), st)))

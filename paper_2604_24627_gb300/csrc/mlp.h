@@ -12,6 +12,7 @@ struct Mlp {
   cudaStream_t st = nullptr;
   float *P = nullptr, *G = nullptr, *Ma = nullptr, *Va = nullptr;  // params, grads, Adam moments
   float *h1 = nullptr, *h2 = nullptr, *z = nullptr, *dz = nullptr, *dh = nullptr;
+  float* part = nullptr;  // split-K partials of the weight gradients
   int* err = nullptr;
   double* loss = nullptr;
   int cap = 0;

@@ -19,6 +19,8 @@
 // The separate API calls run the same kernels with a subset of the passes;
 // the exchange passes through an FP64 per-cell buffer in the same summation
 // order, so results do not depend on how a step is called.
+#include <mutex>
+
 #include "common.cuh"
 #include "sr.h"
 #include "step.h"
@@ -2039,13 +2041,25 @@ cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t s
   }
 }
 
+// The dynamic shared-memory limit of the event kernels is a process-wide
+// attribute of each function: contexts with smaller slabs share it with
+// larger ones, so it is only ever raised (per device, under a lock), never
+// lowered under a context that needs more.
 cudaError_t set_step_smem_limits(size_t bytes) {
-  cudaError_t e;
+  static std::mutex mu;
+  static size_t set_for[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t* cur = dev >= 0 && dev < 64 ? &set_for[dev] : nullptr;
+  if (cur && bytes <= *cur) return cudaSuccess;
   const int b = (int)bytes;
   if ((e = cudaFuncSetAttribute(event_kernel<PH_ABSORB>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) ||
       (e = cudaFuncSetAttribute(event_kernel<PH_EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) ||
       (e = cudaFuncSetAttribute(event_kernel<PH_ABSORB | PH_EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
     return e;
+  if (cur) *cur = bytes;
   return cudaSuccess;
 }
 

@@ -17,6 +17,8 @@ cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t s
 constexpr int kStepKernels = 3;
 // Comma-separated names of the kernels a PH_ALL step launches, in order.
 const char* step_kernel_names();
+// Raises (never lowers) the event kernels' dynamic shared-memory limit on the
+// current device to at least `bytes`.
 cudaError_t set_step_smem_limits(size_t bytes);
 // CTAs of the decision kernel (chunk of 2, 4 or 8 cells) that the current
 // device holds at once.

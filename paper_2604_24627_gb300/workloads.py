@@ -5,9 +5,11 @@ fields and option values, none of the method's arithmetic, and serves both the
 CUDA path and the oracle.
 
 Constants chosen here (time steps, macroparticle weights) were derived once
-from the paper's rates and are stated in the design notes; each dt makes the
-per-step probabilities small (about 1e-2 at the median equilibrium axion
-energy).
+from the paper's rates: each dt makes the total absorption depth of the
+median Maxwell-Boltzmann equilibrium axion (x = E/T = 2.674) over one step
+equal to 1e-2, so per-step probabilities stay small; the axion weight is
+w_a_over_w_gamma times a Planck photon weight that the caller picks
+(photon_weight below).
 """
 from dataclasses import dataclass, field
 
