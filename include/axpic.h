@@ -120,15 +120,21 @@ typedef struct {
                                warp per cell); 0: default 128 */
   int32_t decide_chunk;     /* cells per chunk of a decision warp: 2, 4 or 8;
                                0: default 8 (launch shape, see axpic_autotune) */
-  int32_t rate_model;       /* 0: closed forms (default); 1: exact FP32 table;
-                               2: surrogate network (axpic_set_surrogate) with
-                               the table where it is not trusted. Models 1 and
-                               2 take the full decisions' Primakoff and
-                               absorption rates and the emission energies from
-                               per-cell spectral records; they need one ion
-                               species with Z in {1, 2}, Debye screening and
-                               ions as Primakoff targets. Not part of the
-                               paper's method. */
+  int32_t rate_model;       /* 0: closed forms (default); 1: exact FP32 table:
+                               the full decisions' Primakoff and absorption
+                               rates and the emission energies from per-cell
+                               spectral records interpolated from the table;
+                               2: surrogate network (axpic_set_surrogate):
+                               where it is trusted its per-cell emissivity
+                               constants set the prefactors of every rate's
+                               closed functional form (emission, absorption,
+                               Primakoff both ways) and its quantiles the
+                               emission energies, evaluated by the feedback
+                               kernel after each temperature update; the
+                               table's records elsewhere. Models 1 and 2 need
+                               one ion species with Z in {1, 2}, Debye
+                               screening and ions as Primakoff targets. Not
+                               part of the paper's method. */
   int32_t sr_table_nkt;     /* table nodes in ln(kappa/T) (0: 128) */
   int32_t sr_table_nne;     /* table nodes in log10 n_e (0: 64) */
   int32_t step_branches;    /* axpic_run_steps: the cells run as 1, 2, 4 or
@@ -414,10 +420,11 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc *desc, const axpic_param
  * (for the remainder): the decision, event and feedback kernels, with the
  * step index read from device counters that the feedback kernels advance.
  * Inside a graph the cells run as step_branches independent ranges on forked
- * streams, each range with its own counter, joined at the graph's end. The
- * graphs are captured on first use for a channel mask (on private streams of
- * the context, ordered after the context's stream) and kept until the launch
- * shape changes. Asynchronous; results are identical to nsteps calls of
+ * streams, each range with its own counter, joined at the graph's end. Both
+ * graphs are captured on the first call for a channel mask, whatever its
+ * nsteps (on private streams of the context, ordered after the context's
+ * stream), so later calls launch without capturing; they are kept until the
+ * launch shape changes. Asynchronous; results are identical to nsteps calls of
  * axpic_step. AXPIC_E_INVALID for
  * nsteps < 0, a step range outside [0, 2^32 - 1) or unknown channel bits.
  * Not part of the paper's method: batching of many small boxes in one
@@ -475,7 +482,9 @@ const char *axpic_step_kernel_names(const axpic_ctx *ctx);
  * f = (ln x, ln(kappa/T), log10 n_e, Z) of axpic_surrogate_features is
  *   y_o = shape_o(x, kappa/T) + mu_o + sum_{i=1..3} S_oi f_i + sigma_o z_o,
  * z the network's output at the cell features (0, f_1, f_2, f_3): shape_o
- * carries every x-dependence, so the learned part is a function of the cell.
+ * carries every x-dependence, so the learned part is a function of the cell,
+ * and a cell's three ln-emissivity constants c_o = y_o - shape_o (o = 0, 32,
+ * 64) are all the step needs from the network for its rates.
  * S is an FP32 linear map (axpic_mlp_set_skip; its column i = 0 multiplies
  * zero) and shape_o is fixed: for the ln-emissivity outputs (o = 0, 32, 64)
  * the channel's exact x-dependence at fixed cell,
@@ -513,7 +522,8 @@ axpic_status axpic_mlp_destroy(axpic_mlp *m);
 const char *axpic_mlp_last_error(const axpic_mlp *m);
 
 /* Output normalisation of the network (mu, sigma of the model above), 96
- * floats each; set by axpic_surrogate_fit. sigma must be > 0. */
+ * floats each; set by axpic_surrogate_fit. sigma must be >= 0 (0: the
+ * output is the constant mu). */
 axpic_status axpic_mlp_set_norm(axpic_mlp *m, const float *mu, const float *sigma);
 axpic_status axpic_mlp_get_norm(axpic_mlp *m, float *mu, float *sigma);
 /* The linear map S of the model above, 96 x 4 floats, S[o][i] at o * 4 + i
@@ -542,35 +552,61 @@ axpic_status axpic_surrogate_features(const double *in, int32_t n, float *out);
  * log-uniform x each (the learned part does not depend on x: 1 suffices),
  * targets from axpic_surrogate_targets. mu and S by least squares, sigma
  * the residual spread (floors 1e-4 on rates, 1e-5 on quantiles; rates
- * weighted 16 in the loss) set on the handle; `steps` Adam steps on
+ * weighted 16 in the loss) set on the handle; the Compton-like and
+ * bremsstrahlung quantiles, which do not depend on the cell, are the exact
+ * knots in mu with sigma and S zero. The weight gradients are summed in a
+ * fixed order, so a fit is reproducible bit for bit. `steps` Adam steps on
  * consecutive batches of `batch` rows with a cosine learning rate from lr to
  * lr / 100. *loss_out (may be NULL): final loss on the whole set
  * (normalised units). Synchronises. */
 axpic_status axpic_surrogate_fit(axpic_mlp *m, int32_t ncells, int32_t x_per_cell, int32_t steps, int32_t batch,
                                  float lr, uint64_t seed, double brems_shape, double *loss_out);
-/* Error of the trained network on a grid of nT temperatures (uniform in
+/* Error of the trained network on a grid of nT temperatures (log-uniform in
  * [0.5, 10] keV) x nne densities (log-uniform in [1e23, 1e26]) x Z in {1, 2}
- * (node (Z-1, j, i) at index ((Z-1) nne + j) nT + i), each at 32 x values
- * log-spaced on [0.05, 20]: err_out[2 node] = largest |ln(dQ/dx) error| over
- * x and channels (the relative rate error), err_out[2 node + 1] = largest
- * relative quantile error. Synchronises. */
+ * (node (Z-1, j, i) at index ((Z-1) nne + j) nT + i; nT, nne in [2, 4096]),
+ * each at 8 x values log-spaced on [0.05, 20] (the learned part depends on
+ * the cell alone): err_out[3 node] = largest
+ * |ln(dQ/dx) error| over x and channels (the relative rate error),
+ * err_out[3 node + 1] = largest relative error of the Compton-like and
+ * bremsstrahlung quantiles (those the step samples emission energies from),
+ * err_out[3 node + 2] = that of the Primakoff quantiles (which the step does
+ * not use: gamma->a products inherit the photon's momentum). Synchronises. */
 axpic_status axpic_surrogate_validate(axpic_mlp *m, int32_t nT, int32_t nne, double brems_shape, float *err_out);
 
 /* Gives a context with rate_model 2 its network: the parameters, output
- * normalisation and a trust map from axpic_surrogate_validate's err_out
- * (nT x nne x 2 nodes): a cell uses the network where the four nodes around
- * its (T, n_e) at its Z have a rate error <= tol, the table elsewhere (the
- * error between nodes can exceed the nodes': a tol below the bound wanted
- * leaves a margin). Copies everything (the network may be destroyed
- * afterwards) and rebuilds the spectral records: the network kernel writes
- * the trusted cells (one tensor-core row per cell), the table kernel the
- * others. Synchronises. AXPIC_E_INVALID for another rate model or grid sizes
- * below 2. */
+ * model and a trust map from axpic_surrogate_validate's err_out (nT x nne x
+ * 2 nodes, 3 floats each): a cell uses the network where the four nodes
+ * around its (T, n_e) at its Z have a rate error <= tol_rate and a sampled-
+ * quantile error <= tol_quantile, the table elsewhere (the error between
+ * nodes can exceed the nodes': a finer grid and tolerances below the bound
+ * wanted leave a margin). Copies everything (the network may be destroyed
+ * afterwards) and rebuilds the cells' records: trusted cells get the
+ * network's prefactors (one tensor-core row per cell), the others the
+ * table's spectral record. Synchronises. AXPIC_E_INVALID for another rate
+ * model, grid sizes outside [2, 4096], negative tolerances, or a network
+ * whose Compton-like or bremsstrahlung quantiles depend on the cell. */
 axpic_status axpic_set_surrogate(axpic_ctx *ctx, axpic_mlp *m, const float *err_map, int32_t nT, int32_t nne,
-                                 float tol);
-/* The spectral records of cells [first, first + count) (rate models 1 and 2):
- * 192 floats per cell to out (host): ln(dQ_c/dx) at unit coupling on x_k =
- * 0.05 400^(k/31) (c * 32 + k; c = Primakoff, Compton-like, brems), the
+                                 float tol_rate, float tol_quantile);
+/* The cell records of cells [first, first + count), AXPIC_REC_LEN floats per
+ * cell to rec_out (host), and (src_out: host, may be NULL) one byte per cell:
+ * 1 where the cell's rates come from its spectral record (rate model 1; rate
+ * model 2 where the network is not trusted), 0 otherwise. Record slots:
+ * [0] T [keV], [1] 1/T, [2] 4/kappa^2, [3] lambda_C/w_e and [4] lambda_B/w_e
+ * (emission Poisson means per unit electron weight), [5] and [6] the
+ * Compton-like and bremsstrahlung absorption prefactors (tau_C = [5] x^2
+ * e^x/(e^x - 1) and tau_B = [6] x^(a-3) for Maxwell-Boltzmann targets),
+ * [7] Gamma_0 dt of gamma->a (Gamma dt = [7] F(s)), [8] m [7] as the
+ * composition gives it, [9] n_e and [10] n_eff (1e24 cm^-3), [11] rho
+ * [g cm^-3], [12] X_H, [13] the Primakoff target sum (1e24 cm^-3).
+ * Synchronises. */
+#define AXPIC_REC_LEN 16
+axpic_status axpic_get_cell_records(axpic_ctx *ctx, int32_t first, int32_t count, float *rec_out,
+                                    uint8_t *src_out);
+/* The spectral records of cells [first, first + count) (rate models 1 and 2;
+ * under model 2 only the cells the network is not trusted for have one, see
+ * axpic_get_cell_records): 192 floats per cell to out (host): ln(dQ_c/dx) +
+ * x_k at unit coupling on x_k = 0.05 e^((k - 1) h), h = ln(400) / 29,
+ * k = 0..31 (c * 32 + k; c = Primakoff, Compton-like, brems), the
  * quantiles x(j/32) (96 + c * 31 + j - 1), then ln(g_agg^2 dt pi^2 (hbar c)^3
  * / (T^4 keV)), ln(g_ae^2 dt 2 pi^2 (hbar c)^3 / (T^4 keV)) and T.
  * Synchronises. */

@@ -310,12 +310,13 @@ def absorb_cell(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTa
         parts["g"] = parts["g"].concat(new_g)
 
 
-def _emit(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, n_g0=None, rec=None):
+def _emit(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, n_g0=None, rec=None, qrec=None):
     """Forward operators: Primakoff on photons present at step start, then
     thermal-bath emission on electrons. With a spectral record the Primakoff
-    rate (x in [0.05, 20]) and the emitted energies come from it. Returns the
-    photons with their remaining weights, which of them stay, and the new
-    axions."""
+    rate (x in [0.05, 20]) and the emitted energies come from it; qrec (a
+    record whose quantiles the energies come from, when rec is None) serves
+    the surrogate model's network cells. Returns the photons with their
+    remaining weights, which of them stay, and the new axions."""
     if n_g0 is None:
         n_g0 = len(parts["g"])
     g = parts["g"]
@@ -373,11 +374,12 @@ def _emit(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, n
             sub = np.concatenate([np.arange(k) for k in Kc])
             uu = event_uniforms(p, step, cell, STREAM_EV_E, parent, sub)
             is_c = f32(uu[:, 3]) < frac_c[parent]
-            if rec is None:
+            qr = rec if rec is not None else qrec
+            if qr is None:
                 xE = np.where(is_c, spectra.compton_icdf(uu[:, 2]),
                               spectra.brems_icdf(p.brems_gamma_shape, uu[:, 2]))
             else:
-                xE = np.where(is_c, surrogate.rec_sample_x(rec, 1, uu[:, 2]), surrogate.rec_sample_x(rec, 2, uu[:, 2]))
+                xE = np.where(is_c, surrogate.rec_sample_x(qr, 1, uu[:, 2]), surrogate.rec_sample_x(qr, 2, uu[:, 2]))
             E = xE * cs.T_keV
             dx, dy, dz = isotropic(uu[:, 0], uu[:, 1])
             pm = E / K.ME_C2_KEV
@@ -477,17 +479,25 @@ class CellInput:
     A: np.ndarray
 
 
-def step_cell(ci: CellInput, parts, p: Params, step, cell, mask, res_E=0.0, res_P=None, feedback=True, rec=None):
+def step_cell(ci: CellInput, parts, p: Params, step, cell, mask, res_E=0.0, res_P=None, feedback=True, rec=None,
+              net=None):
     """absorb -> emit -> feedback for one cell; returns (tally, feedback result).
     The axions made in the emit phase reuse the axion slots freed in the
-    absorb phase (recycle). rec: the cell's spectral record (table or
-    surrogate rate model) or None."""
+    absorb phase (recycle). rec: the cell's spectral record (table rate model,
+    or the surrogate model where the network is not trusted) or None. net:
+    (c, qrec) for a cell the surrogate network is trusted for: its three
+    ln-emissivity constants (surrogate.network_cell_state) and a record
+    holding the network's quantiles the energies come from."""
     cs = cell_state(ci.T_keV, ci.n_ion, ci.Z, ci.A, p)
+    qrec = None
+    if net is not None:
+        cs = surrogate.network_cell_state(cs, net[0], p)
+        qrec = net[1]
     tally = StepTally()
     a2, keep_a, new_g = _absorb(cs, parts, p, step, cell, mask, tally, rec)
     if len(new_g):
         parts["g"] = parts["g"].concat(new_g)
-    g2, keep_g, new_a = _emit(cs, parts, p, step, cell, mask, tally, n_g0=tally.n_g0, rec=rec)
+    g2, keep_g, new_a = _emit(cs, parts, p, step, cell, mask, tally, n_g0=tally.n_g0, rec=rec, qrec=qrec)
     parts["g"] = g2.take(tail_fill(keep_g))
     parts["a"] = recycle(a2, keep_a, new_a)
     fb = None

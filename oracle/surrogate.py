@@ -182,6 +182,48 @@ def targets(x, kT, ne, Z, brems_shape=1.70):
     return y
 
 
+def universal_output(o):
+    """Whether output o does not depend on the cell: the Compton-like and
+    bremsstrahlung quantiles (their number spectra in x are the same in every
+    cell), o = 33..63 and 65..95."""
+    return o > 32 and o % 32 != 0
+
+
+def cell_constants(z, X, mu, sigma, skip, brems_shape=1.70):
+    """A cell's three ln-emissivity constants c_c = y_c - shape_c (c = Primakoff,
+    Compton-like, bremsstrahlung; outputs 0, 32, 64 of model_output), x-
+    independent by construction of the model."""
+    y = model_output(z, X, mu, sigma, skip, brems_shape)
+    sh = shape(X, brems_shape)
+    return (y - sh)[:, [0, 32, 64]]
+
+
+def network_cell_state(cs, c, p):
+    """The cell's rate parameters under the surrogate rate model where the
+    network is trusted: every channel keeps its closed functional form and the
+    network's constants c = (c_P, c_C, c_B) (ln-emissivity at unit coupling
+    minus the exact x-shape) set the prefactors:
+    * Primakoff (Eq. prim_rate with Planck photons): dQ_P/dx = Gamma_0 T^4 keV
+      x^3 F(s) / (pi^2 (hbar c)^3 (e^x - 1)), so Gamma_0 = g^2 e^c_P pi^2
+      (hbar c)^3 / (T^4 keV);
+    * Compton-like: dQ_C/dx = Q_C x^5 / (e^x - 1) / (Gamma(6) zeta(6)), so Q_C =
+      g_ae^2 e^c_C Gamma(6) zeta(6);
+    * bremsstrahlung: Q_B = g_ae^2 e^c_B Gamma(a + 1);
+    and Gamma_C, Gamma_B = Q / (n_e <E>) as in Eqs. GammaC and the text after
+    eps_ee (the absorption rates follow from them, Eq. gamma_abs)."""
+    import copy
+    out = copy.copy(cs)
+    a = p.brems_gamma_shape
+    T = cs.T_keV
+    out.Gamma0_P = (p.g_agg_GeV_inv ** 2 * math.exp(c[0]) * math.pi ** 2 * K.HBARC_KEV_CM ** 3
+                    / (T ** 4 * K.KEV_ERG))
+    out.Q_C = p.g_ae ** 2 * math.exp(c[1]) * math.gamma(6.0) * special.zeta(6.0)
+    out.Q_B = p.g_ae ** 2 * math.exp(c[2]) * math.gamma(a + 1.0)
+    out.Gamma_C = out.Q_C / (cs.n_e * spectra.compton_mean_x() * T * K.KEV_ERG) if cs.n_e > 0 else 0.0
+    out.Gamma_B = out.Q_B / (cs.n_e * a * T * K.KEV_ERG) if cs.n_e > 0 else 0.0
+    return out
+
+
 def in_domain(kT, ne, Z):
     T = temperature(kT, ne, Z)
     return T_LO <= T <= T_HI and NE_LO <= ne <= NE_HI
@@ -267,11 +309,26 @@ def adam(P, G, M, V, t, lr, b1=0.9, b2=0.999, eps=1e-8):
 # ln(g_ae^2 dt 2 pi^2 (hbar c)^3 / (T^4 keV)) and T. The table holds the
 # targets at nodes uniform in ln(kappa/T) on [ln 0.012, ln 41] and in
 # log10 n_e on [23, 26], for Z = 1 and 2, stored in binary32; a cell's record
-# is bilinear in (ln kappa/T, log10 n_e) at its Z.
+# is bilinear in (ln kappa/T, log10 n_e) at its Z. The bremsstrahlung row is
+# tabulated with the fit's brackets divided out (ln_brackets below) and a
+# cell's record adds them back for its own eta: the brackets' 1e-3 floor puts
+# a kink into ln Q_B, which bilinear interpolation across it would smear.
 
 SR_LEN = 192
 GRID_H = math.log(X_HI / X_LO) / 29.0
 X_GRID = np.exp(np.log(X_LO) + GRID_H * (np.arange(32) - 1.0))
+
+
+def ln_brackets(eta, Z):
+    """ln of the bremsstrahlung fit's brackets (Eqs. eps_eZ, eps_ee), each
+    floored at 1e-3 and weighted as in Q_B, normalised to 1 at eta = 0:
+    ln((b_eZ + c b_ee) / (1 + c)), c = (1 + X_H) / (2 sqrt 2), X_H = 1 for
+    hydrogen (Z = 1), 0 for helium."""
+    XH = 1.0 if Z == 1 else 0.0
+    c = (1.0 + XH) / (2.0 * math.sqrt(2.0))
+    bz = max(1e-3, 1.0 - 6.98e-2 * eta)
+    be = max(1e-3, 1.0 - 0.140 * eta)
+    return math.log((bz + c * be) / (1.0 + c))
 
 
 def build_table(nkt, nne, brems_shape=1.70):
@@ -283,8 +340,10 @@ def build_table(nkt, nne, brems_shape=1.70):
                 ne = 10.0 ** (23.0 + 3.0 * j / (nne - 1))
                 Z = z + 1
                 T = temperature(kT, ne, Z)
+                lnbr = ln_brackets(cell(T, ne, Z, brems_shape)[0].eta, Z)
                 for c, ch in enumerate(CHANNELS):
-                    tab[z, j, i, 32 * c:32 * c + 32] = np.log(emissivity(ch, X_GRID, T, ne, Z, brems_shape)) + X_GRID
+                    tab[z, j, i, 32 * c:32 * c + 32] = (np.log(emissivity(ch, X_GRID, T, ne, Z, brems_shape)) + X_GRID
+                                                        - (lnbr if ch == "brems" else 0.0))
                     tab[z, j, i, 96 + 31 * c:96 + 31 * c + 31] = quantiles(ch, T, ne, Z, brems_shape)
     return tab
 
@@ -302,6 +361,7 @@ def table_record(tab, T, kappa, ne, Z, g_agg, g_ae, dt):
     t = tab[int(Z) - 1].astype(np.float64)
     rec = np.empty(SR_LEN)
     rec[:189] = ((1 - fv) * ((1 - fu) * t[j, i] + fu * t[j, i + 1]) + fv * ((1 - fu) * t[j + 1, i] + fu * t[j + 1, i + 1]))
+    rec[64:96] += ln_brackets(cell(T, ne, Z)[0].eta, Z)
     hc3 = K.HBARC_KEV_CM ** 3
     rec[189] = math.log(g_agg ** 2 * dt * math.pi ** 2 * hc3 / K.KEV_ERG) - 4.0 * math.log(T)
     rec[190] = math.log(g_ae ** 2 * dt * 2.0 * math.pi ** 2 * hc3 / K.KEV_ERG) - 4.0 * math.log(T)

@@ -76,7 +76,9 @@ EXPORTS = {
                                             ctypes.c_float, ctypes.POINTER(ctypes.c_double)]),
     "axpic_mlp_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "axpic_set_surrogate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
-                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_float]),
+                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float]),
+    "axpic_get_cell_records": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),
     "axpic_get_spectral_records": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                                   ctypes.POINTER(ctypes.c_float)]),
     "axpic_mlp_set_norm": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
@@ -418,19 +420,31 @@ def axpic_surrogate_fit(h, ncells, x_per_cell, steps, batch, lr, seed=0, brems_s
 
 
 def axpic_surrogate_validate(h, nT, nne, brems_shape=1.70):
-    """(2, nne, nT) arrays: largest ln-rate error and largest relative
-    quantile error per grid node, indexed [Z - 1, j, i]."""
+    """(2, nne, nT, 3) array per grid node, indexed [Z - 1, j, i]: largest
+    ln-rate error, largest relative error of the Compton-like and
+    bremsstrahlung quantiles, and of the Primakoff quantiles."""
     import numpy as np
-    out = np.empty(nT * nne * 2 * 2, dtype=np.float32)
+    out = np.empty(nT * nne * 2 * 3, dtype=np.float32)
     _mlp_check(h, lib().axpic_surrogate_validate(h, nT, nne, brems_shape, _fptr(out)))
-    out = out.reshape(2, nne, nT, 2)
-    return out[..., 0], out[..., 1]
+    return out.reshape(2, nne, nT, 3)
 
 
-def axpic_set_surrogate(ctx, net_handle, err_map, nT, nne, tol):
+def axpic_set_surrogate(ctx, net_handle, err_map, nT, nne, tol_rate, tol_quantile=1e-3):
+    """err_map: axpic_surrogate_validate's array for the same (nT, nne)."""
     import numpy as np
-    e = np.ascontiguousarray(err_map, dtype=np.float32)
-    _check(ctx, lib().axpic_set_surrogate(ctx, net_handle, _fptr(e), nT, nne, tol))
+    e = np.ascontiguousarray(err_map, dtype=np.float32).reshape(-1)
+    assert e.size == 2 * nT * nne * 3
+    _check(ctx, lib().axpic_set_surrogate(ctx, net_handle, _fptr(e), nT, nne, tol_rate, tol_quantile))
+
+
+def axpic_get_cell_records(ctx, first, count):
+    """(records [count, 16] float32, sources [count] uint8: 1 = the cell's
+    rates come from its spectral record)."""
+    import numpy as np
+    rec = np.empty((max(count, 1), 16), dtype=np.float32)
+    src = np.empty(max(count, 1), dtype=np.uint8)
+    _check(ctx, lib().axpic_get_cell_records(ctx, first, count, _fptr(rec), src.ctypes.data_as(ctypes.c_void_p)))
+    return rec[:count], src[:count]
 
 
 def axpic_stream_axions(ctx, dims, h_cm, dt_s, boundary, mass_keV=0.0):

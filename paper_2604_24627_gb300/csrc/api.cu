@@ -106,7 +106,9 @@ struct axpic_ctx {
   float* sur_sigma = nullptr;
   float* sur_skip = nullptr;
   uint8_t* sur_trust = nullptr;
-  uint8_t* sr_net = nullptr;  // [ncells]: 1 where the network kernel wrote the record
+  uint8_t* sr_src = nullptr;       // [ncells] rate model 2: 1 = table record, 0 = network prefactors
+  float* sur_uni = nullptr;        // [kSrLen] the network's cell-independent quantiles
+  unsigned char* sur_img = nullptr;  // the network laid out for the fused kernels
   // axion streaming scratch, made by the first axpic_stream_axions call
   uint8_t* st_dir = nullptr;  // [ncells * axion capacity]
   int32_t* st_cnt = nullptr;  // [ncells * 27 * 2]: counts, then group offsets
@@ -115,9 +117,8 @@ struct axpic_ctx {
   // axion merging scratch, made by the first axpic_merge_axions call
   uint8_t* mg_grp = nullptr;  // [ncells * axion capacity]
   double* mg_removed = nullptr;
-  void* sur_W16 = nullptr;  // layers 2 and 3 laid out for the tensor cores
   int sr_nkt = 0, sr_nne = 0, tnT = 0, tnne = 0, sur_set = 0, sur_any_trusted = 0;
-  float ln_gP = 0.f, ln_gA = 0.f;
+  float ln_gP = 0.f, ln_gA = 0.f, lnK_CC = 0.f, lnK_CB = 0.f;
   int64_t last_absorb_step = -1;
   std::string last_error;
   std::vector<cudaEvent_t> prof_events;  // 5 per recorded step, created by axpic_profile_begin
@@ -238,6 +239,33 @@ static void fold_constants(axpic_ctx* ctx) {
 }
 
 
+// The rate models' records and network, as the kernels see them.
+static RecordArgs make_record_args(axpic_ctx* ctx) {
+  RecordArgs a;
+  std::memset(&a, 0, sizeof(a));
+  if (!ctx->prm.rate_model) return a;
+  a.sr = ctx->sr;
+  a.tab = ctx->srtab;
+  a.nkt = ctx->sr_nkt;
+  a.nne = ctx->sr_nne;
+  a.Z = ctx->desc.nspecies > 0 ? (float)ctx->desc.Z[0] : 1.f;
+  a.ln_gP = ctx->ln_gP;
+  a.ln_gA = ctx->ln_gA;
+  a.lnK_CC = ctx->lnK_CC;
+  a.lnK_CB = ctx->lnK_CB;
+  // the e-e term's weight (1 + X_H) / (2 sqrt 2) of the single ion species
+  a.bee_c = (float)((a.Z == 1.f ? 2.0 : 1.0) / (2.0 * std::sqrt(2.0)));
+  a.k_T7 = ctx->cc.k_T7;
+  // no trusted node: the network is never evaluated (every cell keeps the table)
+  a.trust = ctx->sur_set && ctx->sur_any_trusted ? ctx->sur_trust : nullptr;
+  a.tnT = ctx->tnT;
+  a.tnne = ctx->tnne;
+  a.img = ctx->sur_img;
+  a.src = ctx->sr_src;
+  a.uni = ctx->sur_uni;
+  return a;
+}
+
 static StepArgs make_args(axpic_ctx* ctx, int64_t step, int mask) {
   const axpic_params& p = ctx->prm;
   StepArgs A;
@@ -301,7 +329,7 @@ static StepArgs make_args(axpic_ctx* ctx, int64_t step, int mask) {
   A.ctr_rows = ctx->ctr_rows;
   A.step_dev = nullptr;
   A.rate_model = ctx->prm.rate_model;
-  A.sr = ctx->sr;
+  A.ra = make_record_args(ctx);
   A.guard_margin = ctx->prm.rate_model ? 1.05f : 1.0f;
   A.cc = ctx->cc;
   return A;
@@ -313,35 +341,18 @@ static SrArgs make_sr_args(axpic_ctx* ctx) {
   a.ncells = ctx->desc.ncells;
   a.cell0 = 0;
   a.rec = ctx->rec;
-  a.sr = ctx->sr;
-  a.tab = ctx->srtab;
-  a.nkt = ctx->sr_nkt;
-  a.nne = ctx->sr_nne;
-  a.Z = ctx->desc.nspecies > 0 ? (float)ctx->desc.Z[0] : 1.f;
-  a.ln_gP = ctx->ln_gP;
-  a.ln_gA = ctx->ln_gA;
-  a.P = ctx->sur_P;
-  a.mu = ctx->sur_mu;
-  a.sigma = ctx->sur_sigma;
-  a.skip = ctx->sur_skip;
-  a.brems_a = (float)ctx->prm.brems_gamma_shape;
-  // no trusted node: the network is never evaluated (every cell keeps the table)
-  a.trust = ctx->sur_set && ctx->sur_any_trusted ? ctx->sur_trust : nullptr;
-  a.W16 = ctx->sur_W16;
-  a.net = ctx->sr_net;
-  a.tnT = ctx->tnT;
-  a.tnne = ctx->tnne;
+  a.ra = make_record_args(ctx);
   a.err = ctx->err;
   return a;
 }
 
-// Rebuilds every cell's spectral record for its current T: once a network is
-// trusted somewhere, the fused network kernel writes the cells where it is
-// trusted and flags them; the table kernel then writes the rest (its CTAs
-// whose 32 cells are all flagged exit at once).
+// Rebuilds every cell's rate-model record for its current T and composition
+// (the cell records' closed-form slots must be current): the table model's
+// spectral records; under the surrogate model the network's prefactors
+// where it is trusted and the table's records elsewhere.
 static cudaError_t build_records(axpic_ctx* ctx, cudaStream_t st) {
   if (!ctx->prm.rate_model) return cudaSuccess;
-  return launch_sr_records(make_sr_args(ctx), st);
+  return launch_sr_records(ctx->prm.rate_model, make_sr_args(ctx), st);
 }
 
 static void free_events(axpic_ctx* ctx) {
@@ -370,8 +381,8 @@ static void free_ctx(axpic_ctx* ctx) {
   void* bufs[] = {ctx->rec,    ctx->mom,   ctx->xbuf,     ctx->res, ctx->diag,    ctx->photon_start,
                   ctx->tables, ctx->tally, ctx->counters, ctx->err, ctx->scratch, ctx->bits,
                   ctx->recA,   ctx->recG,  ctx->recE,     ctx->step_dev, ctx->sr, ctx->srtab,
-                  ctx->sur_P,  ctx->sur_mu, ctx->sur_sigma, ctx->sur_trust, ctx->sur_W16, ctx->sur_skip,
-                  ctx->sr_net, ctx->st_dir, ctx->st_cnt, ctx->st_buf, ctx->st_stats, ctx->mg_grp,
+                  ctx->sur_P,  ctx->sur_mu, ctx->sur_sigma, ctx->sur_trust, ctx->sur_img, ctx->sur_skip,
+                  ctx->sr_src, ctx->sur_uni, ctx->st_dir, ctx->st_cnt, ctx->st_buf, ctx->st_stats, ctx->mg_grp,
                   ctx->mg_removed};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -456,6 +467,14 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
     const double gcm = p.g_agg_GeV_inv;  // the records are at g_agg = 1 GeV^-1
     ctx->ln_gP = (float)std::log(gcm * gcm * p.dt_phys_s * kPi * kPi * hc3 / kKeVerg);
     ctx->ln_gA = (float)std::log(p.g_ae * p.g_ae * p.dt_phys_s * 2.0 * kPi * kPi * hc3 / kKeVerg);
+    // the network's emission rates per unit electron weight: lambda / w_e =
+    // Q dt / (n_e <E> w_a) with Q_C = g_ae^2 e^c_C Gamma(6) zeta(6), <E>_C =
+    // 5 zeta(6) / zeta(5) T, Q_B = g_ae^2 e^c_B Gamma(a + 1), <E>_B = a T (the
+    // cell divides by n_e / 1e24 and T)
+    const double wa32 = (double)(float)p.w_a, a = p.brems_gamma_shape, z6 = zeta(6.0), z5 = zeta(5.0);
+    const double gae2 = p.g_ae * p.g_ae;
+    ctx->lnK_CC = (float)std::log(gae2 * 120.0 * z6 * p.dt_phys_s / (wa32 * (5.0 * z6 / z5) * kKeVerg * 1e24));
+    ctx->lnK_CB = (float)std::log(gae2 * std::tgamma(a + 1.0) * p.dt_phys_s / (wa32 * a * kKeVerg * 1e24));
   }
   ctx->dec_chunk = p.decide_chunk ? p.decide_chunk : kDefaultDecChunk;
   ctx->branches = p.step_branches                    ? p.step_branches
@@ -486,13 +505,16 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
   ALLOC(ctx->step_dev, sizeof(uint32_t) * kMaxBranches);
   if (p.rate_model) {
     ALLOC(ctx->sr, sizeof(float) * kSrLen * (size_t)n);
-    ALLOC(ctx->sr_net, (size_t)n);
     ALLOC(ctx->srtab, sizeof(float) * kSrTabOut * 2 * (size_t)ctx->sr_nkt * ctx->sr_nne);
+  }
+  if (p.rate_model == 2) {
+    ALLOC(ctx->sr_src, (size_t)n);
     ALLOC(ctx->sur_P, sizeof(float) * AXPIC_MLP_PARAMS);
     ALLOC(ctx->sur_mu, sizeof(float) * 96);
     ALLOC(ctx->sur_sigma, sizeof(float) * 96);
     ALLOC(ctx->sur_skip, sizeof(float) * 96 * 4);
-    ALLOC(ctx->sur_W16, kSrW16Bytes);
+    ALLOC(ctx->sur_uni, sizeof(float) * kSrLen);
+    ALLOC(ctx->sur_img, kNetImgBytes);
   }
   ALLOC(ctx->err, sizeof(int));
   ALLOC(ctx->scratch, sizeof(double) * (8 + kNumCounters + (size_t)kInfoChunk * AXPIC_CELL_INFO_LEN));
@@ -675,6 +697,8 @@ static axpic_status read_err(axpic_ctx* ctx) {
   CK(cudaStreamSynchronize(ctx->stream), "synchronize");
   if (h & ERR_CAPACITY) return fail(ctx, AXPIC_E_CAPACITY, "a slab capacity was exceeded; products were dropped");
   if (h & ERR_NUMERIC) return fail(ctx, AXPIC_E_NUMERIC, "a non-finite or non-positive temperature was found");
+  if (h & ERR_TIMEOUT)
+    return fail(ctx, AXPIC_E_TIMEOUT, "a tensor-core wait of the surrogate network ran out (its cells kept the table)");
   return AXPIC_OK;
 }
 
@@ -738,8 +762,8 @@ axpic_status axpic_eval_rates(axpic_ctx* ctx, int32_t cell, const float* E_keV, 
   if (!ctx) return AXPIC_E_INVALID;
   if (cell < 0 || cell >= ctx->desc.ncells || n < 0 || (n > 0 && (!E_keV || !out)))
     return fail(ctx, AXPIC_E_INVALID, "axpic_eval_rates: bad cell, count or pointer");
-  CK(launch_rates(ctx->rec, cell, E_keV, n, ctx->prm.eq_stats, (float)(ctx->prm.brems_gamma_shape - 3.0), out,
-                  ctx->stream),
+  CK(launch_rates(ctx->rec, cell, E_keV, n, ctx->prm.eq_stats, (float)(ctx->prm.brems_gamma_shape - 3.0),
+                  ctx->cc.prim_mult, out, ctx->stream),
      "rates");
   return AXPIC_OK;
 }
@@ -914,10 +938,12 @@ axpic_status axpic_run_steps(axpic_ctx* ctx, int64_t first_step, int32_t nsteps,
   // ordered after the work already queued on the context's stream
   CK(cudaEventRecord(ctx->graph_ev[0], ctx->stream), "event record");
   CK(cudaStreamWaitEvent(gs, ctx->graph_ev[0], 0), "stream wait");
+  // both graphs (32 steps and one) are captured on the first call for a mask,
+  // so that later calls of any length launch without capturing
   cudaGraphExec_t many = nullptr, one = nullptr;
   axpic_status st;
-  if (nsteps >= kGraphSteps && (st = step_graph(ctx, first_step, kGraphSteps, channel_mask, &many))) return st;
-  if (nsteps % kGraphSteps && (st = step_graph(ctx, first_step, 1, channel_mask, &one))) return st;
+  if ((st = step_graph(ctx, first_step, kGraphSteps, channel_mask, &many))) return st;
+  if ((st = step_graph(ctx, first_step, 1, channel_mask, &one))) return st;
   CK(launch_set_step(ctx->step_dev, (uint32_t)first_step, kMaxBranches, gs), "set step");
   for (int32_t k = 0; k < nsteps / kGraphSteps; ++k) CK(cudaGraphLaunch(many, gs), "graph launch");
   for (int32_t k = 0; k < nsteps % kGraphSteps; ++k) CK(cudaGraphLaunch(one, gs), "graph launch");
@@ -958,8 +984,8 @@ axpic_status axpic_run_steps_streamed(axpic_ctx* ctx, int64_t first_step, int32_
   CK(cudaEventRecord(ctx->graph_ev[0], ctx->stream), "event record");
   CK(cudaStreamWaitEvent(gs, ctx->graph_ev[0], 0), "stream wait");
   cudaGraphExec_t many = nullptr, one = nullptr;
-  if (nsteps >= kGraphSteps && (st = step_graph(ctx, first_step, kGraphSteps, channel_mask, &many, &sa))) return st;
-  if (nsteps % kGraphSteps && (st = step_graph(ctx, first_step, 1, channel_mask, &one, &sa))) return st;
+  if ((st = step_graph(ctx, first_step, kGraphSteps, channel_mask, &many, &sa))) return st;
+  if ((st = step_graph(ctx, first_step, 1, channel_mask, &one, &sa))) return st;
   CK(launch_set_step(ctx->step_dev, (uint32_t)first_step, kMaxBranches, gs), "set step");
   for (int32_t k = 0; k < nsteps / kGraphSteps; ++k) CK(cudaGraphLaunch(many, gs), "graph launch");
   for (int32_t k = 0; k < nsteps % kGraphSteps; ++k) CK(cudaGraphLaunch(one, gs), "graph launch");
@@ -995,6 +1021,7 @@ static std::vector<std::pair<void*, size_t>> state_buffers(axpic_ctx* ctx, bool 
   b.emplace_back(ctx->err, sizeof(int));
   b.emplace_back(ctx->bits, bit_words * sizeof(uint32_t));
   if (ctx->sr) b.emplace_back(ctx->sr, n * kSrLen * sizeof(float));
+  if (ctx->sr_src) b.emplace_back(ctx->sr_src, n);
   return b;
 }
 
@@ -1097,20 +1124,34 @@ axpic_status axpic_autotune(axpic_ctx* ctx, int64_t step, int32_t trial_steps, i
 }
 
 axpic_status axpic_set_surrogate(axpic_ctx* ctx, axpic_mlp* m, const float* err_map, int32_t nT, int32_t nne,
-                                 float tol) {
+                                 float tol_rate, float tol_quantile) {
   AXPIC_RANGE("axpic_set_surrogate");
   if (!ctx || !m || !err_map) return AXPIC_E_INVALID;
   if (ctx->prm.rate_model != 2) return fail(ctx, AXPIC_E_INVALID, "axpic_set_surrogate: rate_model is not 2");
   if (nT < 2 || nne < 2 || nT > 4096 || nne > 4096) return fail(ctx, AXPIC_E_INVALID, "axpic_set_surrogate: grid");
+  if (!(tol_rate >= 0.f) || !(tol_quantile >= 0.f))
+    return fail(ctx, AXPIC_E_INVALID, "axpic_set_surrogate: tolerances must be >= 0");
   std::vector<float> P(AXPIC_MLP_PARAMS), mu(96), sigma(96), skip(96 * 4);
   axpic_status s;
   if ((s = axpic_mlp_get_params(m, P.data())) != AXPIC_OK || (s = axpic_mlp_get_norm(m, mu.data(), sigma.data())) ||
       (s = axpic_mlp_get_skip(m, skip.data())))
     return fail(ctx, s, "axpic_set_surrogate: reading the network");
+  // the step samples emission energies from the Compton-like and
+  // bremsstrahlung quantiles of the model, which must not depend on the cell
+  std::vector<float> uni(kSrLen, 0.f);
+  for (int ch = 1; ch < 3; ++ch)
+    for (int j = 1; j < 32; ++j) {
+      const int o = 32 * ch + j;
+      if (sigma[o] != 0.f || skip[o * 4 + 1] != 0.f || skip[o * 4 + 2] != 0.f || skip[o * 4 + 3] != 0.f)
+        return fail(ctx, AXPIC_E_INVALID,
+                    "axpic_set_surrogate: the Compton-like and bremsstrahlung quantiles must not depend on the cell "
+                    "(their sigma and S zero, as axpic_surrogate_fit leaves them)");
+      uni[96 + 31 * ch + j - 1] = mu[o];
+    }
   std::vector<uint8_t> trust((size_t)2 * nT * nne);
   int any = 0;
   for (size_t i = 0; i < trust.size(); ++i) {
-    trust[i] = err_map[2 * i] <= tol ? 1 : 0;
+    trust[i] = err_map[3 * i] <= tol_rate && err_map[3 * i + 1] <= tol_quantile ? 1 : 0;
     any |= trust[i];
   }
   cudaStream_t st = ctx->stream;
@@ -1122,16 +1163,38 @@ axpic_status axpic_set_surrogate(axpic_ctx* ctx, axpic_mlp* m, const float* err_
   CK(cudaMemcpyAsync(ctx->sur_mu, mu.data(), sizeof(float) * 96, cudaMemcpyHostToDevice, st), "norm");
   CK(cudaMemcpyAsync(ctx->sur_sigma, sigma.data(), sizeof(float) * 96, cudaMemcpyHostToDevice, st), "norm");
   CK(cudaMemcpyAsync(ctx->sur_skip, skip.data(), sizeof(float) * 96 * 4, cudaMemcpyHostToDevice, st), "skip");
+  CK(cudaMemcpyAsync(ctx->sur_uni, uni.data(), sizeof(float) * kSrLen, cudaMemcpyHostToDevice, st), "quantiles");
   CK(cudaMemcpyAsync(ctx->sur_trust, trust.data(), trust.size(), cudaMemcpyHostToDevice, st), "trust map");
-  CK(launch_sr_weights(ctx->sur_P, ctx->sur_W16, st), "weights");
+  CK(launch_net_image(ctx->sur_P, ctx->sur_mu, ctx->sur_sigma, ctx->sur_skip, ctx->sur_img, st), "network image");
   ctx->tnT = nT;
   ctx->tnne = nne;
   ctx->sur_set = 1;
   ctx->sur_any_trusted = any;
   free_graphs(ctx);
-  CK(build_records(ctx, st), "spectral records");
+  const axpic_plasma_desc& d = ctx->desc;
+  CK(launch_records(d.ncells, d.nspecies, ctx->cc, d.T_keV, d.n_ion, ctx->rec, ctx->err, st), "records");
+  CK(build_records(ctx, st), "rate-model records");
   CK(cudaStreamSynchronize(st), "synchronize");
   return read_err(ctx);
+}
+
+axpic_status axpic_get_cell_records(axpic_ctx* ctx, int32_t first, int32_t count, float* rec_out, uint8_t* src_out) {
+  if (!ctx || first < 0 || count < 0 || first + count > ctx->desc.ncells || (count > 0 && !rec_out))
+    return AXPIC_E_INVALID;
+  if (count == 0) return AXPIC_OK;
+  CK(cudaMemcpyAsync(rec_out, ctx->rec + (size_t)first * kRecLen, sizeof(float) * kRecLen * count,
+                     cudaMemcpyDeviceToHost, ctx->stream),
+     "copy records");
+  if (src_out) {
+    if (ctx->sr_src) {
+      CK(cudaMemcpyAsync(src_out, ctx->sr_src + first, (size_t)count, cudaMemcpyDeviceToHost, ctx->stream),
+         "copy sources");
+    } else {
+      std::memset(src_out, ctx->prm.rate_model == 1 ? 1 : 0, (size_t)count);
+    }
+  }
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  return AXPIC_OK;
 }
 
 // Validates the streaming parameters, makes the scratch on first use and fills

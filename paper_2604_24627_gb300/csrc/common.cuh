@@ -50,8 +50,9 @@ enum {
   R_CB,        // Gamma_B dt / w_a
   R_BC,        // Compton absorption prefactor (tau_C = R_BC x^2 [/(1-e^-x)])
   R_BB,        // bremsstrahlung absorption prefactor (tau_B = R_BB x^(a-3) [(1-e^-x)])
-  R_AP,        // Gamma_0 dt of gamma->a (Gamma dt = R_AP * F(s))   [composition]
-  R_APINV,     // m * R_AP (a->gamma)                              [composition]
+  R_AP,        // Gamma_0 dt of gamma->a (Gamma dt = R_AP * F(s))   [composition; the
+               // surrogate network's, per temperature, where rate model 2 trusts it]
+  R_APINV,     // m * R_AP (a->gamma; the step forms m * R_AP itself) [composition]
   R_NE,        // n_e / 1e24 cm^-3                                  [composition]
   R_NEFF,      // n_eff / 1e24 cm^-3                                [composition]
   R_RHO,       // rho, g cm^-3                                      [composition]
@@ -80,7 +81,7 @@ enum {
 };
 
 // Device error flag bits.
-enum { ERR_CAPACITY = 1, ERR_NUMERIC = 2 };
+enum { ERR_CAPACITY = 1, ERR_NUMERIC = 2, ERR_TIMEOUT = 4 };
 
 // Rows of per-CTA event counters (CTAs share rows beyond this).
 constexpr int kCounterRows = 4096;
@@ -105,6 +106,33 @@ struct CellConst {
   float k_CB;       // dt / (w_a a keV_erg 1e24)
   float k_BC;       // 2 pi^2 (hbar c)^3 dt / (Gamma(5) zeta(5) <x>_C keV_erg)
   float k_BB;       // 2 pi^2 (hbar c)^3 dt / (Gamma(a) a keV_erg)
+};
+
+// Per-cell spectral records (rate models 1 and 2) and the surrogate network
+// that replaces them where it is trusted (rate model 2).
+//  * rate model 1: every cell's Primakoff and absorption rates (x = omega/T in
+//    [0.05, 20]) and emission energies come from its 192-float spectral
+//    record, interpolated from the exact FP32 table;
+//  * rate model 2: where the network is trusted (src[cell] = 0) it wrote the
+//    cell's rate prefactors into the cell record's slots R_CC..R_AP (the
+//    closed functional forms times the network's per-cell emissivity
+//    constants) and the emission energies come from the network's
+//    cell-independent quantiles (uni); elsewhere (src[cell] = 1) the cell has
+//    the table's spectral record, as in rate model 1.
+struct RecordArgs {
+  float* sr;                  // [ncells * 192] spectral records
+  const float* tab;           // exact table [2][nne][nkt][189]
+  int nkt, nne;
+  float Z;                    // the single ion species' charge
+  float ln_gP, ln_gA;         // ln(g_agg^2 dt pi^2 (hbar c)^3 / keV), ln(g_ae^2 dt 2 pi^2 (hbar c)^3 / keV)
+  float lnK_CC, lnK_CB;       // network emission rates: R_CC = exp(c_C + lnK_CC) / (n_e' T), likewise R_CB
+  float bee_c;                // (1 + X_H) / (2 sqrt 2) of the e-e bremsstrahlung term (0 without it)
+  float k_T7;                 // 1 / (k_B 1e7 K) [1/keV]
+  const uint8_t* trust;       // [2][tnne][tnT] trust map, NULL: the network is used nowhere
+  int tnT, tnne;
+  const unsigned char* img;   // the network in its shared-memory image (kNetImgBytes)
+  uint8_t* src;               // [ncells] rate model 2: 1 = table record, 0 = network prefactors
+  const float* uni;           // [192]: the network's cell-independent quantiles at a record's offsets
 };
 
 struct SpeciesPtrs {
@@ -359,10 +387,11 @@ struct StepArgs {
   int dec_grid;   // CTAs of the persistent decision kernel
   int dec_chunk;  // cells per chunk of a decision warp: 2, 4 or 8
   uint32_t* step_dev;  // NULL, or the device step counter of a replayed graph
-  // rate model: 0 the closed forms; 1 and 2 per-cell spectral records (table,
-  // surrogate) for the full decisions' rates and the emission energies
+  // rate model: 0 the closed forms; 1 the exact table's spectral records for
+  // the full decisions' rates and the emission energies; 2 the surrogate
+  // network where it is trusted, the table's records elsewhere
   int rate_model;
-  const float* sr;     // [ncells * 192] spectral records
+  RecordArgs ra;
   float guard_margin;  // factor on the no-event bounds (covers the records' error)
   CellConst cc;
 };

@@ -12,6 +12,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -512,7 +513,7 @@ const char* axpic_mlp_last_error(const axpic_mlp* h) { return h ? h->last_error.
 axpic_status axpic_mlp_set_norm(axpic_mlp* h, const float* mu, const float* sigma) {
   if (!h || !mu || !sigma) return AXPIC_E_INVALID;
   for (int k = 0; k < 96; ++k) {
-    if (!(sigma[k] > 0.f)) return AXPIC_E_INVALID;
+    if (!(sigma[k] >= 0.f) || !std::isfinite(sigma[k]) || !std::isfinite(mu[k])) return AXPIC_E_INVALID;
     h->mu[k] = mu[k];
     h->sigma[k] = sigma[k];
   }
@@ -616,6 +617,17 @@ axpic_status axpic_surrogate_fit(axpic_mlp* h, int32_t ncells, int32_t x_per_cel
     h->skip[k * 4] = 0.f;
     for (int i = 1; i < kD; ++i) h->skip[k * 4 + i] = (float)(M[i][kD + k] / M[i][i]);
   }
+  // The Compton-like and bremsstrahlung quantiles do not depend on the cell
+  // (their number spectra in x are universal): the model carries them as
+  // constants, mu = the exact knots, with S and sigma zero, so the step can
+  // sample from one row for every cell.
+  double uni[93];
+  axpic::sur_universal_knots(brems_shape, uni);
+  for (int k = 0; k < 96; ++k)
+    if (axpic::sur_universal_output(k)) {
+      h->mu[k] = (float)uni[31 * (k / 32) + k % 32 - 1];
+      for (int i = 0; i < kD; ++i) h->skip[k * 4 + i] = 0.f;
+    }
   // residuals with the binary32 coefficients the model keeps
   std::vector<double> var(96, 0.0);
   for (size_t r = 0; r < n; ++r)
@@ -638,11 +650,15 @@ axpic_status axpic_surrogate_fit(axpic_mlp* h, int32_t ncells, int32_t x_per_cel
   for (int k = 0; k < 96; ++k) {
     const bool rate = k % 32 == 0;
     const double floor = rate ? AXPIC_SIGMA_FLOOR_RATE : AXPIC_SIGMA_FLOOR_Q;
-    h->sigma[k] = (float)(std::max(std::sqrt(var[k] / (double)n), floor) / (rate ? kRateWeight : 1.0));
+    h->sigma[k] = axpic::sur_universal_output(k)
+                      ? 0.f
+                      : (float)(std::max(std::sqrt(var[k] / (double)n), floor) / (rate ? kRateWeight : 1.0));
   }
+  // normalised targets; the network's outputs that sigma zeroes learn zero
   std::vector<float> Zt(n * 96);
   for (size_t r = 0; r < n; ++r)
-    for (int k = 0; k < 96; ++k) Zt[r * 96 + k] = (float)(Y[r * 96 + k] / h->sigma[k]);
+    for (int k = 0; k < 96; ++k)
+      Zt[r * 96 + k] = h->sigma[k] > 0.f ? (float)(Y[r * 96 + k] / h->sigma[k]) : 0.f;
   X = cell_features(X);  // the network's inputs
   std::vector<float> P;
   glorot(seed ^ 0xA5A5A5A5u, P);
@@ -680,28 +696,37 @@ axpic_status axpic_surrogate_validate(axpic_mlp* h, int32_t nT, int32_t nne, dou
   struct Pop {
     ~Pop() { nvtxRangePop(); }
   } pop_range_;
-  if (!h || nT < 2 || nne < 2 || !err_out || !(brems_shape > 0)) return AXPIC_E_INVALID;
-  const int nodes = nT * nne * 2, nx = 32;
+  if (!h || nT < 2 || nne < 2 || nT > 4096 || nne > 4096 || !err_out || !(brems_shape > 0)) return AXPIC_E_INVALID;
+  // the learned part of every output is a function of the cell (the
+  // x-dependence is the exact shape), so a few x per node suffice
+  const int nodes = nT * nne * 2, nx = 8;
   std::vector<float> X((size_t)nodes * nx * 4);
   std::vector<double> Y((size_t)nodes * nx * 96);
-  double knots[93], uni[93];
+  double uni[93];
   axpic::sur_universal_knots(brems_shape, uni);
-  for (int z = 0; z < 2; ++z)
-    for (int j = 0; j < nne; ++j)
-      for (int i = 0; i < nT; ++i) {
-        const int node = (z * nne + j) * nT + i;
-        const double T = axpic::kSurTLo + (axpic::kSurTHi - axpic::kSurTLo) * i / (nT - 1);
-        const double ne = std::pow(10.0, 23.0 + 3.0 * j / (nne - 1));
-        const double Z = z + 1.0;
-        const axpic::SurCell c = axpic::sur_cell(T, ne, Z, brems_shape);
-        axpic::sur_knots(c, knots, uni);
-        for (int k = 0; k < nx; ++k) {
-          const double x = axpic::kSurXLo * std::pow(axpic::kSurXHi / axpic::kSurXLo, k / (double)(nx - 1));
-          const size_t r = (size_t)node * nx + k;
-          axpic::sur_features(x, c.kappa / T, ne, Z, &X[r * 4]);
-          axpic::sur_targets(x, c, knots, &Y[r * 96]);
+  const int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  {
+    std::vector<std::thread> th;
+    for (int t = 0; t < nth; ++t)
+      th.emplace_back([&, t]() {
+        double knots[93];
+        for (int node = t; node < nodes; node += nth) {
+          const int i = node % nT, j = (node / nT) % nne, z = node / (nT * nne);
+          const double T = axpic::kSurTLo * std::pow(axpic::kSurTHi / axpic::kSurTLo, i / (double)(nT - 1));
+          const double ne = std::pow(10.0, 23.0 + 3.0 * j / (nne - 1));
+          const double Z = z + 1.0;
+          const axpic::SurCell c = axpic::sur_cell(T, ne, Z, brems_shape);
+          axpic::sur_knots(c, knots, uni);
+          for (int k = 0; k < nx; ++k) {
+            const double x = axpic::kSurXLo * std::pow(axpic::kSurXHi / axpic::kSurXLo, k / (double)(nx - 1));
+            const size_t r = (size_t)node * nx + k;
+            axpic::sur_features(x, c.kappa / T, ne, Z, &X[r * 4]);
+            axpic::sur_targets(x, c, knots, &Y[r * 96]);
+          }
         }
-      }
+      });
+    for (auto& x : th) x.join();
+  }
   const size_t n = (size_t)nodes * nx;
   float *dX = nullptr, *dZ = nullptr;
   cudaError_t e;
@@ -719,20 +744,24 @@ axpic_status axpic_surrogate_validate(axpic_mlp* h, int32_t nT, int32_t nne, dou
   cudaFree(dZ);
   if (e) return mlp_fail(h, e, "axpic_surrogate_validate");
   // per node: the largest error of ln(dQ/dx) over the x grid and channels
-  // (the relative rate error), and of the quantiles relative to x
+  // (the relative rate error), of the Compton-like and bremsstrahlung
+  // quantiles (those the step samples emission energies from) and of the
+  // Primakoff quantiles, relative to x
   for (int node = 0; node < nodes; ++node) {
-    double eL = 0.0, eQ = 0.0;
+    double eL = 0.0, eQ = 0.0, eQP = 0.0;
     for (int k = 0; k < nx; ++k) {
       const size_t r = (size_t)node * nx + k;
       for (int o = 0; o < 96; ++o) {
         const double y = model_output(h, o, &X[r * 4], (double)Z[r * 96 + o], brems_shape);
         const double d = std::fabs(y - Y[r * 96 + o]);
         if (o % 32 == 0) eL = std::max(eL, d);
+        else if (o < 32) eQP = std::max(eQP, d / Y[r * 96 + o]);
         else eQ = std::max(eQ, d / Y[r * 96 + o]);
       }
     }
-    err_out[2 * node] = (float)eL;
-    err_out[2 * node + 1] = (float)eQ;
+    err_out[3 * node] = (float)eL;
+    err_out[3 * node + 1] = (float)eQ;
+    err_out[3 * node + 2] = (float)eQP;
   }
   return AXPIC_OK;
 }

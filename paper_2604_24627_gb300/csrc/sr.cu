@@ -1,14 +1,19 @@
-// Per-cell spectral records for the table and surrogate rate models.
+// Per-cell records of the table and surrogate rate models.
 //
-// Table model: the exact targets tabulated on the host over (ln kappa/T,
-// log10 n_e, Z) and interpolated bilinearly per cell. Surrogate model: the
-// network evaluated once per cell (its inputs are the cell features; every
-// x-dependence is in the exact shapes) in one fused kernel: features and
-// layer 1 on the CUDA cores, layers 2 and 3 as tcgen05 MMAs with FP32
-// accumulators in tensor memory, the output affine in FP32, the shapes added
-// at the 32 grid points x_k. Cells whose (T, n_e, Z) lies outside the region
-// where the network's validated error is within the bound get the table
-// record (the table kernel, which then skips the others).
+// Table model (rate model 1): the exact targets tabulated on the host over
+// (ln kappa/T, log10 n_e, Z) and interpolated bilinearly per cell into a
+// 192-float spectral record.
+//
+// Surrogate model (rate model 2): the network evaluated once per cell (its
+// inputs are the cell features; every x-dependence is in the exact shapes),
+// one tcgen05 row per cell, giving the cell's three ln-emissivity constants;
+// they become the prefactors of the closed functional forms in the cell
+// record (srnet.cuh). Cells whose (T, n_e, Z) lies outside the region where
+// the network's validated error is within the bound get the table's
+// spectral record instead, written by the same CTA. During evolved-T steps
+// the feedback kernel does this right after each temperature update; the
+// kernel here builds the records at set-up and after the caller changes T
+// or the composition.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -18,8 +23,8 @@
 
 #include "mlp.h"
 #include "sr.h"
+#include "srnet.cuh"
 #include "surrogate.h"
-#include "tc.cuh"
 
 namespace axpic {
 
@@ -39,11 +44,16 @@ void build_sr_table(int nkt, int nne, double brems_shape, float* out) {
         const double Z = z + 1.0;
         const SurCell c = sur_cell(sur_temperature(kT, ne, Z), ne, Z, brems_shape);
         sur_knots(c, knots, uni);
+        // the bremsstrahlung brackets, (b_eZ + c_ee b_ee) / (1 + c_ee) with
+        // the 1e-3 floor, divided out of that row
+        const double XH = Z == 1.0 ? 1.0 : 0.0;
+        const double cee = (1.0 + XH) / (2.0 * std::sqrt(2.0));
+        const double lnbr = std::log((std::max(1e-3, c.bZ) + cee * std::max(1e-3, c.bE)) / (1.0 + cee));
         float* o = out + (size_t)node * kSrTabOut;
         for (int k = 0; k < kSrGrid; ++k) {
           const double x = std::exp(std::log(kSurXLo) + std::log(kSurXHi / kSurXLo) / 29.0 * (k - 1));
           sur_targets(x, c, knots, y);
-          for (int ch = 0; ch < 3; ++ch) o[ch * 32 + k] = (float)(y[32 * ch] + x);
+          for (int ch = 0; ch < 3; ++ch) o[ch * 32 + k] = (float)(y[32 * ch] + x - (ch == 2 ? lnbr : 0.0));
         }
         for (int q = 0; q < 93; ++q) o[96 + q] = (float)knots[q];
       }
@@ -52,104 +62,21 @@ void build_sr_table(int nkt, int nne, double brems_shape, float* out) {
   for (auto& x : th) x.join();
 }
 
-// Cell quantities the records need: T, kappa/T, n_e.
-struct SrCellIn {
-  float T, kT;
-  float lkT, lne;  // ln(kappa/T), log10 n_e
-};
-__device__ __forceinline__ SrCellIn sr_cell(const SrArgs& a, int cell) {
-  const float* rec = a.rec + (size_t)cell * kRecLen;
-  SrCellIn c;
-  c.T = rec[R_T];
-  c.kT = 2.0f * rsqrtf(rec[R_FOURK2]) / c.T;
-  c.lkT = __logf(c.kT);
-  c.lne = log10f(rec[R_NE] * 1e24f);
-  return c;
-}
-// a cell beyond the launch's cells (its values are never used)
-__device__ __forceinline__ SrCellIn sr_cell_none() { return SrCellIn{1.f, 1.f, 0.f, 24.f}; }
-
-// A cell's table interpolation constants: the corner node (i, j) at the
-// cell's Z, the weights in (ln kappa/T, log10 n_e), and the record's
-// per-cell constants.
-struct SrInterp {
-  const float* t00;
-  float fu, fv, lnKP, lnKA, T;
-};
-
-// The record's per-cell constants (entries 189, 190).
-__device__ __forceinline__ void sr_consts(const SrArgs& a, float T, float* lnKP, float* lnKA) {
-  *lnKP = fmaf(-4.0f, __logf(T), a.ln_gP);
-  *lnKA = fmaf(-4.0f, __logf(T), a.ln_gA);
-}
-
-__device__ __forceinline__ void sr_interp(const SrArgs& a, const SrCellIn& c, SrInterp* q) {
-  const float T = c.T;
-  float u = (c.lkT - kSrLnKt0) / kSrLnKtSpan * (a.nkt - 1);
-  float v = (c.lne - 23.0f) / 3.0f * (a.nne - 1);
-  u = fminf(fmaxf(u, 0.f), (float)(a.nkt - 1));
-  v = fminf(fmaxf(v, 0.f), (float)(a.nne - 1));
-  const int i = min((int)u, a.nkt - 2), j = min((int)v, a.nne - 2);
-  const int z = a.Z > 1.5f ? 1 : 0;
-  q->t00 = a.tab + ((size_t)(z * a.nne + j) * a.nkt + i) * kSrTabOut;
-  q->fu = u - i;
-  q->fv = v - j;
-  sr_consts(a, T, &q->lnKP, &q->lnKA);
-  q->T = T;
-}
-
-// Entry o of the table record (bilinear, each rounding step explicit so that
-// both record kernels give the same bits).
-__device__ __forceinline__ float sr_table_entry(const SrArgs& a, const SrInterp& q, int o) {
-  if (o >= kSrTabOut) return o == SR_LNKP ? q.lnKP : (o == SR_LNKA ? q.lnKA : q.T);
-  const float* t01 = q.t00 + (size_t)a.nkt * kSrTabOut;  // j + 1
-  const float v00 = q.t00[o], v10 = q.t00[kSrTabOut + o], v01 = t01[o], v11 = t01[kSrTabOut + o];
-  const float u0 = fmaf(q.fu, v10, __fmul_rn(1.f - q.fu, v00));
-  const float u1 = fmaf(q.fu, v11, __fmul_rn(1.f - q.fu, v01));
-  return fmaf(q.fv, u1, __fmul_rn(1.f - q.fv, u0));
-}
-
-// Whether the network is trusted at (T, n_e, Z): the four validation nodes
-// around it all passed.
-__device__ __forceinline__ bool sr_trusted(const SrArgs& a, const SrCellIn& c, float Z) {
-  float fu = (c.T - (float)kSurTLo) / (float)(kSurTHi - kSurTLo) * (a.tnT - 1);
-  float fv = (c.lne - 23.0f) / 3.0f * (a.tnne - 1);
-  // inside the validated grid (binary32 rounding at its edges tolerated)
-  const float tol = 1e-4f;
-  if (!(fu >= -tol && fu <= (float)(a.tnT - 1) + tol && fv >= -tol && fv <= (float)(a.tnne - 1) + tol)) return false;
-  fu = fminf(fmaxf(fu, 0.f), (float)(a.tnT - 1));
-  fv = fminf(fmaxf(fv, 0.f), (float)(a.tnne - 1));
-  const int i = min((int)fu, a.tnT - 2), j = min((int)fv, a.tnne - 2);
-  const int z = Z > 1.5f ? 1 : 0;
-  const uint8_t* t = a.trust + (size_t)(z * a.tnne + j) * a.tnT + i;
-  return t[0] && t[1] && t[a.tnT] && t[a.tnT + 1];
-}
-
+// ---------------------------------------------------------------- table model
 // A CTA takes 32 cells: warp 0 forms each cell's interpolation constants
 // (lane per cell) in shared memory, then the CTA's threads stream the 32 x
 // 192 record entries (consecutive threads, consecutive entries of a cell).
-// With a trust map (surrogate model) the network kernel ran before and
-// flagged the cells it wrote: those are skipped, and a CTA with none left
-// exits.
 constexpr int kSrTableThreads = 256;
 __global__ void __launch_bounds__(kSrTableThreads) sr_table_kernel(SrArgs a) {
   __shared__ SrInterp ip[32];
-  __shared__ int skip[32];
   const int c0 = a.cell0 + blockIdx.x * 32;
   const int nc = min(32, a.cell0 + a.ncells - c0);
-  int need = 0;
-  if (threadIdx.x < 32 && (int)threadIdx.x < nc) {
-    const int sk = a.trust ? a.net[c0 + threadIdx.x] : 0;
-    skip[threadIdx.x] = sk;
-    if (!sk) {
-      sr_interp(a, sr_cell(a, c0 + threadIdx.x), &ip[threadIdx.x]);
-      need = 1;
-    }
-  }
-  if (!__syncthreads_or(need)) return;
+  if (threadIdx.x < 32 && (int)threadIdx.x < nc)
+    sr_interp(a.ra, sr_cell_from(a.rec + (size_t)(c0 + threadIdx.x) * kRecLen, a.ra.k_T7), &ip[threadIdx.x]);
+  __syncthreads();
   for (int e = threadIdx.x; e < nc * kSrLen; e += kSrTableThreads) {
     const int c = e / kSrLen, o = e - c * kSrLen;
-    if (!skip[c]) a.sr[(size_t)(c0 + c) * kSrLen + o] = sr_table_entry(a, ip[c], o);
+    a.ra.sr[(size_t)(c0 + c) * kSrLen + o] = sr_table_entry(a.ra, ip[c], o);
   }
 }
 
@@ -159,317 +86,109 @@ cudaError_t launch_sr_table(const SrArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- fused network
-// CTA = 128 cells (MMA row r = cell) and 256 threads: thread t takes row
-// t % 128 and half t / 128 of each layer's columns (the warps w and w + 4 read
-// the same tensor-memory lanes). It writes the records of the cells where
-// the network is trusted and flags them for the table kernel, which runs
-// next and writes the others; a CTA with no trusted cell exits at once.
-// Dynamic shared memory: A (128 x 64 bfloat16, core-matrix layout: layer 1's
-// activations, then layer 2's over them once layer 2 has run), W2^T
-// (64 x 64), W3^T (96 x 64), layer 1's constants and the rows' features;
-// once layer 3 has run, the same bytes hold the 128 cells' 96 outputs (FP32,
-// row stride 97, so that a column is conflict-free), from which each warp
-// writes whole records with coalesced stores. Four CTAs fit an SM (shared
-// memory, 64 registers a thread, 4 x 128 tensor-memory columns). Tensor
-// memory: 128 columns, layer 2 in [0, 64), then layer 3 in [0, 96) after
-// layer 2's values were read out.
-constexpr int kSrMlpThreads = 256;
-constexpr int kSrOutStride = 97;
-constexpr size_t kSrOffW2 = 128 * 64 * 2, kSrOffW3 = kSrOffW2 + 64 * 64 * 2, kSrOffL1 = kSrOffW3 + 96 * 64 * 2,
-                 kSrOffB2 = kSrOffL1 + 64 * 16, kSrOffF = kSrOffB2 + 64 * 4, kSrMlpLayers = kSrOffF + 2 * 128 * 4;
-constexpr size_t kSrMlpStage = (size_t)128 * kSrOutStride * sizeof(float);
-constexpr size_t kSrMlpSmem = kSrMlpLayers > kSrMlpStage ? kSrMlpLayers : kSrMlpStage;
-
-// ln F(s), F(s) = (1 + 1/s) ln(1 + s) - 1 the screening function of Sec.
-// II.F, in binary32: below s = 1/2 the alternating series
-// sum_n (-1)^(n+1) s^n / (n (n + 1)) to n = 12 (truncation under 4e-6
-// relative), above it the closed form, whose cancellation costs at most a
-// factor 6 on the rounding of its logarithm. Both forms are taken and one
-// selected: the 32 lanes of a record row span both sides.
-__device__ __forceinline__ float sr_prim_lnF(float s) {
-  float p = -1.0f / 156.0f;  // n = 12
+// ---------------------------------------------------------------- surrogate model
+// CTA = 128 cells, thread t = cell cell0 + 128 b + t = tensor-core row t. The
+// network runs when the CTA has a trusted cell; trusted cells get their rate
+// prefactors, the others the table record (a warp per cell, written after
+// the network).
+__global__ void __launch_bounds__(kNetThreads) sr_cells_kernel(SrArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ int list[kNetThreads];
+  __shared__ int nlist;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int cell = a.cell0 + blockIdx.x * kNetThreads + tid;
+  const bool valid = cell < a.cell0 + a.ncells;
+  if (tid == 0) nlist = 0;
+  float r[kRecLen];
+  SrCellIn ci = {1.f, 1.f, 0.f, 24.f, 0.f};
+  bool trusted = false;
+  if (valid) {
+    const float4* r4 = reinterpret_cast<const float4*>(a.rec + (size_t)cell * kRecLen);
 #pragma unroll
-  for (int n = 11; n >= 1; --n) p = fmaf(p, s, ((n & 1) ? 1.0f : -1.0f) / (float)(n * (n + 1)));
-  const float L = __logf(1.0f + s);
-  const float closed = L + __fdividef(L, s) - 1.0f;
-  return __logf(s < 0.5f ? p * s : closed);
-}
-
-// Layers 2 and 3 as B^T (N x K = 64) bfloat16 in the core-matrix layout, laid
-// out once per network: W2^T (64 x 64) then W3^T (96 x 64).
-__global__ void sr_weights_kernel(const float* __restrict__ P, __nv_bfloat16* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < 64 * 64) {
-    const int n = i >> 6, kk = i & 63;
-    out[core_off(n, kk, 64)] = __float2bfloat16_rn(P[kOffW2 + kk * 64 + n]);
-  } else if (i < 64 * 64 + 96 * 64) {
-    const int j = i - 64 * 64, n = j >> 6, kk = j & 63;
-    out[64 * 64 + core_off(n, kk, 64)] = __float2bfloat16_rn(P[kOffW3 + kk * 96 + n]);
+    for (int i = 0; i < kRecLen / 4; ++i) {
+      const float4 v = r4[i];
+      r[4 * i] = v.x;
+      r[4 * i + 1] = v.y;
+      r[4 * i + 2] = v.z;
+      r[4 * i + 3] = v.w;
+    }
+    ci = sr_cell_from(r, a.ra.k_T7);
+    trusted = a.ra.trust && sr_trusted(a.ra, ci.T, ci.lne);
+  }
+  __syncthreads();
+  if (__syncthreads_or(trusted)) {
+    float c[3];
+    const bool ok = net_rows(sm, a.ra.img, net_f1(ci.lkT), net_f2(ci.lne), a.ra.Z - 1.5f, c, a.err);
+    trusted = trusted && ok;
+    if (trusted) {
+      net_prefactors(a.ra, c, ci.T, r[R_NE], r);
+      float4* o = reinterpret_cast<float4*>(a.rec + (size_t)cell * kRecLen);
+      o[0] = make_float4(r[0], r[1], r[2], r[3]);
+      o[1] = make_float4(r[4], r[5], r[6], r[7]);
+    }
+  }
+  if (valid) {
+    a.ra.src[cell] = trusted ? 0 : 1;
+    if (!trusted) list[atomicAdd(&nlist, 1)] = tid;
+  }
+  __syncthreads();
+  const int n = nlist;
+  for (int k = warp; k < n; k += kNetThreads / 32) {
+    const int t = list[k];
+    const int c = a.cell0 + blockIdx.x * kNetThreads + t;
+    const SrCellIn cc = sr_cell_from(a.rec + (size_t)c * kRecLen, a.ra.k_T7);
+    sr_table_record_warp(a.ra, cc, a.ra.sr + (size_t)c * kSrLen, lane);
   }
 }
 
-cudaError_t launch_sr_weights(const float* P, void* out, cudaStream_t st) {
-  sr_weights_kernel<<<(64 * 64 + 96 * 64 + 255) / 256, 256, 0, st>>>(P, static_cast<__nv_bfloat16*>(out));
+cudaError_t launch_sr_cells(const SrArgs& a, cudaStream_t st) {
+  if (a.ncells <= 0) return cudaSuccess;
+  sr_cells_kernel<<<(a.ncells + kNetThreads - 1) / kNetThreads, kNetThreads, kNetSmemBytes, st>>>(a);
   return cudaGetLastError();
 }
 
-// Per-cell state of the fused kernel.
-struct SrCellSlot {
-  float lnKP, lnKA, T;  // the record's per-cell constants
-  float s_per_x2;       // 4 / (kappa/T)^2: s = x^2 times this
-  int mode;             // 1: the network writes this cell's record
-};
-
-// A trusted cell's six record entries of this lane (entry lane + 32 it) from
-// the network's outputs y (shared memory). shx: the lane's fixed shape
-// terms (Primakoff and Compton-like Planck factors, bremsstrahlung power,
-// each plus x_k); qsrc: the network output of the lane's quantile entries
-// (-1 on lanes 29..31 of the last row: the per-cell constants).
-__device__ __forceinline__ void sr_record_entries(const SrCellSlot& c, const float* y, float x2, const float* shx,
-                                                  const int* qsrc, int lane, float* v) {
-  v[0] = y[0] + shx[0] + sr_prim_lnF(x2 * c.s_per_x2);
-  v[1] = y[32] + shx[1];
-  v[2] = y[64] + shx[2];
-  v[3] = y[qsrc[0]];
-  v[4] = y[qsrc[1]];
-  const float k = lane == 29 ? c.lnKP : (lane == 30 ? c.lnKA : c.T);
-  v[5] = qsrc[2] >= 0 ? y[qsrc[2]] : k;
-}
-
-// Eight activations (columns j0..j0+7 of row r) as bfloat16 into one 16-byte
-// row of a core matrix.
-__device__ __forceinline__ void store8_bf16(__nv_bfloat16* base, int r, int j0, const float* v) {
-  uint4 u;
-  uint32_t* w = reinterpret_cast<uint32_t*>(&u);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-    w[i] = *reinterpret_cast<const uint32_t*>(&h);
-  }
-  *reinterpret_cast<uint4*>(base + core_off(r, j0, 64)) = u;
-}
-
-__global__ void __launch_bounds__(kSrMlpThreads, 4) sr_mlp_kernel(SrArgs a) {
-  extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ SrCellSlot cs[128];
-  // the output affine (mu + sigma b3, sigma, S columns of f1..f3), read as float4
-  __shared__ __align__(16) float sC3[96];
-  __shared__ __align__(16) float sSig[96];
-  __shared__ __align__(16) float sS[3][96];
-  __shared__ uint64_t bar;
-  __shared__ uint32_t tmem_base;
-  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(sm);
-  __nv_bfloat16* sW2 = reinterpret_cast<__nv_bfloat16*>(sm + kSrOffW2);
-  __nv_bfloat16* sW3 = reinterpret_cast<__nv_bfloat16*>(sm + kSrOffW3);
-  float4* sL1 = reinterpret_cast<float4*>(sm + kSrOffL1);  // per unit: b1, W1 rows of f1..f3
-  float* sB2 = reinterpret_cast<float*>(sm + kSrOffB2);
-  float* sF = reinterpret_cast<float*>(sm + kSrOffF);      // [2][128]: f1, f2 of each row
-  float* sOut = reinterpret_cast<float*>(sm);              // after layer 3: [128][kSrOutStride]
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int r = tid & 127, half = tid >> 7;
-  const int c0 = a.cell0 + blockIdx.x * 128;
-  const int nc = min(128, a.cell0 + a.ncells - c0);
-  const bool valid = r < nc;
-  bool trusted = false;
-  if (half == 0) {
-    const SrCellIn c = valid ? sr_cell(a, c0 + r) : sr_cell_none();
-    trusted = valid && sr_trusted(a, c, a.Z);
-    sr_consts(a, c.T, &cs[r].lnKP, &cs[r].lnKA);
-    cs[r].T = c.T;
-    cs[r].s_per_x2 = 4.0f / (c.kT * c.kT);
-    cs[r].mode = trusted ? 1 : 0;
-    sF[r] = (c.lkT - kSrLnKt0) / kSrLnKtSpan * 2.0f - 1.0f;
-    sF[128 + r] = (c.lne - 24.5f) / 1.5f;
-  }
-  // no trusted cell here: the table kernel writes all of them
-  if (!__syncthreads_or(trusted)) {
-    if (half == 0 && valid) a.net[c0 + r] = 0;
-    return;
-  }
-  bool ok = true;
-  if (warp == 0) tmem_alloc(&tmem_base, 128);
-  if (tid == 0) {
-    mbar_init(&bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  // the pre-laid-out weights: 20 KB of 16-byte copies
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(a.W16);
-    uint4* dst = reinterpret_cast<uint4*>(sW2);
-    for (int i = tid; i < (64 * 64 + 96 * 64) / 8; i += kSrMlpThreads) dst[i] = src[i];
-  }
-  if (tid < 64) {
-    sL1[tid] = make_float4(a.P[kOffB1 + tid], a.P[kOffW1 + 64 + tid], a.P[kOffW1 + 128 + tid],
-                           a.P[kOffW1 + 192 + tid]);
-    sB2[tid] = a.P[kOffB2 + tid];
-  } else if (tid >= 128 && tid < 128 + 96) {
-    const int o = tid - 128;
-    sC3[o] = fmaf(a.sigma[o], a.P[kOffB3 + o], a.mu[o]);
-    sSig[o] = a.sigma[o];
-#pragma unroll
-    for (int i = 1; i < 4; ++i) sS[i - 1][o] = a.skip[o * 4 + i];
-  }
-  __syncthreads();
-  // cell features (the ln x input held at zero) and layer 1 on the CUDA
-  // cores: this thread's 32 of the 64 units
-  const float f1 = sF[r], f2 = sF[128 + r], f3 = a.Z - 1.5f;
-#pragma unroll
-  for (int j0 = 32 * half; j0 < 32 * half + 32; j0 += 8) {
-    float v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float4 w = sL1[j0 + j];
-      v[j] = act_tanh(fmaf(f3, w.w, fmaf(f2, w.z, fmaf(f1, w.y, w.x))));
-    }
-    store8_bf16(sA, r, j0, v);
-  }
-  smem_to_async_proxy();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tmem_base;
-  const uint32_t row = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-  const uint32_t lbo = 128, sbo = 8 * 128;
-  // layer 2: D[0, 64) = A1 . W2
-  if (tid == 0) {
-    for (int s = 0; s < 4; ++s)
-      mma_bf16(tmem, mma_desc(smem_u32(sA) + s * 256, lbo, sbo), mma_desc(smem_u32(sW2) + s * 256, lbo, sbo),
-               mma_idesc(128, 64), s > 0);
-    tc_commit(&bar);
-  }
-  // warp 0 waits; the others park in the barrier (no issue slots spent
-  // spinning), and the verdict is CTA-uniform
-  {
-    bool w = true;
-    if (warp == 0) w = __all_sync(0xFFFFFFFFu, mbar_wait(&bar, 0));
-    ok = __syncthreads_and(w) != 0;
-  }
-  tc_fence_after();
-  // layer 2's activations over layer 1's (the MMA that read them is done)
-  if (ok) {
-#pragma unroll
-    for (int j0 = 32 * half; j0 < 32 * half + 32; j0 += 16) {
-      float v[16];
-      tmem_ld16(row + j0, v);
-#pragma unroll
-      for (int j = 0; j < 16; j += 4) {
-        const float4 b = *reinterpret_cast<const float4*>(sB2 + j0 + j);
-        v[j] = act_tanh(v[j] + b.x);
-        v[j + 1] = act_tanh(v[j + 1] + b.y);
-        v[j + 2] = act_tanh(v[j + 2] + b.z);
-        v[j + 3] = act_tanh(v[j + 3] + b.w);
-      }
-      store8_bf16(sA, r, j0, v);
-      store8_bf16(sA, r, j0 + 8, v + 8);
-    }
-  }
-  smem_to_async_proxy();
-  tc_fence_before();
-  ok = __syncthreads_and(ok) != 0;
-  tc_fence_after();
-  // layer 3: D[0, 96) = A2 . W3 (layer 2's columns have been read out)
-  if (ok && tid == 0) {
-    for (int s = 0; s < 4; ++s)
-      mma_bf16(tmem, mma_desc(smem_u32(sA) + s * 256, lbo, sbo), mma_desc(smem_u32(sW3) + s * 256, lbo, sbo),
-               mma_idesc(128, 96), s > 0);
-    tc_commit(&bar);
-  }
-  const bool issued3 = ok;
-  if (ok) {
-    bool w = true;
-    if (warp == 0) w = __all_sync(0xFFFFFFFFu, mbar_wait(&bar, 1));
-    ok = __syncthreads_and(w) != 0;
-  }
-  tc_fence_after();
-  if (!ok && warp == 0) {
-    // flag it and give the tensor core a second bounded wait on whatever it
-    // may still be doing before the tensor memory is released; no record is
-    // written here and the table kernel writes them all
-    if (lane == 0) atomicOr(a.err, 2);
-    mbar_wait(&bar, issued3 ? 1u : 0u);
-  }
-  if (ok) {
-    // this thread's 48 outputs, 16 at a time, through the FP32 output affine
-    // into the stage (the operands' bytes: the MMA that read them is done)
-    float* out = sOut + r * kSrOutStride + 48 * half;
-#pragma unroll
-    for (int j0 = 0; j0 < 48; j0 += 16) {
-      float y[16];
-      tmem_ld16(row + 48 * half + j0, y);
-#pragma unroll
-      for (int i = 0; i < 16; i += 4) {
-        const int o = 48 * half + j0 + i;
-        const float4 c = *reinterpret_cast<const float4*>(sC3 + o);
-        const float4 g = *reinterpret_cast<const float4*>(sSig + o);
-        const float4 s1 = *reinterpret_cast<const float4*>(sS[0] + o);
-        const float4 s2 = *reinterpret_cast<const float4*>(sS[1] + o);
-        const float4 s3 = *reinterpret_cast<const float4*>(sS[2] + o);
-        out[j0 + i] = fmaf(s3.x, f3, fmaf(s2.x, f2, fmaf(s1.x, f1, fmaf(g.x, y[i], c.x))));
-        out[j0 + i + 1] = fmaf(s3.y, f3, fmaf(s2.y, f2, fmaf(s1.y, f1, fmaf(g.y, y[i + 1], c.y))));
-        out[j0 + i + 2] = fmaf(s3.z, f3, fmaf(s2.z, f2, fmaf(s1.z, f1, fmaf(g.z, y[i + 2], c.z))));
-        out[j0 + i + 3] = fmaf(s3.w, f3, fmaf(s2.w, f2, fmaf(s1.w, f1, fmaf(g.w, y[i + 3], c.w))));
-      }
-    }
-  } else if (half == 0) {
-    cs[r].mode = 0;  // no network outputs: the table kernel writes this cell
-  }
-  if (half == 0 && valid) a.net[c0 + r] = cs[r].mode;
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (warp == 0) tmem_free(tmem, 128);
-  // records: warp w writes cells w, w + 8, ..., two at a time, a cell's 192
-  // entries by its 32 lanes (lane k takes grid point x_k of the three rate
-  // rows). A trusted cell's ln-emissivity row is the network's cell constant
-  // plus the exact shape plus x_k; its quantiles are outputs 1..31 of each
-  // channel.
-  constexpr int kW = kSrMlpThreads / 32;
-  const float lnxk = kSrLnX0 + kSrH * (float)lane;
-  const float xk = __expf(lnxk);
-  const float planck = logf(expm1f(xk));
-  const float shx[3] = {3.0f * lnxk - planck + xk, 5.0f * lnxk - planck + xk, a.brems_a * lnxk};
-  int qsrc[3];
-#pragma unroll
-  for (int it = 0; it < 3; ++it) {
-    const int e = lane + 32 * it;  // entry 96 + e: quantile e (e < 93) or a constant
-    qsrc[it] = e < 93 ? 32 * (e / 31) + 1 + e % 31 : -1;
-  }
-  const float x2 = xk * xk;
-  for (int c = warp; c < nc; c += 2 * kW) {
-    const int c1 = c + kW;
-    const bool w0 = cs[c].mode != 0, w1 = c1 < nc && cs[c1].mode != 0;
-    float v0[6], v1[6];
-    if (w0) sr_record_entries(cs[c], sOut + c * kSrOutStride, x2, shx, qsrc, lane, v0);
-    if (w1) sr_record_entries(cs[c1], sOut + c1 * kSrOutStride, x2, shx, qsrc, lane, v1);
-    if (w0) {
-      float* r0 = a.sr + (size_t)(c0 + c) * kSrLen;
-#pragma unroll
-      for (int it = 0; it < 6; ++it) r0[lane + 32 * it] = v0[it];
-    }
-    if (w1) {
-      float* r1 = a.sr + (size_t)(c0 + c1) * kSrLen;
-#pragma unroll
-      for (int it = 0; it < 6; ++it) r1[lane + 32 * it] = v1[it];
-    }
-  }
+cudaError_t launch_sr_records(int model, const SrArgs& a, cudaStream_t st) {
+  if (model == 1) return launch_sr_table(a, st);
+  if (model == 2) return launch_sr_cells(a, st);
+  return cudaSuccess;
 }
 
 cudaError_t sr_init_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(sr_mlp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSrMlpSmem);
-  if (!e) e = cudaFuncSetAttribute(sr_mlp_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  return e;
+  return cudaFuncSetAttribute(sr_cells_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kNetSmemBytes);
 }
 
-cudaError_t launch_sr_records(const SrArgs& a, cudaStream_t st) {
-  cudaError_t e = a.trust ? launch_sr_mlp(a, st) : cudaSuccess;
-  if (!e) e = launch_sr_table(a, st);
-  return e;
+// ---------------------------------------------------------------- network image
+// The image of srnet.cuh from the FP32 parameters and the output model.
+__global__ void net_image_kernel(const float* __restrict__ P, const float* __restrict__ mu,
+                                 const float* __restrict__ sigma, const float* __restrict__ skip,
+                                 unsigned char* __restrict__ img) {
+  __nv_bfloat16* w2 = reinterpret_cast<__nv_bfloat16*>(img + kImgW2);
+  __nv_bfloat16* w3 = reinterpret_cast<__nv_bfloat16*>(img + kImgW3);
+  float4* l1 = reinterpret_cast<float4*>(img + kImgL1);
+  float* b2 = reinterpret_cast<float*>(img + kImgB2);
+  float4* aff = reinterpret_cast<float4*>(img + kImgAff);
+  for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+    const int n = i >> 6, k = i & 63;
+    w2[core_off(n, k, 64)] = __float2bfloat16_rn(P[kOffW2 + k * 64 + n]);
+  }
+  for (int i = threadIdx.x; i < 16 * 64; i += blockDim.x) {
+    const int n = i >> 6, k = i & 63;
+    w3[core_off(n, k, 64)] = __float2bfloat16_rn(n < 3 ? P[kOffW3 + k * 96 + 32 * n] : 0.f);
+  }
+  for (int j = threadIdx.x; j < 64; j += blockDim.x) {
+    l1[j] = make_float4(P[kOffB1 + j], P[kOffW1 + 64 + j], P[kOffW1 + 128 + j], P[kOffW1 + 192 + j]);
+    b2[j] = P[kOffB2 + j];
+  }
+  if (threadIdx.x < 3) {
+    const int o = 32 * threadIdx.x;
+    aff[threadIdx.x] = make_float4(fmaf(sigma[o], P[kOffB3 + o], mu[o]), sigma[o], skip[o * 4 + 1], skip[o * 4 + 2]);
+  }
+  if (threadIdx.x == 0) aff[3] = make_float4(skip[0 * 4 + 3], skip[32 * 4 + 3], skip[64 * 4 + 3], 0.f);
 }
 
-cudaError_t launch_sr_mlp(const SrArgs& a, cudaStream_t st) {
-  if (a.ncells <= 0) return cudaSuccess;
-  sr_mlp_kernel<<<(a.ncells + 127) / 128, kSrMlpThreads, kSrMlpSmem, st>>>(a);
+cudaError_t launch_net_image(const float* P, const float* mu, const float* sigma, const float* skip, void* img,
+                             cudaStream_t st) {
+  net_image_kernel<<<1, 256, 0, st>>>(P, mu, sigma, skip, static_cast<unsigned char*>(img));
   return cudaGetLastError();
 }
 

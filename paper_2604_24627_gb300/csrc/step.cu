@@ -23,6 +23,7 @@
 
 #include "common.cuh"
 #include "sr.h"
+#include "srnet.cuh"
 #include "step.h"
 
 namespace axpic {
@@ -182,7 +183,8 @@ __device__ __forceinline__ AxionDecision axion_decide(const float* rec, const fl
   const float xr = d.om * rec[R_INVT];
   const bool use_sr = sr && sr_in_range(xr);
   if (mask & AXPIC_CH_PRIMAKOFF) {
-    const float P = use_sr ? -expm1f(-A.cc.prim_mult * sr_prim_gdt(sr, xr)) : prim_prob(rec, d.om, rec[R_APINV]);
+    const float P = use_sr ? -expm1f(-A.cc.prim_mult * sr_prim_gdt(sr, xr))
+                           : prim_prob(rec, d.om, A.cc.prim_mult * rec[R_AP]);
     float fac;
     const float le = cap_lambda(w * P * A.inv_w_gref, A.lam_cap, &fac, &d.capped);
     d.K = poisson_inv(u23(wP), le);
@@ -215,6 +217,15 @@ __device__ __forceinline__ AxionDecision axion_decide(const float* rec, const fl
   return d;
 }
 
+// The spectral record a cell's full decisions and emission energies take
+// their rates from: every cell's under the table model, the cells the
+// network is not trusted for under the surrogate model; NULL otherwise (the
+// closed forms with the cell record's prefactors).
+__device__ __forceinline__ const float* cell_sr(const StepArgs& A, int cell) {
+  if (A.rate_model == 1 || (A.rate_model == 2 && A.ra.src[cell])) return A.ra.sr + (size_t)cell * kSrLen;
+  return nullptr;
+}
+
 __device__ __forceinline__ void load_rec(const StepArgs& A, int cell, float* rec) {
   const float4* r4 = reinterpret_cast<const float4*>(A.rec + (size_t)cell * kRecLen);
 #pragma unroll
@@ -233,7 +244,7 @@ __device__ __noinline__ AxionDecision axion_decide_slow(const StepArgs& A, int c
                                                         float py, float pz, uint32_t wP, uint32_t wA) {
   float rec[kRecLen];
   load_rec(A, cell, rec);
-  return axion_decide(rec, A.rate_model ? A.sr + (size_t)cell * kSrLen : nullptr, A, mask, w, px, py, pz, wP, wA);
+  return axion_decide(rec, cell_sr(A, cell), A, mask, w, px, py, pz, wP, wA);
 }
 
 // One photon at the start of the step: gamma->a conversion (Sec. II.F,
@@ -264,7 +275,7 @@ __device__ __noinline__ PhotonDecision photon_decide_slow(const StepArgs& A, int
                                                           float pz, uint32_t wd) {
   float rec[kRecLen];
   load_rec(A, cell, rec);
-  return photon_decide(rec, A.rate_model ? A.sr + (size_t)cell * kSrLen : nullptr, A, w, px, py, pz, wd);
+  return photon_decide(rec, cell_sr(A, cell), A, w, px, py, pz, wd);
 }
 
 // Guards: cheap upper bounds that prove, without the transcendental chain,
@@ -735,7 +746,7 @@ __device__ __forceinline__ int axion_chunk(const StepArgs& A, uint32_t step, int
     const float* rec = A.rec + (size_t)c * kRecLen;
     n = min(max(A.a.count[c], 0), A.a.cap);
     c_s = kMeC2f * kMeC2f * __ldg(rec + R_FOURK2);
-    apinv = conversion_kb(__ldg(rec + R_APINV), A.inv_w_gref, A.guard_margin);
+    apinv = conversion_kb(A.cc.prim_mult * __ldg(rec + R_AP), A.inv_w_gref, A.guard_margin);
     invT = kMeC2f * __ldg(rec + R_INVT);
     r_bc = __ldg(rec + R_BC) * (1.001f * A.guard_margin);
     r_bb = __ldg(rec + R_BB) * (1.001f * A.guard_margin);
@@ -818,6 +829,8 @@ __global__ void __launch_bounds__(kDecThreads, AXPIC_DEC_MIN_CTAS) decide_kernel
 // (Eqs. delta_def to b_def, affine_map) by a whole warp, measuring what was
 // applied; then the temperature update (Eqs. Te_est, Te_relax) and the
 // record's temperature half.
+constexpr int kFeedbackThreadsMax = 128;
+
 struct FbCell {
   double dE, dPx, dPy, dPz;  // this step's exchange
   double rE, rPx, rPy, rPz;  // carried exchange
@@ -898,8 +911,12 @@ __device__ __forceinline__ void fb_prepare(FbCell& f) {
 }
 
 // Carry, moments, diagnostics, temperature and record once the remap (r;
-// null when the cell was not remapped) is done.
-__device__ __forceinline__ void fb_finish(const StepArgs& A, int cell, const FbCell& f, const RemapOut* r) {
+// null when the cell was not remapped) is done. Returns whether the
+// temperature was updated; then rec holds the cell's new record (with the
+// closed-form prefactors), written here except under the surrogate rate
+// model, whose network may still replace the prefactors.
+__device__ __forceinline__ bool fb_finish(const StepArgs& A, int cell, const FbCell& f, const RemapOut* r,
+                                          float* rec) {
   double nrE = f.qE, nrPx = f.qPx, nrPy = f.qPy, nrPz = f.qPz, applied_E = 0.0;
   float var_new = f.var;
   if (r) {
@@ -952,13 +969,63 @@ __device__ __forceinline__ void fb_finish(const StepArgs& A, int cell, const FbC
     double Tn = f.T + (double)dT;
     const float Tnf = Tf + dT;
     if (Tnf <= A.T_floor_f || Tnf >= A.T_ceil_f) Tn = fmin(fmax(Tn, A.T_floor), A.T_ceil);
-    float rec[kRecLen] = {f.rc[0].x, f.rc[0].y, f.rc[0].z, f.rc[0].w, f.rc[1].x, f.rc[1].y, f.rc[1].z, f.rc[1].w,
-                          f.rc[2].x, f.rc[2].y, f.rc[2].z, f.rc[2].w, f.rc[3].x, f.rc[3].y, f.rc[3].z, f.rc[3].w};
+    const float4* rc = f.rc;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      rec[4 * i] = rc[i].x;
+      rec[4 * i + 1] = rc[i].y;
+      rec[4 * i + 2] = rc[i].z;
+      rec[4 * i + 3] = rc[i].w;
+    }
     compute_temperature(A.cc, (float)Tn, rec);
     A.T[cell] = Tn;
+    if (A.rate_model == 2) {
+      // the closed-form Primakoff prefactor (a network value may be there)
+      rec[R_AP] = A.cc.k_AP * rec[R_SZ];
+      return true;
+    }
     float4* r4 = reinterpret_cast<float4*>(A.rec + (size_t)cell * kRecLen);
     r4[0] = make_float4(rec[0], rec[1], rec[2], rec[3]);
     r4[1] = make_float4(rec[4], rec[5], rec[6], rec[7]);
+    return true;
+  }
+  return false;
+}
+
+// Surrogate rate model, after the temperature update of the CTA's cells
+// (thread t: cell t, upd: its T changed, rec: its new record): the network
+// for the CTA's 128 cells (one tensor-core row each) where any is trusted;
+// trusted cells get the network's prefactors, the others the table's
+// spectral record (a warp per cell). All threads of the CTA call it.
+__device__ __forceinline__ void fb_surrogate(const StepArgs& A, int cell, bool upd, float* rec, unsigned char* sm) {
+  __shared__ int tlist[kFeedbackThreadsMax];
+  __shared__ int ntl;
+  if (threadIdx.x == 0) ntl = 0;
+  SrCellIn ci = {1.f, 1.f, 0.f, 24.f, 0.f};
+  bool trusted = false;
+  if (upd) {
+    ci = sr_cell_from(rec, A.ra.k_T7);
+    trusted = A.ra.trust && sr_trusted(A.ra, ci.T, ci.lne);
+  }
+  if (__syncthreads_or(trusted)) {
+    float c[3];
+    const bool ok = net_rows(sm, A.ra.img, net_f1(ci.lkT), net_f2(ci.lne), A.ra.Z - 1.5f, c, A.err);
+    trusted = trusted && ok;
+    if (trusted) net_prefactors(A.ra, c, ci.T, rec[R_NE], rec);
+  }
+  if (upd) {
+    float4* r4 = reinterpret_cast<float4*>(A.rec + (size_t)cell * kRecLen);
+    r4[0] = make_float4(rec[0], rec[1], rec[2], rec[3]);
+    r4[1] = make_float4(rec[4], rec[5], rec[6], rec[7]);
+    A.ra.src[cell] = trusted ? 0 : 1;
+    if (!trusted) tlist[atomicAdd(&ntl, 1)] = cell;
+  }
+  __syncthreads();
+  const int n = ntl, lane = threadIdx.x & 31;
+  for (int k = threadIdx.x >> 5; k < n; k += kFeedbackThreadsMax / 32) {
+    const int c = tlist[k];
+    const SrCellIn cc = sr_cell_from(A.rec + (size_t)c * kRecLen, A.ra.k_T7);
+    sr_table_record_warp(A.ra, cc, A.ra.sr + (size_t)c * kSrLen, lane);
   }
 }
 
@@ -971,6 +1038,7 @@ struct RemapJob {
   float s1, bx, by, bz;
 };
 constexpr int kFeedbackThreads = 128;
+static_assert(kFeedbackThreads == kNetThreads, "a feedback CTA runs the network with a row per cell");
 
 __global__ void __launch_bounds__(kFeedbackThreads) feedback_kernel(StepArgs A) {
   // a replayed graph takes its step index from the device counter: the last
@@ -1013,11 +1081,18 @@ __global__ void __launch_bounds__(kFeedbackThreads) feedback_kernel(StepArgs A) 
     if (lane == 0) outs[k] = r;
   }
   __syncthreads();
-  if (!valid) return;
-  fb_finish(A, cell, f, job >= 0 ? &outs[job] : nullptr);
-  if (f.need) {
-    atomicAdd(A.counters + C_REMAP, 1ull);
-    atomicAdd(A.counters + C_REMAP_E, (unsigned long long)f.ne);
+  float rec[kRecLen];
+  bool upd = false;
+  if (valid) {
+    upd = fb_finish(A, cell, f, job >= 0 ? &outs[job] : nullptr, rec);
+    if (f.need) {
+      atomicAdd(A.counters + C_REMAP, 1ull);
+      atomicAdd(A.counters + C_REMAP_E, (unsigned long long)f.ne);
+    }
+  }
+  if (A.rate_model == 2 && A.T_mode == 2) {
+    extern __shared__ __align__(1024) unsigned char fsm[];
+    fb_surrogate(A, cell, upd, rec, fsm);
   }
 }
 
@@ -1317,12 +1392,19 @@ __device__ __forceinline__ int electron_events(const StepArgs& A, uint32_t step,
   const float wvC = cc ? A.w_a * facC : A.w_a;
   const float wvB = cb ? A.w_a * facB : A.w_a;
   const uint32_t gcell = A.cell_base + (uint32_t)cell;
+  // the energies: the exact inverse CDFs (closed forms), the cell's spectral
+  // record, or the network's cell-independent quantiles
+  const float* q = nullptr;
+  if (A.rate_model) {
+    q = cell_sr(A, cell);
+    if (!q) q = A.ra.uni;
+  }
   for (int k = 0; k < K; ++k) {
     const uint4 r = philox4x32_10(make_uint4(step, gcell, (uint32_t)t.slot, (S_EV_E << 24) | (uint32_t)k), A.rk);
     const bool isC = u23(r.w) < fracC;
     const float3 dv = iso_dir(u23(r.x), u23(r.y));
-    const float E = (A.rate_model ? sr_sample_x(A.sr + (size_t)cell * kSrLen, isC ? 1 : 2, u23(r.z))
-                                  : icdf_lookup(A.tables + (isC ? TAB_COMPTON : TAB_BREMS) * kTableN, u23(r.z))) *
+    const float E = (q ? sr_sample_x(q, isC ? 1 : 2, u23(r.z))
+                       : icdf_lookup(A.tables + (isC ? TAB_COMPTON : TAB_BREMS) * kTableN, u23(r.z))) *
                     r_T;
     const float wv = isC ? wvC : wvB;
     const float pm = E * kInvMeC2f;
@@ -1980,7 +2062,9 @@ static cudaError_t launch_decide(const StepArgs& A, int phases, cudaStream_t st)
 }
 
 static cudaError_t launch_feedback(const StepArgs& A, cudaStream_t st) {
-  feedback_kernel<<<(A.ncells + kFeedbackThreads - 1) / kFeedbackThreads, kFeedbackThreads, 0, st>>>(A);
+  // the surrogate rate model runs the network in the feedback kernel
+  const int smem = A.rate_model == 2 && A.T_mode == 2 ? kNetSmemBytes : 0;
+  feedback_kernel<<<(A.ncells + kFeedbackThreads - 1) / kFeedbackThreads, kFeedbackThreads, smem, st>>>(A);
   return cudaGetLastError();
 }
 
@@ -2008,11 +2092,12 @@ cudaError_t decide_resident_ctas(int chunk, int* out) {
   return cudaSuccess;
 }
 
-// After the temperature update of an evolved-T step the spectral records are
-// rebuilt for the new T (rate models 1 and 2).
+// After the temperature update of an evolved-T step the table model's
+// spectral records are rebuilt for the new T (the surrogate model's are
+// rebuilt by the feedback kernel itself).
 static cudaError_t launch_records_update(const StepArgs& A, const SrArgs* sra, cudaStream_t st) {
-  if (!sra || A.T_mode != 2) return cudaSuccess;
-  return launch_sr_records(*sra, st);
+  if (!sra || A.T_mode != 2 || A.rate_model != 1) return cudaSuccess;
+  return launch_sr_table(*sra, st);
 }
 
 cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t st, cudaEvent_t* ev,

@@ -40,6 +40,9 @@ void sur_feature_xkt(const float* f4, double* x, double* kT);
 // with F the screening function of Sec. II.F. What is left of each
 // ln-emissivity is a function of the cell alone.
 double sur_shape(int o, double x, double kT, double a);
+// Whether output o of the model does not depend on the cell: the
+// Compton-like and bremsstrahlung quantiles (o = 33..63, 65..95).
+inline bool sur_universal_output(int o) { return o > 32 && o % 32 != 0; }
 // ncells random cells of the domain (T uniform, n_e log-uniform, Z in {1, 2};
 // only where both bremsstrahlung brackets are at least kSurBracketMin) with
 // xpc log-uniform x each: features X (rows x 4) and targets Y (rows x 96)

@@ -122,11 +122,14 @@ def config4(nboxes=4096, seed=0):
 
 def config5(n=256):
     """3-D 256^3, T = 5 keV, hydrogen n_e = 6e25 cm^-3, 64 electrons + 32
-    photons per cell, all channels, T evolved, dt = 5.448e11 s."""
+    photons per cell, all channels, T evolved, dt = 5.448e11 s. With w_a =
+    w_gamma the Primakoff exchange moves photons and axions between about 45
+    macroparticles a cell (plus the thermal-bath axions): slabs of 64 photon
+    and 64 axion slots keep the tails of 16.8 M cells."""
     ncells = n ** 3
     n_ion, Z, A = _hydrogen(ncells, 6e25)
-    return Workload("c5-3d-256^3", ncells, (n, n, n), np.full(ncells, 5.0), n_ion, Z, A, VOLUME_1UM3, 64, 32,
-                    0, (64, 48, 48),
+    return Workload("c5-3d-%d^3" % n, ncells, (n, n, n), np.full(ncells, 5.0), n_ion, Z, A, VOLUME_1UM3, 64, 32,
+                    0, (64, 64, 64),
                     params=dict(g_agg_GeV_inv=1e-10, g_ae=1e-13, dt_phys_s=5.448e11, T_mode=2, relax_r=0.1),
                     mask=7, steps=50, w_a_over_w_gamma=1.0)
 

@@ -19,15 +19,16 @@ def to_species(d):
     return ostep.Species(*[np.asarray(d[f], dtype=np.float64) for f in FIELDS])
 
 
-def oracle_step(cell_arrays, T, n_ion, Z, A, prm, step, gcell, mask, res=None, phases="step", rec=None):
+def oracle_step(cell_arrays, T, n_ion, Z, A, prm, step, gcell, mask, res=None, phases="step", rec=None, net=None):
     """Run the oracle's step on one cell's GPU arrays (rec: the oracle's own
-    spectral record for the table/surrogate rate models). Returns (parts,
-    tally, fb)."""
+    spectral record for the table rate model; net: the oracle network's
+    constants and quantile record for a cell the surrogate is trusted for).
+    Returns (parts, tally, fb)."""
     parts = {k: to_species(cell_arrays[k]) for k in "ega"}
     op = oracle_params(prm)
     ci = ostep.CellInput(T, np.asarray(n_ion), np.asarray(Z), np.asarray(A))
     res_E, res_P = (0.0, np.zeros(3)) if res is None else (res[0], np.asarray(res[1:4]))
-    tally, fb = ostep.step_cell(ci, parts, op, step, gcell, mask, res_E, res_P, rec=rec)
+    tally, fb = ostep.step_cell(ci, parts, op, step, gcell, mask, res_E, res_P, rec=rec, net=net)
     return parts, tally, fb
 
 

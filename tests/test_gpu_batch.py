@@ -117,27 +117,40 @@ def test_branched_replay_with_records_equals_step_calls(model):
     if model == 2:
         net = SurrogateNet()
         _lib.axpic_surrogate_fit(net.h, 2048, 1, 400, 2048, 2e-3, 5)
-        err = np.zeros(2 * 4 * 4 * 2, dtype=np.float32)
+        err = np.zeros(2 * 4 * 4 * 3, dtype=np.float32)
         for pl in (a, b):
-            _lib.axpic_set_surrogate(pl.ctx, net.h, err, 4, 4, 1.0)
+            _lib.axpic_set_surrogate(pl.ctx, net.h, err, 4, 4, 1.0, 1.0)
         net.close()
     for s in range(35):
         a.step(s, _lib.CH_ALL)
     b.run_steps(0, 35, _lib.CH_ALL)
     torch.cuda.synchronize()
     assert_same(state(a), state(b), "records of model %d" % model)
-    ra = _lib.axpic_get_spectral_records(a.ctx, 0, 600)
-    rb = _lib.axpic_get_spectral_records(b.ctx, 0, 600)
-    assert np.array_equal(ra, rb)
+    assert_same_records(a, b, 600)
     assert b.launch_shape()[2] == 3  # 600 cells in ranges of whole 128-cell CTAs: 256, 256, 88
     a.close()
     b.close()
 
 
+def rate_records(pl, n):
+    """Cell records, their sources and the spectral records of the cells
+    whose rates come from one (the others' are unused)."""
+    rec, src = _lib.axpic_get_cell_records(pl.ctx, 0, n)
+    sr = _lib.axpic_get_spectral_records(pl.ctx, 0, n)
+    sr[src == 0] = 0.0
+    return rec, src, sr
+
+
+def assert_same_records(a, b, n):
+    for x, y in zip(rate_records(a, n), rate_records(b, n)):
+        assert np.array_equal(x, y)
+
+
 def test_records_rebuilt_in_a_step_equal_a_rebuild_from_scratch():
-    """Cells whose trust changes as T evolves: the records the step rebuilds
-    (network first, then the table over the cells it left) equal the ones a
-    rebuild from scratch gives for the same temperatures."""
+    """Cells whose trust changes as T evolves: the records the feedback kernel
+    rebuilds after its temperature update (the network's prefactors where it
+    is trusted, the table's record elsewhere) equal the ones a rebuild from
+    scratch gives for the same temperatures."""
     from paper_2604_24627_gb300.mlp import SurrogateNet
     prm = base_params(rate_model=2, relax_r=1.0, sr_table_nkt=24, sr_table_nne=12)
     T = np.linspace(1.0, 7.0, 300)
@@ -145,17 +158,21 @@ def test_records_rebuilt_in_a_step_equal_a_rebuild_from_scratch():
     net = SurrogateNet()
     _lib.axpic_surrogate_fit(net.h, 2048, 1, 400, 2048, 2e-3, 5)
     nT, nne = 8, 4
-    err = np.zeros((2, nne, nT, 2), dtype=np.float32)
+    err = np.zeros((2, nne, nT, 3), dtype=np.float32)
     err[:, :, 3:5, 0] = 1.0  # an untrusted band of temperatures between two trusted ones: cells cross its borders
-    _lib.axpic_set_surrogate(pl.ctx, net.h, err.ravel(), nT, nne, 1e-3)
+    _lib.axpic_set_surrogate(pl.ctx, net.h, err, nT, nne, 1e-3, 1e-3)
     net.close()
+    _, src0 = _lib.axpic_get_cell_records(pl.ctx, 0, 300)
     for s in range(4):
         pl.step(s, _lib.CH_ALL)
     torch.cuda.synchronize()
-    in_step = _lib.axpic_get_spectral_records(pl.ctx, 0, 300)
+    in_step = rate_records(pl, 300)
+    assert np.any(in_step[1] != src0)  # some cells changed sides
+    assert 0 < in_step[1].sum() < 300
     _lib.axpic_update_cells(pl.ctx)
-    fresh = _lib.axpic_get_spectral_records(pl.ctx, 0, 300)
-    assert np.array_equal(in_step, fresh)
+    fresh = rate_records(pl, 300)
+    for x, y in zip(in_step, fresh):
+        assert np.array_equal(x, y)
     pl.close()
 
 
@@ -286,14 +303,24 @@ def test_c4_workload_slice_runs():
     pl.close()
 
 
-@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("model", [0, 1, 2])
 def test_steps_over_cell_ranges_equal_step_calls(model):
     """Each step run as ragged, disjoint cell ranges in a shuffled order
-    (axpic_step_cells; closed-form and exact-table rate models) gives what
-    plain step calls give; a range outside the context launches nothing."""
+    (axpic_step_cells; closed-form, exact-table and surrogate rate models)
+    gives what plain step calls give; a range outside the context launches
+    nothing."""
     prm = base_params(rate_model=model)
     caps = (64, 1024, 2048)
     a, b = make_h(300, prm, caps=caps), make_h(300, prm, caps=caps)
+    if model == 2:
+        from paper_2604_24627_gb300.mlp import SurrogateNet
+        net = SurrogateNet()
+        _lib.axpic_surrogate_fit(net.h, 2048, 1, 400, 2048, 2e-3, 5)
+        err = np.zeros((2, 4, 8, 3), dtype=np.float32)
+        err[:, :, 2:4, 0] = 1.0  # part of the cells on the table
+        for pl in (a, b):
+            _lib.axpic_set_surrogate(pl.ctx, net.h, err, 8, 4, 1e-3, 1e-3)
+        net.close()
     cuts = [0, 1, 128, 131, 257, 300]
     order = np.random.default_rng(5).permutation(len(cuts) - 1)
     for s in range(6):
@@ -303,6 +330,8 @@ def test_steps_over_cell_ranges_equal_step_calls(model):
         b.step_cells(s, 300, 0)
     torch.cuda.synchronize()
     assert_same(state(a), state(b), "cell ranges")
+    if model:
+        assert_same_records(a, b, 300)
     for args in ((0, 250, 51), (0, -1, 2), (-1, 0, 4)):
         with pytest.raises(_lib.AxpicError):
             b.step_cells(args[0], args[1], args[2])

@@ -31,32 +31,138 @@ def dev(a):
     return torch.tensor(np.asarray(a, np.float32), device="cuda:0")
 
 
+U = 2.0 ** -7   # one bfloat16 unit, relative (7 stored mantissa bits)
+TANH = 1e-6    # the kernels' activation: absolute error below 7e-7, plus binary32 rounding
+
+
+def forward_bound(P, X):
+    """Element-wise bound on |GPU output - oracle output| (see
+    gradient_bounds): the hidden activations one bfloat16 unit off, the tanh
+    error, FP32 accumulation, carried through |W2| and |W3|."""
+    q = S.bf16
+    acc = 64 * 2.0 ** -24
+    aW2, aW3 = np.abs(q(P["W2"])), np.abs(q(P["W3"]))
+    ah1 = np.abs(np.tanh(X @ P["W1"] + P["b1"]))
+    ah2 = np.abs(np.tanh(q(np.tanh(X @ P["W1"] + P["b1"])) @ q(P["W2"]) + P["b2"]))
+    dh2 = (U * ah1 + TANH) @ aW2 + acc * (ah1 @ aW2) + TANH
+    return (U * ah2 + dh2) @ aW3 + acc * (ah2 @ aW3)
+
+
 @pytest.mark.parametrize("n", [1, 127, 128, 300, 4096])
 def test_forward_matches_oracle(n):
+    """Every output within its bound (forward_bound); most rows meet the
+    oracle's bfloat16 operands exactly, so the typical output agrees to FP32
+    accumulation (median error 2e-5 of the largest output)."""
     P, X, _ = seeded(1, n)
     net = SurrogateNet()
     net.set_params(P)
     got = net.forward(dev(X)).cpu().numpy().astype(np.float64)
     want, _ = S.forward(P, X, bf16_mma=True)
     err = np.abs(got - want)
-    # FP32 accumulation against FP64; an occasional bfloat16 rounding flip of
-    # a hidden activation moves one output by ~1e-3
+    assert np.all(err <= forward_bound(P, X) + 1e-7), float((err - forward_bound(P, X)).max())
     assert np.median(err) <= 2e-5 * max(1.0, np.abs(want).max()), np.median(err)
-    assert err.max() <= 4e-3 * max(1.0, np.abs(want).max()), err.max()
     net.close()
+
+
+def gradient_bounds(P, X, Zt):
+    """Element-wise bounds on |GPU gradient - oracle gradient| that the
+    arithmetic allows, to first order: every rounded activation or gradient
+    operand of a tensor-core product one bfloat16 unit off on one side (the
+    sides round slightly different binary32 and FP64 values; the weights
+    round identically), every FP32 sum off by n 2^-24 of its absolute sum,
+    and the kernels' tanh off by TANH, carried through forward and
+    backward with absolute values."""
+    q = S.bf16
+    n = len(X)
+    acc = lambda m: m * 2.0 ** -24
+    W1, W2, W3 = P["W1"], P["W2"], P["W3"]
+    aW2, aW3 = np.abs(q(W2)), np.abs(q(W3))
+    h1 = np.tanh(X @ W1 + P["b1"])
+    dh1 = np.full_like(h1, TANH)
+    a2 = q(h1) @ q(W2) + P["b2"]
+    h2 = np.tanh(a2)
+    ah1, ah2 = np.abs(h1), np.abs(h2)
+    dh2 = (U * ah1 + dh1) @ aW2 + acc(64) * (ah1 @ aW2) + TANH
+    z = q(h2) @ q(W3) + P["b3"]
+    dzv = (U * ah2 + dh2) @ aW3 + acc(64) * (ah2 @ aW3)
+    g = 2.0 * (z - Zt) / n
+    ag = np.abs(g)
+    dg = 2.0 * dzv / n + 2.0 ** -23 * ag
+    B = {}
+    B["W3"] = (U * ah2 + dh2).T @ ag + ah2.T @ (U * ag + dg) + acc(n) * (ah2.T @ ag)
+    B["b3"] = dg.sum(0) + acc(n) * ag.sum(0)
+    d_h2 = q(g) @ q(W3).T
+    dd_h2 = (U * ag + dg) @ aW3.T + acc(96) * (ag @ aW3.T)
+    da2 = d_h2 * (1 - h2 ** 2)
+    ada2 = np.abs(da2)
+    dda2 = dd_h2 + np.abs(d_h2) * 2 * ah2 * dh2
+    B["W2"] = (U * ah1 + dh1).T @ ada2 + ah1.T @ (U * ada2 + dda2) + acc(n) * (ah1.T @ ada2)
+    B["b2"] = dda2.sum(0) + acc(n) * ada2.sum(0)
+    d_h1 = q(da2) @ q(W2).T
+    dd_h1 = (U * ada2 + dda2) @ aW2.T + acc(64) * (ada2 @ aW2.T)
+    da1 = d_h1 * (1 - h1 ** 2)
+    ada1 = np.abs(da1)
+    dda1 = dd_h1 + np.abs(d_h1) * 2 * ah1 * dh1
+    aX = np.abs(X)
+    B["W1"] = aX.T @ dda1 + acc(n) * (aX.T @ ada1)
+    B["b1"] = dda1.sum(0) + acc(n) * ada1.sum(0)
+    return B
 
 
 @pytest.mark.parametrize("n", [200, 1000])
 def test_gradients_match_oracle(n):
+    """Every gradient element within its bound from gradient_bounds, and the
+    typical element much closer (median relative error below 1e-3)."""
     P, X, Zt = seeded(2, n)
     net = SurrogateNet()
     net.set_params(P)
     loss, G = net.gradients(dev(X), dev(Zt))
     want = S.backward(P, X, Zt, bf16_mma=True)
+    B = gradient_bounds(P, X, Zt)
     assert abs(loss - S.loss(P, X, Zt, bf16_mma=True)) <= 1e-4 * loss
+    rel = []
     for k in want:
-        d = np.linalg.norm(G[k] - want[k])
-        assert d <= 5e-3 * np.linalg.norm(want[k]) + 1e-7, (k, d, np.linalg.norm(want[k]))
+        d = np.abs(G[k] - want[k])
+        bad = d > B[k] + 1e-12
+        assert not bad.any(), (k, int(bad.sum()), float((d - B[k]).max()))
+        big = np.abs(want[k]) > 1e-6 * np.abs(want[k]).max()
+        rel.append((d[big] / np.abs(want[k][big])).ravel())
+    assert np.median(np.concatenate(rel)) < 1e-3, np.median(np.concatenate(rel))
+    net.close()
+
+
+def test_adam_steps_match_oracle():
+    """Three training steps (gradients, then Adam with bias-corrected moments,
+    beta 0.9 and 0.999, eps 1e-8) from the same parameters as the oracle's
+    Adam (oracle.surrogate.adam) on the oracle's gradients: an element whose
+    gradient stays far above its rounding bound (10x) moves as the oracle's
+    within 1e-3 of the learning rate a step plus binary32 rounding; those are
+    at least 90 % of the parameters."""
+    P, X, Zt = seeded(5, 512)
+    net = SurrogateNet()
+    net.set_params(P)   # resets the Adam state
+    lr = 1e-3
+    Po = {k: v.copy() for k, v in P.items()}
+    M = {k: np.zeros_like(v) for k, v in P.items()}
+    V = {k: np.zeros_like(v) for k, v in P.items()}
+    clear = {k: np.ones(v.shape, dtype=bool) for k, v in P.items()}
+    Xd, Zd = dev(X), dev(Zt)
+    for t in range(1, 4):
+        G = S.backward(Po, X, Zt, bf16_mma=True)
+        B = gradient_bounds(Po, X, Zt)
+        for k in G:
+            clear[k] &= np.abs(G[k]) > 10 * B[k]
+        S.adam(Po, G, M, V, t, lr)
+        net.train_step(Xd, Zd, lr)
+    got = net.get_params()
+    frac = sum(c.sum() for c in clear.values()) / sum(c.size for c in clear.values())
+    assert frac >= 0.9, frac
+    for k in got:
+        d = np.abs(got[k] - Po[k])
+        tol = 3 * 1e-3 * lr + 4 * np.spacing(np.abs(Po[k]).astype(np.float32)).astype(np.float64)
+        bad = clear[k] & (d > tol)
+        assert not bad.any(), (k, int(bad.sum()), float(d[clear[k]].max()))
+        assert np.all(d <= 3 * 2 * lr + tol), k   # any element: at most the step size each step
     net.close()
 
 
@@ -88,8 +194,9 @@ def test_batches_that_grow_reuse_the_network():
         net.set_params(P)
         loss, G = net.gradients(dev(X), dev(Zt))
         want = S.backward(P, X, Zt, bf16_mma=True)
+        B = gradient_bounds(P, X, Zt)
         for k in want:
-            assert np.linalg.norm(G[k] - want[k]) <= 5e-3 * np.linalg.norm(want[k]) + 1e-7, (n, k)
+            assert np.all(np.abs(G[k] - want[k]) <= B[k] + 1e-12), (n, k)
         z = net.forward(dev(X)).cpu().numpy()
         zw, _ = S.forward(P, X, bf16_mma=True)
         assert np.median(np.abs(z - zw)) <= 2e-5 * max(1.0, np.abs(zw).max()), n

@@ -75,7 +75,31 @@ def test_table_record_at_a_node_is_the_node():
     ne = 1e26
     T = S.temperature(kT, ne, 1)
     rec = S.table_record(tab, T, kT * T, ne, 1, 1e-10, 1e-13, 1e12)
-    np.testing.assert_allclose(rec[:189], tab[0, 1, 1].astype(np.float64), rtol=1e-12)
+    node = tab[0, 1, 1].astype(np.float64)
+    np.testing.assert_allclose(rec[:64], node[:64], rtol=1e-12)
+    np.testing.assert_allclose(rec[96:189], node[96:189], rtol=1e-12)
+    # the bremsstrahlung row gets the brackets back: the exact targets (to the
+    # table's binary32 rounding)
+    want = np.log(S.emissivity("brems", S.X_GRID, T, ne, 1)) + S.X_GRID
+    np.testing.assert_allclose(rec[64:96], want, rtol=0, atol=2e-5)
+
+
+def test_table_brems_row_across_the_bracket_floor():
+    """Cells between nodes on either side of the brackets' floor: with the
+    brackets divided out of the table and restored per cell, the record's
+    bremsstrahlung row stays within 1e-3 on this coarse 12 x 8 table, where
+    interpolating the kinked ln Q_B itself is off by more than 1 in ln."""
+    nkt, nne = 12, 8
+    tab = S.build_table(nkt, nne)
+    worst = 0.0
+    for T in (0.55, 0.6, 0.7, 0.8):
+        for lne in (25.6, 25.75, 25.9, 25.97):
+            ne = 10 ** lne
+            kT = S.kappa_over_T(T, ne, 1)
+            rec = S.table_record(tab, T, kT * T, ne, 1, 1e-10, 1e-13, 1e12)
+            want = np.log(S.emissivity("brems", S.X_GRID, T, ne, 1)) + S.X_GRID
+            worst = max(worst, float(np.max(np.abs(rec[64:96] - want))))
+    assert worst < 1e-3, worst
 
 
 def test_oracle_step_with_exact_record_matches_closed_forms_statistically():

@@ -206,3 +206,32 @@ def test_adam_first_step():
     V = {"w": np.zeros(3)}
     S.adam(P, G, M, V, 1, 0.01)
     np.testing.assert_allclose(P["w"], [1.0 - 0.01, -2.0 + 0.01, 0.5 - 0.01], rtol=1e-6)
+
+
+@pytest.mark.parametrize("T,ne,Z", [(3.0, 6e25, 1), (1.4, 2e24, 2), (8.0, 5e23, 1)])
+def test_network_cell_state_with_exact_constants_is_the_closed_forms(T, ne, Z):
+    """The surrogate model's rates where the network is trusted keep the
+    closed functional forms with the network's per-cell constants as
+    prefactors: given the exact constants (the targets' ln-emissivity minus
+    the shape, the same at every x), network_cell_state gives back the
+    closed-form Gamma_0 (Eq. prim_rate), Q_C, Q_B and Gamma_C, Gamma_B
+    (Eqs. QC, GammaC and the text after eps_ee), for any coupling."""
+    A = K.A_H if Z == 1 else K.A_HE
+    p = plasma.Params(g_agg_GeV_inv=3e-10, g_ae=2e-13, dt_phys_s=1.0)
+    cs = plasma.cell_state(T, np.array([ne / Z]), np.array([float(Z)]), np.array([A]), p)
+    assert cs.eps_eZ > 0 and cs.eps_ee > 0  # brackets above their floors: the targets' floor is moot
+    kT = cs.kappa_keV / T
+    c = []
+    for x in (0.3, 2.0, 7.0):
+        X = S.features(x, kT, ne, Z)[None, :]
+        y = S.targets(x, kT, ne, Z)
+        c.append([y[o] - S.shape(X)[0, o] for o in (0, 32, 64)])
+    c = np.array(c)
+    np.testing.assert_allclose(c, np.broadcast_to(c[0], c.shape), rtol=0, atol=1e-10)
+    net = S.network_cell_state(cs, c[0], p)
+    for f in ("Gamma0_P", "Q_C", "Q_B", "Gamma_C", "Gamma_B"):
+        assert abs(getattr(net, f) / getattr(cs, f) - 1) < 1e-10, f
+    # and a constant off by d scales the channel's rate by e^d
+    net2 = S.network_cell_state(cs, c[0] + np.array([0.0, 0.0, 1e-3]), p)
+    assert abs(net2.Gamma_B / cs.Gamma_B - math.exp(1e-3)) < 1e-12
+    assert net2.Gamma_C == net.Gamma_C and net2.Gamma0_P == net.Gamma0_P
