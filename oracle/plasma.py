@@ -59,6 +59,7 @@ class Params:
     T_ceil_keV: float = 1e30
     T_mode: int = 0                   # 0 fixed, 1 prescribed field, 2 evolved
     seed: int = 0
+    axion_mass_keV: float = 0.0       # m_a c^2 (Sec. II.B); 0: massless
 
     @property
     def w_gref(self):

@@ -228,6 +228,40 @@ def _in_records(x):
     return (x >= 0.05) & (x <= 20.0)
 
 
+# ---------------------------------------------------------------- massive axions
+# Sec. II.B: an axion of momentum p carries E = sqrt(p^2 + m_a^2); the paper
+# implements finite-mass kinematics (modified emission thresholds and
+# absorption coefficients) without printing them. The readings:
+# * absorption and a->gamma act on an axion with the massless rates taken at
+#   its total energy E (the emission density and the equilibrium density both
+#   carry the axion phase-space factor beta = p/E, which cancels in
+#   Gamma_abs = (d ndot/dE) / (d n_eq/dE), Eq. gamma_abs); the a->gamma photon
+#   takes energy E along p;
+# * emission needs E >= m_a and carries beta: the massive process is the
+#   massless one thinned with acceptance beta(E). A thermal-bath event keeps
+#   its energy when u' < beta(E), u' the event's channel uniform rescaled
+#   inside the interval of its channel (uniform and independent of the
+#   channel choice); gamma->a converts at the rate beta(omega) Gamma and the
+#   axion takes E = omega and momentum beta p_gamma;
+# * the thermal-bath feedback exchanges the total energy E and the momentum p.
+# The thinning and the threshold are decided in binary32, as the kernel
+# decides them. With m_a = 0 every factor is exactly one and nothing is
+# thinned.
+
+def axion_energy_mc2(a: Species, mu):
+    """E / (m_e c^2) of axions, E = sqrt(p^2 + m_a^2); mu = m_a / m_e c^2."""
+    return np.sqrt(a.px ** 2 + a.py ** 2 + a.pz ** 2 + mu * mu)
+
+
+def beta32(e, mu):
+    """The axion phase-space factor p/E at energy e (m_e c^2 units) for mass
+    mu, in binary32: p = sqrt(max(e^2 - mu^2, 0)), 0 below threshold."""
+    e32 = f32(e)
+    m32 = F32(mu)
+    pm = np.sqrt(np.maximum((e32 * e32).astype(F32) - F32(m32 * m32), F32(0.0)).astype(F32)).astype(F32)
+    return (pm / np.where(e32 > 0, e32, F32(1.0))).astype(F32)
+
+
 def _absorb(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, rec=None):
     """Inverse operators on the axions present at the start of the step. With
     a spectral record (table or surrogate rate model) the Primakoff and
@@ -239,7 +273,8 @@ def _absorb(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally,
     new_g = Species.empty()
     if n == 0:
         return a, np.ones(0, dtype=bool), new_g
-    omega = a.pmag() * K.ME_C2_KEV
+    mu = p.axion_mass_keV / K.ME_C2_KEV
+    omega = axion_energy_mc2(a, mu) * K.ME_C2_KEV     # the total energy E
     w = a.w.copy()
     x = omega / cs.T_keV
     use = _in_records(x) if rec is not None else np.zeros(n, dtype=bool)
@@ -257,6 +292,10 @@ def _absorb(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally,
         tally.clamp_hits += int(over.sum())
         if Kc.sum() > 0:
             new_g = _repeat_products(a, Kc, wprod)
+            if mu > 0:  # the photon takes the energy E along p
+                pm = np.repeat(a.pmag(), Kc)
+                f = np.repeat(omega / K.ME_C2_KEV, Kc) / np.where(pm > 0, pm, 1.0)
+                new_g.px, new_g.py, new_g.pz = new_g.px * f, new_g.py * f, new_g.pz * f
     keep = w > 0
     want_c = bool(mask & CH_COMPTON)
     want_b = bool(mask & CH_BREMS)
@@ -327,12 +366,16 @@ def _emit(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, n
     if (mask & CH_PRIMAKOFF) and n_g0 > 0:
         g0 = g.take(np.arange(n_g0))
         omega = g0.pmag() * K.ME_C2_KEV
-        P = primakoff_prob(cs, p, omega)
+        mu = p.axion_mass_keV / K.ME_C2_KEV
+        beta = beta32(omega / K.ME_C2_KEV, mu).astype(np.float64) if mu > 0 else np.ones(n_g0)
+        s = 4.0 * omega ** 2 / cs.kappa_keV ** 2
+        gdt = cs.Gamma0_P * primakoff_F(s) * p.dt_phys_s
         if rec is not None:
             x = omega / cs.T_keV
             use = _in_records(x)
             if use.any():
-                P = np.where(use, -np.expm1(-surrogate.rec_prim_gdt(rec, np.where(use, x, 1.0))), P)
+                gdt = np.where(use, surrogate.rec_prim_gdt(rec, np.where(use, x, 1.0)), gdt)
+        P = -np.expm1(-beta * gdt)
         lam = g0.w * P / w_a
         lam_eff, fac, capped = cap_lambda(lam, p.lambda_cap)
         u = decision_uniforms(p, step, cell, STREAM_PRIM_FWD, n_g0)
@@ -342,6 +385,9 @@ def _emit(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, n
         tally.cap_hits += int(capped.sum())
         tally.clamp_hits += int(over.sum())
         prods = _repeat_products(g0, Kc, wprod)
+        if mu > 0:  # the axion takes E = omega and momentum beta p_gamma
+            bk = np.repeat(beta, Kc)
+            prods.px, prods.py, prods.pz = prods.px * bk, prods.py * bk, prods.pz * bk
         new_blocks.append(prods)
         chan_blocks.append(np.full(len(prods), CH_PRIMAKOFF))
         energy_blocks.append(np.repeat(omega, Kc))
@@ -381,8 +427,21 @@ def _emit(cs: CellState, parts, p: Params, step, cell, mask, tally: StepTally, n
             else:
                 xE = np.where(is_c, surrogate.rec_sample_x(qr, 1, uu[:, 2]), surrogate.rec_sample_x(qr, 2, uu[:, 2]))
             E = xE * cs.T_keV
+            mu = p.axion_mass_keV / K.ME_C2_KEV
+            if mu > 0:
+                # thinning with acceptance beta(E): the channel uniform
+                # rescaled inside its channel's interval, in binary32
+                u3 = f32(uu[:, 3])
+                fc = frac_c[parent]
+                ut = np.where(is_c, (u3 / np.where(fc > 0, fc, F32(1))).astype(F32),
+                              ((u3 - fc).astype(F32) / np.where(fc < 1, (F32(1) - fc).astype(F32), F32(1))).astype(F32))
+                e32 = (f32(E) * F32(1.0 / K.ME_C2_KEV)).astype(F32)
+                keep_ev = ut < beta32(e32, mu)
+                parent, sub, is_c, E, uu = parent[keep_ev], sub[keep_ev], is_c[keep_ev], E[keep_ev], uu[keep_ev]
+                pm = np.sqrt(np.maximum((E / K.ME_C2_KEV) ** 2 - mu * mu, 0.0))
+            else:
+                pm = E / K.ME_C2_KEV
             dx, dy, dz = isotropic(uu[:, 0], uu[:, 1])
-            pm = E / K.ME_C2_KEV
             fac = np.where(is_c, fac_c[parent], fac_b[parent])
             wv = f32(w_a * fac).astype(np.float64)
             prods = Species(wv, pm * dx, pm * dy, pm * dz, e.x[parent], e.y[parent], e.z[parent])

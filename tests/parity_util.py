@@ -8,7 +8,7 @@ from oracle.plasma import Params as OParams, cell_state
 FIELDS = ("w", "px", "py", "pz", "x", "y", "z")
 ORACLE_KEYS = ("g_agg_GeV_inv", "g_ae", "dt_phys_s", "w_a", "w_gamma_ref", "lambda_cap", "kappa_mode",
                "kappa_fixed_keV", "prim_targets", "prim_inverse_mult", "eq_stats", "brems_ee", "absorb_mode",
-               "brems_gamma_shape", "relax_r", "T_floor_keV", "T_ceil_keV", "T_mode", "seed")
+               "brems_gamma_shape", "relax_r", "T_floor_keV", "T_ceil_keV", "T_mode", "seed", "axion_mass_keV")
 
 
 def oracle_params(prm):
