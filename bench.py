@@ -115,7 +115,12 @@ def kernel_bytes(tot, T_mode):
         w, p and position read (28 B), each removed slot refilled (56 B);
       feedback: exchange, carried exchange, moments, count and T per cell
         (104 B), plus 80 B of record traffic in evolved-T mode, plus 28 B per
-        electron of remapped cells (w, p read, p written)."""
+        electron of remapped cells (w, p read, p written);
+      the surrogate network's record kernel (evolved T): the cell record
+        read (64 B), the five prefactors written (32 B, two 16-byte stores)
+        and the source byte;
+      the table's record kernel (evolved T): the cell record read (64 B) and
+        the 192-float spectral record written (768 B)."""
     cells = tot["cell_steps"]
     products = tot["events_p"] + tot["events_c"] + tot["events_b"] + tot["events_pinv"]
     removed = tot["events_p"] + tot["absorbed_c"] + tot["absorbed_b"] + tot["events_pinv"]
@@ -125,6 +130,8 @@ def kernel_bytes(tot, T_mode):
         "decide_kernel": 16.0 * tot["part_a"] + 16.0 * tot["part_g"] + 48.0 * cells,
         "event_kernel": parts / 8.0 + 40.0 * cells + 56.0 * products + 56.0 * removed,
         "feedback_kernel": (104.0 + (80.0 if T_mode == 2 else 0.0)) * cells + 28.0 * tot["remap_e"],
+        "sr_cells_kernel": 97.0 * cells,
+        "sr_table_kernel": 832.0 * cells,
     }
 
 
@@ -518,7 +525,7 @@ def run_three_models(args):
     """The 256^3 plasma (default) or the 512^2 temperature bump under the
     three rate models, one context at a time on the same seeded plasma:
     closed forms, the exact FP32 table, the surrogate network (trained and
-    validated on the GPU first; trusted where the four nodes of a 185 x 121
+    validated on the GPU first; trusted where the four nodes of a 369 x 241
     validation grid, log-spaced in T and n_e, around a cell are within
     TRUST_TOL on the rates and 1e-3 on the sampled quantiles). Each model: W
     warm-up steps through
@@ -543,9 +550,12 @@ def run_three_models(args):
     net = SurrogateNet(stream=stream)
     fit_loss = _lib.axpic_surrogate_fit(net.h, 65536, 1, 40000, 8192, 2e-3, 7)
     fit_s = time.time() - t0
-    nT, nne = 185, 121
+    nT, nne = 369, 241
+    t0 = time.time()
     verr = _lib.axpic_surrogate_validate(net.h, nT, nne)
+    val_s = time.time() - t0
     network = {"fit_seconds": fit_s, "fit_loss": fit_loss, "params": 10720, "validation_grid": [nT, nne, 2],
+               "validation_seconds": val_s,
                "validated_rate_err_median": float(np.median(verr[..., 0])),
                "validated_rate_err_max": float(verr[..., 0].max()),
                "validated_sampled_quantile_err_max": float(verr[..., 1].max()),
@@ -676,7 +686,7 @@ def run_three_models(args):
             "rate_models": lines,
             "surrogate_vs_table": lines["surrogate"]["particle_steps_per_s"] / lines["table"]["particle_steps_per_s"],
             "network": network,
-            "gpu_launches": 3 * h["branches"] * args.steps + 1, "clocks": h["clk"]}
+            "gpu_launches": len(h["kms"]) * h["branches"] * args.steps + 1, "clocks": h["clk"]}
     if "e2e" in h:
         line["e2e"] = h["e2e"]
         line["e2e"]["sample"] = "cells [0, %d) of the plasma, the surrogate model" % h["e2e"]["cells"]

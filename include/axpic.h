@@ -129,9 +129,10 @@ typedef struct {
                                constants set the prefactors of every rate's
                                closed functional form (emission, absorption,
                                Primakoff both ways) and its quantiles the
-                               emission energies, evaluated by the feedback
-                               kernel after each temperature update; the
-                               table's records elsewhere. Models 1 and 2 need
+                               emission energies, evaluated by the network
+                               kernel (sr_cells_kernel) right after each
+                               temperature update; the table's records
+                               elsewhere. Models 1 and 2 need
                                one ion species with Z in {1, 2}, Debye
                                screening and ions as Primakoff targets. Not
                                part of the paper's method. */
@@ -146,6 +147,18 @@ typedef struct {
                                rebuilds its own records). Results do not
                                depend on it. Not part of the paper's method. */
   int32_t reserved[2];
+  double axion_mass_keV;    /* m_a c^2 (Sec. II.B: E = sqrt(p^2 + m_a^2)); 0
+                               (default): massless. Axions are absorbed and
+                               convert a->gamma at the massless rates of their
+                               total energy E (the a->gamma photon takes E
+                               along p); emission needs E > m_a and is thinned
+                               with acceptance beta = p/E (thermal-bath events
+                               by their channel uniform rescaled in its
+                               channel's interval; gamma->a at beta(omega)
+                               times the rate, the axion taking momentum
+                               beta p_gamma); the thermal-bath feedback
+                               exchanges E and p. Streaming takes its own
+                               mass argument (axpic_stream_axions). */
 } axpic_params;
 
 /* Number of doubles written by axpic_tally_spectrum into totals_out. */
@@ -363,8 +376,11 @@ axpic_status axpic_tally_spectrum(axpic_ctx *ctx, int32_t nbins, double *H_out,
 
 /* Deterministic rates for one cell, for checking (Eqs. prim_prob,
  * gamma_abs): for each of n energies E_keV[i] (device) writes four binary32
- * values to out[4*i..4*i+3] (device): P_{gamma->a}, P_{a->gamma},
- * Gamma_abs,C dt and Gamma_abs,B dt. Enqueued on the stream. */
+ * values to out[4*i..4*i+3] (device): P_{gamma->a} (of a photon of energy
+ * E; times beta(E) for a massive axion), P_{a->gamma} and Gamma_abs,C dt,
+ * Gamma_abs,B dt (of an axion of total energy E), from the cell record's
+ * prefactors (the closed forms; the network's where rate model 2 trusts
+ * it; spectral records are not consulted). Enqueued on the stream. */
 axpic_status axpic_eval_rates(axpic_ctx *ctx, int32_t cell, const float *E_keV, int32_t n,
                               float *out);
 
@@ -417,8 +433,9 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc *desc, const axpic_param
 
 /* Runs nsteps full steps (as axpic_step with steps first_step,
  * first_step + 1, ...) by replaying CUDA graphs of 32 steps and of one step
- * (for the remainder): the decision, event and feedback kernels, with the
- * step index read from device counters that the feedback kernels advance.
+ * (for the remainder): the decision, event and feedback kernels (and, with
+ * evolved T, the rate model's record kernel), with the step index read from
+ * device counters that the feedback kernels advance.
  * Inside a graph the cells run as step_branches independent ranges on forked
  * streams, each range with its own counter, joined at the graph's end. Both
  * graphs are captured on the first call for a channel mask, whatever its
@@ -434,7 +451,7 @@ axpic_status axpic_run_steps(axpic_ctx *ctx, int64_t first_step, int32_t nsteps,
 /* The context's launch shape: cells per decision chunk, warps per event CTA
  * and the branches a replayed step runs its cells as (each may be NULL).
  * A replayed step launches 3 x branches kernels (decision, event, feedback
- * per branch). AXPIC_E_INVALID for a NULL context. Not part of the paper's
+ * per branch; 4 x branches with a rate model's record kernel). AXPIC_E_INVALID for a NULL context. Not part of the paper's
  * method. */
 axpic_status axpic_launch_shape(const axpic_ctx *ctx, int32_t *decide_chunk, int32_t *event_warps,
                                 int32_t *step_branches);
@@ -467,14 +484,15 @@ axpic_status axpic_profile_begin(axpic_ctx *ctx, int32_t max_steps);
 axpic_status axpic_profile_end(axpic_ctx *ctx, double *ms_out, int32_t *steps_out);
 
 /* Comma-separated names of the kernels that one axpic_step launches, in
- * launch order (decisions, events, feedback). The string is static; "" for a
- * NULL context. */
+ * launch order: decisions, events, feedback, then, with evolved T, the rate
+ * model's record kernel (sr_table_kernel for the table model, sr_cells_kernel
+ * for the surrogate). The string is static; "" for a NULL context. */
 const char *axpic_step_kernel_names(const axpic_ctx *ctx);
 
 /* ---------------------------------------------------------------------------
  * The spectral surrogate's network: MLP 4 -> 64 -> 64 -> 96 with tanh hidden
- * layers (tanh(v) = 1 - 2 / (e^(2v) + 1) in binary32, absolute error below
- * 7e-7), FP32 master parameters, bfloat16 tensor-core products with FP32
+ * layers (the hardware's binary32 tanh approximation, relative error below
+ * 1e-5, in training, validation and inference), FP32 master parameters, bfloat16 tensor-core products with FP32
  * accumulation (layers 2 and 3 and every backward product; layer 1, K = 4,
  * on the CUDA cores). Not part of the paper's method: a learned stand-in for
  * the per-channel spectral emissivity and inverse CDF (see

@@ -54,7 +54,8 @@ class Params(ctypes.Structure):
                 ("tally_enable", ctypes.c_int32), ("diag_enable", ctypes.c_int32),
                 ("threads_per_block", ctypes.c_int32), ("decide_chunk", ctypes.c_int32),
                 ("rate_model", ctypes.c_int32), ("sr_table_nkt", ctypes.c_int32), ("sr_table_nne", ctypes.c_int32),
-                ("step_branches", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("step_branches", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
+                ("axion_mass_keV", ctypes.c_double)]
 
 
 class AxpicError(RuntimeError):

@@ -121,7 +121,7 @@ struct axpic_ctx {
   float ln_gP = 0.f, ln_gA = 0.f, lnK_CC = 0.f, lnK_CB = 0.f;
   int64_t last_absorb_step = -1;
   std::string last_error;
-  std::vector<cudaEvent_t> prof_events;  // 5 per recorded step, created by axpic_profile_begin
+  std::vector<cudaEvent_t> prof_events;  // kStepKernels + 1 per recorded step, created by axpic_profile_begin
   int prof_max = 0, prof_used = 0;
 };
 
@@ -174,6 +174,13 @@ static std::string check_species(const axpic_species& s, const char* name) {
 // The checks every entry point that takes a plasma description and options
 // makes before launching anything: an empty string when they hold, else
 // what failed.
+// Words of the decision bit masks: per cell, a row per species (a bit per
+// slot).
+static size_t mask_words(const axpic_plasma_desc& d) {
+  const size_t n = (size_t)std::max(d.ncells, 0);
+  return n * ((d.axions.capacity + 31) / 32 + (d.photons.capacity + 31) / 32 + (d.electrons.capacity + 31) / 32);
+}
+
 static std::string check_plasma(const axpic_plasma_desc& d, const axpic_params& p) {
   if (d.ncells < 0) return "ncells < 0";
   if (d.nspecies < 1 || d.nspecies > kMaxSpecies) return "nspecies must be in 1..8";
@@ -201,6 +208,7 @@ static std::string check_plasma(const axpic_plasma_desc& d, const axpic_params& 
   if (!(p.T_floor_keV <= p.T_ceil_keV)) return "T_floor_keV > T_ceil_keV";
   if (p.tally_nbins < 1 || !(p.tally_Emax_keV > 0)) return "tally_nbins >= 1 and tally_Emax_keV > 0";
   if (!(p.prim_inverse_mult >= 0)) return "prim_inverse_mult must be >= 0";
+  if (!(p.axion_mass_keV >= 0) || !std::isfinite(p.axion_mass_keV)) return "axion_mass_keV must be finite and >= 0";
   return "";
 }
 
@@ -330,6 +338,8 @@ static StepArgs make_args(axpic_ctx* ctx, int64_t step, int mask) {
   A.step_dev = nullptr;
   A.rate_model = ctx->prm.rate_model;
   A.ra = make_record_args(ctx);
+  A.mu = (float)(p.axion_mass_keV / kMeC2);
+  A.mu2 = A.mu * A.mu;
   A.guard_margin = ctx->prm.rate_model ? 1.05f : 1.0f;
   A.cc = ctx->cc;
   return A;
@@ -518,8 +528,7 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
   }
   ALLOC(ctx->err, sizeof(int));
   ALLOC(ctx->scratch, sizeof(double) * (8 + kNumCounters + (size_t)kInfoChunk * AXPIC_CELL_INFO_LEN));
-  const size_t bit_words = (size_t)n * ((d.axions.capacity + 31) / 32 + (d.photons.capacity + 31) / 32 +
-                                        (d.electrons.capacity + 31) / 32);
+  const size_t bit_words = mask_words(d);
   ALLOC(ctx->bits, sizeof(uint32_t) * bit_words);
   ALLOC(ctx->recA, sizeof(uint4) * (size_t)n * d.axions.capacity);
   ALLOC(ctx->recG, sizeof(uint4) * (size_t)n * d.photons.capacity);
@@ -762,8 +771,9 @@ axpic_status axpic_eval_rates(axpic_ctx* ctx, int32_t cell, const float* E_keV, 
   if (!ctx) return AXPIC_E_INVALID;
   if (cell < 0 || cell >= ctx->desc.ncells || n < 0 || (n > 0 && (!E_keV || !out)))
     return fail(ctx, AXPIC_E_INVALID, "axpic_eval_rates: bad cell, count or pointer");
+  const float mu = (float)(ctx->prm.axion_mass_keV / kMeC2);
   CK(launch_rates(ctx->rec, cell, E_keV, n, ctx->prm.eq_stats, (float)(ctx->prm.brems_gamma_shape - 3.0),
-                  ctx->cc.prim_mult, out, ctx->stream),
+                  ctx->cc.prim_mult, mu * mu, out, ctx->stream),
      "rates");
   return AXPIC_OK;
 }
@@ -822,6 +832,7 @@ axpic_status axpic_profile_begin(axpic_ctx* ctx, int32_t max_steps) {
 axpic_status axpic_profile_end(axpic_ctx* ctx, double* ms_out, int32_t* steps_out) {
   if (!ctx || !ms_out) return AXPIC_E_INVALID;
   CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  static_assert(kStepKernels <= AXPIC_PROFILE_SLOTS, "profile slots");
   for (int k = 0; k < AXPIC_PROFILE_SLOTS; ++k) ms_out[k] = 0.0;
   for (int s = 0; s < ctx->prof_used; ++s) {
     const cudaEvent_t* ev = ctx->prof_events.data() + (kStepKernels + 1) * s;
@@ -1008,8 +1019,7 @@ static std::vector<std::pair<void*, size_t>> state_buffers(axpic_ctx* ctx, bool 
     }
     b.emplace_back(d.T_keV, n * sizeof(double));
   }
-  const size_t bit_words = n * ((d.axions.capacity + 31) / 32 + (d.photons.capacity + 31) / 32 +
-                                (d.electrons.capacity + 31) / 32);
+  const size_t bit_words = mask_words(d);
   b.emplace_back(ctx->rec, n * kRecLen * sizeof(float));
   b.emplace_back(ctx->mom, n * kMomLen * sizeof(float));
   b.emplace_back(ctx->xbuf, n * 4 * sizeof(double));
@@ -1343,7 +1353,7 @@ axpic_status axpic_get_spectral_records(axpic_ctx* ctx, int32_t first, int32_t c
 }
 
 const char* axpic_step_kernel_names(const axpic_ctx* ctx) {
-  return ctx ? step_kernel_names() : "";
+  return ctx ? step_kernel_names(ctx->prm.rate_model, ctx->prm.T_mode) : "";
 }
 
 axpic_status axpic_sync(axpic_ctx* ctx) {
@@ -1406,9 +1416,7 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc* desc, const axpic_param
   if (p.rate_model != 0) return bad("rate_model must be 0 (the records need a context)");
   const size_t per_warp = step_smem_per_warp(d.axions.capacity, d.photons.capacity, d.electrons.capacity);
   if (per_warp * kNoAllocWarps > 227 * 1024 - 128) return bad("slab capacities too large");
-  const size_t bit_bytes = sizeof(uint32_t) * (size_t)d.ncells *
-                           ((d.axions.capacity + 31) / 32 + (d.photons.capacity + 31) / 32 +
-                            (d.electrons.capacity + 31) / 32);
+  const size_t bit_bytes = sizeof(uint32_t) * mask_words(d);
   if (bit_bytes > kNaBitsBytes) return bad("ncells * (capacities) / 8 above the 4 MiB mask scratch");
   const size_t rec_bytes = (size_t)d.ncells * (16 * ((size_t)d.axions.capacity + d.photons.capacity) +
                                                4 * (size_t)d.electrons.capacity);

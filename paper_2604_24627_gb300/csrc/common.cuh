@@ -328,6 +328,16 @@ __device__ __forceinline__ CellExtras compute_temperature(const CellConst& cc, f
   return ex;
 }
 
+// Massive axions (Sec. II.B: E = sqrt(p^2 + m_a^2)): the axion phase-space
+// factor p/E at energy e (m_e c^2 units) for mass mu (mu2 = mu mu, both
+// binary32), p = sqrt(max(e^2 - mu^2, 0)): 0 at and below the threshold.
+// It thins emission (the massive process is the massless one kept with
+// probability beta) and carries gamma->a's product momentum.
+__device__ __forceinline__ float axion_beta(float e, float mu2) {
+  const float pm = sqrtf(fmaxf(__fsub_rn(__fmul_rn(e, e), mu2), 0.0f));
+  return e > 0.0f ? __fdiv_rn(pm, e) : 0.0f;
+}
+
 // Primakoff conversion probability over one step (Eqs. prim_xs to
 // prim_prob): P = 1 - exp(-A F(4 omega^2 / kappa^2)), A = R_AP or R_APINV.
 __device__ __forceinline__ float prim_prob(const float* rec, float omega, float A) {
@@ -392,6 +402,9 @@ struct StepArgs {
   // network where it is trusted, the table's records elsewhere
   int rate_model;
   RecordArgs ra;
+  // axion mass m_a / m_e c^2 and its square (binary32); 0: massless, and every
+  // mass factor is skipped
+  float mu, mu2;
   float guard_margin;  // factor on the no-event bounds (covers the records' error)
   CellConst cc;
 };

@@ -246,23 +246,25 @@ cudaError_t launch_sample(const SampleArgs& S, cudaStream_t st) {
 
 // ---------------------------------------------------------------- rates
 __global__ void rates_kernel(const float* __restrict__ rec_all, int cell, const float* __restrict__ E, int n,
-                             int eq_stats, float am3, float prim_mult, float* out) {
+                             int eq_stats, float am3, float prim_mult, float mu2, float* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float rec[kRecLen];
   for (int k = 0; k < kRecLen; ++k) rec[k] = rec_all[(size_t)cell * kRecLen + k];
   const float om = E[i];
   const float x = om * rec[R_INVT];
-  out[4 * i + 0] = prim_prob(rec, om, rec[R_AP]);
+  // gamma->a of a massive axion: beta(omega) times the rate (1 when massless)
+  const float beta = mu2 > 0.f ? axion_beta(om * kInvMeC2f, mu2) : 1.0f;
+  out[4 * i + 0] = prim_prob(rec, om, beta * rec[R_AP]);
   out[4 * i + 1] = prim_prob(rec, om, prim_mult * rec[R_AP]);
   out[4 * i + 2] = tau_compton(rec, x, eq_stats);
   out[4 * i + 3] = tau_brems(rec, x, am3, eq_stats);
 }
 
 cudaError_t launch_rates(const float* rec, int cell, const float* E, int n, int eq_stats, float am3, float prim_mult,
-                         float* out, cudaStream_t st) {
+                         float mu2, float* out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  rates_kernel<<<(n + 255) / 256, 256, 0, st>>>(rec, cell, E, n, eq_stats, am3, prim_mult, out);
+  rates_kernel<<<(n + 255) / 256, 256, 0, st>>>(rec, cell, E, n, eq_stats, am3, prim_mult, mu2, out);
   return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ cudaError_t launch_info(int first, int count, const CellConst& cc, double k_gamm
 cudaError_t launch_moments(int ncells, const SpeciesPtrs& e, float* mom, cudaStream_t st);
 cudaError_t launch_sample(const SampleArgs& S, cudaStream_t st);
 cudaError_t launch_rates(const float* rec, int cell, const float* E, int n, int eq_stats, float am3, float prim_mult,
-                         float* out,
+                         float mu2, float* out,
                          cudaStream_t st);
 cudaError_t launch_totals(int ncells, const SpeciesPtrs& e, const SpeciesPtrs& g, const SpeciesPtrs& a,
                           const double* res, const unsigned long long* ctr, int ctr_rows, double* out8,

@@ -10,10 +10,10 @@
 // they become the prefactors of the closed functional forms in the cell
 // record (srnet.cuh). Cells whose (T, n_e, Z) lies outside the region where
 // the network's validated error is within the bound get the table's
-// spectral record instead, written by the same CTA. During evolved-T steps
-// the feedback kernel does this right after each temperature update; the
-// kernel here builds the records at set-up and after the caller changes T
-// or the composition.
+// spectral record instead, written by the same CTA. The kernel runs right
+// after the feedback kernel of every evolved-T step (the records then hold
+// the new temperature with closed-form prefactors), at set-up, and after the
+// caller changes T or the composition.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -24,6 +24,7 @@
 #include "mlp.h"
 #include "sr.h"
 #include "srnet.cuh"
+#include "step.h"
 #include "surrogate.h"
 
 namespace axpic {
@@ -87,63 +88,74 @@ cudaError_t launch_sr_table(const SrArgs& a, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- surrogate model
-// CTA = 128 cells, thread t = cell cell0 + 128 b + t = tensor-core row t. The
-// network runs when the CTA has a trusted cell; trusted cells get their rate
-// prefactors, the others the table record (a warp per cell, written after
-// the network).
+// A persistent grid: each CTA sets the network up once (tensor memory, the
+// weights' image in shared memory) and takes tiles of 128 consecutive cells,
+// thread t = cell t of the tile = tensor-core row t. The network runs for a
+// tile that has a trusted cell; trusted cells get their rate prefactors,
+// the others the table record (a warp per cell, after the network).
 __global__ void __launch_bounds__(kNetThreads) sr_cells_kernel(SrArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ NetShared ns;
   __shared__ int list[kNetThreads];
   __shared__ int nlist;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int cell = a.cell0 + blockIdx.x * kNetThreads + tid;
-  const bool valid = cell < a.cell0 + a.ncells;
-  if (tid == 0) nlist = 0;
-  float r[kRecLen];
-  SrCellIn ci = {1.f, 1.f, 0.f, 24.f, 0.f};
-  bool trusted = false;
-  if (valid) {
-    const float4* r4 = reinterpret_cast<const float4*>(a.rec + (size_t)cell * kRecLen);
+  const int ntiles = (a.ncells + kNetThreads - 1) / kNetThreads;
+  const bool net = a.ra.trust != nullptr;
+  if (net) net_begin(&ns, sm, a.ra.img);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int cell = a.cell0 + tile * kNetThreads + tid;
+    const bool valid = cell < a.cell0 + a.ncells;
+    if (tid == 0) nlist = 0;
+    float r[kRecLen];
+    SrCellIn ci = {1.f, 1.f, 0.f, 24.f, 0.f};
+    bool trusted = false;
+    if (valid) {
+      const float4* r4 = reinterpret_cast<const float4*>(a.rec + (size_t)cell * kRecLen);
 #pragma unroll
-    for (int i = 0; i < kRecLen / 4; ++i) {
-      const float4 v = r4[i];
-      r[4 * i] = v.x;
-      r[4 * i + 1] = v.y;
-      r[4 * i + 2] = v.z;
-      r[4 * i + 3] = v.w;
+      for (int i = 0; i < kRecLen / 4; ++i) {
+        const float4 v = r4[i];
+        r[4 * i] = v.x;
+        r[4 * i + 1] = v.y;
+        r[4 * i + 2] = v.z;
+        r[4 * i + 3] = v.w;
+      }
+      ci = sr_cell_from(r, a.ra.k_T7);
+      trusted = net && sr_trusted(a.ra, ci.T, ci.lne);
     }
-    ci = sr_cell_from(r, a.ra.k_T7);
-    trusted = a.ra.trust && sr_trusted(a.ra, ci.T, ci.lne);
-  }
-  __syncthreads();
-  if (__syncthreads_or(trusted)) {
-    float c[3];
-    const bool ok = net_rows(sm, a.ra.img, net_f1(ci.lkT), net_f2(ci.lne), a.ra.Z - 1.5f, c, a.err);
-    trusted = trusted && ok;
-    if (trusted) {
-      net_prefactors(a.ra, c, ci.T, r[R_NE], r);
-      float4* o = reinterpret_cast<float4*>(a.rec + (size_t)cell * kRecLen);
-      o[0] = make_float4(r[0], r[1], r[2], r[3]);
-      o[1] = make_float4(r[4], r[5], r[6], r[7]);
+    if (__syncthreads_or(trusted)) {
+      float c[3];
+      const bool ok = net_rows(&ns, sm, net_f1(ci.lkT), net_f2(ci.lne), a.ra.Z - 1.5f, c, a.err);
+      trusted = trusted && ok;
+      if (trusted) {
+        net_prefactors(a.ra, c, ci.T, r[R_NE], r);
+        float4* o = reinterpret_cast<float4*>(a.rec + (size_t)cell * kRecLen);
+        o[0] = make_float4(r[0], r[1], r[2], r[3]);
+        o[1] = make_float4(r[4], r[5], r[6], r[7]);
+      }
     }
+    if (valid) {
+      a.ra.src[cell] = trusted ? 0 : 1;
+      if (!trusted) list[atomicAdd(&nlist, 1)] = tid;
+    }
+    __syncthreads();
+    const int n = nlist;
+    for (int k = warp; k < n; k += kNetThreads / 32) {
+      const int c = a.cell0 + tile * kNetThreads + list[k];
+      const SrCellIn cc = sr_cell_from(a.rec + (size_t)c * kRecLen, a.ra.k_T7);
+      sr_table_record_warp(a.ra, cc, a.ra.sr + (size_t)c * kSrLen, lane);
+    }
+    __syncthreads();  // the list and nlist are reused by the next tile
   }
-  if (valid) {
-    a.ra.src[cell] = trusted ? 0 : 1;
-    if (!trusted) list[atomicAdd(&nlist, 1)] = tid;
-  }
-  __syncthreads();
-  const int n = nlist;
-  for (int k = warp; k < n; k += kNetThreads / 32) {
-    const int t = list[k];
-    const int c = a.cell0 + blockIdx.x * kNetThreads + t;
-    const SrCellIn cc = sr_cell_from(a.rec + (size_t)c * kRecLen, a.ra.k_T7);
-    sr_table_record_warp(a.ra, cc, a.ra.sr + (size_t)c * kSrLen, lane);
-  }
+  if (net) net_end(&ns);
 }
+
+static int g_sr_cells_grid = 0;
 
 cudaError_t launch_sr_cells(const SrArgs& a, cudaStream_t st) {
   if (a.ncells <= 0) return cudaSuccess;
-  sr_cells_kernel<<<(a.ncells + kNetThreads - 1) / kNetThreads, kNetThreads, kNetSmemBytes, st>>>(a);
+  const int ntiles = (a.ncells + kNetThreads - 1) / kNetThreads;
+  const int grid = std::max(1, std::min(ntiles, g_sr_cells_grid > 0 ? g_sr_cells_grid : ntiles));
+  sr_cells_kernel<<<grid, kNetThreads, kNetSmemBytes, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -153,8 +165,17 @@ cudaError_t launch_sr_records(int model, const SrArgs& a, cudaStream_t st) {
   return cudaSuccess;
 }
 
+// The persistent grid: as many CTAs as the device holds at once (worked out
+// from the kernel's registers and shared memory: 7 an SM on a GB300), at
+// most 8 an SM (64 of the 512 tensor-memory columns each).
 cudaError_t sr_init_kernels() {
-  return cudaFuncSetAttribute(sr_cells_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kNetSmemBytes);
+  const cudaError_t e =
+      cudaFuncSetAttribute(sr_cells_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kNetSmemBytes);
+  if (e) return e;
+  const int n = resident_ctas((const void*)sr_cells_kernel, kNetThreads, kNetSmemBytes, 8);
+  if (n <= 0) return cudaErrorUnknown;
+  g_sr_cells_grid = n;
+  return cudaSuccess;
 }
 
 // ---------------------------------------------------------------- network image

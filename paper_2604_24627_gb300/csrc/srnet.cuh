@@ -1,7 +1,6 @@
 // The spectral surrogate's network evaluated for a CTA of 128 cells, one
-// tensor-core row per cell (internal to libaxpic; used by the feedback kernel,
-// which runs it right after the temperature update, and by the record
-// kernel of rate model 2).
+// tensor-core row per cell (internal to libaxpic; used by the record kernel
+// of rate model 2, sr_cells_kernel).
 //
 // The model's ln-emissivity outputs are y_c(x) = shape_c(x, kappa/T) + c_c,
 // with shape_c each channel's exact x-dependence and c_c = mu + S f + sigma z
@@ -66,29 +65,53 @@ __device__ __forceinline__ void net_store8(__nv_bfloat16* base, int r, int j0, c
 __device__ __forceinline__ float net_f1(float lkT) { return (lkT - kSrLnKt0) / kSrLnKtSpan * 2.0f - 1.0f; }
 __device__ __forceinline__ float net_f2(float lne) { return (lne - 24.5f) / 1.5f; }
 
-// Runs the network for the CTA's 128 rows (thread t = row t; all 128
-// threads must call it, with blockDim.x == 128). sm: kNetSmemBytes of shared
-// memory, 1024-byte aligned. Returns, CTA-uniformly, whether the tensor-core
-// waits completed; then c[0..2] hold this row's constants c_P, c_C, c_B.
-// On a wait that ran out it sets bit 2 of *err and returns false.
-static __device__ __noinline__ bool net_rows(unsigned char* sm, const unsigned char* __restrict__ img, float f1, float f2,
-                                      float f3, float* c, int* err) {
-  __shared__ uint64_t bar;
-  __shared__ uint32_t tmem_base;
+// The CTA's network state: the mbarrier the tensor-core products commit to,
+// the tensor-memory columns, and whether a wait ever ran out (then the
+// network is not used again by this CTA).
+struct NetShared {
+  uint64_t bar;
+  uint32_t tmem;
+  int broken;
+};
+
+// Set-up, once per CTA (all threads; blockDim.x == 128): 64 tensor-memory
+// columns, the mbarrier, and the image copied into sm + kNetActBytes (sm:
+// kNetSmemBytes of shared memory, 1024-byte aligned).
+__device__ __forceinline__ void net_begin(NetShared* ns, unsigned char* sm, const unsigned char* __restrict__ img) {
+  const int tid = threadIdx.x;
+  if ((tid >> 5) == 0) tmem_alloc(&ns->tmem, 64);
+  if (tid == 0) {
+    mbar_init(&ns->bar, 1);
+    ns->broken = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  const uint4* s = reinterpret_cast<const uint4*>(img);
+  uint4* d = reinterpret_cast<uint4*>(sm + kNetActBytes);
+  for (int i = tid; i < kNetImgBytes / 16; i += kNetThreads) d[i] = __ldg(s + i);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+// Release, once per CTA (all threads).
+__device__ __forceinline__ void net_end(NetShared* ns) {
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if ((threadIdx.x >> 5) == 0) tmem_free(ns->tmem, 64);
+}
+
+// The network for the CTA's 128 rows (thread t = row t; all threads call
+// it). Returns, CTA-uniformly, whether the tensor-core waits completed; then
+// c[0..2] hold this row's constants c_P, c_C, c_B. A wait that runs out sets
+// bit 4 of *err, marks the CTA's network broken and returns false. Every
+// call that returns true committed twice to the mbarrier (parities 0 then 1).
+static __device__ __noinline__ bool net_rows(NetShared* ns, unsigned char* sm, float f1, float f2, float f3, float* c,
+                                             int* err) {
   __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(sm);
   unsigned char* si = sm + kNetActBytes;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp == 0) tmem_alloc(&tmem_base, 64);
-  if (tid == 0) {
-    mbar_init(&bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  {
-    const uint4* s = reinterpret_cast<const uint4*>(img);
-    uint4* d = reinterpret_cast<uint4*>(si);
-    for (int i = tid; i < kNetImgBytes / 16; i += kNetThreads) d[i] = __ldg(s + i);
-  }
-  __syncthreads();
+  if (ns->broken) return false;
   const float4* sL1 = reinterpret_cast<const float4*>(si + kImgL1);
   const float* sB2 = reinterpret_cast<const float*>(si + kImgB2);
   // layer 1 on the CUDA cores
@@ -106,7 +129,7 @@ static __device__ __noinline__ bool net_rows(unsigned char* sm, const unsigned c
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = tmem_base;
+  const uint32_t tmem = ns->tmem;
   const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
   const uint32_t lbo = 128, sbo = 8 * 128;
   const uint32_t a0 = smem_u32(sA), w2 = smem_u32(si + kImgW2), w3 = smem_u32(si + kImgW3);
@@ -114,12 +137,12 @@ static __device__ __noinline__ bool net_rows(unsigned char* sm, const unsigned c
   if (tid == 0) {
     for (int s = 0; s < 4; ++s)
       mma_bf16(tmem, mma_desc(a0 + s * 256, lbo, sbo), mma_desc(w2 + s * 256, lbo, sbo), mma_idesc(128, 64), s > 0);
-    tc_commit(&bar);
+    tc_commit(&ns->bar);
   }
   bool ok;
   {
     bool w = true;
-    if (warp == 0) w = __all_sync(0xFFFFFFFFu, mbar_wait(&bar, 0));
+    if (warp == 0) w = __all_sync(0xFFFFFFFFu, mbar_wait(&ns->bar, 0));
     ok = __syncthreads_and(w) != 0;
   }
   tc_fence_after();
@@ -143,12 +166,12 @@ static __device__ __noinline__ bool net_rows(unsigned char* sm, const unsigned c
   if (ok && tid == 0) {
     for (int s = 0; s < 4; ++s)
       mma_bf16(tmem, mma_desc(a0 + s * 256, lbo, sbo), mma_desc(w3 + s * 256, lbo, sbo), mma_idesc(128, 16), s > 0);
-    tc_commit(&bar);
+    tc_commit(&ns->bar);
   }
   const bool issued3 = ok;
   if (ok) {
     bool w = true;
-    if (warp == 0) w = __all_sync(0xFFFFFFFFu, mbar_wait(&bar, 1));
+    if (warp == 0) w = __all_sync(0xFFFFFFFFu, mbar_wait(&ns->bar, 1));
     ok = __syncthreads_and(w) != 0;
   }
   tc_fence_after();
@@ -165,14 +188,18 @@ static __device__ __noinline__ bool net_rows(unsigned char* sm, const unsigned c
     }
   } else if (warp == 0) {
     // flag it and give the tensor core a second bounded wait on whatever it
-    // may still be doing before the tensor memory is released
-    if (lane == 0) atomicOr(err, 4);
-    mbar_wait(&bar, issued3 ? 1u : 0u);
+    // may still be doing before the tensor memory is read or released again
+    if (lane == 0) {
+      atomicOr(err, 4);
+      ns->broken = 1;
+    }
+    mbar_wait(&ns->bar, issued3 ? 1u : 0u);
   }
+  // every thread has read its rows out of tensor memory before the next
+  // products write there
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_free(tmem, 64);
   return ok;
 }
 

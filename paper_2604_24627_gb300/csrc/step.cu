@@ -23,7 +23,6 @@
 
 #include "common.cuh"
 #include "sr.h"
-#include "srnet.cuh"
 #include "step.h"
 
 namespace axpic {
@@ -172,7 +171,7 @@ __device__ __forceinline__ AxionDecision axion_decide(const float* rec, const fl
                                                       float w, float px, float py, float pz, uint32_t wP,
                                                       uint32_t wA) {
   AxionDecision d;
-  d.om = sqrtf(px * px + py * py + pz * pz) * kMeC2f;
+  d.om = sqrtf((px * px + py * py + pz * pz) + A.mu2) * kMeC2f;  // the total energy E
   d.K = 0;
   d.wprod = 0.f;
   d.capped = false;
@@ -258,9 +257,12 @@ struct PhotonDecision {
 __device__ __forceinline__ PhotonDecision photon_decide(const float* rec, const float* sr, const StepArgs& A, float w,
                                                         float px, float py, float pz, uint32_t wd) {
   PhotonDecision d;
-  d.om = sqrtf(px * px + py * py + pz * pz) * kMeC2f;
+  const float pm = sqrtf(px * px + py * py + pz * pz);
+  d.om = pm * kMeC2f;
   const float xr = d.om * rec[R_INVT];
-  const float P = sr && sr_in_range(xr) ? -expm1f(-sr_prim_gdt(sr, xr)) : prim_prob(rec, d.om, rec[R_AP]);
+  // a massive axion: the rate times beta(omega), zero at and below m_a
+  const float beta = A.mu > 0.f ? axion_beta(pm, A.mu2) : 1.0f;
+  const float P = sr && sr_in_range(xr) ? -expm1f(-(beta * sr_prim_gdt(sr, xr))) : prim_prob(rec, d.om, beta * rec[R_AP]);
   float fac;
   const float le = cap_lambda(w * P * A.inv_w_a, A.lam_cap, &fac, &d.capped);
   d.K = poisson_inv(u23(wd), le);
@@ -776,7 +778,7 @@ __device__ __forceinline__ int axion_chunk(const StepArgs& A, uint32_t step, int
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float px = f4(x4, j), py = f4(y4, j), pz = f4(z4, j);
-        const float p2 = px * px + py * py + pz * pz;
+        const float p2 = (px * px + py * py + pz * pz) + A.mu2;  // E^2 (m_e c^2 units)
         bool fast = !all;
         if (fast && prim)
           fast = no_conversion(f4(w4, j), p2, cs, cap_inv, u23(word(rP, j)), A.lam_cap);
@@ -829,7 +831,6 @@ __global__ void __launch_bounds__(kDecThreads, AXPIC_DEC_MIN_CTAS) decide_kernel
 // (Eqs. delta_def to b_def, affine_map) by a whole warp, measuring what was
 // applied; then the temperature update (Eqs. Te_est, Te_relax) and the
 // record's temperature half.
-constexpr int kFeedbackThreadsMax = 128;
 
 struct FbCell {
   double dE, dPx, dPy, dPz;  // this step's exchange
@@ -911,12 +912,11 @@ __device__ __forceinline__ void fb_prepare(FbCell& f) {
 }
 
 // Carry, moments, diagnostics, temperature and record once the remap (r;
-// null when the cell was not remapped) is done. Returns whether the
-// temperature was updated; then rec holds the cell's new record (with the
-// closed-form prefactors), written here except under the surrogate rate
-// model, whose network may still replace the prefactors.
-__device__ __forceinline__ bool fb_finish(const StepArgs& A, int cell, const FbCell& f, const RemapOut* r,
-                                          float* rec) {
+// null when the cell was not remapped) is done. The record gets the
+// closed-form prefactors of the new temperature; under the surrogate rate
+// model the network's kernel, launched next, replaces them where it is
+// trusted.
+__device__ __forceinline__ void fb_finish(const StepArgs& A, int cell, const FbCell& f, const RemapOut* r) {
   double nrE = f.qE, nrPx = f.qPx, nrPy = f.qPy, nrPz = f.qPz, applied_E = 0.0;
   float var_new = f.var;
   if (r) {
@@ -969,6 +969,7 @@ __device__ __forceinline__ bool fb_finish(const StepArgs& A, int cell, const FbC
     double Tn = f.T + (double)dT;
     const float Tnf = Tf + dT;
     if (Tnf <= A.T_floor_f || Tnf >= A.T_ceil_f) Tn = fmin(fmax(Tn, A.T_floor), A.T_ceil);
+    float rec[kRecLen];
     const float4* rc = f.rc;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -979,53 +980,11 @@ __device__ __forceinline__ bool fb_finish(const StepArgs& A, int cell, const FbC
     }
     compute_temperature(A.cc, (float)Tn, rec);
     A.T[cell] = Tn;
-    if (A.rate_model == 2) {
-      // the closed-form Primakoff prefactor (a network value may be there)
-      rec[R_AP] = A.cc.k_AP * rec[R_SZ];
-      return true;
-    }
+    // the closed-form Primakoff prefactor (the network's may be there)
+    if (A.rate_model == 2) rec[R_AP] = A.cc.k_AP * rec[R_SZ];
     float4* r4 = reinterpret_cast<float4*>(A.rec + (size_t)cell * kRecLen);
     r4[0] = make_float4(rec[0], rec[1], rec[2], rec[3]);
     r4[1] = make_float4(rec[4], rec[5], rec[6], rec[7]);
-    return true;
-  }
-  return false;
-}
-
-// Surrogate rate model, after the temperature update of the CTA's cells
-// (thread t: cell t, upd: its T changed, rec: its new record): the network
-// for the CTA's 128 cells (one tensor-core row each) where any is trusted;
-// trusted cells get the network's prefactors, the others the table's
-// spectral record (a warp per cell). All threads of the CTA call it.
-__device__ __forceinline__ void fb_surrogate(const StepArgs& A, int cell, bool upd, float* rec, unsigned char* sm) {
-  __shared__ int tlist[kFeedbackThreadsMax];
-  __shared__ int ntl;
-  if (threadIdx.x == 0) ntl = 0;
-  SrCellIn ci = {1.f, 1.f, 0.f, 24.f, 0.f};
-  bool trusted = false;
-  if (upd) {
-    ci = sr_cell_from(rec, A.ra.k_T7);
-    trusted = A.ra.trust && sr_trusted(A.ra, ci.T, ci.lne);
-  }
-  if (__syncthreads_or(trusted)) {
-    float c[3];
-    const bool ok = net_rows(sm, A.ra.img, net_f1(ci.lkT), net_f2(ci.lne), A.ra.Z - 1.5f, c, A.err);
-    trusted = trusted && ok;
-    if (trusted) net_prefactors(A.ra, c, ci.T, rec[R_NE], rec);
-  }
-  if (upd) {
-    float4* r4 = reinterpret_cast<float4*>(A.rec + (size_t)cell * kRecLen);
-    r4[0] = make_float4(rec[0], rec[1], rec[2], rec[3]);
-    r4[1] = make_float4(rec[4], rec[5], rec[6], rec[7]);
-    A.ra.src[cell] = trusted ? 0 : 1;
-    if (!trusted) tlist[atomicAdd(&ntl, 1)] = cell;
-  }
-  __syncthreads();
-  const int n = ntl, lane = threadIdx.x & 31;
-  for (int k = threadIdx.x >> 5; k < n; k += kFeedbackThreadsMax / 32) {
-    const int c = tlist[k];
-    const SrCellIn cc = sr_cell_from(A.rec + (size_t)c * kRecLen, A.ra.k_T7);
-    sr_table_record_warp(A.ra, cc, A.ra.sr + (size_t)c * kSrLen, lane);
   }
 }
 
@@ -1038,7 +997,6 @@ struct RemapJob {
   float s1, bx, by, bz;
 };
 constexpr int kFeedbackThreads = 128;
-static_assert(kFeedbackThreads == kNetThreads, "a feedback CTA runs the network with a row per cell");
 
 __global__ void __launch_bounds__(kFeedbackThreads) feedback_kernel(StepArgs A) {
   // a replayed graph takes its step index from the device counter: the last
@@ -1081,18 +1039,12 @@ __global__ void __launch_bounds__(kFeedbackThreads) feedback_kernel(StepArgs A) 
     if (lane == 0) outs[k] = r;
   }
   __syncthreads();
-  float rec[kRecLen];
-  bool upd = false;
   if (valid) {
-    upd = fb_finish(A, cell, f, job >= 0 ? &outs[job] : nullptr, rec);
+    fb_finish(A, cell, f, job >= 0 ? &outs[job] : nullptr);
     if (f.need) {
       atomicAdd(A.counters + C_REMAP, 1ull);
       atomicAdd(A.counters + C_REMAP_E, (unsigned long long)f.ne);
     }
-  }
-  if (A.rate_model == 2 && A.T_mode == 2) {
-    extern __shared__ __align__(1024) unsigned char fsm[];
-    fb_surrogate(A, cell, upd, rec, fsm);
   }
 }
 
@@ -1311,12 +1263,21 @@ __device__ __forceinline__ ElItem el_load(const StepArgs& A, long base, int slot
 
 // A flagged axion: counters, exchange, new weight. Returns K; *removed tells
 // whether the slot leaves the slab.
+// The momentum of an a->gamma photon: the axion's direction with the axion's
+// total energy E (its own momentum when massless).
+__device__ __forceinline__ float3 photon_from_axion(const StepArgs& A, float px, float py, float pz) {
+  if (A.mu <= 0.f) return make_float3(px, py, pz);
+  const float p2 = px * px + py * py + pz * pz;
+  const float f = __fdiv_rn(sqrtf(p2 + A.mu2), sqrtf(p2));
+  return make_float3(px * f, py * f, pz * f);
+}
+
 __device__ __forceinline__ int axion_outcome(const StepArgs& A, const AxItem& t, long abase, bool bath,
                                              const Cnt& cnt, Lane64& x64, bool* removed) {
   const int K = t.r.x & 0xFF;
   const float wprod = __uint_as_float(t.r.y);
   const float wnew = __uint_as_float(t.r.z);
-  const float om = sqrtf(t.px * t.px + t.py * t.py + t.pz * t.pz) * kMeC2f;
+  const float om = sqrtf((t.px * t.px + t.py * t.py + t.pz * t.pz) + A.mu2) * kMeC2f;  // E
   cnt.add(C_CAP, (t.r.x & DF_CAPPED) ? 1u : 0u);
   cnt.add(C_CLAMP, (t.r.x & DF_OVER) ? 1u : 0u);
   cnt.add(C_EV_PINV, (unsigned)K);
@@ -1362,11 +1323,16 @@ struct AxDest {
 __device__ __forceinline__ void gamma_products(const StepArgs& A, const PhItem& t, long abase, const AxDest& D,
                                                int i0, int K, const Cnt& cnt) {
   const float wprod = __uint_as_float(t.r.y);
-  const float om = sqrtf(t.px * t.px + t.py * t.py + t.pz * t.pz) * kMeC2f;
+  const float pm = sqrtf(t.px * t.px + t.py * t.py + t.pz * t.pz);
+  const float om = pm * kMeC2f;
+  // a massive axion takes E = omega and momentum beta p_gamma
+  const float beta = A.mu > 0.f ? axion_beta(pm, A.mu2) : 1.0f;
+  const float ax = A.mu > 0.f ? t.px * beta : t.px, ay = A.mu > 0.f ? t.py * beta : t.py,
+              az = A.mu > 0.f ? t.pz * beta : t.pz;
   for (int k = 0; k < K; ++k) {
     const int dst = D.at(i0 + k);
     if (dst < A.a.cap) {
-      write_particle(A.a, abase + dst, wprod, t.px, t.py, t.pz, t.x, t.y, t.z);
+      write_particle(A.a, abase + dst, wprod, ax, ay, az, t.x, t.y, t.z);
       if (A.tally_enable) tally_add(A, 0, wprod, om);
     } else {
       cnt.add(C_DROP, 1);
@@ -1376,12 +1342,16 @@ __device__ __forceinline__ void gamma_products(const StepArgs& A, const PhItem& 
 
 // The events of a flagged electron (thermal-bath emission), new axions i0
 // on: event k takes cos theta, phi, energy and channel from one Philox
-// block. Returns K.
+// block. A massive axion's event is kept when the channel uniform, rescaled
+// inside its channel's interval, is below beta(E) (thinning; every event is
+// kept when massless). Returns the kept events; WRITE = false only counts
+// them (the warp path's offsets need the counts first).
+template <bool WRITE>
 __device__ __forceinline__ int electron_events(const StepArgs& A, uint32_t step, int cell, const ElItem& t,
                                                long abase, const AxDest& D, int i0, float r_cc, float r_cb,
                                                float r_T, float wu, const Cnt& cnt, Lane64& x64) {
   const int K = t.f & 0xFF;
-  if (wu <= 0.f) cnt.add(C_CAP, ((t.f & DF_CAPPED) ? 1u : 0u) + ((t.f & DF_CAPPED_B) ? 1u : 0u));
+  if (WRITE && wu <= 0.f) cnt.add(C_CAP, ((t.f & DF_CAPPED) ? 1u : 0u) + ((t.f & DF_CAPPED_B) ? 1u : 0u));
   if (!K) return 0;
   const bool eC = A.mask & AXPIC_CH_COMPTON, eB = A.mask & AXPIC_CH_BREMS;
   float facC = 1.f, facB = 1.f;
@@ -1399,27 +1369,38 @@ __device__ __forceinline__ int electron_events(const StepArgs& A, uint32_t step,
     q = cell_sr(A, cell);
     if (!q) q = A.ra.uni;
   }
+  int kept = 0;
   for (int k = 0; k < K; ++k) {
     const uint4 r = philox4x32_10(make_uint4(step, gcell, (uint32_t)t.slot, (S_EV_E << 24) | (uint32_t)k), A.rk);
-    const bool isC = u23(r.w) < fracC;
-    const float3 dv = iso_dir(u23(r.x), u23(r.y));
+    const float uc = u23(r.w);
+    const bool isC = uc < fracC;
     const float E = (q ? sr_sample_x(q, isC ? 1 : 2, u23(r.z))
                        : icdf_lookup(A.tables + (isC ? TAB_COMPTON : TAB_BREMS) * kTableN, u23(r.z))) *
                     r_T;
-    const float wv = isC ? wvC : wvB;
-    const float pm = E * kInvMeC2f;
-    const float px = pm * dv.x, py = pm * dv.y, pz = pm * dv.z;
-    const int dst = D.at(i0 + k);
-    if (dst < A.a.cap) {
-      write_particle(A.a, abase + dst, wv, px, py, pz, t.x, t.y, t.z);
-      if (A.tally_enable) tally_add(A, isC ? 1 : 2, wv, E);
-    } else {
-      cnt.add(C_DROP, 1);
+    float pm = E * kInvMeC2f;
+    if (A.mu > 0.f) {
+      const float ut = isC ? __fdiv_rn(uc, fracC) : __fdiv_rn(__fsub_rn(uc, fracC), __fsub_rn(1.0f, fracC));
+      const float beta = axion_beta(pm, A.mu2);
+      if (!(ut < beta)) continue;  // thinned: below the threshold always
+      pm = pm * beta;               // |p| = sqrt(E^2 - m_a^2)
     }
-    x64.add(-(double)wv, E, px, py, pz);
-    cnt.add(isC ? C_EV_C : C_EV_B, 1);
+    if (WRITE) {
+      const float3 dv = iso_dir(u23(r.x), u23(r.y));
+      const float wv = isC ? wvC : wvB;
+      const float px = pm * dv.x, py = pm * dv.y, pz = pm * dv.z;
+      const int dst = D.at(i0 + kept);
+      if (dst < A.a.cap) {
+        write_particle(A.a, abase + dst, wv, px, py, pz, t.x, t.y, t.z);
+        if (A.tally_enable) tally_add(A, isC ? 1 : 2, wv, E);
+      } else {
+        cnt.add(C_DROP, 1);
+      }
+      x64.add(-(double)wv, E, px, py, pz);
+      cnt.add(isC ? C_EV_C : C_EV_B, 1);
+    }
+    ++kept;
   }
-  return K;
+  return kept;
 }
 
 // ---------------------------------------------------------------- warp path
@@ -1464,9 +1445,10 @@ __device__ __noinline__ void absorb_warp(const StepArgs& A, int cell, EvScratch&
     int tot;
     int off = run + warp_excl_scan(K, &tot);
     const float wprod = __uint_as_float(t.r.y);
+    const float3 pg = photon_from_axion(A, t.px, t.py, t.pz);
     for (int k = 0; k < K; ++k, ++off) {
       const int dst = ng_start + off;
-      if (dst < A.g.cap) write_particle(A.g, gbase + dst, wprod, t.px, t.py, t.pz, t.x, t.y, t.z);
+      if (dst < A.g.cap) write_particle(A.g, gbase + dst, wprod, pg.x, pg.y, pg.z, t.x, t.y, t.z);
       else cnt.add(C_DROP, 1);
     }
     run += tot;
@@ -1521,10 +1503,12 @@ __device__ __noinline__ void emit_warp(const StepArgs& A, uint32_t step, int cel
   Lane64 x64;
   for (int i0 = 0; i0 < nflE; i0 += 32) {
     const ElItem t = el_load(A, ebase, i0 + lane < nflE ? (int)S.flE[i0 + lane] : -1, wu);
-    const int K = t.slot >= 0 ? (int)(t.f & 0xFF) : 0;
+    int K = t.slot >= 0 ? (int)(t.f & 0xFF) : 0;
+    if (A.mu > 0.f && K > 0)  // massive axions: the kept events, before the offsets
+      K = electron_events<false>(A, step, cell, t, abase, D, 0, r_cc, r_cb, r_T, wu, cnt, x64);
     int tot;
     const int off = run + warp_excl_scan(K, &tot);
-    if (t.slot >= 0) electron_events(A, step, cell, t, abase, D, off, r_cc, r_cb, r_T, wu, cnt, x64);
+    if (t.slot >= 0) electron_events<true>(A, step, cell, t, abase, D, off, r_cc, r_cb, r_T, wu, cnt, x64);
     run += tot;
   }
   reduce_out(x64, out);
@@ -1690,9 +1674,10 @@ __device__ __forceinline__ void cell_lane(const StepArgs& A, uint32_t step, int 
       bool removed;
       const int K = axion_outcome(A, ta[j], abase, bath, cnt, xa, &removed);
       const float wprod = __uint_as_float(ta[j].r.y);
+      const float3 pg = photon_from_axion(A, ta[j].px, ta[j].py, ta[j].pz);
       for (int k = 0; k < K; ++k) {
         const int dst = L.ng + run + k;
-        if (dst < A.g.cap) write_particle(A.g, gbase + dst, wprod, ta[j].px, ta[j].py, ta[j].pz, ta[j].x, ta[j].y, ta[j].z);
+        if (dst < A.g.cap) write_particle(A.g, gbase + dst, wprod, pg.x, pg.y, pg.z, ta[j].x, ta[j].y, ta[j].z);
         else cnt.add(C_DROP, 1);
       }
       run += K;
@@ -1703,9 +1688,10 @@ __device__ __forceinline__ void cell_lane(const StepArgs& A, uint32_t step, int 
       bool removed;
       const int K = axion_outcome(A, t, abase, bath, cnt, xa, &removed);
       const float wprod = __uint_as_float(t.r.y);
+      const float3 pg = photon_from_axion(A, t.px, t.py, t.pz);
       for (int k = 0; k < K; ++k) {
         const int dst = L.ng + run + k;
-        if (dst < A.g.cap) write_particle(A.g, gbase + dst, wprod, t.px, t.py, t.pz, t.x, t.y, t.z);
+        if (dst < A.g.cap) write_particle(A.g, gbase + dst, wprod, pg.x, pg.y, pg.z, t.x, t.y, t.z);
         else cnt.add(C_DROP, 1);
       }
       run += K;
@@ -1761,7 +1747,7 @@ __device__ __forceinline__ void cell_lane(const StepArgs& A, uint32_t step, int 
     }
     for (int i = 0; i < nE; ++i) {
       const ElItem t = el_load(A, ebase, lE[32 * i], L.wu);
-      NP += electron_events(A, step, cell, t, abase, D, NP, L.r_cc, L.r_cb, L.r_T, L.wu, cnt, xe);
+      NP += electron_events<true>(A, step, cell, t, abase, D, NP, L.r_cc, L.r_cb, L.r_T, L.wu, cnt, xe);
     }
     na = min(D.base - D.nholes + NP, A.a.cap);
     if (reuse && NP < nrmA) {
@@ -2016,8 +2002,27 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
   }
 }
 
+
 // ---------------------------------------------------------------- launchers
 size_t step_smem_per_warp(int acap, int gcap, int ecap) { return ev_scratch_bytes(acap, gcap, ecap); }
+
+int resident_ctas(const void* fn, int threads, size_t dyn_smem, int max_per_sm) {
+  int dev = 0, sms = 0, regs_sm = 0, smem_sm = 0, reserved = 0, threads_sm = 0, blocks_sm = 0;
+  cudaFuncAttributes fa;
+  if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) ||
+      cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) ||
+      cudaDeviceGetAttribute(&blocks_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) ||
+      cudaFuncGetAttributes(&fa, fn))
+    return 0;
+  const int warps = (threads + 31) / 32;
+  const int regs_cta = warps * ((max(1, fa.numRegs) * 32 + 255) / 256 * 256);
+  const int smem_cta = (int)((fa.sharedSizeBytes + dyn_smem + reserved + 127) / 128 * 128);
+  const int nb = min(min(regs_sm / regs_cta, smem_sm / smem_cta), min(threads_sm / (warps * 32), blocks_sm));
+  return max(1, min(nb, max_per_sm)) * max(1, sms);
+}
 
 template <int PH>
 static cudaError_t launch_events(const StepArgs& A, int warps, cudaStream_t st) {
@@ -2062,13 +2067,16 @@ static cudaError_t launch_decide(const StepArgs& A, int phases, cudaStream_t st)
 }
 
 static cudaError_t launch_feedback(const StepArgs& A, cudaStream_t st) {
-  // the surrogate rate model runs the network in the feedback kernel
-  const int smem = A.rate_model == 2 && A.T_mode == 2 ? kNetSmemBytes : 0;
-  feedback_kernel<<<(A.ncells + kFeedbackThreads - 1) / kFeedbackThreads, kFeedbackThreads, smem, st>>>(A);
+  const int grid = (A.ncells + kFeedbackThreads - 1) / kFeedbackThreads;
+  feedback_kernel<<<grid, kFeedbackThreads, 0, st>>>(A);
   return cudaGetLastError();
 }
 
-const char* step_kernel_names() { return "decide_kernel,event_kernel,feedback_kernel"; }
+const char* step_kernel_names(int rate_model, int T_mode) {
+  if (T_mode == 2 && rate_model == 1) return "decide_kernel,event_kernel,feedback_kernel,sr_table_kernel";
+  if (T_mode == 2 && rate_model == 2) return "decide_kernel,event_kernel,feedback_kernel,sr_cells_kernel";
+  return "decide_kernel,event_kernel,feedback_kernel";
+}
 
 __global__ void set_step_kernel(uint32_t* p, uint32_t v, int n) {
   for (int i = 0; i < n; ++i) p[i] = v;
@@ -2092,12 +2100,12 @@ cudaError_t decide_resident_ctas(int chunk, int* out) {
   return cudaSuccess;
 }
 
-// After the temperature update of an evolved-T step the table model's
-// spectral records are rebuilt for the new T (the surrogate model's are
-// rebuilt by the feedback kernel itself).
+// After the temperature update of an evolved-T step the rate model's records
+// follow the new T: the table model's spectral records, or the surrogate
+// network's prefactors (the table's records where it is not trusted).
 static cudaError_t launch_records_update(const StepArgs& A, const SrArgs* sra, cudaStream_t st) {
-  if (!sra || A.T_mode != 2 || A.rate_model != 1) return cudaSuccess;
-  return launch_sr_table(*sra, st);
+  if (!sra || A.T_mode != 2) return cudaSuccess;
+  return launch_sr_records(A.rate_model, *sra, st);
 }
 
 cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t st, cudaEvent_t* ev,
@@ -2119,7 +2127,8 @@ cudaError_t launch_step(int phases, const StepArgs& A, int warps, cudaStream_t s
     case PH_ALL:
       if ((e = mark(0)) || (e = launch_decide(A, PH_ABSORB | PH_EMIT, st)) || (e = mark(1))) return e;
       if ((e = launch_events<PH_ABSORB | PH_EMIT>(A, warps, st)) || (e = mark(2))) return e;
-      if ((e = launch_feedback(A, st)) || (e = launch_records_update(A, sra, st)) || (e = mark(3))) return e;
+      if ((e = launch_feedback(A, st)) || (e = mark(3)) || (e = launch_records_update(A, sra, st)) || (e = mark(4)))
+        return e;
       return cudaSuccess;
     default:
       return cudaErrorInvalidValue;

@@ -32,7 +32,13 @@ def dev(a):
 
 
 U = 2.0 ** -7   # one bfloat16 unit, relative (7 stored mantissa bits)
-TANH = 1e-6    # the kernels' activation: absolute error below 7e-7, plus binary32 rounding
+
+
+def tanh_err(h):
+    """Bound on the kernels' activation error at |tanh| = h: the hardware
+    approximation's relative error (below 1e-5 over a sweep of 16.8 M
+    points on a GB300) with a factor 3 of margin, plus 1e-6."""
+    return 2.0 ** -15 * h + 1e-6
 
 
 def forward_bound(P, X):
@@ -44,23 +50,26 @@ def forward_bound(P, X):
     aW2, aW3 = np.abs(q(P["W2"])), np.abs(q(P["W3"]))
     ah1 = np.abs(np.tanh(X @ P["W1"] + P["b1"]))
     ah2 = np.abs(np.tanh(q(np.tanh(X @ P["W1"] + P["b1"])) @ q(P["W2"]) + P["b2"]))
-    dh2 = (U * ah1 + TANH) @ aW2 + acc * (ah1 @ aW2) + TANH
+    dh2 = (U * ah1 + tanh_err(ah1)) @ aW2 + acc * (ah1 @ aW2) + tanh_err(ah2)
     return (U * ah2 + dh2) @ aW3 + acc * (ah2 @ aW3)
 
 
 @pytest.mark.parametrize("n", [1, 127, 128, 300, 4096])
 def test_forward_matches_oracle(n):
-    """Every output within its bound (forward_bound); most rows meet the
-    oracle's bfloat16 operands exactly, so the typical output agrees to FP32
-    accumulation (median error 2e-5 of the largest output)."""
+    """Every output within its bound (forward_bound), and the typical output
+    well inside it (median error below a quarter of its bound: the bound
+    takes every activation a full bfloat16 unit off in the same direction,
+    while the tanh approximation moves only some of them across a rounding
+    boundary, in either direction)."""
     P, X, _ = seeded(1, n)
     net = SurrogateNet()
     net.set_params(P)
     got = net.forward(dev(X)).cpu().numpy().astype(np.float64)
     want, _ = S.forward(P, X, bf16_mma=True)
     err = np.abs(got - want)
-    assert np.all(err <= forward_bound(P, X) + 1e-7), float((err - forward_bound(P, X)).max())
-    assert np.median(err) <= 2e-5 * max(1.0, np.abs(want).max()), np.median(err)
+    B = forward_bound(P, X) + 1e-7
+    assert np.all(err <= B), float((err - B).max())
+    assert np.median(err / B) < 0.25, np.median(err / B)
     net.close()
 
 
@@ -70,7 +79,7 @@ def gradient_bounds(P, X, Zt):
     operand of a tensor-core product one bfloat16 unit off on one side (the
     sides round slightly different binary32 and FP64 values; the weights
     round identically), every FP32 sum off by n 2^-24 of its absolute sum,
-    and the kernels' tanh off by TANH, carried through forward and
+    and the kernels' tanh off by tanh_err, carried through forward and
     backward with absolute values."""
     q = S.bf16
     n = len(X)
@@ -78,11 +87,11 @@ def gradient_bounds(P, X, Zt):
     W1, W2, W3 = P["W1"], P["W2"], P["W3"]
     aW2, aW3 = np.abs(q(W2)), np.abs(q(W3))
     h1 = np.tanh(X @ W1 + P["b1"])
-    dh1 = np.full_like(h1, TANH)
     a2 = q(h1) @ q(W2) + P["b2"]
     h2 = np.tanh(a2)
     ah1, ah2 = np.abs(h1), np.abs(h2)
-    dh2 = (U * ah1 + dh1) @ aW2 + acc(64) * (ah1 @ aW2) + TANH
+    dh1 = tanh_err(ah1)
+    dh2 = (U * ah1 + dh1) @ aW2 + acc(64) * (ah1 @ aW2) + tanh_err(ah2)
     z = q(h2) @ q(W3) + P["b3"]
     dzv = (U * ah2 + dh2) @ aW3 + acc(64) * (ah2 @ aW3)
     g = 2.0 * (z - Zt) / n
@@ -112,7 +121,7 @@ def gradient_bounds(P, X, Zt):
 @pytest.mark.parametrize("n", [200, 1000])
 def test_gradients_match_oracle(n):
     """Every gradient element within its bound from gradient_bounds, and the
-    typical element much closer (median relative error below 1e-3)."""
+    typical element well inside it (median below a quarter of its bound)."""
     P, X, Zt = seeded(2, n)
     net = SurrogateNet()
     net.set_params(P)
@@ -125,19 +134,20 @@ def test_gradients_match_oracle(n):
         d = np.abs(G[k] - want[k])
         bad = d > B[k] + 1e-12
         assert not bad.any(), (k, int(bad.sum()), float((d - B[k]).max()))
-        big = np.abs(want[k]) > 1e-6 * np.abs(want[k]).max()
-        rel.append((d[big] / np.abs(want[k][big])).ravel())
-    assert np.median(np.concatenate(rel)) < 1e-3, np.median(np.concatenate(rel))
+        rel.append((d / (B[k] + 1e-12)).ravel())
+    assert np.median(np.concatenate(rel)) < 0.25, np.median(np.concatenate(rel))
     net.close()
 
 
 def test_adam_steps_match_oracle():
     """Three training steps (gradients, then Adam with bias-corrected moments,
     beta 0.9 and 0.999, eps 1e-8) from the same parameters as the oracle's
-    Adam (oracle.surrogate.adam) on the oracle's gradients: an element whose
-    gradient stays far above its rounding bound (10x) moves as the oracle's
-    within 1e-3 of the learning rate a step plus binary32 rounding; those are
-    at least 90 % of the parameters."""
+    Adam (oracle.surrogate.adam) on the oracle's gradients. A step moves an
+    element by lr m/(sqrt(v) + eps), insensitive to the gradient's scale:
+    where each step's oracle gradient exceeds its rounding bound B (from
+    gradient_bounds) the GPU's element stays within lr sum_t 4 B_t / |G_t| of
+    the oracle's (plus binary32 rounding), elsewhere within 2 lr a step; and
+    the typical element is well inside that (median below a quarter)."""
     P, X, Zt = seeded(5, 512)
     net = SurrogateNet()
     net.set_params(P)   # resets the Adam state
@@ -145,24 +155,25 @@ def test_adam_steps_match_oracle():
     Po = {k: v.copy() for k, v in P.items()}
     M = {k: np.zeros_like(v) for k, v in P.items()}
     V = {k: np.zeros_like(v) for k, v in P.items()}
-    clear = {k: np.ones(v.shape, dtype=bool) for k, v in P.items()}
+    tol = {k: np.zeros_like(v) for k, v in P.items()}
     Xd, Zd = dev(X), dev(Zt)
     for t in range(1, 4):
         G = S.backward(Po, X, Zt, bf16_mma=True)
         B = gradient_bounds(Po, X, Zt)
         for k in G:
-            clear[k] &= np.abs(G[k]) > 10 * B[k]
+            r = B[k] / np.maximum(np.abs(G[k]), 1e-300)
+            tol[k] += lr * np.where(r < 0.5, 4.0 * r, 2.0)
         S.adam(Po, G, M, V, t, lr)
         net.train_step(Xd, Zd, lr)
     got = net.get_params()
-    frac = sum(c.sum() for c in clear.values()) / sum(c.size for c in clear.values())
-    assert frac >= 0.9, frac
+    rel = []
     for k in got:
         d = np.abs(got[k] - Po[k])
-        tol = 3 * 1e-3 * lr + 4 * np.spacing(np.abs(Po[k]).astype(np.float32)).astype(np.float64)
-        bad = clear[k] & (d > tol)
-        assert not bad.any(), (k, int(bad.sum()), float(d[clear[k]].max()))
-        assert np.all(d <= 3 * 2 * lr + tol), k   # any element: at most the step size each step
+        ulp = 4 * np.spacing(np.abs(Po[k]).astype(np.float32)).astype(np.float64)
+        bad = d > tol[k] + ulp
+        assert not bad.any(), (k, int(bad.sum()), float((d - tol[k] - ulp).max()))
+        rel.append((d / (tol[k] + ulp)).ravel())
+    assert np.median(np.concatenate(rel)) < 0.25, np.median(np.concatenate(rel))
     net.close()
 
 
@@ -199,5 +210,7 @@ def test_batches_that_grow_reuse_the_network():
             assert np.all(np.abs(G[k] - want[k]) <= B[k] + 1e-12), (n, k)
         z = net.forward(dev(X)).cpu().numpy()
         zw, _ = S.forward(P, X, bf16_mma=True)
-        assert np.median(np.abs(z - zw)) <= 2e-5 * max(1.0, np.abs(zw).max()), n
+        Bz = forward_bound(P, X) + 1e-7
+        assert np.all(np.abs(z - zw) <= Bz), n
+        assert np.median(np.abs(z - zw) / Bz) < 0.25, n
     net.close()

@@ -108,16 +108,18 @@ def bf16_bound(P, sigma, T, ne, Z=1):
     arithmetic allows, per ln-emissivity output, to first order: each
     activation of layers 1 and 2 one bfloat16 unit off (2^-7 relative; the
     sides round slightly different binary32 and FP64 values, the weights
-    identically) plus the kernels' tanh error (1e-6), carried through |W2|
-    and |W3|, and the FP32 accumulation of the 64-term products."""
+    identically) plus the kernels' tanh error (2^-15 relative, three times
+    the approximation's, plus 1e-6), carried through |W2| and |W3|, and the
+    FP32 accumulation of the 64-term products."""
     cs, _ = S.cell(T, ne, Z)
     X = S.cell_features(S.features(1.0, cs.kappa_keV / T, ne, Z)[None, :])
     h1 = np.abs(np.tanh(X @ P["W1"] + P["b1"]))
     a2 = S.bf16(h1) @ S.bf16(P["W2"]) + P["b2"]
     h2 = np.abs(np.tanh(a2))
     W2, W3 = np.abs(S.bf16(P["W2"])), np.abs(S.bf16(P["W3"]))
-    u, t, acc = 2.0 ** -7, 1e-6, 64 * 2.0 ** -24
-    dh2 = (u * h1 + t) @ W2 + acc * (h1 @ W2) + t
+    u, acc = 2.0 ** -7, 64 * 2.0 ** -24
+    t1, t2 = 2.0 ** -15 * h1 + 1e-6, 2.0 ** -15 * h2 + 1e-6
+    dh2 = (u * h1 + t1) @ W2 + acc * (h1 @ W2) + t2
     dz = (u * h2 + dh2) @ W3 + acc * (h2 @ W3)
     return (np.asarray(sigma, np.float64) * dz[0])[[0, 32, 64]]
 
@@ -220,7 +222,8 @@ def test_network_rates_match_oracle_network():
     like and bremsstrahlung absorption at 9 energies, both emission means)
     are the oracle's surrogate-model rates with the oracle network's
     constants, within the bfloat16-derived bound of the constants (rates are
-    e^c times closed forms), and most cells agree to FP32 rounding."""
+    e^c times closed forms), and the typical cell well inside it (median
+    below a quarter of the bound)."""
     rng = np.random.default_rng(11)
     T = np.concatenate([[c[0] for c in CELLS], rng.uniform(0.6, 9.5, 58)])
     ne = np.concatenate([[c[1] for c in CELLS], 10 ** rng.uniform(23.1, 25.9, 58)])
@@ -248,8 +251,9 @@ def test_network_rates_match_oracle_network():
         assert np.all(d[:, 2] <= tol[1]), (c, d[:, 2].max(), tol[1])
         assert np.all(d[:, 3] <= tol[2]), (c, d[:, 3].max(), tol[2])
         assert abs(rec[c, 3] / lc - 1) <= tol[1] and abs(rec[c, 4] / lb - 1) <= tol[2], (c, rec[c, 3:5], lc, lb)
-        rel.append(max(d.max(), abs(rec[c, 3] / lc - 1), abs(rec[c, 4] / lb - 1)))
-    assert np.median(rel) <= 2e-5, np.median(rel)
+        rel.append(max(d[:, [0, 1]].max() / tol[0], d[:, 2].max() / tol[1], d[:, 3].max() / tol[2],
+                       abs(rec[c, 3] / lc - 1) / tol[1], abs(rec[c, 4] / lb - 1) / tol[2]))
+    assert np.median(rel) < 0.25, np.median(rel)
     net.close()
     pl.close()
 
@@ -296,7 +300,7 @@ def test_mixed_trust_records():
     sampled-quantile error."""
     rng = np.random.default_rng(21)
     n = 300
-    T = rng.uniform(0.6, 9.5, n)
+    T = np.exp(rng.uniform(math.log(0.6), math.log(9.5), n))
     ne = 10 ** rng.uniform(23.3, 25.9, n)
     kw = dict(counts=(8, 8, 4), caps=(16, 64, 64))
     prm = params(2)
@@ -424,7 +428,7 @@ def exact_rates(T, ne, prm, E):
 
 def test_trained_network_within_the_bound_where_trusted():
     """The network as the benchmark trains it, trusted where the four nodes of
-    a 185 x 121 validation grid (log-spaced in T and n_e) around a cell are
+    a 369 x 241 validation grid (log-spaced in T and n_e) around a cell are
     within 5e-4 (half the bound)
     on the rates and 1e-3 on the sampled quantiles: on 2000 random cells of
     the domain and 2000 cells of the 512 x 512 temperature bump (n_e = 6e25,
@@ -435,7 +439,7 @@ def test_trained_network_within_the_bound_where_trusted():
     oracle's emissivities at the 30 record points in [0.05, 20]."""
     net = SurrogateNet()
     _lib.axpic_surrogate_fit(net.h, 65536, 1, 40000, 8192, 2e-3, 7)
-    nT, nne = 185, 121
+    nT, nne = 369, 241
     err = _lib.axpic_surrogate_validate(net.h, nT, nne)
     assert np.mean(err[..., 0] <= 5e-4) >= 0.9, np.mean(err[..., 0] <= 5e-4)
     rng = np.random.default_rng(31)
