@@ -450,12 +450,15 @@ def e2e_leg(pl, w, args, ncells, step0, stream, dev, world=1):
     import torch
     import torch.distributed as dist
     caps = {name: slab.capacity for name, slab in pl.slabs.items()}
-    fields = [(name, f) for name, slab in pl.slabs.items() for f in slab.data]
-    host = {(name, f): torch.empty(ncells * caps[name], dtype=torch.float32, pin_memory=True) for name, f in fields}
+    # the slabs' contiguous arrays: the slot records (4 values a slot) and x, y, z
+    fields = [(name, f) for name, slab in pl.slabs.items() for f in slab.storage]
+    width = {f: 4 if f == "wp" else 1 for f in ("wp", "x", "y", "z")}
+    host = {(name, f): torch.empty(ncells * caps[name] * width[f], dtype=torch.float32, pin_memory=True)
+            for name, f in fields}
     host_cnt = {name: torch.empty(ncells, dtype=torch.int32, pin_memory=True) for name in pl.slabs}
     host_T = torch.empty(ncells, dtype=torch.float64, pin_memory=True)
     for (name, f), hb in host.items():
-        hb.copy_(pl.slabs[name].data[f][:ncells * caps[name]])
+        hb.copy_(pl.slabs[name].storage[f][:ncells * caps[name] * width[f]])
     for name, hb in host_cnt.items():
         hb.copy_(pl.slabs[name].count[:ncells])
     host_T.copy_(pl.T[:ncells])
@@ -467,8 +470,8 @@ def e2e_leg(pl, w, args, ncells, step0, stream, dev, world=1):
     def pairs(c0, nc):
         out = []
         for name, f in fields:
-            cap = caps[name]
-            out.append((host[(name, f)][c0 * cap:(c0 + nc) * cap], pl.slabs[name].data[f][c0 * cap:(c0 + nc) * cap]))
+            cap = caps[name] * width[f]
+            out.append((host[(name, f)][c0 * cap:(c0 + nc) * cap], pl.slabs[name].storage[f][c0 * cap:(c0 + nc) * cap]))
         for name in caps:
             out.append((host_cnt[name][c0:c0 + nc], pl.slabs[name].count[c0:c0 + nc]))
         out.append((host_T[c0:c0 + nc], pl.T[c0:c0 + nc]))
@@ -816,12 +819,12 @@ def main():
         cnt = slab.count[:w.ncells]
         n_before = int(cnt.sum())
         n_in_merged = int(cnt[cnt > args.merge_n_target].sum())
-        saved = {f: t.clone() for f, t in slab.data.items()}
+        saved = {f: t.clone() for f, t in slab.storage.items()}
         saved_count = slab.count.clone()
         times = []
         for _ in range(args.merge_calls):
             with torch.cuda.stream(stream):
-                for f, t in slab.data.items():
+                for f, t in slab.storage.items():
                     t.copy_(saved[f])
                 slab.count.copy_(saved_count)
             m0 = torch.cuda.Event(enable_timing=True)

@@ -16,9 +16,10 @@
  * - Units: energies in keV, momenta in m_e c, times in seconds, densities in
  *   cm^-3, volumes in cm^3, couplings g_agg in GeV^-1 and g_ae dimensionless.
  * - Particles live in cell-sorted slabs. Species s of cell c occupies slots
- *   [c*capacity, c*capacity + count[c]) of each of its seven binary32 arrays
- *   (w, px, py, pz, x, y, z); positions are fractions of the cell in [0, 1).
- *   capacity must be a multiple of 4 and every array 16-byte aligned.
+ *   [c*capacity, c*capacity + count[c]) of its four arrays: wp holds each
+ *   slot's weight and momentum as one 16-byte record {w, px, py, pz}, and x,
+ *   y, z its position, as fractions of the cell in [0, 1). capacity must be
+ *   a multiple of 4 and every array 16-byte aligned.
  * - Pointers marked "device" are CUDA device pointers owned by the caller; the
  *   library never frees them. Pointers marked "host" are read or written
  *   synchronously before the call returns. The library owns only its scratch
@@ -64,11 +65,15 @@ enum {
   AXPIC_CH_ALL = 7
 };
 
-/* One particle species in cell-sorted SoA slabs (Sec. II.D.1: weighted
- * macroparticles; Sec. II.B: p in m_e c). All pointers are device pointers of
- * ncells*capacity binary32 values (count: ncells int32). */
+/* One particle species in cell-sorted slabs (Sec. II.D.1: weighted
+ * macroparticles; Sec. II.B: p in m_e c). Device pointers: wp holds
+ * ncells*capacity records of 4 binary32 values {w, px, py, pz} (slot i at
+ * wp[4 i .. 4 i + 3]), x, y and z ncells*capacity binary32 values each, count
+ * ncells int32. A slot's weight and momentum share one 16-byte record because
+ * every decision reads them together and every event moves them together. */
 typedef struct {
-  float *w, *px, *py, *pz, *x, *y, *z;
+  float *wp;
+  float *x, *y, *z;
   int32_t *count;
   int32_t capacity;
 } axpic_species;

@@ -30,8 +30,8 @@ CELL_DIAG_NAMES = ["dE", "dPx", "dPy", "dPz", "S_minus_1", "bx", "by", "bz", "va
 
 
 class Species(ctypes.Structure):
-    _fields_ = [("w", ctypes.c_void_p), ("px", ctypes.c_void_p), ("py", ctypes.c_void_p),
-                ("pz", ctypes.c_void_p), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+    """axpic_species: wp holds 4 binary32 values {w, px, py, pz} a slot."""
+    _fields_ = [("wp", ctypes.c_void_p), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
                 ("z", ctypes.c_void_p), ("count", ctypes.c_void_p), ("capacity", ctypes.c_int32)]
 
 

@@ -135,9 +135,11 @@ struct RecordArgs {
   const float* uni;           // [192]: the network's cell-independent quantiles at a record's offsets
 };
 
+// A species' slabs: wp[i] = {w, px, py, pz} of slot i; positions apart.
 struct SpeciesPtrs {
-  float *w, *px, *py, *pz, *x, *y, *z;
-  int32_t *count;
+  float4* wp;
+  float *x, *y, *z;
+  int32_t* count;
   int32_t cap;
 };
 

@@ -51,11 +51,12 @@ __device__ void merge_group(const MergeArgs& a, long base, const uint16_t* mem, 
   Kahan W, Px, Py, Pz, E, X, Y, Z;
   // member k + 1's fields are loaded before member k's sums (m >= 3)
   long q = base + mem[0];
-  float w = s.w[q], px = s.px[q], py = s.py[q], pz = s.pz[q], x = s.x[q], y = s.y[q], z = s.z[q];
+  float4 r = s.wp[q];
+  float w = r.x, px = r.y, py = r.z, pz = r.w, x = s.x[q], y = s.y[q], z = s.z[q];
   for (int k = 0; k < m; ++k) {
     const long qn = base + mem[min(k + 1, m - 1)];
-    const float wn = s.w[qn], pxn = s.px[qn], pyn = s.py[qn], pzn = s.pz[qn], xn = s.x[qn], yn = s.y[qn],
-                zn = s.z[qn];
+    r = s.wp[qn];
+    const float wn = r.x, pxn = r.y, pyn = r.z, pzn = r.w, xn = s.x[qn], yn = s.y[qn], zn = s.z[qn];
     W.add(w);
     Px.add(__fmul_rn(w, px));
     Py.add(__fmul_rn(w, py));
@@ -102,8 +103,10 @@ __device__ void merge_group(const MergeArgs& a, long base, const uint16_t* mem, 
     pb[j] = __fmul_rn(pm, __fsub_rn(__fmul_rn(ct, e[j]), __fmul_rn(st, qv[j])));
   }
   const long qa = base + sa, qb = base + sb;
-  s.w[qa] = wh, s.px[qa] = pa[0], s.py[qa] = pa[1], s.pz[qa] = pa[2], s.x[qa] = mx, s.y[qa] = my, s.z[qa] = mz;
-  s.w[qb] = wh, s.px[qb] = pb[0], s.py[qb] = pb[1], s.pz[qb] = pb[2], s.x[qb] = mx, s.y[qb] = my, s.z[qb] = mz;
+  s.wp[qa] = make_float4(wh, pa[0], pa[1], pa[2]);
+  s.x[qa] = mx, s.y[qa] = my, s.z[qa] = mz;
+  s.wp[qb] = make_float4(wh, pb[0], pb[1], pb[2]);
+  s.x[qb] = mx, s.y[qb] = my, s.z[qb] = mz;
 }
 
 __device__ __forceinline__ void prefetch_l1(const void* p) {
@@ -133,8 +136,9 @@ __global__ void __launch_bounds__(kWarpsMax * 32, 20) merge_kernel(MergeArgs a) 
       const int slot = s0 + lane;
       if (slot < n) {
         const long q = base + slot;
-        prefetch_l1(s.w + q), prefetch_l1(s.x + q), prefetch_l1(s.y + q), prefetch_l1(s.z + q);
-        const float px = s.px[q], py = s.py[q], pz = s.pz[q];
+        prefetch_l1(s.x + q), prefetch_l1(s.y + q), prefetch_l1(s.z + q);
+        const float4 r = s.wp[q];
+        const float px = r.y, py = r.z, pz = r.w;
         const float p2 = __fadd_rn(__fadd_rn(__fmul_rn(px, px), __fmul_rn(py, py)), __fmul_rn(pz, pz));
         int e = 0;
         for (int k = 0; k < a.nedges; ++k) e += p2 >= a.edges[k] ? 1 : 0;
@@ -215,9 +219,10 @@ __global__ void __launch_bounds__(kWarpsMax * 32, 20) merge_kernel(MergeArgs a) 
       }
       if (j < runTo && from >= 0 && to >= 0) {
         const long qf = base + from, qt = base + to;
-        const float w = s.w[qf], px = s.px[qf], py = s.py[qf], pz = s.pz[qf], x = s.x[qf], y = s.y[qf],
-                    z = s.z[qf];
-        s.w[qt] = w, s.px[qt] = px, s.py[qt] = py, s.pz[qt] = pz, s.x[qt] = x, s.y[qt] = y, s.z[qt] = z;
+        const float4 r = s.wp[qf];
+        const float x = s.x[qf], y = s.y[qf], z = s.z[qf];
+        s.wp[qt] = r;
+        s.x[qt] = x, s.y[qt] = y, s.z[qt] = z;
       }
       if (j0 + 32 >= runTo) break;
     }

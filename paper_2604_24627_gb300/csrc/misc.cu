@@ -91,15 +91,20 @@ __global__ void deposit_kernel(int ncells, int nspecies, SpeciesPtrs e, DepositC
   const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (c >= ncells) return;
   const int n = min(max(e.count[c], 0), e.cap);
-  // cap is a multiple of 4 and the slab 16-byte aligned: quads of slots
-  const float4* w4 = reinterpret_cast<const float4*>(e.w + (long)c * e.cap);
+  // quads of slots (cap is a multiple of 4); the weight is the first word of
+  // each slot's record
+  const float* wr = reinterpret_cast<const float*>(e.wp + (long)c * e.cap);
   float hi = 0.f, lo = 0.f;
   for (int q0 = lane; 4 * q0 < n; q0 += 32 * kU) {
     float4 v[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int q = q0 + 32 * u;
-      v[u] = 4 * q < n ? __ldcs(w4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (4 * q < n) {
+        const float* p = wr + 16 * q;
+        v[u] = make_float4(__ldcs(p), __ldcs(p + 4), __ldcs(p + 8), __ldcs(p + 12));
+      }
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
@@ -146,7 +151,8 @@ __global__ void moments_kernel(int ncells, SpeciesPtrs e, float* mom) {
   float W = 0.f, Px = 0.f, Py = 0.f, Pz = 0.f, U2 = 0.f;
   float wmin = 3.0e38f, wmax = -3.0e38f;
   for (int i = lane; i < n; i += 32) {
-    const float w = e.w[b + i], px = e.px[b + i], py = e.py[b + i], pz = e.pz[b + i];
+    const float4 r = e.wp[b + i];
+    const float w = r.x, px = r.y, py = r.z, pz = r.w;
     wmin = fminf(wmin, w);
     wmax = fmaxf(wmax, w);
     W += w;
@@ -226,10 +232,7 @@ __global__ void sample_kernel(SampleArgs S) {
         pz = pm * d.z;
         w = sp == 1 ? wg : S.w_a;
       }
-      P.w[b + i] = w;
-      P.px[b + i] = px;
-      P.py[b + i] = py;
-      P.pz[b + i] = pz;
+      P.wp[b + i] = make_float4(w, px, py, pz);
       P.x[b + i] = u23(b1.x);
       P.y[b + i] = u23(b1.y);
       P.z[b + i] = u23(b1.z);
@@ -297,19 +300,20 @@ __global__ void totals_kernel(int ncells, SpeciesPtrs e, SpeciesPtrs g, SpeciesP
             ne = min(max(e.count[c], 0), e.cap);
   for (int i = lane; i < na; i += 32) {
     const long k = (long)c * a.cap + i;
-    const float w = a.w[k];
-    v[0] += w;
-    v[1] += (double)w * sqrtf(a.px[k] * a.px[k] + a.py[k] * a.py[k] + a.pz[k] * a.pz[k]);
+    const float4 r = a.wp[k];
+    v[0] += r.x;
+    v[1] += (double)r.x * sqrtf(r.y * r.y + r.z * r.z + r.w * r.w);
   }
   for (int i = lane; i < ng; i += 32) {
     const long k = (long)c * g.cap + i;
-    const float w = g.w[k];
-    v[2] += w;
-    v[3] += (double)w * sqrtf(g.px[k] * g.px[k] + g.py[k] * g.py[k] + g.pz[k] * g.pz[k]);
+    const float4 r = g.wp[k];
+    v[2] += r.x;
+    v[3] += (double)r.x * sqrtf(r.y * r.y + r.z * r.z + r.w * r.w);
   }
   for (int i = lane; i < ne; i += 32) {
     const long k = (long)c * e.cap + i;
-    v[4] += 0.5 * (double)e.w[k] * (double)(e.px[k] * e.px[k] + e.py[k] * e.py[k] + e.pz[k] * e.pz[k]);
+    const float4 r = e.wp[k];
+    v[4] += 0.5 * (double)r.x * (double)(r.y * r.y + r.z * r.z + r.w * r.w);
   }
   if (lane == 0) {
     v[5] = na;

@@ -96,13 +96,15 @@ struct Cnt {
 
 __device__ __forceinline__ void write_particle(const SpeciesPtrs& s, long idx, float w, float px, float py,
                                                float pz, float x, float y, float z) {
-  s.w[idx] = w;
-  s.px[idx] = px;
-  s.py[idx] = py;
-  s.pz[idx] = pz;
+  s.wp[idx] = make_float4(w, px, py, pz);
   s.x[idx] = x;
   s.y[idx] = y;
   s.z[idx] = z;
+}
+
+// A slot's weight alone (the first word of its record).
+__device__ __forceinline__ float& slot_w(const SpeciesPtrs& s, long idx) {
+  return reinterpret_cast<float*>(s.wp + idx)[0];
 }
 
 __device__ __noinline__ void tally_add(const StepArgs& A, int ch, float w, float E) {
@@ -331,16 +333,14 @@ __device__ __noinline__ RemapOut remap_electrons(const StepArgs& A, long ebase, 
   // two quads per lane and pass, both loaded before either is stored; each
   // lane still sums its quads in ascending order
   for (int q0 = lane; q0 < nqe; q0 += 64) {
-    float4 wq[2], xq[2], yq[2], zq[2];
+    float4 v[2][4];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int q = q0 + 32 * h;
       if (q < nqe) {
         const long b = ebase + 4 * q;
-        wq[h] = ld4(A.e.w + b);
-        xq[h] = ld4(A.e.px + b);
-        yq[h] = ld4(A.e.py + b);
-        zq[h] = ld4(A.e.pz + b);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[h][j] = A.e.wp[b + j];
       }
     }
 #pragma unroll
@@ -348,22 +348,16 @@ __device__ __noinline__ RemapOut remap_electrons(const StepArgs& A, long ebase, 
       const int q = q0 + 32 * h;
       if (q >= nqe) break;
       const long b = ebase + 4 * q;
-      const float4 w4 = wq[h];
-      float4 x4 = xq[h], y4 = yq[h], z4 = zq[h];
-      float* xs = reinterpret_cast<float*>(&x4);
-      float* ys = reinterpret_cast<float*>(&y4);
-      float* zs = reinterpret_cast<float*>(&z4);
-      const float* ws = reinterpret_cast<const float*>(&w4);
       const int nj = min(4, ne - 4 * q);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         if (j >= nj) break;
-        const float w = ws[j];
-        const float nx = xs[j] + fmaf(s1, xs[j], fbx);
-        const float ny = ys[j] + fmaf(s1, ys[j], fby);
-        const float nz = zs[j] + fmaf(s1, zs[j], fbz);
-        const float ddx = nx - xs[j], ddy = ny - ys[j], ddz = nz - zs[j];
-        aE += w * (ddx * (2.f * xs[j] + ddx) + ddy * (2.f * ys[j] + ddy) + ddz * (2.f * zs[j] + ddz));
+        const float w = v[h][j].x, px = v[h][j].y, py = v[h][j].z, pz = v[h][j].w;
+        const float nx = px + fmaf(s1, px, fbx);
+        const float ny = py + fmaf(s1, py, fby);
+        const float nz = pz + fmaf(s1, pz, fbz);
+        const float ddx = nx - px, ddy = ny - py, ddz = nz - pz;
+        aE += w * (ddx * (2.f * px + ddx) + ddy * (2.f * py + ddy) + ddz * (2.f * pz + ddz));
         aPx += w * ddx;
         aPy += w * ddy;
         aPz += w * ddz;
@@ -372,20 +366,7 @@ __device__ __noinline__ RemapOut remap_electrons(const StepArgs& A, long ebase, 
         mPy += w * ny;
         mPz += w * nz;
         mU2 += w * (nx * nx + ny * ny + nz * nz);
-        xs[j] = nx;
-        ys[j] = ny;
-        zs[j] = nz;
-      }
-      if (nj == 4) {
-        *reinterpret_cast<float4*>(A.e.px + b) = x4;
-        *reinterpret_cast<float4*>(A.e.py + b) = y4;
-        *reinterpret_cast<float4*>(A.e.pz + b) = z4;
-      } else {
-        for (int j = 0; j < nj; ++j) {
-          A.e.px[b + j] = xs[j];
-          A.e.py[b + j] = ys[j];
-          A.e.pz[b + j] = zs[j];
-        }
+        A.e.wp[b + j] = make_float4(w, nx, ny, nz);
       }
     }
   }
@@ -493,8 +474,9 @@ __device__ __forceinline__ int list_append(uint4* L, int pend, int cell, int slo
 __device__ __forceinline__ void axion_full(const StepArgs& A, uint4 it) {
   const int cell = (int)it.x;
   const long idx = (long)cell * A.a.cap + it.y;
-  const float w = A.a.w[idx];
-  const AxionDecision d = axion_decide_slow(A, cell, A.mask, w, A.a.px[idx], A.a.py[idx], A.a.pz[idx], it.z, it.w);
+  const float4 v = A.a.wp[idx];
+  const float w = v.x;
+  const AxionDecision d = axion_decide_slow(A, cell, A.mask, w, v.y, v.z, v.w, it.z, it.w);
   uint32_t f = (uint32_t)d.K;
   if (d.keep) f |= DF_KEEP;
   if (d.absorbed) f |= DF_ABSORBED;
@@ -510,7 +492,8 @@ __device__ __forceinline__ void axion_full(const StepArgs& A, uint4 it) {
 __device__ __forceinline__ void photon_full(const StepArgs& A, uint4 it) {
   const int cell = (int)it.x;
   const long idx = (long)cell * A.g.cap + it.y;
-  const PhotonDecision d = photon_decide_slow(A, cell, A.g.w[idx], A.g.px[idx], A.g.py[idx], A.g.pz[idx], it.z);
+  const float4 v = A.g.wp[idx];
+  const PhotonDecision d = photon_decide_slow(A, cell, v.x, v.y, v.z, v.w, it.z);
   uint32_t f = (uint32_t)d.K;
   if (d.wrem > 0.f) f |= DF_KEEP;
   if (d.capped) f |= DF_CAPPED;
@@ -665,11 +648,10 @@ __device__ __forceinline__ void electron_chunk(const StepArgs& A, uint32_t step,
         }
       }
     } else {
-      const float4 w4 = ld4(A.e.w + b);
       const float rsum = ((eC ? ccc : 0.f) + (eB ? ccb : 0.f)) * 1.0001f;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const float wj = f4(w4, j);
+        const float wj = slot_w(A.e, b + j);
         const float lbnd = wj * rsum;
         if (j < nj && !(lbnd < A.lam_cap && u23(word(r, j)) <= 1.0f - lbnd - 1e-6f)) {
           float fac;
@@ -717,14 +699,15 @@ __device__ __forceinline__ int photon_chunk(const StepArgs& A, uint32_t step, in
     if (g < R.total) {
       const int nj = min(4, nn - 4 * q);
       const long b = (long)cell * A.g.cap + 4 * q;
-      const float4 w4 = ld4(A.g.w + b), x4 = ld4(A.g.px + b), y4 = ld4(A.g.py + b), z4 = ld4(A.g.pz + b);
+      float4 v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = A.g.wp[b + j];
       r = philox4x32_10(make_uint4(step, A.cell_base + (uint32_t)cell, (uint32_t)q, S_PRIM_FWD << 24), A.rk);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const float px = f4(x4, j), py = f4(y4, j), pz = f4(z4, j);
+        const float px = v[j].y, py = v[j].z, pz = v[j].w;
         const float p2 = px * px + py * py + pz * pz;
-        if (j < nj && !no_conversion(f4(w4, j), p2, cs, ca, u23(word(r, j)), A.lam_cap))
-          nib |= 1u << j;
+        if (j < nj && !no_conversion(v[j].x, p2, cs, ca, u23(word(r, j)), A.lam_cap)) nib |= 1u << j;
       }
     }
     pend = list_append(L, pend, cell, 4 * q, nib, r, r);
@@ -772,16 +755,17 @@ __device__ __forceinline__ int axion_chunk(const StepArgs& A, uint32_t step, int
       const int nj = min(4, nn - 4 * q);
       const uint32_t gcell = A.cell_base + (uint32_t)cell;
       const long b = (long)cell * A.a.cap + 4 * q;
-      const float4 w4 = ld4(A.a.w + b), x4 = ld4(A.a.px + b), y4 = ld4(A.a.py + b), z4 = ld4(A.a.pz + b);
+      float4 v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = A.a.wp[b + j];
       if (prim) rP = philox4x32_10(make_uint4(step, gcell, (uint32_t)q, S_PRIM_INV << 24), A.rk);
       if (bath) rA = philox4x32_10(make_uint4(step, gcell, (uint32_t)q, S_ABSORB << 24), A.rk);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const float px = f4(x4, j), py = f4(y4, j), pz = f4(z4, j);
+        const float px = v[j].y, py = v[j].z, pz = v[j].w;
         const float p2 = (px * px + py * py + pz * pz) + A.mu2;  // E^2 (m_e c^2 units)
         bool fast = !all;
-        if (fast && prim)
-          fast = no_conversion(f4(w4, j), p2, cs, cap_inv, u23(word(rP, j)), A.lam_cap);
+        if (fast && prim) fast = no_conversion(v[j].x, p2, cs, cap_inv, u23(word(rP, j)), A.lam_cap);
         if (fast && bath) fast = no_absorption(cbc, cbb, A, mask, p2 * rsqrtf(p2) * cinvT, u23(word(rA, j)));
         if (j < nj && !fast) nib |= 1u << j;
       }
@@ -1177,7 +1161,10 @@ __device__ __noinline__ void compact_tail(const SpeciesPtrs& s, long base, const
     if (mv) {
       const long src = base + i;
       const long dst = base + rm[run + __popc(m & lt)];
-      write_particle(s, dst, s.w[src], s.px[src], s.py[src], s.pz[src], s.x[src], s.y[src], s.z[src]);
+      s.wp[dst] = s.wp[src];
+      s.x[dst] = s.x[src];
+      s.y[dst] = s.y[src];
+      s.z[dst] = s.z[src];
     }
     run += __popc(m);
   }
@@ -1209,10 +1196,11 @@ __device__ __forceinline__ AxItem ax_load(const StepArgs& A, long base, int slot
   if (slot >= 0) {
     const long src = base + slot;
     t.r = A.recA[src];
-    t.w = A.a.w[src];
-    t.px = A.a.px[src];
-    t.py = A.a.py[src];
-    t.pz = A.a.pz[src];
+    const float4 v = A.a.wp[src];
+    t.w = v.x;
+    t.px = v.y;
+    t.py = v.z;
+    t.pz = v.w;
     t.x = A.a.x[src];
     t.y = A.a.y[src];
     t.z = A.a.z[src];
@@ -1228,9 +1216,10 @@ __device__ __forceinline__ PhItem ph_load(const StepArgs& A, long base, int slot
   if (slot >= 0) {
     const long src = base + slot;
     t.r = A.recG[src];
-    t.px = A.g.px[src];
-    t.py = A.g.py[src];
-    t.pz = A.g.pz[src];
+    const float4 v = A.g.wp[src];
+    t.px = v.y;
+    t.py = v.z;
+    t.pz = v.w;
     t.x = A.g.x[src];
     t.y = A.g.y[src];
     t.z = A.g.z[src];
@@ -1250,7 +1239,7 @@ __device__ __forceinline__ ElItem el_load(const StepArgs& A, long base, int slot
     t.x = A.e.x[src];
     t.y = A.e.y[src];
     t.z = A.e.z[src];
-    if (wu <= 0.f) t.w = A.e.w[src];
+    if (wu <= 0.f) t.w = slot_w(A.e, src);
   }
   return t;
 }
@@ -1291,7 +1280,7 @@ __device__ __forceinline__ int axion_outcome(const StepArgs& A, const AxItem& t,
     x64.add((double)wrem - (double)wnew, om, t.px, t.py, t.pz);
   }
   *removed = !(t.r.x & DF_KEEP);
-  if (!*removed && wnew != t.w) A.a.w[abase + t.slot] = wnew;
+  if (!*removed && wnew != t.w) slot_w(A.a, abase + t.slot) = wnew;
   return K;
 }
 
@@ -1303,7 +1292,7 @@ __device__ __forceinline__ int photon_outcome(const StepArgs& A, const PhItem& t
   cnt.add(C_CLAMP, (t.r.x & DF_OVER) ? 1u : 0u);
   cnt.add(C_EV_P, (unsigned)K);
   *removed = !(t.r.x & DF_KEEP);
-  if (K && !*removed) A.g.w[gbase + t.slot] = __uint_as_float(t.r.z);
+  if (K && !*removed) slot_w(A.g, gbase + t.slot) = __uint_as_float(t.r.z);
   return K;
 }
 
@@ -1587,10 +1576,11 @@ __device__ __forceinline__ Mover mover_load(const SpeciesPtrs& sp, long base, in
   v.dst = dst;
   if (dst >= 0) {
     const long q = base + src;
-    v.w = sp.w[q];
-    v.px = sp.px[q];
-    v.py = sp.py[q];
-    v.pz = sp.pz[q];
+    const float4 r = sp.wp[q];
+    v.w = r.x;
+    v.px = r.y;
+    v.py = r.z;
+    v.pz = r.w;
     v.x = sp.x[q];
     v.y = sp.y[q];
     v.z = sp.z[q];

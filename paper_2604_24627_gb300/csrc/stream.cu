@@ -59,14 +59,15 @@ __global__ void __launch_bounds__(kThreads) stream_move_kernel(StreamArgs a) {
     // two chunks of 32 slots per pass: both chunks' loads are issued before
     // either is stored
     for (int s0 = 0; s0 < n; s0 += 64) {
-      float px[2], py[2], pz[2], x[2], y[2], z[2];
+      float w[2], px[2], py[2], pz[2], x[2], y[2], z[2];
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
         const int slot = s0 + 32 * hh + lane;
-        px[hh] = py[hh] = pz[hh] = x[hh] = y[hh] = z[hh] = 0.f;
+        w[hh] = px[hh] = py[hh] = pz[hh] = x[hh] = y[hh] = z[hh] = 0.f;
         if (slot < n) {
           const long q = base + slot;
-          px[hh] = a.s.px[q], py[hh] = a.s.py[q], pz[hh] = a.s.pz[q];
+          const float4 r = a.s.wp[q];
+          w[hh] = r.x, px[hh] = r.y, py[hh] = r.z, pz[hh] = r.w;
           x[hh] = a.s.x[q], y[hh] = a.s.y[q], z[hh] = a.s.z[q];
         }
       }
@@ -91,12 +92,12 @@ __global__ void __launch_bounds__(kThreads) stream_move_kernel(StreamArgs a) {
           const int ii = ci + sx, jj = cj + sy, kk = ck + sz;
           if (ii < 0 || ii >= a.nx || jj < 0 || jj >= a.ny || kk < 0 || kk >= a.nz) {
             o = kStreamEscaped;
-            const double w = (double)a.s.w[q];
+            const double wd = (double)w[hh];
             const double pm = sqrt((double)px[hh] * px[hh] + (double)py[hh] * py[hh] + (double)pz[hh] * pz[hh] +
                                    (double)a.mu * a.mu);
             atomicAdd(a.stats + 0, 1.0);
-            atomicAdd(a.stats + 1, w);
-            atomicAdd(a.stats + 2, w * pm * kMeC2);
+            atomicAdd(a.stats + 1, wd);
+            atomicAdd(a.stats + 2, wd * pm * kMeC2);
           }
         }
         a.dir[q] = (uint8_t)o;
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(kThreads) stream_move_kernel(StreamArgs a) {
         const int pos = goff + run[wid][o] + __popc(m & lt);
         const long q = base + slot;
         float4* dst = reinterpret_cast<float4*>(a.buf + ((size_t)c * a.s.cap + pos) * 8);
-        dst[0] = make_float4(a.s.w[q], a.s.px[q], a.s.py[q], a.s.pz[q]);
+        dst[0] = a.s.wp[q];
         dst[1] = make_float4(a.s.x[q], a.s.y[q], a.s.z[q], 0.f);
       }
       __syncwarp();
@@ -207,7 +208,8 @@ __global__ void __launch_bounds__(kThreads) stream_place_kernel(StreamArgs a) {
         const float4 u0 = reinterpret_cast<const float4*>(row)[0];
         const float4 u1 = reinterpret_cast<const float4*>(row)[1];
         const long q = base + dst;
-        s.w[q] = u0.x, s.px[q] = u0.y, s.py[q] = u0.z, s.pz[q] = u0.w, s.x[q] = u1.x, s.y[q] = u1.y, s.z[q] = u1.z;
+        s.wp[q] = u0;
+        s.x[q] = u1.x, s.y[q] = u1.y, s.z[q] = u1.z;
       }
     }
     __syncwarp();
@@ -236,9 +238,10 @@ __global__ void __launch_bounds__(kThreads) stream_place_kernel(StreamArgs a) {
         }
         if (j < runTo && from >= 0 && to >= 0) {
           const long qf = base + from, qt = base + to;
-          const float w = s.w[qf], px = s.px[qf], py = s.py[qf], pz = s.pz[qf], x = s.x[qf], y = s.y[qf],
-                      z = s.z[qf];
-          s.w[qt] = w, s.px[qt] = px, s.py[qt] = py, s.pz[qt] = pz, s.x[qt] = x, s.y[qt] = y, s.z[qt] = z;
+          const float4 r = s.wp[qf];
+          const float x = s.x[qf], y = s.y[qf], z = s.z[qf];
+          s.wp[qt] = r;
+          s.x[qt] = x, s.y[qt] = y, s.z[qt] = z;
         }
         if (j0 + 32 >= runTo) break;
       }

@@ -66,6 +66,8 @@ int main(void) {
   P(axpic_params, threads_per_block) P(axpic_params, decide_chunk) P(axpic_params, T_mode)
   P(axpic_params, rate_model) P(axpic_params, sr_table_nne) P(axpic_params, step_branches)
   P(axpic_params, brems_gamma_shape)
+  P(axpic_species, wp) P(axpic_species, x) P(axpic_species, z) P(axpic_species, count)
+  P(axpic_species, capacity)
   return 0;
 }
 ''')
@@ -79,5 +81,6 @@ int main(void) {
     for key, val in out.items():
         if "." in key:
             T, f = key.split(".")
-            cls = _lib.PlasmaDesc if T == "axpic_plasma_desc" else _lib.Params
+            cls = {"axpic_plasma_desc": _lib.PlasmaDesc, "axpic_params": _lib.Params,
+                   "axpic_species": _lib.Species}[T]
             assert getattr(cls, f).offset == int(val), key
