@@ -450,9 +450,9 @@ def e2e_leg(pl, w, args, ncells, step0, stream, dev, world=1):
     import torch
     import torch.distributed as dist
     caps = {name: slab.capacity for name, slab in pl.slabs.items()}
-    # the slabs' contiguous arrays: the slot records (4 values a slot) and x, y, z
+    # the slabs' contiguous arrays: the slot records, 4 values a slot
     fields = [(name, f) for name, slab in pl.slabs.items() for f in slab.storage]
-    width = {f: 4 if f == "wp" else 1 for f in ("wp", "x", "y", "z")}
+    width = {"wp": 4, "xyz": 4}
     host = {(name, f): torch.empty(ncells * caps[name] * width[f], dtype=torch.float32, pin_memory=True)
             for name, f in fields}
     host_cnt = {name: torch.empty(ncells, dtype=torch.int32, pin_memory=True) for name in pl.slabs}

@@ -16,10 +16,10 @@
  * - Units: energies in keV, momenta in m_e c, times in seconds, densities in
  *   cm^-3, volumes in cm^3, couplings g_agg in GeV^-1 and g_ae dimensionless.
  * - Particles live in cell-sorted slabs. Species s of cell c occupies slots
- *   [c*capacity, c*capacity + count[c]) of its four arrays: wp holds each
- *   slot's weight and momentum as one 16-byte record {w, px, py, pz}, and x,
- *   y, z its position, as fractions of the cell in [0, 1). capacity must be
- *   a multiple of 4 and every array 16-byte aligned.
+ *   [c*capacity, c*capacity + count[c]) of its two arrays of 16-byte records:
+ *   wp holds each slot's weight and momentum {w, px, py, pz}, xyz its
+ *   position {x, y, z, unused} as fractions of the cell in [0, 1). capacity
+ *   must be a multiple of 4 and both arrays 16-byte aligned.
  * - Pointers marked "device" are CUDA device pointers owned by the caller; the
  *   library never frees them. Pointers marked "host" are read or written
  *   synchronously before the call returns. The library owns only its scratch
@@ -66,14 +66,16 @@ enum {
 };
 
 /* One particle species in cell-sorted slabs (Sec. II.D.1: weighted
- * macroparticles; Sec. II.B: p in m_e c). Device pointers: wp holds
- * ncells*capacity records of 4 binary32 values {w, px, py, pz} (slot i at
- * wp[4 i .. 4 i + 3]), x, y and z ncells*capacity binary32 values each, count
- * ncells int32. A slot's weight and momentum share one 16-byte record because
- * every decision reads them together and every event moves them together. */
+ * macroparticles; Sec. II.B: p in m_e c). Device pointers: wp and xyz hold
+ * ncells*capacity records of 4 binary32 values each, {w, px, py, pz} and
+ * {x, y, z, unused} (slot i at [4 i .. 4 i + 3]); count holds ncells int32.
+ * A slot's weight and momentum share one record because every decision
+ * reads them together, and its position is one more record because every
+ * event, streaming and merging step moves the three coordinates together.
+ * The library writes 0 into the unused word of the positions it writes. */
 typedef struct {
   float *wp;
-  float *x, *y, *z;
+  float *xyz;
   int32_t *count;
   int32_t capacity;
 } axpic_species;

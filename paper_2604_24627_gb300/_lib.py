@@ -30,9 +30,10 @@ CELL_DIAG_NAMES = ["dE", "dPx", "dPy", "dPz", "S_minus_1", "bx", "by", "bz", "va
 
 
 class Species(ctypes.Structure):
-    """axpic_species: wp holds 4 binary32 values {w, px, py, pz} a slot."""
-    _fields_ = [("wp", ctypes.c_void_p), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
-                ("z", ctypes.c_void_p), ("count", ctypes.c_void_p), ("capacity", ctypes.c_int32)]
+    """axpic_species: wp and xyz hold 4 binary32 values a slot, {w, px, py,
+    pz} and {x, y, z, unused}."""
+    _fields_ = [("wp", ctypes.c_void_p), ("xyz", ctypes.c_void_p), ("count", ctypes.c_void_p),
+                ("capacity", ctypes.c_int32)]
 
 
 class PlasmaDesc(ctypes.Structure):

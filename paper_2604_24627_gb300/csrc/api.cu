@@ -145,9 +145,7 @@ static axpic_status cuda_fail(axpic_ctx* c, cudaError_t e, const char* where) {
 static SpeciesPtrs to_ptrs(const axpic_species& s) {
   SpeciesPtrs p;
   p.wp = reinterpret_cast<float4*>(s.wp);
-  p.x = s.x;
-  p.y = s.y;
-  p.z = s.z;
+  p.xyz = reinterpret_cast<float4*>(s.xyz);
   p.count = s.count;
   p.cap = s.capacity;
   return p;
@@ -160,7 +158,7 @@ static std::string check_species(const axpic_species& s, const char* name) {
   if (s.capacity > 65532) return std::string(name) + ": capacity above 65532";
   if (!s.count) return std::string(name) + ": count is NULL";
   if (s.capacity == 0) return "";
-  const float* f[4] = {s.wp, s.x, s.y, s.z};
+  const float* f[2] = {s.wp, s.xyz};
   for (auto p : f) {
     if (!p) return std::string(name) + ": a particle array is NULL";
     if (!aligned16(p)) return std::string(name) + ": particle arrays must be 16-byte aligned";
@@ -1012,7 +1010,7 @@ static std::vector<std::pair<void*, size_t>> state_buffers(axpic_ctx* ctx, bool 
     for (const axpic_species* s : {&d.electrons, &d.photons, &d.axions}) {
       const size_t slots = n * (size_t)s->capacity * sizeof(float);
       b.emplace_back(s->wp, 4 * slots);
-      for (float* f : {s->x, s->y, s->z}) b.emplace_back(f, slots);
+      b.emplace_back(s->xyz, 4 * slots);
       b.emplace_back(s->count, n * sizeof(int32_t));
     }
     b.emplace_back(d.T_keV, n * sizeof(double));

@@ -135,10 +135,11 @@ struct RecordArgs {
   const float* uni;           // [192]: the network's cell-independent quantiles at a record's offsets
 };
 
-// A species' slabs: wp[i] = {w, px, py, pz} of slot i; positions apart.
+// A species' slabs: wp[i] = {w, px, py, pz} and xyz[i] = {x, y, z, 0} of
+// slot i.
 struct SpeciesPtrs {
   float4* wp;
-  float *x, *y, *z;
+  float4* xyz;
   int32_t* count;
   int32_t cap;
 };

@@ -51,12 +51,13 @@ __device__ void merge_group(const MergeArgs& a, long base, const uint16_t* mem, 
   Kahan W, Px, Py, Pz, E, X, Y, Z;
   // member k + 1's fields are loaded before member k's sums (m >= 3)
   long q = base + mem[0];
-  float4 r = s.wp[q];
-  float w = r.x, px = r.y, py = r.z, pz = r.w, x = s.x[q], y = s.y[q], z = s.z[q];
+  float4 r = s.wp[q], u = s.xyz[q];
+  float w = r.x, px = r.y, py = r.z, pz = r.w, x = u.x, y = u.y, z = u.z;
   for (int k = 0; k < m; ++k) {
     const long qn = base + mem[min(k + 1, m - 1)];
     r = s.wp[qn];
-    const float wn = r.x, pxn = r.y, pyn = r.z, pzn = r.w, xn = s.x[qn], yn = s.y[qn], zn = s.z[qn];
+    u = s.xyz[qn];
+    const float wn = r.x, pxn = r.y, pyn = r.z, pzn = r.w, xn = u.x, yn = u.y, zn = u.z;
     W.add(w);
     Px.add(__fmul_rn(w, px));
     Py.add(__fmul_rn(w, py));
@@ -104,9 +105,9 @@ __device__ void merge_group(const MergeArgs& a, long base, const uint16_t* mem, 
   }
   const long qa = base + sa, qb = base + sb;
   s.wp[qa] = make_float4(wh, pa[0], pa[1], pa[2]);
-  s.x[qa] = mx, s.y[qa] = my, s.z[qa] = mz;
+  s.xyz[qa] = make_float4(mx, my, mz, 0.f);
   s.wp[qb] = make_float4(wh, pb[0], pb[1], pb[2]);
-  s.x[qb] = mx, s.y[qb] = my, s.z[qb] = mz;
+  s.xyz[qb] = make_float4(mx, my, mz, 0.f);
 }
 
 __device__ __forceinline__ void prefetch_l1(const void* p) {
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(kWarpsMax * 32, 20) merge_kernel(MergeArgs a) 
       const int slot = s0 + lane;
       if (slot < n) {
         const long q = base + slot;
-        prefetch_l1(s.x + q), prefetch_l1(s.y + q), prefetch_l1(s.z + q);
+        prefetch_l1(s.xyz + q);
         const float4 r = s.wp[q];
         const float px = r.y, py = r.z, pz = r.w;
         const float p2 = __fadd_rn(__fadd_rn(__fmul_rn(px, px), __fmul_rn(py, py)), __fmul_rn(pz, pz));
@@ -219,10 +220,9 @@ __global__ void __launch_bounds__(kWarpsMax * 32, 20) merge_kernel(MergeArgs a) 
       }
       if (j < runTo && from >= 0 && to >= 0) {
         const long qf = base + from, qt = base + to;
-        const float4 r = s.wp[qf];
-        const float x = s.x[qf], y = s.y[qf], z = s.z[qf];
+        const float4 r = s.wp[qf], u = s.xyz[qf];
         s.wp[qt] = r;
-        s.x[qt] = x, s.y[qt] = y, s.z[qt] = z;
+        s.xyz[qt] = u;
       }
       if (j0 + 32 >= runTo) break;
     }

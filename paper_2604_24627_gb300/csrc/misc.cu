@@ -233,9 +233,7 @@ __global__ void sample_kernel(SampleArgs S) {
         w = sp == 1 ? wg : S.w_a;
       }
       P.wp[b + i] = make_float4(w, px, py, pz);
-      P.x[b + i] = u23(b1.x);
-      P.y[b + i] = u23(b1.y);
-      P.z[b + i] = u23(b1.z);
+      P.xyz[b + i] = make_float4(u23(b1.x), u23(b1.y), u23(b1.z), 0.f);
     }
     if (lane == 0) P.count[c] = n;
   }

@@ -97,9 +97,7 @@ struct Cnt {
 __device__ __forceinline__ void write_particle(const SpeciesPtrs& s, long idx, float w, float px, float py,
                                                float pz, float x, float y, float z) {
   s.wp[idx] = make_float4(w, px, py, pz);
-  s.x[idx] = x;
-  s.y[idx] = y;
-  s.z[idx] = z;
+  s.xyz[idx] = make_float4(x, y, z, 0.f);
 }
 
 // A slot's weight alone (the first word of its record).
@@ -1162,9 +1160,7 @@ __device__ __noinline__ void compact_tail(const SpeciesPtrs& s, long base, const
       const long src = base + i;
       const long dst = base + rm[run + __popc(m & lt)];
       s.wp[dst] = s.wp[src];
-      s.x[dst] = s.x[src];
-      s.y[dst] = s.y[src];
-      s.z[dst] = s.z[src];
+      s.xyz[dst] = s.xyz[src];
     }
     run += __popc(m);
   }
@@ -1201,9 +1197,10 @@ __device__ __forceinline__ AxItem ax_load(const StepArgs& A, long base, int slot
     t.px = v.y;
     t.py = v.z;
     t.pz = v.w;
-    t.x = A.a.x[src];
-    t.y = A.a.y[src];
-    t.z = A.a.z[src];
+    const float4 r = A.a.xyz[src];
+    t.x = r.x;
+    t.y = r.y;
+    t.z = r.z;
   }
   return t;
 }
@@ -1220,9 +1217,10 @@ __device__ __forceinline__ PhItem ph_load(const StepArgs& A, long base, int slot
     t.px = v.y;
     t.py = v.z;
     t.pz = v.w;
-    t.x = A.g.x[src];
-    t.y = A.g.y[src];
-    t.z = A.g.z[src];
+    const float4 r = A.g.xyz[src];
+    t.x = r.x;
+    t.y = r.y;
+    t.z = r.z;
   }
   return t;
 }
@@ -1236,9 +1234,10 @@ __device__ __forceinline__ ElItem el_load(const StepArgs& A, long base, int slot
   if (slot >= 0) {
     const long src = base + slot;
     t.f = A.recE[src];
-    t.x = A.e.x[src];
-    t.y = A.e.y[src];
-    t.z = A.e.z[src];
+    const float4 r = A.e.xyz[src];
+    t.x = r.x;
+    t.y = r.y;
+    t.z = r.z;
     if (wu <= 0.f) t.w = slot_w(A.e, src);
   }
   return t;
@@ -1581,9 +1580,10 @@ __device__ __forceinline__ Mover mover_load(const SpeciesPtrs& sp, long base, in
     v.px = r.y;
     v.py = r.z;
     v.pz = r.w;
-    v.x = sp.x[q];
-    v.y = sp.y[q];
-    v.z = sp.z[q];
+    const float4 u = sp.xyz[q];
+    v.x = u.x;
+    v.y = u.y;
+    v.z = u.z;
   }
   return v;
 }

@@ -66,9 +66,9 @@ __global__ void __launch_bounds__(kThreads) stream_move_kernel(StreamArgs a) {
         w[hh] = px[hh] = py[hh] = pz[hh] = x[hh] = y[hh] = z[hh] = 0.f;
         if (slot < n) {
           const long q = base + slot;
-          const float4 r = a.s.wp[q];
+          const float4 r = a.s.wp[q], u = a.s.xyz[q];
           w[hh] = r.x, px[hh] = r.y, py[hh] = r.z, pz[hh] = r.w;
-          x[hh] = a.s.x[q], y[hh] = a.s.y[q], z[hh] = a.s.z[q];
+          x[hh] = u.x, y[hh] = u.y, z[hh] = u.z;
         }
       }
 #pragma unroll
@@ -83,9 +83,11 @@ __global__ void __launch_bounds__(kThreads) stream_move_kernel(StreamArgs a) {
         int sx = 0, sy = 0, sz = 0;
         if (en > 0.f) {
           const float k = __fdiv_rn(a.kappa, en);
-          if (a.nx > 1) a.s.x[q] = advance(x[hh], __fmul_rn(k, px[hh]), &sx);
-          if (a.ny > 1) a.s.y[q] = advance(y[hh], __fmul_rn(k, py[hh]), &sy);
-          if (a.nz > 1) a.s.z[q] = advance(z[hh], __fmul_rn(k, pz[hh]), &sz);
+          float4 u = make_float4(x[hh], y[hh], z[hh], 0.f);
+          if (a.nx > 1) u.x = advance(x[hh], __fmul_rn(k, px[hh]), &sx);
+          if (a.ny > 1) u.y = advance(y[hh], __fmul_rn(k, py[hh]), &sy);
+          if (a.nz > 1) u.z = advance(z[hh], __fmul_rn(k, pz[hh]), &sz);
+          a.s.xyz[q] = u;
         }
         int o = (sz + 1) * 9 + (sy + 1) * 3 + (sx + 1);
         if (!a.periodic) {
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) stream_move_kernel(StreamArgs a) {
         const long q = base + slot;
         float4* dst = reinterpret_cast<float4*>(a.buf + ((size_t)c * a.s.cap + pos) * 8);
         dst[0] = a.s.wp[q];
-        dst[1] = make_float4(a.s.x[q], a.s.y[q], a.s.z[q], 0.f);
+        dst[1] = a.s.xyz[q];
       }
       __syncwarp();
       if (leave && (m & lt) == 0) run[wid][o] += __popc(m);  // the group's first lane
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(kThreads) stream_place_kernel(StreamArgs a) {
         const float4 u1 = reinterpret_cast<const float4*>(row)[1];
         const long q = base + dst;
         s.wp[q] = u0;
-        s.x[q] = u1.x, s.y[q] = u1.y, s.z[q] = u1.z;
+        s.xyz[q] = u1;
       }
     }
     __syncwarp();
@@ -238,10 +240,9 @@ __global__ void __launch_bounds__(kThreads) stream_place_kernel(StreamArgs a) {
         }
         if (j < runTo && from >= 0 && to >= 0) {
           const long qf = base + from, qt = base + to;
-          const float4 r = s.wp[qf];
-          const float x = s.x[qf], y = s.y[qf], z = s.z[qf];
+          const float4 r = s.wp[qf], u = s.xyz[qf];
           s.wp[qt] = r;
-          s.x[qt] = x, s.y[qt] = y, s.z[qt] = z;
+          s.xyz[qt] = u;
         }
         if (j0 + 32 >= runTo) break;
       }

@@ -15,25 +15,22 @@ FIELDS = ("w", "px", "py", "pz", "x", "y", "z")
 
 class SpeciesSlab:
     """Cell-sorted slab of one species, ncells * capacity slots: the records
-    {w, px, py, pz} of the slots (storage["wp"], 4 binary32 values a slot) and
-    their positions (storage["x"], ["y"], ["z"]). data[f] is a view of field
-    f over the slots (strided for the record's fields)."""
+    {w, px, py, pz} (storage["wp"]) and {x, y, z, unused} (storage["xyz"]) of
+    the slots, 4 binary32 values each. data[f] is a (strided) view of field f
+    over the slots."""
 
     def __init__(self, ncells, capacity, device):
         self.capacity = capacity
         n = max(ncells * capacity, 4)
-        self.storage = {"wp": torch.zeros(4 * n, dtype=torch.float32, device=device)}
-        for f in ("x", "y", "z"):
-            self.storage[f] = torch.zeros(n, dtype=torch.float32, device=device)
-        rec = self.storage["wp"].view(n, 4)
+        self.storage = {k: torch.zeros(4 * n, dtype=torch.float32, device=device) for k in ("wp", "xyz")}
+        rec, pos = self.storage["wp"].view(n, 4), self.storage["xyz"].view(n, 4)
         self.data = {f: rec[:, k] for k, f in enumerate(("w", "px", "py", "pz"))}
-        for f in ("x", "y", "z"):
-            self.data[f] = self.storage[f]
+        self.data.update({f: pos[:, k] for k, f in enumerate(("x", "y", "z"))})
         self.count = torch.zeros(max(ncells, 1), dtype=torch.int32, device=device)
 
     def struct(self):
         s = _lib.Species()
-        for f in ("wp", "x", "y", "z"):
+        for f in ("wp", "xyz"):
             setattr(s, f, self.storage[f].data_ptr())
         s.count = self.count.data_ptr()
         s.capacity = self.capacity

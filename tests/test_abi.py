@@ -66,7 +66,7 @@ int main(void) {
   P(axpic_params, threads_per_block) P(axpic_params, decide_chunk) P(axpic_params, T_mode)
   P(axpic_params, rate_model) P(axpic_params, sr_table_nne) P(axpic_params, step_branches)
   P(axpic_params, brems_gamma_shape)
-  P(axpic_species, wp) P(axpic_species, x) P(axpic_species, z) P(axpic_species, count)
+  P(axpic_species, wp) P(axpic_species, xyz) P(axpic_species, count)
   P(axpic_species, capacity)
   return 0;
 }
