@@ -600,11 +600,14 @@ axpic_status axpic_surrogate_validate(axpic_mlp *m, int32_t nT, int32_t nne, dou
 
 /* Gives a context with rate_model 2 its network: the parameters, output
  * model and a trust map from axpic_surrogate_validate's err_out (nT x nne x
- * 2 nodes, 3 floats each): a cell uses the network where the four nodes
- * around its (T, n_e) at its Z have a rate error <= tol_rate and a sampled-
- * quantile error <= tol_quantile, the table elsewhere (the error between
- * nodes can exceed the nodes': a finer grid and tolerances below the bound
- * wanted leave a margin). Copies everything (the network may be destroyed
+ * 2 nodes, 3 floats each). A node passes where its rate error is <= tol_rate
+ * and its sampled-quantile error <= tol_quantile; it is trusted where it and
+ * its eight neighbours in (T, n_e) at its Z pass (the grid's edge nodes
+ * count their neighbours inside it). A cell uses the network where the four
+ * nodes around its (T, n_e) at its Z are trusted, the table elsewhere. The
+ * error between nodes can exceed the nodes', most where it rises steeply:
+ * the neighbours' test keeps the trusted cells away from failing nodes, and
+ * a finer grid and a tolerance below the bound wanted leave a margin. Copies everything (the network may be destroyed
  * afterwards) and rebuilds the cells' records: trusted cells get the
  * network's prefactors (one tensor-core row per cell), the others the
  * table's spectral record. Synchronises. AXPIC_E_INVALID for another rate

@@ -1154,12 +1154,24 @@ axpic_status axpic_set_surrogate(axpic_ctx* ctx, axpic_mlp* m, const float* err_
                     "(their sigma and S zero, as axpic_surrogate_fit leaves them)");
       uni[96 + 31 * ch + j - 1] = mu[o];
     }
-  std::vector<uint8_t> trust((size_t)2 * nT * nne);
+  // nodes that pass, then trusted nodes: those whose 3 x 3 neighbourhood
+  // (within the grid, per Z) passes
+  std::vector<uint8_t> pass((size_t)2 * nT * nne), trust(pass.size());
+  for (size_t i = 0; i < pass.size(); ++i)
+    pass[i] = err_map[3 * i] <= tol_rate && err_map[3 * i + 1] <= tol_quantile ? 1 : 0;
   int any = 0;
-  for (size_t i = 0; i < trust.size(); ++i) {
-    trust[i] = err_map[3 * i] <= tol_rate && err_map[3 * i + 1] <= tol_quantile ? 1 : 0;
-    any |= trust[i];
-  }
+  for (int z = 0; z < 2; ++z)
+    for (int j = 0; j < nne; ++j)
+      for (int i = 0; i < nT; ++i) {
+        uint8_t t = 1;
+        for (int dj = -1; dj <= 1; ++dj)
+          for (int di = -1; di <= 1; ++di) {
+            const int jj = j + dj, ii = i + di;
+            if (jj >= 0 && jj < nne && ii >= 0 && ii < nT) t &= pass[((size_t)z * nne + jj) * nT + ii];
+          }
+        trust[((size_t)z * nne + j) * nT + i] = t;
+        any |= t;
+      }
   cudaStream_t st = ctx->stream;
   CK(cudaStreamSynchronize(st), "synchronize");
   if (ctx->sur_trust) cudaFree(ctx->sur_trust);

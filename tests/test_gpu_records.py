@@ -293,11 +293,13 @@ def test_network_with_cell_dependent_sampled_quantiles_is_rejected():
 
 def test_mixed_trust_records():
     """Three CTAs of 128 cells (the last one ragged): cells whose four trust
-    nodes pass take the network's prefactors (the oracle network's rates
-    within the bfloat16 bound, never the table model's), the others keep
-    the table's spectral record and closed-form prefactors, bit for bit as
-    the table model has them; a node fails on either its rate or its
-    sampled-quantile error."""
+    nodes are trusted (they and their neighbours pass) take the network's
+    prefactors (the oracle network's rates within the bfloat16 bound, never
+    the table model's), the others keep the table's spectral record and
+    closed-form prefactors, bit for bit as the table model has them; a node
+    fails on either its rate or its sampled-quantile error. Three columns of
+    passing nodes leave the first two trusted: the cells between them take
+    the network."""
     rng = np.random.default_rng(21)
     n = 300
     T = np.exp(rng.uniform(math.log(0.6), math.log(9.5), n))
@@ -310,9 +312,9 @@ def test_mixed_trust_records():
     net = load_net(P, mu, sigma, skip)
     nT = nne = 4
     err = np.ones((2, nne, nT, 3), dtype=np.float32)
-    err[:, :, :2, 0] = 0.0  # the nodes at the two lowest temperatures pass on the rates ...
-    err[:, :, :2, 1] = 0.0  # ... and on the sampled quantiles
-    err[:, :3, :2, 2] = 0.0  # (the Primakoff quantiles do not enter the trust)
+    err[:, :, :3, 0] = 0.0  # the nodes at the three lowest temperatures pass on the rates ...
+    err[:, :, :3, 1] = 0.0  # ... and on the sampled quantiles
+    err[:, :3, :3, 2] = 0.0  # (the Primakoff quantiles do not enter the trust)
     _lib.axpic_set_surrogate(pl.ctx, net.h, err, nT, nne, 1e-3, 1e-3)
     a = _lib.axpic_get_spectral_records(pl.ctx, 0, n)
     b = _lib.axpic_get_spectral_records(ref.ctx, 0, n)
@@ -333,7 +335,7 @@ def test_mixed_trust_records():
         tol = bf16_bound(P, sigma, T[c], ne[c]) + 2e-5
         assert d[0] <= tol[0] and d[2] <= tol[1] and d[3] <= tol[2], (c, d, tol)
     # a sampled-quantile failure alone also sends the cells to the table
-    err[:, :, :2, 1] = 1.0
+    err[:, :, :3, 1] = 1.0
     _lib.axpic_set_surrogate(pl.ctx, net.h, err, nT, nne, 1e-3, 1e-3)
     _, sa = _lib.axpic_get_cell_records(pl.ctx, 0, n)
     assert np.all(sa == 1)
@@ -429,7 +431,7 @@ def exact_rates(T, ne, prm, E):
 def test_trained_network_within_the_bound_where_trusted():
     """The network as the benchmark trains it, trusted where the four nodes of
     a 369 x 241 validation grid (log-spaced in T and n_e) around a cell are
-    within 5e-4 (half the bound)
+    trusted (they and their eight neighbours within 6e-4)
     on the rates and 1e-3 on the sampled quantiles: on 2000 random cells of
     the domain and 2000 cells of the 512 x 512 temperature bump (n_e = 6e25,
     T from 0.8 to 5.5 keV), every trusted cell's rates (Primakoff, Compton-
@@ -448,12 +450,12 @@ def test_trained_network_within_the_bound_where_trusted():
     ne = np.concatenate([10 ** rng.uniform(23.1, 25.9, 2000), np.full(2000, 6e25)])
     prm = params(2, sr_table_nkt=0, sr_table_nne=0)  # the default 128 x 64 table
     pl = make(T, ne, prm, counts=(8, 8, 4), caps=(16, 64, 64))
-    _lib.axpic_set_surrogate(pl.ctx, net.h, err, nT, nne, 5e-4, 1e-3)
+    _lib.axpic_set_surrogate(pl.ctx, net.h, err, nT, nne, 6e-4, 1e-3)
     rec, src = _lib.axpic_get_cell_records(pl.ctx, 0, n)
     srec = _lib.axpic_get_spectral_records(pl.ctx, 0, n)
     on_net = src == 0
-    # the bump's coldest cells (below about 1.2 keV at 6e25) are where the
-    # bremsstrahlung fit's brackets fall under 0.05: outside the trained region
+    # nodes above the tolerance, and their neighbours, leave about a fifth of
+    # the bump's cells to the table (78 % trusted with this fit)
     assert on_net[:2000].mean() >= 0.85 and on_net[2000:].mean() >= 0.75, (on_net[:2000].mean(), on_net[2000:].mean())
     x = np.exp(np.linspace(math.log(0.06), math.log(19.0), 12))
     worst_net, worst_tab, where = 0.0, 0.0, None
