@@ -424,12 +424,13 @@ struct DecLists {
 };
 
 // Flat quad range of a chunk: lanes < nc hold their cell's slot count n; on
-// return every lane holds its cell's first quad (qoff), the starts of cells
-// 1..C-1 (qo, cells beyond nc start at the total) and the total.
+// return lanes < nc hold their cell's first quad (qoff; the lanes beyond
+// hold INT_MAX) and every lane the total. The starts stay in the lanes: a
+// quad's cell is found by shuffles, which keeps the per-chunk state to two
+// registers.
 template <int C>
 struct QuadRange {
   int qoff, total;
-  int qo[C];
 };
 
 template <int C>
@@ -437,20 +438,17 @@ __device__ __forceinline__ QuadRange<C> quad_range(int n, int lane, int nc) {
   QuadRange<C> R;
   const int nq = lane < nc ? (n + 3) >> 2 : 0;
   R.qoff = warp_excl_scan(nq, &R.total);
-#pragma unroll
-  for (int c = 0; c < C; ++c) R.qo[c] = __shfl_sync(kFull, R.qoff, c);
-#pragma unroll
-  for (int c = 0; c < C; ++c)
-    if (c >= nc) R.qo[c] = R.total;
+  if (lane >= nc) R.qoff = 0x7fffffff;
   return R;
 }
 
-// Cell (in the chunk) of flat quad g.
+// Cell (in the chunk) of flat quad g: the last cell whose first quad is at
+// or before g (binary search over the lanes' starts).
 template <int C>
 __device__ __forceinline__ int quad_cell(const QuadRange<C>& R, int g) {
   int lc = 0;
 #pragma unroll
-  for (int c = 1; c < C; ++c) lc += g >= R.qo[c] ? 1 : 0;
+  for (int s = C / 2; s >= 1; s >>= 1) lc += g >= __shfl_sync(kFull, R.qoff, lc + s) ? s : 0;
   return lc;
 }
 
@@ -536,6 +534,11 @@ __device__ __forceinline__ void electron_chunk(const StepArgs& A, uint32_t step,
       const float lc = eC ? cap_lambda(wu * rcc, A.lam_cap, &fac, &cc) : 0.f;
       const float lb = eB ? cap_lambda(wu * rcb, A.lam_cap, &fac, &cb) : 0.f;
       lsum = lc + lb;
+      // every electron of the cell has the capped mean (rare: counted here,
+      // where the cap is found)
+      if (cc || cb)
+        atomicAdd(A.counters + (size_t)(blockIdx.x % A.ctr_rows) * kNumCounters + C_CAP,
+                  (unsigned long long)n * ((unsigned)cc + (unsigned)cb));
       // u23(w) > F0 exactly when (w >> 9) > floor(F0 2^23 - 1/2): the
       // scaling and the subtraction are exact in binary32
       thr = (int)floorf(__fsub_rn(__fmul_rn(expf(-lsum), 8388608.0f), 0.5f));
@@ -585,36 +588,33 @@ __device__ __forceinline__ void electron_chunk(const StepArgs& A, uint32_t step,
     // integer compare alone. Two quads per lane and pass, so that two
     // independent Philox chains are in flight.
     for (int g0 = 0; g0 < R.total; g0 += 64) {
-      int g[2], cell[2], q[2], nj[2], cthr[2];
-      float cls[2];
+      int lc[2], q[2];
       uint4 r[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        g[h] = g0 + 32 * h + lane;
-        const int lc = quad_cell(R, g[h]);
-        const int qb = __shfl_sync(kFull, R.qoff, lc);
-        const int nn = __shfl_sync(kFull, n, lc);
-        cthr[h] = __shfl_sync(kFull, thr, lc);
-        cls[h] = __shfl_sync(kFull, lsum, lc);
-        cell[h] = c0 + lc;
-        q[h] = g[h] - qb;
-        nj[h] = min(4, nn - 4 * q[h]);
-        r[h] = philox4x32_10(make_uint4(step, A.cell_base + (uint32_t)cell[h], (uint32_t)q[h], S_EMIT_E << 24), A.rk);
+        lc[h] = quad_cell(R, g0 + 32 * h + lane);
+        q[h] = g0 + 32 * h + lane - __shfl_sync(kFull, R.qoff, lc[h]);
+        r[h] = philox4x32_10(make_uint4(step, A.cell_base + (uint32_t)(c0 + lc[h]), (uint32_t)q[h], S_EMIT_E << 24), A.rk);
       }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        if (g[h] >= R.total) continue;
-        const long b = (long)cell[h] * A.e.cap + 4 * q[h];
+        const int nn = __shfl_sync(kFull, n, lc[h]);
+        const int cthr = __shfl_sync(kFull, thr, lc[h]);
+        const float cls = __shfl_sync(kFull, lsum, lc[h]);
+        if (g0 + 32 * h + lane >= R.total) continue;
+        const int cell = c0 + lc[h];
+        const int nj = min(4, nn - 4 * q[h]);
+        const long b = (long)cell * A.e.cap + 4 * q[h];
         uint32_t nib = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const uint32_t wj = word(r[h], j);
-          if (j < nj[h] && (int)(wj >> 9) > cthr[h]) {
-            A.recE[b + j] = (uint32_t)poisson_inv(u23(wj), cls[h]);
+          if (j < nj && (int)(wj >> 9) > cthr) {
+            A.recE[b + j] = (uint32_t)poisson_inv(u23(wj), cls);
             nib |= 1u << j;
           }
         }
-        flag_quad(A.bitsE, A.We, cell[h], q[h], nib);
+        flag_quad(A.bitsE, A.We, cell, q[h], nib);
       }
     }
     return;
@@ -753,11 +753,11 @@ __device__ __forceinline__ int axion_chunk(const StepArgs& A, uint32_t step, int
       const int nj = min(4, nn - 4 * q);
       const uint32_t gcell = A.cell_base + (uint32_t)cell;
       const long b = (long)cell * A.a.cap + 4 * q;
+      if (prim) rP = philox4x32_10(make_uint4(step, gcell, (uint32_t)q, S_PRIM_INV << 24), A.rk);
+      if (bath) rA = philox4x32_10(make_uint4(step, gcell, (uint32_t)q, S_ABSORB << 24), A.rk);
       float4 v[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) v[j] = A.a.wp[b + j];
-      if (prim) rP = philox4x32_10(make_uint4(step, gcell, (uint32_t)q, S_PRIM_INV << 24), A.rk);
-      if (bath) rA = philox4x32_10(make_uint4(step, gcell, (uint32_t)q, S_ABSORB << 24), A.rk);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float px = v[j].y, py = v[j].z, pz = v[j].w;
@@ -1411,10 +1411,14 @@ __device__ __forceinline__ void reduce_out(const Lane64& x64, PhaseOut* out) {
 
 // Absorb phase of one cell by the warp: a->gamma products, absorption and
 // weight reduction, then (fill) the axion tail fill; without it the freed
-// slots stay listed, ascending, in S.rmA (marked in S.rbA).
-__device__ __noinline__ void absorb_warp(const StepArgs& A, int cell, EvScratch& S, const uint32_t* row,
-                                         uint32_t* clr, const Cnt& cnt, int na_start, int ng_start, bool fill,
+// slots stay listed, ascending, in S.rmA (marked in S.rbA). sb is the warp's
+// scratch, carved here again: a scratch descriptor passed by reference to an
+// out-of-line call would live in local memory, written by every thread of
+// the kernel.
+__device__ __noinline__ void absorb_warp(const StepArgs& A, int cell, unsigned char* sb, const uint32_t* row,
+                                         uint32_t* clr, const Cnt cnt, int na_start, int ng_start, bool fill,
                                          PhaseOut* out) {
+  const EvScratch S = ev_carve(sb, A.a.cap, A.g.cap, A.e.cap);
   const int lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
   const bool bath = A.mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS);
@@ -1458,10 +1462,11 @@ __device__ __noinline__ void absorb_warp(const StepArgs& A, int cell, EvScratch&
 // Emit phase of one cell by the warp: gamma->a, the thermal-bath events (new
 // axions placed by D), then the photon tail fill (a->gamma products
 // included).
-__device__ __noinline__ void emit_warp(const StepArgs& A, uint32_t step, int cell, EvScratch& S,
+__device__ __noinline__ void emit_warp(const StepArgs& A, uint32_t step, int cell, unsigned char* sb,
                                        const uint32_t* rowG, uint32_t* clrG, const uint32_t* rowE, uint32_t* clrE,
-                                       const Cnt& cnt, AxDest D, int ng_tot, int ng0, int ne, float wu, float r_cc,
+                                       const Cnt cnt, AxDest D, int ng_tot, int ng0, int ne, float wu, float r_cc,
                                        float r_cb, float r_T, PhaseOut* out) {
+  const EvScratch S = ev_carve(sb, A.a.cap, A.g.cap, A.e.cap);
   const int lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
   const long abase = (long)cell * A.a.cap;
@@ -1764,9 +1769,10 @@ __device__ __forceinline__ void cell_lane(const StepArgs& A, uint32_t step, int 
 #define AXPIC_EVENT_MIN_CTAS 4
 #endif
 
-// Round trip 1: counts, per-cell constants, the exchange buffer and the mask
-// rows (staged by cp.async; cleared for the next step as soon as they are
-// read). Each phase runs first in the lanes whose cell is light for it, then
+// Round trip 1: counts and the mask rows (staged by cp.async; cleared for
+// the next step as soon as they are read). Only the cells that have an
+// electron event read the cell constants, and only those with an exchange
+// read and write their exchange buffer. Each phase runs first in the lanes whose cell is light for it, then
 // warp-wide for the heavy cells one by one; a cell's absorb phase ends before
 // its emit phase starts. The absorb and emit exchanges are added to the
 // cell's buffer in that order, whichever way the step was called.
@@ -1782,7 +1788,8 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
   if (lane < kNumCounters) warp_cnt[wid][lane] = 0ull;
   __syncwarp();
   const Cnt cnt{warp_cnt[wid]};
-  EvScratch S = ev_carve(smem + wid * ev_scratch_bytes(A.a.cap, A.g.cap, A.e.cap), A.a.cap, A.g.cap, A.e.cap);
+  unsigned char* const sbase = smem + wid * ev_scratch_bytes(A.a.cap, A.g.cap, A.e.cap);
+  const EvScratch S = ev_carve(sbase, A.a.cap, A.g.cap, A.e.cap);
   uint16_t* lA = S.lt + lane;
   uint16_t* lG = lA + 32 * kLight;
   uint16_t* lE = lG + 32 * kLight;
@@ -1815,19 +1822,6 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
     L.ng = min(max(A.g.count[cell], 0), A.g.cap);
     L.na = min(max(A.a.count[cell], 0), A.a.cap);
     if (!(PH & PH_ABSORB) && A.use_snapshot) pstart = A.photon_start[cell];
-    if (emitE) {
-      const float* rec = A.rec + (size_t)cell * kRecLen;
-      L.wu = A.mom[(size_t)cell * kMomLen + M_WU];
-      L.r_cc = rec[R_CC];
-      L.r_cb = rec[R_CB];
-      L.r_T = rec[R_T];
-    }
-    const double2* x2 = reinterpret_cast<const double2*>(A.xbuf + (size_t)cell * 4);
-    const double2 a = x2[0], b = x2[1];
-    xb[0] = a.x;
-    xb[1] = a.y;
-    xb[2] = b.x;
-    xb[3] = b.y;
   }
   const int ne = L.ne, ng_start = L.ng, na_start = L.na;
   L.ng0 = (PH & PH_ABSORB) ? ng_start : (A.use_snapshot ? min(pstart, ng_start) : ng_start);
@@ -1869,12 +1863,15 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
       hE = (PH & PH_EMIT) != 0;
     }
     if (PH & PH_ABSORB) A.photon_start[cell] = ng_start;
-    if (emitE && L.wu > 0.f) {
-      float fac;
-      bool cc = false, cb = false;
-      if (mask & AXPIC_CH_COMPTON) cap_lambda(L.wu * L.r_cc, A.lam_cap, &fac, &cc);
-      if (mask & AXPIC_CH_BREMS) cap_lambda(L.wu * L.r_cb, A.lam_cap, &fac, &cb);
-      cnt.add(C_CAP, (unsigned)ne * ((unsigned)cc + (unsigned)cb));
+    // the cell constants of the thermal-bath events, for the cells that
+    // have one (the capped means of common-weight cells are counted by the
+    // decision kernel)
+    if (emitE && (!staged || L.nflE > 0)) {
+      const float* rec = A.rec + (size_t)cell * kRecLen;
+      L.wu = A.mom[(size_t)cell * kMomLen + M_WU];
+      L.r_cc = rec[R_CC];
+      L.r_cb = rec[R_CB];
+      L.r_T = rec[R_T];
     }
   }
 
@@ -1891,13 +1888,13 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
       const int c = __shfl_sync(kFull, cell, j);
       const int na0 = __shfl_sync(kFull, na_start, j);
       PhaseOut oa, oe;
-      absorb_warp(A, c, S, staged ? S.rowA + j * S.sA : A.bitsA + (size_t)c * A.Wa,
+      absorb_warp(A, c, sbase, staged ? S.rowA + j * S.sA : A.bitsA + (size_t)c * A.Wa,
                   staged ? nullptr : A.bitsA + (size_t)c * A.Wa, cnt, na0, __shfl_sync(kFull, ng_start, j), false,
                   &oa);
       const int nrmA = na0 - oa.na;
       const uint32_t* gG = emitG ? (staged ? S.rowG + j * S.sG : A.bitsG + (size_t)c * A.Wg) : nullptr;
       const uint32_t* gE = emitE ? (staged ? S.rowE + j * S.sE : A.bitsE + (size_t)c * A.We) : nullptr;
-      emit_warp(A, step, c, S, gG, (emitG && !staged) ? A.bitsG + (size_t)c * A.Wg : nullptr, gE,
+      emit_warp(A, step, c, sbase, gG, (emitG && !staged) ? A.bitsG + (size_t)c * A.Wg : nullptr, gE,
                 (emitE && !staged) ? A.bitsE + (size_t)c * A.We : nullptr, cnt, AxDest{S.rmA, nrmA, 1, na0},
                 oa.ng, __shfl_sync(kFull, L.ng0, j), __shfl_sync(kFull, ne, j), __shfl_sync(kFull, L.wu, j),
                 __shfl_sync(kFull, L.r_cc, j), __shfl_sync(kFull, L.r_cb, j), __shfl_sync(kFull, L.r_T, j), &oe);
@@ -1925,7 +1922,7 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
       const int j = __ffs(hm) - 1;
       const int c = __shfl_sync(kFull, cell, j);
       PhaseOut o;
-      absorb_warp(A, c, S, staged ? S.rowA + j * S.sA : A.bitsA + (size_t)c * A.Wa,
+      absorb_warp(A, c, sbase, staged ? S.rowA + j * S.sA : A.bitsA + (size_t)c * A.Wa,
                   staged ? nullptr : A.bitsA + (size_t)c * A.Wa, cnt, __shfl_sync(kFull, na_start, j),
                   __shfl_sync(kFull, ng_start, j), true, &o);
       if (lane == j) {
@@ -1947,7 +1944,7 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
       PhaseOut o;
       const uint32_t* gG = emitG ? (staged ? S.rowG + j * S.sG : A.bitsG + (size_t)c * A.Wg) : nullptr;
       const uint32_t* gE = emitE ? (staged ? S.rowE + j * S.sE : A.bitsE + (size_t)c * A.We) : nullptr;
-      emit_warp(A, step, c, S, gG, (emitG && !staged) ? A.bitsG + (size_t)c * A.Wg : nullptr, gE,
+      emit_warp(A, step, c, sbase, gG, (emitG && !staged) ? A.bitsG + (size_t)c * A.Wg : nullptr, gE,
                 (emitE && !staged) ? A.bitsE + (size_t)c * A.We : nullptr, cnt,
                 AxDest{nullptr, 0, 1, __shfl_sync(kFull, L.na, j)}, __shfl_sync(kFull, L.ng, j),
                 __shfl_sync(kFull, L.ng0, j), __shfl_sync(kFull, ne, j), __shfl_sync(kFull, L.wu, j),
@@ -1967,6 +1964,12 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
     A.a.count[cell] = L.na;
     A.g.count[cell] = L.ng;
     if (xa.any || xe.any) {
+      const double2* x2 = reinterpret_cast<const double2*>(A.xbuf + (size_t)cell * 4);
+      const double2 a = x2[0], b = x2[1];
+      xb[0] = a.x;
+      xb[1] = a.y;
+      xb[2] = b.x;
+      xb[3] = b.y;
       if (xa.any) {
         xb[0] += xa.dE;
         xb[1] += xa.dPx;
