@@ -125,8 +125,9 @@ typedef struct {
   int32_t diag_enable;      /* 1: feedback writes per-cell diagnostics */
   int32_t threads_per_block;/* threads per CTA of the event kernel (32..128, one
                                warp per cell); 0: default 128 */
-  int32_t decide_chunk;     /* cells per chunk of a decision warp: 2, 4 or 8;
-                               0: default 8 (launch shape, see axpic_autotune) */
+  int32_t decide_chunk;     /* cells per chunk of a decision warp: 4, 8, 16 or
+                               32; 0: default 32 (launch shape, see
+                               axpic_autotune) */
   int32_t rate_model;       /* 0: closed forms (default); 1: exact FP32 table:
                                the full decisions' Primakoff and absorption
                                rates and the emission energies from per-cell
@@ -463,7 +464,7 @@ axpic_status axpic_run_steps(axpic_ctx *ctx, int64_t first_step, int32_t nsteps,
 axpic_status axpic_launch_shape(const axpic_ctx *ctx, int32_t *decide_chunk, int32_t *event_warps,
                                 int32_t *step_branches);
 
-/* Picks the launch shape (cells per decision chunk, 2/4/8, and warps per
+/* Picks the launch shape (cells per decision chunk, 4/8/16/32, and warps per
  * event CTA, 2 or 4) by timing trial_steps steps of the context's own state
  * for each shape (CUDA events, after one untimed step), with the step index
  * `step` and channel_mask. The context's device state (the slabs and counts

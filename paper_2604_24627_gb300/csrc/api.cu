@@ -456,8 +456,9 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
   if (per_warp > smem_limit) return bad("slab capacities too large for shared-memory scratch");
   ctx->max_warps = 4;
   while (ctx->max_warps > 1 && per_warp * ctx->max_warps > smem_limit) --ctx->max_warps;
-  if (p.decide_chunk != 0 && p.decide_chunk != 2 && p.decide_chunk != 4 && p.decide_chunk != 8)
-    return bad("decide_chunk must be 0, 2, 4 or 8");
+  if (p.decide_chunk != 0 && p.decide_chunk != 4 && p.decide_chunk != 8 && p.decide_chunk != 16 &&
+      p.decide_chunk != 32)
+    return bad("decide_chunk must be 0, 4, 8, 16 or 32");
   if (p.step_branches < 0 || p.step_branches > kMaxBranches || (p.step_branches & (p.step_branches - 1)))
     return bad("step_branches must be 0 or a power of two up to 8");
   if (p.rate_model < 0 || p.rate_model > 2) return bad("rate_model must be 0, 1 or 2");
@@ -1083,7 +1084,7 @@ axpic_status axpic_autotune(axpic_ctx* ctx, int64_t step, int32_t trial_steps, i
   cudaError_t e = copy_state(ctx, save, true);
   if (!e) e = cudaEventCreate(&e0);
   if (!e) e = cudaEventCreate(&e1);
-  for (int chunk : {2, 4, 8}) {
+  for (int chunk : {4, 8, 16, 32}) {
     int dgrid = 1;
     if (!e) e = decide_resident_ctas(chunk, &dgrid);
     for (int warps : {2, 4}) {

@@ -69,7 +69,7 @@ constexpr int kMomLen = 8;
 // that launch-shape sweeps override (c2 replayed in 8 branches: 8 cells
 // 0.178 ms per step, 4 cells 0.185, 2 cells 0.210).
 #ifndef AXPIC_DEC_CHUNK
-#define AXPIC_DEC_CHUNK 8
+#define AXPIC_DEC_CHUNK 32
 #endif
 enum { M_W = 0, M_PX, M_PY, M_PZ, M_U2, M_VAR, M_WU };
 
@@ -398,7 +398,7 @@ struct StepArgs {
   uint32_t* recE;
   int* err;
   int dec_grid;   // CTAs of the persistent decision kernel
-  int dec_chunk;  // cells per chunk of a decision warp: 2, 4 or 8
+  int dec_chunk;  // cells per chunk of a decision warp: 4, 8, 16 or 32
   uint32_t* step_dev;  // NULL, or the device step counter of a replayed graph
   // rate model: 0 the closed forms; 1 the exact table's spectral records for
   // the full decisions' rates and the emission energies; 2 the surrogate

@@ -296,7 +296,7 @@ __device__ __forceinline__ bool no_conversion(float w, float p2, float c_s, floa
   const float s = p2 * c_s;
   const float Fb = s < 2.5f ? 0.5f * s : __logf(1.0f + s);
   const float lb = w * kb * Fb;
-  return lb < lam_cap && u <= 1.0f - lb - 1e-6f;
+  return (lb < lam_cap) & (u <= 1.0f - lb - 1e-6f);
 }
 __device__ __forceinline__ float conversion_kb(float Acoef, float inv_wref, float gm) {
   return Acoef * inv_wref * (1.0001f * gm);
@@ -412,9 +412,11 @@ __device__ __forceinline__ void flag_quad(uint32_t* bits, int W, int cell, int q
 // barrier is needed. List order does not matter: records are indexed by slot.
 constexpr int kDecThreads = 256;
 constexpr int kDecWarps = kDecThreads / 32;
-// Cells per chunk: a launch-shape choice (2, 4 or 8), picked per context.
+// Cells per chunk: a launch-shape choice (4, 8, 16 or 32), picked per context. With
+// 32 every lane holds one cell's constants.
 constexpr int kChunkDefault = AXPIC_DEC_CHUNK;
-static_assert(kChunkDefault == 2 || kChunkDefault == 4 || kChunkDefault == 8, "cells per decision chunk");
+static_assert(kChunkDefault == 4 || kChunkDefault == 8 || kChunkDefault == 16 || kChunkDefault == 32,
+              "cells per decision chunk");
 constexpr int kListCap = 32 + 4 * 32;  // < 32 pending + one pass of flags
 
 // Per-warp lists: {cell, slot, decision word(s)}.
@@ -601,7 +603,8 @@ __device__ __forceinline__ void electron_chunk(const StepArgs& A, uint32_t step,
         const int nn = __shfl_sync(kFull, n, lc[h]);
         const int cthr = __shfl_sync(kFull, thr, lc[h]);
         const float cls = __shfl_sync(kFull, lsum, lc[h]);
-        if (g0 + 32 * h + lane >= R.total) continue;
+        const uint32_t m = max(max(r[h].x, r[h].y), max(r[h].z, r[h].w));
+        if (g0 + 32 * h + lane >= R.total || (int)(m >> 9) <= cthr) continue;  // no slot of the quad emits
         const int cell = c0 + lc[h];
         const int nj = min(4, nn - 4 * q[h]);
         const long b = (long)cell * A.e.cap + 4 * q[h];
@@ -705,7 +708,7 @@ __device__ __forceinline__ int photon_chunk(const StepArgs& A, uint32_t step, in
       for (int j = 0; j < 4; ++j) {
         const float px = v[j].y, py = v[j].z, pz = v[j].w;
         const float p2 = px * px + py * py + pz * pz;
-        if (j < nj && !no_conversion(v[j].x, p2, cs, ca, u23(word(r, j)), A.lam_cap)) nib |= 1u << j;
+        nib |= (uint32_t)((j < nj) & !no_conversion(v[j].x, p2, cs, ca, u23(word(r, j)), A.lam_cap)) << j;
       }
     }
     pend = list_append(L, pend, cell, 4 * q, nib, r, r);
@@ -763,9 +766,9 @@ __device__ __forceinline__ int axion_chunk(const StepArgs& A, uint32_t step, int
         const float px = v[j].y, py = v[j].z, pz = v[j].w;
         const float p2 = (px * px + py * py + pz * pz) + A.mu2;  // E^2 (m_e c^2 units)
         bool fast = !all;
-        if (fast && prim) fast = no_conversion(v[j].x, p2, cs, cap_inv, u23(word(rP, j)), A.lam_cap);
-        if (fast && bath) fast = no_absorption(cbc, cbb, A, mask, p2 * rsqrtf(p2) * cinvT, u23(word(rA, j)));
-        if (j < nj && !fast) nib |= 1u << j;
+        if (prim) fast &= no_conversion(v[j].x, p2, cs, cap_inv, u23(word(rP, j)), A.lam_cap);
+        if (bath) fast &= no_absorption(cbc, cbb, A, mask, p2 * rsqrtf(p2) * cinvT, u23(word(rA, j)));
+        nib |= (uint32_t)((j < nj) & !fast) << j;
       }
     }
     pend = list_append(L, pend, cell, 4 * q, nib, rP, rA);
@@ -2046,14 +2049,17 @@ static cudaError_t launch_decide(const StepArgs& A, int phases, cudaStream_t st)
   const int kinds = decide_kinds(A, phases);
   if (kinds == 0) return cudaSuccess;
   switch (A.dec_chunk) {
-    case 2:
-      decide_kernel<2><<<dec_blocks(A), kDecThreads, 0, st>>>(A, kinds);
+    case 4:
+      decide_kernel<4><<<dec_blocks(A), kDecThreads, 0, st>>>(A, kinds);
       break;
     case 8:
       decide_kernel<8><<<dec_blocks(A), kDecThreads, 0, st>>>(A, kinds);
       break;
+    case 16:
+      decide_kernel<16><<<dec_blocks(A), kDecThreads, 0, st>>>(A, kinds);
+      break;
     default:
-      decide_kernel<4><<<dec_blocks(A), kDecThreads, 0, st>>>(A, kinds);
+      decide_kernel<32><<<dec_blocks(A), kDecThreads, 0, st>>>(A, kinds);
       break;
   }
   return cudaGetLastError();
@@ -2085,9 +2091,10 @@ cudaError_t decide_resident_ctas(int chunk, int* out) {
   cudaError_t e;
   if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
     return e;
-  if (chunk == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, decide_kernel<2>, kDecThreads, 0);
+  if (chunk == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, decide_kernel<4>, kDecThreads, 0);
   else if (chunk == 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, decide_kernel<8>, kDecThreads, 0);
-  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, decide_kernel<4>, kDecThreads, 0);
+  else if (chunk == 16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, decide_kernel<16>, kDecThreads, 0);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, decide_kernel<32>, kDecThreads, 0);
   if (e) return e;
   *out = max(1, nb) * max(1, sms);
   return cudaSuccess;

@@ -27,7 +27,7 @@ int resident_ctas(const void* fn, int threads, size_t dyn_smem, int max_per_sm =
 // Raises (never lowers) the event kernels' dynamic shared-memory limit on the
 // current device to at least `bytes`.
 cudaError_t set_step_smem_limits(size_t bytes);
-// CTAs of the decision kernel (chunk of 2, 4 or 8 cells) that the current
+// CTAs of the decision kernel (chunk of 4, 8, 16 or 32 cells) that the current
 // device holds at once.
 cudaError_t decide_resident_ctas(int chunk, int* out);
 constexpr int kDefaultDecChunk = AXPIC_DEC_CHUNK;
