@@ -1400,6 +1400,8 @@ constexpr size_t kNaRecBytes = 16u << 20;  // decision records: cells * (16 (aca
 constexpr size_t kNaRecs = kNaBits + kNaBitsBytes;
 constexpr size_t kNaUnused = kNaRecs + kNaRecBytes;  // diagnostic/tally slots never touched
 constexpr size_t kNoAllocBytes = kNaUnused + 256;
+// the event kernel copies exchange buffers by 16-byte cp.async
+static_assert(kNaXbuf % 16 == 0, "exchange buffers 16-byte aligned");
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_na_mu;
 unsigned char* g_na_base[kNoAllocMaxDevices] = {};

@@ -102,23 +102,39 @@ __global__ void __launch_bounds__(kNetThreads) sr_cells_kernel(SrArgs a) {
   const int ntiles = (a.ncells + kNetThreads - 1) / kNetThreads;
   const bool net = a.ra.trust != nullptr;
   if (net) net_begin(&ns, sm, a.ra.img);
+  // each thread's record one tile ahead: its load runs under this tile's network
+  float4 nx[kRecLen / 4];
+  {
+    const int cell = a.cell0 + blockIdx.x * kNetThreads + tid;
+    if (blockIdx.x < ntiles && cell < a.cell0 + a.ncells) {
+      const float4* r4 = reinterpret_cast<const float4*>(a.rec + (size_t)cell * kRecLen);
+#pragma unroll
+      for (int i = 0; i < kRecLen / 4; ++i) nx[i] = r4[i];
+    }
+  }
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int cell = a.cell0 + tile * kNetThreads + tid;
     const bool valid = cell < a.cell0 + a.ncells;
     if (tid == 0) nlist = 0;
     float r[kRecLen];
+#pragma unroll
+    for (int i = 0; i < kRecLen / 4; ++i) {
+      r[4 * i] = nx[i].x;
+      r[4 * i + 1] = nx[i].y;
+      r[4 * i + 2] = nx[i].z;
+      r[4 * i + 3] = nx[i].w;
+    }
+    {
+      const int nt = tile + gridDim.x, ncell = a.cell0 + nt * kNetThreads + tid;
+      if (nt < ntiles && ncell < a.cell0 + a.ncells) {
+        const float4* r4 = reinterpret_cast<const float4*>(a.rec + (size_t)ncell * kRecLen);
+#pragma unroll
+        for (int i = 0; i < kRecLen / 4; ++i) nx[i] = r4[i];
+      }
+    }
     SrCellIn ci = {1.f, 1.f, 0.f, 24.f, 0.f};
     bool trusted = false;
     if (valid) {
-      const float4* r4 = reinterpret_cast<const float4*>(a.rec + (size_t)cell * kRecLen);
-#pragma unroll
-      for (int i = 0; i < kRecLen / 4; ++i) {
-        const float4 v = r4[i];
-        r[4 * i] = v.x;
-        r[4 * i + 1] = v.y;
-        r[4 * i + 2] = v.z;
-        r[4 * i + 3] = v.w;
-      }
       ci = sr_cell_from(r, a.ra.k_T7);
       trusted = net && sr_trusted(a.ra, ci.T, ci.lne);
     }

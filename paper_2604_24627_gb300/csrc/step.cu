@@ -1062,6 +1062,7 @@ struct EvScratch {
   uint32_t *rbA, *rbG;
   uint16_t* lt;
   uint32_t *rowA, *rowG, *rowE;  // null when some row is longer than 32 words
+  double2* xs;                    // the lanes' exchange buffers, copied in by cp.async
   int sA, sG, sE;
 };
 
@@ -1077,7 +1078,7 @@ __host__ __device__ inline size_t ev_scratch_bytes(int acap, int gcap, int ecap)
   b += kLaneListBytes;
   if (rows_staged(acap, gcap, ecap))
     b += align16(4 * 32 * (size_t)((row_words(acap) | 1) + (row_words(gcap) | 1) + (row_words(ecap) | 1)));
-  return b;
+  return b + 32 * 2 * sizeof(double2);
 }
 
 __device__ inline EvScratch ev_carve(unsigned char* base, int acap, int gcap, int ecap) {
@@ -1102,15 +1103,21 @@ __device__ inline EvScratch ev_carve(unsigned char* base, int acap, int gcap, in
     s.rowA = reinterpret_cast<uint32_t*>(base + off);
     s.rowG = s.rowA + 32 * s.sA;
     s.rowE = s.rowG + 32 * s.sG;
+    off += align16(4 * 32 * (size_t)(s.sA + s.sG + s.sE));
   } else {
     s.rowA = s.rowG = s.rowE = nullptr;
   }
+  s.xs = reinterpret_cast<double2*>(base + off);
   return s;
 }
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 // Waits for this thread's copies; the warp then synchronises to see all.
 __device__ __forceinline__ void cp_async_wait_all() {
@@ -1774,11 +1781,13 @@ __device__ __forceinline__ void cell_lane(const StepArgs& A, uint32_t step, int 
 
 // Round trip 1: counts and the mask rows (staged by cp.async; cleared for
 // the next step as soon as they are read). Only the cells that have an
-// electron event read the cell constants, and only those with an exchange
-// read and write their exchange buffer. Each phase runs first in the lanes whose cell is light for it, then
-// warp-wide for the heavy cells one by one; a cell's absorb phase ends before
-// its emit phase starts. The absorb and emit exchanges are added to the
-// cell's buffer in that order, whichever way the step was called.
+// electron event read the cell constants; only those with a flagged slot
+// read their exchange buffer (while their events run), and only those with
+// an exchange write it. Each phase runs first in the lanes whose cell is
+// light for it, then warp-wide for the heavy cells one by one; a cell's
+// absorb phase ends before its emit phase starts. The absorb and emit
+// exchanges are added to the cell's buffer in that order, whichever way the
+// step was called.
 template <int PH>
 __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1812,6 +1821,7 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
   L.wu = L.r_cc = L.r_cb = L.r_T = 0.f;
   int pstart = 0;
   double xb[4] = {0.0, 0.0, 0.0, 0.0};
+  bool xload = false;
   if (valid) {
     if (staged) {
       if (PH & PH_ABSORB)
@@ -1865,7 +1875,7 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
       hA = (PH & PH_ABSORB) != 0;
       hE = (PH & PH_EMIT) != 0;
     }
-    if (PH & PH_ABSORB) A.photon_start[cell] = ng_start;
+    if (PH == PH_ABSORB) A.photon_start[cell] = ng_start;  // read by the emit call of this step
     // the cell constants of the thermal-bath events, for the cells that
     // have one (the capped means of common-weight cells are counted by the
     // decision kernel)
@@ -1875,6 +1885,13 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
       L.r_cc = rec[R_CC];
       L.r_cb = rec[R_CB];
       L.r_T = rec[R_T];
+    }
+    // the exchange buffer of a cell with an event, loaded while its events run
+    if (!staged || (L.nflA | L.nflG | L.nflE)) {
+      xload = true;
+      const double2* x2 = reinterpret_cast<const double2*>(A.xbuf + (size_t)cell * 4);
+      cp_async16(S.xs + 2 * lane, x2);
+      cp_async16(S.xs + 2 * lane + 1, x2 + 1);
     }
   }
 
@@ -1967,12 +1984,15 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
     A.a.count[cell] = L.na;
     A.g.count[cell] = L.ng;
     if (xa.any || xe.any) {
-      const double2* x2 = reinterpret_cast<const double2*>(A.xbuf + (size_t)cell * 4);
-      const double2 a = x2[0], b = x2[1];
-      xb[0] = a.x;
-      xb[1] = a.y;
-      xb[2] = b.x;
-      xb[3] = b.y;
+      {
+        const double2* x2 = xload ? S.xs + 2 * lane : reinterpret_cast<const double2*>(A.xbuf + (size_t)cell * 4);
+        if (xload) cp_async_wait_all();
+        const double2 a = x2[0], b = x2[1];
+        xb[0] = a.x;
+        xb[1] = a.y;
+        xb[2] = b.x;
+        xb[3] = b.y;
+      }
       if (xa.any) {
         xb[0] += xa.dE;
         xb[1] += xa.dPx;
