@@ -973,27 +973,20 @@ __device__ __forceinline__ void fb_finish(const StepArgs& A, int cell, const FbC
   }
 }
 
-// Thread per cell, every load issued first;
-// cells whose exchange needs an affine remap go to a CTA list and the CTA's
-// warps remap them side by side, a warp per cell; then each thread finishes
-// its cell.
-struct RemapJob {
-  int cell, ne;
-  float s1, bx, by, bz;
-};
+// Thread per cell, every load issued first; a warp remaps the cells among
+// its 32 whose exchange needs an affine remap, one at a time with all lanes
+// (about one warp in twelve has one), then each thread finishes its cell. No
+// CTA barrier: the warps of a CTA never wait for one another's remaps. Five
+// CTAs an SM (96 registers; the remap path spills a little).
 constexpr int kFeedbackThreads = 128;
 
-__global__ void __launch_bounds__(kFeedbackThreads) feedback_kernel(StepArgs A) {
+__global__ void __launch_bounds__(kFeedbackThreads, 5) feedback_kernel(StepArgs A) {
   // a replayed graph takes its step index from the device counter: the last
   // kernel of the step advances it (no kernel of this launch reads it)
   if (A.step_dev && blockIdx.x == 0 && threadIdx.x == 0) *A.step_dev += 1u;
-  __shared__ RemapJob jobs[kFeedbackThreads];
-  __shared__ RemapOut outs[kFeedbackThreads];
-  __shared__ int njobs;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int cell = A.cell0 + blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = cell < A.cell0 + A.ncells;
-  if (threadIdx.x == 0) njobs = 0;
   FbCell f = {};
   if (valid) {
     double* xb = A.xbuf + (size_t)cell * 4;
@@ -1010,22 +1003,18 @@ __global__ void __launch_bounds__(kFeedbackThreads) feedback_kernel(StepArgs A) 
       xb[3] = 0.0;
     }
   }
-  __syncthreads();
-  int job = -1;
-  if (f.need) {
-    job = atomicAdd(&njobs, 1);
-    jobs[job] = RemapJob{cell, f.ne, (float)f.s1d, (float)f.bx, (float)f.by, (float)f.bz};
+  // the warp remaps its cells that need it one by one, all lanes together
+  RemapOut mine;
+  for (unsigned m = __ballot_sync(kFull, f.need); m; m &= m - 1u) {
+    const int j = __ffs(m) - 1;
+    const int c = __shfl_sync(kFull, cell, j);
+    const RemapOut r = remap_electrons(A, (long)c * A.e.cap, __shfl_sync(kFull, f.ne, j),
+                                       __shfl_sync(kFull, (float)f.s1d, j), __shfl_sync(kFull, (float)f.bx, j),
+                                       __shfl_sync(kFull, (float)f.by, j), __shfl_sync(kFull, (float)f.bz, j));
+    if (lane == j) mine = r;
   }
-  __syncthreads();
-  const int nj = njobs;
-  for (int k = wid; k < nj; k += kFeedbackThreads / 32) {
-    const RemapJob J = jobs[k];
-    const RemapOut r = remap_electrons(A, (long)J.cell * A.e.cap, J.ne, J.s1, J.bx, J.by, J.bz);
-    if (lane == 0) outs[k] = r;
-  }
-  __syncthreads();
   if (valid) {
-    fb_finish(A, cell, f, job >= 0 ? &outs[job] : nullptr);
+    fb_finish(A, cell, f, f.need ? &mine : nullptr);
     if (f.need) {
       atomicAdd(A.counters + C_REMAP, 1ull);
       atomicAdd(A.counters + C_REMAP_E, (unsigned long long)f.ne);
