@@ -163,7 +163,7 @@ __device__ __forceinline__ float sr_sample_x(const float* sr, int ch, float u) {
 // (Sec. II.I).
 struct AxionDecision {
   int K;
-  float wprod, wnew, om;
+  float wprod, wnew, om, w;
   bool keep, absorbed, capped, over, abs_c;
 };
 
@@ -237,13 +237,17 @@ __device__ __forceinline__ void load_rec(const StepArgs& A, int cell, float* rec
   }
 }
 
-// Out-of-line full decisions: they reload the cell's record themselves so
-// that the caller's record stays in registers.
-__device__ __noinline__ AxionDecision axion_decide_slow(const StepArgs& A, int cell, int mask, float w, float px,
-                                                        float py, float pz, uint32_t wP, uint32_t wA) {
+// Out-of-line full decisions of slot idx: they load the slot's record and
+// the cell's record together (one round trip), so that the caller's cell
+// constants stay in registers.
+__device__ __noinline__ AxionDecision axion_decide_slow(const StepArgs& A, int cell, int mask, long idx, uint32_t wP,
+                                                        uint32_t wA) {
+  const float4 v = A.a.wp[idx];
   float rec[kRecLen];
   load_rec(A, cell, rec);
-  return axion_decide(rec, cell_sr(A, cell), A, mask, w, px, py, pz, wP, wA);
+  AxionDecision d = axion_decide(rec, cell_sr(A, cell), A, mask, v.x, v.y, v.z, v.w, wP, wA);
+  d.w = v.x;
+  return d;
 }
 
 // One photon at the start of the step: gamma->a conversion (Sec. II.F,
@@ -273,11 +277,11 @@ __device__ __forceinline__ PhotonDecision photon_decide(const float* rec, const 
   return d;
 }
 
-__device__ __noinline__ PhotonDecision photon_decide_slow(const StepArgs& A, int cell, float w, float px, float py,
-                                                          float pz, uint32_t wd) {
+__device__ __noinline__ PhotonDecision photon_decide_slow(const StepArgs& A, int cell, long idx, uint32_t wd) {
+  const float4 v = A.g.wp[idx];
   float rec[kRecLen];
   load_rec(A, cell, rec);
-  return photon_decide(rec, cell_sr(A, cell), A, w, px, py, pz, wd);
+  return photon_decide(rec, cell_sr(A, cell), A, v.x, v.y, v.z, v.w, wd);
 }
 
 // Guards: cheap upper bounds that prove, without the transcendental chain,
@@ -472,9 +476,8 @@ __device__ __forceinline__ int list_append(uint4* L, int pend, int cell, int slo
 __device__ __forceinline__ void axion_full(const StepArgs& A, uint4 it) {
   const int cell = (int)it.x;
   const long idx = (long)cell * A.a.cap + it.y;
-  const float4 v = A.a.wp[idx];
-  const float w = v.x;
-  const AxionDecision d = axion_decide_slow(A, cell, A.mask, w, v.y, v.z, v.w, it.z, it.w);
+  const AxionDecision d = axion_decide_slow(A, cell, A.mask, idx, it.z, it.w);
+  const float w = d.w;
   uint32_t f = (uint32_t)d.K;
   if (d.keep) f |= DF_KEEP;
   if (d.absorbed) f |= DF_ABSORBED;
@@ -490,8 +493,7 @@ __device__ __forceinline__ void axion_full(const StepArgs& A, uint4 it) {
 __device__ __forceinline__ void photon_full(const StepArgs& A, uint4 it) {
   const int cell = (int)it.x;
   const long idx = (long)cell * A.g.cap + it.y;
-  const float4 v = A.g.wp[idx];
-  const PhotonDecision d = photon_decide_slow(A, cell, v.x, v.y, v.z, v.w, it.z);
+  const PhotonDecision d = photon_decide_slow(A, cell, idx, it.z);
   uint32_t f = (uint32_t)d.K;
   if (d.wrem > 0.f) f |= DF_KEEP;
   if (d.capped) f |= DF_CAPPED;
