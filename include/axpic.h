@@ -458,9 +458,11 @@ axpic_status axpic_run_steps(axpic_ctx *ctx, int64_t first_step, int32_t nsteps,
 
 /* The context's launch shape: cells per decision chunk, warps per event CTA
  * and the branches a replayed step runs its cells as (each may be NULL).
- * A replayed step launches 3 x branches kernels (decision, event, feedback
- * per branch; 4 x branches with a rate model's record kernel). AXPIC_E_INVALID for a NULL context. Not part of the paper's
- * method. */
+ * A replayed step launches 4 x branches kernels (decision, event, the event
+ * kernel of the cells with more flagged slots than a lane takes, feedback per
+ * branch; 5 x branches with a rate model's record kernel) and one 4-byte
+ * memset per branch. AXPIC_E_INVALID for a NULL context. Not part of the
+ * paper's method. */
 axpic_status axpic_launch_shape(const axpic_ctx *ctx, int32_t *decide_chunk, int32_t *event_warps,
                                 int32_t *step_branches);
 
@@ -491,10 +493,12 @@ axpic_status axpic_autotune(axpic_ctx *ctx, int64_t step, int32_t trial_steps, i
 axpic_status axpic_profile_begin(axpic_ctx *ctx, int32_t max_steps);
 axpic_status axpic_profile_end(axpic_ctx *ctx, double *ms_out, int32_t *steps_out);
 
-/* Comma-separated names of the kernels that one axpic_step launches, in
- * launch order: decisions, events, feedback, then, with evolved T, the rate
- * model's record kernel (sr_table_kernel for the table model, sr_cells_kernel
- * for the surrogate). The string is static; "" for a NULL context. */
+/* Comma-separated names of the profiled kernels of one axpic_step, in
+ * launch order: decisions, events (its slot also times event_heavy_kernel,
+ * launched right after it for the cells with more flagged slots than a lane
+ * takes), feedback, then, with evolved T, the rate model's record kernel
+ * (sr_table_kernel for the table model, sr_cells_kernel for the surrogate).
+ * The string is static; "" for a NULL context. */
 const char *axpic_step_kernel_names(const axpic_ctx *ctx);
 
 /* ---------------------------------------------------------------------------

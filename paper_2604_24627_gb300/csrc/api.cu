@@ -90,6 +90,8 @@ struct axpic_ctx {
   int dec_grid = 1;   // CTAs of the persistent decision kernel
   int dec_chunk = kDefaultDecChunk;
   uint32_t* step_dev = nullptr;      // step counter of replayed graphs
+  int32_t* heavy = nullptr;          // cells left to the warp-path event kernel
+  int32_t* heavy_n = nullptr;        // their count, per branch
   cudaStream_t graph_stream = nullptr;
   cudaEvent_t graph_ev[2] = {nullptr, nullptr};
   int branches = 1;                  // independent cell ranges of a replayed step
@@ -331,6 +333,8 @@ static StepArgs make_args(axpic_ctx* ctx, int64_t step, int mask) {
   A.dec_chunk = ctx->dec_chunk;
   A.ctr_rows = ctx->ctr_rows;
   A.step_dev = nullptr;
+  A.heavy = ctx->heavy;
+  A.heavy_n = ctx->heavy_n;
   A.rate_model = ctx->prm.rate_model;
   A.ra = make_record_args(ctx);
   A.mu = (float)(p.axion_mass_keV / kMeC2);
@@ -388,7 +392,7 @@ static void free_ctx(axpic_ctx* ctx) {
                   ctx->recA,   ctx->recG,  ctx->recE,     ctx->step_dev, ctx->sr, ctx->srtab,
                   ctx->sur_P,  ctx->sur_mu, ctx->sur_sigma, ctx->sur_trust, ctx->sur_img, ctx->sur_skip,
                   ctx->sr_src, ctx->sur_uni, ctx->st_dir, ctx->st_cnt, ctx->st_buf, ctx->st_stats, ctx->mg_grp,
-                  ctx->mg_removed};
+                  ctx->mg_removed, ctx->heavy, ctx->heavy_n};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete ctx;
@@ -509,6 +513,8 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
   ALLOC(ctx->tally, sizeof(double) * (3 * (size_t)p.tally_nbins + 6));
   ALLOC(ctx->counters, sizeof(unsigned long long) * kNumCounters * (size_t)ctx->ctr_rows);
   ALLOC(ctx->step_dev, sizeof(uint32_t) * kMaxBranches);
+  ALLOC(ctx->heavy, sizeof(int32_t) * (size_t)n);
+  ALLOC(ctx->heavy_n, sizeof(int32_t) * kMaxBranches);
   if (p.rate_model) {
     ALLOC(ctx->sr, sizeof(float) * kSrLen * (size_t)n);
     ALLOC(ctx->srtab, sizeof(float) * kSrTabOut * 2 * (size_t)ctx->sr_nkt * ctx->sr_nne);
@@ -870,6 +876,7 @@ static cudaError_t capture_steps(axpic_ctx* ctx, StepArgs A, int nsteps, cudaStr
     B.cell0 = c0;
     B.ncells = std::min(part, n - c0);
     B.step_dev = ctx->step_dev + nb;
+    B.heavy_n = ctx->heavy_n + nb;
     SrArgs Bsr;
     if (sra) {  // the branch's records, rebuilt after its temperature update
       Bsr = *sra;
@@ -1398,7 +1405,9 @@ constexpr size_t kNaBitsBytes = 4u << 20;  // decision bit masks: cells * (acap 
 constexpr size_t kNaBits = kNaStart + sizeof(int32_t) * kNoAllocMaxCells;
 constexpr size_t kNaRecBytes = 16u << 20;  // decision records: cells * (16 (acap + gcap) + 4 ecap) bytes
 constexpr size_t kNaRecs = kNaBits + kNaBitsBytes;
-constexpr size_t kNaUnused = kNaRecs + kNaRecBytes;  // diagnostic/tally slots never touched
+constexpr size_t kNaHeavy = kNaRecs + kNaRecBytes;  // cells left to the warp-path event kernel
+constexpr size_t kNaHeavyN = kNaHeavy + sizeof(int32_t) * kNoAllocMaxCells;
+constexpr size_t kNaUnused = kNaHeavyN + 256;  // diagnostic/tally slots never touched
 constexpr size_t kNoAllocBytes = kNaUnused + 256;
 // the event kernel copies exchange buffers by 16-byte cp.async
 static_assert(kNaXbuf % 16 == 0, "exchange buffers 16-byte aligned");
@@ -1475,6 +1484,8 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc* desc, const axpic_param
   c.tally = reinterpret_cast<double*>(base + kNaUnused);
   c.bits = reinterpret_cast<uint32_t*>(base + kNaBits);
   c.recA = reinterpret_cast<uint4*>(base + kNaRecs);
+  c.heavy = reinterpret_cast<int32_t*>(base + kNaHeavy);
+  c.heavy_n = reinterpret_cast<int32_t*>(base + kNaHeavyN);
   c.recG = c.recA + (size_t)d.ncells * d.axions.capacity;
   c.recE = reinterpret_cast<uint32_t*>(c.recG + (size_t)d.ncells * d.photons.capacity);
   c.res = carry;

@@ -400,6 +400,11 @@ struct StepArgs {
   int dec_grid;   // CTAs of the persistent decision kernel
   int dec_chunk;  // cells per chunk of a decision warp: 4, 8, 16 or 32
   uint32_t* step_dev;  // NULL, or the device step counter of a replayed graph
+  // cells a full step's event kernel leaves to the warp-path kernel, stored
+  // from index cell0 on, and their count (one counter per branch of a
+  // replayed step)
+  int32_t* heavy;
+  int32_t* heavy_n;
   // rate model: 0 the closed forms; 1 the exact table's spectral records for
   // the full decisions' rates and the emission energies; 2 the surrogate
   // network where it is trusted, the table's records elsewhere

@@ -1769,18 +1769,26 @@ __device__ __forceinline__ void cell_lane(const StepArgs& A, uint32_t step, int 
 #ifndef AXPIC_EVENT_MIN_CTAS
 #define AXPIC_EVENT_MIN_CTAS 4
 #endif
+// the full-step kernel, without the warp paths (event_heavy_kernel takes
+// them), fits more CTAs an SM
+#ifndef AXPIC_EVENT_FULL_MIN_CTAS
+#define AXPIC_EVENT_FULL_MIN_CTAS 5
+#endif
 
 // Round trip 1: counts and the mask rows (staged by cp.async; cleared for
 // the next step as soon as they are read). Only the cells that have an
 // electron event read the cell constants; only those with a flagged slot
 // read their exchange buffer (while their events run), and only those with
 // an exchange write it. Each phase runs first in the lanes whose cell is
-// light for it, then warp-wide for the heavy cells one by one; a cell's
-// absorb phase ends before its emit phase starts. The absorb and emit
+// light for it, then warp-wide for the heavy cells one by one (in a full
+// step, by event_heavy_kernel: without the warp paths this kernel holds 5
+// CTAs an SM instead of 4); a cell's absorb phase ends before its emit
+// phase starts. The absorb and emit
 // exchanges are added to the cell's buffer in that order, whichever way the
 // step was called.
 template <int PH>
-__global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepArgs A) {
+__global__ void __launch_bounds__(128, PH == 3 ? AXPIC_EVENT_FULL_MIN_CTAS : AXPIC_EVENT_MIN_CTAS)
+    event_kernel(StepArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned long long warp_cnt[4][kNumCounters];
   const int wid = threadIdx.x >> 5;
@@ -1845,32 +1853,33 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
   __syncwarp();
 
   bool hA = false, hE = false;
+  // a full step leaves a cell heavy in either phase, rows uncleared, to
+  // event_heavy_kernel
+  bool defer = false;
   if (valid) {
     if (staged) {
-      uint32_t nz;
-      if (PH & PH_ABSORB) {
-        L.nflA = scan_row(rA, na_start, lA, &nz);
-        clear_row(A.bitsA, A.Wa, cell, nz);
-      }
-      if (emitG) {
-        L.nflG = scan_row(rG, L.ng0, lG, &nz);
-        clear_row(A.bitsG, A.Wg, cell, nz);
-      }
-      if (emitE) {
-        L.nflE = scan_row(rE, ne, lE, &nz);
-        clear_row(A.bitsE, A.We, cell, nz);
-      }
+      uint32_t nzA = 0u, nzG = 0u, nzE = 0u;
+      if (PH & PH_ABSORB) L.nflA = scan_row(rA, na_start, lA, &nzA);
+      if (emitG) L.nflG = scan_row(rG, L.ng0, lG, &nzG);
+      if (emitE) L.nflE = scan_row(rE, ne, lE, &nzE);
       hA = L.nflA > kLight;
       hE = L.nflG > kLight || L.nflE > kLightE;
+      defer = PH == (PH_ABSORB | PH_EMIT) && (hA || hE);
+      if (!defer) {
+        if (PH & PH_ABSORB) clear_row(A.bitsA, A.Wa, cell, nzA);
+        if (emitG) clear_row(A.bitsG, A.Wg, cell, nzG);
+        if (emitE) clear_row(A.bitsE, A.We, cell, nzE);
+      }
     } else {
       hA = (PH & PH_ABSORB) != 0;
       hE = (PH & PH_EMIT) != 0;
+      defer = PH == (PH_ABSORB | PH_EMIT);
     }
     if (PH == PH_ABSORB) A.photon_start[cell] = ng_start;  // read by the emit call of this step
     // the cell constants of the thermal-bath events, for the cells that
     // have one (the capped means of common-weight cells are counted by the
     // decision kernel)
-    if (emitE && (!staged || L.nflE > 0)) {
+    if (!defer && emitE && (!staged || L.nflE > 0)) {
       const float* rec = A.rec + (size_t)cell * kRecLen;
       L.wu = A.mom[(size_t)cell * kMomLen + M_WU];
       L.r_cc = rec[R_CC];
@@ -1878,7 +1887,7 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
       L.r_T = rec[R_T];
     }
     // the exchange buffer of a cell with an event, loaded while its events run
-    if (!staged || (L.nflA | L.nflG | L.nflE)) {
+    if (!defer && (!staged || (L.nflA | L.nflG | L.nflE))) {
       xload = true;
       const double2* x2 = reinterpret_cast<const double2*>(A.xbuf + (size_t)cell * 4);
       cp_async16(S.xs + 2 * lane, x2);
@@ -1889,42 +1898,17 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
   Lane64 xa, xe;
   if (PH == (PH_ABSORB | PH_EMIT)) {
     // full step: a cell light in both phases is taken by its lane, any other
-    // by the whole warp; either way the new axions reuse the freed slots
-    const bool heavy = valid && (hA || hE);
-    if (valid && !heavy && (L.nflA | L.nflG | L.nflE))
+    // by event_heavy_kernel after this kernel (a warp per cell); either way
+    // the new axions reuse the freed slots
+    if (valid && !defer && (L.nflA | L.nflG | L.nflE))
       cell_lane(A, step, cell, true, true, lA, lG, lE, L, cnt, xa, xe);
-    __syncwarp();
-    for (unsigned hm = __ballot_sync(kFull, heavy); hm; hm &= hm - 1u) {
-      const int j = __ffs(hm) - 1;
-      const int c = __shfl_sync(kFull, cell, j);
-      const int na0 = __shfl_sync(kFull, na_start, j);
-      PhaseOut oa, oe;
-      absorb_warp(A, c, sbase, staged ? S.rowA + j * S.sA : A.bitsA + (size_t)c * A.Wa,
-                  staged ? nullptr : A.bitsA + (size_t)c * A.Wa, cnt, na0, __shfl_sync(kFull, ng_start, j), false,
-                  &oa);
-      const int nrmA = na0 - oa.na;
-      const uint32_t* gG = emitG ? (staged ? S.rowG + j * S.sG : A.bitsG + (size_t)c * A.Wg) : nullptr;
-      const uint32_t* gE = emitE ? (staged ? S.rowE + j * S.sE : A.bitsE + (size_t)c * A.We) : nullptr;
-      emit_warp(A, step, c, sbase, gG, (emitG && !staged) ? A.bitsG + (size_t)c * A.Wg : nullptr, gE,
-                (emitE && !staged) ? A.bitsE + (size_t)c * A.We : nullptr, cnt, AxDest{S.rmA, nrmA, 1, na0},
-                oa.ng, __shfl_sync(kFull, L.ng0, j), __shfl_sync(kFull, ne, j), __shfl_sync(kFull, L.wu, j),
-                __shfl_sync(kFull, L.r_cc, j), __shfl_sync(kFull, L.r_cb, j), __shfl_sync(kFull, L.r_T, j), &oe);
-      // freed slots left over: closed from the tail
-      if (oe.np < nrmA) compact_tail(A.a, (long)c * A.a.cap, S.rmA + oe.np, S.rbA, oe.na, na0);
-      if (lane == j) {
-        L.na = oe.na;
-        L.ng = oe.ng;
-        xa.dE = oa.x[0];
-        xa.dPx = oa.x[1];
-        xa.dPy = oa.x[2];
-        xa.dPz = oa.x[3];
-        xa.any = oa.any;
-        xe.dE = oe.x[0];
-        xe.dPx = oe.x[1];
-        xe.dPy = oe.x[2];
-        xe.dPz = oe.x[3];
-        xe.any = oe.any;
-      }
+    // the heavy cells are listed for event_heavy_kernel, from index cell0
+    const unsigned hm = __ballot_sync(kFull, defer);
+    if (hm) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(A.heavy_n, __popc(hm));
+      base = __shfl_sync(kFull, base, 0);
+      if (defer) A.heavy[A.cell0 + base + __popc(hm & ((1u << lane) - 1u))] = cell;
     }
   } else if (PH == PH_ABSORB) {
     if (valid && !hA && L.nflA) cell_lane(A, step, cell, true, false, lA, lG, lE, L, cnt, xa, xe);
@@ -1971,7 +1955,7 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
       }
     }
   }
-  if (valid) {
+  if (valid && !defer) {
     A.a.count[cell] = L.na;
     A.g.count[cell] = L.ng;
     if (xa.any || xe.any) {
@@ -2010,6 +1994,84 @@ __global__ void __launch_bounds__(128, AXPIC_EVENT_MIN_CTAS) event_kernel(StepAr
 }
 
 
+// The full step of the cells the event kernel listed as heavy (more flagged
+// slots in a phase than a lane takes): a warp per cell, persistent over the
+// list, with the mask rows read and cleared in global memory. Cells are
+// independent within a step, so each gets what the warp path inside the
+// event kernel gave it; the list order does not matter.
+constexpr int kHeavyGrid = 608;  // 4 CTAs on each of the 152 SMs
+
+__global__ void __launch_bounds__(128) event_heavy_kernel(StepArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned long long warp_cnt[4][kNumCounters];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  if (lane < kNumCounters) warp_cnt[wid][lane] = 0ull;
+  __syncwarp();
+  const Cnt cnt{warp_cnt[wid]};
+  unsigned char* const sbase = smem + wid * ev_scratch_bytes(A.a.cap, A.g.cap, A.e.cap);
+  const EvScratch S = ev_carve(sbase, A.a.cap, A.g.cap, A.e.cap);
+  const uint32_t step = step_of(A);
+  const bool emitG = (A.mask & AXPIC_CH_PRIMAKOFF) != 0;
+  const bool emitE = (A.mask & (AXPIC_CH_COMPTON | AXPIC_CH_BREMS)) != 0;
+  const int n = *A.heavy_n;
+  for (int k = blockIdx.x * nw + wid; k < n; k += gridDim.x * nw) {
+    const int c = A.heavy[A.cell0 + k];
+    const int na0 = min(max(A.a.count[c], 0), A.a.cap);
+    const int ng0 = min(max(A.g.count[c], 0), A.g.cap);
+    const int ne = min(max(A.e.count[c], 0), A.e.cap);
+    float wu = 0.f, r_cc = 0.f, r_cb = 0.f, r_T = 0.f;
+    if (emitE) {
+      const float* rec = A.rec + (size_t)c * kRecLen;
+      wu = A.mom[(size_t)c * kMomLen + M_WU];
+      r_cc = rec[R_CC];
+      r_cb = rec[R_CB];
+      r_T = rec[R_T];
+    }
+    uint32_t* rowA = A.bitsA + (size_t)c * A.Wa;
+    uint32_t* rowG = emitG ? A.bitsG + (size_t)c * A.Wg : nullptr;
+    uint32_t* rowE = emitE ? A.bitsE + (size_t)c * A.We : nullptr;
+    PhaseOut oa, oe;
+    absorb_warp(A, c, sbase, rowA, rowA, cnt, na0, ng0, false, &oa);
+    const int nrmA = na0 - oa.na;
+    emit_warp(A, step, c, sbase, rowG, rowG, rowE, rowE, cnt, AxDest{S.rmA, nrmA, 1, na0}, oa.ng, ng0, ne, wu, r_cc,
+              r_cb, r_T, &oe);
+    // freed slots left over: closed from the tail
+    if (oe.np < nrmA) compact_tail(A.a, (long)c * A.a.cap, S.rmA + oe.np, S.rbA, oe.na, na0);
+    if (lane == 0) {
+      A.a.count[c] = oe.na;
+      A.g.count[c] = oe.ng;
+      if (oa.any || oe.any) {
+        double* xb = A.xbuf + (size_t)c * 4;
+        double x0 = xb[0], x1 = xb[1], x2 = xb[2], x3 = xb[3];
+        if (oa.any) {
+          x0 += oa.x[0];
+          x1 += oa.x[1];
+          x2 += oa.x[2];
+          x3 += oa.x[3];
+        }
+        if (oe.any) {
+          x0 += oe.x[0];
+          x1 += oe.x[1];
+          x2 += oe.x[2];
+          x3 += oe.x[3];
+        }
+        xb[0] = x0;
+        xb[1] = x1;
+        xb[2] = x2;
+        xb[3] = x3;
+      }
+    }
+    __syncwarp();
+  }
+  __syncwarp();
+  if (lane < kNumCounters) {
+    const unsigned long long v = warp_cnt[wid][lane];
+    if (v) atomicAdd(A.counters + (size_t)(blockIdx.x % A.ctr_rows) * kNumCounters + lane, v);
+    if (lane == C_DROP && v) atomicOr(A.err, ERR_CAPACITY);
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 size_t step_smem_per_warp(int acap, int gcap, int ecap) { return ev_scratch_bytes(acap, gcap, ecap); }
 
@@ -2035,7 +2097,17 @@ template <int PH>
 static cudaError_t launch_events(const StepArgs& A, int warps, cudaStream_t st) {
   const size_t per = ev_scratch_bytes(A.a.cap, A.g.cap, A.e.cap);
   const int grid = (A.ncells + 32 * warps - 1) / (32 * warps);
+  if (PH == (PH_ABSORB | PH_EMIT)) {
+    cudaError_t e = cudaMemsetAsync(A.heavy_n, 0, sizeof(int32_t), st);
+    if (e) return e;
+  }
   event_kernel<PH><<<grid, warps * 32, per * warps, st>>>(A);
+  if (PH == (PH_ABSORB | PH_EMIT)) {
+    // persistent over the heavy list: a warp per cell, at most one warp per
+    // cell of the launch and kHeavyGrid CTAs
+    const int hgrid = max(1, min((A.ncells + warps - 1) / warps, kHeavyGrid));
+    event_heavy_kernel<<<hgrid, warps * 32, per * warps, st>>>(A);
+  }
   return cudaGetLastError();
 }
 
@@ -2162,7 +2234,8 @@ cudaError_t set_step_smem_limits(size_t bytes) {
   const int b = (int)bytes;
   if ((e = cudaFuncSetAttribute(event_kernel<PH_ABSORB>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) ||
       (e = cudaFuncSetAttribute(event_kernel<PH_EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) ||
-      (e = cudaFuncSetAttribute(event_kernel<PH_ABSORB | PH_EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
+      (e = cudaFuncSetAttribute(event_kernel<PH_ABSORB | PH_EMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)) ||
+      (e = cudaFuncSetAttribute(event_heavy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
     return e;
   if (cur) *cur = bytes;
   return cudaSuccess;
