@@ -126,7 +126,9 @@ typedef struct {
   int32_t threads_per_block;/* threads per CTA of the event kernel (32..128, one
                                warp per cell); 0: default 128 */
   int32_t decide_chunk;     /* cells per chunk of a decision warp: 4, 8, 16 or
-                               32; 0: default 32 (launch shape, see
+                               32; 0: the largest of 32, 16 and 8 that still
+                               gives every resident decision warp a chunk of
+                               the plasma's cells, else 4 (launch shape, see
                                axpic_autotune) */
   int32_t rate_model;       /* 0: closed forms (default); 1: exact FP32 table:
                                the full decisions' Primakoff and absorption

@@ -554,7 +554,7 @@ axpic_status axpic_init_plasma(axpic_ctx** out, const axpic_plasma_desc* desc, c
       (e = cudaMemsetAsync(ctx->err, 0, sizeof(int), st)) ||
       (e = cudaMemsetAsync(ctx->bits, 0, sizeof(uint32_t) * (bit_words > 0 ? bit_words : 1), st)) ||
       (e = set_step_smem_limits(per_warp * ctx->max_warps)) ||
-      (e = decide_resident_ctas(ctx->dec_chunk, &ctx->dec_grid)) ||
+      (e = decide_shape(p.decide_chunk, n, &ctx->dec_chunk, &ctx->dec_grid)) ||
       (e = launch_records(n, d.nspecies, ctx->cc, d.T_keV, d.n_ion, ctx->rec, ctx->err, st)) ||
       (e = launch_moments(n, to_ptrs(d.electrons), ctx->mom, st)) ||
       (p.rate_model && (e = cudaMemcpyAsync(ctx->srtab, srtab.data(), srtab.size() * sizeof(float),
@@ -1494,14 +1494,18 @@ axpic_status axpic_step_noalloc(const axpic_plasma_desc* desc, const axpic_param
   c.ctr_rows = std::max(1, std::min(kCounterRows, (d.ncells + 3) / 4));
   c.dec_chunk = kDefaultDecChunk;
   fold_constants(&c);
+  cudaError_t e = decide_shape(p.decide_chunk, d.ncells, &c.dec_chunk, &c.dec_grid);
+  if (e) {
+    fprintf(stderr, "axpic_step_noalloc: %s\n", cudaGetErrorString(e));
+    return AXPIC_E_CUDA;
+  }
   const StepArgs A = make_args(&c, step, channel_mask);
   int h_err = 0;
-  cudaError_t e;
   if ((e = cudaMemsetAsync(c.err, 0, sizeof(int), st)) ||
       (e = cudaMemsetAsync(c.counters, 0, sizeof(unsigned long long) * kNumCounters * (size_t)c.ctr_rows, st)) ||
       (e = cudaMemsetAsync(c.xbuf, 0, sizeof(double) * 4 * (size_t)d.ncells, st)) ||
       (e = cudaMemsetAsync(c.bits, 0, bit_bytes > 0 ? bit_bytes : 4, st)) ||
-      (e = set_step_smem_limits(per_warp * kNoAllocWarps)) || (e = decide_resident_ctas(c.dec_chunk, &c.dec_grid)) ||
+      (e = set_step_smem_limits(per_warp * kNoAllocWarps)) ||
       (e = launch_records(d.ncells, d.nspecies, c.cc, d.T_keV, d.n_ion, c.rec, c.err, st)) ||
       (e = launch_moments(d.ncells, to_ptrs(d.electrons), c.mom, st)) ||
       (e = launch_step(PH_ALL, A, kNoAllocWarps, st)) ||

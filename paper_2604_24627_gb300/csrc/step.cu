@@ -1999,7 +1999,7 @@ __global__ void __launch_bounds__(128, PH == 3 ? AXPIC_EVENT_FULL_MIN_CTAS : AXP
 // list, with the mask rows read and cleared in global memory. Cells are
 // independent within a step, so each gets what the warp path inside the
 // event kernel gave it; the list order does not matter.
-constexpr int kHeavyGrid = 608;  // 4 CTAs on each of the 152 SMs
+constexpr int kHeavyGrid = 152;  // one CTA on each of the 152 SMs
 
 __global__ void __launch_bounds__(128) event_heavy_kernel(StepArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -2167,6 +2167,25 @@ __global__ void set_step_kernel(uint32_t* p, uint32_t v, int n) {
 cudaError_t launch_set_step(uint32_t* p, uint32_t v, int n, cudaStream_t st) {
   set_step_kernel<<<1, 1, 0, st>>>(p, v, n);
   return cudaGetLastError();
+}
+
+cudaError_t decide_shape(int requested, int ncells, int* chunk, int* grid) {
+  int c = requested;
+  if (c == 0) {
+    int g = 1;
+    const cudaError_t e = decide_resident_ctas(32, &g);
+    if (e) return e;
+    const long warps = (long)g * kDecWarps;
+    c = 4;
+    for (int k : {32, 16, 8}) {
+      if ((long)ncells / k >= warps) {
+        c = k;
+        break;
+      }
+    }
+  }
+  *chunk = c;
+  return decide_resident_ctas(c, grid);
 }
 
 cudaError_t decide_resident_ctas(int chunk, int* out) {

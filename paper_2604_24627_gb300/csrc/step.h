@@ -30,6 +30,10 @@ cudaError_t set_step_smem_limits(size_t bytes);
 // CTAs of the decision kernel (chunk of 4, 8, 16 or 32 cells) that the current
 // device holds at once.
 cudaError_t decide_resident_ctas(int chunk, int* out);
+// The decision kernel's cells per chunk (requested, or 0 for the default:
+// the largest of 32, 16 and 8 that still gives every resident decision warp
+// a chunk of the ncells, else 4) and its persistent grid.
+cudaError_t decide_shape(int requested, int ncells, int* chunk, int* grid);
 constexpr int kDefaultDecChunk = AXPIC_DEC_CHUNK;
 // Writes v to the n device step counters p[0, n) (one thread).
 cudaError_t launch_set_step(uint32_t* p, uint32_t v, int n, cudaStream_t st);
