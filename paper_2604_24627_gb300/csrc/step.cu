@@ -1044,8 +1044,9 @@ __global__ void __launch_bounds__(kFeedbackThreads, 5) feedback_kernel(StepArgs 
 // (electrons: kLightE, each event with its own Philox block).
 constexpr int kLight = 8;
 constexpr int kLightE = 4;
-// Flagged slots and tail movers per species whose loads go out together.
-constexpr int kLoad = 2;
+// Flagged slots and tail movers per species whose loads go out together
+// (one: more in flight cost registers, and occupancy gained more).
+constexpr int kLoad = 1;
 constexpr size_t kLaneListBytes = 3 * kLight * 32 * sizeof(uint16_t);
 
 struct EvScratch {
@@ -1772,7 +1773,7 @@ __device__ __forceinline__ void cell_lane(const StepArgs& A, uint32_t step, int 
 // the full-step kernel, without the warp paths (event_heavy_kernel takes
 // them), fits more CTAs an SM
 #ifndef AXPIC_EVENT_FULL_MIN_CTAS
-#define AXPIC_EVENT_FULL_MIN_CTAS 5
+#define AXPIC_EVENT_FULL_MIN_CTAS 6
 #endif
 
 // Round trip 1: counts and the mask rows (staged by cp.async; cleared for
@@ -1781,9 +1782,9 @@ __device__ __forceinline__ void cell_lane(const StepArgs& A, uint32_t step, int 
 // read their exchange buffer (while their events run), and only those with
 // an exchange write it. Each phase runs first in the lanes whose cell is
 // light for it, then warp-wide for the heavy cells one by one (in a full
-// step, by event_heavy_kernel: without the warp paths this kernel holds 5
-// CTAs an SM instead of 4); a cell's absorb phase ends before its emit
-// phase starts. The absorb and emit
+// step, by event_heavy_kernel: without the warp paths, and with one load of
+// each kind in flight, this kernel holds 6 CTAs an SM instead of 4); a
+// cell's absorb phase ends before its emit phase starts. The absorb and emit
 // exchanges are added to the cell's buffer in that order, whichever way the
 // step was called.
 template <int PH>

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) stream_place_kernel(StreamArgs a) {
       const int e = __shfl_sync(kAll, excl, sel);
       const int gs = __shfl_sync(kAll, g, sel), ss = __shfl_sync(kAll, src, sel);
       int dst = n + (t - H);
-      const int need = min(t0 + 32, H);  // freed slots this round: indices t0 .. need - 1
+      const int need = min(t0 + 32, H);  // freed slots of this pass: indices t0 .. need - 1
       if (t0 < need) {
         int run = 0;
         for (int s0 = 0; s0 < n && run < need; s0 += 32) {
